@@ -1,0 +1,670 @@
+/*
+ * oracle.c -- plain, slow, FP64 CPU reference of the electron-swarm Monte
+ * Carlo step loop of "Betaboltz: a Monte-Carlo simulation tool for gas
+ * scattering processes" (Renda, Ciubotaru, Banu; arXiv:1901.08140).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the CPU
+ * baseline leg of the benchmark may load this library.  It shares no code,
+ * header, table or constant with the CUDA path and never calls it.
+ *
+ * Everything is FP64 and follows the paper's steps in order, one particle at
+ * a time, one free flight at a time:
+ *   - free flight by the null-collision technique, Eq. (3) random_time,
+ *     null test Eq. (4) null_fraction (Sec. 2);
+ *   - real collision frequency nu(eps) channel by channel, Eq. (2) frequency,
+ *     each table linearly interpolated (Sec. 5) and extended per Sec. 2.2,
+ *     Eqs. (12)-(14);
+ *   - classical motion in uniform static E and B (UniformFieldClassic, Sec. 3.6);
+ *   - scattering angle isotropic or screened Coulomb, Eq. (5) collision_angle;
+ *   - energy exchange Eq. (8) delta_energy_ela and Eq. (9) delta_energy_ine,
+ *     attachment as a plastic collision and ionization with an energy split
+ *     (Sec. 2);
+ *   - fail detection and revert to the last real collision (Sec. 6).
+ * Random numbers come from Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11),
+ * implemented here from its published definition.
+ *
+ * Readings of points the paper leaves open (each is listed with its reason in
+ * the design notes): force axis +z with W > 0; the flight uniform is used
+ * directly as 1-R; fail => revert and raise the particle's trial frequency to
+ * 1.25 nu; radicand of Eq. (9) clamped at 0; the ionization remainder is split
+ * uniformly between primary and secondary; a dummy attachment leaves the
+ * electron at rest; an inelastic table that starts above its threshold rises
+ * linearly from (threshold, 0).
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* CODATA 2018 */
+#define OR_QE 1.602176634e-19      /* elementary charge [C] */
+#define OR_ME 9.1093837015e-31     /* electron mass [kg] */
+#define OR_HARTREE_EV 27.211386245988
+#define OR_TD 1e-21                /* 1 Townsend [V m^2] */
+#define OR_PI 3.14159265358979323846
+
+enum { OR_ELASTIC = 0, OR_EXCITATION = 1, OR_ATTACHMENT = 2, OR_IONIZATION = 3 };
+enum { OR_ISOTROPIC = 0, OR_SCREENED_COULOMB = 1 };
+enum { OR_DEC_FAIL = -2, OR_DEC_NULL = -1 };
+enum { OR_ST_DONE = 0, OR_ST_TIME = 1, OR_ST_STEPS = 2, OR_ST_TRIAL = 3 };
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10 (Salmon et al., SC'11, Sec. 4): 10 rounds of the Philox      */
+/* S-P network on a 4x32-bit counter with a 2x32-bit key bumped by the Weyl   */
+/* constants after each round.                                                */
+/* ------------------------------------------------------------------------ */
+void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; ++r) {
+        uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* 24-bit uniform on the open interval (0,1): ((w >> 8) + 1/2) / 2^24. */
+double or_uniform(uint32_t w) { return ((double)(w >> 8) + 0.5) * (1.0 / 16777216.0); }
+
+static void draw4(uint64_t seed, uint64_t id, uint32_t step, uint32_t sub, double u[4])
+{
+    uint32_t ctr[4] = {(uint32_t)id, (uint32_t)(id >> 32), step, sub};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t w[4];
+    or_philox4x32_10(ctr, key, w);
+    for (int i = 0; i < 4; ++i) u[i] = or_uniform(w[i]);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Mixture: per-channel tables, kept exactly as given.                        */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int gas, kind, n;
+    double threshold;
+    double *e, *s;
+} or_channel;
+
+typedef struct {
+    double M, n;
+    int angular;
+} or_gas;
+
+typedef struct {
+    int n_gas, n_ch;
+    or_gas *gas;
+    or_channel *ch;
+    double n_total;
+    double eps_cap, nu_max, eps_at_max;
+} or_mixture;
+
+/* sigma of one channel at eps [eV] -- Sec. 5 (linear interpolation inside the
+ * table) and Sec. 2.2 (extensions): elastic tables extend to the left with
+ * their first value, inelastic ones are zero below threshold; to the right a
+ * power law sigma = A eps^K through the last two points, Eqs. (12)-(14).
+ * Where either of the two points is zero the power law is undefined and the
+ * last value is continued. */
+double or_sigma(const or_mixture *m, int c, double eps)
+{
+    const or_channel *ch = &m->ch[c];
+    const double *e = ch->e, *s = ch->s;
+    int n = ch->n;
+    if (ch->kind != OR_ELASTIC) {
+        if (eps < ch->threshold) return 0.0;
+        if (eps < e[0]) return s[0] * (eps - ch->threshold) / (e[0] - ch->threshold);
+    } else if (eps < e[0]) {
+        return s[0];
+    }
+    if (eps >= e[n - 1]) {
+        if (n < 2 || eps == e[n - 1]) return s[n - 1];
+        if (s[n - 1] > 0.0 && s[n - 2] > 0.0) {
+            double K = log(s[n - 1] / s[n - 2]) / log(e[n - 1] / e[n - 2]);
+            double A = s[n - 1] / pow(e[n - 1], K);
+            return A * pow(eps, K);
+        }
+        return s[n - 1];
+    }
+    int lo = 0, hi = n - 1; /* e[lo] <= eps < e[hi] */
+    while (hi - lo > 1) {
+        int mid = (lo + hi) / 2;
+        if (e[mid] <= eps) lo = mid; else hi = mid;
+    }
+    return s[lo] + (s[hi] - s[lo]) * (eps - e[lo]) / (e[hi] - e[lo]);
+}
+
+/* Eq. (2): nu(eps) = sqrt(2 eps / m) * sum_k n_k (sigma_k + sum_i sigma_ki).
+ * The sum runs gas by gas, channel by channel, adding n_k sigma_kj one term at
+ * a time -- the same order in which the channel is later chosen, so that the
+ * last cumulative term equals nu exactly. */
+static double speed_of(double eps) { return sqrt(2.0 * eps * OR_QE / OR_ME); }
+
+double or_density_sum(const or_mixture *m, double eps)
+{
+    double S = 0.0;
+    for (int c = 0; c < m->n_ch; ++c) S += m->gas[m->ch[c].gas].n * or_sigma(m, c, eps);
+    return S;
+}
+
+double or_nu(const or_mixture *m, double eps) { return speed_of(eps) * or_density_sum(m, eps); }
+
+/* Channel choice of a real collision: the first channel j whose cumulative
+ * frequency sqrt(2 eps/m) sum_{l<=j} n sigma_l reaches r (0 < r <= nu). */
+int or_select_channel(const or_mixture *m, double eps, double r)
+{
+    double v = speed_of(eps), cum = 0.0;
+    for (int c = 0; c < m->n_ch; ++c) {
+        cum += m->gas[m->ch[c].gas].n * or_sigma(m, c, eps);
+        if (v * cum >= r) return c;
+    }
+    return m->n_ch - 1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Trial frequency (Sec. 6.2, LazyTrialFrequency, made exact): the maximum of */
+/* nu(eps) over [0, eps_cap].  Between consecutive breakpoints (table points  */
+/* and thresholds) where no channel is in its power-law tail the density sum  */
+/* is linear, S = a + b eps, so sqrt(eps) (a + b eps) peaks at an end or at   */
+/* eps* = -a/(3b).  Pieces with a tail are searched by dense sampling plus a  */
+/* golden-section refinement.                                                 */
+/* ------------------------------------------------------------------------ */
+static int cmp_double(const void *a, const void *b)
+{
+    double x = *(const double *)a, y = *(const double *)b;
+    return (x > y) - (x < y);
+}
+
+static void consider(const or_mixture *m, double eps, double *best, double *best_eps)
+{
+    if (!(eps >= 0.0)) return;
+    double v = or_nu(m, eps);
+    if (v > *best) { *best = v; *best_eps = eps; }
+}
+
+static double linear_piece_value(double a, double b, double eps) { return sqrt(eps) * (a + b * eps); }
+
+void or_majorant(or_mixture *m, double eps_cap)
+{
+    int total = 0;
+    for (int c = 0; c < m->n_ch; ++c) total += m->ch[c].n + 1;
+    double *bp = (double *)malloc(sizeof(double) * (size_t)(total + 2));
+    int nb = 0;
+    for (int c = 0; c < m->n_ch; ++c) {
+        for (int i = 0; i < m->ch[c].n; ++i)
+            if (m->ch[c].e[i] < eps_cap) bp[nb++] = m->ch[c].e[i];
+        if (m->ch[c].kind != OR_ELASTIC && m->ch[c].threshold < eps_cap) bp[nb++] = m->ch[c].threshold;
+    }
+    bp[nb++] = eps_cap;
+    qsort(bp, (size_t)nb, sizeof(double), cmp_double);
+    int u = 0;
+    for (int i = 0; i < nb; ++i)
+        if (u == 0 || bp[i] != bp[u - 1]) bp[u++] = bp[i];
+    nb = u;
+
+    double best = 0.0, best_eps = 0.0;
+    /* below the first breakpoint the density sum is constant (its value at 0),
+     * so nu grows with eps up to the breakpoint */
+    {
+        double v = speed_of(bp[0]) * or_density_sum(m, 0.0);
+        if (v > best) { best = v; best_eps = bp[0]; }
+    }
+    consider(m, bp[0], &best, &best_eps);
+    for (int i = 0; i + 1 < nb; ++i) {
+        double lo = bp[i], hi = bp[i + 1], w = hi - lo;
+        int tail = 0;
+        for (int c = 0; c < m->n_ch; ++c)
+            if (m->ch[c].e[m->ch[c].n - 1] < hi) tail = 1;
+        if (!tail) {
+            double e1 = lo + w / 3.0, e2 = lo + 2.0 * w / 3.0;
+            double s1 = or_density_sum(m, e1), s2 = or_density_sum(m, e2);
+            double b = (s2 - s1) / (e2 - e1), a = s1 - b * e1;
+            double k = sqrt(2.0 * OR_QE / OR_ME);
+            double cand[3] = {lo, hi, (b != 0.0) ? -a / (3.0 * b) : lo};
+            for (int j = 0; j < 3; ++j) {
+                double x = cand[j];
+                if (!(x >= lo && x <= hi)) continue;
+                double v = k * linear_piece_value(a, b, x);
+                if (v > best) { best = v; best_eps = x; }
+            }
+        } else {
+            const int NS = 1024;
+            int arg = 0;
+            double vmax = -1.0;
+            for (int j = 0; j <= NS; ++j) {
+                double x = lo + w * (double)j / NS;
+                double v = or_nu(m, x);
+                if (v > vmax) { vmax = v; arg = j; }
+            }
+            double a = lo + w * (double)(arg > 0 ? arg - 1 : 0) / NS;
+            double b = lo + w * (double)(arg < NS ? arg + 1 : NS) / NS;
+            const double g = 0.6180339887498949;
+            double x1 = b - g * (b - a), x2 = a + g * (b - a);
+            double f1 = or_nu(m, x1), f2 = or_nu(m, x2);
+            for (int it = 0; it < 200 && (b - a) > 1e-14 * b; ++it) {
+                if (f1 < f2) { a = x1; x1 = x2; f1 = f2; x2 = a + g * (b - a); f2 = or_nu(m, x2); }
+                else { b = x2; x2 = x1; f2 = f1; x1 = b - g * (b - a); f1 = or_nu(m, x1); }
+            }
+            consider(m, lo + w * (double)arg / NS, &best, &best_eps);
+            consider(m, x1, &best, &best_eps);
+            consider(m, x2, &best, &best_eps);
+            consider(m, hi, &best, &best_eps);
+        }
+    }
+    free(bp);
+    m->eps_cap = eps_cap;
+    m->nu_max = best;
+    m->eps_at_max = best_eps;
+}
+
+/* Mixture from flat arrays (tables are copied). Returns 0 or -1 on bad input. */
+int or_mixture_create(int n_gas, const double *gas_mass, const double *gas_density, const int *gas_angular,
+                      int n_ch, const int *ch_gas, const int *ch_kind, const double *ch_threshold,
+                      const int64_t *ch_offset, const int *ch_n, const double *energy, const double *sigma,
+                      double eps_cap, or_mixture **out)
+{
+    *out = NULL;
+    if (n_gas <= 0 || n_ch <= 0) return -1;
+    or_mixture *m = (or_mixture *)calloc(1, sizeof(or_mixture));
+    m->n_gas = n_gas;
+    m->n_ch = n_ch;
+    m->gas = (or_gas *)calloc((size_t)n_gas, sizeof(or_gas));
+    m->ch = (or_channel *)calloc((size_t)n_ch, sizeof(or_channel));
+    double emax = 0.0;
+    for (int g = 0; g < n_gas; ++g) {
+        m->gas[g].M = gas_mass[g];
+        m->gas[g].n = gas_density[g];
+        m->gas[g].angular = gas_angular[g];
+        m->n_total += gas_density[g];
+    }
+    for (int c = 0; c < n_ch; ++c) {
+        or_channel *ch = &m->ch[c];
+        ch->gas = ch_gas[c];
+        ch->kind = ch_kind[c];
+        ch->threshold = ch_threshold[c];
+        ch->n = ch_n[c];
+        ch->e = (double *)malloc(sizeof(double) * (size_t)ch->n);
+        ch->s = (double *)malloc(sizeof(double) * (size_t)ch->n);
+        memcpy(ch->e, energy + ch_offset[c], sizeof(double) * (size_t)ch->n);
+        memcpy(ch->s, sigma + ch_offset[c], sizeof(double) * (size_t)ch->n);
+        if (ch->n > 0 && ch->e[ch->n - 1] > emax) emax = ch->e[ch->n - 1];
+    }
+    or_majorant(m, eps_cap > 0.0 ? eps_cap : emax);
+    *out = m;
+    return 0;
+}
+
+void or_mixture_destroy(or_mixture *m)
+{
+    if (!m) return;
+    for (int c = 0; c < m->n_ch; ++c) { free(m->ch[c].e); free(m->ch[c].s); }
+    free(m->ch);
+    free(m->gas);
+    free(m);
+}
+
+double or_mixture_nu_max(const or_mixture *m) { return m->nu_max; }
+double or_mixture_eps_at_max(const or_mixture *m) { return m->eps_at_max; }
+double or_mixture_n_total(const or_mixture *m) { return m->n_total; }
+
+/* ------------------------------------------------------------------------ */
+/* Scattering (Sec. 2).                                                      */
+/* ------------------------------------------------------------------------ */
+/* Eq. (5) collision_angle (screened Coulomb, eps in Hartree) or isotropic. */
+double or_cos_theta(int angular, double eps_eV, double R)
+{
+    if (angular == OR_SCREENED_COULOMB) {
+        double e = eps_eV / OR_HARTREE_EV;
+        return 1.0 - 2.0 * R / (1.0 + 8.0 * e * (1.0 - R));
+    }
+    return 1.0 - 2.0 * R;
+}
+
+/* Eq. (8) delta_energy_ela: eps_f/eps_i for an elastic collision. */
+double or_ratio_elastic(double m, double M, double cos_t)
+{
+    return 1.0 - 2.0 * m * M * (1.0 - cos_t) / ((m + M) * (m + M));
+}
+
+/* Eq. (9) delta_energy_ine: eps_f/eps_i for an inelastic collision with loss
+ * eps_k.  The radicand is clamped at 0 and the result at 0 (the formula is
+ * undefined in the kinematically closed band eps_k <= eps_i < eps_k (m+M)/M). */
+double or_ratio_inelastic(double m, double M, double eps_i, double eps_k, double cos_t)
+{
+    double x = eps_k / eps_i;
+    double rad = 1.0 - (m + M) / M * x;
+    if (rad < 0.0) rad = 0.0;
+    double r = 1.0 - M / (m + M) * x + 2.0 * m * M / ((m + M) * (m + M)) * (sqrt(rad) * cos_t - 1.0);
+    return r < 0.0 ? 0.0 : r;
+}
+
+/* New direction: d rotated by polar angle theta and azimuth phi about itself.
+ * The azimuth origin e1 = (a x d)/|a x d| uses the coordinate axis a along the
+ * smallest |component| of d (first such axis on ties); e2 = d x e1. */
+void or_rotate(const double d[3], double cos_t, double phi, double out[3])
+{
+    double ax = fabs(d[0]), ay = fabs(d[1]), az = fabs(d[2]);
+    double e1[3];
+    if (ax <= ay && ax <= az) { e1[0] = 0.0; e1[1] = -d[2]; e1[2] = d[1]; }
+    else if (ay <= az) { e1[0] = d[2]; e1[1] = 0.0; e1[2] = -d[0]; }
+    else { e1[0] = -d[1]; e1[1] = d[0]; e1[2] = 0.0; }
+    double nrm = sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
+    e1[0] /= nrm; e1[1] /= nrm; e1[2] /= nrm;
+    double e2[3] = {d[1] * e1[2] - d[2] * e1[1], d[2] * e1[0] - d[0] * e1[2], d[0] * e1[1] - d[1] * e1[0]};
+    double st = sqrt(fmax(0.0, 1.0 - cos_t * cos_t));
+    double cp = cos(phi), sp = sin(phi);
+    for (int i = 0; i < 3; ++i) out[i] = cos_t * d[i] + st * (cp * e1[i] + sp * e2[i]);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Motion in uniform static fields (Sec. 3.6, UniformFieldClassic).          */
+/* The electron (q = -e) is pushed along +z by the electric force with       */
+/* acceleration a = eE/m; B = |B| (sin thB, 0, cos thB).  With B != 0 the    */
+/* velocity splits into a part along b = B/|B| (uniformly accelerated), the  */
+/* E x B drift v_D = (b x a z)/w and a remainder u rotating about b at       */
+/* w = e|B|/m:  u(t) = u0 cos wt + (b x u0) sin wt.                           */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    double a;              /* eE/m along +z [m/s^2] */
+    double B;              /* |B| [T] */
+    double b[3];           /* unit B */
+    double w;              /* e|B|/m */
+    double E;              /* |E| [V/m] */
+} or_field;
+
+static void field_setup(or_field *f, double e_over_n_Td, double n_total, double b_T, double angle)
+{
+    f->E = e_over_n_Td * OR_TD * n_total;
+    f->a = OR_QE * f->E / OR_ME;
+    f->B = b_T;
+    f->b[0] = sin(angle); f->b[1] = 0.0; f->b[2] = cos(angle);
+    f->w = OR_QE * b_T / OR_ME;
+}
+
+static void cross(const double a[3], const double b[3], double o[3])
+{
+    o[0] = a[1] * b[2] - a[2] * b[1];
+    o[1] = a[2] * b[0] - a[0] * b[2];
+    o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+void or_move(const or_field *f, double x[3], double v[3], double dt)
+{
+    if (f->B == 0.0) {
+        x[0] += v[0] * dt;
+        x[1] += v[1] * dt;
+        x[2] += v[2] * dt + 0.5 * f->a * dt * dt;
+        v[2] += f->a * dt;
+        return;
+    }
+    const double *b = f->b;
+    double az[3] = {0.0, 0.0, f->a};
+    double bxa[3];
+    cross(b, az, bxa);
+    double vD[3] = {bxa[0] / f->w, bxa[1] / f->w, bxa[2] / f->w};
+    double a_par = f->a * b[2];
+    double v_par = v[0] * b[0] + v[1] * b[1] + v[2] * b[2];
+    double u0[3], bxu[3];
+    for (int i = 0; i < 3; ++i) u0[i] = v[i] - v_par * b[i] - vD[i];
+    cross(b, u0, bxu);
+    double wt = f->w * dt, c = cos(wt), s = sin(wt), h = sin(0.5 * wt);
+    double omc = 2.0 * h * h; /* 1 - cos(wt) */
+    for (int i = 0; i < 3; ++i) {
+        x[i] += (v_par * dt + 0.5 * a_par * dt * dt) * b[i] + vD[i] * dt + (u0[i] * s + bxu[i] * omc) / f->w;
+        v[i] = (v_par + a_par * dt) * b[i] + vD[i] + u0[i] * c + bxu[i] * s;
+    }
+}
+
+/* Exported for the motion pins: one flight of duration dt. */
+void or_move_flat(double e_over_n_Td, double n_total, double b_T, double angle, double *x, double *v, double dt)
+{
+    or_field f;
+    field_setup(&f, e_over_n_Td, n_total, b_T, angle);
+    or_move(&f, x, v, dt);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Swarm run.                                                                */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    double e_over_n_Td, b_T, b_angle_rad;
+    double nu_trial;          /* >0: start value of nu' (fixed mode: the value) */
+    int fixed;                /* 1: FixedTrialFrequency -- a fail stops the particle */
+    uint32_t real_collisions; /* I */
+    double t_end;             /* >0: time limit [s] */
+    double eps0_mean_eV;      /* Maxwellian start, mean energy */
+    uint64_t seed;
+    uint64_t max_trials;
+    int attach_keep_state;    /* 1: a dummy attachment leaves the electron unchanged */
+} or_config;
+
+typedef struct {
+    double *x, *y, *z, *t, *vx, *vy, *vz, *sum_e, *sum_e2, *nu_p;
+    uint32_t *n_real, *n_null, *n_fail, *n_ion, *n_att, *steps, *status;
+} or_particles;
+
+static void init_velocity(const or_config *cf, uint64_t id, double v[3])
+{
+    double u[4];
+    draw4(cf->seed, id, 0u, 2u, u);
+    double kT = (2.0 / 3.0) * cf->eps0_mean_eV * OR_QE; /* mean energy = 3/2 kT */
+    double sv = sqrt(kT / OR_ME);
+    double r0 = sqrt(-2.0 * log(u[0])), r1 = sqrt(-2.0 * log(u[2]));
+    v[0] = sv * r0 * cos(2.0 * OR_PI * u[1]);
+    v[1] = sv * r0 * sin(2.0 * OR_PI * u[1]);
+    v[2] = sv * r1 * cos(2.0 * OR_PI * u[3]);
+}
+
+/* One real collision on channel c at energy eps (velocity v is updated). */
+static void collide(const or_mixture *m, const or_config *cf, uint64_t id, uint32_t step, int c, double eps,
+                    const double u[4], double v[3], double *eps_f, int *ion, int *att)
+{
+    const or_channel *ch = &m->ch[c];
+    const or_gas *g = &m->gas[ch->gas];
+    double cos_t = or_cos_theta(g->angular, eps, u[2]);
+    double phi = 2.0 * OR_PI * u[3];
+    double ratio;
+    *ion = 0;
+    *att = 0;
+    if (ch->kind == OR_ELASTIC) {
+        ratio = or_ratio_elastic(OR_ME, g->M, cos_t);
+    } else if (ch->kind == OR_ATTACHMENT) {
+        *att = 1;
+        if (cf->attach_keep_state) { *eps_f = eps; return; }
+        ratio = 0.0; /* plastic collision: all energy is given up */
+    } else {
+        ratio = or_ratio_inelastic(OR_ME, g->M, eps, ch->threshold, cos_t);
+        if (ch->kind == OR_IONIZATION) {
+            double w[4];
+            draw4(cf->seed, id, step, 1u, w);
+            ratio *= (1.0 - w[0]); /* the secondary takes w0 of the remainder */
+            *ion = 1;
+        }
+    }
+    double speed = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    double d[3] = {0.0, 0.0, 1.0};
+    if (speed > 0.0) { d[0] = v[0] / speed; d[1] = v[1] / speed; d[2] = v[2] / speed; }
+    double nd[3];
+    or_rotate(d, cos_t, phi, nd);
+    double sp = speed * sqrt(ratio);
+    v[0] = sp * nd[0]; v[1] = sp * nd[1]; v[2] = sp * nd[2];
+    *eps_f = ratio * eps;
+}
+
+static double energy_of(const double v[3]) { return 0.5 * OR_ME * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) / OR_QE; }
+
+static void run_particle(const or_mixture *m, const or_config *cf, const or_field *f, uint64_t id,
+                         const or_particles *P, int64_t slot)
+{
+    double x[3] = {0.0, 0.0, 0.0}, v[3], t = 0.0;
+    init_velocity(cf, id, v);
+    double sx[3] = {0, 0, 0}, sv[3] = {v[0], v[1], v[2]}, st = 0.0; /* last real collision */
+    double nu_p = cf->nu_trial;
+    double sum_e = 0.0, sum_e2 = 0.0;
+    uint32_t n_real = 0, n_null = 0, n_fail = 0, n_ion = 0, n_att = 0, k = 0, status = OR_ST_DONE;
+    while (n_real < cf->real_collisions) {
+        if ((uint64_t)k >= cf->max_trials) { status = OR_ST_STEPS; break; }
+        double u[4];
+        uint32_t step = k++;
+        draw4(cf->seed, id, step, 0u, u);
+        /* Eq. (3): t_c = -ln(1-R)/nu'; the draw u0 plays the role of 1-R. */
+        double tau = -log(u[0]) / nu_p;
+        if (cf->t_end > 0.0 && t + tau >= cf->t_end) {
+            or_move(f, x, v, cf->t_end - t);
+            t = cf->t_end;
+            status = OR_ST_TIME;
+            break;
+        }
+        or_move(f, x, v, tau);
+        t += tau;
+        double eps = energy_of(v);
+        double nu = or_nu(m, eps);
+        if (nu > nu_p) { /* fail: Sec. 6 -- back to the last real collision */
+            ++n_fail;
+            if (cf->fixed) { status = OR_ST_TRIAL; break; }
+            for (int i = 0; i < 3; ++i) { x[i] = sx[i]; v[i] = sv[i]; }
+            t = st;
+            nu_p = fmax(nu_p, 1.25 * nu);
+            continue;
+        }
+        double r = u[1] * nu_p;
+        if (r > nu) { ++n_null; continue; } /* Eq. (4) */
+        int c = or_select_channel(m, eps, r);
+        double eps_f;
+        int ion, att;
+        collide(m, cf, id, step, c, eps, u, v, &eps_f, &ion, &att);
+        n_ion += (uint32_t)ion;
+        n_att += (uint32_t)att;
+        sum_e += eps;
+        sum_e2 += eps_f;
+        ++n_real;
+        for (int i = 0; i < 3; ++i) { sx[i] = x[i]; sv[i] = v[i]; }
+        st = t;
+    }
+    P->x[slot] = x[0]; P->y[slot] = x[1]; P->z[slot] = x[2]; P->t[slot] = t;
+    P->vx[slot] = v[0]; P->vy[slot] = v[1]; P->vz[slot] = v[2];
+    P->sum_e[slot] = sum_e; P->sum_e2[slot] = sum_e2; P->nu_p[slot] = nu_p;
+    P->n_real[slot] = n_real; P->n_null[slot] = n_null; P->n_fail[slot] = n_fail;
+    P->n_ion[slot] = n_ion; P->n_att[slot] = n_att; P->steps[slot] = k; P->status[slot] = status;
+}
+
+typedef struct {
+    const or_mixture *m;
+    const or_config *cf;
+    const or_field *f;
+    const or_particles *P;
+    uint64_t id0;
+    int64_t begin, end;
+} or_job;
+
+static void *run_range(void *arg)
+{
+    const or_job *j = (const or_job *)arg;
+    for (int64_t i = j->begin; i < j->end; ++i) run_particle(j->m, j->cf, j->f, j->id0 + (uint64_t)i, j->P, i);
+    return NULL;
+}
+
+/* Runs particles id0 .. id0+n-1; outputs go to slot i = id - id0.  Particles
+ * are independent, so the result does not depend on n_threads. */
+int or_run_swarm(const or_mixture *m, const or_config *cf, uint64_t id0, int64_t n, int n_threads,
+                 double *x, double *y, double *z, double *t, double *vx, double *vy, double *vz,
+                 double *sum_e, double *sum_e2, double *nu_p, uint32_t *n_real, uint32_t *n_null,
+                 uint32_t *n_fail, uint32_t *n_ion, uint32_t *n_att, uint32_t *steps, uint32_t *status)
+{
+    or_particles P = {x, y, z, t, vx, vy, vz, sum_e, sum_e2, nu_p, n_real, n_null, n_fail, n_ion, n_att, steps, status};
+    or_config c = *cf;
+    if (c.nu_trial <= 0.0) c.nu_trial = m->nu_max * (1.0 + 1e-6);
+    if (c.max_trials == 0) c.max_trials = 0x7FFFFFFFu;
+    or_field f;
+    field_setup(&f, c.e_over_n_Td, m->n_total, c.b_T, c.b_angle_rad);
+    if (n_threads < 1) n_threads = 1;
+    if (n_threads > 256) n_threads = 256;
+    pthread_t th[256];
+    or_job jobs[256];
+    int64_t per = (n + n_threads - 1) / n_threads;
+    int launched = 0;
+    for (int i = 0; i < n_threads; ++i) {
+        int64_t b = (int64_t)i * per, e = b + per < n ? b + per : n;
+        if (b >= e) break;
+        jobs[i] = (or_job){m, &c, &f, &P, id0, b, e};
+        if (n_threads == 1) { run_range(&jobs[i]); continue; }
+        pthread_create(&th[i], NULL, run_range, &jobs[i]);
+        ++launched;
+    }
+    for (int i = 0; i < launched; ++i) pthread_join(th[i], NULL);
+    return 0;
+}
+
+/* One trial step from a state at a real collision (single-step replay).
+ * state[8*i ..] = x, y, z, vx, vy, vz, t, nu'; out has the same 8 values after
+ * the step; decision = channel index, -1 null, -2 fail; eps_io[2i] = energy
+ * before the collision, eps_io[2i+1] = energy after (real collisions only). */
+int or_step_replay(const or_mixture *m, const or_config *cf, int64_t n, const double *state,
+                   const uint64_t *ids, const uint32_t *steps, double *out, int32_t *decision, double *eps_io)
+{
+    or_field f;
+    field_setup(&f, cf->e_over_n_Td, m->n_total, cf->b_T, cf->b_angle_rad);
+    for (int64_t i = 0; i < n; ++i) {
+        const double *s = state + 8 * i;
+        double x[3] = {s[0], s[1], s[2]}, v[3] = {s[3], s[4], s[5]}, t = s[6], nu_p = s[7];
+        double u[4];
+        draw4(cf->seed, ids[i], steps[i], 0u, u);
+        double tau = -log(u[0]) / nu_p;
+        or_move(&f, x, v, tau);
+        t += tau;
+        double eps = energy_of(v), nu = or_nu(m, eps);
+        double eps_f = 0.0;
+        int32_t dec;
+        if (nu > nu_p) {
+            dec = OR_DEC_FAIL;
+            x[0] = s[0]; x[1] = s[1]; x[2] = s[2]; v[0] = s[3]; v[1] = s[4]; v[2] = s[5]; t = s[6];
+            nu_p = fmax(nu_p, 1.25 * nu);
+        } else if (u[1] * nu_p > nu) {
+            dec = OR_DEC_NULL;
+        } else {
+            int c = or_select_channel(m, eps, u[1] * nu_p), ion, att;
+            collide(m, cf, ids[i], steps[i], c, eps, u, v, &eps_f, &ion, &att);
+            dec = c;
+        }
+        double *o = out + 8 * i;
+        o[0] = x[0]; o[1] = x[1]; o[2] = x[2]; o[3] = v[0]; o[4] = v[1]; o[5] = v[2]; o[6] = t; o[7] = nu_p;
+        decision[i] = dec;
+        eps_io[2 * i] = eps;
+        eps_io[2 * i + 1] = eps_f;
+    }
+    return 0;
+}
+
+/* The state of particle `id` right after initialisation (for pins). */
+void or_initial_velocity(double eps0_mean_eV, uint64_t seed, uint64_t id, double v[3])
+{
+    or_config c;
+    memset(&c, 0, sizeof c);
+    c.eps0_mean_eV = eps0_mean_eV;
+    c.seed = seed;
+    init_velocity(&c, id, v);
+}
+
+/* Vectorised helpers for the pins (plain loops over the scalar functions). */
+void or_nu_many(const or_mixture *m, int64_t n, const double *eps, double *out)
+{
+    for (int64_t i = 0; i < n; ++i) out[i] = or_nu(m, eps[i]);
+}
+
+void or_sigma_many(const or_mixture *m, int c, int64_t n, const double *eps, double *out)
+{
+    for (int64_t i = 0; i < n; ++i) out[i] = or_sigma(m, c, eps[i]);
+}
+
+void or_initial_velocity_many(double eps0_mean_eV, uint64_t seed, uint64_t id0, int64_t n, double *v)
+{
+    for (int64_t i = 0; i < n; ++i) or_initial_velocity(eps0_mean_eV, seed, id0 + (uint64_t)i, v + 3 * i);
+}

@@ -1,0 +1,498 @@
+"""Pins of the FP64 oracle against things other than itself.
+
+Each test checks the oracle against a closed form, an exact invariant, a
+brute-force computation or a value printed in the paper, chosen so that a
+plausible slip (dropped term, wrong sign, swapped operand, wrong index) in
+the corresponding oracle function fails.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import stats
+
+from conftest import read_golden
+from oracle import oracle as O
+from oracle import tallies as T
+from paper_1901_08140_gb300 import workloads as W
+
+QE = 1.602176634e-19
+ME = 9.1093837015e-31
+HARTREE = 27.211386245988
+
+
+# --------------------------------------------------------------------------
+# Random numbers: the method asks for independent uniforms on [0,1)
+# (Eqs. 3, 4, 5); these pins check exactly that.
+# --------------------------------------------------------------------------
+def _words(n, step=0, sub=0, key=(12345, 678)):
+    return np.array([O.philox([i, 0, step, sub], key) for i in range(n)], dtype=np.uint64)
+
+
+def test_philox_uniformity_and_independence():
+    w = _words(20000)
+    u = (((w >> 8).astype(np.float64)) + 0.5) / 2 ** 24
+    flat = u.ravel()
+    assert abs(flat.mean() - 0.5) < 4 * math.sqrt(1 / 12 / flat.size)
+    assert abs(flat.var() - 1 / 12) < 0.01 * (1 / 12)
+    counts, _ = np.histogram(flat, bins=64, range=(0, 1))
+    assert stats.chisquare(counts).pvalue > 1e-4
+    # the four words of one call and consecutive counters are uncorrelated
+    for a, b in [(0, 1), (1, 2), (2, 3), (0, 3)]:
+        r = np.corrcoef(u[:, a], u[:, b])[0, 1]
+        assert abs(r) < 4 / math.sqrt(len(u))
+    r = np.corrcoef(u[:-1, 0], u[1:, 0])[0, 1]
+    assert abs(r) < 4 / math.sqrt(len(u))
+    # every 32-bit output bit is balanced
+    bits = ((w[:, :, None] >> np.arange(32, dtype=np.uint64)) & 1).reshape(-1, 32).mean(axis=0)
+    assert np.all(np.abs(bits - 0.5) < 5 * 0.5 / math.sqrt(w.size))
+
+
+def test_philox_counter_and_key_avalanche():
+    base = O.philox([7, 0, 3, 0], [1, 2]).astype(np.uint64)
+    flips = []
+    for word in range(4):
+        for bit in (0, 13, 31):
+            ctr = [7, 0, 3, 0]
+            ctr[word] ^= 1 << bit
+            o = O.philox(ctr, [1, 2]).astype(np.uint64)
+            flips.append(sum(bin(int(a ^ b)).count("1") for a, b in zip(base, o)))
+    for kw in range(2):
+        key = [1, 2]
+        key[kw] ^= 1 << 5
+        o = O.philox([7, 0, 3, 0], key).astype(np.uint64)
+        flips.append(sum(bin(int(a ^ b)).count("1") for a, b in zip(base, o)))
+    assert 56 < np.mean(flips) < 72  # 128 bits, half flip on average
+
+
+def test_uniform_open_interval_lattice():
+    assert O.uniform(0) == 0.5 / 2 ** 24
+    assert O.uniform(0xFFFFFFFF) == 1 - 0.5 / 2 ** 24
+    assert O.uniform(0xFF) == O.uniform(0)          # only the top 24 bits count
+    assert O.uniform(1 << 8) == 1.5 / 2 ** 24
+
+
+# --------------------------------------------------------------------------
+# Tables and their extension (Sec. 2.2, Eqs. 12-14), worked by hand.
+# --------------------------------------------------------------------------
+def _gas(channels, mass=40 * W.ATOMIC_MASS_UNIT, n=1e25, angular=W.ISOTROPIC):
+    return W.Gas("t", mass, n, angular, channels)
+
+
+def test_table_interpolation_and_extension_by_hand():
+    el = W.Channel(W.ELASTIC, 0.0, np.array([1.0, 10.0]), np.array([1e-20, 1e-21]))
+    ex = W.Channel(W.EXCITATION, 2.0, np.array([3.0, 5.0]), np.array([4e-21, 6e-21]))
+    at = W.Channel(W.ATTACHMENT, 3.0, np.array([3.0, 4.0, 6.0]), np.array([0.0, 2e-22, 0.0]))
+    m = O.Mixture([_gas([el, ex, at])])
+    # elastic: constant to the left, linear inside, power law to the right
+    assert m.sigma(0, 0.01) == 1e-20
+    assert m.sigma(0, 5.5) == pytest.approx(1e-20 + (1e-21 - 1e-20) * 4.5 / 9.0, rel=1e-14, abs=0.0)
+    # K = ln(0.1)/ln(10) = -1, A = 1e-21 * 10: sigma(100) = 1e-22, sigma(20) = 5e-22
+    assert m.sigma(0, 100.0) == pytest.approx(1e-22, rel=1e-12, abs=0.0)
+    assert m.sigma(0, 20.0) == pytest.approx(5e-22, rel=1e-12, abs=0.0)
+    # inelastic: zero below threshold, linear rise from (threshold, 0) to the first point
+    assert m.sigma(1, 1.99) == 0.0
+    assert m.sigma(1, 2.5) == pytest.approx(2e-21, rel=1e-14, abs=0.0)
+    assert m.sigma(1, 4.0) == pytest.approx(5e-21, rel=1e-14, abs=0.0)
+    # K = ln(6/4)/ln(5/3); sigma(15) = 6e-21 * 3^K
+    K = math.log(1.5) / math.log(5 / 3)
+    assert m.sigma(1, 15.0) == pytest.approx(6e-21 * 3 ** K, rel=1e-12, abs=0.0)
+    # a table ending in zero extends with zero
+    assert m.sigma(2, 5.0) == pytest.approx(1e-22, rel=1e-14, abs=0.0)
+    assert m.sigma(2, 50.0) == 0.0
+    # Eq. (2): nu = sqrt(2 eps/m) sum n sigma
+    eps = 4.0
+    S = 1e25 * (m.sigma(0, eps) + m.sigma(1, eps) + m.sigma(2, eps))
+    assert m.nu(eps) == pytest.approx(math.sqrt(2 * eps * QE / ME) * S, rel=1e-14, abs=0.0)
+
+
+def test_density_weighting_of_components():
+    el1 = W.Channel(W.ELASTIC, 0.0, np.array([1.0, 10.0]), np.array([1e-20, 1e-20]))
+    el2 = W.Channel(W.ELASTIC, 0.0, np.array([1.0, 10.0]), np.array([3e-20, 3e-20]))
+    m = O.Mixture([_gas([el1], n=2e25), _gas([el2], n=1e25)])
+    eps = 2.0
+    assert m.nu(eps) == pytest.approx(math.sqrt(2 * eps * QE / ME) * (2e25 * 1e-20 + 1e25 * 3e-20), rel=1e-14, abs=0.0)
+
+
+# --------------------------------------------------------------------------
+# Trial frequency: exact maximum of nu over [0, eps_cap] (Sec. 6.2).
+# --------------------------------------------------------------------------
+def _inner_tail_gas():
+    e = np.geomspace(1e-3, 100.0, 300)
+    el = W.Channel(W.ELASTIC, 0.0, e, 2e-20 / (1 + e))
+    ex = W.Channel(W.EXCITATION, 5.0, np.linspace(5.0, 30.0, 20), np.linspace(0.0, 3e-20, 20))
+    return _gas([el, ex])
+
+
+@pytest.mark.parametrize("name", ["maxwell", "argon", "arco2", "inner_tail"])
+def test_majorant_matches_brute_force(name):
+    gases = {"maxwell": [W.maxwell_gas()], "argon": [W.argon_like()], "arco2": W.ar_co2_mixture(),
+             "inner_tail": [_inner_tail_gas()]}[name]
+    m = O.Mixture(gases)
+    cap = max(float(ch.energy_eV[-1]) for g in gases for ch in g.channels)
+    pts = [np.geomspace(1e-7, cap, 400000), np.linspace(0.0, cap, 400000)]
+    for g in gases:
+        for ch in g.channels:
+            pts.append(ch.energy_eV[ch.energy_eV <= cap])
+    grid = np.unique(np.concatenate(pts))
+    brute = m.nu_many(grid).max()
+    assert brute <= m.nu_max * (1 + 1e-12)
+    assert brute >= m.nu_max * (1 - 1e-6)
+
+
+# --------------------------------------------------------------------------
+# Channel choice and null fraction (Eqs. 2 and 4): chi-square against the
+# table ratios, through the whole trial step with no field.
+# --------------------------------------------------------------------------
+def test_channel_frequencies_match_table_ratios():
+    gas = W.argon_like()
+    m = O.Mixture([gas])
+    eps = 14.0
+    speed = math.sqrt(2 * eps * QE / ME)
+    n = 200000
+    state = np.zeros((n, 8))
+    state[:, 5] = speed
+    state[:, 7] = m.nu_max
+    ids = np.arange(n, dtype=np.uint64)
+    out, dec, eps_io = O.step_replay(m, state, ids, np.full(n, 5, np.uint32), e_over_n_Td=0.0, seed=99)
+    assert np.allclose(eps_io[:, 0], eps, rtol=1e-12)
+    nu_ch = np.array([gas.number_density_m3 * m.sigma(c, eps) * speed for c in range(m.n_channels)])
+    p = np.concatenate([[1 - nu_ch.sum() / m.nu_max], nu_ch / m.nu_max])
+    assert p[-1] == 0.0  # ionization is closed at 14 eV
+    keep = p > 0
+    counts = np.array([np.sum(dec == O.DEC_NULL)] + [np.sum(dec == c) for c in range(m.n_channels)])
+    assert counts[~keep].sum() == 0
+    assert stats.chisquare(counts[keep], p[keep] * n).pvalue > 1e-4
+
+
+# --------------------------------------------------------------------------
+# Scattering angle (Eq. 5) and energy exchange (Eqs. 8, 9).
+# --------------------------------------------------------------------------
+def test_isotropic_angle_moments():
+    R = (np.arange(100000) + 0.5) / 100000
+    c = np.array([O.cos_theta(W.ISOTROPIC, 3.0, r) for r in R])
+    assert abs(c.mean()) < 1e-9
+    assert c.var() == pytest.approx(1 / 3, rel=1e-6, abs=0.0)
+
+
+@pytest.mark.parametrize("eps", [0.0, 0.01, 1.0, 27.0, 300.0])
+def test_screened_coulomb_mean_deflection(eps):
+    R = (np.arange(200000) + 0.5) / 200000
+    c = np.array([O.cos_theta(W.SCREENED_COULOMB, eps, r) for r in R])
+    cc = 8 * eps / HARTREE
+    exact = 1.0 if cc == 0 else (2 / cc ** 2) * ((1 + cc) * math.log1p(cc) - cc)
+    assert np.mean(1 - c) == pytest.approx(exact, rel=1e-6, abs=0.0)
+    assert np.all(c <= 1) and np.all(c >= -1)
+
+
+def _two_body(m, M, eps_i, eps_k, cos_cm, rng):
+    """Electron (mass m) on a target at rest, exact kinematics in the CM frame."""
+    d = rng.normal(size=3)
+    d /= np.linalg.norm(d)
+    v = math.sqrt(2 * eps_i * QE / m) * d
+    V = m * v / (m + M)
+    u = v - V                                # electron in the CM frame
+    mu = m * M / (m + M)
+    E_cm = 0.5 * mu * (v @ v)                # kinetic energy available in the CM frame
+    scale = math.sqrt(1 - eps_k * QE / E_cm)
+    a = np.cross(d, [1.0, 0.0, 0.0] if abs(d[0]) < 0.9 else [0.0, 1.0, 0.0])
+    a /= np.linalg.norm(a)
+    sin_cm = math.sqrt(1 - cos_cm ** 2)
+    u_new = scale * np.linalg.norm(u) * (cos_cm * d + sin_cm * a)
+    v_new = V + u_new
+    U_new = V - (m / M) * u_new              # target, from momentum conservation
+    # conservation checks of the construction itself
+    assert np.allclose(m * v, m * v_new + M * U_new, rtol=1e-12, atol=1e-40)
+    ke0 = 0.5 * m * (v @ v)
+    ke1 = 0.5 * m * (v_new @ v_new) + 0.5 * M * (U_new @ U_new) + eps_k * QE
+    assert ke1 == pytest.approx(ke0, rel=1e-12, abs=0.0)
+    return 0.5 * m * (v_new @ v_new) / QE / eps_i
+
+
+def test_energy_exchange_matches_two_body_kinematics():
+    rng = np.random.default_rng(3)
+    for _ in range(300):
+        M = rng.uniform(1.0, 200.0) * W.ATOMIC_MASS_UNIT
+        if rng.uniform() < 0.3:
+            M = rng.uniform(2.0, 50.0) * ME       # light targets exercise the mass terms
+        eps_i = float(np.exp(rng.uniform(-2, 5)))
+        cos_cm = rng.uniform(-1, 1)
+        assert O.ratio_elastic(ME, M, cos_cm) == pytest.approx(_two_body(ME, M, eps_i, 0.0, cos_cm, rng), rel=1e-11, abs=0.0)
+        eps_k = eps_i * rng.uniform(0.0, 0.95) * M / (ME + M)
+        got = O.ratio_inelastic(ME, M, eps_i, eps_k, cos_cm)
+        assert got == pytest.approx(_two_body(ME, M, eps_i, eps_k, cos_cm, rng), rel=1e-10, abs=1e-13)
+
+
+def test_mean_elastic_loss_is_kappa():
+    M = 40 * W.ATOMIC_MASS_UNIT
+    kappa = 2 * ME * M / (ME + M) ** 2
+    R = (np.arange(50000) + 0.5) / 50000
+    r = np.array([O.ratio_elastic(ME, M, O.cos_theta(W.ISOTROPIC, 1.0, x)) for x in R])
+    assert np.mean(1 - r) == pytest.approx(kappa, rel=1e-8, abs=0.0)
+
+
+def test_inelastic_closed_band_is_clamped():
+    M = 40 * W.ATOMIC_MASS_UNIT
+    assert O.ratio_inelastic(ME, M, 11.5, 11.5, 1.0) == 0.0
+    assert O.ratio_inelastic(ME, M, 11.5 * (1 + 0.5 * ME / M), 11.5, -1.0) == 0.0
+
+
+def test_rotation_geometry():
+    rng = np.random.default_rng(5)
+    for _ in range(500):
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        ct = rng.uniform(-1, 1)
+        phi = rng.uniform(0, 2 * math.pi)
+        o = O.rotate(d, ct, phi)
+        assert np.linalg.norm(o) == pytest.approx(1.0, abs=1e-14)
+        assert o @ d == pytest.approx(ct, abs=1e-14)
+    # uniform azimuth averages to the axis
+    d = np.array([0.3, -0.5, 0.8])
+    d /= np.linalg.norm(d)
+    phis = (np.arange(720) + 0.5) * 2 * math.pi / 720
+    mean = np.mean([O.rotate(d, 0.2, p) for p in phis], axis=0)
+    assert np.allclose(mean, 0.2 * d, atol=1e-12)
+    # a quarter turn of azimuth gives an orthogonal transverse part
+    t0 = O.rotate(d, 0.0, 0.0)
+    t1 = O.rotate(d, 0.0, math.pi / 2)
+    assert abs(t0 @ t1) < 1e-14 and abs(t0 @ d) < 1e-14
+
+
+# --------------------------------------------------------------------------
+# Motion in uniform static E and B (Sec. 3.6): closed form against RK4.
+# --------------------------------------------------------------------------
+def _rk4(x, v, accel_E, qm, Bv, T, steps):
+    dt = T / steps
+
+    def f(v):
+        return accel_E + qm * np.cross(v, Bv)
+
+    for _ in range(steps):
+        k1v = f(v); k1x = v
+        k2v = f(v + 0.5 * dt[:, None] * k1v); k2x = v + 0.5 * dt[:, None] * k1v
+        k3v = f(v + 0.5 * dt[:, None] * k2v); k3x = v + 0.5 * dt[:, None] * k2v
+        k4v = f(v + dt[:, None] * k3v); k4x = v + dt[:, None] * k3v
+        x = x + dt[:, None] / 6 * (k1x + 2 * k2x + 2 * k3x + k4x)
+        v = v + dt[:, None] / 6 * (k1v + 2 * k2v + 2 * k3v + k4v)
+    return x, v
+
+
+@pytest.mark.parametrize("b_T,angle", [(0.1, 0.0), (1.0, math.pi / 2), (2.0, math.pi / 6), (0.7, 2.4)])
+def test_motion_matches_rk4(b_T, angle):
+    rng = np.random.default_rng(11)
+    n_total, eon = W.N_STP_293, 100.0
+    E = eon * 1e-21 * n_total
+    omega = QE * b_T / ME
+    n = 40
+    x0 = rng.normal(size=(n, 3)) * 1e-5
+    v0 = rng.normal(size=(n, 3)) * 1e6
+    T = rng.uniform(0.01, 10.0, size=n) / omega
+    # the electron (q = -e) is pushed along +z: E points along -z
+    accel = np.array([0.0, 0.0, QE * E / ME])
+    Bv = b_T * np.array([math.sin(angle), 0.0, math.cos(angle)])
+    xr, vr = _rk4(x0.copy(), v0.copy(), accel, -QE / ME, Bv, T, 6000)
+    for i in range(n):
+        xo, vo = O.move(x0[i], v0[i], T[i], eon, n_total, b_T, angle)
+        scale_x = np.linalg.norm(v0[i]) * T[i] + 1e-3 * np.linalg.norm(x0[i])
+        assert np.allclose(xo, xr[i], rtol=0, atol=1e-9 * scale_x + 1e-12 * np.linalg.norm(x0[i]))
+        assert np.allclose(vo, vr[i], rtol=0, atol=1e-9 * (np.linalg.norm(v0[i]) + E / b_T))
+        # B does no work: the kinetic energy change equals the work of the electric force
+        dke = 0.5 * ME * (vo @ vo - v0[i] @ v0[i])
+        assert dke == pytest.approx(QE * E * (xo[2] - x0[i][2]), rel=1e-8, abs=1e-12 * 0.5 * ME * (v0[i] @ v0[i]))
+
+
+def test_motion_without_b_is_a_parabola_and_guiding_centre_drifts_at_exb():
+    E = 10.0 * 1e-21 * W.N_STP_293
+    a = QE * E / ME
+    x, v = O.move([1.0, 2.0, 3.0], [4.0, 5.0, 6.0], 1e-9, 10.0, W.N_STP_293)
+    assert np.allclose(x, [1 + 4e-9, 2 + 5e-9, 3 + 6e-9 + 0.5 * a * 1e-18], rtol=1e-15)
+    assert np.allclose(v, [4.0, 5.0, 6.0 + a * 1e-9], rtol=1e-15)
+    # B along x, E along -z: E x B / B^2 = (-E z) x (B x) / B^2 = -(E/B) y
+    b = 1.0
+    omega = QE * b / ME
+    periods = 1000.0
+    T = periods * 2 * math.pi / omega
+    x, v = O.move([0.0, 0.0, 0.0], [3e5, -2e5, 1e5], T, 100.0, W.N_STP_293, b, math.pi / 2)
+    E100 = 100.0 * 1e-21 * W.N_STP_293
+    assert x[1] / T == pytest.approx(-E100 / b, rel=1e-6, abs=0.0)
+    assert abs(x[2]) < 1e-4 * abs(x[1])
+    assert x[0] == pytest.approx(3e5 * T, rel=1e-9, abs=0.0)  # motion along B is free
+
+
+# --------------------------------------------------------------------------
+# Whole step loop: the constant-frequency Maxwell model has closed forms.
+# --------------------------------------------------------------------------
+def _maxwell_closed_forms(I, eps0, nu, kappa, vd):
+    mvd2 = ME * vd * vd / QE                   # eV
+    B = np.empty(I)
+    B[0] = eps0 + mvd2
+    for i in range(1, I):
+        B[i] = (1 - kappa) * B[i - 1] + mvd2
+    mean_eps = B.mean()
+    # E[v_x^2] of flight i (0 = initial flight), in (m/s)^2
+    vx2 = np.empty(I)
+    vx2[0] = 2 * eps0 * QE / (3 * ME)
+    vx2[1:] = 2 * QE / (3 * ME) * (1 - kappa) * B[:-1]
+    DT = vx2.sum() / (nu * I)
+    DL = (vx2.sum() + I * vd * vd) / (nu * I)
+    return mean_eps, DT, DL
+
+
+def _group_se(vals_per_group):
+    v = np.asarray(vals_per_group)
+    return np.std(v, ddof=1) / math.sqrt(len(v))
+
+
+def test_maxwell_model_closed_forms():
+    spec = W.maxwell_swarm(n_electrons=10000, real_collisions=1000)
+    gas = spec.gases[0]
+    m = O.Mixture(spec.gases)
+    p = O.run_swarm(m, e_over_n_Td=spec.e_over_n_Td, real_collisions=spec.real_collisions,
+                    n=spec.n_electrons, seed=spec.seed, eps0_mean_eV=spec.eps0_mean_eV,
+                    threads=O.cpu_count())
+    assert np.all(p["n_real"] == 1000) and np.all(p["n_fail"] == 0)
+    nu = 1e12
+    E = spec.e_over_n_Td * 1e-21 * gas.number_density_m3
+    vd = QE * E / (ME * nu)
+    assert vd == pytest.approx(4.40316e4, rel=1e-5, abs=0.0)
+    M = gas.mass_kg
+    kappa = 2 * ME * M / (ME + M) ** 2
+    mean_eps, DT, DL = _maxwell_closed_forms(1000, 0.1, nu, kappa, vd)
+    assert mean_eps == pytest.approx(5.2580, abs=5e-4)
+    assert DT == pytest.approx(0.61523, rel=1e-4, abs=0.0)
+    assert DL == pytest.approx(0.61717, rel=1e-4, abs=0.0)
+    tr = T.swarm_tallies(p, spec.e_over_n_Td, gas.number_density_m3)
+    assert abs(tr["W"] - vd) < 3 * tr["W_se"]
+    assert abs(tr["eps"] - mean_eps) < 3 * tr["eps_se"]
+    assert tr["eps_after"] == pytest.approx((1 - kappa) * tr["eps"], rel=2e-4, abs=0.0)
+    g = p["id"] % 32
+    x, y, z, t = p["x"], p["y"], p["z"], p["t"]
+    est_T = [np.sum(x[g == j] ** 2 + y[g == j] ** 2) / (4 * np.sum(t[g == j])) for j in range(32)]
+    est_L = [np.sum((z[g == j] - vd * t[g == j]) ** 2) / (2 * np.sum(t[g == j])) for j in range(32)]
+    est_W = [np.sum(z[g == j]) / np.sum(t[g == j]) for j in range(32)]
+    assert abs(np.sum(x ** 2 + y ** 2) / (4 * np.sum(t)) - DT) < 3 * _group_se(est_T)
+    assert abs(np.sum((z - vd * t) ** 2) / (2 * np.sum(t)) - DL) < 3 * _group_se(est_L)
+    assert abs(np.sum(z) / np.sum(t) - vd) < 3 * _group_se(est_W)
+    # the mean flight time is 1/nu
+    assert np.mean(t) == pytest.approx(1000 / nu, rel=3 * math.sqrt(1000) / 1000 / math.sqrt(10000) * 3, abs=0.0)
+
+
+def test_initial_velocities_are_maxwellian_with_mean_energy():
+    v = O.initial_velocities(0.1, 77, 0, 200000)
+    eps = 0.5 * ME * np.sum(v * v, axis=1) / QE
+    assert abs(eps.mean() - 0.1) < 4 * eps.std() / math.sqrt(len(eps))
+    sv = math.sqrt((2 / 3) * 0.1 * QE / ME)
+    for k in range(3):
+        assert stats.kstest(v[:, k] / sv, "norm").pvalue > 1e-4
+
+
+# --------------------------------------------------------------------------
+# Collision bookkeeping: ionization split and dummy attachment (readings).
+# --------------------------------------------------------------------------
+def test_ionization_split_and_attachment_energy_accounting():
+    gases = [W.co2_like()]
+    m = O.Mixture(gases)
+    rng = np.random.default_rng(9)
+    n = 60000
+    eps = np.where(rng.uniform(size=n) < 0.5, 40.0, 4.4)
+    speed = np.sqrt(2 * eps * QE / ME)
+    d = rng.normal(size=(n, 3))
+    d /= np.linalg.norm(d, axis=1)[:, None]
+    state = np.zeros((n, 8))
+    state[:, 3:6] = d * speed[:, None]
+    state[:, 7] = np.array([m.nu(e) for e in eps]) * (1 + 1e-9)   # nearly every trial is real
+    ids = np.arange(n, dtype=np.uint64)
+    steps = np.full(n, 3, np.uint32)
+    seed = 4242
+    out, dec, eio = O.step_replay(m, state, ids, steps, e_over_n_Td=0.0, seed=seed)
+    kinds = m.ch_kind
+    ion = np.array([c >= 0 and kinds[c] == W.IONIZATION for c in dec])
+    att = np.array([c >= 0 and kinds[c] == W.ATTACHMENT for c in dec])
+    assert ion.sum() > 20 and att.sum() > 3
+    for i in np.nonzero(ion)[0]:
+        c = dec[i]
+        u = [O.uniform(w) for w in O.philox([i, 0, 3, 0], [seed, 0])]
+        w4 = O.uniform(O.philox([i, 0, 3, 1], [seed, 0])[0])
+        M = m.gas_mass[m.ch_gas[c]]
+        r = O.ratio_inelastic(ME, M, eps[i], m.ch_threshold[c], 1 - 2 * u[2])
+        assert eio[i, 1] == pytest.approx(r * (1 - w4) * eps[i], rel=1e-12, abs=0.0)
+        ef = 0.5 * ME * np.sum(out[i, 3:6] ** 2) / QE
+        assert ef == pytest.approx(eio[i, 1], rel=1e-10, abs=0.0)
+    assert np.all(eio[att, 1] == 0.0) and np.all(out[att, 3:6] == 0.0)
+
+
+def test_fail_revert_and_fixed_mode():
+    gases = [W.argon_like()]
+    m = O.Mixture(gases)
+    low = 0.3 * m.nu_max
+    p = O.run_swarm(m, e_over_n_Td=300.0, real_collisions=200, n=200, seed=5, nu_trial=low, threads=4)
+    assert p["n_fail"].sum() > 0
+    assert np.all(p["n_real"] == 200)
+    assert np.all(p["nu_p"] >= low)
+    assert np.any(p["nu_p"] > low)
+    q = O.run_swarm(m, e_over_n_Td=300.0, real_collisions=200, n=50, seed=5, nu_trial=low, fixed=True)
+    assert np.all(q["status"][q["n_fail"] > 0] == O.ST_TRIAL)
+    assert np.all(q["n_fail"] <= 1)
+
+
+def test_time_limit_truncates_the_last_flight():
+    m = O.Mixture([W.argon_like()])
+    t_end = 2e-11
+    p = O.run_swarm(m, e_over_n_Td=50.0, real_collisions=10 ** 6, n=100, seed=8, t_end=t_end)
+    assert np.all(p["status"] == O.ST_TIME)
+    assert np.all(p["t"] == t_end)
+
+
+# --------------------------------------------------------------------------
+# Swarm estimators and units, pinned by the worked example of Sec. 7.
+# --------------------------------------------------------------------------
+def test_worked_example_conventions():
+    g = read_golden("drifter_example.txt")
+    N = g["gas_density"] * 1e6                       # m^-3
+    E = g["electric_field"] * 1e5                    # V/m
+    W_ = g["drift_velocity"] * 1e4                   # m/s
+    assert E / N / 1e-21 == pytest.approx(g["reduced_field"], rel=1e-5, abs=0.0)
+    d = T.derived(W_, g["diffusion"] * 1e-4, g["diffusion_long"] * 1e-4, g["diffusion_tran"] * 1e-4,
+                  E / N / 1e-21, N)
+    assert d["mu"] * 1e4 == pytest.approx(g["mobility"], rel=1e-5, abs=0.0)
+    assert d["mu_N"] * 1e-2 == pytest.approx(g["mobility_norm"], rel=1e-5, abs=0.0)
+    assert d["mu_0"] * 1e4 == pytest.approx(g["mobility_reduced"], rel=1e-5, abs=0.0)
+    assert d["D_over_mu"] == pytest.approx(g["diffusion_ratio"], rel=1e-5, abs=0.0)
+    assert d["D_L_over_mu"] == pytest.approx(g["diffusion_long_ratio"], rel=1e-5, abs=0.0)
+    assert d["D_T_over_mu"] == pytest.approx(g["diffusion_tran_ratio"], rel=1e-5, abs=0.0)
+    assert d["ND"] * 1e-2 == pytest.approx(g["diffusion_norm"], rel=1e-5, abs=0.0)
+    # D carries no 1/6: the printed D equals 2 D_L + 4 D_T to the printed digits
+    assert 2 * g["diffusion_long"] + 4 * g["diffusion_tran"] == pytest.approx(g["diffusion"], abs=0.5)
+    eff = 100 * T.efficiency(g["real_collisions"], g["null_collisions"], g["fail_collisions"])
+    assert eff == pytest.approx(g["efficiency"], abs=5e-4)
+    # N of the example is p / (k_B T) at 101.325 kPa, 293.15 K
+    assert W.N_STP_293 == pytest.approx(N, rel=1e-5, abs=0.0)
+
+
+def test_estimators_on_a_hand_worked_swarm():
+    # two particles; W_vec = mean(x/t) = (0, 0, 3); d = x - t W_vec
+    p = {"x": np.array([1.0, -2.0]), "y": np.array([0.0, 0.0]), "z": np.array([2.0, 8.0]),
+         "t": np.array([1.0, 2.0]), "sum_e": np.array([10.0, 20.0]), "sum_e2": np.array([9.0, 18.0]),
+         "n_real": np.array([10, 10]), "n_null": np.array([5, 5]), "n_fail": np.array([0, 0]),
+         "n_ion": np.array([1, 0]), "n_att": np.array([0, 2]), "id": np.array([0, 1], dtype=np.uint64)}
+    tr = T.swarm_tallies(p, 1.0, 1e25, groups=2)
+    assert tr["W"] == 3.0 and tr["Wx"] == 0.0
+    # d = (1, 0, -1) and (-2, 0, 2)
+    assert tr["D"] == pytest.approx((2 / 1 + 8 / 2) / 2, abs=0.0)
+    assert tr["D_L"] == pytest.approx((1 / 2 + 4 / 4) / 2, abs=0.0)
+    assert tr["D_T"] == pytest.approx((1 / 4 + 4 / 8) / 2, abs=0.0)
+    assert tr["D"] == pytest.approx(2 * tr["D_L"] + 4 * tr["D_T"], abs=0.0)
+    assert tr["sig"] == pytest.approx((2 * math.sqrt(2) + 2 * math.sqrt(8)) / 2, abs=0.0)
+    assert tr["sig_L"] == pytest.approx((2 + 4) / 2, abs=0.0)
+    assert tr["sig_T"] == pytest.approx((2 + 4) / 2, abs=0.0)
+    assert tr["alpha"] == pytest.approx((1 / 2 + 0) / 2, abs=0.0)
+    assert tr["eta"] == pytest.approx((0 + 2 / 8) / 2, abs=0.0)
+    assert tr["eps"] == pytest.approx(30 / 20, abs=0.0) and tr["eps_after"] == pytest.approx(27 / 20, abs=0.0)
+    assert tr["efficiency"] == pytest.approx(20 / 30, abs=0.0)
+    # with a transverse drift the full drift vector is taken out of d
+    p["x"] = np.array([2.0, 2.0])
+    tr = T.swarm_tallies(p, 1.0, 1e25, groups=2)
+    assert tr["Wx"] == 1.5
+    # d_x = 2 - 1.5 = 0.5 and 2 - 3 = -1
+    assert tr["D_T"] == pytest.approx((0.25 / 4 + 1 / 8) / 2, abs=0.0)
