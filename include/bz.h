@@ -1,0 +1,255 @@
+/*
+ * bz.h -- C ABI of the GB300 electron-swarm Monte Carlo library (libbz.so).
+ *
+ * The library runs the per-electron step loop of "Betaboltz: a Monte-Carlo
+ * simulation tool for gas scattering processes" (Renda, Ciubotaru, Banu,
+ * arXiv:1901.08140) on one NVIDIA GB300 GPU (sm_103a): electrons drift
+ * through a user-defined gas mixture under static uniform E and B fields
+ * (Sec. 2; "Nature of problem" in the program summary), by null-collision
+ * free flights (Eqs. 3-4), analytic classical motion (Sec. 3.6), a collision
+ * channel drawn from the mixture's cross-section tables (Eq. 2), scattering
+ * (Eqs. 5, 8, 9) and FP64 swarm tallies (Sec. 2.3, Eqs. 15-27).
+ *
+ * Conventions used by every call:
+ *   - SI units, except energies in eV and reduced fields in Td
+ *     (1 Td = 1e-21 V m^2).
+ *   - Axes: the electric force on the electron points along +z, so the
+ *     reported drift velocity W is positive (the paper aligns z with the
+ *     field and prints W > 0).  B lies in the xz plane at angle
+ *     b_angle_rad from +z: B = |B| (sin a, 0, cos a) (Sec. 2.3).
+ *   - Pointers named *_dev are device pointers on the context's device;
+ *     all other pointers are host pointers.
+ *   - Every call returns a bz_status.  On failure the thread-local message
+ *     of bz_last_error() says why; outputs are left untouched.
+ *   - No call falls back to the CPU.  If the CUDA device or kernels are not
+ *     usable, calls return BZ_ECUDA.
+ */
+#ifndef BZ_H
+#define BZ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BZ_ABI_VERSION 1
+
+typedef enum {
+    BZ_OK = 0,
+    BZ_EINVAL = 1,    /* invalid argument or table */
+    BZ_ENOMEM = 2,    /* device or host allocation failed */
+    BZ_EBUDGET = 3,   /* request exceeds an admission or size limit */
+    BZ_ETRIAL = 4,    /* fixed trial frequency was exceeded (Sec. 6.1) */
+    BZ_ETIMEOUT = 5,  /* a bounded device wait gave up */
+    BZ_ECUDA = 6,     /* CUDA runtime or kernel error */
+    BZ_ECANCEL = 7,   /* request cancelled */
+    BZ_ENOTREADY = 8  /* result not available yet (non-blocking query) */
+} bz_status;
+
+typedef enum { BZ_ELASTIC = 0, BZ_EXCITATION = 1, BZ_ATTACHMENT = 2, BZ_IONIZATION = 3 } bz_kind;
+typedef enum { BZ_ANG_ISOTROPIC = 0, BZ_ANG_SCREENED_COULOMB = 1 } bz_angular;
+typedef enum { BZ_TRIAL_LAZY = 0, BZ_TRIAL_FIXED = 1 } bz_trial_mode;
+
+typedef struct bz_ctx bz_ctx;
+typedef struct bz_mixture bz_mixture;
+typedef struct bz_swarm bz_swarm;
+
+/* Device-memory provider.  alloc returns a device pointer of at least
+ * `bytes` usable on `stream` (NULL on failure); free releases it.  Passing
+ * NULL to bz_create uses cudaMallocAsync / cudaFreeAsync. */
+typedef struct {
+    void *(*alloc)(size_t bytes, void *stream, void *user);
+    void (*free)(void *ptr, size_t bytes, void *stream, void *user);
+    void *user;
+} bz_allocator;
+
+/* Creates a context on CUDA device `device`.  The allocator is copied.
+ * Errors: BZ_EINVAL (bad device), BZ_ECUDA. */
+bz_status bz_create(int device, const bz_allocator *alloc, bz_ctx **out);
+void bz_destroy(bz_ctx *ctx);
+/* Message of the last failure on the calling thread ("" if none). */
+const char *bz_last_error(void);
+int bz_abi_version(void);
+
+/* ------------------------------------------------------------------------
+ * Gas mixtures (Eq. 2; Sec. 3.5 GasMixture by number density).
+ *
+ * A gas is a set of channels with its molecule mass M and number density
+ * n_k.  A channel is a cross-section table sigma(eps) on strictly increasing
+ * energies, interpolated linearly (Sec. 5) and extended per Sec. 2.2:
+ * elastic tables continue to the left with their first value, inelastic
+ * ones are zero below threshold (and rise linearly from (threshold, 0) when
+ * the table starts above it); to the right a power law sigma = A eps^K goes
+ * through the last two points (Eqs. 12-14), or the last value continues when
+ * one of them is zero.  threshold_eV is the energy loss eps_k of Eq. (9)
+ * (the ionization potential for ionization; ignored for elastic).
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    int32_t kind;             /* bz_kind */
+    int32_t n_points;         /* >= 1 */
+    double threshold_eV;      /* >= 0 */
+    const double *energy_eV;  /* host, n_points, strictly increasing, >= 0 */
+    const double *sigma_m2;   /* host, n_points, >= 0; 0 below threshold */
+} bz_channel;
+
+typedef struct {
+    double mass_kg;           /* > 0 */
+    double number_density_m3; /* > 0 */
+    int32_t angular;          /* bz_angular of every channel of this gas */
+    int32_t n_channels;       /* >= 1 */
+    const bz_channel *channels;
+} bz_gas;
+
+typedef struct {
+    double eps_cap_eV;        /* majorant range [0, eps_cap]; <= 0: largest table energy */
+    double majorant_guard;    /* nu' = (1 + guard) max nu; < 0: default 1e-6 */
+    int32_t channels_in_smem; /* -1 auto, 0 channel tables stay in L2, 1 stage them in shared memory */
+    int32_t smem_budget;      /* bytes of shared memory per block for tables; <= 0: auto */
+} bz_mixture_opts;
+
+/* Validates and compiles a mixture: union energy grid over all channels and
+ * thresholds, per-interval density sums and slopes, per-channel interval
+ * coefficients, power-law tails, a log-energy bucket index and the exact
+ * trial frequency nu' = max over [0, eps_cap] of nu(eps) (Sec. 6.2,
+ * LazyTrialFrequency made exact).  Tables are deep-copied to the device;
+ * the caller's arrays may be freed on return.  opts may be NULL (defaults).
+ * Errors: BZ_EINVAL (non-monotone grid, negative or non-finite sigma, sigma
+ * > 0 below threshold, mass or density <= 0, > 65535 union points),
+ * BZ_ENOMEM, BZ_ECUDA. */
+bz_status bz_create_gas_mixture(bz_ctx *ctx, const bz_gas *gases, int32_t n_gases,
+                                const bz_mixture_opts *opts, bz_mixture **out);
+void bz_destroy_mixture(bz_mixture *mix);
+
+typedef struct {
+    double nu_max;            /* majorant before the guard [1/s] */
+    double nu_trial;          /* nu' used by lazy mode [1/s] */
+    double eps_at_max;        /* energy of the maximum [eV] */
+    double eps_cap;           /* [eV] */
+    double n_total;           /* sum of number densities [1/m^3] */
+    int32_t n_gases, n_channels, n_records, n_buckets;
+    int32_t smem_bytes;       /* shared memory the step kernel stages */
+    int32_t channels_in_smem;
+    int32_t first_tail_record;
+    int32_t reserved;
+} bz_mixture_info;
+
+bz_status bz_mixture_get_info(const bz_mixture *mix, bz_mixture_info *out);
+
+/* ------------------------------------------------------------------------
+ * Swarm runs (Sec. 2.3: N primaries at the origin, I real collisions each;
+ * Sec. 3.2 limiters: interactions, time).
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    double e_over_n_Td;       /* set by bz_set_fields */
+    double b_T;
+    double b_angle_rad;
+    uint64_t n_electrons;     /* N >= 1 */
+    uint32_t real_collisions; /* I: InteractionBulletLimiter; >= 1 */
+    int32_t precision;        /* 32: FP32 flights and scattering, FP64 tallies; 64: FP64 throughout */
+    int32_t trial_mode;       /* bz_trial_mode */
+    int32_t attach_keep_state;/* 1: a dummy attachment leaves the electron unchanged */
+    double nu_trial;          /* fixed mode: nu' [1/s]; lazy mode: > 0 overrides the start value */
+    double eps0_mean_eV;      /* isotropic Maxwellian start with this mean energy (0: at rest) */
+    double t_end_s;           /* > 0: TimeBulletLimiter, the last flight is cut at t_end */
+    uint64_t max_trials;      /* per particle, 0: 2^31 - 1 */
+    uint64_t seed;            /* Philox key of the swarm */
+    uint64_t id_offset;       /* first particle id: ids id_offset .. id_offset + N - 1 */
+    int32_t block_threads;    /* launch shape, 0: auto */
+    int32_t blocks_per_sm;    /* 0: auto (occupancy) */
+} bz_swarm_config;
+
+/* Fills *cfg with defaults: N = 1e4, I = 1000, FP32, lazy mode, Maxwellian
+ * start with mean 0.1 eV, no time limit, seed 1901081400, fields zero. */
+void bz_config_defaults(bz_swarm_config *cfg);
+
+/* Sets the fields of a configuration: reduced field E/N [Td] (E = (E/N) N
+ * with N the mixture's total density), |B| [T] and the angle of B from +z
+ * in the xz plane [rad].  Errors: BZ_EINVAL (negative or non-finite). */
+bz_status bz_set_fields(bz_swarm_config *cfg, double e_over_n_Td, double b_T, double b_angle_rad);
+
+/* Launches one swarm on `stream` (cudaStream_t; NULL: the legacy default
+ * stream) and returns at once.  The swarm owns its device buffers until
+ * bz_destroy_swarm.  Each electron starts at the origin with an isotropic
+ * Maxwellian velocity and runs until its I-th real collision (or t_end).
+ * Ionizations and attachments are dummy (counted, Sec. 2.3).
+ * Errors: BZ_EINVAL, BZ_ENOMEM, BZ_ECUDA. */
+bz_status bz_run_swarm(bz_ctx *ctx, const bz_mixture *mix, const bz_swarm_config *cfg,
+                       void *stream, bz_swarm **out);
+
+/* Swarm results (Sec. 2.3 and the Drifter fields of the worked example in
+ * Sec. 7).  Per-particle ratio means as the paper writes them; "_flux"
+ * fields are ratios of sums; "_se" fields are standard errors from 32 batch
+ * groups (particle id mod 32).  d_n = x_n - t_n W_vec (full drift vector). */
+typedef struct {
+    double W, W_se;           /* <z/t> [m/s] (Eq. 15) */
+    double Wx, Wy;            /* <x/t>, <y/t> (E x B drift) */
+    double W_flux;            /* sum z / sum t */
+    double lorentz_angle;     /* atan2(|W_perp|, W) [rad] */
+    double mu, mu_N, mu_0;    /* W/E; mu N; mu N / N_Loschmidt */
+    double eps, eps_se;       /* mean energy just before real collisions [eV] (Eq. 18) */
+    double eps_after, eps_after_se; /* just after (Eq. 19) */
+    double alpha, alpha_se, eta, eta_se; /* <G/z>, <D/z> [1/m] (Eqs. 16-17) */
+    double alpha_flux, eta_flux;
+    double D, D_se, D_L, D_L_se, D_T, D_T_se; /* [m^2/s] (Eqs. 22-24) */
+    double D_L_flux, D_T_flux;
+    double sig, sig_se, sig_L, sig_L_se, sig_T, sig_T_se; /* [m] (Eqs. 25-27) */
+    double efficiency;        /* real / (real + null + fail) (Eq. 28) */
+    double E_V_m, n_total, nu_trial, t_mean;
+    uint64_t n_particles, n_real, n_null, n_fail, n_ion, n_att, n_incomplete;
+    int32_t error_flags;      /* device error bits (see BZ_ERR_*) */
+    int32_t reserved;
+} bz_tallies;
+
+#define BZ_ERR_STAGE_TIMEOUT 1u /* table staging wait gave up */
+#define BZ_ERR_TRIAL 2u         /* fixed nu' exceeded */
+#define BZ_ERR_NONFINITE 4u     /* non-finite energy met; particle stopped */
+#define BZ_ERR_MAX_TRIALS 8u    /* a particle reached max_trials */
+
+/* Waits for the swarm and copies its tallies into *out.
+ * Errors: BZ_ETRIAL (fixed mode exceeded), BZ_ETIMEOUT, BZ_ECUDA. */
+bz_status bz_read_tallies(bz_swarm *sw, bz_tallies *out);
+/* Non-blocking: BZ_ENOTREADY while the swarm runs, else as bz_read_tallies. */
+bz_status bz_query_tallies(bz_swarm *sw, bz_tallies *out);
+
+/* Per-particle final state (slot i = particle id_offset + i), copied into
+ * caller-owned host arrays of length >= N; any pointer may be NULL.  Waits
+ * for the swarm. */
+typedef struct {
+    double *x, *y, *z, *t;         /* position [m] and time [s] at the end */
+    double *sum_e, *sum_e2;        /* energy sums before / after real collisions [eV] */
+    float *vx, *vy, *vz;           /* final velocity [m/s] */
+    float *nu_p;                   /* final trial frequency of the particle [1/s] */
+    uint32_t *n_real, *n_null, *n_fail, *n_ion, *n_att, *steps, *status;
+} bz_particles;
+
+bz_status bz_read_particles(bz_swarm *sw, const bz_particles *out);
+void bz_destroy_swarm(bz_swarm *sw);
+
+/* ------------------------------------------------------------------------
+ * Verification entry points.
+ * ------------------------------------------------------------------------ */
+
+/* One trial step per particle from a state at a real collision (single-step
+ * replay, Sec. 2): state_in_dev[8 n] holds, per particle i, at 8i..8i+7:
+ * x, y, z, vx, vy, vz, t, nu'.  The step draws Philox counter
+ * (id, steps[i], 0), flies, and takes the fail / null / real decision.
+ * Outputs: state_out_dev[8 n] the state after the step; decision_dev[n] the
+ * global channel index, -1 null, -2 fail; eps_dev[2 n] the energy before and
+ * after the collision.  Uses cfg's fields, precision, seed and trial mode.
+ * Asynchronous on `stream`. */
+bz_status bz_step_replay(bz_ctx *ctx, const bz_mixture *mix, const bz_swarm_config *cfg, int64_t n,
+                         const double *state_in_dev, const uint64_t *ids_dev, const uint32_t *steps_dev,
+                         double *state_out_dev, int32_t *decision_dev, double *eps_dev, void *stream);
+
+/* Philox4x32-10 (Salmon et al., SC'11) on the device: out_dev[4 i..] =
+ * Philox(ctr_dev[4 i..], key) for i < n.  Asynchronous on `stream`. */
+bz_status bz_philox(bz_ctx *ctx, int64_t n, const uint32_t *ctr_dev, uint64_t key, uint32_t *out_dev,
+                    void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BZ_H */

@@ -74,8 +74,11 @@ void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out
     out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
-/* 24-bit uniform on the open interval (0,1): ((w >> 8) + 1/2) / 2^24. */
-double or_uniform(uint32_t w) { return ((double)(w >> 8) + 0.5) * (1.0 / 16777216.0); }
+/* Uniform on the open interval (0,1) from the top 23 bits of a word:
+ * ((w >> 9) + 1/2) / 2^23.  Every value is an odd multiple of 2^-24 below 1,
+ * exactly representable in FP32 and FP64, so an FP32 consumer of the same
+ * word sees the same number. */
+double or_uniform(uint32_t w) { return ((double)(w >> 9) + 0.5) * (1.0 / 8388608.0); }
 
 static void draw4(uint64_t seed, uint64_t id, uint32_t step, uint32_t sub, double u[4])
 {

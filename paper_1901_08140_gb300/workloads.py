@@ -146,28 +146,37 @@ def _triangle(e: np.ndarray, th: float, peak: float, width: float) -> np.ndarray
     return peak * np.clip(np.minimum(up, down), 0.0, None)
 
 
+def _on_grid(grid: np.ndarray, th: float, lo: float = 0.0, hi: float = np.inf) -> np.ndarray:
+    """Energies of an inelastic table on a gas's common grid: the threshold,
+    then the grid points above it (inside [lo, hi])."""
+    pts = grid[(grid > th) & (grid >= lo) & (grid <= hi)]
+    return np.concatenate([[th], pts])
+
+
 def co2_like(n: float = N_STP_293, points: int = 500) -> Gas:
-    e_el = np.geomspace(1e-3, 100.0, points)
-    s_el = 1e-20 + 9e-20 / (1.0 + (e_el / 0.5) ** 0.8)
-    chans = [Channel(ELASTIC, 0.0, e_el, s_el)]
+    """20 channels; every table lives on the gas's 500-point log grid
+    (1e-3 - 100 eV), inelastic ones from their threshold upwards."""
+    grid = np.geomspace(1e-3, 100.0, points)
+    s_el = 1e-20 + 9e-20 / (1.0 + (grid / 0.5) ** 0.8)
+    chans = [Channel(ELASTIC, 0.0, grid, s_el)]
     for th in np.geomspace(0.083, 2.5, 8):
-        e = np.geomspace(th, 100.0, points)
+        e = _on_grid(grid, float(th))
         s = _triangle(e, th, 2e-21, max(0.3 * th, 0.05))
         s[0] = 0.0
         chans.append(Channel(EXCITATION, float(th), e, s))
     for th in np.linspace(7.0, 13.0, 9):
-        e = np.geomspace(th, 100.0, points)
+        e = _on_grid(grid, float(th))
         s = np.where(e <= th + 5.0, 5e-22 * (e - th) / 5.0, 5e-22)
         s[0] = 0.0
         chans.append(Channel(EXCITATION, float(th), e, s))
     # dissociative attachment: Gaussian peak at 4.4 eV, zero outside 3-6 eV
-    e = np.concatenate([np.geomspace(3.0, 6.0, points - 1), [100.0]])
+    e = np.concatenate([_on_grid(grid, 3.0, hi=6.0), [6.0, 100.0]])
     s = 1.5e-22 * np.exp(-0.5 * ((e - 4.4) / 0.5) ** 2)
     s[0] = 0.0
     s[-2:] = 0.0
     chans.append(Channel(ATTACHMENT, 3.0, e, s))
     ip = 13.8
-    e = np.geomspace(ip, 100.0, points)
+    e = _on_grid(grid, ip)
     s = 2e-20 * (e - ip) / (100.0 - ip)
     chans.append(Channel(IONIZATION, ip, e, s))
     return Gas("co2-like", 44.01 * ATOMIC_MASS_UNIT, n, ISOTROPIC, chans)
@@ -194,17 +203,17 @@ def random_gas(rng: np.random.Generator, name: str, n: float = N_STP_293) -> Gas
         pick = rng.uniform()
         if pick < 0.45:
             th = float(np.exp(rng.uniform(np.log(0.05), np.log(3.0))))
-            e = np.geomspace(th, 100.0, points)
+            e = _on_grid(e_el, th)
             s = _triangle(e, th, float(rng.uniform(5e-22, 3e-21)), max(0.3 * th, 0.05))
         elif pick < 0.85 or has_ion:
             th = float(rng.uniform(6.0, 15.0))
-            e = np.geomspace(th, 100.0, points)
+            e = _on_grid(e_el, th)
             peak = float(rng.uniform(1e-22, 1e-21))
             s = np.where(e <= th + 5.0, peak * (e - th) / 5.0, peak)
         elif pick < 0.93 and not has_att:
             has_att = True
             c = float(rng.uniform(2.0, 8.0))
-            e = np.concatenate([np.geomspace(c - 1.5, c + 1.5, points - 1), [100.0]])
+            e = np.concatenate([_on_grid(e_el, c - 1.5, hi=c + 1.5), [c + 1.5, 100.0]])
             s = float(rng.uniform(5e-23, 3e-22)) * np.exp(-0.5 * ((e - c) / 0.5) ** 2)
             s[0] = 0.0
             s[-2:] = 0.0
@@ -213,7 +222,7 @@ def random_gas(rng: np.random.Generator, name: str, n: float = N_STP_293) -> Gas
         else:
             has_ion = True
             th = float(rng.uniform(10.0, 25.0))
-            e = np.geomspace(th, 100.0, points)
+            e = _on_grid(e_el, th)
             s = float(rng.uniform(1e-20, 4e-20)) * (e - th) / (100.0 - th)
             s[0] = 0.0
             chans.append(Channel(IONIZATION, th, e, s))

@@ -31,7 +31,7 @@ def _words(n, step=0, sub=0, key=(12345, 678)):
 
 def test_philox_uniformity_and_independence():
     w = _words(20000)
-    u = (((w >> 8).astype(np.float64)) + 0.5) / 2 ** 24
+    u = (((w >> 9).astype(np.float64)) + 0.5) / 2 ** 23
     flat = u.ravel()
     assert abs(flat.mean() - 0.5) < 4 * math.sqrt(1 / 12 / flat.size)
     assert abs(flat.var() - 1 / 12) < 0.01 * (1 / 12)
@@ -66,10 +66,14 @@ def test_philox_counter_and_key_avalanche():
 
 
 def test_uniform_open_interval_lattice():
-    assert O.uniform(0) == 0.5 / 2 ** 24
-    assert O.uniform(0xFFFFFFFF) == 1 - 0.5 / 2 ** 24
-    assert O.uniform(0xFF) == O.uniform(0)          # only the top 24 bits count
-    assert O.uniform(1 << 8) == 1.5 / 2 ** 24
+    assert O.uniform(0) == 0.5 / 2 ** 23
+    assert O.uniform(0xFFFFFFFF) == 1 - 0.5 / 2 ** 23
+    assert O.uniform(0x1FF) == O.uniform(0)         # only the top 23 bits count
+    assert O.uniform(1 << 9) == 1.5 / 2 ** 23
+    # every value is exactly representable in FP32
+    for w in (0, 1 << 9, 0x80000000, 0xFFFFFFFF, 0x12345678, 0xDEADBEEF):
+        u = O.uniform(w)
+        assert float(np.float32(u)) == u
 
 
 # --------------------------------------------------------------------------
