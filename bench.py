@@ -1,0 +1,328 @@
+#!/usr/bin/env python
+"""Benchmark of the electron-swarm step loop on GB300.
+
+One step = the whole hot path over one batch: the Argon-like E/N sweep
+(32 log-spaced points, 1-1000 Td), 1e6 electrons per point, each electron
+run to its 1000th real collision with FP32 flights and FP64 tallies, every
+swarm's tallies reduced on the device and copied to the host.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  ``value`` is real collisions per second over
+all ranks (device time, CUDA events on the launching stream, max over
+ranks); ``e2e`` is the same metric through the C ABI with host tables and a
+host read of the tallies inside the timed region; ``roofline`` relates the
+step kernel's algorithmic thread operations to the SM issue rate;
+``cpu_baseline`` is the FP64 oracle timed on this host's cores.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes as C
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "collisions/s batched vs plain at ≤0.5% drift-velocity error; p99 swarm latency"
+UNIT = "real collisions/s"
+# Algorithmic thread operations of one trial step and the extra of a real
+# collision (counted from the method's arithmetic; see the design notes).
+ALG_OPS_PER_TRIAL = 95
+ALG_OPS_PER_REAL = 110
+SM_COUNT_NOMINAL = 152
+LANES_PER_SM_CLOCK = 4 * 32     # 4 schedulers x 32 lanes issue per clock
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--points", type=int, default=32)
+    ap.add_argument("--electrons", type=int, default=1_000_000)
+    ap.add_argument("--collisions", type=int, default=1000)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="bound of the CPU-baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["clock sampling unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def sweep_specs(args, rank):
+    from paper_1901_08140_gb300 import workloads as W
+    specs = W.argon_sweep(n_electrons=args.electrons, real_collisions=args.collisions, points=args.points)
+    return specs
+
+
+def cpu_baseline(args, specs, budget_s):
+    """The FP64 oracle, as it stands, on this host's cores: a bounded sample
+    of the same sweep (the same particle ids of each point, taken point by
+    point in a round-robin of id blocks until the time bound)."""
+    from oracle import oracle as O
+    m = O.Mixture(specs[0].gases)
+    cores = O.cpu_count()
+    block = 64 * cores
+    reals = trials = 0
+    t0 = time.perf_counter()
+    rounds = 0
+    done_points = 0
+    while True:
+        for i, s in enumerate(specs):
+            p = O.run_swarm(m, e_over_n_Td=s.e_over_n_Td, real_collisions=s.real_collisions, n=block, seed=s.seed,
+                            id0=rounds * block, threads=cores)
+            reals += int(p["n_real"].sum())
+            trials += int(p["n_real"].sum() + p["n_null"].sum() + p["n_fail"].sum())
+            done_points += 1
+            if time.perf_counter() - t0 > budget_s and done_points >= min(len(specs), 4):
+                break
+        else:
+            rounds += 1
+            continue
+        break
+    dt = time.perf_counter() - t0
+    sample = (f"{done_points} (E/N point, {block}-electron id block) units of the sweep, "
+              f"I={specs[0].real_collisions}, {reals} real / {trials} trial collisions in {dt:.1f} s")
+    return {"value": reals / dt, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+            "trial_collisions_per_s": trials / dt}
+
+
+def run_ours(args):
+    import torch
+    world, rank, local = dist()
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1901_08140_gb300 import build as B
+    B.build()
+    from paper_1901_08140_gb300 import bz
+    specs = sweep_specs(args, rank)
+    ctx = bz.Context(local)
+    mix = bz.Mixture(ctx, specs[0].gases)
+    # weak scaling: every rank runs the whole sweep on its own particle ids
+    cfgs = [bz.config_from_spec(s, id_offset=rank * args.electrons) for s in specs]
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
+
+    def one_step():
+        return [bz.run_swarm(ctx, mix, c, stream) for c in cfgs]
+
+    for _ in range(args.warmup):
+        for sw in one_step():
+            sw.tallies()
+            sw.close()
+    torch.cuda.synchronize(dev)
+
+    clocks = Clocks(local)
+    total_ms = 0.0
+    reals = trials = 0
+    kern_ms = 0.0
+    work = 0.0
+    w_err = []
+    launches = 0
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            torch.distributed.barrier()
+        ev0.record(stream)
+        swarms = one_step()
+        ev1.record(stream)
+        ev1.synchronize()
+        total_ms += ev0.elapsed_time(ev1)
+        torch.cuda.synchronize(dev)
+        for sw in swarms:
+            t = sw.tallies()
+            km, _ = sw.timing()
+            reals += t["n_real"]
+            tr = t["n_real"] + t["n_null"] + t["n_fail"]
+            trials += tr
+            kern_ms += km
+            work += ALG_OPS_PER_TRIAL * tr + ALG_OPS_PER_REAL * t["n_real"]
+            w_err.append(t["W_se"] / abs(t["W"]) if t["W"] else float("inf"))
+            launches += 5   # step kernel + 4 tally kernels
+            sw.close()
+    clk = clocks.stop()
+    t_max = total_ms
+    tot_reals = reals
+    if world > 1:
+        import torch.distributed as tdist
+        x = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        tdist.all_reduce(x, op=tdist.ReduceOp.MAX)
+        t_max = float(x.item())
+        y = torch.tensor([float(reals)], device=dev, dtype=torch.float64)
+        tdist.all_reduce(y)
+        tot_reals = int(y.item())
+    value = tot_reals / (t_max / 1e3)
+
+    # end to end through the C ABI: host tables in, host tallies out
+    e2e = None
+    if not args.no_e2e:
+        h2d = d2h = 0
+        e_reals = 0
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        m2 = bz.Mixture(ctx, specs[0].gases)
+        h2d += m2.info["table_bytes"]
+        sws = [bz.run_swarm(ctx, m2, c, stream) for c in cfgs]
+        h2d += len(cfgs) * (16 + 256)   # counter/flag reset and kernel arguments
+        for sw in sws:
+            e_reals += sw.tallies()["n_real"]
+            d2h += C.sizeof(bz.bz_tallies)
+        torch.cuda.synchronize(dev)
+        dt = time.perf_counter() - t0
+        for sw in sws:
+            sw.close()
+        m2.close()
+        e2e = {"value": e_reals / dt, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    sm_mhz = clk.get("sm_mhz") or 2070.0
+    peak = torch.cuda.get_device_properties(dev).multi_processor_count * LANES_PER_SM_CLOCK * sm_mhz * 1e6
+    achieved = work / (kern_ms / 1e3)
+    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tops/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "swarm_kernel<float,true>",
+                "note": f"algorithmic thread-ops ({ALG_OPS_PER_TRIAL}/trial + {ALG_OPS_PER_REAL}/real) over "
+                        f"SMs x 128 lanes x median SM clock {sm_mhz:.0f} MHz"}
+    if rank != 0:
+        return
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu = cpu_baseline(args, specs, args.cpu_seconds)
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"Argon-like E/N sweep: {args.points} log points 1-1000 Td x "
+                               f"{args.electrons} electrons x {args.collisions} real collisions, "
+                               "FP32 flights, FP64 tallies, lazy exact trial frequency, B = 0",
+                   "mode": "plain (one persistent launch per swarm)", "swarms": args.points,
+                   "electrons_per_swarm": args.electrons, "real_collisions": args.collisions,
+                   "l2": "flushed between steps (256 MiB write)", "parallelism": f"dp{world} (particle ids)"},
+        "trial_collisions_per_s": trials * world / (t_max / 1e3) if world == 1 else None,
+        "efficiency": reals / trials if trials else None,
+        "max_rel_se_W": max(w_err) if w_err else None,
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
+    }
+    print(json.dumps(out), flush=True)
+
+
+def run_reference(args):
+    world, rank, local = dist()
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    specs = sweep_specs(args, 0)
+    m = O.Mixture(specs[0].gases)
+    cores = O.cpu_count()
+    block = 16 * cores
+    # one step: a bounded sample of the sweep (every E/N point, `block` electrons)
+
+    def step(k):
+        r = t = 0
+        for s in specs:
+            p = O.run_swarm(m, e_over_n_Td=s.e_over_n_Td, real_collisions=s.real_collisions, n=block, seed=s.seed,
+                            id0=k * block, threads=cores)
+            r += int(p["n_real"].sum())
+            t += int(p["n_real"].sum() + p["n_null"].sum() + p["n_fail"].sum())
+        return r, t
+
+    for k in range(args.warmup):
+        step(k)
+    t0 = time.perf_counter()
+    reals = trials = 0
+    for k in range(args.steps):
+        r, t = step(args.warmup + k)
+        reals += r
+        trials += t
+    dt = time.perf_counter() - t0
+    value = reals / dt
+    sample = (f"per step: all {len(specs)} E/N points x {block} electrons x I={specs[0].real_collisions} "
+              f"(FP64 oracle, {cores} threads)")
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": f"Argon-like E/N sweep: {args.points} log points 1-1000 Td x "
+                               f"{args.electrons} electrons x {args.collisions} real collisions, "
+                               "FP32 flights, FP64 tallies, lazy exact trial frequency, B = 0",
+                   "sample": sample},
+        "trial_collisions_per_s": trials / dt,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

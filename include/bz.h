@@ -132,10 +132,16 @@ typedef struct {
     int32_t smem_bytes;       /* shared memory the step kernel stages */
     int32_t channels_in_smem;
     int32_t first_tail_record;
-    int32_t reserved;
+    int32_t table_bytes;      /* device bytes of the compiled tables (FP32 + FP64 copies) */
 } bz_mixture_info;
 
 bz_status bz_mixture_get_info(const bz_mixture *mix, bz_mixture_info *out);
+
+/* Host only: validates and compiles a mixture exactly as
+ * bz_create_gas_mixture does and reports its info, without touching a
+ * device (smem_bytes and channels_in_smem are left 0).  Same errors. */
+bz_status bz_mixture_compile_info(const bz_gas *gases, int32_t n_gases, const bz_mixture_opts *opts,
+                                  bz_mixture_info *out);
 
 /* ------------------------------------------------------------------------
  * Swarm runs (Sec. 2.3: N primaries at the origin, I real collisions each;
@@ -225,6 +231,11 @@ typedef struct {
 } bz_particles;
 
 bz_status bz_read_particles(bz_swarm *sw, const bz_particles *out);
+
+/* Device time of the swarm's step kernel and of its tally kernels [ms],
+ * from CUDA events recorded around them on the swarm's stream.  Waits for
+ * the swarm. */
+bz_status bz_swarm_timing(bz_swarm *sw, double *step_ms, double *tally_ms);
 void bz_destroy_swarm(bz_swarm *sw);
 
 /* ------------------------------------------------------------------------

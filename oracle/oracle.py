@@ -130,6 +130,7 @@ class Mixture:
         self.ch_gas = f["ch_gas"]
         self.ch_threshold = f["ch_threshold"]
         self.gas_mass = f["gas_mass"]
+        self.gas_density = f["gas_density"]
         self.gas_angular = f["gas_angular"]
 
     def __del__(self):

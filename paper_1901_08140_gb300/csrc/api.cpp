@@ -1,0 +1,492 @@
+// api.cpp -- the C ABI of libbz.so (declared in include/bz.h).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+
+#include "bz.h"
+#include "kernels.h"
+
+struct bz_ctx {
+    int device;
+    bz_allocator alloc;
+    bool custom_alloc;
+    int sm_count;
+    int smem_optin;
+};
+
+struct bz_mixture {
+    bz_ctx *ctx;
+    bz::CompiledMixture cm;
+    uint8_t *blob32, *blob64;
+    size_t bytes32, bytes64;
+    bool ch_smem32, ch_smem64;
+};
+
+struct bz_swarm {
+    bz_ctx *ctx;
+    bz_swarm_config cfg;
+    cudaStream_t stream;
+    uint8_t *mem;
+    size_t bytes;
+    bz::ParticlesDev p;
+    uint32_t *err;
+    bz_tallies *tallies_dev;
+    bz_tallies *tallies_host;  // pinned
+    cudaEvent_t done;
+    cudaEvent_t ev[3];  // before the step kernel, after it, after the tallies
+    uint64_t n;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+bz_status fail(bz_status s, const std::string &msg)
+{
+    g_err = msg;
+    return s;
+}
+
+bz_status cuda_fail(cudaError_t e, const char *where)
+{
+    g_err = std::string(where) + ": " + cudaGetErrorString(e);
+    return BZ_ECUDA;
+}
+
+void *dev_alloc(bz_ctx *c, size_t bytes, cudaStream_t s)
+{
+    if (c->custom_alloc) return c->alloc.alloc(bytes, (void *)s, c->alloc.user);
+    void *p = nullptr;
+    if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) return nullptr;
+    return p;
+}
+
+void dev_free(bz_ctx *c, void *p, size_t bytes, cudaStream_t s)
+{
+    if (!p) return;
+    if (c->custom_alloc) c->alloc.free(p, bytes, (void *)s, c->alloc.user);
+    else cudaFreeAsync(p, s);
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+bz::Fields make_fields(const bz_swarm_config &cfg, double n_total)
+{
+    bz::Fields f;
+    memset(&f, 0, sizeof f);
+    const double E = cfg.e_over_n_Td * bz::kTownsend * n_total;
+    f.a = bz::kQe * E / bz::kMe;
+    f.has_b = cfg.b_T > 0.0 ? 1 : 0;
+    f.b[0] = sin(cfg.b_angle_rad);
+    f.b[1] = 0.0;
+    f.b[2] = cos(cfg.b_angle_rad);
+    f.w = bz::kQe * cfg.b_T / bz::kMe;
+    if (f.has_b) {
+        // E x B drift of the electron: (b x a z) / w
+        f.vD[0] = f.a * f.b[1] / f.w;
+        f.vD[1] = -f.a * f.b[0] / f.w;
+        f.vD[2] = 0.0;
+    }
+    f.a_par = f.a * f.b[2];
+    return f;
+}
+
+bz_status validate_config(const bz_swarm_config *cfg)
+{
+    if (!cfg) return fail(BZ_EINVAL, "null configuration");
+    if (cfg->precision != 32 && cfg->precision != 64) return fail(BZ_EINVAL, "precision must be 32 or 64");
+    if (cfg->n_electrons < 1) return fail(BZ_EINVAL, "n_electrons must be >= 1");
+    if (cfg->real_collisions < 1) return fail(BZ_EINVAL, "real_collisions must be >= 1");
+    if (!(cfg->e_over_n_Td >= 0.0) || !isfinite(cfg->e_over_n_Td)) return fail(BZ_EINVAL, "bad E/N");
+    if (!(cfg->b_T >= 0.0) || !isfinite(cfg->b_T) || !isfinite(cfg->b_angle_rad)) return fail(BZ_EINVAL, "bad B");
+    if (cfg->trial_mode != BZ_TRIAL_LAZY && cfg->trial_mode != BZ_TRIAL_FIXED) return fail(BZ_EINVAL, "bad trial mode");
+    if (cfg->trial_mode == BZ_TRIAL_FIXED && !(cfg->nu_trial > 0.0)) return fail(BZ_EINVAL, "fixed mode needs nu_trial > 0");
+    if (!(cfg->eps0_mean_eV >= 0.0) || !isfinite(cfg->eps0_mean_eV)) return fail(BZ_EINVAL, "bad eps0_mean_eV");
+    if (!(cfg->t_end_s >= 0.0) || !isfinite(cfg->t_end_s)) return fail(BZ_EINVAL, "bad t_end_s");
+    if (cfg->max_trials > 0xFFFFFFFFull) return fail(BZ_EINVAL, "max_trials must fit 32 bits");
+    if (cfg->block_threads != 0 && cfg->block_threads != 256) return fail(BZ_EINVAL, "block_threads must be 0 or 256");
+    if (cfg->blocks_per_sm < 0) return fail(BZ_EINVAL, "blocks_per_sm must be >= 0");
+    return BZ_OK;
+}
+
+// Fills the kernel arguments common to swarm runs and replays.
+bz_status prepare_run(const bz_mixture *mix, const bz_swarm_config *cfg, bz::RunArgs *a, bool *ch_smem)
+{
+    memset(a, 0, sizeof *a);
+    const bool p64 = cfg->precision == 64;
+    a->blob = p64 ? mix->blob64 : mix->blob32;
+    a->lay = p64 ? mix->cm.lay64 : mix->cm.lay32;
+    *ch_smem = p64 ? mix->ch_smem64 : mix->ch_smem32;
+    a->stage_bytes = *ch_smem ? a->lay.stage_all : a->lay.stage_tables;
+    if ((int)a->stage_bytes > mix->ctx->smem_optin - 1024)
+        return fail(BZ_EBUDGET, "mixture tables exceed the shared memory of one block");
+    a->key0 = (uint32_t)cfg->seed;
+    a->key1 = (uint32_t)(cfg->seed >> 32);
+    a->id_offset = cfg->id_offset;
+    a->n = cfg->n_electrons;
+    a->I = cfg->real_collisions;
+    a->fixed = cfg->trial_mode == BZ_TRIAL_FIXED;
+    a->attach_keep = cfg->attach_keep_state != 0;
+    a->nu0 = (cfg->nu_trial > 0.0) ? cfg->nu_trial : mix->cm.nu_trial;
+    a->eps0_mean = cfg->eps0_mean_eV;
+    a->t_end = cfg->t_end_s;
+    a->max_trials = cfg->max_trials ? cfg->max_trials : 0x7FFFFFFFull;
+    a->f = make_fields(*cfg, mix->cm.n_total);
+    return BZ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *bz_last_error(void) { return g_err.c_str(); }
+int bz_abi_version(void) { return BZ_ABI_VERSION; }
+
+bz_status bz_create(int device, const bz_allocator *alloc, bz_ctx **out)
+{
+    if (!out) return fail(BZ_EINVAL, "null output");
+    *out = nullptr;
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+    if (device < 0 || device >= n) return fail(BZ_EINVAL, "no such CUDA device");
+    if ((e = cudaSetDevice(device)) != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    if (alloc && (!alloc->alloc || !alloc->free)) return fail(BZ_EINVAL, "allocator needs alloc and free");
+    bz_ctx *c = new (std::nothrow) bz_ctx();
+    if (!c) return fail(BZ_ENOMEM, "host allocation");
+    c->device = device;
+    c->custom_alloc = alloc != nullptr;
+    if (alloc) c->alloc = *alloc;
+    cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+    cudaDeviceGetAttribute(&c->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    *out = c;
+    return BZ_OK;
+}
+
+void bz_destroy(bz_ctx *ctx) { delete ctx; }
+
+bz_status bz_create_gas_mixture(bz_ctx *ctx, const bz_gas *gases, int32_t n_gases, const bz_mixture_opts *opts,
+                                bz_mixture **out)
+{
+    if (!ctx || !out) return fail(BZ_EINVAL, "null argument");
+    *out = nullptr;
+    bz_mixture *m = new (std::nothrow) bz_mixture();
+    if (!m) return fail(BZ_ENOMEM, "host allocation");
+    m->ctx = ctx;
+    std::string err;
+    bz_status st = bz::compile_mixture(gases, n_gases, opts, &m->cm, &err);
+    if (st != BZ_OK) {
+        delete m;
+        return fail(st, err);
+    }
+    cudaSetDevice(ctx->device);
+    m->bytes32 = m->cm.blob32.size();
+    m->bytes64 = m->cm.blob64.size();
+    m->blob32 = (uint8_t *)dev_alloc(ctx, m->bytes32, 0);
+    m->blob64 = (uint8_t *)dev_alloc(ctx, m->bytes64, 0);
+    if (!m->blob32 || !m->blob64) {
+        dev_free(ctx, m->blob32, m->bytes32, 0);
+        dev_free(ctx, m->blob64, m->bytes64, 0);
+        delete m;
+        return fail(BZ_ENOMEM, "device allocation of the mixture tables");
+    }
+    cudaError_t e = cudaMemcpy(m->blob32, m->cm.blob32.data(), m->bytes32, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(m->blob64, m->cm.blob64.data(), m->bytes64, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        dev_free(ctx, m->blob32, m->bytes32, 0);
+        dev_free(ctx, m->blob64, m->bytes64, 0);
+        delete m;
+        return cuda_fail(e, "copy of the mixture tables");
+    }
+    const int mode = opts ? opts->channels_in_smem : -1;
+    int budget = (opts && opts->smem_budget > 0) ? opts->smem_budget : 96 * 1024;
+    if (budget > ctx->smem_optin - 1024) budget = ctx->smem_optin - 1024;
+    m->ch_smem32 = mode == 1 ? true : mode == 0 ? false : (int)m->cm.lay32.stage_all <= budget;
+    m->ch_smem64 = mode == 1 ? true : mode == 0 ? false : (int)m->cm.lay64.stage_all <= budget;
+    if (m->ch_smem32 && (int)m->cm.lay32.stage_all > ctx->smem_optin - 1024) m->ch_smem32 = false;
+    if (m->ch_smem64 && (int)m->cm.lay64.stage_all > ctx->smem_optin - 1024) m->ch_smem64 = false;
+    m->cm.info.channels_in_smem = m->ch_smem32 ? 1 : 0;
+    m->cm.info.smem_bytes = (int32_t)(m->ch_smem32 ? m->cm.lay32.stage_all : m->cm.lay32.stage_tables);
+    m->cm.info.table_bytes = (int32_t)(m->bytes32 + m->bytes64);
+    *out = m;
+    return BZ_OK;
+}
+
+void bz_destroy_mixture(bz_mixture *mix)
+{
+    if (!mix) return;
+    cudaSetDevice(mix->ctx->device);
+    cudaDeviceSynchronize();
+    dev_free(mix->ctx, mix->blob32, mix->bytes32, 0);
+    dev_free(mix->ctx, mix->blob64, mix->bytes64, 0);
+    delete mix;
+}
+
+bz_status bz_mixture_get_info(const bz_mixture *mix, bz_mixture_info *out)
+{
+    if (!mix || !out) return fail(BZ_EINVAL, "null argument");
+    *out = mix->cm.info;
+    return BZ_OK;
+}
+
+bz_status bz_mixture_compile_info(const bz_gas *gases, int32_t n_gases, const bz_mixture_opts *opts,
+                                  bz_mixture_info *out)
+{
+    if (!out) return fail(BZ_EINVAL, "null argument");
+    bz::CompiledMixture cm;
+    std::string err;
+    bz_status st = bz::compile_mixture(gases, n_gases, opts, &cm, &err);
+    if (st != BZ_OK) return fail(st, err);
+    *out = cm.info;
+    return BZ_OK;
+}
+
+void bz_config_defaults(bz_swarm_config *cfg)
+{
+    if (!cfg) return;
+    memset(cfg, 0, sizeof *cfg);
+    cfg->n_electrons = 10000;
+    cfg->real_collisions = 1000;
+    cfg->precision = 32;
+    cfg->trial_mode = BZ_TRIAL_LAZY;
+    cfg->eps0_mean_eV = 0.1;
+    cfg->seed = 1901081400ull;
+}
+
+bz_status bz_set_fields(bz_swarm_config *cfg, double e_over_n_Td, double b_T, double b_angle_rad)
+{
+    if (!cfg) return fail(BZ_EINVAL, "null configuration");
+    if (!(e_over_n_Td >= 0.0) || !isfinite(e_over_n_Td)) return fail(BZ_EINVAL, "E/N must be finite and >= 0");
+    if (!(b_T >= 0.0) || !isfinite(b_T)) return fail(BZ_EINVAL, "|B| must be finite and >= 0");
+    if (!isfinite(b_angle_rad)) return fail(BZ_EINVAL, "B angle must be finite");
+    cfg->e_over_n_Td = e_over_n_Td;
+    cfg->b_T = b_T;
+    cfg->b_angle_rad = b_angle_rad;
+    return BZ_OK;
+}
+
+bz_status bz_run_swarm(bz_ctx *ctx, const bz_mixture *mix, const bz_swarm_config *cfg, void *stream,
+                       bz_swarm **out)
+{
+    if (!ctx || !mix || !out) return fail(BZ_EINVAL, "null argument");
+    *out = nullptr;
+    bz_status st = validate_config(cfg);
+    if (st != BZ_OK) return st;
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    bz::RunArgs a;
+    bool ch_smem;
+    if ((st = prepare_run(mix, cfg, &a, &ch_smem)) != BZ_OK) return st;
+    const uint64_t n = cfg->n_electrons;
+    const int block = 256;
+    int bps = bz::swarm_occupancy(cfg->precision, ch_smem, block, a.stage_bytes);
+    if (bps < 1) return fail(BZ_ECUDA, "step kernel cannot be resident with these tables");
+    if (cfg->blocks_per_sm > 0 && cfg->blocks_per_sm < bps) bps = cfg->blocks_per_sm;
+    uint64_t grid64 = (uint64_t)ctx->sm_count * bps, need = (n + block - 1) / block;
+    const int grid = (int)(grid64 < need ? grid64 : need);
+    const int tblocks = bz::tally_blocks(n, ctx->sm_count);
+
+    bz_swarm *s = new (std::nothrow) bz_swarm();
+    if (!s) return fail(BZ_ENOMEM, "host allocation");
+    s->ctx = ctx;
+    s->cfg = *cfg;
+    s->stream = (cudaStream_t)stream;
+    s->n = n;
+    // one device block: particle outputs, counter and flags, tally scratch
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return o; };
+    const size_t o_x = take(8 * n), o_y = take(8 * n), o_z = take(8 * n), o_t = take(8 * n);
+    const size_t o_se = take(8 * n), o_se2 = take(8 * n);
+    const size_t o_vx = take(4 * n), o_vy = take(4 * n), o_vz = take(4 * n), o_nup = take(4 * n);
+    const size_t o_u[7] = {take(4 * n), take(4 * n), take(4 * n), take(4 * n), take(4 * n), take(4 * n), take(4 * n)};
+    const size_t o_ctr = take(16);
+    const size_t o_p1 = take(sizeof(double) * tblocks * bz::kGroups * bz::kQ1);
+    const size_t o_p2 = take(sizeof(double) * tblocks * bz::kGroups * bz::kQ2);
+    const size_t o_gs = take(sizeof(double) * (bz::kGroups * (bz::kQ1 + bz::kQ2) + 8));
+    const size_t o_tal = take(sizeof(bz_tallies));
+    s->bytes = off;
+    s->mem = (uint8_t *)dev_alloc(ctx, s->bytes, s->stream);
+    if (!s->mem) {
+        delete s;
+        return fail(BZ_ENOMEM, "device allocation of the swarm state");
+    }
+    uint8_t *M = s->mem;
+    s->p = bz::ParticlesDev{(double *)(M + o_x), (double *)(M + o_y), (double *)(M + o_z), (double *)(M + o_t),
+                            (double *)(M + o_se), (double *)(M + o_se2), (float *)(M + o_vx), (float *)(M + o_vy),
+                            (float *)(M + o_vz), (float *)(M + o_nup), (uint32_t *)(M + o_u[0]),
+                            (uint32_t *)(M + o_u[1]), (uint32_t *)(M + o_u[2]), (uint32_t *)(M + o_u[3]),
+                            (uint32_t *)(M + o_u[4]), (uint32_t *)(M + o_u[5]), (uint32_t *)(M + o_u[6])};
+    unsigned long long *counter = (unsigned long long *)(M + o_ctr);
+    s->err = (uint32_t *)(M + o_ctr + 8);
+    s->tallies_dev = (bz_tallies *)(M + o_tal);
+    if ((e = cudaMallocHost(&s->tallies_host, sizeof(bz_tallies))) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&s->done, cudaEventDisableTiming)) != cudaSuccess) {
+        dev_free(ctx, s->mem, s->bytes, s->stream);
+        if (s->tallies_host) cudaFreeHost(s->tallies_host);
+        delete s;
+        return cuda_fail(e, "swarm set-up");
+    }
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaEventCreate(&s->ev[i]);
+    if (e == cudaSuccess) e = cudaMemsetAsync(M + o_ctr, 0, 16, s->stream);
+    a.counter = counter;
+    a.err = s->err;
+    a.out = s->p;
+    if (e == cudaSuccess) e = cudaEventRecord(s->ev[0], s->stream);
+    if (e == cudaSuccess) e = bz::launch_swarm(cfg->precision, ch_smem, a, grid, block, s->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(s->ev[1], s->stream);
+    bz::TallyArgs t;
+    memset(&t, 0, sizeof t);
+    t.x = s->p.x; t.y = s->p.y; t.z = s->p.z; t.t = s->p.t; t.se = s->p.se; t.se2 = s->p.se2;
+    t.n_real = s->p.n_real; t.n_null = s->p.n_null; t.n_fail = s->p.n_fail; t.n_ion = s->p.n_ion;
+    t.n_att = s->p.n_att; t.status = s->p.status;
+    t.n = n;
+    t.id_offset = cfg->id_offset;
+    t.part1 = (double *)(M + o_p1);
+    t.part2 = (double *)(M + o_p2);
+    t.gsum = (double *)(M + o_gs);
+    t.blocks = tblocks;
+    t.E_V_m = cfg->e_over_n_Td * bz::kTownsend * mix->cm.n_total;
+    t.n_total = mix->cm.n_total;
+    t.nu_trial = a.nu0;
+    t.err = s->err;
+    t.out = s->tallies_dev;
+    if (e == cudaSuccess) e = bz::launch_tallies(t, s->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(s->ev[2], s->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s->tallies_host, s->tallies_dev, sizeof(bz_tallies), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(s->done, s->stream);
+    if (e != cudaSuccess) {
+        cudaStreamSynchronize(s->stream);
+        bz_destroy_swarm(s);
+        return cuda_fail(e, "swarm launch");
+    }
+    *out = s;
+    return BZ_OK;
+}
+
+static bz_status finish_tallies(bz_swarm *sw, bz_tallies *out)
+{
+    *out = *sw->tallies_host;
+    if (out->error_flags & BZ_ERR_STAGE_TIMEOUT) return fail(BZ_ETIMEOUT, "table staging timed out");
+    if (out->error_flags & BZ_ERR_TRIAL) return fail(BZ_ETRIAL, "fixed trial frequency exceeded");
+    return BZ_OK;
+}
+
+bz_status bz_read_tallies(bz_swarm *sw, bz_tallies *out)
+{
+    if (!sw || !out) return fail(BZ_EINVAL, "null argument");
+    cudaError_t e = cudaEventSynchronize(sw->done);
+    if (e != cudaSuccess) return cuda_fail(e, "swarm");
+    return finish_tallies(sw, out);
+}
+
+bz_status bz_query_tallies(bz_swarm *sw, bz_tallies *out)
+{
+    if (!sw || !out) return fail(BZ_EINVAL, "null argument");
+    cudaError_t e = cudaEventQuery(sw->done);
+    if (e == cudaErrorNotReady) return BZ_ENOTREADY;
+    if (e != cudaSuccess) return cuda_fail(e, "swarm");
+    return finish_tallies(sw, out);
+}
+
+bz_status bz_read_particles(bz_swarm *sw, const bz_particles *o)
+{
+    if (!sw || !o) return fail(BZ_EINVAL, "null argument");
+    cudaError_t e = cudaEventSynchronize(sw->done);
+    if (e != cudaSuccess) return cuda_fail(e, "swarm");
+    const size_t n = sw->n;
+    struct { void *dst; const void *src; size_t bytes; } cp[] = {
+        {o->x, sw->p.x, 8 * n}, {o->y, sw->p.y, 8 * n}, {o->z, sw->p.z, 8 * n}, {o->t, sw->p.t, 8 * n},
+        {o->sum_e, sw->p.se, 8 * n}, {o->sum_e2, sw->p.se2, 8 * n}, {o->vx, sw->p.vx, 4 * n},
+        {o->vy, sw->p.vy, 4 * n}, {o->vz, sw->p.vz, 4 * n}, {o->nu_p, sw->p.nup, 4 * n},
+        {o->n_real, sw->p.n_real, 4 * n}, {o->n_null, sw->p.n_null, 4 * n}, {o->n_fail, sw->p.n_fail, 4 * n},
+        {o->n_ion, sw->p.n_ion, 4 * n}, {o->n_att, sw->p.n_att, 4 * n}, {o->steps, sw->p.steps, 4 * n},
+        {o->status, sw->p.status, 4 * n}};
+    for (auto &c : cp) {
+        if (!c.dst) continue;
+        if ((e = cudaMemcpy(c.dst, c.src, c.bytes, cudaMemcpyDeviceToHost)) != cudaSuccess)
+            return cuda_fail(e, "copy of particle state");
+    }
+    return BZ_OK;
+}
+
+void bz_destroy_swarm(bz_swarm *sw)
+{
+    if (!sw) return;
+    cudaSetDevice(sw->ctx->device);
+    if (sw->done) cudaEventSynchronize(sw->done);
+    else cudaStreamSynchronize(sw->stream);
+    dev_free(sw->ctx, sw->mem, sw->bytes, sw->stream);
+    if (sw->tallies_host) cudaFreeHost(sw->tallies_host);
+    if (sw->done) cudaEventDestroy(sw->done);
+    for (int i = 0; i < 3; ++i)
+        if (sw->ev[i]) cudaEventDestroy(sw->ev[i]);
+    delete sw;
+}
+
+bz_status bz_swarm_timing(bz_swarm *sw, double *step_ms, double *tally_ms)
+{
+    if (!sw) return fail(BZ_EINVAL, "null argument");
+    cudaError_t e = cudaEventSynchronize(sw->done);
+    float a = 0.f, b = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&a, sw->ev[0], sw->ev[1]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&b, sw->ev[1], sw->ev[2]);
+    if (e != cudaSuccess) return cuda_fail(e, "swarm timing");
+    if (step_ms) *step_ms = a;
+    if (tally_ms) *tally_ms = b;
+    return BZ_OK;
+}
+
+bz_status bz_step_replay(bz_ctx *ctx, const bz_mixture *mix, const bz_swarm_config *cfg, int64_t n,
+                         const double *state_in_dev, const uint64_t *ids_dev, const uint32_t *steps_dev,
+                         double *state_out_dev, int32_t *decision_dev, double *eps_dev, void *stream)
+{
+    if (!ctx || !mix || !cfg) return fail(BZ_EINVAL, "null argument");
+    if (n < 0) return fail(BZ_EINVAL, "n must be >= 0");
+    if (n == 0) return BZ_OK;
+    if (!state_in_dev || !ids_dev || !steps_dev || !state_out_dev || !decision_dev || !eps_dev)
+        return fail(BZ_EINVAL, "null buffer");
+    if (cfg->precision != 32 && cfg->precision != 64) return fail(BZ_EINVAL, "precision must be 32 or 64");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    bz::ReplayArgs r;
+    bool ch_smem;
+    bz_status st = prepare_run(mix, cfg, &r.run, &ch_smem);
+    if (st != BZ_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    uint32_t *err = (uint32_t *)dev_alloc(ctx, 256, s);
+    if (!err) return fail(BZ_ENOMEM, "device allocation");
+    cudaMemsetAsync(err, 0, 4, s);
+    r.run.err = err;
+    r.n = n;
+    r.state_in = state_in_dev;
+    r.ids = ids_dev;
+    r.steps = steps_dev;
+    r.state_out = state_out_dev;
+    r.decision = decision_dev;
+    r.eps_io = eps_dev;
+    const int block = 256;
+    int64_t g = (n + block - 1) / block;
+    const int grid = (int)(g < ctx->sm_count * 4 ? g : ctx->sm_count * 4);
+    e = bz::launch_replay(cfg->precision, ch_smem, r, grid, block, s);
+    dev_free(ctx, err, 256, s);
+    if (e != cudaSuccess) return cuda_fail(e, "replay launch");
+    return BZ_OK;
+}
+
+bz_status bz_philox(bz_ctx *ctx, int64_t n, const uint32_t *ctr_dev, uint64_t key, uint32_t *out_dev, void *stream)
+{
+    if (!ctx) return fail(BZ_EINVAL, "null context");
+    if (n < 0) return fail(BZ_EINVAL, "n must be >= 0");
+    if (n > 0 && (!ctr_dev || !out_dev)) return fail(BZ_EINVAL, "null buffer");
+    if (((uintptr_t)ctr_dev | (uintptr_t)out_dev) & 15) return fail(BZ_EINVAL, "buffers must be 16-byte aligned");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e == cudaSuccess) e = bz::launch_philox(n, ctr_dev, key, out_dev, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "philox launch");
+    return BZ_OK;
+}
+
+}  // extern "C"

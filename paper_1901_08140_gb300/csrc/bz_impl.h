@@ -1,0 +1,77 @@
+// bz_impl.h -- internal layout shared by the mixture compiler (host C++) and
+// the CUDA kernels.  Not part of the public ABI.
+#pragma once
+
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "bz.h"
+
+namespace bz {
+
+// Physical constants (CODATA 2018).
+constexpr double kQe = 1.602176634e-19;       // C
+constexpr double kMe = 9.1093837015e-31;      // kg
+constexpr double kHartreeEv = 27.211386245988;
+constexpr double kTownsend = 1e-21;           // V m^2
+constexpr double kLoschmidt = 2.686780111e25; // m^-3 (273.15 K, 101.325 kPa)
+
+constexpr int kGroups = 32;   // batch groups for standard errors (id mod 32)
+constexpr int kQ1 = 18;       // first-pass tally quantities
+constexpr int kQ2 = 8;        // second-pass tally quantities
+
+// One interval [e_lo, e_hi) of the union energy grid: the density sum
+// S(eps) = sum n_k sigma_kj(eps) of all channels not in their power-law
+// tail is S_lo + slope (eps - e_lo) there.
+template <typename R>
+struct alignas(4 * sizeof(R)) Rec {
+    R e_lo, e_hi, S_lo, slope;
+};
+
+// Per-channel constants.  bits: kind | angular << 4 | tail_zero << 8.
+// Tail: n sigma(eps) = exp(tail_logc + tail_K ln eps) for eps >= e_last.
+template <typename R>
+struct alignas(16) ChParam {
+    R kappa2;     // 2 m M / (m + M)^2            (Eq. 8)
+    R mfrac;      // M / (m + M)                  (Eq. 9)
+    R minv;       // (m + M) / M                  (Eq. 9)
+    R eps_k;      // energy loss [eV]             (Eq. 9)
+    R e_last;     // last table energy [eV]
+    R tail_logc;
+    R tail_K;
+    int32_t bits;
+};
+
+// Per-interval, per-channel density n sigma_j = val + slope (eps - e_lo).
+template <typename R>
+struct alignas(2 * sizeof(R)) ChVal {
+    R val, slope;
+};
+
+// Where each section of a compiled mixture sits in its device blob.  The
+// blob is [records | buckets | channel params | channel values]; the prefix
+// up to stage_tables (or stage_all) is copied into shared memory.
+struct Layout {
+    int32_t n_rec, n_buckets, n_ch, first_tail_rec;
+    float log2_lo, inv_bw;
+    uint32_t off_bucket, off_chp, off_chval;
+    uint32_t stage_tables;   // bytes of records + buckets + channel params
+    uint32_t stage_all;      // + channel values
+    uint32_t total;
+};
+
+struct CompiledMixture {
+    std::vector<uint8_t> blob32, blob64;
+    Layout lay32, lay64;
+    bz_mixture_info info;
+    double n_total;
+    double nu_max, nu_trial;
+};
+
+// Host mixture compiler (mixture.cpp).  Returns BZ_OK or an error with *err.
+bz_status compile_mixture(const bz_gas *gases, int32_t n_gases, const bz_mixture_opts *opts,
+                          CompiledMixture *out, std::string *err);
+
+}  // namespace bz

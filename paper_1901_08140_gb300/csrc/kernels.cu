@@ -1,0 +1,1008 @@
+// kernels.cu -- the electron-swarm step loop on sm_103a.
+//
+// One thread owns one electron at a time and runs it from the origin to its
+// I-th real collision (Sec. 2.3), then takes the next electron from a
+// per-swarm counter (warp-aggregated atomic).  A trial step (Sec. 2):
+//   1. Philox4x32-10 at counter (id, step, 0) gives four uniforms;
+//   2. free flight t_c = -ln(1-R)/nu' (Eq. 3);
+//   3. analytic motion in uniform static E and B (Sec. 3.6), evaluated from
+//      the state at the last real collision and the time since then, so null
+//      collisions touch no position state;
+//   4. nu(eps) = |v| S(eps) from the union-grid record that a log-energy
+//      bucket index points at (Eq. 2, Sec. 5, Sec. 2.2 tails);
+//   5. fail if nu > nu' (Sec. 6): back to the last real collision and raise
+//      nu' to 1.25 nu; else null if R nu' > nu (Eq. 4);
+//   6. on a real collision: the channel whose cumulative frequency reaches
+//      R nu', angle (Eq. 5 or isotropic), energy exchange (Eqs. 8, 9;
+//      attachment plastic; ionization split with a second draw), rotation,
+//      and the per-collision energy tallies (Eqs. 18-19).
+// The mixture's tables (records, bucket index, channel constants and, when
+// they fit, the per-channel coefficients) are staged into shared memory by
+// one TMA bulk copy per block (cp.async.bulk + mbarrier, bounded wait).
+// FP32 kernels keep position and time at real collisions, and the energy
+// sums, as compensated float pairs; all tallies are reduced in FP64.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "kernels.h"
+
+namespace bz {
+namespace {
+
+constexpr int kBlock = 256;
+constexpr uint32_t kStageChunk = 32768;
+constexpr uint32_t kWaitLimit = 1u << 24;
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of the
+// multiply-xor S-P network; the key is bumped by the Weyl constants after
+// each round.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                                        uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+        const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+        const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return make_uint4(c0, c1, c2, c3);
+}
+
+// ((w >> 9) + 1/2) 2^-23: an odd multiple of 2^-24 in (0,1), exact in FP32.
+template <typename R>
+__device__ __forceinline__ R uni(uint32_t w)
+{
+    return ((R)(w >> 9) + (R)0.5) * (R)(1.0 / 8388608.0);
+}
+
+// Math wrappers resolved per precision.
+__device__ __forceinline__ float log_(float x) { return logf(x); }
+__device__ __forceinline__ double log_(double x) { return log(x); }
+__device__ __forceinline__ float exp_(float x) { return expf(x); }
+__device__ __forceinline__ double exp_(double x) { return exp(x); }
+__device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+__device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+__device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsqrt_(double x) { return rsqrt(x); }
+__device__ __forceinline__ void sincos_(float x, float *s, float *c) { sincosf(x, s, c); }
+__device__ __forceinline__ void sincos_(double x, double *s, double *c) { sincos(x, s, c); }
+__device__ __forceinline__ void sincospi_(float x, float *s, float *c) { sincospif(x, s, c); }
+__device__ __forceinline__ void sincospi_(double x, double *s, double *c) { sincospi(x, s, c); }
+__device__ __forceinline__ float max_(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double max_(double a, double b) { return fmax(a, b); }
+
+// Compensated accumulator: a float pair (TwoSum) for FP32, a double for FP64.
+template <typename R>
+struct Acc;
+template <>
+struct Acc<float> {
+    float hi, lo;
+    __device__ __forceinline__ void set(double v)
+    {
+        hi = (float)v;
+        lo = (float)(v - (double)hi);
+    }
+    __device__ __forceinline__ void add(float b)
+    {
+        const float s = hi + b;
+        const float bb = s - hi;
+        const float e = (hi - (s - bb)) + (b - bb);
+        hi = s;
+        lo += e;
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+    __device__ __forceinline__ float approx() const { return hi + lo; }
+};
+template <>
+struct Acc<double> {
+    double v;
+    __device__ __forceinline__ void set(double x) { v = x; }
+    __device__ __forceinline__ void add(double b) { v += b; }
+    __device__ __forceinline__ double value() const { return v; }
+    __device__ __forceinline__ double approx() const { return v; }
+};
+
+// ---------------------------------------------------------------------------
+// Tables
+// ---------------------------------------------------------------------------
+template <typename R>
+struct Tab {
+    const Rec<R> *rec;
+    const uint16_t *bucket;
+    const ChParam<R> *chp;
+    const ChVal<R> *chval;
+    int n_rec, n_buckets, n_ch, first_tail;
+    float log2_lo, inv_bw;
+};
+
+template <typename R>
+__device__ __forceinline__ Tab<R> make_tab(const uint8_t *smem, const uint8_t *blob, const Layout &L, bool ch_smem)
+{
+    Tab<R> T;
+    T.rec = (const Rec<R> *)smem;
+    T.bucket = (const uint16_t *)(smem + L.off_bucket);
+    T.chp = (const ChParam<R> *)(smem + L.off_chp);
+    T.chval = (const ChVal<R> *)((ch_smem ? smem : blob) + L.off_chval);
+    T.n_rec = L.n_rec;
+    T.n_buckets = L.n_buckets;
+    T.n_ch = L.n_ch;
+    T.first_tail = L.first_tail_rec;
+    T.log2_lo = L.log2_lo;
+    T.inv_bw = L.inv_bw;
+    return T;
+}
+
+// Sum of the power-law tails of the channels whose table ends at or below
+// the record's lower edge (Sec. 2.2, Eqs. 12-14).
+template <typename R>
+__device__ __noinline__ R tail_sum(const Tab<R> &T, R eps, R e_lo)
+{
+    const R le = log_(eps);
+    R S = 0;
+    for (int j = 0; j < T.n_ch; ++j) {
+        const ChParam<R> p = T.chp[j];
+        if (e_lo >= p.e_last && !(p.bits & 0x100)) S += exp_(p.tail_logc + p.tail_K * le);
+    }
+    return S;
+}
+
+// Density sum S(eps) = sum n_k sigma_kj(eps) [1/m] and the record holding eps.
+template <typename R>
+__device__ __forceinline__ R density(const Tab<R> &T, R eps, int &ri, R &e_lo)
+{
+    float fb = (__log2f((float)eps) - T.log2_lo) * T.inv_bw;
+    fb = fminf(fmaxf(fb, 0.0f), (float)(T.n_buckets - 1));
+    int i = T.bucket[(int)fb];
+    Rec<R> r = T.rec[i];
+    while (i > 0 && eps < r.e_lo) r = T.rec[--i];
+    while (i < T.n_rec - 1 && eps >= r.e_hi) r = T.rec[++i];
+    R S = r.S_lo + r.slope * (eps - r.e_lo);
+    if (i >= T.first_tail) S += tail_sum(T, eps, r.e_lo);
+    ri = i;
+    e_lo = r.e_lo;
+    return S;
+}
+
+template <typename R>
+__device__ __forceinline__ ChVal<R> load_chval(const ChVal<R> *p, bool ch_smem)
+{
+    if (ch_smem) return *p;
+    ChVal<R> v;
+    v.val = __ldg(&p->val);
+    v.slope = __ldg(&p->slope);
+    return v;
+}
+
+// First channel whose cumulative density reaches `target` (= R nu'/|v|).
+template <typename R, bool CH_SMEM>
+__device__ __forceinline__ int select_channel(const Tab<R> &T, int ri, R e_lo, R eps, R target)
+{
+    const ChVal<R> *row = T.chval + (size_t)ri * T.n_ch;
+    const R de = eps - e_lo;
+    const bool tails = ri >= T.first_tail;
+    const R le = tails ? log_(eps) : (R)0;
+    R cum = 0;
+    int last = 0;
+    for (int j = 0; j < T.n_ch; ++j) {
+        const ChVal<R> cv = load_chval(row + j, CH_SMEM);
+        R d = cv.val + cv.slope * de;
+        if (tails) {
+            const ChParam<R> p = T.chp[j];
+            if (e_lo >= p.e_last && !(p.bits & 0x100)) d += exp_(p.tail_logc + p.tail_K * le);
+        }
+        if (d > (R)0) last = j;
+        cum += d;
+        if (cum >= target) return j;
+    }
+    return last;  // rounding left the sum a hair short of S: last channel that is open
+}
+
+template <typename R>
+struct Fld {
+    R a, b0, b1, b2, w, inv_w, vD0, vD1, vD2, a_par, Ke;
+    int has_b;
+};
+
+template <typename R>
+__device__ __forceinline__ Fld<R> make_fld(const Fields &f)
+{
+    Fld<R> F;
+    F.a = (R)f.a;
+    F.has_b = f.has_b;
+    F.b0 = (R)f.b[0];
+    F.b1 = (R)f.b[1];
+    F.b2 = (R)f.b[2];
+    F.w = (R)f.w;
+    F.inv_w = f.has_b ? (R)(1.0 / f.w) : (R)0;
+    F.vD0 = (R)f.vD[0];
+    F.vD1 = (R)f.vD[1];
+    F.vD2 = (R)f.vD[2];
+    F.a_par = (R)f.a_par;
+    F.Ke = (R)(0.5 * kMe / kQe);  // eV per (m/s)^2
+    return F;
+}
+
+// ---------------------------------------------------------------------------
+// Particle state
+// ---------------------------------------------------------------------------
+template <typename R>
+struct PState {
+    R vr0, vr1, vr2;         // velocity right after the last real collision
+    R T;                     // time since then
+    R nu_p, inv_nu;          // trial frequency of this particle
+    R vpar, u0x, u0y, u0z, bux, buy, buz;  // B != 0: v = vpar b + vD + u0 cos + (b x u0) sin
+    Acc<R> x, y, z, t;       // position and time at the last real collision
+    Acc<R> se, se2;          // energy sums before / after real collisions
+    uint32_t id_lo, id_hi, k, n_real, n_null, n_fail, n_ion, n_att, status;
+    bool done;
+};
+
+template <typename R>
+__device__ __forceinline__ void set_b_cache(const Fld<R> &F, PState<R> &s)
+{
+    if (!F.has_b) return;
+    s.vpar = s.vr0 * F.b0 + s.vr1 * F.b1 + s.vr2 * F.b2;
+    s.u0x = s.vr0 - s.vpar * F.b0 - F.vD0;
+    s.u0y = s.vr1 - s.vpar * F.b1 - F.vD1;
+    s.u0z = s.vr2 - s.vpar * F.b2 - F.vD2;
+    s.bux = F.b1 * s.u0z - F.b2 * s.u0y;
+    s.buy = F.b2 * s.u0x - F.b0 * s.u0z;
+    s.buz = F.b0 * s.u0y - F.b1 * s.u0x;
+}
+
+// Velocity after time T since the last real collision; (sn, cs) = sincos(wT).
+template <typename R>
+__device__ __forceinline__ void velocity_at(const Fld<R> &F, const PState<R> &s, R T, R &v0, R &v1, R &v2, R &sn,
+                                            R &cs)
+{
+    if (F.has_b) {
+        sincos_(F.w * T, &sn, &cs);
+        const R vp = s.vpar + F.a_par * T;
+        v0 = vp * F.b0 + F.vD0 + s.u0x * cs + s.bux * sn;
+        v1 = vp * F.b1 + F.vD1 + s.u0y * cs + s.buy * sn;
+        v2 = vp * F.b2 + F.vD2 + s.u0z * cs + s.buz * sn;
+    } else {
+        sn = 0;
+        cs = 1;
+        v0 = s.vr0;
+        v1 = s.vr1;
+        v2 = s.vr2 + F.a * T;
+    }
+}
+
+// Displacement after time T since the last real collision.
+template <typename R>
+__device__ __forceinline__ void displacement(const Fld<R> &F, const PState<R> &s, R T, R sn, R cs, R &dx, R &dy,
+                                             R &dz)
+{
+    if (F.has_b) {
+        const R omc = (cs > (R)0) ? sn * sn / ((R)1 + cs) : (R)1 - cs;  // 1 - cos(wT) without cancellation
+        const R par = s.vpar * T + (R)0.5 * F.a_par * T * T;
+        dx = par * F.b0 + F.vD0 * T + (s.u0x * sn + s.bux * omc) * F.inv_w;
+        dy = par * F.b1 + F.vD1 * T + (s.u0y * sn + s.buy * omc) * F.inv_w;
+        dz = par * F.b2 + F.vD2 * T + (s.u0z * sn + s.buz * omc) * F.inv_w;
+    } else {
+        dx = s.vr0 * T;
+        dy = s.vr1 * T;
+        dz = s.vr2 * T + (R)0.5 * F.a * T * T;
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ void init_particle(const RunArgs &P, const Fld<R> &F, PState<R> &s, uint64_t id)
+{
+    s.id_lo = (uint32_t)id;
+    s.id_hi = (uint32_t)(id >> 32);
+    const uint4 w = philox(s.id_lo, s.id_hi, 0u, 2u, P.key0, P.key1);
+    // isotropic Maxwellian with mean energy eps0 = 3/2 kT (Box-Muller)
+    const R sv = (R)sqrt((2.0 / 3.0) * P.eps0_mean * kQe / kMe);
+    const R r0 = sqrt_((R)-2 * log_(uni<R>(w.x))), r1 = sqrt_((R)-2 * log_(uni<R>(w.z)));
+    R s1, c1, s3, c3;
+    sincospi_((R)2 * uni<R>(w.y), &s1, &c1);
+    sincospi_((R)2 * uni<R>(w.w), &s3, &c3);
+    s.vr0 = sv * r0 * c1;
+    s.vr1 = sv * r0 * s1;
+    s.vr2 = sv * r1 * c3;
+    s.T = 0;
+    s.nu_p = (R)P.nu0;
+    s.inv_nu = (R)1 / s.nu_p;
+    s.x.set(0.0);
+    s.y.set(0.0);
+    s.z.set(0.0);
+    s.t.set(0.0);
+    s.se.set(0.0);
+    s.se2.set(0.0);
+    s.k = 0;
+    s.n_real = s.n_null = s.n_fail = s.n_ion = s.n_att = 0;
+    s.status = ST_DONE;
+    s.done = false;
+    set_b_cache(F, s);
+}
+
+// One trial step.  Returns the decision (channel, DEC_NULL or DEC_FAIL);
+// eps_i / eps_f receive the energy before and after a real collision.
+template <typename R, bool CH_SMEM>
+__device__ __forceinline__ int trial(const Tab<R> &T, const Fld<R> &F, const RunArgs &P, PState<R> &s, R &eps_i,
+                                     R &eps_f)
+{
+    const uint32_t step = s.k++;
+    const uint4 w = philox(s.id_lo, s.id_hi, step, 0u, P.key0, P.key1);
+    const R u1 = uni<R>(w.y), u2 = uni<R>(w.z), u3 = uni<R>(w.w);
+    // Eq. (3): the draw stands for 1 - R
+    R Tn = s.T - log_(uni<R>(w.x)) * s.inv_nu;
+    bool cut = false;
+    if (P.t_end > 0.0 && s.t.value() + (double)Tn >= P.t_end) {
+        Tn = (R)(P.t_end - s.t.value());  // TimeBulletLimiter: the flight stops at t_end
+        cut = true;
+    }
+    R v0, v1, v2, sn, cs;
+    velocity_at(F, s, Tn, v0, v1, v2, sn, cs);
+    if (cut) {
+        R dx, dy, dz;
+        displacement(F, s, Tn, sn, cs, dx, dy, dz);
+        s.x.add(dx);
+        s.y.add(dy);
+        s.z.add(dz);
+        s.t.set(P.t_end);
+        s.vr0 = v0;
+        s.vr1 = v1;
+        s.vr2 = v2;
+        s.T = 0;
+        s.status = ST_TIME;
+        s.done = true;
+        eps_i = F.Ke * (v0 * v0 + v1 * v1 + v2 * v2);
+        eps_f = 0;
+        return DEC_NULL;
+    }
+    const R vsq = v0 * v0 + v1 * v1 + v2 * v2;
+    const R eps = F.Ke * vsq;
+    int ri;
+    R elo;
+    const R S = density(T, eps, ri, elo);
+    const R inv_sp = vsq > (R)0 ? rsqrt_(vsq) : (R)0;
+    const R sp = vsq * inv_sp;
+    const R nu = sp * S;
+    eps_i = eps;
+    eps_f = 0;
+    if (!(nu <= s.nu_p)) {
+        if (!(nu == nu)) {  // non-finite state: stop this particle, flag it
+            atomicOr(P.err, BZ_ERR_NONFINITE);
+            s.status = ST_ERROR;
+            s.done = true;
+            return DEC_FAIL;
+        }
+        ++s.n_fail;
+        if (P.fixed) {  // FixedTrialFrequency (Sec. 6.1): an error
+            atomicOr(P.err, BZ_ERR_TRIAL);
+            s.status = ST_TRIAL;
+            s.done = true;
+            return DEC_FAIL;
+        }
+        s.T = 0;  // fail (Sec. 6): back to the last real collision
+        s.nu_p = max_(s.nu_p, (R)1.25 * nu);
+        s.inv_nu = (R)1 / s.nu_p;
+        return DEC_FAIL;
+    }
+    const R r = u1 * s.nu_p;
+    if (r > nu) {  // Eq. (4): null collision
+        ++s.n_null;
+        s.T = Tn;
+        return DEC_NULL;
+    }
+    // ---- real collision ----
+    const int c = select_channel<R, CH_SMEM>(T, ri, elo, eps, r * inv_sp);
+    {
+        R dx, dy, dz;
+        displacement(F, s, Tn, sn, cs, dx, dy, dz);
+        s.x.add(dx);
+        s.y.add(dy);
+        s.z.add(dz);
+        s.t.add(Tn);
+        s.T = 0;
+    }
+    const ChParam<R> p = T.chp[c];
+    const int kind = p.bits & 15;
+    R ct;
+    if ((p.bits >> 4) & 15) {  // Eq. (5), eps in Hartree
+        ct = (R)1 - (R)2 * u2 / ((R)1 + (R)8 * (eps * (R)(1.0 / kHartreeEv)) * ((R)1 - u2));
+    } else {
+        ct = (R)1 - (R)2 * u2;
+    }
+    R ratio;
+    bool rotate = true;
+    if (kind == BZ_ELASTIC) {
+        ratio = (R)1 - p.kappa2 * ((R)1 - ct);  // Eq. (8)
+    } else if (kind == BZ_ATTACHMENT) {
+        ++s.n_att;
+        if (P.attach_keep) {
+            ratio = 1;
+            rotate = false;
+        } else {
+            ratio = 0;  // plastic collision: the electron stops
+        }
+    } else {
+        const R x = p.eps_k / eps;  // Eq. (9), radicand clamped at 0
+        const R rad = max_((R)0, (R)1 - p.minv * x);
+        ratio = max_((R)0, (R)1 - p.mfrac * x + p.kappa2 * (sqrt_(rad) * ct - (R)1));
+        if (kind == BZ_IONIZATION) {
+            const uint4 w2 = philox(s.id_lo, s.id_hi, step, 1u, P.key0, P.key1);
+            ratio *= (R)1 - uni<R>(w2.x);  // the secondary takes the rest
+            ++s.n_ion;
+        }
+    }
+    if (rotate) {
+        R d0 = v0 * inv_sp, d1 = v1 * inv_sp, d2 = v2 * inv_sp;
+        if (!(vsq > (R)0)) {
+            d0 = 0;
+            d1 = 0;
+            d2 = 1;
+        }
+        // azimuth origin e1 = (a x d)/|a x d|, a the axis of the smallest |d_i|
+        const R ax = fabs(d0), ay = fabs(d1), az = fabs(d2);
+        R e0, e1, e2;
+        if (ax <= ay && ax <= az) {
+            e0 = 0;
+            e1 = -d2;
+            e2 = d1;
+        } else if (ay <= az) {
+            e0 = d2;
+            e1 = 0;
+            e2 = -d0;
+        } else {
+            e0 = -d1;
+            e1 = d0;
+            e2 = 0;
+        }
+        const R ie = rsqrt_(e0 * e0 + e1 * e1 + e2 * e2);
+        e0 *= ie;
+        e1 *= ie;
+        e2 *= ie;
+        const R f0 = d1 * e2 - d2 * e1, f1 = d2 * e0 - d0 * e2, f2 = d0 * e1 - d1 * e0;  // d x e1
+        const R st = sqrt_(max_((R)0, (R)1 - ct * ct));
+        R sp3, cp3;
+        sincospi_((R)2 * u3, &sp3, &cp3);
+        const R nsp = sp * sqrt_(ratio);
+        s.vr0 = nsp * (ct * d0 + st * (cp3 * e0 + sp3 * f0));
+        s.vr1 = nsp * (ct * d1 + st * (cp3 * e1 + sp3 * f1));
+        s.vr2 = nsp * (ct * d2 + st * (cp3 * e2 + sp3 * f2));
+    } else {
+        s.vr0 = v0;
+        s.vr1 = v1;
+        s.vr2 = v2;
+    }
+    set_b_cache(F, s);
+    eps_f = ratio * eps;
+    s.se.add(eps);
+    s.se2.add(eps_f);
+    if (++s.n_real >= P.I) s.done = true;
+    return c;
+}
+
+template <typename R>
+__device__ __forceinline__ void write_particle(const RunArgs &P, const PState<R> &s, uint64_t slot)
+{
+    const ParticlesDev &o = P.out;
+    o.x[slot] = s.x.value();
+    o.y[slot] = s.y.value();
+    o.z[slot] = s.z.value();
+    o.t[slot] = s.t.value();
+    o.se[slot] = s.se.value();
+    o.se2[slot] = s.se2.value();
+    o.vx[slot] = (float)s.vr0;
+    o.vy[slot] = (float)s.vr1;
+    o.vz[slot] = (float)s.vr2;
+    o.nup[slot] = (float)s.nu_p;
+    o.n_real[slot] = s.n_real;
+    o.n_null[slot] = s.n_null;
+    o.n_fail[slot] = s.n_fail;
+    o.n_ion[slot] = s.n_ion;
+    o.n_att[slot] = s.n_att;
+    o.steps[slot] = s.k;
+    o.status[slot] = s.status;
+}
+
+// ---------------------------------------------------------------------------
+// Table staging: one TMA bulk copy (global -> shared) per block, completion
+// tracked by an mbarrier; every wait is bounded and a timeout is reported.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t mb, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.b32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(mb), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ bool stage_tables(const uint8_t *src, uint8_t *dst, uint32_t bytes, uint64_t *mbar, uint32_t *err)
+{
+    const uint32_t mb = smem_u32(mbar);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    if (bytes == 0) return true;
+    if (threadIdx.x == 0) {
+        asm volatile(
+            "{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(mb),
+            "r"(bytes)
+            : "memory");
+        const uint32_t d = smem_u32(dst);
+        for (uint32_t off = 0; off < bytes; off += kStageChunk) {
+            const uint32_t sz = (bytes - off < kStageChunk) ? bytes - off : kStageChunk;
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    d + off),
+                "l"(src + off), "r"(sz), "r"(mb)
+                : "memory");
+        }
+    }
+    bool ok = false;
+    for (uint32_t it = 0; it < kWaitLimit && !ok; ++it) ok = mbar_try_wait(mb, 0);
+    const int failed = __syncthreads_or(!ok);
+    if (failed) {
+        if (threadIdx.x == 0) atomicOr(err, BZ_ERR_STAGE_TIMEOUT);
+        // wait (bounded) for the copy still in flight before the block exits
+        bool done = ok;
+        for (uint32_t it = 0; it < kWaitLimit && !done; ++it) done = mbar_try_wait(mb, 0);
+        __syncthreads();
+        return false;
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// Kernels
+// ---------------------------------------------------------------------------
+template <typename R, bool CH_SMEM>
+__global__ void __launch_bounds__(kBlock) swarm_kernel(const RunArgs P)
+{
+    extern __shared__ __align__(128) uint8_t smem[];
+    __shared__ __align__(8) uint64_t mbar;
+    if (!stage_tables(P.blob, smem, P.stage_bytes, &mbar, P.err)) return;
+    const Tab<R> T = make_tab<R>(smem, P.blob, P.lay, CH_SMEM);
+    const Fld<R> F = make_fld<R>(P.f);
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    PState<R> s;
+    bool have = false, exhausted = false;
+    uint64_t slot = 0;
+    for (;;) {
+        const unsigned need = __ballot_sync(FULL, !have);
+        if (need && !exhausted) {
+            const int leader = __ffs(need) - 1;
+            unsigned long long base = 0;
+            if (lane == leader) base = atomicAdd(P.counter, (unsigned long long)__popc(need));
+            base = __shfl_sync(FULL, base, leader);
+            if (base >= P.n) exhausted = true;
+            if (!have) {
+                const unsigned long long idx = base + __popc(need & ((1u << lane) - 1u));
+                if (idx < P.n) {
+                    init_particle<R>(P, F, s, P.id_offset + idx);
+                    slot = idx;
+                    have = true;
+                }
+            }
+        }
+        if (!__any_sync(FULL, have)) break;
+        if (have) {
+            if (s.k >= P.max_trials) {
+                s.status = ST_STEPS;
+                s.done = true;
+                atomicOr(P.err, BZ_ERR_MAX_TRIALS);
+            } else {
+                R ei, ef;
+                trial<R, CH_SMEM>(T, F, P, s, ei, ef);
+            }
+            if (s.done) {
+                write_particle<R>(P, s, slot);
+                have = false;
+            }
+        }
+    }
+}
+
+template <typename R, bool CH_SMEM>
+__global__ void __launch_bounds__(kBlock) replay_kernel(const ReplayArgs A)
+{
+    extern __shared__ __align__(128) uint8_t smem[];
+    __shared__ __align__(8) uint64_t mbar;
+    const RunArgs &P = A.run;
+    if (!stage_tables(P.blob, smem, P.stage_bytes, &mbar, P.err)) return;
+    const Tab<R> T = make_tab<R>(smem, P.blob, P.lay, CH_SMEM);
+    const Fld<R> F = make_fld<R>(P.f);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < A.n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double *in = A.state_in + 8 * i;
+        PState<R> s;
+        const uint64_t id = A.ids[i];
+        s.id_lo = (uint32_t)id;
+        s.id_hi = (uint32_t)(id >> 32);
+        s.x.set(in[0]);
+        s.y.set(in[1]);
+        s.z.set(in[2]);
+        s.vr0 = (R)in[3];
+        s.vr1 = (R)in[4];
+        s.vr2 = (R)in[5];
+        s.t.set(in[6]);
+        s.nu_p = (R)in[7];
+        s.inv_nu = (R)1 / s.nu_p;
+        s.T = 0;
+        s.se.set(0.0);
+        s.se2.set(0.0);
+        s.k = A.steps[i];
+        s.n_real = s.n_null = s.n_fail = s.n_ion = s.n_att = 0;
+        s.status = ST_DONE;
+        s.done = false;
+        set_b_cache(F, s);
+        R ei, ef;
+        const int dec = trial<R, CH_SMEM>(T, F, P, s, ei, ef);
+        // state at the trial point: last real collision advanced by s.T
+        R v0, v1, v2, sn, cs, dx, dy, dz;
+        velocity_at(F, s, s.T, v0, v1, v2, sn, cs);
+        displacement(F, s, s.T, sn, cs, dx, dy, dz);
+        double *o = A.state_out + 8 * i;
+        o[0] = s.x.value() + (double)dx;
+        o[1] = s.y.value() + (double)dy;
+        o[2] = s.z.value() + (double)dz;
+        o[3] = (double)v0;
+        o[4] = (double)v1;
+        o[5] = (double)v2;
+        o[6] = s.t.value() + (double)s.T;
+        o[7] = (double)s.nu_p;
+        A.decision[i] = dec;
+        A.eps_io[2 * i] = (double)ei;
+        A.eps_io[2 * i + 1] = (double)ef;
+    }
+}
+
+__global__ void philox_kernel(int64_t n, const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t *out)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint4 c = reinterpret_cast<const uint4 *>(ctr)[i];
+        reinterpret_cast<uint4 *>(out)[i] = philox(c.x, c.y, c.z, c.w, k0, k1);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 tallies (Sec. 2.3).  Pass 1 sums, per batch group (id mod 32), the
+// per-particle quantities whose means give W_vec, alpha, eta, <eps>, the flux
+// forms and the collision counts.  The middle step fixes W_vec; pass 2 sums
+// the displacement terms d = x - t W_vec of Eqs. (22)-(27).  Per-block
+// partial sums are reduced in a fixed order, so results are reproducible.
+// Threads keep one group each: blocks and the grid stride are multiples of 32.
+// ---------------------------------------------------------------------------
+constexpr int kTallyBlock = 256;
+
+template <int Q>
+__device__ void block_group_reduce(double (&acc)[Q], double *out_block, uint64_t id_offset)
+{
+    __shared__ double red[kTallyBlock / 32][32][Q > kQ1 ? Q : kQ1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) red[warp][lane][q] = acc[q];
+    __syncthreads();
+    if (warp == 0) {
+        const int g = (int)((id_offset + (uint64_t)lane) & 31u);
+        for (int q = 0; q < Q; ++q) {
+            double v = 0.0;
+            for (int w = 0; w < kTallyBlock / 32; ++w) v += red[w][lane][q];
+            out_block[g * Q + q] = v;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kTallyBlock) tally_pass1(const TallyArgs A)
+{
+    double acc[kQ1];
+#pragma unroll
+    for (int q = 0; q < kQ1; ++q) acc[q] = 0.0;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < A.n; i += stride) {
+        const double t = A.t[i];
+        const uint32_t st = A.status[i];
+        acc[17] += (st != ST_DONE && st != ST_TIME) ? 1.0 : 0.0;
+        if (!(t > 0.0)) continue;
+        const double x = A.x[i], y = A.y[i], z = A.z[i];
+        const double G = (double)A.n_ion[i], D = (double)A.n_att[i];
+        acc[0] += 1.0;
+        acc[1] += x / t;
+        acc[2] += y / t;
+        acc[3] += z / t;
+        acc[4] += G / z;
+        acc[5] += D / z;
+        acc[6] += x;
+        acc[7] += y;
+        acc[8] += z;
+        acc[9] += t;
+        acc[10] += A.se[i];
+        acc[11] += A.se2[i];
+        acc[12] += (double)A.n_real[i];
+        acc[13] += (double)A.n_null[i];
+        acc[14] += (double)A.n_fail[i];
+        acc[15] += G;
+        acc[16] += D;
+    }
+    block_group_reduce<kQ1>(acc, A.part1 + (size_t)blockIdx.x * kGroups * kQ1, A.id_offset);
+}
+
+// gsum layout: [g][0..kQ1) pass 1, [g][kQ1..kQ1+kQ2) pass 2, then summary
+// values at kGroups*(kQ1+kQ2): Wx, Wy, Wz, Wfx, Wfy, Wfz.
+constexpr int kGS = kQ1 + kQ2;
+
+__global__ void tally_mid(const TallyArgs A)
+{
+    const int g = threadIdx.x / kQ1, q = threadIdx.x % kQ1;
+    if (threadIdx.x < kGroups * kQ1) {
+        double v = 0.0;
+        for (int b = 0; b < A.blocks; ++b) v += A.part1[((size_t)b * kGroups + g) * kQ1 + q];
+        A.gsum[g * kGS + q] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double c = 0, sx = 0, sy = 0, sz = 0, X = 0, Y = 0, Z = 0, Tt = 0;
+        for (int k = 0; k < kGroups; ++k) {
+            const double *r = A.gsum + k * kGS;
+            c += r[0];
+            sx += r[1];
+            sy += r[2];
+            sz += r[3];
+            X += r[6];
+            Y += r[7];
+            Z += r[8];
+            Tt += r[9];
+        }
+        double *S = A.gsum + kGroups * kGS;
+        S[0] = c > 0 ? sx / c : 0.0;
+        S[1] = c > 0 ? sy / c : 0.0;
+        S[2] = c > 0 ? sz / c : 0.0;
+        S[3] = Tt > 0 ? X / Tt : 0.0;
+        S[4] = Tt > 0 ? Y / Tt : 0.0;
+        S[5] = Tt > 0 ? Z / Tt : 0.0;
+    }
+}
+
+__global__ void __launch_bounds__(kTallyBlock) tally_pass2(const TallyArgs A)
+{
+    const double *S = A.gsum + kGroups * kGS;
+    const double Wx = S[0], Wy = S[1], Wz = S[2], Fx = S[3], Fy = S[4], Fz = S[5];
+    double acc[kQ2];
+#pragma unroll
+    for (int q = 0; q < kQ2; ++q) acc[q] = 0.0;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < A.n; i += stride) {
+        const double t = A.t[i];
+        if (!(t > 0.0)) continue;
+        const double x = A.x[i], y = A.y[i], z = A.z[i];
+        const double dx = x - t * Wx, dy = y - t * Wy, dz = z - t * Wz;
+        const double dp2 = dx * dx + dy * dy, d2 = dp2 + dz * dz;
+        acc[0] += d2 / t;
+        acc[1] += dz * dz / (2.0 * t);
+        acc[2] += dp2 / (4.0 * t);
+        acc[3] += 2.0 * sqrt(d2);
+        acc[4] += 2.0 * fabs(dz);
+        acc[5] += 2.0 * sqrt(dp2);
+        const double fz = z - Fz * t, fx = x - Fx * t, fy = y - Fy * t;
+        acc[6] += fz * fz;
+        acc[7] += fx * fx + fy * fy;
+    }
+    block_group_reduce<kQ2>(acc, A.part2 + (size_t)blockIdx.x * kGroups * kQ2, A.id_offset);
+}
+
+__device__ double group_se(const double *v, const bool *has, int G)
+{
+    int n = 0;
+    double m = 0.0;
+    for (int g = 0; g < G; ++g)
+        if (has[g]) {
+            m += v[g];
+            ++n;
+        }
+    if (n < 2) return __longlong_as_double(0x7ff8000000000000ll);
+    m /= n;
+    double s = 0.0;
+    for (int g = 0; g < G; ++g)
+        if (has[g]) s += (v[g] - m) * (v[g] - m);
+    return sqrt(s / (n - 1)) / sqrt((double)n);
+}
+
+__global__ void tally_final(const TallyArgs A)
+{
+    const int g = threadIdx.x / kQ2, q = threadIdx.x % kQ2;
+    if (threadIdx.x < kGroups * kQ2) {
+        double v = 0.0;
+        for (int b = 0; b < A.blocks; ++b) v += A.part2[((size_t)b * kGroups + g) * kQ2 + q];
+        A.gsum[g * kGS + kQ1 + q] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    double tot[kGS];
+    for (int k = 0; k < kGS; ++k) {
+        tot[k] = 0.0;
+        for (int gg = 0; gg < kGroups; ++gg) tot[k] += A.gsum[gg * kGS + k];
+    }
+    const double *S = A.gsum + kGroups * kGS;
+    bz_tallies o;
+    memset(&o, 0, sizeof o);
+    const double N = tot[0];
+    const double inv = N > 0 ? 1.0 / N : 0.0;
+    o.W = tot[3] * inv;
+    o.Wx = tot[1] * inv;
+    o.Wy = tot[2] * inv;
+    o.W_flux = S[5];
+    o.lorentz_angle = atan2(sqrt(o.Wx * o.Wx + o.Wy * o.Wy), o.W);
+    o.alpha = tot[4] * inv;
+    o.eta = tot[5] * inv;
+    o.alpha_flux = tot[15] / tot[8];
+    o.eta_flux = tot[16] / tot[8];
+    o.eps = tot[12] > 0 ? tot[10] / tot[12] : 0.0;
+    o.eps_after = tot[12] > 0 ? tot[11] / tot[12] : 0.0;
+    o.D = tot[kQ1 + 0] * inv;
+    o.D_L = tot[kQ1 + 1] * inv;
+    o.D_T = tot[kQ1 + 2] * inv;
+    o.sig = tot[kQ1 + 3] * inv;
+    o.sig_L = tot[kQ1 + 4] * inv;
+    o.sig_T = tot[kQ1 + 5] * inv;
+    o.D_L_flux = tot[9] > 0 ? tot[kQ1 + 6] / (2.0 * tot[9]) : 0.0;
+    o.D_T_flux = tot[9] > 0 ? tot[kQ1 + 7] / (4.0 * tot[9]) : 0.0;
+    const double trials = tot[12] + tot[13] + tot[14];
+    o.efficiency = trials > 0 ? tot[12] / trials : 0.0;
+    o.E_V_m = A.E_V_m;
+    o.n_total = A.n_total;
+    o.nu_trial = A.nu_trial;
+    o.t_mean = tot[9] * inv;
+    o.mu = A.E_V_m > 0 ? o.W / A.E_V_m : 0.0;
+    o.mu_N = o.mu * A.n_total;
+    o.mu_0 = o.mu_N / kLoschmidt;
+    o.n_particles = (uint64_t)(N + 0.5);
+    o.n_real = (uint64_t)(tot[12] + 0.5);
+    o.n_null = (uint64_t)(tot[13] + 0.5);
+    o.n_fail = (uint64_t)(tot[14] + 0.5);
+    o.n_ion = (uint64_t)(tot[15] + 0.5);
+    o.n_att = (uint64_t)(tot[16] + 0.5);
+    o.n_incomplete = (uint64_t)(tot[17] + 0.5);
+    o.error_flags = (int32_t)*A.err;
+    // batch-mean standard errors
+    bool has[kGroups];
+    double v[kGroups];
+    for (int k = 0; k < kGroups; ++k) has[k] = A.gsum[k * kGS] > 0.0;
+    auto se_of = [&](int num, int den, double scale) {
+        for (int k = 0; k < kGroups; ++k) {
+            const double *r = A.gsum + k * kGS;
+            v[k] = has[k] && r[den] > 0 ? scale * r[num] / r[den] : 0.0;
+        }
+        return group_se(v, has, kGroups);
+    };
+    o.W_se = se_of(3, 0, 1.0);
+    o.alpha_se = se_of(4, 0, 1.0);
+    o.eta_se = se_of(5, 0, 1.0);
+    o.eps_se = se_of(10, 12, 1.0);
+    o.eps_after_se = se_of(11, 12, 1.0);
+    o.D_se = se_of(kQ1 + 0, 0, 1.0);
+    o.D_L_se = se_of(kQ1 + 1, 0, 1.0);
+    o.D_T_se = se_of(kQ1 + 2, 0, 1.0);
+    o.sig_se = se_of(kQ1 + 3, 0, 1.0);
+    o.sig_L_se = se_of(kQ1 + 4, 0, 1.0);
+    o.sig_T_se = se_of(kQ1 + 5, 0, 1.0);
+    *A.out = o;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+template <typename K>
+static cudaError_t prep_smem(K kernel, size_t smem)
+{
+    if (smem > 48 * 1024) return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return cudaSuccess;
+}
+
+cudaError_t launch_swarm(int precision, bool ch_smem, const RunArgs &a, int grid, int block, cudaStream_t s)
+{
+    if (block != kBlock) return cudaErrorInvalidValue;
+    const size_t smem = a.stage_bytes;
+    cudaError_t e;
+#define BZ_LAUNCH(R, C)                                                        \
+    do {                                                                       \
+        e = prep_smem(swarm_kernel<R, C>, smem);                               \
+        if (e != cudaSuccess) return e;                                        \
+        swarm_kernel<R, C><<<grid, block, smem, s>>>(a);                       \
+    } while (0)
+    if (precision == 64) {
+        if (ch_smem) BZ_LAUNCH(double, true); else BZ_LAUNCH(double, false);
+    } else {
+        if (ch_smem) BZ_LAUNCH(float, true); else BZ_LAUNCH(float, false);
+    }
+#undef BZ_LAUNCH
+    return cudaGetLastError();
+}
+
+cudaError_t launch_replay(int precision, bool ch_smem, const ReplayArgs &a, int grid, int block, cudaStream_t s)
+{
+    if (block != kBlock) return cudaErrorInvalidValue;
+    const size_t smem = a.run.stage_bytes;
+    cudaError_t e;
+#define BZ_LAUNCH(R, C)                                                        \
+    do {                                                                       \
+        e = prep_smem(replay_kernel<R, C>, smem);                              \
+        if (e != cudaSuccess) return e;                                        \
+        replay_kernel<R, C><<<grid, block, smem, s>>>(a);                      \
+    } while (0)
+    if (precision == 64) {
+        if (ch_smem) BZ_LAUNCH(double, true); else BZ_LAUNCH(double, false);
+    } else {
+        if (ch_smem) BZ_LAUNCH(float, true); else BZ_LAUNCH(float, false);
+    }
+#undef BZ_LAUNCH
+    return cudaGetLastError();
+}
+
+int swarm_occupancy(int precision, bool ch_smem, int block, size_t smem)
+{
+    int n = 0;
+    cudaError_t e;
+    if (precision == 64) {
+        if (ch_smem) {
+            prep_smem(swarm_kernel<double, true>, smem);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, swarm_kernel<double, true>, block, smem);
+        } else {
+            prep_smem(swarm_kernel<double, false>, smem);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, swarm_kernel<double, false>, block, smem);
+        }
+    } else {
+        if (ch_smem) {
+            prep_smem(swarm_kernel<float, true>, smem);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, swarm_kernel<float, true>, block, smem);
+        } else {
+            prep_smem(swarm_kernel<float, false>, smem);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, swarm_kernel<float, false>, block, smem);
+        }
+    }
+    return e == cudaSuccess ? n : 0;
+}
+
+cudaError_t launch_philox(int64_t n, const uint32_t *ctr, uint64_t key, uint32_t *out, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    const int block = 256;
+    const int grid = (int)((n + block - 1) / block < 4096 ? (n + block - 1) / block : 4096);
+    philox_kernel<<<grid, block, 0, s>>>(n, ctr, (uint32_t)key, (uint32_t)(key >> 32), out);
+    return cudaGetLastError();
+}
+
+int tally_blocks(uint64_t n, int sm_count)
+{
+    uint64_t b = (n + kTallyBlock - 1) / kTallyBlock;
+    uint64_t cap = (uint64_t)sm_count * 2;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+cudaError_t launch_tallies(const TallyArgs &a, cudaStream_t s)
+{
+    tally_pass1<<<a.blocks, kTallyBlock, 0, s>>>(a);
+    tally_mid<<<1, kGroups * kQ1, 0, s>>>(a);
+    tally_pass2<<<a.blocks, kTallyBlock, 0, s>>>(a);
+    tally_final<<<1, kGroups * kQ2, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace bz

@@ -1,0 +1,81 @@
+// kernels.h -- host-side launch interface of the CUDA kernels (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "bz_impl.h"
+
+namespace bz {
+
+enum { ST_DONE = 0, ST_TIME = 1, ST_STEPS = 2, ST_TRIAL = 3, ST_ERROR = 4 };
+enum { DEC_FAIL = -2, DEC_NULL = -1 };
+
+// Uniform static fields in the force frame (force on the electron along +z).
+struct Fields {
+    double a;        // eE/m [m/s^2]
+    int32_t has_b;
+    double b[3];     // unit vector of B
+    double w;        // e|B|/m [rad/s]
+    double vD[3];    // E x B drift (b x a z)/w
+    double a_par;    // a (z . b)
+};
+
+struct ParticlesDev {
+    double *x, *y, *z, *t, *se, *se2;
+    float *vx, *vy, *vz, *nup;
+    uint32_t *n_real, *n_null, *n_fail, *n_ion, *n_att, *steps, *status;
+};
+
+struct RunArgs {
+    const uint8_t *blob;     // compiled mixture (device)
+    Layout lay;
+    uint32_t stage_bytes;    // prefix of the blob staged into shared memory
+    uint32_t key0, key1;     // Philox key (swarm seed)
+    uint64_t id_offset, n;
+    uint32_t I;              // real collisions per particle
+    int32_t fixed;           // fixed trial frequency: a fail stops the particle
+    int32_t attach_keep;
+    double nu0;              // starting trial frequency
+    double eps0_mean;        // Maxwellian start, mean energy [eV]
+    double t_end;            // > 0: time limit [s]
+    uint64_t max_trials;
+    Fields f;
+    unsigned long long *counter;  // next particle slot
+    uint32_t *err;
+    ParticlesDev out;
+};
+
+struct ReplayArgs {
+    RunArgs run;
+    int64_t n;
+    const double *state_in;
+    const uint64_t *ids;
+    const uint32_t *steps;
+    double *state_out;
+    int32_t *decision;
+    double *eps_io;
+};
+
+struct TallyArgs {
+    const double *x, *y, *z, *t, *se, *se2;
+    const uint32_t *n_real, *n_null, *n_fail, *n_ion, *n_att, *status;
+    uint64_t n, id_offset;
+    double *part1, *part2;   // [blocks][kGroups][kQ1 | kQ2] scratch
+    double *gsum;            // [kGroups][kQ1 + kQ2] + 8 summary values, scratch
+    int32_t blocks;
+    double E_V_m, n_total, nu_trial;
+    const uint32_t *err;
+    bz_tallies *out;         // device
+};
+
+// Launch helpers (kernels.cu).  precision is 32 or 64.
+cudaError_t launch_swarm(int precision, bool ch_smem, const RunArgs &a, int grid, int block, cudaStream_t s);
+cudaError_t launch_replay(int precision, bool ch_smem, const ReplayArgs &a, int grid, int block, cudaStream_t s);
+cudaError_t launch_philox(int64_t n, const uint32_t *ctr, uint64_t key, uint32_t *out, cudaStream_t s);
+cudaError_t launch_tallies(const TallyArgs &a, cudaStream_t s);
+int tally_blocks(uint64_t n, int sm_count);
+// Blocks of `block` threads that fit on one SM with `smem` bytes of tables.
+int swarm_occupancy(int precision, bool ch_smem, int block, size_t smem);
+
+}  // namespace bz

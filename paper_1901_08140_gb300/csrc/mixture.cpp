@@ -1,0 +1,317 @@
+// mixture.cpp -- host compiler of a gas mixture into the tables the step
+// kernels read.
+//
+// What the kernels need is nu(eps) = sqrt(2 eps/m) sum_k n_k sum_j sigma_kj(eps)
+// (Eq. 2) and, on a real collision, the channel whose cumulative frequency
+// reaches the drawn value.  Every table is linear between its points
+// (Sec. 5) and is extended per Sec. 2.2 (Eqs. 12-14), so between two
+// consecutive points of the union of all tables and thresholds each channel
+// is a single linear function (or, above its last point, its power-law
+// tail).  The compiler therefore emits one record per union interval holding
+// the density sum and its slope, exact up to rounding; per-channel
+// coefficients on the same intervals; a log-energy bucket index that lands
+// within a record or two of the right one; and the exact maximum of nu over
+// [0, eps_cap], which is the constant trial frequency (Sec. 6.2).
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <limits>
+
+#include "bz_impl.h"
+
+namespace bz {
+namespace {
+
+struct Chan {
+    int kind, gas;
+    double th;
+    std::vector<double> e, s;
+    double n;            // number density of the gas
+    // right extension n sigma(eps) = n s_last (eps/e_last)^K
+    bool tail_zero;
+    double tail_K;
+};
+
+// Linear piece a + b eps of channel c on an interval whose midpoint is m;
+// returns false if the channel is in its right extension there.
+bool piece(const Chan &c, double m, double *a, double *b)
+{
+    const std::vector<double> &e = c.e, &s = c.s;
+    size_t n = e.size();
+    if (m > e[n - 1]) return false;
+    if (c.kind != BZ_ELASTIC) {
+        if (m < c.th) { *a = 0.0; *b = 0.0; return true; }
+        if (m < e[0]) {  // linear rise from (threshold, 0) to the first point
+            *b = s[0] / (e[0] - c.th);
+            *a = -*b * c.th;
+            return true;
+        }
+    } else if (m < e[0]) {
+        *a = s[0]; *b = 0.0; return true;
+    }
+    size_t k = (size_t)(std::upper_bound(e.begin(), e.end(), m) - e.begin());  // e[k-1] <= m < e[k]
+    if (k == 0) k = 1;
+    if (k >= n) k = n - 1;
+    double e0 = e[k - 1], e1 = e[k], s0 = s[k - 1], s1 = s[k];
+    *b = (s1 - s0) / (e1 - e0);
+    *a = s0 - *b * e0;
+    return true;
+}
+
+double tail_value(const Chan &c, double eps)
+{
+    double sl = c.s.back();
+    if (c.tail_zero) return 0.0;
+    return c.n * sl * pow(eps / c.e.back(), c.tail_K);
+}
+
+double speed_of(double eps) { return sqrt(2.0 * eps * kQe / kMe); }
+
+// Exact density sum at eps in record (a, b): linear part plus active tails.
+double record_density(const std::vector<Chan> &ch, double a, double b, double eps)
+{
+    double mid = 0.5 * (a + b), S = 0.0;
+    for (const Chan &c : ch) {
+        double pa, pb;
+        if (piece(c, mid, &pa, &pb)) S += c.n * (pa + pb * eps);
+        else S += tail_value(c, eps);
+    }
+    return S;
+}
+
+template <typename R>
+void emit(const std::vector<Chan> &ch, const std::vector<double> &g, const std::vector<double> &Slo,
+          const std::vector<double> &Ssl, const std::vector<std::vector<double>> &cv,
+          const std::vector<std::vector<double>> &cs, const std::vector<uint16_t> &bucket,
+          const std::vector<ChParam<double>> &cp, int first_tail, float log2_lo, float inv_bw,
+          std::vector<uint8_t> *blob, Layout *lay)
+{
+    const int n_rec = (int)Slo.size(), n_ch = (int)ch.size(), nb = (int)bucket.size();
+    auto pad16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
+    size_t off_rec = 0;
+    size_t off_bucket = pad16(off_rec + sizeof(Rec<R>) * n_rec);
+    size_t off_chp = pad16(off_bucket + sizeof(uint16_t) * nb);
+    size_t off_chval = pad16(off_chp + sizeof(ChParam<R>) * n_ch);
+    size_t total = pad16(off_chval + sizeof(ChVal<R>) * (size_t)n_rec * n_ch);
+    blob->assign(total, 0);
+    Rec<R> *rec = (Rec<R> *)(blob->data() + off_rec);
+    for (int i = 0; i < n_rec; ++i) {
+        double lo = (i == 0) ? 0.0 : g[i - 1];
+        double hi = (i < n_rec - 1) ? g[i] : std::numeric_limits<double>::infinity();
+        rec[i].e_lo = (R)lo;
+        rec[i].e_hi = (R)hi;
+        rec[i].S_lo = (R)Slo[i];
+        rec[i].slope = (R)Ssl[i];
+    }
+    memcpy(blob->data() + off_bucket, bucket.data(), sizeof(uint16_t) * nb);
+    ChParam<R> *p = (ChParam<R> *)(blob->data() + off_chp);
+    for (int j = 0; j < n_ch; ++j) {
+        p[j].kappa2 = (R)cp[j].kappa2;
+        p[j].mfrac = (R)cp[j].mfrac;
+        p[j].minv = (R)cp[j].minv;
+        p[j].eps_k = (R)cp[j].eps_k;
+        p[j].e_last = (R)cp[j].e_last;
+        p[j].tail_logc = (R)cp[j].tail_logc;
+        p[j].tail_K = (R)cp[j].tail_K;
+        p[j].bits = cp[j].bits;
+    }
+    ChVal<R> *v = (ChVal<R> *)(blob->data() + off_chval);
+    for (int i = 0; i < n_rec; ++i)
+        for (int j = 0; j < n_ch; ++j) {
+            v[(size_t)i * n_ch + j].val = (R)cv[i][j];
+            v[(size_t)i * n_ch + j].slope = (R)cs[i][j];
+        }
+    lay->n_rec = n_rec;
+    lay->n_buckets = nb;
+    lay->n_ch = n_ch;
+    lay->first_tail_rec = first_tail;
+    lay->log2_lo = log2_lo;
+    lay->inv_bw = inv_bw;
+    lay->off_bucket = (uint32_t)off_bucket;
+    lay->off_chp = (uint32_t)off_chp;
+    lay->off_chval = (uint32_t)off_chval;
+    lay->stage_tables = (uint32_t)off_chval;
+    lay->stage_all = (uint32_t)total;
+    lay->total = (uint32_t)total;
+}
+
+bool finite(double x) { return std::isfinite(x); }
+
+}  // namespace
+
+bz_status compile_mixture(const bz_gas *gases, int32_t n_gases, const bz_mixture_opts *opts,
+                          CompiledMixture *out, std::string *err)
+{
+    if (!gases || n_gases < 1) { *err = "need at least one gas"; return BZ_EINVAL; }
+    std::vector<Chan> ch;
+    std::vector<ChParam<double>> cp;
+    double n_total = 0.0, emax = 0.0;
+    const double m = kMe;
+    for (int gi = 0; gi < n_gases; ++gi) {
+        const bz_gas &G = gases[gi];
+        if (!(G.mass_kg > 0.0) || !finite(G.mass_kg)) { *err = "gas mass must be > 0"; return BZ_EINVAL; }
+        if (!(G.number_density_m3 > 0.0) || !finite(G.number_density_m3)) {
+            *err = "gas number density must be > 0"; return BZ_EINVAL;
+        }
+        if (G.angular != BZ_ANG_ISOTROPIC && G.angular != BZ_ANG_SCREENED_COULOMB) {
+            *err = "unknown angular model"; return BZ_EINVAL;
+        }
+        if (G.n_channels < 1 || !G.channels) { *err = "a gas needs at least one channel"; return BZ_EINVAL; }
+        n_total += G.number_density_m3;
+        const double M = G.mass_kg;
+        for (int c = 0; c < G.n_channels; ++c) {
+            const bz_channel &C = G.channels[c];
+            if (C.kind < BZ_ELASTIC || C.kind > BZ_IONIZATION) { *err = "unknown channel kind"; return BZ_EINVAL; }
+            if (C.n_points < 1 || !C.energy_eV || !C.sigma_m2) { *err = "empty cross-section table"; return BZ_EINVAL; }
+            if (!(C.threshold_eV >= 0.0) || !finite(C.threshold_eV)) { *err = "threshold must be >= 0"; return BZ_EINVAL; }
+            Chan k;
+            k.kind = C.kind;
+            k.gas = gi;
+            k.th = (C.kind == BZ_ELASTIC) ? 0.0 : C.threshold_eV;
+            k.n = G.number_density_m3;
+            k.e.assign(C.energy_eV, C.energy_eV + C.n_points);
+            k.s.assign(C.sigma_m2, C.sigma_m2 + C.n_points);
+            for (int i = 0; i < C.n_points; ++i) {
+                if (!finite(k.e[i]) || k.e[i] < 0.0) { *err = "energies must be finite and >= 0"; return BZ_EINVAL; }
+                if (!finite(k.s[i]) || k.s[i] < 0.0) { *err = "cross sections must be finite and >= 0"; return BZ_EINVAL; }
+                if (i > 0 && !(k.e[i] > k.e[i - 1])) { *err = "energies must be strictly increasing"; return BZ_EINVAL; }
+                if (C.kind != BZ_ELASTIC && k.e[i] < k.th && k.s[i] > 0.0) {
+                    *err = "cross section > 0 below the threshold"; return BZ_EINVAL;
+                }
+            }
+            size_t n = k.e.size();
+            double sl = k.s[n - 1];
+            k.tail_zero = (sl == 0.0);
+            k.tail_K = 0.0;
+            if (n >= 2 && k.s[n - 1] > 0.0 && k.s[n - 2] > 0.0)
+                k.tail_K = log(k.s[n - 1] / k.s[n - 2]) / log(k.e[n - 1] / k.e[n - 2]);
+            emax = std::max(emax, k.e[n - 1]);
+            ChParam<double> p;
+            p.kappa2 = 2.0 * m * M / ((m + M) * (m + M));
+            p.mfrac = M / (m + M);
+            p.minv = (m + M) / M;
+            p.eps_k = k.th;
+            p.e_last = k.e[n - 1];
+            p.tail_K = k.tail_K;
+            p.tail_logc = k.tail_zero ? 0.0 : log(k.n * sl) - k.tail_K * log(k.e[n - 1]);
+            p.bits = C.kind | (G.angular << 4) | ((k.tail_zero ? 1 : 0) << 8);
+            ch.push_back(std::move(k));
+            cp.push_back(p);
+        }
+    }
+    const int n_ch = (int)ch.size();
+    // union grid of all table energies and inelastic thresholds
+    std::vector<double> g;
+    for (const Chan &c : ch) {
+        g.insert(g.end(), c.e.begin(), c.e.end());
+        if (c.kind != BZ_ELASTIC) g.push_back(c.th);
+    }
+    std::sort(g.begin(), g.end());
+    g.erase(std::unique(g.begin(), g.end()), g.end());
+    const int P = (int)g.size();
+    const int n_rec = P + 1;
+    if (n_rec > 65535) { *err = "more than 65535 union grid points"; return BZ_EINVAL; }
+    std::vector<double> Slo(n_rec), Ssl(n_rec);
+    std::vector<std::vector<double>> cv(n_rec, std::vector<double>(n_ch, 0.0)), cs = cv;
+    int first_tail = n_rec - 1;
+    for (int i = 0; i < n_rec; ++i) {
+        double lo = (i == 0) ? 0.0 : g[i - 1];
+        double hi = (i < n_rec - 1) ? g[i] : lo * 2.0 + 1.0;
+        // record 0 is [0, g0): every channel is on its left extension there
+        double mid = (i == 0) ? 0.5 * g[0] : 0.5 * (lo + hi);
+        double S = 0.0, sl = 0.0;
+        bool any_tail = false;
+        for (int j = 0; j < n_ch; ++j) {
+            double a, b;
+            if (i == n_rec - 1 || !piece(ch[j], mid, &a, &b)) { any_tail = true; continue; }
+            cv[i][j] = ch[j].n * (a + b * lo);
+            cs[i][j] = ch[j].n * b;
+            S += cv[i][j];
+            sl += cs[i][j];
+        }
+        Slo[i] = S;
+        Ssl[i] = sl;
+        if (any_tail && i < first_tail) first_tail = i;
+    }
+    // exact maximum of nu over [0, eps_cap]
+    double cap = (opts && opts->eps_cap_eV > 0.0) ? opts->eps_cap_eV : emax;
+    double best = speed_of(g[0]) * Slo[0], best_eps = g[0];
+    auto consider = [&](double eps, double S) {
+        double v = speed_of(eps) * S;
+        if (v > best) { best = v; best_eps = eps; }
+    };
+    for (int i = 1; i < n_rec; ++i) {
+        double lo = g[i - 1];
+        if (lo >= cap) break;
+        double hi = (i < n_rec - 1) ? std::min(g[i], cap) : cap;
+        if (i < first_tail) {
+            double B = Ssl[i], A = Slo[i] - B * lo;
+            consider(lo, A + B * lo);
+            consider(hi, A + B * hi);
+            if (B != 0.0) {
+                double x = -A / (3.0 * B);
+                if (x > lo && x < hi) consider(x, A + B * x);
+            }
+        } else {
+            double rhi = (i < n_rec - 1) ? g[i] : hi;
+            auto f = [&](double x) { return speed_of(x) * record_density(ch, lo, rhi, x); };
+            const int NS = 2048;
+            int arg = 0;
+            double vm = -1.0;
+            for (int k = 0; k <= NS; ++k) {
+                double x = lo + (hi - lo) * k / NS, v = f(x);
+                if (v > vm) { vm = v; arg = k; }
+            }
+            double a = lo + (hi - lo) * std::max(arg - 1, 0) / NS, b = lo + (hi - lo) * std::min(arg + 1, NS) / NS;
+            const double gr = 0.6180339887498949;
+            double x1 = b - gr * (b - a), x2 = a + gr * (b - a), f1 = f(x1), f2 = f(x2);
+            for (int it = 0; it < 200 && (b - a) > 1e-14 * b; ++it) {
+                if (f1 < f2) { a = x1; x1 = x2; f1 = f2; x2 = a + gr * (b - a); f2 = f(x2); }
+                else { b = x2; x2 = x1; f2 = f1; x1 = b - gr * (b - a); f1 = f(x1); }
+            }
+            double xs[4] = {lo + (hi - lo) * arg / NS, x1, x2, hi};
+            for (double x : xs) {
+                double v = f(x);
+                if (v > best) { best = v; best_eps = x; }
+            }
+        }
+    }
+    double guard = (opts && opts->majorant_guard >= 0.0) ? opts->majorant_guard : 1e-6;
+    // bucket index over log2 energy of the positive union points
+    int ipos = 0;
+    while (ipos < P && g[ipos] <= 0.0) ++ipos;
+    double L0 = (ipos < P) ? log2(g[ipos]) : 0.0, L1 = log2(g[P - 1] > 0.0 ? g[P - 1] : 1.0);
+    int nb = std::min(std::max(2 * P, 64), 65535);
+    double w = (L1 > L0) ? (L1 - L0) / nb : 0.0;
+    if (w == 0.0) nb = 1;
+    std::vector<uint16_t> bucket(nb);
+    for (int b = 0; b < nb; ++b) {
+        double e = exp2(L0 + b * w);
+        // record i holds [g[i-1], g[i]) for i >= 1, [0, g[0]) for i = 0
+        int i = (int)(std::upper_bound(g.begin(), g.end(), e) - g.begin());
+        bucket[b] = (uint16_t)i;
+    }
+    float log2_lo = (float)L0, inv_bw = (w > 0.0) ? (float)(1.0 / w) : 0.0f;
+
+    emit<float>(ch, g, Slo, Ssl, cv, cs, bucket, cp, first_tail, log2_lo, inv_bw, &out->blob32, &out->lay32);
+    emit<double>(ch, g, Slo, Ssl, cv, cs, bucket, cp, first_tail, log2_lo, inv_bw, &out->blob64, &out->lay64);
+    out->n_total = n_total;
+    out->nu_max = best;
+    out->nu_trial = best * (1.0 + guard);
+    bz_mixture_info &I = out->info;
+    memset(&I, 0, sizeof I);
+    I.nu_max = best;
+    I.nu_trial = out->nu_trial;
+    I.eps_at_max = best_eps;
+    I.eps_cap = cap;
+    I.n_total = n_total;
+    I.n_gases = n_gases;
+    I.n_channels = n_ch;
+    I.n_records = n_rec;
+    I.n_buckets = nb;
+    I.first_tail_record = first_tail;
+    return BZ_OK;
+}
+
+}  // namespace bz

@@ -1,0 +1,342 @@
+"""CUDA path against the FP64 oracle, through the C ABI.
+
+Bit-exact where the work is integer (Philox); 1e-5 relative for one FP32
+trial step replayed from identical counters (1e-11 in FP64); swarm tallies
+within 3 combined standard errors (and 0.5 % where the sample allows) of the
+oracle; FP64 reductions of identical per-particle data to 1e-10.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from oracle import tallies as OT
+from paper_1901_08140_gb300 import bz
+from paper_1901_08140_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+QE = 1.602176634e-19
+ME = 9.1093837015e-31
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1901_08140_gb300 import build as B
+    B.build()
+    c = bz.Context(0)
+    yield c
+    c.close()
+
+
+# ---------------------------------------------------------------------------
+def test_philox_bit_exact(ctx):
+    rng = np.random.default_rng(1)
+    ctr = rng.integers(0, 2 ** 32, size=(3000, 4), dtype=np.uint64).astype(np.uint32)
+    ctr[:10] = 0
+    ctr[10:20] = 0xFFFFFFFF
+    for key in (0, 0xFFFFFFFFFFFFFFFF, W.swarm_seed(7)):
+        got = bz.philox(ctx, ctr, key)
+        want = np.array([O.philox(c, [key & 0xFFFFFFFF, key >> 32]) for c in ctr])
+        assert np.array_equal(got, want)
+
+
+# ---------------------------------------------------------------------------
+# single-step replay
+# ---------------------------------------------------------------------------
+def _screened(g):
+    import dataclasses
+    return dataclasses.replace(g, angular=W.SCREENED_COULOMB)
+
+
+def _inner_tail_gases():
+    e = np.geomspace(1e-3, 100.0, 300)
+    el = W.Channel(W.ELASTIC, 0.0, e, 2e-20 / (1 + e))
+    ex = W.Channel(W.EXCITATION, 5.0, np.linspace(5.0, 30.0, 20), np.linspace(0.0, 3e-20, 20))
+    io = W.Channel(W.IONIZATION, 12.0, np.linspace(12.0, 60.0, 30), np.linspace(0.0, 2e-20, 30))
+    return [W.Gas("tails", 40 * W.ATOMIC_MASS_UNIT, W.N_STP_293, W.ISOTROPIC, [el, ex, io])]
+
+
+CASES = {
+    "argon_100Td": (lambda: [W.argon_like()], 100.0, 0.0, 0.0),
+    "arco2_B1T": (W.ar_co2_mixture, 100.0, 1.0, math.pi / 2),
+    "screened_B_oblique": (lambda: [_screened(W.argon_like())], 30.0, 0.3, 0.7),
+    "batched_mix": (lambda: W.batched_swarms(count=6)[5].gases, 200.0, 1.7, 2.2),
+    "inner_tails": (_inner_tail_gases, 300.0, 0.0, 0.0),
+    "maxwell": (lambda: [W.maxwell_gas()], 10.0, 0.0, 0.0),
+}
+
+
+def _random_states(rng, n, nu_trial, emax=400.0):
+    eps = np.exp(rng.uniform(np.log(1e-3), np.log(emax), n))
+    eps[:8] = [0.0, 1e-6, 99.999, 100.0, 100.001, 11.5, 15.76, 13.8][: min(8, n)]
+    d = rng.normal(size=(n, 3))
+    d /= np.linalg.norm(d, axis=1)[:, None]
+    st = np.zeros((n, 8))
+    st[:, 0:3] = rng.normal(size=(n, 3)) * 1e-5
+    st[:, 3:6] = d * np.sqrt(2 * eps * QE / ME)[:, None]
+    st[:, 6] = rng.uniform(0, 1e-9, n)
+    st[:, 7] = nu_trial * np.where(rng.uniform(size=n) < 0.1, rng.uniform(0.05, 1.0, n), 1.0)
+    return st
+
+
+def _margins(m, out_o, dec_o, eps_o, ids, steps, seed, state):
+    """Distance of each draw from its decision boundaries, relative to nu'."""
+    n = len(ids)
+    marg = np.full(n, np.inf)
+    for i in range(n):
+        nu_p = state[i, 7]
+        e = eps_o[i, 0]
+        nu = m.nu(e)
+        w = O.philox([int(ids[i]) & 0xFFFFFFFF, int(ids[i]) >> 32, int(steps[i]), 0], [seed & 0xFFFFFFFF, seed >> 32])
+        r = O.uniform(w[1]) * nu_p
+        mg = min(abs(nu - nu_p), abs(r - nu)) / nu_p
+        if dec_o[i] >= 0:
+            v = math.sqrt(2 * e * QE / ME)
+            cum = 0.0
+            for c in range(m.n_channels):
+                cum += m.gas_density[m.ch_gas[c]] * m.sigma(c, e)
+                mg = min(mg, abs(v * cum - r) / nu_p)
+        marg[i] = mg
+    return marg
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("precision", [32, 64])
+def test_single_step_replay_matches_oracle(ctx, case, precision):
+    make, eon, b, ang = CASES[case]
+    gases = make()
+    m = O.Mixture(gases)
+    mix = bz.Mixture(ctx, gases)
+    rng = np.random.default_rng(hash((case, precision)) % 2 ** 32)
+    n = 4000
+    state = _random_states(rng, n, mix.info["nu_trial"])
+    ids = rng.integers(0, 2 ** 40, n, dtype=np.uint64)
+    steps = rng.integers(0, 2 ** 31, n, dtype=np.uint64).astype(np.uint32)
+    seed = W.swarm_seed(hash(case) % 1000)
+    cfg = bz.make_config(n_electrons=1, real_collisions=1, e_over_n_Td=eon, b_T=b, b_angle_rad=ang,
+                         precision=precision, seed=seed)
+    out_g, dec_g, eps_g = bz.step_replay(ctx, mix, cfg, state, ids, steps)
+    out_o, dec_o, eps_o = O.step_replay(m, state, ids, steps, e_over_n_Td=eon, seed=seed, b_T=b, b_angle_rad=ang)
+    tol = 1e-5 if precision == 32 else 1e-11
+    marg = _margins(m, out_o, dec_o, eps_o, ids, steps, seed, state)
+    near = marg < (1e-5 if precision == 32 else 1e-11)
+    same = dec_g == dec_o
+    assert np.all(same | near), f"decisions differ away from boundaries: {np.nonzero(~(same | near))[0][:10]}"
+    assert near.mean() < 0.01
+    k = same & ~near
+    assert k.sum() > 0.9 * n
+    # energies before / after
+    assert np.allclose(eps_g[k, 0], eps_o[k, 0], rtol=tol, atol=1e-30)
+    real = k & (dec_o >= 0)
+    assert real.sum() > 50
+    scale_e = np.maximum(eps_o[real, 1], 1e-6 * eps_o[real, 0])
+    assert np.all(np.abs(eps_g[real, 1] - eps_o[real, 1]) <= tol * 10 * scale_e + 1e-30)
+    # state after the step
+    dpos = np.linalg.norm(out_o[k, 0:3] - state[k, 0:3], axis=1)
+    pscale = np.maximum(dpos, 1e-7 * np.linalg.norm(state[k, 0:3], axis=1))
+    assert np.all(np.linalg.norm(out_g[k, 0:3] - out_o[k, 0:3], axis=1) <= 10 * tol * pscale + 1e-13 *
+                  np.linalg.norm(state[k, 0:3], axis=1))
+    vscale = np.linalg.norm(out_o[k, 3:6], axis=1)
+    assert np.all(np.linalg.norm(out_g[k, 3:6] - out_o[k, 3:6], axis=1) <= 10 * tol * vscale + 1e-20)
+    dt = out_o[k, 6] - state[k, 6]
+    assert np.all(np.abs(out_g[k, 6] - out_o[k, 6]) <= 10 * tol * dt + 1e-13 * state[k, 6] + 1e-300)
+    assert np.allclose(out_g[k, 7], out_o[k, 7], rtol=10 * tol, atol=0)
+    # every kind of decision occurred
+    assert (dec_o == O.DEC_NULL).sum() > 0 and (dec_o >= 0).sum() > 0
+    if case != "maxwell":
+        assert (dec_o == O.DEC_FAIL).sum() > 0
+
+
+# ---------------------------------------------------------------------------
+# swarm runs
+# ---------------------------------------------------------------------------
+def _gpu_swarm(ctx, gases, **kw):
+    mix = bz.Mixture(ctx, gases)
+    cfg = bz.make_config(**kw)
+    sw = bz.run_swarm(ctx, mix, cfg)
+    t = sw.tallies()
+    p = sw.particles()
+    sw.close()
+    return t, p, mix
+
+
+def test_tally_reduction_equals_oracle_estimators_on_same_particles(ctx):
+    gases = W.ar_co2_mixture()
+    t, p, mix = _gpu_swarm(ctx, gases, n_electrons=20037, real_collisions=60, e_over_n_Td=150.0, b_T=0.8,
+                           b_angle_rad=1.1, seed=11, id_offset=5)
+    ref = OT.swarm_tallies(p, 150.0, mix.info["n_total"])
+    for k in ["W", "Wx", "Wy", "W_flux", "eps", "eps_after", "alpha", "eta", "D", "D_L", "D_T", "sig", "sig_L",
+              "sig_T", "D_L_flux", "D_T_flux", "alpha_flux", "eta_flux", "efficiency", "mu", "mu_N", "mu_0",
+              "lorentz_angle"]:
+        assert t[k] == pytest.approx(ref[k], rel=1e-10, abs=1e-300), k
+    for k in ["W_se", "eps_se", "D_se", "D_L_se", "D_T_se", "sig_se", "alpha_se"]:
+        assert t[k] == pytest.approx(ref[k], rel=1e-8, abs=1e-300), k
+    for k in ["n_real", "n_null", "n_fail", "n_ion", "n_att", "n_particles"]:
+        assert t[k] == ref[k], k
+    assert t["error_flags"] == 0 and t["n_incomplete"] == 0
+
+
+def _paired(p_g, p_o):
+    same = np.ones(len(p_o["t"]), bool)
+    for k in ["n_real", "n_null", "n_fail", "n_ion", "n_att", "steps"]:
+        same &= p_g[k] == p_o[k]
+    return same
+
+
+def _rel(a, b, scale):
+    return np.abs(a - b) / scale
+
+
+def test_paired_fp64_swarm_maxwell(ctx):
+    spec = W.maxwell_swarm(n_electrons=1000, real_collisions=500)
+    m = O.Mixture(spec.gases)
+    t, p, mix = _gpu_swarm(ctx, spec.gases, **_cfg_kw(spec))
+    po = O.run_swarm(m, e_over_n_Td=spec.e_over_n_Td, real_collisions=spec.real_collisions, n=spec.n_electrons,
+                     seed=spec.seed, threads=O.cpu_count())
+    same = _paired(p, po)
+    assert same.mean() > 0.99
+    for k in ["z", "t", "sum_e", "sum_e2"]:
+        assert np.all(_rel(p[k][same], po[k][same], np.abs(po[k][same]) + 1e-300) < 1e-9), k
+    for k in ["x", "y"]:
+        sc = np.abs(po["z"][same]) + np.abs(po[k][same])
+        assert np.all(_rel(p[k][same], po[k][same], sc) < 1e-9), k
+
+
+def _cfg_kw(spec, **over):
+    kw = dict(n_electrons=spec.n_electrons, real_collisions=spec.real_collisions, e_over_n_Td=spec.e_over_n_Td,
+              b_T=spec.b_T, b_angle_rad=spec.b_angle_rad, precision=spec.precision, seed=spec.seed,
+              eps0_mean_eV=spec.eps0_mean_eV)
+    kw.update(over)
+    return kw
+
+
+@pytest.mark.parametrize("case", ["argon_30Td", "arco2_B1T", "argon_1000Td"])
+def test_paired_fp32_swarm_against_fp64_oracle(ctx, case):
+    if case == "arco2_B1T":
+        spec = W.ar_co2_swarm(n_electrons=3000, real_collisions=200)
+    else:
+        eon = 30.0 if case == "argon_30Td" else 1000.0
+        spec = W.SwarmSpec([W.argon_like()], eon, 0.0, 0.0, 3000, 200, W.swarm_seed(77))
+    m = O.Mixture(spec.gases)
+    t, p, mix = _gpu_swarm(ctx, spec.gases, **_cfg_kw(spec))
+    po = O.run_swarm(m, e_over_n_Td=spec.e_over_n_Td, b_T=spec.b_T, b_angle_rad=spec.b_angle_rad,
+                     real_collisions=spec.real_collisions, n=spec.n_electrons, seed=spec.seed,
+                     threads=O.cpu_count())
+    same = _paired(p, po)
+    assert same.mean() > 0.5
+    for k in ["t", "sum_e", "sum_e2"]:
+        r = _rel(p[k][same], po[k][same], np.abs(po[k][same]) + 1e-300)
+        assert np.median(r) < 1e-5 and np.max(r) < 1e-2, k
+    # swarm statistics within 3 combined standard errors
+    to = OT.swarm_tallies(po, spec.e_over_n_Td, m.n_total)
+    for k in ["W", "eps", "eps_after", "D_L", "D_T"]:
+        se = math.hypot(t[k + "_se"], to[k + "_se"])
+        assert abs(t[k] - to[k]) <= 3 * se + 1e-12 * abs(to[k]), (k, t[k], to[k], se)
+
+
+def test_maxwell_model_closed_forms_on_gpu_fp64(ctx):
+    from test_oracle_pins import _maxwell_closed_forms
+    spec = W.maxwell_swarm(n_electrons=300000, real_collisions=1000)
+    gas = spec.gases[0]
+    t, p, mix = _gpu_swarm(ctx, spec.gases, **_cfg_kw(spec))
+    assert t["n_particles"] == 300000 and t["error_flags"] == 0
+    nu = 1e12
+    E = spec.e_over_n_Td * 1e-21 * gas.number_density_m3
+    vd = QE * E / (ME * nu)
+    kappa = 2 * ME * gas.mass_kg / (ME + gas.mass_kg) ** 2
+    mean_eps, DT, DL = _maxwell_closed_forms(1000, 0.1, nu, kappa, vd)
+    assert abs(t["W_flux"] - vd) < 0.005 * vd
+    assert abs(t["W"] - vd) < max(3 * t["W_se"], 0.005 * vd)
+    assert abs(t["eps"] - mean_eps) < 3 * t["eps_se"] and abs(t["eps"] / mean_eps - 1) < 0.005
+    x, y, z, tt = p["x"], p["y"], p["z"], p["t"]
+    g = p["id"] % 32
+    DT_hat = np.sum(x ** 2 + y ** 2) / (4 * np.sum(tt))
+    DL_hat = np.sum((z - vd * tt) ** 2) / (2 * np.sum(tt))
+    se_T = np.std([np.sum(x[g == j] ** 2 + y[g == j] ** 2) / (4 * np.sum(tt[g == j])) for j in range(32)], ddof=1) / math.sqrt(32)
+    se_L = np.std([np.sum((z[g == j] - vd * tt[g == j]) ** 2) / (2 * np.sum(tt[g == j])) for j in range(32)], ddof=1) / math.sqrt(32)
+    assert abs(DT_hat - DT) < 3 * se_T
+    assert abs(DL_hat - DL) < 3 * se_L
+
+
+def test_full_size_argon_swarm_sampled_against_oracle(ctx):
+    """The workload the benchmark times (one E/N point of the Argon-like
+    sweep, 1e6 electrons x 1000 real collisions, FP32), checked on particles
+    the oracle recomputes one by one, plus size-independent invariants."""
+    spec = W.argon_sweep(points=32)[8]
+    t, p, mix = _gpu_swarm(ctx, spec.gases, **_cfg_kw(spec))
+    assert t["n_particles"] == spec.n_electrons and t["error_flags"] == 0 and t["n_incomplete"] == 0
+    assert np.all(p["n_real"] == spec.real_collisions) and np.all(p["status"] == bz.ST_DONE)
+    assert np.all(p["t"] > 0) and np.all(np.isfinite(p["z"]))
+    assert t["n_real"] == spec.n_electrons * spec.real_collisions
+    m = O.Mixture(spec.gases)
+    rng = np.random.default_rng(3)
+    sample = np.sort(rng.choice(spec.n_electrons, 48, replace=False))
+    sample[0] = spec.n_electrons - 1
+    same = 0
+    for i in sample:
+        po = O.run_swarm(m, e_over_n_Td=spec.e_over_n_Td, real_collisions=spec.real_collisions, n=1,
+                         seed=spec.seed, id0=int(i))
+        if all(p[k][i] == po[k][0] for k in ["n_null", "n_fail", "n_ion", "n_att", "steps"]):
+            same += 1
+            assert abs(p["t"][i] / po["t"][0] - 1) < 1e-3
+            assert abs(p["sum_e"][i] / po["sum_e"][0] - 1) < 1e-3
+    assert same >= 0.5 * len(sample)
+
+
+def test_sharding_by_id_range_is_invariant(ctx):
+    gases = [W.argon_like()]
+    kw = dict(real_collisions=100, e_over_n_Td=50.0, seed=123)
+    _, p_all, _ = _gpu_swarm(ctx, gases, n_electrons=5000, **kw)
+    _, p_a, _ = _gpu_swarm(ctx, gases, n_electrons=2000, **kw)
+    _, p_b, _ = _gpu_swarm(ctx, gases, n_electrons=3000, id_offset=2000, **kw)
+    for k in ["x", "y", "z", "t", "sum_e", "n_null", "steps"]:
+        assert np.array_equal(p_all[k], np.concatenate([p_a[k], p_b[k]])), k
+
+
+@pytest.mark.parametrize("n", [1, 31, 33, 257, 1000])
+def test_ragged_sizes_complete(ctx, n):
+    t, p, _ = _gpu_swarm(ctx, [W.argon_like()], n_electrons=n, real_collisions=7, e_over_n_Td=20.0, seed=n)
+    assert t["n_particles"] == n and np.all(p["n_real"] == 7) and t["n_real"] == 7 * n
+
+
+def test_degenerate_and_limit_cases(ctx):
+    gases = [W.argon_like()]
+    # no field: no drift beyond noise
+    t, p, _ = _gpu_swarm(ctx, gases, n_electrons=20000, real_collisions=50, e_over_n_Td=0.0, seed=4)
+    assert abs(t["W"]) < 5 * t["W_se"]
+    # one real collision per particle
+    t, p, _ = _gpu_swarm(ctx, gases, n_electrons=1000, real_collisions=1, e_over_n_Td=10.0, seed=4)
+    assert np.all(p["n_real"] == 1)
+    # time limit: every particle stops at t_end
+    t, p, _ = _gpu_swarm(ctx, gases, n_electrons=500, real_collisions=10 ** 6, e_over_n_Td=50.0, seed=4,
+                         t_end_s=2e-11)
+    assert np.all(p["status"] == bz.ST_TIME) and np.allclose(p["t"], 2e-11, rtol=1e-12, atol=0)
+    # trial cap
+    t, p, _ = _gpu_swarm(ctx, gases, n_electrons=100, real_collisions=10 ** 6, e_over_n_Td=50.0, seed=4,
+                         max_trials=500)
+    assert np.all(p["status"] == bz.ST_STEPS) and np.all(p["steps"] == 500)
+    assert t["error_flags"] & 8 and t["n_incomplete"] == 100
+
+
+def test_fixed_trial_frequency_exceeded_is_an_error(ctx):
+    mix = bz.Mixture(ctx, [W.argon_like()])
+    cfg = bz.make_config(n_electrons=1000, real_collisions=100, e_over_n_Td=300.0, seed=1,
+                         trial_mode=bz.BZ_TRIAL_FIXED, nu_trial=0.2 * mix.info["nu_trial"])
+    sw = bz.run_swarm(ctx, mix, cfg)
+    with pytest.raises(bz.BzError) as ei:
+        sw.tallies()
+    assert ei.value.status == bz.BZ_ETRIAL
+    sw.close()
+
+
+def test_invalid_configurations_are_rejected(ctx):
+    mix = bz.Mixture(ctx, [W.argon_like()])
+    for over in [dict(precision=16), dict(n_electrons=0), dict(real_collisions=0), dict(eps0_mean_eV=-1.0)]:
+        kw = dict(n_electrons=10, real_collisions=10, e_over_n_Td=1.0)
+        kw.update(over)
+        cfg = bz.make_config(**kw)
+        with pytest.raises(bz.BzError) as ei:
+            bz.run_swarm(ctx, mix, cfg)
+        assert ei.value.status == bz.BZ_EINVAL
