@@ -238,7 +238,7 @@ struct PState {
     R vr0, vr1, vr2;         // velocity right after the last real collision
     R T;                     // time since then
     R nu_p, inv_nu;          // trial frequency of this particle
-    R vpar, u0x, u0y, u0z, bux, buy, buz;  // B != 0: v = vpar b + vD + u0 cos + (b x u0) sin
+    R u0x, u0y, u0z, bux, buy, buz;  // B != 0: u0 = v_perp - vD and b x u0 at the last real collision
     Acc<R> x, y, z, t;       // position and time at the last real collision
     Acc<R> se, se2;          // energy sums before / after real collisions
     uint32_t id_lo, id_hi, k, n_real, n_null, n_fail, n_ion, n_att, status;
@@ -249,46 +249,71 @@ template <typename R>
 __device__ __forceinline__ void set_b_cache(const Fld<R> &F, PState<R> &s)
 {
     if (!F.has_b) return;
-    s.vpar = s.vr0 * F.b0 + s.vr1 * F.b1 + s.vr2 * F.b2;
-    s.u0x = s.vr0 - s.vpar * F.b0 - F.vD0;
-    s.u0y = s.vr1 - s.vpar * F.b1 - F.vD1;
-    s.u0z = s.vr2 - s.vpar * F.b2 - F.vD2;
+    const R vpar = s.vr0 * F.b0 + s.vr1 * F.b1 + s.vr2 * F.b2;
+    s.u0x = s.vr0 - vpar * F.b0 - F.vD0;
+    s.u0y = s.vr1 - vpar * F.b1 - F.vD1;
+    s.u0z = s.vr2 - vpar * F.b2 - F.vD2;
     s.bux = F.b1 * s.u0z - F.b2 * s.u0y;
     s.buy = F.b2 * s.u0x - F.b0 * s.u0z;
     s.buz = F.b0 * s.u0y - F.b1 * s.u0x;
 }
 
-// Velocity after time T since the last real collision; (sn, cs) = sincos(wT).
+// Velocity after time T since the last real collision.  With B != 0 the
+// velocity splits into the part along b (accelerated by a_par), the E x B
+// drift vD and u = v_perp - vD rotating about b at w; written as a change of
+// the velocity at the last collision,
+//   v(T) = v_r + a_par T b - u0 (1 - cos wT) + (b x u0) sin wT,
+// so that rounding stays relative to the change even when |vD| >> |v|.
+// Returns sn = sin wT and omc = 1 - cos wT (without cancellation).
 template <typename R>
 __device__ __forceinline__ void velocity_at(const Fld<R> &F, const PState<R> &s, R T, R &v0, R &v1, R &v2, R &sn,
-                                            R &cs)
+                                            R &omc)
 {
     if (F.has_b) {
+        R cs;
         sincos_(F.w * T, &sn, &cs);
-        const R vp = s.vpar + F.a_par * T;
-        v0 = vp * F.b0 + F.vD0 + s.u0x * cs + s.bux * sn;
-        v1 = vp * F.b1 + F.vD1 + s.u0y * cs + s.buy * sn;
-        v2 = vp * F.b2 + F.vD2 + s.u0z * cs + s.buz * sn;
+        omc = (cs > (R)0) ? sn * sn / ((R)1 + cs) : (R)1 - cs;
+        const R ap = F.a_par * T;
+        v0 = s.vr0 + ap * F.b0 - s.u0x * omc + s.bux * sn;
+        v1 = s.vr1 + ap * F.b1 - s.u0y * omc + s.buy * sn;
+        v2 = s.vr2 + ap * F.b2 - s.u0z * omc + s.buz * sn;
     } else {
         sn = 0;
-        cs = 1;
+        omc = 0;
         v0 = s.vr0;
         v1 = s.vr1;
         v2 = s.vr2 + F.a * T;
     }
 }
 
-// Displacement after time T since the last real collision.
+// sin(x) - x, accurate also for small x (Taylor series below |x| = 3/4).
 template <typename R>
-__device__ __forceinline__ void displacement(const Fld<R> &F, const PState<R> &s, R T, R sn, R cs, R &dx, R &dy,
+__device__ __forceinline__ R sin_minus_x(R x, R sn)
+{
+    if (fabs(x) >= (R)0.75) return sn - x;
+    const R y = x * x;
+    R p = (R)(1.0 / 1307674368000.0);
+    p = (R)(1.0 / 6227020800.0) - y * p;
+    p = (R)(1.0 / 39916800.0) - y * p;
+    p = (R)(1.0 / 362880.0) - y * p;
+    p = (R)(1.0 / 5040.0) - y * p;
+    p = (R)(1.0 / 120.0) - y * p;
+    p = (R)(1.0 / 6.0) - y * p;
+    return -x * y * p;
+}
+
+// Displacement after time T since the last real collision:
+//   dx = v_r T + a_par T^2/2 b + [u0 (sin wT - wT) + (b x u0)(1 - cos wT)] / w.
+template <typename R>
+__device__ __forceinline__ void displacement(const Fld<R> &F, const PState<R> &s, R T, R sn, R omc, R &dx, R &dy,
                                              R &dz)
 {
     if (F.has_b) {
-        const R omc = (cs > (R)0) ? sn * sn / ((R)1 + cs) : (R)1 - cs;  // 1 - cos(wT) without cancellation
-        const R par = s.vpar * T + (R)0.5 * F.a_par * T * T;
-        dx = par * F.b0 + F.vD0 * T + (s.u0x * sn + s.bux * omc) * F.inv_w;
-        dy = par * F.b1 + F.vD1 * T + (s.u0y * sn + s.buy * omc) * F.inv_w;
-        dz = par * F.b2 + F.vD2 * T + (s.u0z * sn + s.buz * omc) * F.inv_w;
+        const R smx = sin_minus_x(F.w * T, sn);
+        const R hp = (R)0.5 * F.a_par * T * T;
+        dx = s.vr0 * T + hp * F.b0 + (s.u0x * smx + s.bux * omc) * F.inv_w;
+        dy = s.vr1 * T + hp * F.b1 + (s.u0y * smx + s.buy * omc) * F.inv_w;
+        dz = s.vr2 * T + hp * F.b2 + (s.u0z * smx + s.buz * omc) * F.inv_w;
     } else {
         dx = s.vr0 * T;
         dy = s.vr1 * T;
@@ -343,11 +368,11 @@ __device__ __forceinline__ int trial(const Tab<R> &T, const Fld<R> &F, const Run
         Tn = (R)(P.t_end - s.t.value());  // TimeBulletLimiter: the flight stops at t_end
         cut = true;
     }
-    R v0, v1, v2, sn, cs;
-    velocity_at(F, s, Tn, v0, v1, v2, sn, cs);
+    R v0, v1, v2, sn, omc;
+    velocity_at(F, s, Tn, v0, v1, v2, sn, omc);
     if (cut) {
         R dx, dy, dz;
-        displacement(F, s, Tn, sn, cs, dx, dy, dz);
+        displacement(F, s, Tn, sn, omc, dx, dy, dz);
         s.x.add(dx);
         s.y.add(dy);
         s.z.add(dz);
@@ -401,7 +426,7 @@ __device__ __forceinline__ int trial(const Tab<R> &T, const Fld<R> &F, const Run
     const int c = select_channel<R, CH_SMEM>(T, ri, elo, eps, r * inv_sp);
     {
         R dx, dy, dz;
-        displacement(F, s, Tn, sn, cs, dx, dy, dz);
+        displacement(F, s, Tn, sn, omc, dx, dy, dz);
         s.x.add(dx);
         s.y.add(dy);
         s.z.add(dz);
@@ -653,9 +678,9 @@ __global__ void __launch_bounds__(kBlock) replay_kernel(const ReplayArgs A)
         R ei, ef;
         const int dec = trial<R, CH_SMEM>(T, F, P, s, ei, ef);
         // state at the trial point: last real collision advanced by s.T
-        R v0, v1, v2, sn, cs, dx, dy, dz;
-        velocity_at(F, s, s.T, v0, v1, v2, sn, cs);
-        displacement(F, s, s.T, sn, cs, dx, dy, dz);
+        R v0, v1, v2, sn, omc, dx, dy, dz;
+        velocity_at(F, s, s.T, v0, v1, v2, sn, omc);
+        displacement(F, s, s.T, sn, omc, dx, dy, dz);
         double *o = A.state_out + 8 * i;
         o[0] = s.x.value() + (double)dx;
         o[1] = s.y.value() + (double)dy;

@@ -124,9 +124,8 @@ def test_single_step_replay_matches_oracle(ctx, case, precision):
     near = marg < (1e-5 if precision == 32 else 1e-11)
     same = dec_g == dec_o
     assert np.all(same | near), f"decisions differ away from boundaries: {np.nonzero(~(same | near))[0][:10]}"
-    assert near.mean() < 0.01
-    k = same & ~near
-    assert k.sum() > 0.9 * n
+    assert (~same).mean() < 0.01
+    k = same
     # energies before / after
     assert np.allclose(eps_g[k, 0], eps_o[k, 0], rtol=tol, atol=1e-30)
     real = k & (dec_o >= 0)
@@ -143,10 +142,10 @@ def test_single_step_replay_matches_oracle(ctx, case, precision):
     dt = out_o[k, 6] - state[k, 6]
     assert np.all(np.abs(out_g[k, 6] - out_o[k, 6]) <= 10 * tol * dt + 1e-13 * state[k, 6] + 1e-300)
     assert np.allclose(out_g[k, 7], out_o[k, 7], rtol=10 * tol, atol=0)
-    # every kind of decision occurred
-    assert (dec_o == O.DEC_NULL).sum() > 0 and (dec_o >= 0).sum() > 0
+    # every kind of decision occurred (with nu = nu' the Maxwell gas has no null collisions)
+    assert (dec_o >= 0).sum() > 0
     if case != "maxwell":
-        assert (dec_o == O.DEC_FAIL).sum() > 0
+        assert (dec_o == O.DEC_NULL).sum() > 0 and (dec_o == O.DEC_FAIL).sum() > 0
 
 
 # ---------------------------------------------------------------------------
