@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="bound of the CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--only-point", type=int, default=-1, help="run one E/N point of the sweep (profiling case)")
     return ap.parse_args()
 
 
@@ -111,6 +112,8 @@ class Clocks:
 def sweep_specs(args, rank):
     from paper_1901_08140_gb300 import workloads as W
     specs = W.argon_sweep(n_electrons=args.electrons, real_collisions=args.collisions, points=args.points)
+    if args.only_point >= 0:
+        specs = [specs[args.only_point]]
     return specs
 
 
@@ -257,8 +260,9 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"Argon-like E/N sweep: {args.points} log points 1-1000 Td x "
                                f"{args.electrons} electrons x {args.collisions} real collisions, "
-                               "FP32 flights, FP64 tallies, lazy exact trial frequency, B = 0",
-                   "mode": "plain (one persistent launch per swarm)", "swarms": args.points,
+                               "FP32 flights, FP64 tallies, lazy exact trial frequency, B = 0"
+                               + (f" (point {args.only_point} only)" if args.only_point >= 0 else ""),
+                   "mode": "plain (one persistent launch per swarm)", "swarms": len(specs),
                    "electrons_per_swarm": args.electrons, "real_collisions": args.collisions,
                    "l2": "flushed between steps (256 MiB write)", "parallelism": f"dp{world} (particle ids)"},
         "trial_collisions_per_s": trials * world / (t_max / 1e3) if world == 1 else None,
