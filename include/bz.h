@@ -68,6 +68,8 @@ typedef struct {
 /* Creates a context on CUDA device `device`.  The allocator is copied.
  * Errors: BZ_EINVAL (bad device), BZ_ECUDA. */
 bz_status bz_create(int device, const bz_allocator *alloc, bz_ctx **out);
+/* Releases the caller's hold on the context.  Mixtures and swarms created
+ * from it keep it alive; it is freed when the last of them is destroyed. */
 void bz_destroy(bz_ctx *ctx);
 /* Message of the last failure on the calling thread ("" if none). */
 const char *bz_last_error(void);

@@ -13,6 +13,7 @@ from __future__ import annotations
 
 import ctypes as C
 import os
+import sys
 from typing import Dict, Optional, Sequence
 
 import numpy as np
@@ -226,6 +227,9 @@ class Context:
             self.h = None
 
     def __del__(self):
+        # at interpreter shutdown the allocator callbacks may already be gone
+        if sys.is_finalizing():
+            return
         try:
             self.close()
         except Exception:
@@ -270,6 +274,9 @@ class Mixture:
             self.h = None
 
     def __del__(self):
+        # at interpreter shutdown the allocator callbacks may already be gone
+        if sys.is_finalizing():
+            return
         try:
             self.close()
         except Exception:
@@ -359,6 +366,9 @@ class Swarm:
             self.h = None
 
     def __del__(self):
+        # at interpreter shutdown the allocator callbacks may already be gone
+        if sys.is_finalizing():
+            return
         try:
             self.close()
         except Exception:

@@ -3,6 +3,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <atomic>
 #include <new>
 #include <string>
 
@@ -10,6 +11,7 @@
 #include "kernels.h"
 
 struct bz_ctx {
+    std::atomic<int> refs;  // the context itself + each live mixture and swarm
     int device;
     bz_allocator alloc;
     bool custom_alloc;
@@ -72,6 +74,13 @@ void dev_free(bz_ctx *c, void *p, size_t bytes, cudaStream_t s)
 }
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+void ctx_retain(bz_ctx *c) { c->refs.fetch_add(1); }
+
+void ctx_release(bz_ctx *c)
+{
+    if (c->refs.fetch_sub(1) == 1) delete c;
+}
 
 bz::Fields make_fields(const bz_swarm_config &cfg, double n_total)
 {
@@ -140,6 +149,8 @@ bz_status prepare_run(const bz_mixture *mix, const bz_swarm_config *cfg, bz::Run
 
 }  // namespace
 
+void bz::set_last_error(const std::string &msg) { g_err = msg; }
+
 extern "C" {
 
 const char *bz_last_error(void) { return g_err.c_str(); }
@@ -157,6 +168,7 @@ bz_status bz_create(int device, const bz_allocator *alloc, bz_ctx **out)
     if (alloc && (!alloc->alloc || !alloc->free)) return fail(BZ_EINVAL, "allocator needs alloc and free");
     bz_ctx *c = new (std::nothrow) bz_ctx();
     if (!c) return fail(BZ_ENOMEM, "host allocation");
+    c->refs.store(1);
     c->device = device;
     c->custom_alloc = alloc != nullptr;
     if (alloc) c->alloc = *alloc;
@@ -166,7 +178,10 @@ bz_status bz_create(int device, const bz_allocator *alloc, bz_ctx **out)
     return BZ_OK;
 }
 
-void bz_destroy(bz_ctx *ctx) { delete ctx; }
+void bz_destroy(bz_ctx *ctx)
+{
+    if (ctx) ctx_release(ctx);
+}
 
 bz_status bz_create_gas_mixture(bz_ctx *ctx, const bz_gas *gases, int32_t n_gases, const bz_mixture_opts *opts,
                                 bz_mixture **out)
@@ -211,6 +226,7 @@ bz_status bz_create_gas_mixture(bz_ctx *ctx, const bz_gas *gases, int32_t n_gase
     m->cm.info.channels_in_smem = m->ch_smem32 ? 1 : 0;
     m->cm.info.smem_bytes = (int32_t)(m->ch_smem32 ? m->cm.lay32.stage_all : m->cm.lay32.stage_tables);
     m->cm.info.table_bytes = (int32_t)(m->bytes32 + m->bytes64);
+    ctx_retain(ctx);
     *out = m;
     return BZ_OK;
 }
@@ -222,7 +238,9 @@ void bz_destroy_mixture(bz_mixture *mix)
     cudaDeviceSynchronize();
     dev_free(mix->ctx, mix->blob32, mix->bytes32, 0);
     dev_free(mix->ctx, mix->blob64, mix->bytes64, 0);
+    bz_ctx *ctx = mix->ctx;
     delete mix;
+    ctx_release(ctx);
 }
 
 bz_status bz_mixture_get_info(const bz_mixture *mix, bz_mixture_info *out)
@@ -292,6 +310,7 @@ bz_status bz_run_swarm(bz_ctx *ctx, const bz_mixture *mix, const bz_swarm_config
     bz_swarm *s = new (std::nothrow) bz_swarm();
     if (!s) return fail(BZ_ENOMEM, "host allocation");
     s->ctx = ctx;
+    ctx_retain(ctx);
     s->cfg = *cfg;
     s->stream = (cudaStream_t)stream;
     s->n = n;
@@ -311,6 +330,7 @@ bz_status bz_run_swarm(bz_ctx *ctx, const bz_mixture *mix, const bz_swarm_config
     s->mem = (uint8_t *)dev_alloc(ctx, s->bytes, s->stream);
     if (!s->mem) {
         delete s;
+        ctx_release(ctx);
         return fail(BZ_ENOMEM, "device allocation of the swarm state");
     }
     uint8_t *M = s->mem;
@@ -326,7 +346,9 @@ bz_status bz_run_swarm(bz_ctx *ctx, const bz_mixture *mix, const bz_swarm_config
         (e = cudaEventCreateWithFlags(&s->done, cudaEventDisableTiming)) != cudaSuccess) {
         dev_free(ctx, s->mem, s->bytes, s->stream);
         if (s->tallies_host) cudaFreeHost(s->tallies_host);
+        if (s->done) cudaEventDestroy(s->done);
         delete s;
+        ctx_release(ctx);
         return cuda_fail(e, "swarm set-up");
     }
     for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaEventCreate(&s->ev[i]);
@@ -424,7 +446,9 @@ void bz_destroy_swarm(bz_swarm *sw)
     if (sw->done) cudaEventDestroy(sw->done);
     for (int i = 0; i < 3; ++i)
         if (sw->ev[i]) cudaEventDestroy(sw->ev[i]);
+    bz_ctx *ctx = sw->ctx;
     delete sw;
+    ctx_release(ctx);
 }
 
 bz_status bz_swarm_timing(bz_swarm *sw, double *step_ms, double *tally_ms)

@@ -70,6 +70,9 @@ struct CompiledMixture {
     double nu_max, nu_trial;
 };
 
+// Sets the calling thread's message returned by bz_last_error (api.cpp).
+void set_last_error(const std::string &msg);
+
 // Host mixture compiler (mixture.cpp).  Returns BZ_OK or an error with *err.
 bz_status compile_mixture(const bz_gas *gases, int32_t n_gases, const bz_mixture_opts *opts,
                           CompiledMixture *out, std::string *err);

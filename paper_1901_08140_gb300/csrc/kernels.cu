@@ -30,6 +30,9 @@ namespace bz {
 namespace {
 
 constexpr int kBlock = 256;
+#ifndef BZ_SWARM_MIN_BLOCKS
+#define BZ_SWARM_MIN_BLOCKS 1  // resident blocks per SM the register allocation must allow
+#endif
 constexpr uint32_t kStageChunk = 32768;
 constexpr uint32_t kWaitLimit = 1u << 24;
 
@@ -596,7 +599,7 @@ __device__ bool stage_tables(const uint8_t *src, uint8_t *dst, uint32_t bytes, u
 // Kernels
 // ---------------------------------------------------------------------------
 template <typename R, bool CH_SMEM>
-__global__ void __launch_bounds__(kBlock) swarm_kernel(const RunArgs P)
+__global__ void __launch_bounds__(kBlock, BZ_SWARM_MIN_BLOCKS) swarm_kernel(const RunArgs P)
 {
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ __align__(8) uint64_t mbar;
