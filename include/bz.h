@@ -241,6 +241,45 @@ bz_status bz_swarm_timing(bz_swarm *sw, double *step_ms, double *tally_ms);
 void bz_destroy_swarm(bz_swarm *sw);
 
 /* ------------------------------------------------------------------------
+ * Allocation-free tally reduction.  The paper has no counterpart: this entry
+ * exists for callers that cannot allocate device memory at the point where
+ * they need swarm statistics -- code whose device memory is entirely held by
+ * another allocator (a framework's caching pool or a serving process with a
+ * fixed HBM plan, where cudaMalloc fails or fragments the pool), and
+ * latency-sensitive loops in which cudaMalloc / cudaFree would synchronize
+ * the device.  It computes the same bz_tallies as bz_read_tallies from
+ * caller-owned per-particle device arrays (the layout bz_read_particles
+ * returns), using scratch that lives in a fixed static device array of
+ * libbz.so (BZ_NOALLOC_SCRATCH_BYTES, held by every GPU that loads the
+ * library until the process exits) instead of allocating.
+ * ------------------------------------------------------------------------ */
+#define BZ_NOALLOC_SPAN 32768u              /* particles per reduction block */
+#define BZ_NOALLOC_MAX_BLOCKS 512u
+#define BZ_NOALLOC_MAX_PARTICLES (BZ_NOALLOC_SPAN * BZ_NOALLOC_MAX_BLOCKS) /* 16777216 */
+#define BZ_NOALLOC_SCRATCH_BYTES (8u * (BZ_NOALLOC_MAX_BLOCKS * 32u * 26u + 32u * 26u + 8u) + 256u)
+
+typedef struct {
+    const double *x, *y, *z, *t;      /* device, n each: final position [m], time [s] */
+    const double *sum_e, *sum_e2;     /* device, n each: energy sums [eV] */
+    const uint32_t *n_real, *n_null, *n_fail, *n_ion, *n_att, *status;  /* device, n each */
+} bz_particle_arrays;
+
+/* Reduces n particles (ids id_offset .. id_offset + n - 1) into *out_dev (a
+ * device bz_tallies) on `stream`, asynchronously, without allocating:
+ * it calls no cudaMalloc, cudaFree or allocating library routine.
+ * e_over_n_Td and n_total_m3 give E for the mobility fields; nu_trial is
+ * copied into the result.  The first call on a device looks up the scratch
+ * array's device address (cudaGetSymbolAddress with that device current) and
+ * caches it; make that first call before any stream capture.  All calls on
+ * a device share the one scratch array and overwrite it, so calls whose
+ * kernels overlap on the GPU (concurrent streams, or threads) race: order
+ * them on one stream.  Errors: BZ_EINVAL (null pointer, n = 0),
+ * BZ_EBUDGET (n > BZ_NOALLOC_MAX_PARTICLES), BZ_ECUDA. */
+bz_status bz_reduce_tallies_noalloc(const bz_particle_arrays *in, uint64_t n, uint64_t id_offset,
+                                    double e_over_n_Td, double n_total_m3, double nu_trial,
+                                    bz_tallies *out_dev, void *stream);
+
+/* ------------------------------------------------------------------------
  * Verification entry points.
  * ------------------------------------------------------------------------ */
 

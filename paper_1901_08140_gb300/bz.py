@@ -90,6 +90,14 @@ class bz_particles(C.Structure):
         [(k, C.POINTER(C.c_uint32)) for k in _PART_U]
 
 
+class bz_particle_arrays(C.Structure):
+    _fields_ = [(k, C.c_void_p) for k in ["x", "y", "z", "t", "sum_e", "sum_e2", "n_real", "n_null", "n_fail",
+                                          "n_ion", "n_att", "status"]]
+
+
+BZ_NOALLOC_MAX_PARTICLES = 32768 * 512
+
+
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 
@@ -124,6 +132,8 @@ SIGNATURES = {
     "bz_read_particles": (C.c_int, [C.c_void_p, C.POINTER(bz_particles)]),
     "bz_destroy_swarm": (None, [C.c_void_p]),
     "bz_swarm_timing": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "bz_reduce_tallies_noalloc": (C.c_int, [C.POINTER(bz_particle_arrays), C.c_uint64, C.c_uint64, C.c_double,
+                                            C.c_double, C.c_double, C.c_void_p, C.c_void_p]),
     "bz_step_replay": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(bz_swarm_config), C.c_int64, C.c_void_p,
                                  C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "bz_philox": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p]),
@@ -172,6 +182,7 @@ def bz_query_tallies(sw, out): return lib().bz_query_tallies(sw, out)
 def bz_read_particles(sw, out): return lib().bz_read_particles(sw, out)
 def bz_destroy_swarm(sw): return lib().bz_destroy_swarm(sw)
 def bz_swarm_timing(sw, a, b): return lib().bz_swarm_timing(sw, a, b)
+def bz_reduce_tallies_noalloc(*a): return lib().bz_reduce_tallies_noalloc(*a)
 def bz_step_replay(*a): return lib().bz_step_replay(*a)
 def bz_philox(*a): return lib().bz_philox(*a)
 
