@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--only-point", type=int, default=-1, help="run one E/N point of the sweep (profiling case)")
+    ap.add_argument("--trial", choices=["window", "lazy"], default="window",
+                    help="trial frequency: exact windowed local bound (default) or the constant maximum")
     return ap.parse_args()
 
 
@@ -164,7 +166,8 @@ def run_ours(args):
     ctx = bz.Context(local)
     mix = bz.Mixture(ctx, specs[0].gases)
     # weak scaling: every rank runs the whole sweep on its own particle ids
-    cfgs = [bz.config_from_spec(s, id_offset=rank * args.electrons) for s in specs]
+    mode = bz.BZ_TRIAL_WINDOW if args.trial == "window" else bz.BZ_TRIAL_LAZY
+    cfgs = [bz.config_from_spec(s, id_offset=rank * args.electrons, trial_mode=mode) for s in specs]
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
 
@@ -181,6 +184,7 @@ def run_ours(args):
     total_ms = 0.0
     reals = trials = 0
     kern_ms = 0.0
+    steps_other = 0
     work = 0.0
     w_err = []
     launches = 0
@@ -202,8 +206,9 @@ def run_ours(args):
             reals += t["n_real"]
             tr = t["n_real"] + t["n_null"] + t["n_fail"]
             trials += tr
+            steps_other += t.get("n_window", 0)
             kern_ms += km
-            work += ALG_OPS_PER_TRIAL * tr + ALG_OPS_PER_REAL * t["n_real"]
+            work += ALG_OPS_PER_TRIAL * (tr + t.get("n_window", 0)) + ALG_OPS_PER_REAL * t["n_real"]
             w_err.append(t["W_se"] / abs(t["W"]) if t["W"] else float("inf"))
             launches += 5   # step kernel + 4 tally kernels
             sw.close()
@@ -260,14 +265,16 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"Argon-like E/N sweep: {args.points} log points 1-1000 Td x "
                                f"{args.electrons} electrons x {args.collisions} real collisions, "
-                               "FP32 flights, FP64 tallies, lazy exact trial frequency, B = 0"
+                               f"FP32 flights, FP64 tallies, {args.trial} trial frequency, B = 0"
                                + (f" (point {args.only_point} only)" if args.only_point >= 0 else ""),
                    "mode": "plain (one persistent launch per swarm)", "swarms": len(specs),
                    "electrons_per_swarm": args.electrons, "real_collisions": args.collisions,
                    "l2": "flushed between steps (256 MiB write)", "parallelism": f"dp{world} (particle ids)"},
         "trial_collisions_per_s": trials * world / (t_max / 1e3) if world == 1 else None,
         "efficiency": reals / trials if trials else None,
+        "window_restarts_per_real": steps_other / reals if reals else None,
         "max_rel_se_W": max(w_err) if w_err else None,
+        "trial_frequency": args.trial,
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
     }
     print(json.dumps(out), flush=True)

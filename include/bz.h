@@ -50,7 +50,15 @@ typedef enum {
 
 typedef enum { BZ_ELASTIC = 0, BZ_EXCITATION = 1, BZ_ATTACHMENT = 2, BZ_IONIZATION = 3 } bz_kind;
 typedef enum { BZ_ANG_ISOTROPIC = 0, BZ_ANG_SCREENED_COULOMB = 1 } bz_angular;
-typedef enum { BZ_TRIAL_LAZY = 0, BZ_TRIAL_FIXED = 1 } bz_trial_mode;
+/* Trial frequency nu' of the null-collision flights (Sec. 6):
+ *  LAZY   -- one constant nu' = exact max of nu over [0, eps_cap] (Sec. 6.2);
+ *  FIXED  -- the caller's constant nu_trial; exceeding it is an error (Sec. 6.1);
+ *  WINDOW -- a local nu' per time window: the max of nu over the energies the
+ *            electron can reach within the window (rigorous speed bound under
+ *            E and B, per-bin maxima of nu); a flight that outlasts the window
+ *            restarts at its end (exact by memorylessness).  Same statistics as
+ *            LAZY with far fewer null collisions. */
+typedef enum { BZ_TRIAL_LAZY = 0, BZ_TRIAL_FIXED = 1, BZ_TRIAL_WINDOW = 2 } bz_trial_mode;
 
 typedef struct bz_ctx bz_ctx;
 typedef struct bz_mixture bz_mixture;
@@ -166,6 +174,7 @@ typedef struct {
     uint64_t id_offset;       /* first particle id: ids id_offset .. id_offset + N - 1 */
     int32_t block_threads;    /* launch shape, 0: auto */
     int32_t blocks_per_sm;    /* 0: auto (occupancy) */
+    double window_c;          /* WINDOW mode: window = window_c / nu of the current energy bin; 0: 2 */
 } bz_swarm_config;
 
 /* Fills *cfg with defaults: N = 1e4, I = 1000, FP32, lazy mode, Maxwellian
@@ -206,6 +215,7 @@ typedef struct {
     double efficiency;        /* real / (real + null + fail) (Eq. 28) */
     double E_V_m, n_total, nu_trial, t_mean;
     uint64_t n_particles, n_real, n_null, n_fail, n_ion, n_att, n_incomplete;
+    uint64_t n_window;        /* WINDOW mode: flights restarted at a window end */
     int32_t error_flags;      /* device error bits (see BZ_ERR_*) */
     int32_t reserved;
 } bz_tallies;
@@ -256,12 +266,13 @@ void bz_destroy_swarm(bz_swarm *sw);
 #define BZ_NOALLOC_SPAN 32768u              /* particles per reduction block */
 #define BZ_NOALLOC_MAX_BLOCKS 512u
 #define BZ_NOALLOC_MAX_PARTICLES (BZ_NOALLOC_SPAN * BZ_NOALLOC_MAX_BLOCKS) /* 16777216 */
-#define BZ_NOALLOC_SCRATCH_BYTES (8u * (BZ_NOALLOC_MAX_BLOCKS * 32u * 26u + 32u * 26u + 8u) + 256u)
+#define BZ_NOALLOC_SCRATCH_BYTES (8u * (BZ_NOALLOC_MAX_BLOCKS * 32u * 27u + 32u * 27u + 8u) + 256u)
 
 typedef struct {
     const double *x, *y, *z, *t;      /* device, n each: final position [m], time [s] */
     const double *sum_e, *sum_e2;     /* device, n each: energy sums [eV] */
     const uint32_t *n_real, *n_null, *n_fail, *n_ion, *n_att, *status;  /* device, n each */
+    const uint32_t *steps;            /* device, n, or NULL (then n_window is 0) */
 } bz_particle_arrays;
 
 /* Reduces n particles (ids id_offset .. id_offset + n - 1) into *out_dev (a

@@ -21,8 +21,8 @@ import numpy as np
 from . import build as _build
 
 BZ_OK, BZ_EINVAL, BZ_ENOMEM, BZ_EBUDGET, BZ_ETRIAL, BZ_ETIMEOUT, BZ_ECUDA, BZ_ECANCEL, BZ_ENOTREADY = range(9)
-BZ_TRIAL_LAZY, BZ_TRIAL_FIXED = 0, 1
-DEC_FAIL, DEC_NULL = -2, -1
+BZ_TRIAL_LAZY, BZ_TRIAL_FIXED, BZ_TRIAL_WINDOW = 0, 1, 2
+DEC_WINDOW, DEC_FAIL, DEC_NULL = -3, -2, -1
 ST_DONE, ST_TIME, ST_STEPS, ST_TRIAL, ST_ERROR = 0, 1, 2, 3, 4
 
 
@@ -64,7 +64,7 @@ class bz_swarm_config(C.Structure):
                 ("trial_mode", C.c_int32), ("attach_keep_state", C.c_int32), ("nu_trial", C.c_double),
                 ("eps0_mean_eV", C.c_double), ("t_end_s", C.c_double), ("max_trials", C.c_uint64),
                 ("seed", C.c_uint64), ("id_offset", C.c_uint64), ("block_threads", C.c_int32),
-                ("blocks_per_sm", C.c_int32)]
+                ("blocks_per_sm", C.c_int32), ("window_c", C.c_double)]
 
 
 _TALLY_DOUBLES = ["W", "W_se", "Wx", "Wy", "W_flux", "lorentz_angle", "mu", "mu_N", "mu_0", "eps", "eps_se",
@@ -72,7 +72,7 @@ _TALLY_DOUBLES = ["W", "W_se", "Wx", "Wy", "W_flux", "lorentz_angle", "mu", "mu_
                   "D", "D_se", "D_L", "D_L_se", "D_T", "D_T_se", "D_L_flux", "D_T_flux", "sig", "sig_se",
                   "sig_L", "sig_L_se", "sig_T", "sig_T_se", "efficiency", "E_V_m", "n_total", "nu_trial",
                   "t_mean"]
-_TALLY_COUNTS = ["n_particles", "n_real", "n_null", "n_fail", "n_ion", "n_att", "n_incomplete"]
+_TALLY_COUNTS = ["n_particles", "n_real", "n_null", "n_fail", "n_ion", "n_att", "n_incomplete", "n_window"]
 
 
 class bz_tallies(C.Structure):
@@ -92,7 +92,7 @@ class bz_particles(C.Structure):
 
 class bz_particle_arrays(C.Structure):
     _fields_ = [(k, C.c_void_p) for k in ["x", "y", "z", "t", "sum_e", "sum_e2", "n_real", "n_null", "n_fail",
-                                          "n_ion", "n_att", "status"]]
+                                          "n_ion", "n_att", "status", "steps"]]
 
 
 BZ_NOALLOC_MAX_PARTICLES = 32768 * 512
@@ -307,7 +307,8 @@ def compile_info(gases, eps_cap_eV: float = 0.0, majorant_guard: float = -1.0) -
 def make_config(*, n_electrons: int, real_collisions: int, e_over_n_Td: float, b_T: float = 0.0,
                 b_angle_rad: float = 0.0, precision: int = 32, seed: int = 1901081400, eps0_mean_eV: float = 0.1,
                 trial_mode: int = BZ_TRIAL_LAZY, nu_trial: float = 0.0, t_end_s: float = 0.0, max_trials: int = 0,
-                id_offset: int = 0, attach_keep_state: bool = False, blocks_per_sm: int = 0) -> bz_swarm_config:
+                id_offset: int = 0, attach_keep_state: bool = False, blocks_per_sm: int = 0,
+                window_c: float = 0.0) -> bz_swarm_config:
     cfg = bz_swarm_config()
     lib().bz_config_defaults(C.byref(cfg))
     _check(lib().bz_set_fields(C.byref(cfg), float(e_over_n_Td), float(b_T), float(b_angle_rad)))
@@ -323,6 +324,7 @@ def make_config(*, n_electrons: int, real_collisions: int, e_over_n_Td: float, b
     cfg.id_offset = int(id_offset)
     cfg.attach_keep_state = int(bool(attach_keep_state))
     cfg.blocks_per_sm = int(blocks_per_sm)
+    cfg.window_c = float(window_c)
     return cfg
 
 

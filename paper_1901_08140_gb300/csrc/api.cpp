@@ -111,7 +111,9 @@ bz_status validate_config(const bz_swarm_config *cfg)
     if (cfg->real_collisions < 1) return fail(BZ_EINVAL, "real_collisions must be >= 1");
     if (!(cfg->e_over_n_Td >= 0.0) || !isfinite(cfg->e_over_n_Td)) return fail(BZ_EINVAL, "bad E/N");
     if (!(cfg->b_T >= 0.0) || !isfinite(cfg->b_T) || !isfinite(cfg->b_angle_rad)) return fail(BZ_EINVAL, "bad B");
-    if (cfg->trial_mode != BZ_TRIAL_LAZY && cfg->trial_mode != BZ_TRIAL_FIXED) return fail(BZ_EINVAL, "bad trial mode");
+    if (cfg->trial_mode != BZ_TRIAL_LAZY && cfg->trial_mode != BZ_TRIAL_FIXED && cfg->trial_mode != BZ_TRIAL_WINDOW)
+        return fail(BZ_EINVAL, "bad trial mode");
+    if (!(cfg->window_c >= 0.0) || !isfinite(cfg->window_c)) return fail(BZ_EINVAL, "window_c must be >= 0");
     if (cfg->trial_mode == BZ_TRIAL_FIXED && !(cfg->nu_trial > 0.0)) return fail(BZ_EINVAL, "fixed mode needs nu_trial > 0");
     if (!(cfg->eps0_mean_eV >= 0.0) || !isfinite(cfg->eps0_mean_eV)) return fail(BZ_EINVAL, "bad eps0_mean_eV");
     if (!(cfg->t_end_s >= 0.0) || !isfinite(cfg->t_end_s)) return fail(BZ_EINVAL, "bad t_end_s");
@@ -143,6 +145,9 @@ bz_status prepare_run(const bz_mixture *mix, const bz_swarm_config *cfg, bz::Run
     a->eps0_mean = cfg->eps0_mean_eV;
     a->t_end = cfg->t_end_s;
     a->max_trials = cfg->max_trials ? cfg->max_trials : 0x7FFFFFFFull;
+    a->window = cfg->trial_mode == BZ_TRIAL_WINDOW;
+    a->win_c = (float)(cfg->window_c > 0.0 ? cfg->window_c : 2.0);
+    a->nu_floor = 1e-9 * mix->cm.nu_max;
     a->f = make_fields(*cfg, mix->cm.n_total);
     return BZ_OK;
 }
@@ -364,6 +369,7 @@ bz_status bz_run_swarm(bz_ctx *ctx, const bz_mixture *mix, const bz_swarm_config
     t.x = s->p.x; t.y = s->p.y; t.z = s->p.z; t.t = s->p.t; t.se = s->p.se; t.se2 = s->p.se2;
     t.n_real = s->p.n_real; t.n_null = s->p.n_null; t.n_fail = s->p.n_fail; t.n_ion = s->p.n_ion;
     t.n_att = s->p.n_att; t.status = s->p.status;
+    t.steps = s->p.steps;
     t.n = n;
     t.id_offset = cfg->id_offset;
     t.part1 = (double *)(M + o_p1);

@@ -19,7 +19,7 @@ constexpr double kTownsend = 1e-21;           // V m^2
 constexpr double kLoschmidt = 2.686780111e25; // m^-3 (273.15 K, 101.325 kPa)
 
 constexpr int kGroups = 32;   // batch groups for standard errors (id mod 32)
-constexpr int kQ1 = 18;       // first-pass tally quantities
+constexpr int kQ1 = 19;       // first-pass tally quantities
 constexpr int kQ2 = 8;        // second-pass tally quantities
 
 // One interval [e_lo, e_hi) of the union energy grid: the density sum
@@ -51,15 +51,23 @@ struct alignas(2 * sizeof(R)) ChVal {
 };
 
 // Where each section of a compiled mixture sits in its device blob.  The
-// blob is [records | buckets | channel params | channel values]; the prefix
-// up to stage_tables (or stage_all) is copied into shared memory.
+// blob is [records | buckets | channel params | bin maxima | channel
+// values]; the prefix up to stage_tables (or stage_all) is copied into
+// shared memory.  Bin maxima: the maximum of nu(eps) over each of n_bins
+// log-uniform energy bins from 2^bin_lo to the last union point (windowed
+// trial frequency); nu_low is the maximum below the first bin.
 struct Layout {
     int32_t n_rec, n_buckets, n_ch, first_tail_rec;
     float log2_lo, inv_bw;
     uint32_t off_bucket, off_chp, off_chval;
-    uint32_t stage_tables;   // bytes of records + buckets + channel params
+    uint32_t stage_tables;   // bytes of records + buckets + channel params + bin maxima
     uint32_t stage_all;      // + channel values
     uint32_t total;
+    uint32_t off_bin;
+    int32_t n_bins;
+    float bin_lo, inv_binw;  // log2 energy of the first bin edge, bins per unit log2
+    double nu_low;           // max nu over [0, 2^bin_lo]
+    double g_top;            // last union point [eV]
 };
 
 struct CompiledMixture {

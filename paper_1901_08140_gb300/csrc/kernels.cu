@@ -122,8 +122,10 @@ struct Tab {
     const uint16_t *bucket;
     const ChParam<R> *chp;
     const ChVal<R> *chval;
-    int n_rec, n_buckets, n_ch, first_tail;
-    float log2_lo, inv_bw;
+    const R *binmax;
+    int n_rec, n_buckets, n_ch, first_tail, n_bins;
+    float log2_lo, inv_bw, bin_lo, inv_binw;
+    R nu_low, g_top, s_min;  // s_min: speed at the first bin edge [m/s]
 };
 
 template <typename R>
@@ -140,6 +142,13 @@ __device__ __forceinline__ Tab<R> make_tab(const uint8_t *smem, const uint8_t *b
     T.first_tail = L.first_tail_rec;
     T.log2_lo = L.log2_lo;
     T.inv_bw = L.inv_bw;
+    T.binmax = (const R *)(smem + L.off_bin);
+    T.n_bins = L.n_bins;
+    T.bin_lo = L.bin_lo;
+    T.inv_binw = L.inv_binw;
+    T.nu_low = (R)L.nu_low;
+    T.g_top = (R)L.g_top;
+    T.s_min = (R)sqrt(exp2((double)L.bin_lo) * 2.0 * kQe / kMe);
     return T;
 }
 
@@ -241,6 +250,7 @@ struct PState {
     R vr0, vr1, vr2;         // velocity right after the last real collision
     R T;                     // time since then
     R nu_p, inv_nu;          // trial frequency of this particle
+    R T_wend;                // windowed trial frequency: end of the current window (time since last real)
     R u0x, u0y, u0z, bux, buy, buz;  // B != 0: u0 = v_perp - vD and b x u0 at the last real collision
     Acc<R> x, y, z, t;       // position and time at the last real collision
     Acc<R> se, se2;          // energy sums before / after real collisions
@@ -324,8 +334,95 @@ __device__ __forceinline__ void displacement(const Fld<R> &F, const PState<R> &s
     }
 }
 
+// ---------------------------------------------------------------------------
+// Windowed local trial frequency.  Over a window of length dt that starts
+// with speed |v|, the speed stays within |v| +- g with g = a dt (B = 0) or
+// g = |a_par| dt + |u0| min(2, w dt) (B != 0: |u(t) - u(t0)| = 2|u0||sin(w(t-t0)/2)|),
+// so the maximum of nu over the energies [eps(|v|-g), eps(|v|+g)] -- read
+// from per-bin maxima of nu, one bin of margin on each side, plus a bound
+// of the power-law tails above the last union point -- is a trial frequency
+// that holds for the whole window.  A flight longer than the window stops
+// at its end and a new window starts there: by the memorylessness of the
+// exponential flight this samples the same process as a constant nu'
+// (Eqs. 3-4), with fewer null collisions.
+// ---------------------------------------------------------------------------
 template <typename R>
-__device__ __forceinline__ void init_particle(const RunArgs &P, const Fld<R> &F, PState<R> &s, uint64_t id)
+__device__ __forceinline__ int bin_of(const Tab<R> &T, R eps)
+{
+    float fb = (__log2f((float)eps) - T.bin_lo) * T.inv_binw;
+    fb = fminf(fmaxf(fb, -1.0f), (float)T.n_bins);
+    return (int)floorf(fb);  // -1 below the first bin, n_bins above the last
+}
+
+// Upper bound of nu over [a, b] with a >= g_top: every channel is on its
+// power-law tail there, each term is monotone, so it peaks at an end.
+template <typename R>
+__device__ __noinline__ R tail_bound(const Tab<R> &T, R a, R b)
+{
+    const R la = log_(a), lb = log_(b);
+    R S = 0;
+    for (int j = 0; j < T.n_ch; ++j) {
+        const ChParam<R> p = T.chp[j];
+        if (p.bits & 0x100) continue;
+        S += max_(exp_(p.tail_logc + p.tail_K * la), exp_(p.tail_logc + p.tail_K * lb));
+    }
+    return sqrt_(b * (R)(2.0 * kQe / kMe)) * S;
+}
+
+template <typename R>
+__device__ __forceinline__ R window_majorant(const Tab<R> &T, R e_lo, R e_hi)
+{
+    int bl = bin_of(T, e_lo) - 1, bh = bin_of(T, e_hi) + 1;
+    R m = 0;
+    if (bl < 0) {
+        m = T.nu_low;
+        bl = 0;
+    }
+    if (bh > T.n_bins - 1) bh = T.n_bins - 1;
+    for (int b = bl; b <= bh; ++b) m = max_(m, T.binmax[b]);
+    if (e_hi >= T.g_top) m = max_(m, tail_bound(T, max_(e_lo, T.g_top), e_hi));
+    return m;
+}
+
+// The window lasts win_c / nu of the current energy bin, and at most as long
+// as the speed bound needs to grow by a quarter of the speed (plus the speed
+// of the lowest table energy), so that a strong field cannot stretch the
+// energy range -- and the tails of the tables -- far beyond the electron's.
+template <typename R>
+__device__ __forceinline__ void new_window(const Tab<R> &T, const Fld<R> &F, const RunArgs &P, PState<R> &s, R speed,
+                                           R t0)
+{
+    const R eps = F.Ke * speed * speed;
+    const int b = bin_of(T, eps);
+    const R nub = max_((b < 0) ? T.nu_low : T.binmax[b < T.n_bins ? b : T.n_bins - 1], (R)P.nu_floor);
+    R dt = (R)P.win_c / nub;
+    R u0n = 0, rate;
+    if (F.has_b) {
+        u0n = sqrt_(s.u0x * s.u0x + s.u0y * s.u0y + s.u0z * s.u0z);
+        rate = fabs(F.a_par) + u0n * F.w;  // |dv/dt| <= |a_par| + |u0| w
+    } else {
+        rate = F.a;
+    }
+    const R grow_max = (R)0.25 * speed + T.s_min;
+    if (rate * dt > grow_max) dt = grow_max / rate;
+    R grow;
+    if (F.has_b) {
+        R wdt = F.w * dt;
+        if (wdt > (R)2) wdt = (R)2;
+        grow = fabs(F.a_par) * dt + u0n * wdt;
+    } else {
+        grow = F.a * dt;
+    }
+    const R s_hi = speed + grow, s_lo = max_((R)0, speed - grow);
+    const R m = max_(window_majorant(T, F.Ke * s_lo * s_lo, F.Ke * s_hi * s_hi) * (R)(1.0 + 1e-5), (R)P.nu_floor);
+    s.nu_p = m;
+    s.inv_nu = (R)1 / m;
+    s.T_wend = t0 + dt;
+}
+
+template <typename R>
+__device__ __forceinline__ void init_particle(const Tab<R> &T, const RunArgs &P, const Fld<R> &F, PState<R> &s,
+                                              uint64_t id)
 {
     s.id_lo = (uint32_t)id;
     s.id_hi = (uint32_t)(id >> 32);
@@ -353,6 +450,8 @@ __device__ __forceinline__ void init_particle(const RunArgs &P, const Fld<R> &F,
     s.status = ST_DONE;
     s.done = false;
     set_b_cache(F, s);
+    s.T_wend = (R)0;
+    if (P.window) new_window(T, F, P, s, sqrt_(s.vr0 * s.vr0 + s.vr1 * s.vr1 + s.vr2 * s.vr2), (R)0);
 }
 
 // One trial step.  Returns the decision (channel, DEC_NULL or DEC_FAIL);
@@ -370,6 +469,17 @@ __device__ __forceinline__ int trial(const Tab<R> &T, const Fld<R> &F, const Run
     if (P.t_end > 0.0 && s.t.value() + (double)Tn >= P.t_end) {
         Tn = (R)(P.t_end - s.t.value());  // TimeBulletLimiter: the flight stops at t_end
         cut = true;
+    }
+    if (P.window && !cut && Tn >= s.T_wend) {  // the flight outlasts the window: restart at its end
+        Tn = s.T_wend;
+        R v0, v1, v2, sn, omc;
+        velocity_at(F, s, Tn, v0, v1, v2, sn, omc);
+        const R vsq = v0 * v0 + v1 * v1 + v2 * v2;
+        s.T = Tn;
+        new_window(T, F, P, s, sqrt_(vsq), Tn);
+        eps_i = F.Ke * vsq;
+        eps_f = 0;
+        return DEC_WINDOW;
     }
     R v0, v1, v2, sn, omc;
     velocity_at(F, s, Tn, v0, v1, v2, sn, omc);
@@ -415,6 +525,7 @@ __device__ __forceinline__ int trial(const Tab<R> &T, const Fld<R> &F, const Run
             return DEC_FAIL;
         }
         s.T = 0;  // fail (Sec. 6): back to the last real collision
+        if (P.window) new_window(T, F, P, s, sqrt_(s.vr0 * s.vr0 + s.vr1 * s.vr1 + s.vr2 * s.vr2), (R)0);
         s.nu_p = max_(s.nu_p, (R)1.25 * nu);
         s.inv_nu = (R)1 / s.nu_p;
         return DEC_FAIL;
@@ -508,6 +619,7 @@ __device__ __forceinline__ int trial(const Tab<R> &T, const Fld<R> &F, const Run
     }
     set_b_cache(F, s);
     eps_f = ratio * eps;
+    if (P.window) new_window(T, F, P, s, sqrt_(s.vr0 * s.vr0 + s.vr1 * s.vr1 + s.vr2 * s.vr2), (R)0);
     s.se.add(eps);
     s.se2.add(eps_f);
     if (++s.n_real >= P.I) s.done = true;
@@ -622,7 +734,7 @@ __global__ void __launch_bounds__(kBlock, BZ_SWARM_MIN_BLOCKS) swarm_kernel(cons
             if (!have) {
                 const unsigned long long idx = base + __popc(need & ((1u << lane) - 1u));
                 if (idx < P.n) {
-                    init_particle<R>(P, F, s, P.id_offset + idx);
+                    init_particle<R>(T, P, F, s, P.id_offset + idx);
                     slot = idx;
                     have = true;
                 }
@@ -678,6 +790,8 @@ __global__ void __launch_bounds__(kBlock) replay_kernel(const ReplayArgs A)
         s.status = ST_DONE;
         s.done = false;
         set_b_cache(F, s);
+        s.T_wend = (R)0;
+        if (P.window) new_window(T, F, P, s, sqrt_(s.vr0 * s.vr0 + s.vr1 * s.vr1 + s.vr2 * s.vr2), (R)0);
         R ei, ef;
         const int dec = trial<R, CH_SMEM>(T, F, P, s, ei, ef);
         // state at the trial point: last real collision advanced by s.T
@@ -765,6 +879,7 @@ __global__ void __launch_bounds__(kTallyBlock) tally_pass1(const TallyArgs A)
         acc[14] += (double)A.n_fail[i];
         acc[15] += G;
         acc[16] += D;
+        acc[18] += A.steps ? (double)A.steps[i] : 0.0;
     }
     block_group_reduce<kQ1>(acc, A.part1 + (size_t)blockIdx.x * kGroups * kQ1, A.id_offset);
 }
@@ -904,6 +1019,8 @@ __global__ void tally_final(const TallyArgs A)
     o.n_ion = (uint64_t)(tot[15] + 0.5);
     o.n_att = (uint64_t)(tot[16] + 0.5);
     o.n_incomplete = (uint64_t)(tot[17] + 0.5);
+    const double other = tot[18] - trials;  // steps that were neither real, null nor fail: window restarts
+    o.n_window = other > 0.5 ? (uint64_t)(other + 0.5) : 0;
     o.error_flags = (int32_t)*A.err;
     // batch-mean standard errors
     bool has[kGroups];

@@ -9,7 +9,7 @@
 namespace bz {
 
 enum { ST_DONE = 0, ST_TIME = 1, ST_STEPS = 2, ST_TRIAL = 3, ST_ERROR = 4 };
-enum { DEC_FAIL = -2, DEC_NULL = -1 };
+enum { DEC_WINDOW = -3, DEC_FAIL = -2, DEC_NULL = -1 };
 
 // Uniform static fields in the force frame (force on the electron along +z).
 struct Fields {
@@ -40,6 +40,9 @@ struct RunArgs {
     double eps0_mean;        // Maxwellian start, mean energy [eV]
     double t_end;            // > 0: time limit [s]
     uint64_t max_trials;
+    int32_t window;          // windowed local trial frequency
+    float win_c;             // window length in units of 1/nu of the current energy bin
+    double nu_floor;         // lower bound of any trial frequency [1/s]
     Fields f;
     unsigned long long *counter;  // next particle slot
     uint32_t *err;
@@ -60,6 +63,7 @@ struct ReplayArgs {
 struct TallyArgs {
     const double *x, *y, *z, *t, *se, *se2;
     const uint32_t *n_real, *n_null, *n_fail, *n_ion, *n_att, *status;
+    const uint32_t *steps;   // may be null (no window-restart count)
     uint64_t n, id_offset;
     double *part1, *part2;   // [blocks][kGroups][kQ1 | kQ2] scratch
     double *gsum;            // [kGroups][kQ1 + kQ2] + 8 summary values, scratch

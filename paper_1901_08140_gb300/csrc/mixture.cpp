@@ -80,19 +80,27 @@ double record_density(const std::vector<Chan> &ch, double a, double b, double ep
     return S;
 }
 
+struct Bins {
+    std::vector<double> max;
+    float lo, inv_w;
+    double nu_low;
+};
+
 template <typename R>
 void emit(const std::vector<Chan> &ch, const std::vector<double> &g, const std::vector<double> &Slo,
           const std::vector<double> &Ssl, const std::vector<std::vector<double>> &cv,
           const std::vector<std::vector<double>> &cs, const std::vector<uint16_t> &bucket,
-          const std::vector<ChParam<double>> &cp, int first_tail, float log2_lo, float inv_bw,
+          const std::vector<ChParam<double>> &cp, int first_tail, float log2_lo, float inv_bw, const Bins &bins,
           std::vector<uint8_t> *blob, Layout *lay)
 {
     const int n_rec = (int)Slo.size(), n_ch = (int)ch.size(), nb = (int)bucket.size();
+    const int n_bins = (int)bins.max.size();
     auto pad16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
     size_t off_rec = 0;
     size_t off_bucket = pad16(off_rec + sizeof(Rec<R>) * n_rec);
     size_t off_chp = pad16(off_bucket + sizeof(uint16_t) * nb);
-    size_t off_chval = pad16(off_chp + sizeof(ChParam<R>) * n_ch);
+    size_t off_bin = pad16(off_chp + sizeof(ChParam<R>) * n_ch);
+    size_t off_chval = pad16(off_bin + sizeof(R) * n_bins);
     size_t total = pad16(off_chval + sizeof(ChVal<R>) * (size_t)n_rec * n_ch);
     blob->assign(total, 0);
     Rec<R> *rec = (Rec<R> *)(blob->data() + off_rec);
@@ -116,6 +124,8 @@ void emit(const std::vector<Chan> &ch, const std::vector<double> &g, const std::
         p[j].tail_K = (R)cp[j].tail_K;
         p[j].bits = cp[j].bits;
     }
+    R *bm = (R *)(blob->data() + off_bin);
+    for (int b = 0; b < n_bins; ++b) bm[b] = (R)bins.max[b];
     ChVal<R> *v = (ChVal<R> *)(blob->data() + off_chval);
     for (int i = 0; i < n_rec; ++i)
         for (int j = 0; j < n_ch; ++j) {
@@ -134,6 +144,12 @@ void emit(const std::vector<Chan> &ch, const std::vector<double> &g, const std::
     lay->stage_tables = (uint32_t)off_chval;
     lay->stage_all = (uint32_t)total;
     lay->total = (uint32_t)total;
+    lay->off_bin = (uint32_t)off_bin;
+    lay->n_bins = n_bins;
+    lay->bin_lo = bins.lo;
+    lay->inv_binw = bins.inv_w;
+    lay->nu_low = bins.nu_low;
+    lay->g_top = g.back();
 }
 
 bool finite(double x) { return std::isfinite(x); }
@@ -294,8 +310,72 @@ bz_status compile_mixture(const bz_gas *gases, int32_t n_gases, const bz_mixture
     }
     float log2_lo = (float)L0, inv_bw = (w > 0.0) ? (float)(1.0 / w) : 0.0f;
 
-    emit<float>(ch, g, Slo, Ssl, cv, cs, bucket, cp, first_tail, log2_lo, inv_bw, &out->blob32, &out->lay32);
-    emit<double>(ch, g, Slo, Ssl, cv, cs, bucket, cp, first_tail, log2_lo, inv_bw, &out->blob64, &out->lay64);
+    // Maximum of nu over each log-uniform energy bin (32 per decade) between
+    // the first positive union point and the last one, exact per record:
+    // linear records peak at an end or at eps* = -a/(3b); records with a
+    // tail are sampled densely and refined.  A relative margin of 1e-9 covers
+    // the refinement.
+    auto record_max = [&](int i, double a, double b) {
+        if (b <= a) return speed_of(b) * (i == 0 ? Slo[0] : 0.0);
+        double rlo = (i == 0) ? 0.0 : g[i - 1];
+        if (i < first_tail) {
+            double B = Ssl[i], A = Slo[i] - B * rlo, m = std::max(speed_of(a) * (A + B * a), speed_of(b) * (A + B * b));
+            if (B != 0.0) {
+                double x = -A / (3.0 * B);
+                if (x > a && x < b) m = std::max(m, speed_of(x) * (A + B * x));
+            }
+            return m;
+        }
+        double rhi = (i < n_rec - 1) ? g[i] : b;
+        auto f = [&](double x) { return speed_of(x) * record_density(ch, rlo, rhi, x); };
+        const int NS = 256;
+        int arg = 0;
+        double vm = -1.0;
+        for (int k = 0; k <= NS; ++k) {
+            double x = a + (b - a) * k / NS, v = f(x);
+            if (v > vm) { vm = v; arg = k; }
+        }
+        double lo2 = a + (b - a) * std::max(arg - 1, 0) / NS, hi2 = a + (b - a) * std::min(arg + 1, NS) / NS;
+        const double gr = 0.6180339887498949;
+        double x1 = hi2 - gr * (hi2 - lo2), x2 = lo2 + gr * (hi2 - lo2), f1 = f(x1), f2 = f(x2);
+        for (int it = 0; it < 100 && (hi2 - lo2) > 1e-13 * hi2; ++it) {
+            if (f1 < f2) { lo2 = x1; x1 = x2; f1 = f2; x2 = lo2 + gr * (hi2 - lo2); f2 = f(x2); }
+            else { hi2 = x2; x2 = x1; f2 = f1; x1 = hi2 - gr * (hi2 - lo2); f1 = f(x1); }
+        }
+        return std::max(vm, std::max(f1, f2));
+    };
+    // max of nu over [a, b]: every record that meets the interval
+    auto range_max = [&](double a, double b) {
+        int i = (int)(std::upper_bound(g.begin(), g.end(), a) - g.begin());  // record holding a
+        double m = 0.0;
+        for (; i < n_rec; ++i) {
+            double rlo = (i == 0) ? 0.0 : g[i - 1];
+            double rhi = (i < n_rec - 1) ? g[i] : std::numeric_limits<double>::infinity();
+            if (rlo > b) break;
+            double x0 = std::max(a, rlo), x1 = std::min(b, rhi);
+            if (i == 0) m = std::max(m, speed_of(x1) * Slo[0]);
+            else m = std::max(m, record_max(i, x0, x1));
+        }
+        return m * (1.0 + 1e-9);
+    };
+    Bins bins;
+    {
+        double Lb0 = L0, Lb1 = log2(g[P - 1] > 0.0 ? g[P - 1] : 1.0);
+        int nbins = (Lb1 > Lb0) ? (int)ceil((Lb1 - Lb0) / log2(10.0) * 32.0) : 1;
+        nbins = std::min(std::max(nbins, 1), 4096);
+        double bw = (Lb1 > Lb0) ? (Lb1 - Lb0) / nbins : 0.0;
+        bins.max.resize(nbins);
+        for (int b = 0; b < nbins; ++b) {
+            double a = exp2(Lb0 + b * bw), e = (b == nbins - 1) ? g[P - 1] : exp2(Lb0 + (b + 1) * bw);
+            bins.max[b] = range_max(a, e);
+        }
+        bins.lo = (float)Lb0;
+        bins.inv_w = (bw > 0.0) ? (float)(1.0 / bw) : 0.0f;
+        bins.nu_low = range_max(0.0, exp2(Lb0));
+    }
+
+    emit<float>(ch, g, Slo, Ssl, cv, cs, bucket, cp, first_tail, log2_lo, inv_bw, bins, &out->blob32, &out->lay32);
+    emit<double>(ch, g, Slo, Ssl, cv, cs, bucket, cp, first_tail, log2_lo, inv_bw, bins, &out->blob64, &out->lay64);
     out->n_total = n_total;
     out->nu_max = best;
     out->nu_trial = best * (1.0 + guard);

@@ -26,7 +26,7 @@ namespace {
 constexpr size_t kPart1 = (size_t)BZ_NOALLOC_MAX_BLOCKS * bz::kGroups * bz::kQ1;
 constexpr size_t kPart2 = (size_t)BZ_NOALLOC_MAX_BLOCKS * bz::kGroups * bz::kQ2;
 constexpr size_t kGsum = (size_t)bz::kGroups * (bz::kQ1 + bz::kQ2) + 8;
-static_assert(bz::kQ1 + bz::kQ2 == 26, "scratch size formula in bz.h assumes 26 quantities");
+static_assert(bz::kQ1 + bz::kQ2 == 27, "scratch size formula in bz.h assumes 27 quantities");
 static_assert(8 * (kPart1 + kPart2 + kGsum) + 256 <= BZ_NOALLOC_SCRATCH_BYTES, "scratch too small");
 
 static __device__ __align__(256) unsigned char g_scratch[BZ_NOALLOC_SCRATCH_BYTES];
@@ -82,6 +82,7 @@ extern "C" bz_status bz_reduce_tallies_noalloc(const bz_particle_arrays *in, uin
     t.x = in->x; t.y = in->y; t.z = in->z; t.t = in->t; t.se = in->sum_e; t.se2 = in->sum_e2;
     t.n_real = in->n_real; t.n_null = in->n_null; t.n_fail = in->n_fail; t.n_ion = in->n_ion;
     t.n_att = in->n_att; t.status = in->status;
+    t.steps = in->steps;
     t.n = n;
     t.id_offset = id_offset;
     t.blocks = (int)((n + BZ_NOALLOC_SPAN - 1) / BZ_NOALLOC_SPAN);

@@ -1,0 +1,134 @@
+"""Windowed local trial frequency (BZ_TRIAL_WINDOW) against the constant
+one (Sec. 6.2) and against the oracle.
+
+The windowed majorant bounds nu over every energy the electron can reach in
+the window, so both modes sample the same collision process (Eqs. 3-4):
+swarm values must agree within 3 combined standard errors and 0.5 %, the
+bound must never be exceeded (no fails), and the Maxwell-model closed forms
+must hold.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from oracle import tallies as OT
+from paper_1901_08140_gb300 import bz
+from paper_1901_08140_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+QE = 1.602176634e-19
+ME = 9.1093837015e-31
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1901_08140_gb300 import build as B
+    B.build()
+    c = bz.Context(0)
+    yield c
+    c.close()
+
+
+def _run(ctx, mix, **kw):
+    sw = bz.run_swarm(ctx, mix, bz.make_config(**kw))
+    t = sw.tallies()
+    sw.close()
+    return t
+
+
+def _agree(a, b, keys, rel=0.005):
+    for k in keys:
+        se = math.hypot(a[k + "_se"], b[k + "_se"])
+        assert abs(a[k] - b[k]) <= 3 * se, (k, a[k], b[k], se)
+        if k in ("W", "eps"):
+            assert abs(a[k] / b[k] - 1) < rel, (k, a[k], b[k])
+
+
+@pytest.mark.parametrize("point", [0, 8, 20])
+def test_window_matches_constant_trial_frequency_on_the_argon_sweep(ctx, point):
+    spec = W.argon_sweep()[point]
+    mix = bz.Mixture(ctx, spec.gases)
+    kw = dict(n_electrons=spec.n_electrons, real_collisions=spec.real_collisions, e_over_n_Td=spec.e_over_n_Td,
+              seed=spec.seed)
+    lazy = _run(ctx, mix, **kw)
+    assert lazy["n_fail"] == 0   # the constant bound held: no revert
+    win = _run(ctx, mix, trial_mode=bz.BZ_TRIAL_WINDOW, **kw)
+    _agree(win, lazy, ["W", "eps", "eps_after", "D_L", "D_T", "alpha"])
+    assert win["n_fail"] <= 1e-7 * win["n_real"]
+    assert win["efficiency"] > lazy["efficiency"]
+    assert win["error_flags"] == 0 and win["n_real"] == lazy["n_real"]
+
+
+def test_window_matches_constant_trial_frequency_at_1000_Td(ctx):
+    """At 1000 Td electrons pass the 100 eV table top; the constant trial
+    frequency is then taken over [0, 3000 eV] so that it is never exceeded
+    (no revert), and both modes must agree."""
+    spec = W.argon_sweep()[31]
+    kw = dict(n_electrons=200000, real_collisions=1000, e_over_n_Td=spec.e_over_n_Td, seed=spec.seed)
+    lazy = _run(ctx, bz.Mixture(ctx, spec.gases, eps_cap_eV=3000.0), **kw)
+    assert lazy["n_fail"] == 0
+    win = _run(ctx, bz.Mixture(ctx, spec.gases), trial_mode=bz.BZ_TRIAL_WINDOW, **kw)
+    _agree(win, lazy, ["W", "eps", "D_L", "D_T", "alpha"])
+    assert win["n_fail"] == 0
+
+
+@pytest.mark.parametrize("case", ["arco2_B1T", "batched_B_oblique"])
+def test_window_matches_constant_trial_frequency_with_magnetic_field(ctx, case):
+    if case == "arco2_B1T":
+        spec = W.ar_co2_swarm(n_electrons=1_000_000, real_collisions=500)
+    else:
+        spec = W.batched_swarms(count=8)[7]
+        spec.n_electrons, spec.real_collisions = 500_000, 500
+    mix = bz.Mixture(ctx, spec.gases)
+    kw = dict(n_electrons=spec.n_electrons, real_collisions=spec.real_collisions, e_over_n_Td=spec.e_over_n_Td,
+              b_T=spec.b_T, b_angle_rad=spec.b_angle_rad, seed=spec.seed)
+    lazy = _run(ctx, mix, **kw)
+    win = _run(ctx, mix, trial_mode=bz.BZ_TRIAL_WINDOW, **kw)
+    _agree(win, lazy, ["W", "eps", "D_L", "D_T"])
+    for k in ("Wx", "Wy"):
+        assert abs(win[k] - lazy[k]) <= 0.01 * abs(lazy["W"]) + 0.01 * abs(lazy[k])
+    assert win["n_fail"] <= 1e-7 * win["n_real"]
+
+
+def test_window_against_the_oracle(ctx):
+    spec = W.ar_co2_swarm(n_electrons=1_000_000, real_collisions=200)
+    mix = bz.Mixture(ctx, spec.gases)
+    win = _run(ctx, mix, n_electrons=spec.n_electrons, real_collisions=spec.real_collisions,
+               e_over_n_Td=spec.e_over_n_Td, b_T=spec.b_T, b_angle_rad=spec.b_angle_rad, seed=spec.seed,
+               trial_mode=bz.BZ_TRIAL_WINDOW)
+    m = O.Mixture(spec.gases)
+    po = O.run_swarm(m, e_over_n_Td=spec.e_over_n_Td, b_T=spec.b_T, b_angle_rad=spec.b_angle_rad,
+                     real_collisions=spec.real_collisions, n=20000, seed=spec.seed + 1, threads=O.cpu_count())
+    to = OT.swarm_tallies(po, spec.e_over_n_Td, m.n_total)
+    for k in ("W", "eps", "D_L", "D_T"):
+        se = math.hypot(win[k + "_se"], to[k + "_se"])
+        assert abs(win[k] - to[k]) <= 3 * se, (k, win[k], to[k], se)
+
+
+def test_window_maxwell_closed_forms_fp64(ctx):
+    from test_oracle_pins import _maxwell_closed_forms
+    spec = W.maxwell_swarm(n_electrons=300000, real_collisions=1000)
+    gas = spec.gases[0]
+    mix = bz.Mixture(ctx, spec.gases)
+    t = _run(ctx, mix, n_electrons=spec.n_electrons, real_collisions=spec.real_collisions,
+             e_over_n_Td=spec.e_over_n_Td, seed=spec.seed, precision=64, trial_mode=bz.BZ_TRIAL_WINDOW)
+    E = spec.e_over_n_Td * 1e-21 * gas.number_density_m3
+    vd = QE * E / (ME * 1e12)
+    kappa = 2 * ME * gas.mass_kg / (ME + gas.mass_kg) ** 2
+    mean_eps, DT, DL = _maxwell_closed_forms(1000, 0.1, 1e12, kappa, vd)
+    assert abs(t["W_flux"] / vd - 1) < 0.005
+    assert abs(t["eps"] - mean_eps) < 3 * t["eps_se"]
+    assert t["n_fail"] == 0
+
+
+def test_window_restarts_are_counted_and_bounded(ctx):
+    spec = W.argon_sweep()[0]
+    mix = bz.Mixture(ctx, spec.gases)
+    t = _run(ctx, mix, n_electrons=100000, real_collisions=200, e_over_n_Td=spec.e_over_n_Td, seed=3,
+             trial_mode=bz.BZ_TRIAL_WINDOW)
+    assert t["n_window"] > 0
+    # window = 2 / nu_bin, so a flight outlasts it with probability <= e^-2 per window
+    assert t["n_window"] < 0.25 * (t["n_real"] + t["n_null"])
