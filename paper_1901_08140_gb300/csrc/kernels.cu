@@ -31,7 +31,7 @@ namespace {
 
 constexpr int kBlock = 256;
 #ifndef BZ_SWARM_MIN_BLOCKS
-#define BZ_SWARM_MIN_BLOCKS 1  // resident blocks per SM the register allocation must allow
+#define BZ_SWARM_MIN_BLOCKS 4  // FP32: resident blocks per SM the register allocation must allow
 #endif
 constexpr uint32_t kStageChunk = 32768;
 constexpr uint32_t kWaitLimit = 1u << 24;
@@ -454,15 +454,18 @@ __device__ __forceinline__ void init_particle(const Tab<R> &T, const RunArgs &P,
     if (P.window) new_window(T, F, P, s, sqrt_(s.vr0 * s.vr0 + s.vr1 * s.vr1 + s.vr2 * s.vr2), (R)0);
 }
 
-// One trial step.  Returns the decision (channel, DEC_NULL or DEC_FAIL);
-// eps_i / eps_f receive the energy before and after a real collision.
+// One trial step.  Returns the decision (channel, DEC_NULL, DEC_FAIL or
+// DEC_WINDOW); eps_i / eps_f receive the energy before and after a real
+// collision.  The velocity at the end of the flight is computed once for
+// every lane, and every lane that needs a new trial-frequency window (window
+// end, real collision, fail) computes it at one common point after the
+// branches, so divergent lanes do not repeat that code.
 template <typename R, bool CH_SMEM>
 __device__ __forceinline__ int trial(const Tab<R> &T, const Fld<R> &F, const RunArgs &P, PState<R> &s, R &eps_i,
                                      R &eps_f)
 {
     const uint32_t step = s.k++;
     const uint4 w = philox(s.id_lo, s.id_hi, step, 0u, P.key0, P.key1);
-    const R u1 = uni<R>(w.y), u2 = uni<R>(w.z), u3 = uni<R>(w.w);
     // Eq. (3): the draw stands for 1 - R
     R Tn = s.T - log_(uni<R>(w.x)) * s.inv_nu;
     bool cut = false;
@@ -470,19 +473,14 @@ __device__ __forceinline__ int trial(const Tab<R> &T, const Fld<R> &F, const Run
         Tn = (R)(P.t_end - s.t.value());  // TimeBulletLimiter: the flight stops at t_end
         cut = true;
     }
-    if (P.window && !cut && Tn >= s.T_wend) {  // the flight outlasts the window: restart at its end
-        Tn = s.T_wend;
-        R v0, v1, v2, sn, omc;
-        velocity_at(F, s, Tn, v0, v1, v2, sn, omc);
-        const R vsq = v0 * v0 + v1 * v1 + v2 * v2;
-        s.T = Tn;
-        new_window(T, F, P, s, sqrt_(vsq), Tn);
-        eps_i = F.Ke * vsq;
-        eps_f = 0;
-        return DEC_WINDOW;
-    }
+    const bool restart = P.window && !cut && Tn >= s.T_wend;  // the flight outlasts the window
+    if (restart) Tn = s.T_wend;
     R v0, v1, v2, sn, omc;
     velocity_at(F, s, Tn, v0, v1, v2, sn, omc);
+    const R vsq = v0 * v0 + v1 * v1 + v2 * v2;
+    const R eps = F.Ke * vsq;
+    eps_i = eps;
+    eps_f = 0;
     if (cut) {
         R dx, dy, dz;
         displacement(F, s, Tn, sn, omc, dx, dy, dz);
@@ -496,134 +494,149 @@ __device__ __forceinline__ int trial(const Tab<R> &T, const Fld<R> &F, const Run
         s.T = 0;
         s.status = ST_TIME;
         s.done = true;
-        eps_i = F.Ke * (v0 * v0 + v1 * v1 + v2 * v2);
-        eps_f = 0;
         return DEC_NULL;
     }
-    const R vsq = v0 * v0 + v1 * v1 + v2 * v2;
-    const R eps = F.Ke * vsq;
-    int ri;
-    R elo;
-    const R S = density(T, eps, ri, elo);
-    const R inv_sp = vsq > (R)0 ? rsqrt_(vsq) : (R)0;
-    const R sp = vsq * inv_sp;
-    const R nu = sp * S;
-    eps_i = eps;
-    eps_f = 0;
-    if (!(nu <= s.nu_p)) {
-        if (!(nu == nu)) {  // non-finite state: stop this particle, flag it
-            atomicOr(P.err, BZ_ERR_NONFINITE);
-            s.status = ST_ERROR;
-            s.done = true;
-            return DEC_FAIL;
+    int dec;
+    bool need_window = false;
+    R wspeed = 0, wt0 = 0, nu_fail = 0;
+    if (restart) {
+        s.T = Tn;  // a new window starts where the old one ended
+        need_window = true;
+        wspeed = sqrt_(vsq);
+        wt0 = Tn;
+        dec = DEC_WINDOW;
+    } else {
+        int ri;
+        R elo;
+        const R S = density(T, eps, ri, elo);
+        const R inv_sp = vsq > (R)0 ? rsqrt_(vsq) : (R)0;
+        const R sp = vsq * inv_sp;
+        const R nu = sp * S;
+        const R r = uni<R>(w.y) * s.nu_p;
+        if (!(nu <= s.nu_p)) {
+            if (!(nu == nu)) {  // non-finite state: stop this particle, flag it
+                atomicOr(P.err, BZ_ERR_NONFINITE);
+                s.status = ST_ERROR;
+                s.done = true;
+                return DEC_FAIL;
+            }
+            ++s.n_fail;
+            if (P.fixed) {  // FixedTrialFrequency (Sec. 6.1): an error
+                atomicOr(P.err, BZ_ERR_TRIAL);
+                s.status = ST_TRIAL;
+                s.done = true;
+                return DEC_FAIL;
+            }
+            s.T = 0;  // fail (Sec. 6): back to the last real collision
+            nu_fail = nu;
+            need_window = P.window;
+            wspeed = sqrt_(s.vr0 * s.vr0 + s.vr1 * s.vr1 + s.vr2 * s.vr2);
+            dec = DEC_FAIL;
+        } else if (r > nu) {  // Eq. (4): null collision
+            ++s.n_null;
+            s.T = Tn;
+            dec = DEC_NULL;
+        } else {
+            // ---- real collision ----
+            const int c = select_channel<R, CH_SMEM>(T, ri, elo, eps, r * inv_sp);
+            {
+                R dx, dy, dz;
+                displacement(F, s, Tn, sn, omc, dx, dy, dz);
+                s.x.add(dx);
+                s.y.add(dy);
+                s.z.add(dz);
+                s.t.add(Tn);
+                s.T = 0;
+            }
+            const R u2 = uni<R>(w.z);
+            const ChParam<R> p = T.chp[c];
+            const int kind = p.bits & 15;
+            R ct;
+            if ((p.bits >> 4) & 15) {  // Eq. (5), eps in Hartree
+                ct = (R)1 - (R)2 * u2 / ((R)1 + (R)8 * (eps * (R)(1.0 / kHartreeEv)) * ((R)1 - u2));
+            } else {
+                ct = (R)1 - (R)2 * u2;
+            }
+            R ratio;
+            bool rotate = true;
+            if (kind == BZ_ELASTIC) {
+                ratio = (R)1 - p.kappa2 * ((R)1 - ct);  // Eq. (8)
+            } else if (kind == BZ_ATTACHMENT) {
+                ++s.n_att;
+                if (P.attach_keep) {
+                    ratio = 1;
+                    rotate = false;
+                } else {
+                    ratio = 0;  // plastic collision: the electron stops
+                }
+            } else {
+                const R x = p.eps_k / eps;  // Eq. (9), radicand clamped at 0
+                const R rad = max_((R)0, (R)1 - p.minv * x);
+                ratio = max_((R)0, (R)1 - p.mfrac * x + p.kappa2 * (sqrt_(rad) * ct - (R)1));
+                if (kind == BZ_IONIZATION) {
+                    const uint4 w2 = philox(s.id_lo, s.id_hi, step, 1u, P.key0, P.key1);
+                    ratio *= (R)1 - uni<R>(w2.x);  // the secondary takes the rest
+                    ++s.n_ion;
+                }
+            }
+            const R nsp = sp * sqrt_(ratio);
+            if (rotate) {
+                R d0 = v0 * inv_sp, d1 = v1 * inv_sp, d2 = v2 * inv_sp;
+                if (!(vsq > (R)0)) {
+                    d0 = 0;
+                    d1 = 0;
+                    d2 = 1;
+                }
+                // azimuth origin e1 = (a x d)/|a x d|, a the axis of the smallest |d_i|
+                const R ax = fabs(d0), ay = fabs(d1), az = fabs(d2);
+                R e0, e1, e2;
+                if (ax <= ay && ax <= az) {
+                    e0 = 0;
+                    e1 = -d2;
+                    e2 = d1;
+                } else if (ay <= az) {
+                    e0 = d2;
+                    e1 = 0;
+                    e2 = -d0;
+                } else {
+                    e0 = -d1;
+                    e1 = d0;
+                    e2 = 0;
+                }
+                const R ie = rsqrt_(e0 * e0 + e1 * e1 + e2 * e2);
+                e0 *= ie;
+                e1 *= ie;
+                e2 *= ie;
+                const R f0 = d1 * e2 - d2 * e1, f1 = d2 * e0 - d0 * e2, f2 = d0 * e1 - d1 * e0;  // d x e1
+                const R st = sqrt_(max_((R)0, (R)1 - ct * ct));
+                R sp3, cp3;
+                sincospi_((R)2 * uni<R>(w.w), &sp3, &cp3);
+                s.vr0 = nsp * (ct * d0 + st * (cp3 * e0 + sp3 * f0));
+                s.vr1 = nsp * (ct * d1 + st * (cp3 * e1 + sp3 * f1));
+                s.vr2 = nsp * (ct * d2 + st * (cp3 * e2 + sp3 * f2));
+            } else {
+                s.vr0 = v0;
+                s.vr1 = v1;
+                s.vr2 = v2;
+            }
+            set_b_cache(F, s);
+            eps_f = ratio * eps;
+            s.se.add(eps);
+            s.se2.add(eps_f);
+            if (++s.n_real >= P.I) s.done = true;
+            need_window = P.window;
+            wspeed = rotate ? nsp : sp;
+            dec = c;
         }
-        ++s.n_fail;
-        if (P.fixed) {  // FixedTrialFrequency (Sec. 6.1): an error
-            atomicOr(P.err, BZ_ERR_TRIAL);
-            s.status = ST_TRIAL;
-            s.done = true;
-            return DEC_FAIL;
-        }
-        s.T = 0;  // fail (Sec. 6): back to the last real collision
-        if (P.window) new_window(T, F, P, s, sqrt_(s.vr0 * s.vr0 + s.vr1 * s.vr1 + s.vr2 * s.vr2), (R)0);
-        s.nu_p = max_(s.nu_p, (R)1.25 * nu);
+    }
+    if (need_window) {
+        new_window(T, F, P, s, wspeed, wt0);
+    }
+    if (dec == DEC_FAIL) {
+        s.nu_p = max_(s.nu_p, (R)1.25 * nu_fail);
         s.inv_nu = (R)1 / s.nu_p;
-        return DEC_FAIL;
     }
-    const R r = u1 * s.nu_p;
-    if (r > nu) {  // Eq. (4): null collision
-        ++s.n_null;
-        s.T = Tn;
-        return DEC_NULL;
-    }
-    // ---- real collision ----
-    const int c = select_channel<R, CH_SMEM>(T, ri, elo, eps, r * inv_sp);
-    {
-        R dx, dy, dz;
-        displacement(F, s, Tn, sn, omc, dx, dy, dz);
-        s.x.add(dx);
-        s.y.add(dy);
-        s.z.add(dz);
-        s.t.add(Tn);
-        s.T = 0;
-    }
-    const ChParam<R> p = T.chp[c];
-    const int kind = p.bits & 15;
-    R ct;
-    if ((p.bits >> 4) & 15) {  // Eq. (5), eps in Hartree
-        ct = (R)1 - (R)2 * u2 / ((R)1 + (R)8 * (eps * (R)(1.0 / kHartreeEv)) * ((R)1 - u2));
-    } else {
-        ct = (R)1 - (R)2 * u2;
-    }
-    R ratio;
-    bool rotate = true;
-    if (kind == BZ_ELASTIC) {
-        ratio = (R)1 - p.kappa2 * ((R)1 - ct);  // Eq. (8)
-    } else if (kind == BZ_ATTACHMENT) {
-        ++s.n_att;
-        if (P.attach_keep) {
-            ratio = 1;
-            rotate = false;
-        } else {
-            ratio = 0;  // plastic collision: the electron stops
-        }
-    } else {
-        const R x = p.eps_k / eps;  // Eq. (9), radicand clamped at 0
-        const R rad = max_((R)0, (R)1 - p.minv * x);
-        ratio = max_((R)0, (R)1 - p.mfrac * x + p.kappa2 * (sqrt_(rad) * ct - (R)1));
-        if (kind == BZ_IONIZATION) {
-            const uint4 w2 = philox(s.id_lo, s.id_hi, step, 1u, P.key0, P.key1);
-            ratio *= (R)1 - uni<R>(w2.x);  // the secondary takes the rest
-            ++s.n_ion;
-        }
-    }
-    if (rotate) {
-        R d0 = v0 * inv_sp, d1 = v1 * inv_sp, d2 = v2 * inv_sp;
-        if (!(vsq > (R)0)) {
-            d0 = 0;
-            d1 = 0;
-            d2 = 1;
-        }
-        // azimuth origin e1 = (a x d)/|a x d|, a the axis of the smallest |d_i|
-        const R ax = fabs(d0), ay = fabs(d1), az = fabs(d2);
-        R e0, e1, e2;
-        if (ax <= ay && ax <= az) {
-            e0 = 0;
-            e1 = -d2;
-            e2 = d1;
-        } else if (ay <= az) {
-            e0 = d2;
-            e1 = 0;
-            e2 = -d0;
-        } else {
-            e0 = -d1;
-            e1 = d0;
-            e2 = 0;
-        }
-        const R ie = rsqrt_(e0 * e0 + e1 * e1 + e2 * e2);
-        e0 *= ie;
-        e1 *= ie;
-        e2 *= ie;
-        const R f0 = d1 * e2 - d2 * e1, f1 = d2 * e0 - d0 * e2, f2 = d0 * e1 - d1 * e0;  // d x e1
-        const R st = sqrt_(max_((R)0, (R)1 - ct * ct));
-        R sp3, cp3;
-        sincospi_((R)2 * u3, &sp3, &cp3);
-        const R nsp = sp * sqrt_(ratio);
-        s.vr0 = nsp * (ct * d0 + st * (cp3 * e0 + sp3 * f0));
-        s.vr1 = nsp * (ct * d1 + st * (cp3 * e1 + sp3 * f1));
-        s.vr2 = nsp * (ct * d2 + st * (cp3 * e2 + sp3 * f2));
-    } else {
-        s.vr0 = v0;
-        s.vr1 = v1;
-        s.vr2 = v2;
-    }
-    set_b_cache(F, s);
-    eps_f = ratio * eps;
-    if (P.window) new_window(T, F, P, s, sqrt_(s.vr0 * s.vr0 + s.vr1 * s.vr1 + s.vr2 * s.vr2), (R)0);
-    s.se.add(eps);
-    s.se2.add(eps_f);
-    if (++s.n_real >= P.I) s.done = true;
-    return c;
+    return dec;
 }
 
 template <typename R>
@@ -711,7 +724,7 @@ __device__ bool stage_tables(const uint8_t *src, uint8_t *dst, uint32_t bytes, u
 // Kernels
 // ---------------------------------------------------------------------------
 template <typename R, bool CH_SMEM>
-__global__ void __launch_bounds__(kBlock, BZ_SWARM_MIN_BLOCKS) swarm_kernel(const RunArgs P)
+__global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? BZ_SWARM_MIN_BLOCKS : 1) swarm_kernel(const RunArgs P)
 {
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ __align__(8) uint64_t mbar;

@@ -39,10 +39,17 @@ def _run(ctx, mix, **kw):
     return t
 
 
+# Each test compares up to 6 quantities whose standard errors come from 32
+# batch groups (31 degrees of freedom); 3.5 combined SE keeps the family's
+# false-alarm rate near 1 % (a separate check with 4 independent seeds x 2e6
+# electrons per mode found every difference within 1.9 SE).
+Z_FAMILY = 3.5
+
+
 def _agree(a, b, keys, rel=0.005):
     for k in keys:
         se = math.hypot(a[k + "_se"], b[k + "_se"])
-        assert abs(a[k] - b[k]) <= 3 * se, (k, a[k], b[k], se)
+        assert abs(a[k] - b[k]) <= Z_FAMILY * se, (k, a[k], b[k], se)
         if k in ("W", "eps"):
             assert abs(a[k] / b[k] - 1) < rel, (k, a[k], b[k])
 
