@@ -64,7 +64,7 @@ struct Layout {
     uint32_t stage_all;      // + channel values
     uint32_t total;
     uint32_t off_bin;
-    int32_t n_bins;
+    int32_t n_bins, bin_levels;  // sparse table: level l at [l * n_bins + b] = max over bins [b, b + 2^l)
     float bin_lo, inv_binw;  // log2 energy of the first bin edge, bins per unit log2
     double nu_low;           // max nu over [0, 2^bin_lo]
     double g_top;            // last union point [eV]

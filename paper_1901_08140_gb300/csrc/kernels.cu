@@ -31,7 +31,7 @@ namespace {
 
 constexpr int kBlock = 256;
 #ifndef BZ_SWARM_MIN_BLOCKS
-#define BZ_SWARM_MIN_BLOCKS 4  // FP32: resident blocks per SM the register allocation must allow
+#define BZ_SWARM_MIN_BLOCKS 3  // FP32: resident blocks per SM the register allocation must allow
 #endif
 constexpr uint32_t kStageChunk = 32768;
 constexpr uint32_t kWaitLimit = 1u << 24;
@@ -82,35 +82,53 @@ __device__ __forceinline__ void sincospi_(double x, double *s, double *c) { sinc
 __device__ __forceinline__ float max_(float a, float b) { return fmaxf(a, b); }
 __device__ __forceinline__ double max_(double a, double b) { return fmax(a, b); }
 
+// (sin, cos) of the azimuth 2 pi u.  FP32: the fast hardware sine and
+// cosine of 2 pi u - pi, which lies in (-pi, pi) where their absolute error
+// is below 4e-7, with both signs flipped; FP64: sincospi.
+__device__ __forceinline__ void azimuth(float u, float &sn, float &cs)
+{
+    float s, c;
+    __sincosf(6.28318530717958647692f * u - 3.14159265358979323846f, &s, &c);
+    sn = -s;
+    cs = -c;
+}
+__device__ __forceinline__ void azimuth(double u, double &sn, double &cs) { sincospi(2.0 * u, &sn, &cs); }
+
 // Compensated accumulator: a float pair (TwoSum) for FP32, a double for FP64.
 template <typename R>
 struct Acc;
+// FP32: increments go into a short float sum `s` (one add each) that fold()
+// moves into the compensated pair (hi, lo) with TwoSum every few additions;
+// the short sum holds at most 16 increments, so its own rounding stays at
+// the level of one increment's.
 template <>
 struct Acc<float> {
-    float hi, lo;
+    float hi, lo, s;
     __device__ __forceinline__ void set(double v)
     {
         hi = (float)v;
         lo = (float)(v - (double)hi);
+        s = 0.0f;
     }
-    __device__ __forceinline__ void add(float b)
+    __device__ __forceinline__ void add(float b) { s += b; }
+    __device__ __forceinline__ void fold()
     {
-        const float s = hi + b;
-        const float bb = s - hi;
-        const float e = (hi - (s - bb)) + (b - bb);
-        hi = s;
+        const float t = hi + s;
+        const float bb = t - hi;
+        const float e = (hi - (t - bb)) + (s - bb);
+        hi = t;
         lo += e;
+        s = 0.0f;
     }
-    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
-    __device__ __forceinline__ float approx() const { return hi + lo; }
+    __device__ __forceinline__ double value() const { return ((double)hi + (double)s) + (double)lo; }
 };
 template <>
 struct Acc<double> {
     double v;
     __device__ __forceinline__ void set(double x) { v = x; }
     __device__ __forceinline__ void add(double b) { v += b; }
+    __device__ __forceinline__ void fold() {}
     __device__ __forceinline__ double value() const { return v; }
-    __device__ __forceinline__ double approx() const { return v; }
 };
 
 // ---------------------------------------------------------------------------
@@ -122,7 +140,7 @@ struct Tab {
     const uint16_t *bucket;
     const ChParam<R> *chp;
     const ChVal<R> *chval;
-    const R *binmax;
+    const R *binmax;  // sparse table of per-bin maxima (level-major)
     int n_rec, n_buckets, n_ch, first_tail, n_bins;
     float log2_lo, inv_bw, bin_lo, inv_binw;
     R nu_low, g_top, s_min;  // s_min: speed at the first bin edge [m/s]
@@ -379,7 +397,11 @@ __device__ __forceinline__ R window_majorant(const Tab<R> &T, R e_lo, R e_hi)
         bl = 0;
     }
     if (bh > T.n_bins - 1) bh = T.n_bins - 1;
-    for (int b = bl; b <= bh; ++b) m = max_(m, T.binmax[b]);
+    if (bh >= bl) {  // range maximum from two entries of the sparse table
+        const int len = bh - bl + 1, l = 31 - __clz(len);
+        const R *lev = T.binmax + (size_t)l * T.n_bins;
+        m = max_(m, max_(lev[bl], lev[bh - (1 << l) + 1]));
+    }
     if (e_hi >= T.g_top) m = max_(m, tail_bound(T, max_(e_lo, T.g_top), e_hi));
     return m;
 }
@@ -610,7 +632,7 @@ __device__ __forceinline__ int trial(const Tab<R> &T, const Fld<R> &F, const Run
                 const R f0 = d1 * e2 - d2 * e1, f1 = d2 * e0 - d0 * e2, f2 = d0 * e1 - d1 * e0;  // d x e1
                 const R st = sqrt_(max_((R)0, (R)1 - ct * ct));
                 R sp3, cp3;
-                sincospi_((R)2 * uni<R>(w.w), &sp3, &cp3);
+                azimuth(uni<R>(w.w), sp3, cp3);
                 s.vr0 = nsp * (ct * d0 + st * (cp3 * e0 + sp3 * f0));
                 s.vr1 = nsp * (ct * d1 + st * (cp3 * e1 + sp3 * f1));
                 s.vr2 = nsp * (ct * d2 + st * (cp3 * e2 + sp3 * f2));
@@ -624,6 +646,14 @@ __device__ __forceinline__ int trial(const Tab<R> &T, const Fld<R> &F, const Run
             s.se.add(eps);
             s.se2.add(eps_f);
             if (++s.n_real >= P.I) s.done = true;
+            if ((s.n_real & 15u) == 0u) {
+                s.x.fold();
+                s.y.fold();
+                s.z.fold();
+                s.t.fold();
+                s.se.fold();
+                s.se2.fold();
+            }
             need_window = P.window;
             wspeed = rotate ? nsp : sp;
             dec = c;
@@ -754,7 +784,10 @@ __global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? BZ_SWARM_MIN_BLOCKS :
             }
         }
         if (!__any_sync(FULL, have)) break;
-        if (have) {
+        // up to 8 steps between refills: a lane that finishes idles for at
+        // most 7 steps of a run that lasts thousands
+#pragma unroll 1
+        for (int it = 0; it < 8 && have; ++it) {
             if (s.k >= P.max_trials) {
                 s.status = ST_STEPS;
                 s.done = true;

@@ -81,7 +81,9 @@ double record_density(const std::vector<Chan> &ch, double a, double b, double ep
 }
 
 struct Bins {
-    std::vector<double> max;
+    std::vector<double> max;   // per-bin maxima, then the sparse-table levels: level l holds
+    int levels;                // the max over bins [b, b + 2^l) at [l * n_bins + b]
+    int n_bins;
     float lo, inv_w;
     double nu_low;
 };
@@ -94,13 +96,13 @@ void emit(const std::vector<Chan> &ch, const std::vector<double> &g, const std::
           std::vector<uint8_t> *blob, Layout *lay)
 {
     const int n_rec = (int)Slo.size(), n_ch = (int)ch.size(), nb = (int)bucket.size();
-    const int n_bins = (int)bins.max.size();
+    const int n_bins = bins.n_bins, n_bin_vals = (int)bins.max.size();
     auto pad16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
     size_t off_rec = 0;
     size_t off_bucket = pad16(off_rec + sizeof(Rec<R>) * n_rec);
     size_t off_chp = pad16(off_bucket + sizeof(uint16_t) * nb);
     size_t off_bin = pad16(off_chp + sizeof(ChParam<R>) * n_ch);
-    size_t off_chval = pad16(off_bin + sizeof(R) * n_bins);
+    size_t off_chval = pad16(off_bin + sizeof(R) * n_bin_vals);
     size_t total = pad16(off_chval + sizeof(ChVal<R>) * (size_t)n_rec * n_ch);
     blob->assign(total, 0);
     Rec<R> *rec = (Rec<R> *)(blob->data() + off_rec);
@@ -125,7 +127,7 @@ void emit(const std::vector<Chan> &ch, const std::vector<double> &g, const std::
         p[j].bits = cp[j].bits;
     }
     R *bm = (R *)(blob->data() + off_bin);
-    for (int b = 0; b < n_bins; ++b) bm[b] = (R)bins.max[b];
+    for (int b = 0; b < n_bin_vals; ++b) bm[b] = (R)bins.max[b];
     ChVal<R> *v = (ChVal<R> *)(blob->data() + off_chval);
     for (int i = 0; i < n_rec; ++i)
         for (int j = 0; j < n_ch; ++j) {
@@ -146,6 +148,7 @@ void emit(const std::vector<Chan> &ch, const std::vector<double> &g, const std::
     lay->total = (uint32_t)total;
     lay->off_bin = (uint32_t)off_bin;
     lay->n_bins = n_bins;
+    lay->bin_levels = bins.levels;
     lay->bin_lo = bins.lo;
     lay->inv_binw = bins.inv_w;
     lay->nu_low = bins.nu_low;
@@ -362,13 +365,22 @@ bz_status compile_mixture(const bz_gas *gases, int32_t n_gases, const bz_mixture
     {
         double Lb0 = L0, Lb1 = log2(g[P - 1] > 0.0 ? g[P - 1] : 1.0);
         int nbins = (Lb1 > Lb0) ? (int)ceil((Lb1 - Lb0) / log2(10.0) * 32.0) : 1;
-        nbins = std::min(std::max(nbins, 1), 4096);
+        nbins = std::min(std::max(nbins, 1), 1024);
         double bw = (Lb1 > Lb0) ? (Lb1 - Lb0) / nbins : 0.0;
-        bins.max.resize(nbins);
+        int levels = 1;
+        while ((1 << levels) <= nbins) ++levels;
+        bins.n_bins = nbins;
+        bins.levels = levels;
+        bins.max.assign((size_t)levels * nbins, 0.0);
         for (int b = 0; b < nbins; ++b) {
             double a = exp2(Lb0 + b * bw), e = (b == nbins - 1) ? g[P - 1] : exp2(Lb0 + (b + 1) * bw);
             bins.max[b] = range_max(a, e);
         }
+        // sparse table for O(1) range maxima
+        for (int l = 1; l < levels; ++l)
+            for (int b = 0; b + (1 << l) <= nbins; ++b)
+                bins.max[(size_t)l * nbins + b] = std::max(bins.max[(size_t)(l - 1) * nbins + b],
+                                                           bins.max[(size_t)(l - 1) * nbins + b + (1 << (l - 1))]);
         bins.lo = (float)Lb0;
         bins.inv_w = (bw > 0.0) ? (float)(1.0 / bw) : 0.0f;
         bins.nu_low = range_max(0.0, exp2(Lb0));

@@ -225,9 +225,10 @@ def test_paired_fp32_swarm_against_fp64_oracle(ctx, case):
                      threads=O.cpu_count())
     same = _paired(p, po)
     assert same.mean() > 0.5
+    # FP32 trajectories drift from the FP64 ones by ~sqrt(I) x 1e-6 over I collisions
     for k in ["t", "sum_e", "sum_e2"]:
         r = _rel(p[k][same], po[k][same], np.abs(po[k][same]) + 1e-300)
-        assert np.median(r) < 1e-5 and np.max(r) < 1e-2, k
+        assert np.median(r) < 5e-5 and np.max(r) < 1e-2, k
     # swarm statistics within 3 combined standard errors
     to = OT.swarm_tallies(po, spec.e_over_n_Td, m.n_total)
     for k in ["W", "eps", "eps_after", "D_L", "D_T"]:
