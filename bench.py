@@ -151,6 +151,27 @@ def cpu_baseline(args, specs, budget_s):
             "trial_collisions_per_s": trials / dt}
 
 
+def _timed(stream, flush, steps, fn, world, dev):
+    """Runs fn() `steps` times; device time per step from CUDA events on `stream`."""
+    import torch
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    total = 0.0
+    outs = []
+    for _ in range(steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            torch.distributed.barrier()
+        ev0.record(stream)
+        h = fn()
+        ev1.record(stream)
+        ev1.synchronize()
+        total += ev0.elapsed_time(ev1)
+        torch.cuda.synchronize(dev)
+        outs.append(h)
+    return total, outs
+
+
 def run_ours(args):
     import torch
     world, rank, local = dist()
@@ -171,88 +192,91 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
 
-    def one_step():
+    # ---- plain: one persistent launch per swarm, back to back on one stream
+    def plain_step():
         return [bz.run_swarm(ctx, mix, c, stream) for c in cfgs]
 
     for _ in range(args.warmup):
-        for sw in one_step():
+        for sw in plain_step():
             sw.tallies()
             sw.close()
-    torch.cuda.synchronize(dev)
+    plain_ms, plain_outs = _timed(stream, flush, args.steps, plain_step, world, dev)
+    plain_reals = 0
+    for sws in plain_outs:
+        for sw in sws:
+            plain_reals += sw.tallies()["n_real"]
+            sw.close()
 
+    # ---- batched: every swarm in one persistent launch, replayed from a CUDA graph
+    batch = bz.Batch(ctx, [mix] * len(cfgs), cfgs)
+
+    def batch_step():
+        batch.launch(stream)
+        return None
+
+    for _ in range(args.warmup):
+        batch_step()
+        batch.tallies()
     clocks = Clocks(local)
-    total_ms = 0.0
     reals = trials = 0
     kern_ms = 0.0
     steps_other = 0
     work = 0.0
     w_err = []
-    launches = 0
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    total_ms = 0.0
     for _ in range(args.steps):
-        flush.fill_(1.0)
-        torch.cuda.synchronize(dev)
-        if world > 1:
-            torch.distributed.barrier()
-        ev0.record(stream)
-        swarms = one_step()
-        ev1.record(stream)
-        ev1.synchronize()
-        total_ms += ev0.elapsed_time(ev1)
-        torch.cuda.synchronize(dev)
-        for sw in swarms:
-            t = sw.tallies()
-            km, _ = sw.timing()
-            reals += t["n_real"]
+        ms, _ = _timed(stream, flush, 1, batch_step, world, dev)
+        total_ms += ms
+        ts = batch.tallies()
+        km, _ = batch.timing()
+        kern_ms += km
+        for t in ts:
             tr = t["n_real"] + t["n_null"] + t["n_fail"]
+            reals += t["n_real"]
             trials += tr
-            steps_other += t.get("n_window", 0)
-            kern_ms += km
-            work += ALG_OPS_PER_TRIAL * (tr + t.get("n_window", 0)) + ALG_OPS_PER_REAL * t["n_real"]
+            steps_other += t["n_window"]
+            work += ALG_OPS_PER_TRIAL * (tr + t["n_window"]) + ALG_OPS_PER_REAL * t["n_real"]
             w_err.append(t["W_se"] / abs(t["W"]) if t["W"] else float("inf"))
-            launches += 5   # step kernel + 4 tally kernels
-            sw.close()
     clk = clocks.stop()
-    t_max = total_ms
-    tot_reals = reals
+    launches = 5 * args.steps   # batch kernel + 4 multi-swarm tally kernels, in one graph
+    t_max, p_max = total_ms, plain_ms
+    tot_reals, tot_plain = reals, plain_reals
     if world > 1:
         import torch.distributed as tdist
-        x = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        x = torch.tensor([total_ms, plain_ms], device=dev, dtype=torch.float64)
         tdist.all_reduce(x, op=tdist.ReduceOp.MAX)
-        t_max = float(x.item())
-        y = torch.tensor([float(reals)], device=dev, dtype=torch.float64)
+        t_max, p_max = float(x[0].item()), float(x[1].item())
+        y = torch.tensor([float(reals), float(plain_reals)], device=dev, dtype=torch.float64)
         tdist.all_reduce(y)
-        tot_reals = int(y.item())
+        tot_reals, tot_plain = int(y[0].item()), int(y[1].item())
     value = tot_reals / (t_max / 1e3)
+    plain_value = tot_plain / (p_max / 1e3)
 
     # end to end through the C ABI: host tables in, host tallies out
     e2e = None
     if not args.no_e2e:
-        h2d = d2h = 0
-        e_reals = 0
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         m2 = bz.Mixture(ctx, specs[0].gases)
-        h2d += m2.info["table_bytes"]
-        sws = [bz.run_swarm(ctx, m2, c, stream) for c in cfgs]
-        h2d += len(cfgs) * (16 + 256)   # counter/flag reset and kernel arguments
-        for sw in sws:
-            e_reals += sw.tallies()["n_real"]
-            d2h += C.sizeof(bz.bz_tallies)
+        b2 = bz.Batch(ctx, [m2] * len(cfgs), cfgs)
+        b2.launch(stream)
+        e_reals = sum(t["n_real"] for t in b2.tallies())
         torch.cuda.synchronize(dev)
         dt = time.perf_counter() - t0
-        for sw in sws:
-            sw.close()
+        h2d = m2.info["table_bytes"] + len(cfgs) * (C.sizeof(bz.bz_swarm_config) + 4096)
+        d2h = len(cfgs) * C.sizeof(bz.bz_tallies)
+        b2.close()
         m2.close()
         e2e = {"value": e_reals / dt, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+    batch.close()
 
     sm_mhz = clk.get("sm_mhz") or 2070.0
     peak = torch.cuda.get_device_properties(dev).multi_processor_count * LANES_PER_SM_CLOCK * sm_mhz * 1e6
     achieved = work / (kern_ms / 1e3)
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tops/s",
                 "frac": achieved / peak, "traffic": None,
-                "kernel": "swarm_kernel<float,true>",
-                "note": f"algorithmic thread-ops ({ALG_OPS_PER_TRIAL}/trial + {ALG_OPS_PER_REAL}/real) over "
+                "kernel": "batch_kernel<float,true>",
+                "note": f"algorithmic thread-ops ({ALG_OPS_PER_TRIAL}/step + {ALG_OPS_PER_REAL}/real) over "
                         f"SMs x 128 lanes x median SM clock {sm_mhz:.0f} MHz"}
     if rank != 0:
         return
@@ -267,10 +291,13 @@ def run_ours(args):
                                f"{args.electrons} electrons x {args.collisions} real collisions, "
                                f"FP32 flights, FP64 tallies, {args.trial} trial frequency, B = 0"
                                + (f" (point {args.only_point} only)" if args.only_point >= 0 else ""),
-                   "mode": "plain (one persistent launch per swarm)", "swarms": len(specs),
-                   "electrons_per_swarm": args.electrons, "real_collisions": args.collisions,
+                   "mode": "batched: all swarms in one persistent launch replayed from a CUDA graph",
+                   "swarms": len(specs), "electrons_per_swarm": args.electrons, "real_collisions": args.collisions,
                    "l2": "flushed between steps (256 MiB write)", "parallelism": f"dp{world} (particle ids)"},
-        "trial_collisions_per_s": trials * world / (t_max / 1e3) if world == 1 else None,
+        "plain": {"value": plain_value, "ms_per_step": p_max / args.steps,
+                  "mode": "one persistent launch per swarm, back to back on one stream"},
+        "batched_over_plain": value / plain_value,
+        "trial_collisions_per_s": trials * world / (t_max / 1e3),
         "efficiency": reals / trials if trials else None,
         "window_restarts_per_real": steps_other / reals if reals else None,
         "max_rel_se_W": max(w_err) if w_err else None,

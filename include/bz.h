@@ -251,6 +251,42 @@ bz_status bz_swarm_timing(bz_swarm *sw, double *step_ms, double *tally_ms);
 void bz_destroy_swarm(bz_swarm *sw);
 
 /* ------------------------------------------------------------------------
+ * Batched swarms: many swarms of uneven size and different mixtures in one
+ * persistent launch (the GPU counterpart of the paper's many independent
+ * particles of Sec. 4).  Work is split into tiles (swarm, particle range)
+ * ordered by mixture; a block re-stages tables only when the mixture
+ * changes.  The launch, the FP64 tallies of every swarm and the copy of
+ * the tallies to the host are captured once in a CUDA graph and replayed
+ * by bz_launch_batch.  Every swarm's results equal those of bz_run_swarm
+ * with the same configuration.
+ * ------------------------------------------------------------------------ */
+typedef struct bz_batch bz_batch;
+
+typedef struct {
+    int32_t tile_particles;   /* electrons per tile; <= 0: about 16 tiles per resident block */
+    int32_t blocks_per_sm;    /* <= 0: as many as fit */
+    int32_t use_graph;        /* 1: CUDA graph (default when opts is NULL), 0: plain launches */
+    int32_t reserved;
+} bz_batch_opts;
+
+/* Prepares a batch of n swarms: mixtures[i] and cfgs[i] as for
+ * bz_run_swarm (all the same precision).  Allocates the device state of all
+ * swarms once.  Errors: BZ_EINVAL, BZ_EBUDGET (tables too large for shared
+ * memory), BZ_ENOMEM, BZ_ECUDA. */
+bz_status bz_create_batch(bz_ctx *ctx, int32_t n, const bz_mixture *const *mixtures, const bz_swarm_config *cfgs,
+                          const bz_batch_opts *opts, bz_batch **out);
+/* Runs the batch on `stream` (asynchronous); may be called again after the
+ * previous run finished (same results: counters are keyed by the seeds). */
+bz_status bz_launch_batch(bz_batch *b, void *stream);
+/* Waits for the last launch and copies the n swarms' tallies into out[n]. */
+bz_status bz_batch_read_tallies(bz_batch *b, bz_tallies *out);
+/* Waits, then copies swarm i's per-particle results (as bz_read_particles). */
+bz_status bz_batch_read_particles(bz_batch *b, int32_t i, const bz_particles *out);
+/* Device time of the last launch: the batch kernel and the tally kernels [ms]. */
+bz_status bz_batch_timing(bz_batch *b, double *step_ms, double *tally_ms);
+void bz_destroy_batch(bz_batch *b);
+
+/* ------------------------------------------------------------------------
  * Allocation-free tally reduction.  The paper has no counterpart: this entry
  * exists for callers that cannot allocate device memory at the point where
  * they need swarm statistics -- code whose device memory is entirely held by

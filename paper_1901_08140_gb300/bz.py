@@ -98,6 +98,11 @@ class bz_particle_arrays(C.Structure):
 BZ_NOALLOC_MAX_PARTICLES = 32768 * 512
 
 
+class bz_batch_opts(C.Structure):
+    _fields_ = [("tile_particles", C.c_int32), ("blocks_per_sm", C.c_int32), ("use_graph", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 
@@ -132,6 +137,13 @@ SIGNATURES = {
     "bz_read_particles": (C.c_int, [C.c_void_p, C.POINTER(bz_particles)]),
     "bz_destroy_swarm": (None, [C.c_void_p]),
     "bz_swarm_timing": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "bz_create_batch": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_void_p), C.POINTER(bz_swarm_config),
+                                  C.POINTER(bz_batch_opts), C.POINTER(C.c_void_p)]),
+    "bz_launch_batch": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "bz_batch_read_tallies": (C.c_int, [C.c_void_p, C.POINTER(bz_tallies)]),
+    "bz_batch_read_particles": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(bz_particles)]),
+    "bz_batch_timing": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "bz_destroy_batch": (None, [C.c_void_p]),
     "bz_reduce_tallies_noalloc": (C.c_int, [C.POINTER(bz_particle_arrays), C.c_uint64, C.c_uint64, C.c_double,
                                             C.c_double, C.c_double, C.c_void_p, C.c_void_p]),
     "bz_step_replay": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(bz_swarm_config), C.c_int64, C.c_void_p,
@@ -182,6 +194,12 @@ def bz_query_tallies(sw, out): return lib().bz_query_tallies(sw, out)
 def bz_read_particles(sw, out): return lib().bz_read_particles(sw, out)
 def bz_destroy_swarm(sw): return lib().bz_destroy_swarm(sw)
 def bz_swarm_timing(sw, a, b): return lib().bz_swarm_timing(sw, a, b)
+def bz_create_batch(*a): return lib().bz_create_batch(*a)
+def bz_launch_batch(b, stream): return lib().bz_launch_batch(b, stream)
+def bz_batch_read_tallies(b, out): return lib().bz_batch_read_tallies(b, out)
+def bz_batch_read_particles(b, i, out): return lib().bz_batch_read_particles(b, i, out)
+def bz_batch_timing(b, a, c): return lib().bz_batch_timing(b, a, c)
+def bz_destroy_batch(b): return lib().bz_destroy_batch(b)
 def bz_reduce_tallies_noalloc(*a): return lib().bz_reduce_tallies_noalloc(*a)
 def bz_step_replay(*a): return lib().bz_step_replay(*a)
 def bz_philox(*a): return lib().bz_philox(*a)
@@ -380,6 +398,72 @@ class Swarm:
 
     def __del__(self):
         # at interpreter shutdown the allocator callbacks may already be gone
+        if sys.is_finalizing():
+            return
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _tally_dict(t) -> Dict[str, float]:
+    out = {k: getattr(t, k) for k in _TALLY_DOUBLES + _TALLY_COUNTS}
+    out["error_flags"] = t.error_flags
+    return out
+
+
+def _particle_arrays(n: int):
+    arrs = {k: np.zeros(n, np.float64) for k in _PART_D}
+    arrs.update({k: np.zeros(n, np.float32) for k in _PART_F})
+    arrs.update({k: np.zeros(n, np.uint32) for k in _PART_U})
+    p = bz_particles(*[arrs[k].ctypes.data_as(C.POINTER(C.c_double)) for k in _PART_D],
+                     *[arrs[k].ctypes.data_as(C.POINTER(C.c_float)) for k in _PART_F],
+                     *[arrs[k].ctypes.data_as(C.POINTER(C.c_uint32)) for k in _PART_U])
+    return arrs, p
+
+
+class Batch:
+    """Many swarms in one persistent launch (bz_create_batch / bz_launch_batch)."""
+
+    def __init__(self, ctx: Context, mixtures: Sequence["Mixture"], cfgs: Sequence[bz_swarm_config],
+                 tile_particles: int = 0, blocks_per_sm: int = 0, use_graph: bool = True):
+        self.ctx, self.mixtures, self.n = ctx, list(mixtures), len(cfgs)
+        self.cfgs = (bz_swarm_config * self.n)(*cfgs)
+        mh = (C.c_void_p * self.n)(*[m.h.value for m in mixtures])
+        opts = bz_batch_opts(int(tile_particles), int(blocks_per_sm), int(bool(use_graph)), 0)
+        h = C.c_void_p()
+        _check(lib().bz_create_batch(ctx.h, self.n, mh, self.cfgs, C.byref(opts), C.byref(h)))
+        self.h = h
+
+    def launch(self, stream=None):
+        _check(lib().bz_launch_batch(self.h, C.c_void_p(_stream_handle(stream))))
+
+    def tallies(self, check: bool = True):
+        out = (bz_tallies * self.n)()
+        st = lib().bz_batch_read_tallies(self.h, out)
+        if check:
+            _check(st)
+        return [_tally_dict(t) for t in out]
+
+    def particles(self, i: int) -> Dict[str, np.ndarray]:
+        n = int(self.cfgs[i].n_electrons)
+        arrs, p = _particle_arrays(n)
+        _check(lib().bz_batch_read_particles(self.h, int(i), C.byref(p)))
+        off = int(self.cfgs[i].id_offset)
+        arrs["id"] = np.arange(off, off + n, dtype=np.uint64)
+        return arrs
+
+    def timing(self):
+        a, b = C.c_double(), C.c_double()
+        _check(lib().bz_batch_timing(self.h, C.byref(a), C.byref(b)))
+        return a.value, b.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().bz_destroy_batch(self.h)
+            self.h = None
+
+    def __del__(self):
         if sys.is_finalizing():
             return
         try:

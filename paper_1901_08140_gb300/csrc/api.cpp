@@ -3,9 +3,11 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <atomic>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "bz.h"
 #include "kernels.h"
@@ -42,6 +44,30 @@ struct bz_swarm {
     uint64_t n;
 };
 
+struct bz_batch {
+    bz_ctx *ctx;
+    int32_t n;
+    int precision;
+    bool ch_smem, use_graph;
+    size_t smem;
+    int grid, n_tiles, max_tblocks;
+    std::vector<uint64_t> n_el;
+    std::vector<bz::ParticlesDev> p;
+    uint8_t *mem;
+    size_t bytes;
+    bz::RunArgs *desc;
+    uint4 *tiles;
+    unsigned int *tile_counter;
+    uint32_t *errs;
+    bz::TallyArgs *targs;
+    bz_tallies *tallies_dev, *tallies_host;
+    cudaStream_t cap;
+    cudaGraph_t graph[2];      // [0]: counters + step kernel, [1]: tallies + copy to the host
+    cudaGraphExec_t exec[2];
+    cudaEvent_t ev[3], done;
+    bool launched;
+};
+
 namespace {
 
 thread_local std::string g_err;
@@ -74,6 +100,17 @@ void dev_free(bz_ctx *c, void *p, size_t bytes, cudaStream_t s)
 }
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Electrons per tile: ~n / (blocks x per_block), rounded up to a multiple of
+// 256, within [256, 8192].
+uint32_t tile_size_for(uint64_t n, uint64_t blocks, uint64_t per_block)
+{
+    uint64_t t = (n + blocks * per_block - 1) / (blocks * per_block);
+    t = (t + 255) / 256 * 256;
+    if (t < 256) t = 256;
+    if (t > 8192) t = 8192;
+    return (uint32_t)t;
+}
 
 void ctx_retain(bz_ctx *c) { c->refs.fetch_add(1); }
 
@@ -304,12 +341,17 @@ bz_status bz_run_swarm(bz_ctx *ctx, const bz_mixture *mix, const bz_swarm_config
     bool ch_smem;
     if ((st = prepare_run(mix, cfg, &a, &ch_smem)) != BZ_OK) return st;
     const uint64_t n = cfg->n_electrons;
+    if (n > 0xFFFFFFFFull) return fail(BZ_EINVAL, "a swarm holds at most 2^32-1 electrons");
     const int block = 256;
-    int bps = bz::swarm_occupancy(cfg->precision, ch_smem, block, a.stage_bytes);
+    int bps = bz::batch_occupancy(cfg->precision, ch_smem, block, a.stage_bytes);
     if (bps < 1) return fail(BZ_ECUDA, "step kernel cannot be resident with these tables");
     if (cfg->blocks_per_sm > 0 && cfg->blocks_per_sm < bps) bps = cfg->blocks_per_sm;
-    uint64_t grid64 = (uint64_t)ctx->sm_count * bps, need = (n + block - 1) / block;
-    const int grid = (int)(grid64 < need ? grid64 : need);
+    const uint64_t grid64 = (uint64_t)ctx->sm_count * bps;
+    // about 8 tiles per block (load balance at the end of the launch), each a
+    // multiple of the block size (balance inside a tile)
+    const uint32_t tile = tile_size_for(n, grid64, 8);
+    const uint64_t n_tiles = (n + tile - 1) / tile;
+    const int grid = (int)(grid64 < n_tiles ? grid64 : n_tiles);
     const int tblocks = bz::tally_blocks(n, ctx->sm_count);
 
     bz_swarm *s = new (std::nothrow) bz_swarm();
@@ -358,11 +400,19 @@ bz_status bz_run_swarm(bz_ctx *ctx, const bz_mixture *mix, const bz_swarm_config
     }
     for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaEventCreate(&s->ev[i]);
     if (e == cudaSuccess) e = cudaMemsetAsync(M + o_ctr, 0, 16, s->stream);
-    a.counter = counter;
+    a.counter = nullptr;
     a.err = s->err;
     a.out = s->p;
+    bz::BatchArgs ba;
+    memset(&ba, 0, sizeof ba);
+    ba.desc = nullptr;
+    ba.tiles = nullptr;
+    ba.n_tiles = (int32_t)n_tiles;
+    ba.tile_size = tile;
+    ba.tile_counter = (unsigned int *)counter;
+    ba.single = a;
     if (e == cudaSuccess) e = cudaEventRecord(s->ev[0], s->stream);
-    if (e == cudaSuccess) e = bz::launch_swarm(cfg->precision, ch_smem, a, grid, block, s->stream);
+    if (e == cudaSuccess) e = bz::launch_batch(cfg->precision, ch_smem, ba, a.stage_bytes, grid, block, s->stream);
     if (e == cudaSuccess) e = cudaEventRecord(s->ev[1], s->stream);
     bz::TallyArgs t;
     memset(&t, 0, sizeof t);
@@ -468,6 +518,286 @@ bz_status bz_swarm_timing(bz_swarm *sw, double *step_ms, double *tally_ms)
     if (step_ms) *step_ms = a;
     if (tally_ms) *tally_ms = b;
     return BZ_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batches
+// ---------------------------------------------------------------------------
+// part 0: counters and the step kernel; part 1: tallies and their copy to the host
+static cudaError_t batch_part(bz_batch *b, int part, cudaStream_t s)
+{
+    cudaError_t e;
+    if (part == 0) {
+        e = cudaMemsetAsync(b->tile_counter, 0, sizeof(unsigned int) * (2 + b->n), s);
+        bz::BatchArgs a;
+        memset(&a, 0, sizeof a);
+        a.desc = b->desc;
+        a.tiles = b->tiles;
+        a.n_tiles = b->n_tiles;
+        a.tile_counter = b->tile_counter;
+        if (e == cudaSuccess) e = bz::launch_batch(b->precision, b->ch_smem, a, b->smem, b->grid, 256, s);
+        return e;
+    }
+    e = bz::launch_tallies_multi(b->targs, b->n, b->max_tblocks, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->tallies_host, b->tallies_dev, sizeof(bz_tallies) * b->n, cudaMemcpyDeviceToHost, s);
+    return e;
+}
+
+static bz_status batch_sequence(bz_batch *b, cudaStream_t s)
+{
+    cudaError_t e = cudaEventRecord(b->ev[0], s);
+    for (int part = 0; part < 2 && e == cudaSuccess; ++part) {
+        e = b->use_graph ? cudaGraphLaunch(b->exec[part], s) : batch_part(b, part, s);
+        if (e == cudaSuccess) e = cudaEventRecord(b->ev[1 + part], s);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "batch launch");
+    return BZ_OK;
+}
+
+bz_status bz_create_batch(bz_ctx *ctx, int32_t n, const bz_mixture *const *mixtures, const bz_swarm_config *cfgs,
+                          const bz_batch_opts *opts, bz_batch **out)
+{
+    if (!ctx || !out || !mixtures || !cfgs) return fail(BZ_EINVAL, "null argument");
+    *out = nullptr;
+    if (n < 1) return fail(BZ_EINVAL, "a batch needs at least one swarm");
+    const int precision = cfgs[0].precision;
+    for (int i = 0; i < n; ++i) {
+        bz_status st = validate_config(&cfgs[i]);
+        if (st != BZ_OK) return st;
+        if (!mixtures[i]) return fail(BZ_EINVAL, "null mixture");
+        if (cfgs[i].precision != precision) return fail(BZ_EINVAL, "all swarms of a batch need the same precision");
+        if (cfgs[i].n_electrons > 0xFFFFFFFFull) return fail(BZ_EINVAL, "a batched swarm holds at most 2^32-1 electrons");
+    }
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    bz_batch *b = new (std::nothrow) bz_batch();
+    if (!b) return fail(BZ_ENOMEM, "host allocation");
+    b->ctx = ctx;
+    b->n = n;
+    b->precision = precision;
+    b->use_graph = opts ? opts->use_graph != 0 : true;
+    // tables of every mixture must fit; channel tables go to shared memory only if all fit
+    b->ch_smem = true;
+    std::vector<bz::RunArgs> desc(n);
+    for (int i = 0; i < n; ++i) {
+        bool ch;
+        bz_status st = prepare_run(mixtures[i], &cfgs[i], &desc[i], &ch);
+        if (st != BZ_OK) {
+            delete b;
+            return st;
+        }
+        b->ch_smem = b->ch_smem && ch;
+    }
+    b->smem = 0;
+    for (int i = 0; i < n; ++i) {
+        desc[i].stage_bytes = b->ch_smem ? desc[i].lay.stage_all : desc[i].lay.stage_tables;
+        b->smem = std::max(b->smem, (size_t)desc[i].stage_bytes);
+    }
+    int bps = bz::batch_occupancy(precision, b->ch_smem, 256, b->smem);
+    if (bps < 1) {
+        delete b;
+        return fail(BZ_ECUDA, "batch kernel cannot be resident with these tables");
+    }
+    if (opts && opts->blocks_per_sm > 0 && opts->blocks_per_sm < bps) bps = opts->blocks_per_sm;
+    uint64_t total = 0;
+    for (int i = 0; i < n; ++i) total += cfgs[i].n_electrons;
+    const uint32_t tile = (opts && opts->tile_particles > 0) ? (uint32_t)opts->tile_particles
+                                                             : tile_size_for(total, (uint64_t)ctx->sm_count * bps, 16);
+    // tiles, grouped by mixture (tables), then by swarm
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return desc[x].blob < desc[y].blob; });
+    std::vector<uint4> tiles;
+    for (int i : order)
+        for (uint64_t s0 = 0; s0 < cfgs[i].n_electrons; s0 += tile) {
+            uint64_t c = std::min<uint64_t>(tile, cfgs[i].n_electrons - s0);
+            tiles.push_back(make_uint4((unsigned)i, (unsigned)s0, (unsigned)c, 0u));
+        }
+    b->n_tiles = (int)tiles.size();
+    b->grid = std::min(ctx->sm_count * bps, b->n_tiles);
+    // one device allocation for everything
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return o; };
+    const size_t o_desc = take(sizeof(bz::RunArgs) * n), o_tiles = take(sizeof(uint4) * tiles.size());
+    const size_t o_ctr = take(sizeof(unsigned int) * (2 + n));
+    const size_t o_targs = take(sizeof(bz::TallyArgs) * n), o_tal = take(sizeof(bz_tallies) * n);
+    std::vector<size_t> o_part(n), o_p1(n), o_p2(n), o_gs(n);
+    std::vector<int> tb(n);
+    b->n_el.resize(n);
+    b->max_tblocks = 1;
+    for (int i = 0; i < n; ++i) {
+        const uint64_t m = cfgs[i].n_electrons;
+        b->n_el[i] = m;
+        o_part[i] = take((6 * 8 + 4 * 4 + 7 * 4) * m + 17 * 256);
+        tb[i] = bz::tally_blocks(m, ctx->sm_count);
+        b->max_tblocks = std::max(b->max_tblocks, tb[i]);
+        o_p1[i] = take(sizeof(double) * tb[i] * bz::kGroups * bz::kQ1);
+        o_p2[i] = take(sizeof(double) * tb[i] * bz::kGroups * bz::kQ2);
+        o_gs[i] = take(sizeof(double) * (bz::kGroups * (bz::kQ1 + bz::kQ2) + 8));
+    }
+    b->bytes = off;
+    b->mem = (uint8_t *)dev_alloc(ctx, b->bytes, 0);
+    if (!b->mem) {
+        delete b;
+        return fail(BZ_ENOMEM, "device allocation of the batch");
+    }
+    ctx_retain(ctx);
+    uint8_t *M = b->mem;
+    b->desc = (bz::RunArgs *)(M + o_desc);
+    b->tiles = (uint4 *)(M + o_tiles);
+    b->tile_counter = (unsigned int *)(M + o_ctr);
+    b->errs = b->tile_counter + 2;
+    b->targs = (bz::TallyArgs *)(M + o_targs);
+    b->tallies_dev = (bz_tallies *)(M + o_tal);
+    std::vector<bz::TallyArgs> targs(n);
+    b->p.resize(n);
+    for (int i = 0; i < n; ++i) {
+        const uint64_t m = b->n_el[i];
+        size_t q = o_part[i];
+        auto sub = [&](size_t bytes) { size_t o = q; q = align256(q + bytes); return (void *)(M + o); };
+        bz::ParticlesDev &P = b->p[i];
+        P.x = (double *)sub(8 * m); P.y = (double *)sub(8 * m); P.z = (double *)sub(8 * m); P.t = (double *)sub(8 * m);
+        P.se = (double *)sub(8 * m); P.se2 = (double *)sub(8 * m);
+        P.vx = (float *)sub(4 * m); P.vy = (float *)sub(4 * m); P.vz = (float *)sub(4 * m); P.nup = (float *)sub(4 * m);
+        P.n_real = (uint32_t *)sub(4 * m); P.n_null = (uint32_t *)sub(4 * m); P.n_fail = (uint32_t *)sub(4 * m);
+        P.n_ion = (uint32_t *)sub(4 * m); P.n_att = (uint32_t *)sub(4 * m); P.steps = (uint32_t *)sub(4 * m);
+        P.status = (uint32_t *)sub(4 * m);
+        desc[i].out = P;
+        desc[i].err = b->errs + i;
+        desc[i].counter = nullptr;
+        bz::TallyArgs &t = targs[i];
+        memset(&t, 0, sizeof t);
+        t.x = P.x; t.y = P.y; t.z = P.z; t.t = P.t; t.se = P.se; t.se2 = P.se2;
+        t.n_real = P.n_real; t.n_null = P.n_null; t.n_fail = P.n_fail; t.n_ion = P.n_ion; t.n_att = P.n_att;
+        t.status = P.status; t.steps = P.steps;
+        t.n = m;
+        t.id_offset = cfgs[i].id_offset;
+        t.part1 = (double *)(M + o_p1[i]);
+        t.part2 = (double *)(M + o_p2[i]);
+        t.gsum = (double *)(M + o_gs[i]);
+        t.blocks = tb[i];
+        t.E_V_m = cfgs[i].e_over_n_Td * bz::kTownsend * mixtures[i]->cm.n_total;
+        t.n_total = mixtures[i]->cm.n_total;
+        t.nu_trial = desc[i].nu0;
+        t.err = b->errs + i;
+        t.out = b->tallies_dev + i;
+    }
+    e = cudaMemcpy(b->desc, desc.data(), sizeof(bz::RunArgs) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->tiles, tiles.data(), sizeof(uint4) * tiles.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->targs, targs.data(), sizeof(bz::TallyArgs) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMallocHost(&b->tallies_host, sizeof(bz_tallies) * n);
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaEventCreate(&b->ev[i]);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        bz_destroy_batch(b);
+        return cuda_fail(e, "batch set-up");
+    }
+    if (b->use_graph) {
+        // make sure the kernels' shared-memory limits are set before capture
+        bz::batch_occupancy(precision, b->ch_smem, 256, b->smem);
+        for (int part = 0; part < 2 && e == cudaSuccess; ++part) {
+            e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+            cudaError_t e1 = (e == cudaSuccess) ? batch_part(b, part, b->cap) : e;
+            cudaError_t e2 = cudaStreamEndCapture(b->cap, &b->graph[part]);
+            if (e == cudaSuccess) e = (e1 != cudaSuccess) ? e1 : e2;
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec[part], b->graph[part], 0);
+        }
+        if (e != cudaSuccess) {
+            bz_destroy_batch(b);
+            return cuda_fail(e, "batch graph capture");
+        }
+    }
+    *out = b;
+    return BZ_OK;
+}
+
+bz_status bz_launch_batch(bz_batch *b, void *stream)
+{
+    if (!b) return fail(BZ_EINVAL, "null batch");
+    cudaError_t e = cudaSetDevice(b->ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (e == cudaSuccess && b->launched) e = cudaEventSynchronize(b->done);
+    if (e != cudaSuccess) return cuda_fail(e, "batch launch");
+    bz_status st = batch_sequence(b, s);
+    if (st != BZ_OK) return st;
+    e = cudaEventRecord(b->done, s);
+    if (e != cudaSuccess) return cuda_fail(e, "batch launch");
+    b->launched = true;
+    return BZ_OK;
+}
+
+bz_status bz_batch_read_tallies(bz_batch *b, bz_tallies *out)
+{
+    if (!b || !out) return fail(BZ_EINVAL, "null argument");
+    if (!b->launched) return fail(BZ_EINVAL, "batch not launched");
+    cudaError_t e = cudaEventSynchronize(b->done);
+    if (e != cudaSuccess) return cuda_fail(e, "batch");
+    bz_status st = BZ_OK;
+    for (int i = 0; i < b->n; ++i) {
+        out[i] = b->tallies_host[i];
+        if (out[i].error_flags & BZ_ERR_STAGE_TIMEOUT) st = fail(BZ_ETIMEOUT, "table staging timed out");
+        else if ((out[i].error_flags & BZ_ERR_TRIAL) && st == BZ_OK) st = fail(BZ_ETRIAL, "fixed trial frequency exceeded");
+    }
+    return st;
+}
+
+bz_status bz_batch_read_particles(bz_batch *b, int32_t i, const bz_particles *o)
+{
+    if (!b || !o || i < 0 || i >= b->n) return fail(BZ_EINVAL, "bad argument");
+    cudaError_t e = b->launched ? cudaEventSynchronize(b->done) : cudaSuccess;
+    if (e != cudaSuccess) return cuda_fail(e, "batch");
+    const size_t m = b->n_el[i];
+    const bz::ParticlesDev &p = b->p[i];
+    struct { void *dst; const void *src; size_t bytes; } cp[] = {
+        {o->x, p.x, 8 * m}, {o->y, p.y, 8 * m}, {o->z, p.z, 8 * m}, {o->t, p.t, 8 * m}, {o->sum_e, p.se, 8 * m},
+        {o->sum_e2, p.se2, 8 * m}, {o->vx, p.vx, 4 * m}, {o->vy, p.vy, 4 * m}, {o->vz, p.vz, 4 * m},
+        {o->nu_p, p.nup, 4 * m}, {o->n_real, p.n_real, 4 * m}, {o->n_null, p.n_null, 4 * m},
+        {o->n_fail, p.n_fail, 4 * m}, {o->n_ion, p.n_ion, 4 * m}, {o->n_att, p.n_att, 4 * m},
+        {o->steps, p.steps, 4 * m}, {o->status, p.status, 4 * m}};
+    for (auto &c : cp) {
+        if (!c.dst) continue;
+        if ((e = cudaMemcpy(c.dst, c.src, c.bytes, cudaMemcpyDeviceToHost)) != cudaSuccess)
+            return cuda_fail(e, "copy of particle state");
+    }
+    return BZ_OK;
+}
+
+bz_status bz_batch_timing(bz_batch *b, double *step_ms, double *tally_ms)
+{
+    if (!b || !b->launched) return fail(BZ_EINVAL, "batch not launched");
+    cudaError_t e = cudaEventSynchronize(b->done);
+    float a = 0.f, c = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&a, b->ev[0], b->ev[1]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&c, b->ev[1], b->ev[2]);
+    if (e != cudaSuccess) return cuda_fail(e, "batch timing");
+    if (step_ms) *step_ms = a;
+    if (tally_ms) *tally_ms = c;
+    return BZ_OK;
+}
+
+void bz_destroy_batch(bz_batch *b)
+{
+    if (!b) return;
+    cudaSetDevice(b->ctx->device);
+    if (b->launched) cudaEventSynchronize(b->done);
+    for (int i = 0; i < 2; ++i) {
+        if (b->exec[i]) cudaGraphExecDestroy(b->exec[i]);
+        if (b->graph[i]) cudaGraphDestroy(b->graph[i]);
+    }
+    if (b->cap) cudaStreamDestroy(b->cap);
+    for (int i = 0; i < 3; ++i)
+        if (b->ev[i]) cudaEventDestroy(b->ev[i]);
+    if (b->done) cudaEventDestroy(b->done);
+    if (b->tallies_host) cudaFreeHost(b->tallies_host);
+    bz_ctx *ctx = b->ctx;
+    if (b->mem) {
+        dev_free(ctx, b->mem, b->bytes, 0);
+        cudaDeviceSynchronize();
+        ctx_release(ctx);
+    }
+    delete b;
 }
 
 bz_status bz_step_replay(bz_ctx *ctx, const bz_mixture *mix, const bz_swarm_config *cfg, int64_t n,

@@ -753,54 +753,136 @@ __device__ bool stage_tables(const uint8_t *src, uint8_t *dst, uint32_t bytes, u
 // ---------------------------------------------------------------------------
 // Kernels
 // ---------------------------------------------------------------------------
+// Re-stages the tables of a new mixture into shared memory through the
+// block's mbarrier (already initialised), waiting on phase `parity`.
+__device__ bool restage_tables(const uint8_t *src, uint8_t *dst, uint32_t bytes, uint32_t mb, uint32_t parity,
+                               uint32_t *err)
+{
+    if (threadIdx.x == 0) {
+        // the generic-proxy reads of the previous tables are ordered before
+        // the asynchronous copy that overwrites them
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile(
+            "{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(mb),
+            "r"(bytes)
+            : "memory");
+        const uint32_t d = smem_u32(dst);
+        for (uint32_t off = 0; off < bytes; off += kStageChunk) {
+            const uint32_t sz = (bytes - off < kStageChunk) ? bytes - off : kStageChunk;
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    d + off),
+                "l"(src + off), "r"(sz), "r"(mb)
+                : "memory");
+        }
+    }
+    bool ok = false;
+    for (uint32_t it = 0; it < kWaitLimit && !ok; ++it) ok = mbar_try_wait(mb, parity);
+    if (__syncthreads_or(!ok)) {
+        if (threadIdx.x == 0) atomicOr(err, BZ_ERR_STAGE_TIMEOUT);
+        bool done = ok;
+        for (uint32_t it = 0; it < kWaitLimit && !done; ++it) done = mbar_try_wait(mb, parity);
+        __syncthreads();
+        return false;
+    }
+    return true;
+}
+
+// The step kernel: one persistent launch over tiles (swarm, first particle,
+// count), ordered by mixture -- of many swarms (batched form) or of one
+// (bz_run_swarm), so that a swarm's results do not depend on how it was
+// launched.  A block takes a tile, copies that swarm's parameters into
+// shared memory, re-stages the tables only if the mixture differs from the
+// one it holds, runs the tile's electrons with per-lane refill (a lane that
+// finishes an electron takes the next one of the tile), and synchronises
+// before the next tile.
 template <typename R, bool CH_SMEM>
-__global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? BZ_SWARM_MIN_BLOCKS : 1) swarm_kernel(const RunArgs P)
+__global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? BZ_SWARM_MIN_BLOCKS : 1)
+    batch_kernel(const __grid_constant__ BatchArgs B)
 {
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ __align__(8) uint64_t mbar;
-    if (!stage_tables(P.blob, smem, P.stage_bytes, &mbar, P.err)) return;
-    const Tab<R> T = make_tab<R>(smem, P.blob, P.lay, CH_SMEM);
-    const Fld<R> F = make_fld<R>(P.f);
+    __shared__ __align__(16) RunArgs P;
+    __shared__ int s_tile;
+    __shared__ unsigned int s_next;
+    const uint32_t mb = smem_u32(&mbar);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    uint32_t phase = 0;
+    const uint8_t *staged = nullptr;
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    PState<R> s;
-    bool have = false, exhausted = false;
-    uint64_t slot = 0;
     for (;;) {
-        const unsigned need = __ballot_sync(FULL, !have);
-        if (need && !exhausted) {
-            const int leader = __ffs(need) - 1;
-            unsigned long long base = 0;
-            if (lane == leader) base = atomicAdd(P.counter, (unsigned long long)__popc(need));
-            base = __shfl_sync(FULL, base, leader);
-            if (base >= P.n) exhausted = true;
-            if (!have) {
-                const unsigned long long idx = base + __popc(need & ((1u << lane) - 1u));
-                if (idx < P.n) {
-                    init_particle<R>(T, P, F, s, P.id_offset + idx);
-                    slot = idx;
-                    have = true;
+        if (threadIdx.x == 0) {
+            s_tile = (int)atomicAdd(B.tile_counter, 1u);
+            s_next = 0;
+        }
+        __syncthreads();
+        const int ti = s_tile;
+        if (ti >= B.n_tiles) break;
+        uint4 tile;
+        if (B.tiles) {
+            tile = B.tiles[ti];
+        } else {
+            const uint64_t first = (uint64_t)ti * B.tile_size;
+            const uint64_t left = B.single.n - first;
+            tile = make_uint4(0u, (uint32_t)first, (uint32_t)(left < B.tile_size ? left : B.tile_size), 0u);
+        }
+        {
+            const uint32_t *src = (const uint32_t *)(B.desc ? B.desc + tile.x : &B.single);
+            uint32_t *dst = (uint32_t *)&P;
+            for (int i = threadIdx.x; i < (int)(sizeof(RunArgs) / 4); i += blockDim.x) dst[i] = src[i];
+        }
+        __syncthreads();
+        if (P.blob != staged) {
+            if (!restage_tables(P.blob, smem, P.stage_bytes, mb, phase, P.err)) return;
+            phase ^= 1u;
+            staged = P.blob;
+        }
+        const Tab<R> T = make_tab<R>(smem, P.blob, P.lay, CH_SMEM);
+        const Fld<R> F = make_fld<R>(P.f);
+        PState<R> s;
+        bool have = false, exhausted = false;
+        uint64_t slot = 0;
+        for (;;) {
+            const unsigned need = __ballot_sync(FULL, !have);
+            if (need && !exhausted) {
+                const int leader = __ffs(need) - 1;
+                unsigned int base = 0;
+                if (lane == leader) base = atomicAdd(&s_next, (unsigned int)__popc(need));
+                base = __shfl_sync(FULL, base, leader);
+                if (base >= tile.z) exhausted = true;
+                if (!have) {
+                    const unsigned int idx = base + __popc(need & ((1u << lane) - 1u));
+                    if (idx < tile.z) {
+                        slot = (uint64_t)tile.y + idx;
+                        init_particle<R>(T, P, F, s, P.id_offset + slot);
+                        have = true;
+                    }
+                }
+            }
+            if (!__any_sync(FULL, have)) break;
+#pragma unroll 1
+            for (int it = 0; it < 8 && have; ++it) {
+                if (s.k >= P.max_trials) {
+                    s.status = ST_STEPS;
+                    s.done = true;
+                    atomicOr(P.err, BZ_ERR_MAX_TRIALS);
+                } else {
+                    R ei, ef;
+                    trial<R, CH_SMEM>(T, F, P, s, ei, ef);
+                }
+                if (s.done) {
+                    write_particle<R>(P, s, slot);
+                    have = false;
                 }
             }
         }
-        if (!__any_sync(FULL, have)) break;
-        // up to 8 steps between refills: a lane that finishes idles for at
-        // most 7 steps of a run that lasts thousands
-#pragma unroll 1
-        for (int it = 0; it < 8 && have; ++it) {
-            if (s.k >= P.max_trials) {
-                s.status = ST_STEPS;
-                s.done = true;
-                atomicOr(P.err, BZ_ERR_MAX_TRIALS);
-            } else {
-                R ei, ef;
-                trial<R, CH_SMEM>(T, F, P, s, ei, ef);
-            }
-            if (s.done) {
-                write_particle<R>(P, s, slot);
-                have = false;
-            }
-        }
+        __syncthreads();
     }
 }
 
@@ -895,13 +977,13 @@ __device__ void block_group_reduce(double (&acc)[Q], double *out_block, uint64_t
     }
 }
 
-__global__ void __launch_bounds__(kTallyBlock) tally_pass1(const TallyArgs A)
+__device__ void tally_pass1_body(const TallyArgs &A, int bx, int nbx)
 {
     double acc[kQ1];
 #pragma unroll
     for (int q = 0; q < kQ1; ++q) acc[q] = 0.0;
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < A.n; i += stride) {
+    const uint64_t stride = (uint64_t)nbx * blockDim.x;
+    for (uint64_t i = (uint64_t)bx * blockDim.x + threadIdx.x; i < A.n; i += stride) {
         const double t = A.t[i];
         const uint32_t st = A.status[i];
         acc[17] += (st != ST_DONE && st != ST_TIME) ? 1.0 : 0.0;
@@ -927,14 +1009,14 @@ __global__ void __launch_bounds__(kTallyBlock) tally_pass1(const TallyArgs A)
         acc[16] += D;
         acc[18] += A.steps ? (double)A.steps[i] : 0.0;
     }
-    block_group_reduce<kQ1>(acc, A.part1 + (size_t)blockIdx.x * kGroups * kQ1, A.id_offset);
+    block_group_reduce<kQ1>(acc, A.part1 + (size_t)bx * kGroups * kQ1, A.id_offset);
 }
 
 // gsum layout: [g][0..kQ1) pass 1, [g][kQ1..kQ1+kQ2) pass 2, then summary
 // values at kGroups*(kQ1+kQ2): Wx, Wy, Wz, Wfx, Wfy, Wfz.
 constexpr int kGS = kQ1 + kQ2;
 
-__global__ void tally_mid(const TallyArgs A)
+__device__ void tally_mid_body(const TallyArgs &A)
 {
     const int g = threadIdx.x / kQ1, q = threadIdx.x % kQ1;
     if (threadIdx.x < kGroups * kQ1) {
@@ -966,15 +1048,15 @@ __global__ void tally_mid(const TallyArgs A)
     }
 }
 
-__global__ void __launch_bounds__(kTallyBlock) tally_pass2(const TallyArgs A)
+__device__ void tally_pass2_body(const TallyArgs &A, int bx, int nbx)
 {
     const double *S = A.gsum + kGroups * kGS;
     const double Wx = S[0], Wy = S[1], Wz = S[2], Fx = S[3], Fy = S[4], Fz = S[5];
     double acc[kQ2];
 #pragma unroll
     for (int q = 0; q < kQ2; ++q) acc[q] = 0.0;
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < A.n; i += stride) {
+    const uint64_t stride = (uint64_t)nbx * blockDim.x;
+    for (uint64_t i = (uint64_t)bx * blockDim.x + threadIdx.x; i < A.n; i += stride) {
         const double t = A.t[i];
         if (!(t > 0.0)) continue;
         const double x = A.x[i], y = A.y[i], z = A.z[i];
@@ -990,7 +1072,7 @@ __global__ void __launch_bounds__(kTallyBlock) tally_pass2(const TallyArgs A)
         acc[6] += fz * fz;
         acc[7] += fx * fx + fy * fy;
     }
-    block_group_reduce<kQ2>(acc, A.part2 + (size_t)blockIdx.x * kGroups * kQ2, A.id_offset);
+    block_group_reduce<kQ2>(acc, A.part2 + (size_t)bx * kGroups * kQ2, A.id_offset);
 }
 
 __device__ double group_se(const double *v, const bool *has, int G)
@@ -1010,7 +1092,7 @@ __device__ double group_se(const double *v, const bool *has, int G)
     return sqrt(s / (n - 1)) / sqrt((double)n);
 }
 
-__global__ void tally_final(const TallyArgs A)
+__device__ void tally_final_body(const TallyArgs &A)
 {
     const int g = threadIdx.x / kQ2, q = threadIdx.x % kQ2;
     if (threadIdx.x < kGroups * kQ2) {
@@ -1093,6 +1175,27 @@ __global__ void tally_final(const TallyArgs A)
     *A.out = o;
 }
 
+
+__global__ void __launch_bounds__(kTallyBlock) tally_pass1(const TallyArgs A) { tally_pass1_body(A, blockIdx.x, gridDim.x); }
+__global__ void tally_mid(const TallyArgs A) { tally_mid_body(A); }
+__global__ void __launch_bounds__(kTallyBlock) tally_pass2(const TallyArgs A) { tally_pass2_body(A, blockIdx.x, gridDim.x); }
+__global__ void tally_final(const TallyArgs A) { tally_final_body(A); }
+
+// Many swarms at once: blockIdx.y (passes) or blockIdx.x (the one-block
+// steps) selects the swarm's arguments.
+__global__ void __launch_bounds__(kTallyBlock) tally_pass1_multi(const TallyArgs *As)
+{
+    const TallyArgs &A = As[blockIdx.y];
+    if ((int)blockIdx.x < A.blocks) tally_pass1_body(A, blockIdx.x, A.blocks);
+}
+__global__ void tally_mid_multi(const TallyArgs *As) { tally_mid_body(As[blockIdx.x]); }
+__global__ void __launch_bounds__(kTallyBlock) tally_pass2_multi(const TallyArgs *As)
+{
+    const TallyArgs &A = As[blockIdx.y];
+    if ((int)blockIdx.x < A.blocks) tally_pass2_body(A, blockIdx.x, A.blocks);
+}
+__global__ void tally_final_multi(const TallyArgs *As) { tally_final_body(As[blockIdx.x]); }
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -1105,16 +1208,16 @@ static cudaError_t prep_smem(K kernel, size_t smem)
     return cudaSuccess;
 }
 
-cudaError_t launch_swarm(int precision, bool ch_smem, const RunArgs &a, int grid, int block, cudaStream_t s)
+cudaError_t launch_batch(int precision, bool ch_smem, const BatchArgs &a, size_t smem, int grid, int block,
+                         cudaStream_t s)
 {
     if (block != kBlock) return cudaErrorInvalidValue;
-    const size_t smem = a.stage_bytes;
     cudaError_t e;
 #define BZ_LAUNCH(R, C)                                                        \
     do {                                                                       \
-        e = prep_smem(swarm_kernel<R, C>, smem);                               \
+        e = prep_smem(batch_kernel<R, C>, smem);                               \
         if (e != cudaSuccess) return e;                                        \
-        swarm_kernel<R, C><<<grid, block, smem, s>>>(a);                       \
+        batch_kernel<R, C><<<grid, block, smem, s>>>(a);                       \
     } while (0)
     if (precision == 64) {
         if (ch_smem) BZ_LAUNCH(double, true); else BZ_LAUNCH(double, false);
@@ -1122,6 +1225,34 @@ cudaError_t launch_swarm(int precision, bool ch_smem, const RunArgs &a, int grid
         if (ch_smem) BZ_LAUNCH(float, true); else BZ_LAUNCH(float, false);
     }
 #undef BZ_LAUNCH
+    return cudaGetLastError();
+}
+
+int batch_occupancy(int precision, bool ch_smem, int block, size_t smem)
+{
+    int n = 0;
+    cudaError_t e;
+#define BZ_OCC(R, C)                                                                        \
+    do {                                                                                    \
+        prep_smem(batch_kernel<R, C>, smem);                                                \
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<R, C>, block, smem); \
+    } while (0)
+    if (precision == 64) {
+        if (ch_smem) BZ_OCC(double, true); else BZ_OCC(double, false);
+    } else {
+        if (ch_smem) BZ_OCC(float, true); else BZ_OCC(float, false);
+    }
+#undef BZ_OCC
+    return e == cudaSuccess ? n : 0;
+}
+
+cudaError_t launch_tallies_multi(const TallyArgs *args_dev, int n_swarms, int max_blocks, cudaStream_t s)
+{
+    if (n_swarms <= 0) return cudaSuccess;
+    tally_pass1_multi<<<dim3(max_blocks, n_swarms), kTallyBlock, 0, s>>>(args_dev);
+    tally_mid_multi<<<n_swarms, kGroups * kQ1, 0, s>>>(args_dev);
+    tally_pass2_multi<<<dim3(max_blocks, n_swarms), kTallyBlock, 0, s>>>(args_dev);
+    tally_final_multi<<<n_swarms, kGroups * kQ2, 0, s>>>(args_dev);
     return cudaGetLastError();
 }
 
@@ -1143,30 +1274,6 @@ cudaError_t launch_replay(int precision, bool ch_smem, const ReplayArgs &a, int 
     }
 #undef BZ_LAUNCH
     return cudaGetLastError();
-}
-
-int swarm_occupancy(int precision, bool ch_smem, int block, size_t smem)
-{
-    int n = 0;
-    cudaError_t e;
-    if (precision == 64) {
-        if (ch_smem) {
-            prep_smem(swarm_kernel<double, true>, smem);
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, swarm_kernel<double, true>, block, smem);
-        } else {
-            prep_smem(swarm_kernel<double, false>, smem);
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, swarm_kernel<double, false>, block, smem);
-        }
-    } else {
-        if (ch_smem) {
-            prep_smem(swarm_kernel<float, true>, smem);
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, swarm_kernel<float, true>, block, smem);
-        } else {
-            prep_smem(swarm_kernel<float, false>, smem);
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, swarm_kernel<float, false>, block, smem);
-        }
-    }
-    return e == cudaSuccess ? n : 0;
 }
 
 cudaError_t launch_philox(int64_t n, const uint32_t *ctr, uint64_t key, uint32_t *out, cudaStream_t s)

@@ -73,13 +73,27 @@ struct TallyArgs {
     bz_tallies *out;         // device
 };
 
+// Batched launch: tiles (x = swarm, y = first particle, z = count) over the
+// per-swarm parameters desc[] (RunArgs without the counter).
+struct BatchArgs {
+    const RunArgs *desc;     // null: one swarm, described by `single`
+    const uint4 *tiles;      // null: tiles of tile_size electrons over `single`
+    int32_t n_tiles;
+    uint32_t tile_size;
+    unsigned int *tile_counter;
+    RunArgs single;
+};
+
 // Launch helpers (kernels.cu).  precision is 32 or 64.
-cudaError_t launch_swarm(int precision, bool ch_smem, const RunArgs &a, int grid, int block, cudaStream_t s);
 cudaError_t launch_replay(int precision, bool ch_smem, const ReplayArgs &a, int grid, int block, cudaStream_t s);
 cudaError_t launch_philox(int64_t n, const uint32_t *ctr, uint64_t key, uint32_t *out, cudaStream_t s);
 cudaError_t launch_tallies(const TallyArgs &a, cudaStream_t s);
-int tally_blocks(uint64_t n, int sm_count);
+cudaError_t launch_batch(int precision, bool ch_smem, const BatchArgs &a, size_t smem, int grid, int block,
+                         cudaStream_t s);
 // Blocks of `block` threads that fit on one SM with `smem` bytes of tables.
-int swarm_occupancy(int precision, bool ch_smem, int block, size_t smem);
+int batch_occupancy(int precision, bool ch_smem, int block, size_t smem);
+// Tallies of n_swarms swarms; args_dev is a device array of TallyArgs.
+cudaError_t launch_tallies_multi(const TallyArgs *args_dev, int n_swarms, int max_blocks, cudaStream_t s);
+int tally_blocks(uint64_t n, int sm_count);
 
 }  // namespace bz

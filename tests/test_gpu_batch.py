@@ -1,0 +1,80 @@
+"""Batched swarms (one persistent launch over many swarms, CUDA graph):
+every swarm's results equal those of its own bz_run_swarm."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1901_08140_gb300 import bz
+from paper_1901_08140_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1901_08140_gb300 import build as B
+    B.build()
+    c = bz.Context(0)
+    yield c
+    c.close()
+
+
+def _items(ctx):
+    gases = {"ar": [W.argon_like()], "arco2": W.ar_co2_mixture(), "r1": W.batched_swarms(count=3)[1].gases,
+             "r2": W.batched_swarms(count=3)[2].gases}
+    mixes = {k: bz.Mixture(ctx, g) for k, g in gases.items()}
+    spec = [("ar", 1, 10.0, 0.0, 0.0, 0), ("arco2", 33, 100.0, 1.0, math.pi / 2, 0), ("r1", 1000, 50.0, 0.5, 1.0, 2),
+            ("ar", 5000, 300.0, 0.0, 0.0, 2), ("r2", 20000, 5.0, 1.5, 2.5, 2), ("arco2", 4097, 20.0, 0.0, 0.0, 0),
+            ("r1", 257, 700.0, 0.0, 0.0, 2), ("ar", 3000, 1.0, 2.0, 0.3, 2)]
+    items = []
+    for i, (mk, n, eon, b, ang, mode) in enumerate(spec):
+        cfg = bz.make_config(n_electrons=n, real_collisions=60, e_over_n_Td=eon, b_T=b, b_angle_rad=ang,
+                             seed=W.swarm_seed(900 + i), trial_mode=mode, id_offset=7 * i)
+        items.append((mixes[mk], cfg))
+    return items
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_batch_equals_individual_runs(ctx, use_graph):
+    items = _items(ctx)
+    batch = bz.Batch(ctx, [m for m, _ in items], [c for _, c in items], tile_particles=512, use_graph=use_graph)
+    batch.launch()
+    bt = batch.tallies()
+    for i, (mix, cfg) in enumerate(items):
+        sw = bz.run_swarm(ctx, mix, cfg)
+        t = sw.tallies()
+        p = sw.particles()
+        sw.close()
+        q = batch.particles(i)
+        for k in ["x", "y", "z", "t", "sum_e", "sum_e2", "n_real", "n_null", "n_fail", "n_ion", "n_att", "steps"]:
+            assert np.array_equal(p[k], q[k]), (i, k)
+        for k in ["W", "eps", "D_L", "D_T", "W_se", "alpha", "efficiency"]:
+            assert bt[i][k] == t[k] or (math.isnan(t[k]) and math.isnan(bt[i][k])), (i, k)
+        assert bt[i]["n_real"] == t["n_real"] and bt[i]["error_flags"] == 0
+    km, tm = batch.timing()
+    assert km > 0 and tm > 0
+    batch.close()
+
+
+def test_batch_relaunch_is_reproducible(ctx):
+    items = _items(ctx)
+    batch = bz.Batch(ctx, [m for m, _ in items], [c for _, c in items])
+    batch.launch()
+    a = batch.tallies()
+    pa = batch.particles(4)
+    batch.launch()
+    b = batch.tallies()
+    pb = batch.particles(4)
+    assert all(x["W"] == y["W"] and x["n_null"] == y["n_null"] for x, y in zip(a, b))
+    assert np.array_equal(pa["z"], pb["z"])
+    batch.close()
+
+
+def test_batch_rejects_mixed_precision(ctx):
+    items = _items(ctx)[:2]
+    cfgs = [c for _, c in items]
+    cfgs[1].precision = 64
+    with pytest.raises(bz.BzError) as ei:
+        bz.Batch(ctx, [m for m, _ in items], cfgs)
+    assert ei.value.status == bz.BZ_EINVAL
