@@ -207,8 +207,13 @@ def run_ours(args):
             plain_reals += sw.tallies()["n_real"]
             sw.close()
 
-    # ---- batched: every swarm in one persistent launch, replayed from a CUDA graph
-    batch = bz.Batch(ctx, [mix] * len(cfgs), cfgs)
+    # ---- batched: every swarm in one persistent launch, replayed from a CUDA graph,
+    # with the launch options the autotuner picks (cached per GPU and workload class)
+    from paper_1901_08140_gb300 import autotune
+    choice = autotune.tune(ctx, [mix] * len(cfgs), cfgs)
+    bcfgs = autotune.apply(cfgs, choice)
+    batch = bz.Batch(ctx, [mix] * len(cfgs), bcfgs, tile_particles=choice["tile_particles"],
+                     blocks_per_sm=choice["blocks_per_sm"])
 
     def batch_step():
         batch.launch(stream)
@@ -258,7 +263,8 @@ def run_ours(args):
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         m2 = bz.Mixture(ctx, specs[0].gases)
-        b2 = bz.Batch(ctx, [m2] * len(cfgs), cfgs)
+        b2 = bz.Batch(ctx, [m2] * len(cfgs), bcfgs, tile_particles=choice["tile_particles"],
+                      blocks_per_sm=choice["blocks_per_sm"])
         b2.launch(stream)
         e_reals = sum(t["n_real"] for t in b2.tallies())
         torch.cuda.synchronize(dev)
@@ -293,7 +299,8 @@ def run_ours(args):
                                + (f" (point {args.only_point} only)" if args.only_point >= 0 else ""),
                    "mode": "batched: all swarms in one persistent launch replayed from a CUDA graph",
                    "swarms": len(specs), "electrons_per_swarm": args.electrons, "real_collisions": args.collisions,
-                   "l2": "flushed between steps (256 MiB write)", "parallelism": f"dp{world} (particle ids)"},
+                   "l2": "flushed between steps (256 MiB write)", "parallelism": f"dp{world} (particle ids)",
+                   "autotuned": {k: choice[k] for k in ("window_c", "tile_particles", "blocks_per_sm", "cached")}},
         "plain": {"value": plain_value, "ms_per_step": p_max / args.steps,
                   "mode": "one persistent launch per swarm, back to back on one stream"},
         "batched_over_plain": value / plain_value,

@@ -1,0 +1,110 @@
+"""Autotuner of the batched step launch.
+
+Picks, for a batch of swarms, the launch options that maximise real
+collisions per second of device time: the trial-frequency window length
+(``window_c``, windowed mode only; any value samples the same process), the
+tile size and the resident blocks per SM.  It times candidates by
+coordinate descent on a reduced copy of the batch -- every swarm keeps its
+electrons, mixture and fields but runs fewer real collisions per electron,
+so tiles and load balance look like the full batch's -- and caches the
+result in a JSON file keyed by the GPU name and a signature of the workload
+(swarm count, electron count and trial-mode mix), so later runs of the same
+class skip the search.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import json
+import math
+import os
+from typing import Dict, List, Optional, Sequence
+
+from . import bz
+
+CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_autotune_cache.json")
+
+DEFAULT = {"window_c": 2.0, "tile_particles": 0, "blocks_per_sm": 0}
+WINDOW_C = [1.0, 1.5, 2.0, 3.0]
+TILES = [0, 512, 1024, 2048, 4096]
+BLOCKS = [0, 2, 1]
+
+
+def signature(cfgs: Sequence[bz.bz_swarm_config]) -> str:
+    """Workload class: number of swarms, log2 of the total electrons, trial modes."""
+    total = sum(int(c.n_electrons) for c in cfgs)
+    modes = sorted({int(c.trial_mode) for c in cfgs})
+    prec = sorted({int(c.precision) for c in cfgs})
+    return f"n{len(cfgs)}-e{int(math.log2(max(total, 1)))}-m{'.'.join(map(str, modes))}-p{'.'.join(map(str, prec))}"
+
+
+def load_cache(path: str = CACHE) -> Dict[str, dict]:
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def store_cache(cache: Dict[str, dict], path: str = CACHE) -> None:
+    tmp = path + f".tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(cache, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def _copy_cfg(c: bz.bz_swarm_config, **over) -> bz.bz_swarm_config:
+    d = bz.bz_swarm_config()
+    C.memmove(C.byref(d), C.byref(c), C.sizeof(bz.bz_swarm_config))
+    for k, v in over.items():
+        setattr(d, k, v)
+    return d
+
+
+def apply(cfgs: Sequence[bz.bz_swarm_config], choice: dict) -> List[bz.bz_swarm_config]:
+    """Configurations with the chosen window length (windowed swarms only)."""
+    return [_copy_cfg(c, window_c=float(choice["window_c"])) if c.trial_mode == bz.BZ_TRIAL_WINDOW else c
+            for c in cfgs]
+
+
+def _measure(ctx, mixtures, cfgs, choice, repeats=2) -> float:
+    """Real collisions per millisecond of step-kernel time."""
+    b = bz.Batch(ctx, mixtures, apply(cfgs, choice), tile_particles=choice["tile_particles"],
+                 blocks_per_sm=choice["blocks_per_sm"])
+    best = 0.0
+    for _ in range(repeats):
+        b.launch()
+        reals = sum(t["n_real"] for t in b.tallies(check=False))
+        ms, _ = b.timing()
+        best = max(best, reals / max(ms, 1e-6))
+    b.close()
+    return best
+
+
+def tune(ctx, mixtures: Sequence, cfgs: Sequence[bz.bz_swarm_config], scale: float = 0.1,
+         use_cache: bool = True, cache_path: str = CACHE, gpu_name: Optional[str] = None) -> dict:
+    """Best launch options for this batch (cached per GPU and workload class)."""
+    if gpu_name is None:
+        import torch
+        gpu_name = torch.cuda.get_device_name(ctx.device)
+    key = f"{gpu_name}|{signature(cfgs)}"
+    cache = load_cache(cache_path) if use_cache else {}
+    if key in cache:
+        return dict(cache[key], cached=True)
+    small = [_copy_cfg(c, real_collisions=max(20, int(c.real_collisions * scale))) for c in cfgs]
+    best = dict(DEFAULT)
+    best_rate = _measure(ctx, mixtures, small, best)
+    windowed = any(c.trial_mode == bz.BZ_TRIAL_WINDOW for c in cfgs)
+    for name, values in (("window_c", WINDOW_C if windowed else []), ("tile_particles", TILES),
+                         ("blocks_per_sm", BLOCKS)):
+        for v in values:
+            if v == best[name]:
+                continue
+            cand = dict(best, **{name: v})
+            r = _measure(ctx, mixtures, small, cand)
+            if r > best_rate * 1.01:
+                best, best_rate = cand, r
+    best["rate_per_ms"] = best_rate
+    cache[key] = best
+    if use_cache:
+        store_cache(cache, cache_path)
+    return dict(best, cached=False)

@@ -1,0 +1,47 @@
+"""Autotuner: workload signature, cache round trip, and (GPU) a tuned batch."""
+import pytest
+
+from paper_1901_08140_gb300 import autotune, bz
+from paper_1901_08140_gb300 import build as B
+from paper_1901_08140_gb300 import workloads as W
+
+
+@pytest.fixture(scope="module")
+def L():
+    B.build()
+    return bz.lib()
+
+
+def test_signature_and_apply(L):
+    cfgs = [bz.make_config(n_electrons=1000 * (i + 1), real_collisions=100, e_over_n_Td=10.0,
+                           trial_mode=bz.BZ_TRIAL_WINDOW if i % 2 else bz.BZ_TRIAL_LAZY) for i in range(4)]
+    sig = autotune.signature(cfgs)
+    assert sig == "n4-e13-m0.2-p32"
+    out = autotune.apply(cfgs, {"window_c": 3.0, "tile_particles": 0, "blocks_per_sm": 0})
+    assert [c.window_c for c in out] == [0.0, 3.0, 0.0, 3.0]
+    assert [c.window_c for c in cfgs] == [0.0, 0.0, 0.0, 0.0]   # inputs untouched
+
+
+def test_cache_round_trip(tmp_path, L):
+    path = str(tmp_path / "cache.json")
+    assert autotune.load_cache(path) == {}
+    autotune.store_cache({"gpu|sig": {"window_c": 1.5, "tile_particles": 512, "blocks_per_sm": 2}}, path)
+    assert autotune.load_cache(path)["gpu|sig"]["tile_particles"] == 512
+
+
+@pytest.mark.gpu
+def test_tune_a_small_batch(tmp_path, L):
+    ctx = bz.Context(0)
+    specs = W.argon_sweep(n_electrons=20000, real_collisions=200, points=4)
+    mix = bz.Mixture(ctx, specs[0].gases)
+    cfgs = [bz.config_from_spec(s, trial_mode=bz.BZ_TRIAL_WINDOW) for s in specs]
+    path = str(tmp_path / "c.json")
+    choice = autotune.tune(ctx, [mix] * 4, cfgs, cache_path=path)
+    assert choice["cached"] is False and choice["window_c"] in autotune.WINDOW_C
+    again = autotune.tune(ctx, [mix] * 4, cfgs, cache_path=path)
+    assert again["cached"] is True and again["window_c"] == choice["window_c"]
+    b = bz.Batch(ctx, [mix] * 4, autotune.apply(cfgs, choice), tile_particles=choice["tile_particles"],
+                 blocks_per_sm=choice["blocks_per_sm"])
+    b.launch()
+    assert all(t["n_real"] == 20000 * 200 and t["error_flags"] == 0 for t in b.tallies())
+    b.close()
