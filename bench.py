@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--only-point", type=int, default=-1, help="run one E/N point of the sweep (profiling case)")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-rates", default="250,1000,2000", help="Poisson arrival rates [req/s] of the serving run")
+    ap.add_argument("--serve-seconds", type=float, default=1.0, help="arrival window of each serving run")
     ap.add_argument("--trial", choices=["window", "lazy"], default="window",
                     help="trial frequency: exact windowed local bound (default) or the constant maximum")
     return ap.parse_args()
@@ -172,6 +175,36 @@ def _timed(stream, flush, steps, fn, world, dev):
     return total, outs
 
 
+def serving_runs(ctx, rates, seconds, collisions=100, pool=64, streams=16):
+    """Continuous-batching request loop under Poisson arrivals: swarm sizes,
+    mixtures and fields of the batched workload (a pool of compiled
+    mixtures), I real collisions per request, windowed trial frequency."""
+    from paper_1901_08140_gb300 import bz, serving
+    from paper_1901_08140_gb300 import workloads as W
+    import numpy as np
+    specs = W.batched_swarms(count=pool, real_collisions=collisions)
+    mixes = [bz.Mixture(ctx, s.gases) for s in specs]
+    backend = serving.GpuBackend(ctx, n_streams=streams)
+    out = []
+    for k, rate in enumerate(rates):
+        n = max(1, int(rate * seconds))
+        arr = serving.poisson_arrivals(rate, n, seed=100 + k)
+        rng = np.random.default_rng(200 + k)
+        reqs = []
+        for i in range(n):
+            j = int(rng.integers(pool))
+            cfg = bz.config_from_spec(specs[j], trial_mode=bz.BZ_TRIAL_WINDOW, seed=W.swarm_seed(10 ** 6 + 10 ** 4 * k + i))
+            reqs.append(serving.Request(i, mixes[j], cfg, arrival=float(arr[i]), n_electrons=int(cfg.n_electrons)))
+        srv = serving.Server(backend, memory_budget=60e9)
+        done = srv.run(reqs, realtime=True)
+        summ = serving.latency_summary(done)
+        offered = sum(r.n_electrons for r in reqs) * collisions / arr[-1] if n > 1 else float("nan")
+        summ.update({"rate_req_s": rate, "offered_real_collisions_per_s": offered,
+                     "max_concurrent": srv.max_concurrent})
+        out.append(summ)
+    return out
+
+
 def run_ours(args):
     import torch
     world, rank, local = dist()
@@ -284,6 +317,10 @@ def run_ours(args):
                 "kernel": "batch_kernel<float,true>",
                 "note": f"algorithmic thread-ops ({ALG_OPS_PER_TRIAL}/step + {ALG_OPS_PER_REAL}/real) over "
                         f"SMs x 128 lanes x median SM clock {sm_mhz:.0f} MHz"}
+    serve = None
+    if not args.no_serving and rank == 0:
+        rates = [float(x) for x in args.serve_rates.split(",") if x]
+        serve = serving_runs(ctx, rates, args.serve_seconds)
     if rank != 0:
         return
     cpu = None
@@ -310,6 +347,10 @@ def run_ours(args):
         "max_rel_se_W": max(w_err) if w_err else None,
         "trial_frequency": args.trial,
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
+        "serving": serve,
+        "p99_swarm_latency_ms": (min((x["p99_ms"] for x in serve
+                                      if x["real_collisions_per_s"] >= 0.9 * x["offered_real_collisions_per_s"]),
+                                     default=None) if serve else None),
     }
     print(json.dumps(out), flush=True)
 

@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -19,6 +20,14 @@ struct bz_ctx {
     bool custom_alloc;
     int sm_count;
     int smem_optin;
+    // pinned host slots for swarm tallies, allocated in chunks and reused
+    std::mutex pin_mu;
+    std::vector<bz_tallies *> pin_free;
+    std::vector<void *> pin_chunks;
+    ~bz_ctx()
+    {
+        for (void *p : pin_chunks) cudaFreeHost(p);
+    }
 };
 
 struct bz_mixture {
@@ -113,6 +122,28 @@ uint32_t tile_size_for(uint64_t n, uint64_t blocks, uint64_t per_block)
 }
 
 void ctx_retain(bz_ctx *c) { c->refs.fetch_add(1); }
+
+bz_tallies *pinned_slot(bz_ctx *c)
+{
+    std::lock_guard<std::mutex> lock(c->pin_mu);
+    if (c->pin_free.empty()) {
+        const int chunk = 256;
+        void *p = nullptr;
+        if (cudaMallocHost(&p, sizeof(bz_tallies) * chunk) != cudaSuccess) return nullptr;
+        c->pin_chunks.push_back(p);
+        for (int i = chunk - 1; i >= 0; --i) c->pin_free.push_back((bz_tallies *)p + i);
+    }
+    bz_tallies *t = c->pin_free.back();
+    c->pin_free.pop_back();
+    return t;
+}
+
+void pinned_release(bz_ctx *c, bz_tallies *t)
+{
+    if (!t) return;
+    std::lock_guard<std::mutex> lock(c->pin_mu);
+    c->pin_free.push_back(t);
+}
 
 void ctx_release(bz_ctx *c)
 {
@@ -389,10 +420,12 @@ bz_status bz_run_swarm(bz_ctx *ctx, const bz_mixture *mix, const bz_swarm_config
     unsigned long long *counter = (unsigned long long *)(M + o_ctr);
     s->err = (uint32_t *)(M + o_ctr + 8);
     s->tallies_dev = (bz_tallies *)(M + o_tal);
-    if ((e = cudaMallocHost(&s->tallies_host, sizeof(bz_tallies))) != cudaSuccess ||
-        (e = cudaEventCreateWithFlags(&s->done, cudaEventDisableTiming)) != cudaSuccess) {
+    s->tallies_host = pinned_slot(ctx);
+    if (!s->tallies_host) e = cudaErrorMemoryAllocation;
+    else e = cudaEventCreateWithFlags(&s->done, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
         dev_free(ctx, s->mem, s->bytes, s->stream);
-        if (s->tallies_host) cudaFreeHost(s->tallies_host);
+        pinned_release(ctx, s->tallies_host);
         if (s->done) cudaEventDestroy(s->done);
         delete s;
         ctx_release(ctx);
@@ -498,7 +531,7 @@ void bz_destroy_swarm(bz_swarm *sw)
     if (sw->done) cudaEventSynchronize(sw->done);
     else cudaStreamSynchronize(sw->stream);
     dev_free(sw->ctx, sw->mem, sw->bytes, sw->stream);
-    if (sw->tallies_host) cudaFreeHost(sw->tallies_host);
+    pinned_release(sw->ctx, sw->tallies_host);
     if (sw->done) cudaEventDestroy(sw->done);
     for (int i = 0; i < 3; ++i)
         if (sw->ev[i]) cudaEventDestroy(sw->ev[i]);

@@ -1,0 +1,113 @@
+"""Serving loop: host-side admission and ordering with a fake backend (CPU),
+and on the GPU each request's result alone and in the mix."""
+import numpy as np
+import pytest
+
+from paper_1901_08140_gb300 import serving as S
+
+
+class FakeBackend:
+    """Completes a launch a fixed number of polls after it starts."""
+
+    def __init__(self, slots=3, polls=5):
+        self._slots = slots
+        self.polls = polls
+        self.log = []
+
+    @property
+    def slots(self):
+        return self._slots
+
+    def launch(self, req, slot):
+        self.log.append(("launch", req.rid, slot))
+        return {"req": req, "left": self.polls}
+
+    def poll(self, h):
+        h["left"] -= 1
+        if h["left"] > 0:
+            return None
+        return {"n_real": h["req"].n_electrons, "status": 0}
+
+    def release(self, h):
+        self.log.append(("release", h["req"].rid))
+
+
+class Clock:
+    def __init__(self):
+        self.t = 0.0
+
+    def __call__(self):
+        self.t += 1e-3
+        return self.t
+
+
+def _reqs(sizes, arrivals):
+    return [S.Request(i, None, None, arrival=a, n_electrons=n) for i, (n, a) in enumerate(zip(sizes, arrivals))]
+
+
+def test_admission_respects_slots_and_budget():
+    be = FakeBackend(slots=3)
+    budget = S.BYTES_PER_ELECTRON * 2500 + 2 * S.BYTES_PER_SWARM
+    srv = S.Server(be, memory_budget=budget, clock=Clock(), idle_sleep=0)
+    done = srv.run(_reqs([1000, 1000, 1000, 500, 2000], [0, 0, 0, 0, 0]), realtime=False)
+    assert sorted(r.rid for r in done) == [0, 1, 2, 3, 4]
+    assert srv.max_concurrent <= 3
+    assert srv.peak_in_use <= budget
+    # admission is in arrival order: request 3 starts only after request 0 or 1 ends
+    launches = [e for e in be.log if e[0] == "launch"]
+    assert [e[1] for e in launches] == [0, 1, 2, 3, 4]
+    assert all(r.done > r.admitted >= r.arrival for r in done)
+
+
+def test_requests_arriving_while_others_run_are_admitted_at_once():
+    be = FakeBackend(slots=4, polls=50)
+    srv = S.Server(be, memory_budget=1e12, clock=Clock(), idle_sleep=0)
+    done = srv.run(_reqs([10, 10, 10], [0.0, 0.005, 0.010]), realtime=True)
+    by = {r.rid: r for r in done}
+    # the later requests start before the first one finished
+    assert by[1].admitted < by[0].done and by[2].admitted < by[0].done
+    assert srv.max_concurrent == 3
+
+
+def test_oversized_request_is_rejected():
+    srv = S.Server(FakeBackend(), memory_budget=1e6, clock=Clock(), idle_sleep=0)
+    with pytest.raises(ValueError):
+        srv.run(_reqs([10 ** 7], [0.0]))
+
+
+def test_poisson_arrivals_and_summary():
+    a = S.poisson_arrivals(1000.0, 20000, seed=3)
+    gaps = np.diff(a)
+    assert abs(gaps.mean() - 1e-3) < 3e-5 and np.all(gaps > 0)
+    rs = _reqs([1] * 3, [0.0, 0.1, 0.2])
+    for r, d in zip(rs, [0.05, 0.2, 0.4]):
+        r.done = d
+        r.tallies = {"n_real": 10}
+    s = S.latency_summary(rs)
+    assert s["requests"] == 3 and abs(s["p50_ms"] - 100.0) < 1e-9
+
+
+@pytest.mark.gpu
+def test_results_are_the_same_alone_and_in_the_mix():
+    from paper_1901_08140_gb300 import build as B
+    B.build()
+    from paper_1901_08140_gb300 import bz
+    from paper_1901_08140_gb300 import workloads as W
+    ctx = bz.Context(0)
+    specs = W.batched_swarms(count=24, real_collisions=100, max_electrons=30000)
+    mixes = [bz.Mixture(ctx, s.gases) for s in specs]
+    cfgs = [bz.config_from_spec(s, trial_mode=bz.BZ_TRIAL_WINDOW if i % 2 else bz.BZ_TRIAL_LAZY)
+            for i, s in enumerate(specs)]
+    alone = []
+    for m, c in zip(mixes, cfgs):
+        sw = bz.run_swarm(ctx, m, c)
+        alone.append(sw.tallies())
+        sw.close()
+    reqs = [S.Request(i, m, c, arrival=0.0, n_electrons=int(c.n_electrons)) for i, (m, c) in enumerate(zip(mixes, cfgs))]
+    srv = S.Server(S.GpuBackend(ctx, n_streams=8), memory_budget=60e9)
+    done = srv.run(reqs, realtime=False)
+    assert srv.max_concurrent > 1
+    for r in done:
+        a = alone[r.rid]
+        for k in ("W", "eps", "D_L", "D_T", "n_real", "n_null", "n_window"):
+            assert r.tallies[k] == a[k], (r.rid, k)
