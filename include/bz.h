@@ -278,6 +278,8 @@ bz_status bz_create_batch(bz_ctx *ctx, int32_t n, const bz_mixture *const *mixtu
 /* Runs the batch on `stream` (asynchronous); may be called again after the
  * previous run finished (same results: counters are keyed by the seeds). */
 bz_status bz_launch_batch(bz_batch *b, void *stream);
+/* Non-blocking: BZ_ENOTREADY while the last launch runs, BZ_OK when done. */
+bz_status bz_batch_query(bz_batch *b);
 /* Waits for the last launch and copies the n swarms' tallies into out[n]. */
 bz_status bz_batch_read_tallies(bz_batch *b, bz_tallies *out);
 /* Waits, then copies swarm i's per-particle results (as bz_read_particles). */

@@ -140,6 +140,7 @@ SIGNATURES = {
     "bz_create_batch": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_void_p), C.POINTER(bz_swarm_config),
                                   C.POINTER(bz_batch_opts), C.POINTER(C.c_void_p)]),
     "bz_launch_batch": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "bz_batch_query": (C.c_int, [C.c_void_p]),
     "bz_batch_read_tallies": (C.c_int, [C.c_void_p, C.POINTER(bz_tallies)]),
     "bz_batch_read_particles": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(bz_particles)]),
     "bz_batch_timing": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
@@ -196,6 +197,7 @@ def bz_destroy_swarm(sw): return lib().bz_destroy_swarm(sw)
 def bz_swarm_timing(sw, a, b): return lib().bz_swarm_timing(sw, a, b)
 def bz_create_batch(*a): return lib().bz_create_batch(*a)
 def bz_launch_batch(b, stream): return lib().bz_launch_batch(b, stream)
+def bz_batch_query(b): return lib().bz_batch_query(b)
 def bz_batch_read_tallies(b, out): return lib().bz_batch_read_tallies(b, out)
 def bz_batch_read_particles(b, i, out): return lib().bz_batch_read_particles(b, i, out)
 def bz_batch_timing(b, a, c): return lib().bz_batch_timing(b, a, c)
@@ -437,6 +439,13 @@ class Batch:
 
     def launch(self, stream=None):
         _check(lib().bz_launch_batch(self.h, C.c_void_p(_stream_handle(stream))))
+
+    def ready(self) -> bool:
+        st = lib().bz_batch_query(self.h)
+        if st == BZ_ENOTREADY:
+            return False
+        _check(st)
+        return True
 
     def tallies(self, check: bool = True):
         out = (bz_tallies * self.n)()

@@ -24,9 +24,11 @@ struct bz_ctx {
     std::mutex pin_mu;
     std::vector<bz_tallies *> pin_free;
     std::vector<void *> pin_chunks;
+    std::vector<std::pair<size_t, void *>> pin_blocks;  // free pinned blocks (capacity, pointer) for batches
     ~bz_ctx()
     {
         for (void *p : pin_chunks) cudaFreeHost(p);
+        for (auto &b : pin_blocks) cudaFreeHost(b.second);
     }
 };
 
@@ -70,6 +72,7 @@ struct bz_batch {
     uint32_t *errs;
     bz::TallyArgs *targs;
     bz_tallies *tallies_dev, *tallies_host;
+    size_t tallies_cap;
     cudaStream_t cap;
     cudaGraph_t graph[2];      // [0]: counters + step kernel, [1]: tallies + copy to the host
     cudaGraphExec_t exec[2];
@@ -143,6 +146,34 @@ void pinned_release(bz_ctx *c, bz_tallies *t)
     if (!t) return;
     std::lock_guard<std::mutex> lock(c->pin_mu);
     c->pin_free.push_back(t);
+}
+
+// Pinned host block of at least `bytes` (power-of-two capacity), reused.
+void *pinned_block(bz_ctx *c, size_t bytes, size_t *cap)
+{
+    size_t want = 4096;
+    while (want < bytes) want <<= 1;
+    {
+        std::lock_guard<std::mutex> lock(c->pin_mu);
+        for (size_t i = 0; i < c->pin_blocks.size(); ++i)
+            if (c->pin_blocks[i].first == want) {
+                void *p = c->pin_blocks[i].second;
+                c->pin_blocks.erase(c->pin_blocks.begin() + i);
+                *cap = want;
+                return p;
+            }
+    }
+    void *p = nullptr;
+    if (cudaMallocHost(&p, want) != cudaSuccess) return nullptr;
+    *cap = want;
+    return p;
+}
+
+void pinned_block_release(bz_ctx *c, void *p, size_t cap)
+{
+    if (!p) return;
+    std::lock_guard<std::mutex> lock(c->pin_mu);
+    c->pin_blocks.emplace_back(cap, p);
 }
 
 void ctx_release(bz_ctx *c)
@@ -719,10 +750,13 @@ bz_status bz_create_batch(bz_ctx *ctx, int32_t n, const bz_mixture *const *mixtu
     e = cudaMemcpy(b->desc, desc.data(), sizeof(bz::RunArgs) * n, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->tiles, tiles.data(), sizeof(uint4) * tiles.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->targs, targs.data(), sizeof(bz::TallyArgs) * n, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMallocHost(&b->tallies_host, sizeof(bz_tallies) * n);
+    if (e == cudaSuccess) {
+        b->tallies_host = (bz_tallies *)pinned_block(ctx, sizeof(bz_tallies) * n, &b->tallies_cap);
+        if (!b->tallies_host) e = cudaErrorMemoryAllocation;
+    }
     for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaEventCreate(&b->ev[i]);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess && b->use_graph) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         bz_destroy_batch(b);
         return cuda_fail(e, "batch set-up");
@@ -823,14 +857,23 @@ void bz_destroy_batch(bz_batch *b)
     for (int i = 0; i < 3; ++i)
         if (b->ev[i]) cudaEventDestroy(b->ev[i]);
     if (b->done) cudaEventDestroy(b->done);
-    if (b->tallies_host) cudaFreeHost(b->tallies_host);
     bz_ctx *ctx = b->ctx;
+    pinned_block_release(ctx, b->tallies_host, b->tallies_cap);
     if (b->mem) {
+        // the batch's work is complete (waited above), so the memory is free on any stream
         dev_free(ctx, b->mem, b->bytes, 0);
-        cudaDeviceSynchronize();
         ctx_release(ctx);
     }
     delete b;
+}
+
+bz_status bz_batch_query(bz_batch *b)
+{
+    if (!b || !b->launched) return fail(BZ_EINVAL, "batch not launched");
+    cudaError_t e = cudaEventQuery(b->done);
+    if (e == cudaErrorNotReady) return BZ_ENOTREADY;
+    if (e != cudaSuccess) return cuda_fail(e, "batch");
+    return BZ_OK;
 }
 
 bz_status bz_step_replay(bz_ctx *ctx, const bz_mixture *mix, const bz_swarm_config *cfg, int64_t n,

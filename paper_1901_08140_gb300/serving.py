@@ -1,14 +1,16 @@
 """Serving loop: swarm requests with continuous batching on one GPU.
 
 Requests (a compiled mixture plus a swarm configuration) arrive over time.
-The server admits a request as soon as a launch slot (one of S CUDA
-streams) and device memory within the admission budget are free, launches
-its swarm asynchronously, and polls completions without blocking; swarms
-from different streams run concurrently on the GPU, so requests that
-arrive while others are running start immediately and their work overlaps
-on the device.  Each swarm's results depend only on its configuration
-(counter-based random numbers keyed by the swarm seed and particle ids),
-so a request's tallies are the same alone and in the mix.
+Whenever a launch slot (one of S CUDA streams) is free, the server takes
+the queued requests in arrival order, as many as fit the device-memory
+admission budget (and a group-size cap), and launches them together as one
+batched persistent launch on that slot; it polls completions without
+blocking.  Groups on different slots run concurrently, so requests that
+arrive while others are on the GPU are admitted as soon as a slot and
+memory free up and their work overlaps on the device.  Each swarm's
+results depend only on its configuration (counter-based random numbers
+keyed by the swarm seed and particle ids, one step kernel for every launch
+form), so a request's tallies are the same alone and in the mix.
 
 The scheduling logic is independent of the GPU: a backend object launches,
 polls and releases swarms (``GpuBackend`` drives libbz.so; the tests drive
@@ -81,18 +83,54 @@ class GpuBackend:
         handle.close()
 
 
+class GpuBatchBackend:
+    """Launches groups of requests as one batched launch of libbz.so per slot."""
+
+    def __init__(self, ctx, n_streams: int = 4):
+        import torch
+        from . import bz
+        self.bz = bz
+        self.ctx = ctx
+        dev = torch.device("cuda", ctx.device)
+        self.streams = [torch.cuda.Stream(device=dev) for _ in range(n_streams)]
+
+    @property
+    def slots(self) -> int:
+        return len(self.streams)
+
+    def launch_group(self, reqs: Sequence[Request], slot: int):
+        b = self.bz.Batch(self.ctx, [r.mixture for r in reqs], [r.cfg for r in reqs], use_graph=False)
+        b.launch(self.streams[slot])
+        return b
+
+    def poll_group(self, handle) -> Optional[List[Dict[str, float]]]:
+        if not handle.ready():
+            return None
+        return handle.tallies(check=False)
+
+    def release_group(self, handle) -> None:
+        handle.close()
+
+
 class Server:
-    """Continuous-batching request loop with memory-budget admission."""
+    """Continuous-batching request loop with memory-budget admission.
+
+    With a backend that launches groups (``launch_group``), each free slot
+    takes up to ``max_group`` queued requests at once; otherwise one request
+    per slot.
+    """
 
     def __init__(self, backend, memory_budget: float = 60e9, clock: Callable[[], float] = time.perf_counter,
-                 idle_sleep: float = 2e-5):
+                 idle_sleep: float = 2e-5, max_group: int = 512):
         self.backend = backend
         self.budget = float(memory_budget)
         self.clock = clock
         self.idle_sleep = idle_sleep
+        self.max_group = max_group if hasattr(backend, "launch_group") else 1
         self.in_use = 0.0
         self.peak_in_use = 0.0
         self.max_concurrent = 0
+        self.groups = 0
 
     def run(self, requests: Sequence[Request], realtime: bool = True) -> List[Request]:
         """Serves `requests` (sorted by arrival); returns them completed.
@@ -107,36 +145,50 @@ class Server:
         pending: Deque[Request] = collections.deque(reqs)
         queue: Deque[Request] = collections.deque()
         free = list(range(self.backend.slots))[::-1]
-        running: Dict[int, tuple] = {}
+        running: Dict[int, tuple] = {}   # slot -> (requests, handle)
         t0 = self.clock()
         done: List[Request] = []
+        grouped = self.max_group > 1
         while pending or queue or running:
             now = self.clock() - t0
             while pending and (not realtime or pending[0].arrival <= now):
                 queue.append(pending.popleft())
             # admit in arrival order while a slot and memory are free
             while queue and free and self.in_use + queue[0].device_bytes() <= self.budget:
-                r = queue.popleft()
+                group, need = [], 0.0
+                while (queue and len(group) < self.max_group
+                       and self.in_use + need + queue[0].device_bytes() <= self.budget):
+                    r = queue.popleft()
+                    need += r.device_bytes()
+                    group.append(r)
                 slot = free.pop()
-                r.admitted = self.clock() - t0
-                running[r.rid] = (r, slot, self.backend.launch(r, slot))
-                self.in_use += r.device_bytes()
+                t_adm = self.clock() - t0
+                for r in group:
+                    r.admitted = t_adm
+                h = self.backend.launch_group(group, slot) if grouped else self.backend.launch(group[0], slot)
+                running[slot] = (group, h)
+                self.groups += 1
+                self.in_use += need
                 self.peak_in_use = max(self.peak_in_use, self.in_use)
-                self.max_concurrent = max(self.max_concurrent, len(running))
+                self.max_concurrent = max(self.max_concurrent, sum(len(g) for g, _ in running.values()))
             progressed = False
-            for rid in list(running):
-                r, slot, h = running[rid]
-                t = self.backend.poll(h)
-                if t is None:
+            for slot in list(running):
+                group, h = running[slot]
+                res = self.backend.poll_group(h) if grouped else self.backend.poll(h)
+                if res is None:
                     continue
-                r.done = self.clock() - t0
-                r.tallies = t
-                r.status = int(t.get("status", 0))
-                self.backend.release(h)
-                del running[rid]
+                t_done = self.clock() - t0
+                if not grouped:
+                    res = [res]
+                for r, t in zip(group, res):
+                    r.done = t_done
+                    r.tallies = t
+                    r.status = int(t.get("status", 0))
+                    self.in_use -= r.device_bytes()
+                    done.append(r)
+                (self.backend.release_group if grouped else self.backend.release)(h)
+                del running[slot]
                 free.append(slot)
-                self.in_use -= r.device_bytes()
-                done.append(r)
                 progressed = True
             if not progressed and self.idle_sleep > 0:
                 time.sleep(self.idle_sleep)

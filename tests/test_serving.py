@@ -32,6 +32,21 @@ class FakeBackend:
         self.log.append(("release", h["req"].rid))
 
 
+class FakeGroupBackend(FakeBackend):
+    def launch_group(self, reqs, slot):
+        self.log.append(("group", tuple(r.rid for r in reqs), slot))
+        return {"reqs": list(reqs), "left": self.polls}
+
+    def poll_group(self, h):
+        h["left"] -= 1
+        if h["left"] > 0:
+            return None
+        return [{"n_real": r.n_electrons, "status": 0} for r in h["reqs"]]
+
+    def release_group(self, h):
+        self.log.append(("release", tuple(r.rid for r in h["reqs"])))
+
+
 class Clock:
     def __init__(self):
         self.t = 0.0
@@ -69,6 +84,17 @@ def test_requests_arriving_while_others_run_are_admitted_at_once():
     assert srv.max_concurrent == 3
 
 
+def test_queued_requests_are_launched_together_within_budget():
+    be = FakeGroupBackend(slots=2, polls=20)
+    budget = S.BYTES_PER_ELECTRON * 3000 + 3 * S.BYTES_PER_SWARM
+    srv = S.Server(be, memory_budget=budget, clock=Clock(), idle_sleep=0, max_group=8)
+    done = srv.run(_reqs([1000] * 7, [0.0] * 7), realtime=False)
+    groups = [e[1] for e in be.log if e[0] == "group"]
+    assert groups[0] == (0, 1, 2)              # as many as the memory budget allows
+    assert sorted(r for g in groups for r in g) == list(range(7))
+    assert srv.peak_in_use <= budget and len(done) == 7
+
+
 def test_oversized_request_is_rejected():
     srv = S.Server(FakeBackend(), memory_budget=1e6, clock=Clock(), idle_sleep=0)
     with pytest.raises(ValueError):
@@ -103,11 +129,14 @@ def test_results_are_the_same_alone_and_in_the_mix():
         sw = bz.run_swarm(ctx, m, c)
         alone.append(sw.tallies())
         sw.close()
-    reqs = [S.Request(i, m, c, arrival=0.0, n_electrons=int(c.n_electrons)) for i, (m, c) in enumerate(zip(mixes, cfgs))]
-    srv = S.Server(S.GpuBackend(ctx, n_streams=8), memory_budget=60e9)
-    done = srv.run(reqs, realtime=False)
-    assert srv.max_concurrent > 1
-    for r in done:
-        a = alone[r.rid]
-        for k in ("W", "eps", "D_L", "D_T", "n_real", "n_null", "n_window"):
-            assert r.tallies[k] == a[k], (r.rid, k)
+    for backend, arrivals in ((S.GpuBackend(ctx, n_streams=8), [0.0] * len(cfgs)),
+                              (S.GpuBatchBackend(ctx, n_streams=3), list(np.linspace(0.0, 0.02, len(cfgs))))):
+        reqs = [S.Request(i, m, c, arrival=a, n_electrons=int(c.n_electrons))
+                for i, (m, c, a) in enumerate(zip(mixes, cfgs, arrivals))]
+        srv = S.Server(backend, memory_budget=60e9, max_group=6)
+        done = srv.run(reqs, realtime=True)
+        assert srv.max_concurrent > 1 and len(done) == len(reqs)
+        for r in done:
+            a = alone[r.rid]
+            for k in ("W", "eps", "D_L", "D_T", "n_real", "n_null", "n_window"):
+                assert r.tallies[k] == a[k], (r.rid, k)
