@@ -18,6 +18,7 @@ constexpr double kHartreeEv = 27.211386245988;
 constexpr double kTownsend = 1e-21;           // V m^2
 constexpr double kLoschmidt = 2.686780111e25; // m^-3 (273.15 K, 101.325 kPa)
 
+constexpr int kMaxGases = 16;  // gases per mixture
 constexpr int kGroups = 32;   // batch groups for standard errors (id mod 32)
 constexpr int kQ1 = 19;       // first-pass tally quantities
 constexpr int kQ2 = 8;        // second-pass tally quantities
@@ -68,6 +69,11 @@ struct Layout {
     float bin_lo, inv_binw;  // log2 energy of the first bin edge, bins per unit log2
     double nu_low;           // max nu over [0, 2^bin_lo]
     double g_top;            // last union point [eV]
+    // per-gas density sums per record ({val, slope}, n_rec x n_gases, global
+    // memory) and each gas's channel range, for a two-level channel search
+    uint32_t off_gval;
+    int32_t n_gases;
+    int16_t gas_first[kMaxGases], gas_count[kMaxGases];
 };
 
 struct CompiledMixture {

@@ -81,6 +81,8 @@ __device__ __forceinline__ void sincospi_(float x, float *s, float *c) { sincosp
 __device__ __forceinline__ void sincospi_(double x, double *s, double *c) { sincospi(x, s, c); }
 __device__ __forceinline__ float max_(float a, float b) { return fmaxf(a, b); }
 __device__ __forceinline__ double max_(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ float min_(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ double min_(double a, double b) { return fmin(a, b); }
 
 // (sin, cos) of the azimuth 2 pi u.  FP32: the fast hardware sine and
 // cosine of 2 pi u - pi, which lies in (-pi, pi) where their absolute error
@@ -141,7 +143,9 @@ struct Tab {
     const ChParam<R> *chp;
     const ChVal<R> *chval;
     const R *binmax;  // sparse table of per-bin maxima (level-major)
-    int n_rec, n_buckets, n_ch, first_tail, n_bins;
+    const ChVal<R> *gval;  // per-record, per-gas density sums (global memory)
+    const Layout *lay;     // gas channel ranges
+    int n_rec, n_buckets, n_ch, first_tail, n_bins, n_gases;
     float log2_lo, inv_bw, bin_lo, inv_binw;
     R nu_low, g_top, s_min;  // s_min: speed at the first bin edge [m/s]
 };
@@ -167,6 +171,9 @@ __device__ __forceinline__ Tab<R> make_tab(const uint8_t *smem, const uint8_t *b
     T.nu_low = (R)L.nu_low;
     T.g_top = (R)L.g_top;
     T.s_min = (R)sqrt(exp2((double)L.bin_lo) * 2.0 * kQe / kMe);
+    T.gval = (const ChVal<R> *)(blob + L.off_gval);
+    T.lay = &L;
+    T.n_gases = L.n_gases;
     return T;
 }
 
@@ -211,12 +218,37 @@ __device__ __forceinline__ ChVal<R> load_chval(const ChVal<R> *p, bool ch_smem)
     return v;
 }
 
-// First channel whose cumulative density reaches `target` (= R nu'/|v|).
+// First channel whose cumulative density reaches `target` (= R nu'/|v|),
+// in the order of Eq. (2): gas by gas, channel by channel.  Outside the
+// power-law tails the search is two-level: per-gas sums find the gas, then
+// that gas's channels are scanned (the same cumulative partition).
 template <typename R, bool CH_SMEM>
 __device__ __forceinline__ int select_channel(const Tab<R> &T, int ri, R e_lo, R eps, R target)
 {
-    const ChVal<R> *row = T.chval + (size_t)ri * T.n_ch;
     const R de = eps - e_lo;
+    if (ri < T.first_tail && T.n_gases > 1) {
+        const ChVal<R> *grow = T.gval + (size_t)ri * T.n_gases;
+        R cum = 0;
+        int g = 0;
+        for (; g < T.n_gases - 1; ++g) {
+            const ChVal<R> gv = load_chval(grow + g, false);
+            const R d = gv.val + gv.slope * de;
+            if (cum + d >= target) break;
+            cum += d;
+        }
+        const int j0 = T.lay->gas_first[g], j1 = j0 + T.lay->gas_count[g];
+        const ChVal<R> *row = T.chval + (size_t)ri * T.n_ch;
+        int last = j0;
+        for (int j = j0; j < j1; ++j) {
+            const ChVal<R> cv = load_chval(row + j, CH_SMEM);
+            const R d = cv.val + cv.slope * de;
+            if (d > (R)0) last = j;
+            cum += d;
+            if (cum >= target) return j;
+        }
+        return last;  // rounding left the sum a hair short: last open channel of that gas
+    }
+    const ChVal<R> *row = T.chval + (size_t)ri * T.n_ch;
     const bool tails = ri >= T.first_tail;
     const R le = tails ? log_(eps) : (R)0;
     R cum = 0;
@@ -237,7 +269,7 @@ __device__ __forceinline__ int select_channel(const Tab<R> &T, int ri, R e_lo, R
 
 template <typename R>
 struct Fld {
-    R a, b0, b1, b2, w, inv_w, vD0, vD1, vD2, a_par, Ke;
+    R a, b0, b1, b2, w, inv_w, vD0, vD1, vD2, vDn, a_par, Ke;
     int has_b;
 };
 
@@ -255,6 +287,7 @@ __device__ __forceinline__ Fld<R> make_fld(const Fields &f)
     F.vD0 = (R)f.vD[0];
     F.vD1 = (R)f.vD[1];
     F.vD2 = (R)f.vD[2];
+    F.vDn = (R)sqrt(f.vD[0] * f.vD[0] + f.vD[1] * f.vD[1] + f.vD[2] * f.vD[2]);
     F.a_par = (R)f.a_par;
     F.Ke = (R)(0.5 * kMe / kQe);  // eV per (m/s)^2
     return F;
@@ -410,32 +443,40 @@ __device__ __forceinline__ R window_majorant(const Tab<R> &T, R e_lo, R e_hi)
 // as the speed bound needs to grow by a quarter of the speed (plus the speed
 // of the lowest table energy), so that a strong field cannot stretch the
 // energy range -- and the tails of the tables -- far beyond the electron's.
+// With B != 0 a second bound holds for any window length: the velocity is
+// v_par(t) b + vD + u(t) with vD, u perpendicular to b and |u| = |u0|, so
+// |v|^2 lies between v_par^2 + (|vD| - |u0|)^2 and v_par^2 + (|vD| + |u0|)^2;
+// the window then only has to bound the change of v_par, and the tighter of
+// the two bounds is used.
 template <typename R>
-__device__ __forceinline__ void new_window(const Tab<R> &T, const Fld<R> &F, const RunArgs &P, PState<R> &s, R speed,
-                                           R t0)
+__device__ __forceinline__ void new_window(const Tab<R> &T, const Fld<R> &F, const RunArgs &P, PState<R> &s, R v0,
+                                           R v1, R v2, R t0)
 {
+    const R speed = sqrt_(v0 * v0 + v1 * v1 + v2 * v2);
     const R eps = F.Ke * speed * speed;
     const int b = bin_of(T, eps);
     const R nub = max_((b < 0) ? T.nu_low : T.binmax[b < T.n_bins ? b : T.n_bins - 1], (R)P.nu_floor);
     R dt = (R)P.win_c / nub;
-    R u0n = 0, rate;
-    if (F.has_b) {
-        u0n = sqrt_(s.u0x * s.u0x + s.u0y * s.u0y + s.u0z * s.u0z);
-        rate = fabs(F.a_par) + u0n * F.w;  // |dv/dt| <= |a_par| + |u0| w
-    } else {
-        rate = F.a;
-    }
     const R grow_max = (R)0.25 * speed + T.s_min;
-    if (rate * dt > grow_max) dt = grow_max / rate;
-    R grow;
+    R s_hi, s_lo;
     if (F.has_b) {
+        const R u0n = sqrt_(s.u0x * s.u0x + s.u0y * s.u0y + s.u0z * s.u0z);
+        const R apar = fabs(F.a_par);
+        if (apar * dt > grow_max) dt = grow_max / apar;
         R wdt = F.w * dt;
         if (wdt > (R)2) wdt = (R)2;
-        grow = fabs(F.a_par) * dt + u0n * wdt;
+        const R grow = apar * dt + u0n * wdt;  // |v(t) - v(t0)| <= |a_par| dt + |u0| min(2, w dt)
+        const R vp = fabs(v0 * F.b0 + v1 * F.b1 + v2 * F.b2);
+        const R vp_hi = vp + apar * dt, vp_lo = max_((R)0, vp - apar * dt);
+        const R g_hi = F.vDn + u0n, g_lo = F.vDn - u0n;
+        s_hi = min_(speed + grow, sqrt_(vp_hi * vp_hi + g_hi * g_hi));
+        s_lo = max_(max_((R)0, speed - grow), sqrt_(vp_lo * vp_lo + g_lo * g_lo));
     } else {
-        grow = F.a * dt;
+        if (F.a * dt > grow_max) dt = grow_max / F.a;
+        const R grow = F.a * dt;
+        s_hi = speed + grow;
+        s_lo = max_((R)0, speed - grow);
     }
-    const R s_hi = speed + grow, s_lo = max_((R)0, speed - grow);
     const R m = max_(window_majorant(T, F.Ke * s_lo * s_lo, F.Ke * s_hi * s_hi) * (R)(1.0 + 1e-5), (R)P.nu_floor);
     s.nu_p = m;
     s.inv_nu = (R)1 / m;
@@ -473,7 +514,7 @@ __device__ __forceinline__ void init_particle(const Tab<R> &T, const RunArgs &P,
     s.done = false;
     set_b_cache(F, s);
     s.T_wend = (R)0;
-    if (P.window) new_window(T, F, P, s, sqrt_(s.vr0 * s.vr0 + s.vr1 * s.vr1 + s.vr2 * s.vr2), (R)0);
+    if (P.window) new_window(T, F, P, s, s.vr0, s.vr1, s.vr2, (R)0);
 }
 
 // One trial step.  Returns the decision (channel, DEC_NULL, DEC_FAIL or
@@ -520,11 +561,11 @@ __device__ __forceinline__ int trial(const Tab<R> &T, const Fld<R> &F, const Run
     }
     int dec;
     bool need_window = false;
-    R wspeed = 0, wt0 = 0, nu_fail = 0;
+    R wt0 = 0, nu_fail = 0;
+    R w0 = v0, w1 = v1, w2 = v2;  // velocity at the start of a new window
     if (restart) {
         s.T = Tn;  // a new window starts where the old one ended
         need_window = true;
-        wspeed = sqrt_(vsq);
         wt0 = Tn;
         dec = DEC_WINDOW;
     } else {
@@ -552,7 +593,9 @@ __device__ __forceinline__ int trial(const Tab<R> &T, const Fld<R> &F, const Run
             s.T = 0;  // fail (Sec. 6): back to the last real collision
             nu_fail = nu;
             need_window = P.window;
-            wspeed = sqrt_(s.vr0 * s.vr0 + s.vr1 * s.vr1 + s.vr2 * s.vr2);
+            w0 = s.vr0;
+            w1 = s.vr1;
+            w2 = s.vr2;
             dec = DEC_FAIL;
         } else if (r > nu) {  // Eq. (4): null collision
             ++s.n_null;
@@ -655,12 +698,14 @@ __device__ __forceinline__ int trial(const Tab<R> &T, const Fld<R> &F, const Run
                 s.se2.fold();
             }
             need_window = P.window;
-            wspeed = rotate ? nsp : sp;
+            w0 = s.vr0;
+            w1 = s.vr1;
+            w2 = s.vr2;
             dec = c;
         }
     }
     if (need_window) {
-        new_window(T, F, P, s, wspeed, wt0);
+        new_window(T, F, P, s, w0, w1, w2, wt0);
     }
     if (dec == DEC_FAIL) {
         s.nu_p = max_(s.nu_p, (R)1.25 * nu_fail);
@@ -919,7 +964,7 @@ __global__ void __launch_bounds__(kBlock) replay_kernel(const ReplayArgs A)
         s.done = false;
         set_b_cache(F, s);
         s.T_wend = (R)0;
-        if (P.window) new_window(T, F, P, s, sqrt_(s.vr0 * s.vr0 + s.vr1 * s.vr1 + s.vr2 * s.vr2), (R)0);
+        if (P.window) new_window(T, F, P, s, s.vr0, s.vr1, s.vr2, (R)0);
         R ei, ef;
         const int dec = trial<R, CH_SMEM>(T, F, P, s, ei, ef);
         // state at the trial point: last real collision advanced by s.T

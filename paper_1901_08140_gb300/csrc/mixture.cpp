@@ -103,7 +103,10 @@ void emit(const std::vector<Chan> &ch, const std::vector<double> &g, const std::
     size_t off_chp = pad16(off_bucket + sizeof(uint16_t) * nb);
     size_t off_bin = pad16(off_chp + sizeof(ChParam<R>) * n_ch);
     size_t off_chval = pad16(off_bin + sizeof(R) * n_bin_vals);
-    size_t total = pad16(off_chval + sizeof(ChVal<R>) * (size_t)n_rec * n_ch);
+    size_t off_gval = pad16(off_chval + sizeof(ChVal<R>) * (size_t)n_rec * n_ch);
+    int n_gases = 0;
+    for (const Chan &c : ch) n_gases = std::max(n_gases, c.gas + 1);
+    size_t total = pad16(off_gval + sizeof(ChVal<R>) * (size_t)n_rec * n_gases);
     blob->assign(total, 0);
     Rec<R> *rec = (Rec<R> *)(blob->data() + off_rec);
     for (int i = 0; i < n_rec; ++i) {
@@ -134,6 +137,28 @@ void emit(const std::vector<Chan> &ch, const std::vector<double> &g, const std::
             v[(size_t)i * n_ch + j].val = (R)cv[i][j];
             v[(size_t)i * n_ch + j].slope = (R)cs[i][j];
         }
+    ChVal<R> *gv = (ChVal<R> *)(blob->data() + off_gval);
+    for (int i = 0; i < n_rec; ++i) {
+        std::vector<double> sv(n_gases, 0.0), ss(n_gases, 0.0);
+        for (int j = 0; j < n_ch; ++j) {
+            sv[ch[j].gas] += cv[i][j];
+            ss[ch[j].gas] += cs[i][j];
+        }
+        for (int gI = 0; gI < n_gases; ++gI) {
+            gv[(size_t)i * n_gases + gI].val = (R)sv[gI];
+            gv[(size_t)i * n_gases + gI].slope = (R)ss[gI];
+        }
+    }
+    lay->off_gval = (uint32_t)off_gval;
+    lay->n_gases = n_gases;
+    for (int gI = 0; gI < kMaxGases; ++gI) {
+        lay->gas_first[gI] = 0;
+        lay->gas_count[gI] = 0;
+    }
+    for (int j = n_ch - 1; j >= 0; --j) {
+        lay->gas_first[ch[j].gas] = (int16_t)j;
+        lay->gas_count[ch[j].gas] += 1;
+    }
     lay->n_rec = n_rec;
     lay->n_buckets = nb;
     lay->n_ch = n_ch;
@@ -163,6 +188,7 @@ bz_status compile_mixture(const bz_gas *gases, int32_t n_gases, const bz_mixture
                           CompiledMixture *out, std::string *err)
 {
     if (!gases || n_gases < 1) { *err = "need at least one gas"; return BZ_EINVAL; }
+    if (n_gases > kMaxGases) { *err = "at most 16 gases per mixture"; return BZ_EINVAL; }
     std::vector<Chan> ch;
     std::vector<ChParam<double>> cp;
     double n_total = 0.0, emax = 0.0;
