@@ -221,7 +221,9 @@ def run_ours(args):
     mix = bz.Mixture(ctx, specs[0].gases)
     # weak scaling: every rank runs the whole sweep on its own particle ids
     mode = bz.BZ_TRIAL_WINDOW if args.trial == "window" else bz.BZ_TRIAL_LAZY
-    cfgs = [bz.config_from_spec(s, id_offset=rank * args.electrons, trial_mode=mode) for s in specs]
+    from paper_1901_08140_gb300 import sharding
+    cfgs = [bz.config_from_spec(s, id_offset=sharding.weak_offset(rank, args.electrons), trial_mode=mode)
+            for s in specs]
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
 
@@ -277,16 +279,8 @@ def run_ours(args):
             w_err.append(t["W_se"] / abs(t["W"]) if t["W"] else float("inf"))
     clk = clocks.stop()
     launches = 5 * args.steps   # batch kernel + 4 multi-swarm tally kernels, in one graph
-    t_max, p_max = total_ms, plain_ms
-    tot_reals, tot_plain = reals, plain_reals
-    if world > 1:
-        import torch.distributed as tdist
-        x = torch.tensor([total_ms, plain_ms], device=dev, dtype=torch.float64)
-        tdist.all_reduce(x, op=tdist.ReduceOp.MAX)
-        t_max, p_max = float(x[0].item()), float(x[1].item())
-        y = torch.tensor([float(reals), float(plain_reals)], device=dev, dtype=torch.float64)
-        tdist.all_reduce(y)
-        tot_reals, tot_plain = int(y[0].item()), int(y[1].item())
+    t_max, tot_reals = sharding.reduce_step(total_ms, reals)
+    p_max, tot_plain = sharding.reduce_step(plain_ms, plain_reals)
     value = tot_reals / (t_max / 1e3)
     plain_value = tot_plain / (p_max / 1e3)
 
