@@ -47,7 +47,7 @@
 enum { OR_ELASTIC = 0, OR_EXCITATION = 1, OR_ATTACHMENT = 2, OR_IONIZATION = 3 };
 enum { OR_ISOTROPIC = 0, OR_SCREENED_COULOMB = 1 };
 enum { OR_DEC_FAIL = -2, OR_DEC_NULL = -1 };
-enum { OR_ST_DONE = 0, OR_ST_TIME = 1, OR_ST_STEPS = 2, OR_ST_TRIAL = 3 };
+enum { OR_ST_DONE = 0, OR_ST_TIME = 1, OR_ST_STEPS = 2, OR_ST_TRIAL = 3, OR_ST_ERROR = 4, OR_ST_ATTACHED = 5 };
 
 /* ------------------------------------------------------------------------ */
 /* Philox4x32-10 (Salmon et al., SC'11, Sec. 4): 10 rounds of the Philox      */
@@ -447,7 +447,22 @@ typedef struct {
     uint64_t seed;
     uint64_t max_trials;
     int attach_keep_state;    /* 1: a dummy attachment leaves the electron unchanged */
+    int spawn;                /* 1: ionizations create electrons, attachments remove them */
+    uint64_t pop_cap;         /* spawn mode: at most this many electrons in all */
 } or_config;
+
+/* Identifier of the electron that the ionization at `step` of electron
+ * `parent` creates: the SplitMix64 finaliser (Steele, Lea, Flood 2014) of
+ * parent * 0x9E3779B97F4A7C15 + step + 1, with the top bit set so that it
+ * never equals a primary's id. */
+uint64_t or_secondary_id(uint64_t parent, uint32_t step)
+{
+    uint64_t z = parent * 0x9E3779B97F4A7C15ull + (uint64_t)step + 1ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return z | 0x8000000000000000ull;
+}
 
 typedef struct {
     double *x, *y, *z, *t, *vx, *vy, *vz, *sum_e, *sum_e2, *nu_p;
@@ -466,9 +481,12 @@ static void init_velocity(const or_config *cf, uint64_t id, double v[3])
     v[2] = sv * r1 * cos(2.0 * OR_PI * u[3]);
 }
 
-/* One real collision on channel c at energy eps (velocity v is updated). */
+/* One real collision on channel c at energy eps (velocity v is updated).
+ * For an ionization, sec_v receives the secondary's velocity (the ejected
+ * electron takes the fraction w0 of the energy left after Eq. (9) and
+ * leaves isotropically: cos = 1 - 2 w1, azimuth 2 pi w2). */
 static void collide(const or_mixture *m, const or_config *cf, uint64_t id, uint32_t step, int c, double eps,
-                    const double u[4], double v[3], double *eps_f, int *ion, int *att)
+                    const double u[4], double v[3], double *eps_f, int *ion, int *att, double sec_v[3])
 {
     const or_channel *ch = &m->ch[c];
     const or_gas *g = &m->gas[ch->gas];
@@ -488,6 +506,11 @@ static void collide(const or_mixture *m, const or_config *cf, uint64_t id, uint3
         if (ch->kind == OR_IONIZATION) {
             double w[4];
             draw4(cf->seed, id, step, 1u, w);
+            double es = w[0] * ratio * eps;   /* the secondary's energy */
+            double ss = sqrt(2.0 * es * OR_QE / OR_ME), cs = 1.0 - 2.0 * w[1], sn = sqrt(fmax(0.0, 1.0 - cs * cs));
+            sec_v[0] = ss * sn * cos(2.0 * OR_PI * w[2]);
+            sec_v[1] = ss * sn * sin(2.0 * OR_PI * w[2]);
+            sec_v[2] = ss * cs;
             ratio *= (1.0 - w[0]); /* the secondary takes w0 of the remainder */
             *ion = 1;
         }
@@ -504,11 +527,23 @@ static void collide(const or_mixture *m, const or_config *cf, uint64_t id, uint3
 
 static double energy_of(const double v[3]) { return 0.5 * OR_ME * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) / OR_QE; }
 
-static void run_particle(const or_mixture *m, const or_config *cf, const or_field *f, uint64_t id,
-                         const or_particles *P, int64_t slot)
+/* Spawn bookkeeping of one particle run (spawn mode). */
+typedef struct {
+    uint64_t *ids;     /* secondaries created, in order */
+    double *t_birth;   /* absolute birth time */
+    double *v_birth;   /* 3 per secondary */
+    int64_t n, cap;    /* count, room */
+} or_spawns;
+
+/* Runs one electron from birth (time t0, velocity v0; t0 = 0 and a
+ * Maxwellian start for primaries) to its limiters.  Positions and times are
+ * kept relative to birth; the time limit is absolute. */
+static void run_particle_from(const or_mixture *m, const or_config *cf, const or_field *f, uint64_t id, double t0,
+                              const double *v0, const or_particles *P, int64_t slot, or_spawns *sp)
 {
     double x[3] = {0.0, 0.0, 0.0}, v[3], t = 0.0;
-    init_velocity(cf, id, v);
+    if (v0) { v[0] = v0[0]; v[1] = v0[1]; v[2] = v0[2]; }
+    else init_velocity(cf, id, v);
     double sx[3] = {0, 0, 0}, sv[3] = {v[0], v[1], v[2]}, st = 0.0; /* last real collision */
     double nu_p = cf->nu_trial;
     double sum_e = 0.0, sum_e2 = 0.0;
@@ -520,9 +555,9 @@ static void run_particle(const or_mixture *m, const or_config *cf, const or_fiel
         draw4(cf->seed, id, step, 0u, u);
         /* Eq. (3): t_c = -ln(1-R)/nu'; the draw u0 plays the role of 1-R. */
         double tau = -log(u[0]) / nu_p;
-        if (cf->t_end > 0.0 && t + tau >= cf->t_end) {
-            or_move(f, x, v, cf->t_end - t);
-            t = cf->t_end;
+        if (cf->t_end > 0.0 && t0 + t + tau >= cf->t_end) {
+            or_move(f, x, v, cf->t_end - t0 - t);
+            t = cf->t_end - t0;
             status = OR_ST_TIME;
             break;
         }
@@ -541,14 +576,21 @@ static void run_particle(const or_mixture *m, const or_config *cf, const or_fiel
         double r = u[1] * nu_p;
         if (r > nu) { ++n_null; continue; } /* Eq. (4) */
         int c = or_select_channel(m, eps, r);
-        double eps_f;
+        double eps_f, sec_v[3];
         int ion, att;
-        collide(m, cf, id, step, c, eps, u, v, &eps_f, &ion, &att);
+        collide(m, cf, id, step, c, eps, u, v, &eps_f, &ion, &att, sec_v);
         n_ion += (uint32_t)ion;
         n_att += (uint32_t)att;
         sum_e += eps;
         sum_e2 += eps_f;
         ++n_real;
+        if (cf->spawn && ion && sp && sp->n < sp->cap) {   /* a new electron at this point */
+            sp->ids[sp->n] = or_secondary_id(id, step);
+            sp->t_birth[sp->n] = t0 + t;
+            for (int i = 0; i < 3; ++i) sp->v_birth[3 * sp->n + i] = sec_v[i];
+            ++sp->n;
+        }
+        if (cf->spawn && att && !cf->attach_keep_state) { status = OR_ST_ATTACHED; break; }
         for (int i = 0; i < 3; ++i) { sx[i] = x[i]; sv[i] = v[i]; }
         st = t;
     }
@@ -557,6 +599,12 @@ static void run_particle(const or_mixture *m, const or_config *cf, const or_fiel
     P->sum_e[slot] = sum_e; P->sum_e2[slot] = sum_e2; P->nu_p[slot] = nu_p;
     P->n_real[slot] = n_real; P->n_null[slot] = n_null; P->n_fail[slot] = n_fail;
     P->n_ion[slot] = n_ion; P->n_att[slot] = n_att; P->steps[slot] = k; P->status[slot] = status;
+}
+
+static void run_particle(const or_mixture *m, const or_config *cf, const or_field *f, uint64_t id,
+                         const or_particles *P, int64_t slot)
+{
+    run_particle_from(m, cf, f, id, 0.0, NULL, P, slot, NULL);
 }
 
 typedef struct {
@@ -573,6 +621,49 @@ static void *run_range(void *arg)
     const or_job *j = (const or_job *)arg;
     for (int64_t i = j->begin; i < j->end; ++i) run_particle(j->m, j->cf, j->f, j->id0 + (uint64_t)i, j->P, i);
     return NULL;
+}
+
+/* Spawn mode: primaries id0 .. id0+n-1 first, then every secondary in the
+ * order it was created (a FIFO queue), one electron at a time, until no
+ * electron is left or pop_cap electrons exist.  Output slot k holds the
+ * k-th electron run; ids_out[k] its id, t_birth_out[k] its birth time.
+ * Returns the number of electrons (the slots filled). */
+int64_t or_run_swarm_spawn(const or_mixture *m, const or_config *cf, uint64_t id0, int64_t n, int64_t cap,
+                           double *x, double *y, double *z, double *t, double *vx, double *vy, double *vz,
+                           double *sum_e, double *sum_e2, double *nu_p, uint32_t *n_real, uint32_t *n_null,
+                           uint32_t *n_fail, uint32_t *n_ion, uint32_t *n_att, uint32_t *steps, uint32_t *status,
+                           uint64_t *ids_out, double *t_birth_out)
+{
+    or_particles P = {x, y, z, t, vx, vy, vz, sum_e, sum_e2, nu_p, n_real, n_null, n_fail, n_ion, n_att, steps, status};
+    or_config c = *cf;
+    if (c.nu_trial <= 0.0) c.nu_trial = m->nu_max * (1.0 + 1e-6);
+    if (c.max_trials == 0) c.max_trials = 0x7FFFFFFFu;
+    or_field f;
+    field_setup(&f, c.e_over_n_Td, m->n_total, c.b_T, c.b_angle_rad);
+    int64_t room = cap - n;
+    if (room < 0) return -1;
+    or_spawns sp;
+    sp.ids = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(room + 1));
+    sp.t_birth = (double *)malloc(sizeof(double) * (size_t)(room + 1));
+    sp.v_birth = (double *)malloc(sizeof(double) * 3 * (size_t)(room + 1));
+    sp.n = 0;
+    sp.cap = room;
+    for (int64_t i = 0; i < n; ++i) {
+        ids_out[i] = id0 + (uint64_t)i;
+        t_birth_out[i] = 0.0;
+        run_particle_from(m, &c, &f, ids_out[i], 0.0, NULL, &P, i, &sp);
+    }
+    for (int64_t k = 0; k < sp.n; ++k) {
+        int64_t slot = n + k;
+        ids_out[slot] = sp.ids[k];
+        t_birth_out[slot] = sp.t_birth[k];
+        run_particle_from(m, &c, &f, sp.ids[k], sp.t_birth[k], sp.v_birth + 3 * k, &P, slot, &sp);
+    }
+    int64_t total = n + sp.n;
+    free(sp.ids);
+    free(sp.t_birth);
+    free(sp.v_birth);
+    return total;
 }
 
 /* Runs particles id0 .. id0+n-1; outputs go to slot i = id - id0.  Particles
@@ -634,7 +725,8 @@ int or_step_replay(const or_mixture *m, const or_config *cf, int64_t n, const do
             dec = OR_DEC_NULL;
         } else {
             int c = or_select_channel(m, eps, u[1] * nu_p), ion, att;
-            collide(m, cf, ids[i], steps[i], c, eps, u, v, &eps_f, &ion, &att);
+            double sec_v[3];
+            collide(m, cf, ids[i], steps[i], c, eps, u, v, &eps_f, &ion, &att, sec_v);
             dec = c;
         }
         double *o = out + 8 * i;

@@ -32,7 +32,7 @@ from . import build as _build
 _lib = None
 
 DEC_FAIL, DEC_NULL = -2, -1
-ST_DONE, ST_TIME, ST_STEPS, ST_TRIAL = 0, 1, 2, 3
+ST_DONE, ST_TIME, ST_STEPS, ST_TRIAL, ST_ERROR, ST_ATTACHED = 0, 1, 2, 3, 4, 5
 
 _dp = C.POINTER(C.c_double)
 _u32p = C.POINTER(C.c_uint32)
@@ -45,7 +45,8 @@ class _Config(C.Structure):
     _fields_ = [("e_over_n_Td", C.c_double), ("b_T", C.c_double), ("b_angle_rad", C.c_double),
                 ("nu_trial", C.c_double), ("fixed", C.c_int), ("real_collisions", C.c_uint32),
                 ("t_end", C.c_double), ("eps0_mean_eV", C.c_double), ("seed", C.c_uint64),
-                ("max_trials", C.c_uint64), ("attach_keep_state", C.c_int)]
+                ("max_trials", C.c_uint64), ("attach_keep_state", C.c_int), ("spawn", C.c_int),
+                ("pop_cap", C.c_uint64)]
 
 
 def lib():
@@ -86,6 +87,11 @@ def lib():
         L.or_step_replay.argtypes = [C.c_void_p, C.POINTER(_Config), C.c_int64, _dp, _u64p, _u32p, _dp, _i32p, _dp]
         L.or_initial_velocity.argtypes = [C.c_double, C.c_uint64, C.c_uint64, _dp]
         L.or_nu_many.argtypes = [C.c_void_p, C.c_int64, _dp, _dp]
+        L.or_secondary_id.restype = C.c_uint64
+        L.or_secondary_id.argtypes = [C.c_uint64, C.c_uint32]
+        L.or_run_swarm_spawn.restype = C.c_int64
+        L.or_run_swarm_spawn.argtypes = [C.c_void_p, C.POINTER(_Config), C.c_uint64, C.c_int64, C.c_int64] + \
+            [_dp] * 10 + [_u32p] * 7 + [_u64p, _dp]
         L.or_sigma_many.argtypes = [C.c_void_p, C.c_int, C.c_int64, _dp, _dp]
         L.or_initial_velocity_many.argtypes = [C.c_double, C.c_uint64, C.c_uint64, C.c_int64, _dp]
         _lib = L
@@ -214,10 +220,37 @@ def initial_velocities(eps0_mean_eV: float, seed: int, id0: int, n: int) -> np.n
 
 
 def _config(e_over_n_Td, b_T, b_angle_rad, real_collisions, seed, eps0_mean_eV, nu_trial, fixed, t_end,
-            max_trials, attach_keep_state) -> _Config:
+            max_trials, attach_keep_state, spawn=False, pop_cap=0) -> _Config:
     return _Config(float(e_over_n_Td), float(b_T), float(b_angle_rad), float(nu_trial), int(bool(fixed)),
                    int(real_collisions), float(t_end), float(eps0_mean_eV), int(seed) & 0xFFFFFFFFFFFFFFFF,
-                   int(max_trials), int(bool(attach_keep_state)))
+                   int(max_trials), int(bool(attach_keep_state)), int(bool(spawn)), int(pop_cap))
+
+
+def secondary_id(parent: int, step: int) -> int:
+    return lib().or_secondary_id(int(parent), int(step))
+
+
+def run_swarm_spawn(mix: Mixture, *, e_over_n_Td: float, real_collisions: int, n: int, seed: int, pop_cap: int,
+                    b_T: float = 0.0, b_angle_rad: float = 0.0, id0: int = 0, eps0_mean_eV: float = 0.1,
+                    nu_trial: float = 0.0, t_end: float = 0.0, max_trials: int = 0) -> Dict[str, np.ndarray]:
+    """Spawn mode: ionizations create electrons, attachments remove them."""
+    cf = _config(e_over_n_Td, b_T, b_angle_rad, real_collisions, seed, eps0_mean_eV, nu_trial, False, t_end,
+                 max_trials, False, spawn=True, pop_cap=pop_cap)
+    names_d = ["x", "y", "z", "t", "vx", "vy", "vz", "sum_e", "sum_e2", "nu_p"]
+    names_u = ["n_real", "n_null", "n_fail", "n_ion", "n_att", "steps", "status"]
+    out = {k: np.zeros(pop_cap, dtype=np.float64) for k in names_d}
+    out.update({k: np.zeros(pop_cap, dtype=np.uint32) for k in names_u})
+    ids = np.zeros(pop_cap, dtype=np.uint64)
+    tb = np.zeros(pop_cap, dtype=np.float64)
+    total = lib().or_run_swarm_spawn(mix.h, C.byref(cf), int(id0), int(n), int(pop_cap),
+                                     *[_p(out[k], _dp) for k in names_d], *[_p(out[k], _u32p) for k in names_u],
+                                     _p(ids, _u64p), _p(tb, _dp))
+    if total < 0:
+        raise ValueError("pop_cap below the number of primaries")
+    res = {k: v[:total] for k, v in out.items()}
+    res["id"] = ids[:total]
+    res["t_birth"] = tb[:total]
+    return res
 
 
 def run_swarm(mix: Mixture, *, e_over_n_Td: float, real_collisions: int, n: int, seed: int,

@@ -500,3 +500,59 @@ def test_estimators_on_a_hand_worked_swarm():
     assert tr["Wx"] == 1.5
     # d_x = 2 - 1.5 = 0.5 and 2 - 3 = -1
     assert tr["D_T"] == pytest.approx((0.25 / 4 + 1 / 8) / 2, abs=0.0)
+
+
+# --------------------------------------------------------------------------
+# Spawn mode: closed forms of constant-rate branching and removal.
+# --------------------------------------------------------------------------
+def _const_rate_gas(nu_el, nu_ion=0.0, nu_att=0.0):
+    """sigma proportional to 1/v for each channel, so each rate is constant."""
+    e = np.geomspace(1e-6, 1e4, 3001)
+    v = np.sqrt(2 * e * QE / ME)
+    n = W.N_STP_293
+    ch = [W.Channel(W.ELASTIC, 0.0, e, nu_el / (n * v))]
+    if nu_ion:
+        ch.append(W.Channel(W.IONIZATION, 0.0, e, nu_ion / (n * v)))
+    if nu_att:
+        ch.append(W.Channel(W.ATTACHMENT, 0.0, e, nu_att / (n * v)))
+    return W.Gas("const", 1000 * ME, n, W.ISOTROPIC, ch)
+
+
+def test_spawn_population_grows_as_a_yule_process():
+    nu_i = 1e11
+    m = O.Mixture([_const_rate_gas(1e12, nu_ion=nu_i)])
+    n0, t_end = 2000, 3.0 / nu_i
+    p = O.run_swarm_spawn(m, e_over_n_Td=50.0, real_collisions=10 ** 9, n=n0, seed=21, pop_cap=200000, t_end=t_end)
+    total = len(p["t"])
+    expect = n0 * math.exp(nu_i * t_end)
+    sd = math.sqrt(n0 * math.exp(nu_i * t_end) * (math.exp(nu_i * t_end) - 1))
+    assert abs(total - expect) < 4 * sd
+    assert np.all(p["status"] == O.ST_TIME)
+    # one secondary per ionization, born inside the run, with the derived id
+    assert total - n0 == int(p["n_ion"].sum())
+    assert np.all(p["t_birth"][n0:] > 0) and np.all(p["t_birth"][n0:] < t_end)
+    assert np.all(p["t_birth"] + p["t"] == pytest.approx(t_end, rel=1e-12, abs=0.0))
+    assert len(np.unique(p["id"])) == total and np.all(p["id"][n0:] >= 2 ** 63)
+
+
+def test_spawn_attachment_removes_at_a_constant_rate():
+    nu_a = 1e11
+    m = O.Mixture([_const_rate_gas(1e12, nu_att=nu_a)])
+    n0, t_end = 20000, 1.5 / nu_a
+    p = O.run_swarm_spawn(m, e_over_n_Td=10.0, real_collisions=10 ** 9, n=n0, seed=5, pop_cap=n0, t_end=t_end)
+    alive = int(np.sum(p["status"] == O.ST_TIME))
+    q = math.exp(-nu_a * t_end)
+    assert abs(alive - n0 * q) < 4 * math.sqrt(n0 * q * (1 - q))
+    removed = p["status"] == O.ST_ATTACHED
+    assert np.all(p["n_att"][removed] == 1) and np.all(p["n_att"][~removed] == 0)
+
+
+def test_secondary_ids_follow_the_splitmix64_finaliser():
+    # SplitMix64 finaliser of parent * golden + step + 1, top bit set (written out here in integers)
+    def mix(parent, step):
+        z = (parent * 0x9E3779B97F4A7C15 + step + 1) & (2 ** 64 - 1)
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & (2 ** 64 - 1)
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & (2 ** 64 - 1)
+        return (z ^ (z >> 31)) | 2 ** 63
+    for parent, step in [(0, 0), (1, 7), (2 ** 40 + 3, 123456), (2 ** 63 + 9, 2 ** 32 - 1)]:
+        assert O.secondary_id(parent, step) == mix(parent, step)
