@@ -175,6 +175,9 @@ typedef struct {
     int32_t block_threads;    /* launch shape, 0: auto */
     int32_t blocks_per_sm;    /* 0: auto (occupancy) */
     double window_c;          /* WINDOW mode: window = window_c / nu of the current energy bin; 0: 2 */
+    int32_t spawn;            /* 1: ionizations create electrons, attachments remove them (Sec. 2) */
+    int32_t reserved0;
+    uint64_t pop_cap;         /* spawn mode: at most this many electrons in all; 0: 64 x n_electrons */
 } bz_swarm_config;
 
 /* Fills *cfg with defaults: N = 1e4, I = 1000, FP32, lazy mode, Maxwellian
@@ -190,7 +193,16 @@ bz_status bz_set_fields(bz_swarm_config *cfg, double e_over_n_Td, double b_T, do
  * stream) and returns at once.  The swarm owns its device buffers until
  * bz_destroy_swarm.  Each electron starts at the origin with an isotropic
  * Maxwellian velocity and runs until its I-th real collision (or t_end).
- * Ionizations and attachments are dummy (counted, Sec. 2.3).
+ * With spawn = 0, ionizations and attachments are dummy (counted, Sec.
+ * 2.3).  With spawn = 1 (ChildrenBulletLimiter, Sec. 3.2) an ionization
+ * creates an electron at the collision point with the fraction u of the
+ * energy left after Eq. (9), leaving isotropically (u and the direction from
+ * the second draw of that step), with id derived from (parent id, step); an
+ * attachment removes the electron; past pop_cap electrons, ionizations are
+ * only counted.  Every electron has its own limiters (I real collisions,
+ * absolute t_end) and reports position and time relative to its birth.  In
+ * spawn mode the call runs generation after generation of new electrons
+ * and returns when none is left (it blocks).
  * Errors: BZ_EINVAL, BZ_ENOMEM, BZ_ECUDA. */
 bz_status bz_run_swarm(bz_ctx *ctx, const bz_mixture *mix, const bz_swarm_config *cfg,
                        void *stream, bz_swarm **out);
@@ -216,6 +228,10 @@ typedef struct {
     double E_V_m, n_total, nu_trial, t_mean;
     uint64_t n_particles, n_real, n_null, n_fail, n_ion, n_att, n_incomplete;
     uint64_t n_window;        /* WINDOW mode: flights restarted at a window end */
+    uint64_t n_spawned;       /* spawn mode: electrons created by ionization */
+    uint64_t n_alive;         /* electrons stopped by the time limit (alive at t_end) */
+    uint64_t n_removed;       /* spawn mode: electrons removed by attachment */
+    uint64_t n_capped;        /* spawn mode: ionizations that found the population at its cap */
     int32_t error_flags;      /* device error bits (see BZ_ERR_*) */
     int32_t reserved;
 } bz_tallies;
@@ -235,12 +251,25 @@ bz_status bz_query_tallies(bz_swarm *sw, bz_tallies *out);
  * caller-owned host arrays of length >= N; any pointer may be NULL.  Waits
  * for the swarm. */
 typedef struct {
-    double *x, *y, *z, *t;         /* position [m] and time [s] at the end */
+    double *x, *y, *z, *t;         /* position [m] and time [s] at the end, relative to birth */
     double *sum_e, *sum_e2;        /* energy sums before / after real collisions [eV] */
     float *vx, *vy, *vz;           /* final velocity [m/s] */
     float *nu_p;                   /* final trial frequency of the particle [1/s] */
     uint32_t *n_real, *n_null, *n_fail, *n_ion, *n_att, *steps, *status;
+    uint64_t *id;                  /* particle id (secondaries: derived from parent id and step) */
+    double *t_birth;               /* birth time [s] (0 for the initial electrons) */
 } bz_particles;
+
+/* Status codes of bz_particles.status. */
+#define BZ_ST_DONE 0     /* reached I real collisions */
+#define BZ_ST_TIME 1     /* stopped at t_end */
+#define BZ_ST_STEPS 2    /* reached max_trials */
+#define BZ_ST_TRIAL 3    /* fixed nu' exceeded */
+#define BZ_ST_ERROR 4    /* non-finite state */
+#define BZ_ST_ATTACHED 5 /* removed by attachment (spawn mode) */
+
+/* Number of electrons of the swarm (initial + created); waits for it. */
+bz_status bz_swarm_size(bz_swarm *sw, uint64_t *n);
 
 bz_status bz_read_particles(bz_swarm *sw, const bz_particles *out);
 
@@ -304,7 +333,7 @@ void bz_destroy_batch(bz_batch *b);
 #define BZ_NOALLOC_SPAN 32768u              /* particles per reduction block */
 #define BZ_NOALLOC_MAX_BLOCKS 512u
 #define BZ_NOALLOC_MAX_PARTICLES (BZ_NOALLOC_SPAN * BZ_NOALLOC_MAX_BLOCKS) /* 16777216 */
-#define BZ_NOALLOC_SCRATCH_BYTES (8u * (BZ_NOALLOC_MAX_BLOCKS * 32u * 27u + 32u * 27u + 8u) + 256u)
+#define BZ_NOALLOC_SCRATCH_BYTES (8u * (BZ_NOALLOC_MAX_BLOCKS * 32u * 29u + 32u * 29u + 8u) + 256u)
 
 typedef struct {
     const double *x, *y, *z, *t;      /* device, n each: final position [m], time [s] */

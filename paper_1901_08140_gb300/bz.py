@@ -23,7 +23,7 @@ from . import build as _build
 BZ_OK, BZ_EINVAL, BZ_ENOMEM, BZ_EBUDGET, BZ_ETRIAL, BZ_ETIMEOUT, BZ_ECUDA, BZ_ECANCEL, BZ_ENOTREADY = range(9)
 BZ_TRIAL_LAZY, BZ_TRIAL_FIXED, BZ_TRIAL_WINDOW = 0, 1, 2
 DEC_WINDOW, DEC_FAIL, DEC_NULL = -3, -2, -1
-ST_DONE, ST_TIME, ST_STEPS, ST_TRIAL, ST_ERROR = 0, 1, 2, 3, 4
+ST_DONE, ST_TIME, ST_STEPS, ST_TRIAL, ST_ERROR, ST_ATTACHED = 0, 1, 2, 3, 4, 5
 
 
 class BzError(RuntimeError):
@@ -64,7 +64,8 @@ class bz_swarm_config(C.Structure):
                 ("trial_mode", C.c_int32), ("attach_keep_state", C.c_int32), ("nu_trial", C.c_double),
                 ("eps0_mean_eV", C.c_double), ("t_end_s", C.c_double), ("max_trials", C.c_uint64),
                 ("seed", C.c_uint64), ("id_offset", C.c_uint64), ("block_threads", C.c_int32),
-                ("blocks_per_sm", C.c_int32), ("window_c", C.c_double)]
+                ("blocks_per_sm", C.c_int32), ("window_c", C.c_double), ("spawn", C.c_int32),
+                ("reserved0", C.c_int32), ("pop_cap", C.c_uint64)]
 
 
 _TALLY_DOUBLES = ["W", "W_se", "Wx", "Wy", "W_flux", "lorentz_angle", "mu", "mu_N", "mu_0", "eps", "eps_se",
@@ -72,7 +73,8 @@ _TALLY_DOUBLES = ["W", "W_se", "Wx", "Wy", "W_flux", "lorentz_angle", "mu", "mu_
                   "D", "D_se", "D_L", "D_L_se", "D_T", "D_T_se", "D_L_flux", "D_T_flux", "sig", "sig_se",
                   "sig_L", "sig_L_se", "sig_T", "sig_T_se", "efficiency", "E_V_m", "n_total", "nu_trial",
                   "t_mean"]
-_TALLY_COUNTS = ["n_particles", "n_real", "n_null", "n_fail", "n_ion", "n_att", "n_incomplete", "n_window"]
+_TALLY_COUNTS = ["n_particles", "n_real", "n_null", "n_fail", "n_ion", "n_att", "n_incomplete", "n_window",
+                 "n_spawned", "n_alive", "n_removed", "n_capped"]
 
 
 class bz_tallies(C.Structure):
@@ -87,7 +89,8 @@ _PART_U = ["n_real", "n_null", "n_fail", "n_ion", "n_att", "steps", "status"]
 
 class bz_particles(C.Structure):
     _fields_ = [(k, C.POINTER(C.c_double)) for k in _PART_D] + [(k, C.POINTER(C.c_float)) for k in _PART_F] + \
-        [(k, C.POINTER(C.c_uint32)) for k in _PART_U]
+        [(k, C.POINTER(C.c_uint32)) for k in _PART_U] + [("id", C.POINTER(C.c_uint64)),
+                                                        ("t_birth", C.POINTER(C.c_double))]
 
 
 class bz_particle_arrays(C.Structure):
@@ -137,6 +140,7 @@ SIGNATURES = {
     "bz_read_particles": (C.c_int, [C.c_void_p, C.POINTER(bz_particles)]),
     "bz_destroy_swarm": (None, [C.c_void_p]),
     "bz_swarm_timing": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "bz_swarm_size": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64)]),
     "bz_create_batch": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_void_p), C.POINTER(bz_swarm_config),
                                   C.POINTER(bz_batch_opts), C.POINTER(C.c_void_p)]),
     "bz_launch_batch": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -195,6 +199,7 @@ def bz_query_tallies(sw, out): return lib().bz_query_tallies(sw, out)
 def bz_read_particles(sw, out): return lib().bz_read_particles(sw, out)
 def bz_destroy_swarm(sw): return lib().bz_destroy_swarm(sw)
 def bz_swarm_timing(sw, a, b): return lib().bz_swarm_timing(sw, a, b)
+def bz_swarm_size(sw, n): return lib().bz_swarm_size(sw, n)
 def bz_create_batch(*a): return lib().bz_create_batch(*a)
 def bz_launch_batch(b, stream): return lib().bz_launch_batch(b, stream)
 def bz_batch_query(b): return lib().bz_batch_query(b)
@@ -328,7 +333,7 @@ def make_config(*, n_electrons: int, real_collisions: int, e_over_n_Td: float, b
                 b_angle_rad: float = 0.0, precision: int = 32, seed: int = 1901081400, eps0_mean_eV: float = 0.1,
                 trial_mode: int = BZ_TRIAL_LAZY, nu_trial: float = 0.0, t_end_s: float = 0.0, max_trials: int = 0,
                 id_offset: int = 0, attach_keep_state: bool = False, blocks_per_sm: int = 0,
-                window_c: float = 0.0) -> bz_swarm_config:
+                window_c: float = 0.0, spawn: bool = False, pop_cap: int = 0) -> bz_swarm_config:
     cfg = bz_swarm_config()
     lib().bz_config_defaults(C.byref(cfg))
     _check(lib().bz_set_fields(C.byref(cfg), float(e_over_n_Td), float(b_T), float(b_angle_rad)))
@@ -345,6 +350,8 @@ def make_config(*, n_electrons: int, real_collisions: int, e_over_n_Td: float, b
     cfg.attach_keep_state = int(bool(attach_keep_state))
     cfg.blocks_per_sm = int(blocks_per_sm)
     cfg.window_c = float(window_c)
+    cfg.spawn = int(bool(spawn))
+    cfg.pop_cap = int(pop_cap)
     return cfg
 
 
@@ -375,16 +382,15 @@ class Swarm:
         out["status"] = st
         return out
 
+    def size(self) -> int:
+        n = C.c_uint64()
+        _check(lib().bz_swarm_size(self.h, C.byref(n)))
+        return int(n.value)
+
     def particles(self) -> Dict[str, np.ndarray]:
-        n = int(self.cfg.n_electrons)
-        arrs = {k: np.zeros(n, np.float64) for k in _PART_D}
-        arrs.update({k: np.zeros(n, np.float32) for k in _PART_F})
-        arrs.update({k: np.zeros(n, np.uint32) for k in _PART_U})
-        p = bz_particles(*[arrs[k].ctypes.data_as(C.POINTER(C.c_double)) for k in _PART_D],
-                         *[arrs[k].ctypes.data_as(C.POINTER(C.c_float)) for k in _PART_F],
-                         *[arrs[k].ctypes.data_as(C.POINTER(C.c_uint32)) for k in _PART_U])
+        n = self.size()
+        arrs, p = _particle_arrays(n)
         _check(lib().bz_read_particles(self.h, C.byref(p)))
-        arrs["id"] = np.arange(int(self.cfg.id_offset), int(self.cfg.id_offset) + n, dtype=np.uint64)
         return arrs
 
     def timing(self):
@@ -418,9 +424,13 @@ def _particle_arrays(n: int):
     arrs = {k: np.zeros(n, np.float64) for k in _PART_D}
     arrs.update({k: np.zeros(n, np.float32) for k in _PART_F})
     arrs.update({k: np.zeros(n, np.uint32) for k in _PART_U})
+    arrs["id"] = np.zeros(n, np.uint64)
+    arrs["t_birth"] = np.zeros(n, np.float64)
     p = bz_particles(*[arrs[k].ctypes.data_as(C.POINTER(C.c_double)) for k in _PART_D],
                      *[arrs[k].ctypes.data_as(C.POINTER(C.c_float)) for k in _PART_F],
-                     *[arrs[k].ctypes.data_as(C.POINTER(C.c_uint32)) for k in _PART_U])
+                     *[arrs[k].ctypes.data_as(C.POINTER(C.c_uint32)) for k in _PART_U],
+                     arrs["id"].ctypes.data_as(C.POINTER(C.c_uint64)),
+                     arrs["t_birth"].ctypes.data_as(C.POINTER(C.c_double)))
     return arrs, p
 
 

@@ -52,7 +52,10 @@ struct bz_swarm {
     bz_tallies *tallies_host;  // pinned
     cudaEvent_t done;
     cudaEvent_t ev[3];  // before the step kernel, after it, after the tallies
-    uint64_t n;
+    uint64_t n;          // electrons (spawn mode: initial + created)
+    uint64_t n_primary;
+    uint64_t *bid;       // spawn mode: ids and birth times of the created electrons
+    double *bt;
 };
 
 struct bz_batch {
@@ -62,7 +65,7 @@ struct bz_batch {
     bool ch_smem, use_graph;
     size_t smem;
     int grid, n_tiles, max_tblocks;
-    std::vector<uint64_t> n_el;
+    std::vector<uint64_t> n_el, id_offset;
     std::vector<bz::ParticlesDev> p;
     uint8_t *mem;
     size_t bytes;
@@ -219,6 +222,9 @@ bz_status validate_config(const bz_swarm_config *cfg)
     if (cfg->max_trials > 0xFFFFFFFFull) return fail(BZ_EINVAL, "max_trials must fit 32 bits");
     if (cfg->block_threads != 0 && cfg->block_threads != 256) return fail(BZ_EINVAL, "block_threads must be 0 or 256");
     if (cfg->blocks_per_sm < 0) return fail(BZ_EINVAL, "blocks_per_sm must be >= 0");
+    if (cfg->spawn != 0 && cfg->spawn != 1) return fail(BZ_EINVAL, "spawn must be 0 or 1");
+    if (cfg->spawn && cfg->pop_cap && cfg->pop_cap < cfg->n_electrons)
+        return fail(BZ_EINVAL, "pop_cap below the number of initial electrons");
     return BZ_OK;
 }
 
@@ -403,18 +409,15 @@ bz_status bz_run_swarm(bz_ctx *ctx, const bz_mixture *mix, const bz_swarm_config
     bool ch_smem;
     if ((st = prepare_run(mix, cfg, &a, &ch_smem)) != BZ_OK) return st;
     const uint64_t n = cfg->n_electrons;
-    if (n > 0xFFFFFFFFull) return fail(BZ_EINVAL, "a swarm holds at most 2^32-1 electrons");
+    const bool spawn = cfg->spawn != 0;
+    const uint64_t cap = spawn ? (cfg->pop_cap ? cfg->pop_cap : 64 * n) : n;  // electron slots
+    if (cap > 0xFFFFFFFFull) return fail(BZ_EINVAL, "a swarm holds at most 2^32-1 electrons");
     const int block = 256;
     int bps = bz::batch_occupancy(cfg->precision, ch_smem, block, a.stage_bytes);
     if (bps < 1) return fail(BZ_ECUDA, "step kernel cannot be resident with these tables");
     if (cfg->blocks_per_sm > 0 && cfg->blocks_per_sm < bps) bps = cfg->blocks_per_sm;
     const uint64_t grid64 = (uint64_t)ctx->sm_count * bps;
-    // about 8 tiles per block (load balance at the end of the launch), each a
-    // multiple of the block size (balance inside a tile)
-    const uint32_t tile = tile_size_for(n, grid64, 8);
-    const uint64_t n_tiles = (n + tile - 1) / tile;
-    const int grid = (int)(grid64 < n_tiles ? grid64 : n_tiles);
-    const int tblocks = bz::tally_blocks(n, ctx->sm_count);
+    const int tblocks = bz::tally_blocks(cap, ctx->sm_count);
 
     bz_swarm *s = new (std::nothrow) bz_swarm();
     if (!s) return fail(BZ_ENOMEM, "host allocation");
@@ -423,14 +426,18 @@ bz_status bz_run_swarm(bz_ctx *ctx, const bz_mixture *mix, const bz_swarm_config
     s->cfg = *cfg;
     s->stream = (cudaStream_t)stream;
     s->n = n;
-    // one device block: particle outputs, counter and flags, tally scratch
+    s->n_primary = n;
+    // one device block: particle outputs, counters and flags, birth records, tally scratch
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return o; };
-    const size_t o_x = take(8 * n), o_y = take(8 * n), o_z = take(8 * n), o_t = take(8 * n);
-    const size_t o_se = take(8 * n), o_se2 = take(8 * n);
-    const size_t o_vx = take(4 * n), o_vy = take(4 * n), o_vz = take(4 * n), o_nup = take(4 * n);
-    const size_t o_u[7] = {take(4 * n), take(4 * n), take(4 * n), take(4 * n), take(4 * n), take(4 * n), take(4 * n)};
-    const size_t o_ctr = take(16);
+    const uint64_t m = cap;
+    const size_t o_x = take(8 * m), o_y = take(8 * m), o_z = take(8 * m), o_t = take(8 * m);
+    const size_t o_se = take(8 * m), o_se2 = take(8 * m);
+    const size_t o_vx = take(4 * m), o_vy = take(4 * m), o_vz = take(4 * m), o_nup = take(4 * m);
+    const size_t o_u[7] = {take(4 * m), take(4 * m), take(4 * m), take(4 * m), take(4 * m), take(4 * m), take(4 * m)};
+    const size_t o_ctr = take(32);  // tile counter, error word, capped counter, electron counter
+    const uint64_t nb = spawn ? cap - n : 0;
+    const size_t o_bt = take(8 * nb), o_bid = take(8 * nb), o_bv = take(24 * nb);
     const size_t o_p1 = take(sizeof(double) * tblocks * bz::kGroups * bz::kQ1);
     const size_t o_p2 = take(sizeof(double) * tblocks * bz::kGroups * bz::kQ2);
     const size_t o_gs = take(sizeof(double) * (bz::kGroups * (bz::kQ1 + bz::kQ2) + 8));
@@ -448,8 +455,12 @@ bz_status bz_run_swarm(bz_ctx *ctx, const bz_mixture *mix, const bz_swarm_config
                             (float *)(M + o_vz), (float *)(M + o_nup), (uint32_t *)(M + o_u[0]),
                             (uint32_t *)(M + o_u[1]), (uint32_t *)(M + o_u[2]), (uint32_t *)(M + o_u[3]),
                             (uint32_t *)(M + o_u[4]), (uint32_t *)(M + o_u[5]), (uint32_t *)(M + o_u[6])};
-    unsigned long long *counter = (unsigned long long *)(M + o_ctr);
+    unsigned int *counter = (unsigned int *)(M + o_ctr);
     s->err = (uint32_t *)(M + o_ctr + 8);
+    unsigned int *n_capped = (unsigned int *)(M + o_ctr + 12);
+    unsigned long long *n_total = (unsigned long long *)(M + o_ctr + 16);
+    s->bt = (double *)(M + o_bt);
+    s->bid = (uint64_t *)(M + o_bid);
     s->tallies_dev = (bz_tallies *)(M + o_tal);
     s->tallies_host = pinned_slot(ctx);
     if (!s->tallies_host) e = cudaErrorMemoryAllocation;
@@ -463,20 +474,60 @@ bz_status bz_run_swarm(bz_ctx *ctx, const bz_mixture *mix, const bz_swarm_config
         return cuda_fail(e, "swarm set-up");
     }
     for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaEventCreate(&s->ev[i]);
-    if (e == cudaSuccess) e = cudaMemsetAsync(M + o_ctr, 0, 16, s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(M + o_ctr, 0, 32, s->stream);
     a.counter = nullptr;
     a.err = s->err;
     a.out = s->p;
+    a.spawn = spawn ? 1 : 0;
+    a.n_primary = n;
+    a.cap = cap;
+    a.n_total = n_total;
+    a.n_capped = n_capped;
+    a.bt = s->bt;
+    a.bid = s->bid;
+    a.bvx = (double *)(M + o_bv);
+    a.bvy = a.bvx + nb;
+    a.bvz = a.bvy + nb;
     bz::BatchArgs ba;
     memset(&ba, 0, sizeof ba);
-    ba.desc = nullptr;
-    ba.tiles = nullptr;
-    ba.n_tiles = (int32_t)n_tiles;
-    ba.tile_size = tile;
-    ba.tile_counter = (unsigned int *)counter;
+    ba.tile_counter = counter;
     ba.single = a;
+    // tiles over slots [lo, hi): one launch, or in spawn mode one per
+    // generation of newly created electrons until none is left
+    auto launch_range = [&](uint64_t lo, uint64_t hi) {
+        const uint32_t tile = tile_size_for(hi - lo, grid64, 8);
+        const uint64_t n_tiles = (hi - lo + tile - 1) / tile;
+        ba.n_tiles = (int32_t)n_tiles;
+        ba.tile_size = tile;
+        ba.slot_lo = lo;
+        ba.single.n = hi;
+        const int grid = (int)(grid64 < n_tiles ? grid64 : n_tiles);
+        cudaError_t r = cudaMemsetAsync(counter, 0, sizeof(unsigned int), s->stream);
+        if (r == cudaSuccess) r = bz::launch_batch(cfg->precision, ch_smem, ba, a.stage_bytes, grid, block, s->stream);
+        return r;
+    };
     if (e == cudaSuccess) e = cudaEventRecord(s->ev[0], s->stream);
-    if (e == cudaSuccess) e = bz::launch_batch(cfg->precision, ch_smem, ba, a.stage_bytes, grid, block, s->stream);
+    uint64_t total = n;
+    if (!spawn) {
+        if (e == cudaSuccess) e = launch_range(0, n);
+    } else {
+        unsigned long long init = n, now = n;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(n_total, &init, sizeof init, cudaMemcpyHostToDevice, s->stream);
+        uint64_t lo = 0, hi = n;
+        for (uint64_t gen = 0; e == cudaSuccess && hi > lo; ++gen) {
+            if (gen > 1000000) {
+                e = cudaErrorLaunchTimeout;
+                break;
+            }
+            e = launch_range(lo, hi);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(&now, n_total, sizeof now, cudaMemcpyDeviceToHost, s->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+            lo = hi;
+            hi = now < cap ? now : cap;
+        }
+        total = hi;
+        s->n = total;
+    }
     if (e == cudaSuccess) e = cudaEventRecord(s->ev[1], s->stream);
     bz::TallyArgs t;
     memset(&t, 0, sizeof t);
@@ -484,7 +535,10 @@ bz_status bz_run_swarm(bz_ctx *ctx, const bz_mixture *mix, const bz_swarm_config
     t.n_real = s->p.n_real; t.n_null = s->p.n_null; t.n_fail = s->p.n_fail; t.n_ion = s->p.n_ion;
     t.n_att = s->p.n_att; t.status = s->p.status;
     t.steps = s->p.steps;
-    t.n = n;
+    t.n = total;
+    t.n_primary = n;
+    t.ids = spawn ? s->bid : nullptr;
+    t.capped = spawn ? n_capped : nullptr;
     t.id_offset = cfg->id_offset;
     t.part1 = (double *)(M + o_p1);
     t.part2 = (double *)(M + o_p2);
@@ -552,6 +606,26 @@ bz_status bz_read_particles(bz_swarm *sw, const bz_particles *o)
         if ((e = cudaMemcpy(c.dst, c.src, c.bytes, cudaMemcpyDeviceToHost)) != cudaSuccess)
             return cuda_fail(e, "copy of particle state");
     }
+    const uint64_t np = sw->n_primary < n ? sw->n_primary : n;
+    if (o->id) {
+        for (uint64_t i = 0; i < np; ++i) o->id[i] = sw->cfg.id_offset + i;
+        if (n > np && (e = cudaMemcpy(o->id + np, sw->bid, 8 * (n - np), cudaMemcpyDeviceToHost)) != cudaSuccess)
+            return cuda_fail(e, "copy of particle ids");
+    }
+    if (o->t_birth) {
+        for (uint64_t i = 0; i < np; ++i) o->t_birth[i] = 0.0;
+        if (n > np && (e = cudaMemcpy(o->t_birth + np, sw->bt, 8 * (n - np), cudaMemcpyDeviceToHost)) != cudaSuccess)
+            return cuda_fail(e, "copy of birth times");
+    }
+    return BZ_OK;
+}
+
+bz_status bz_swarm_size(bz_swarm *sw, uint64_t *n)
+{
+    if (!sw || !n) return fail(BZ_EINVAL, "null argument");
+    cudaError_t e = cudaEventSynchronize(sw->done);
+    if (e != cudaSuccess) return cuda_fail(e, "swarm");
+    *n = sw->n;
     return BZ_OK;
 }
 
@@ -631,6 +705,7 @@ bz_status bz_create_batch(bz_ctx *ctx, int32_t n, const bz_mixture *const *mixtu
         if (st != BZ_OK) return st;
         if (!mixtures[i]) return fail(BZ_EINVAL, "null mixture");
         if (cfgs[i].precision != precision) return fail(BZ_EINVAL, "all swarms of a batch need the same precision");
+        if (cfgs[i].spawn) return fail(BZ_EINVAL, "spawn-mode swarms run through bz_run_swarm");
         if (cfgs[i].n_electrons > 0xFFFFFFFFull) return fail(BZ_EINVAL, "a batched swarm holds at most 2^32-1 electrons");
     }
     cudaError_t e = cudaSetDevice(ctx->device);
@@ -689,6 +764,8 @@ bz_status bz_create_batch(bz_ctx *ctx, int32_t n, const bz_mixture *const *mixtu
     std::vector<size_t> o_part(n), o_p1(n), o_p2(n), o_gs(n);
     std::vector<int> tb(n);
     b->n_el.resize(n);
+    b->id_offset.resize(n);
+    for (int i = 0; i < n; ++i) b->id_offset[i] = cfgs[i].id_offset;
     b->max_tblocks = 1;
     for (int i = 0; i < n; ++i) {
         const uint64_t m = cfgs[i].n_electrons;
@@ -827,6 +904,10 @@ bz_status bz_batch_read_particles(bz_batch *b, int32_t i, const bz_particles *o)
         if (!c.dst) continue;
         if ((e = cudaMemcpy(c.dst, c.src, c.bytes, cudaMemcpyDeviceToHost)) != cudaSuccess)
             return cuda_fail(e, "copy of particle state");
+    }
+    for (uint64_t k = 0; k < m; ++k) {
+        if (o->id) o->id[k] = b->id_offset[i] + k;
+        if (o->t_birth) o->t_birth[k] = 0.0;
     }
     return BZ_OK;
 }

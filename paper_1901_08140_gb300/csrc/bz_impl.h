@@ -20,7 +20,7 @@ constexpr double kLoschmidt = 2.686780111e25; // m^-3 (273.15 K, 101.325 kPa)
 
 constexpr int kMaxGases = 16;  // gases per mixture
 constexpr int kGroups = 32;   // batch groups for standard errors (id mod 32)
-constexpr int kQ1 = 19;       // first-pass tally quantities
+constexpr int kQ1 = 21;       // first-pass tally quantities
 constexpr int kQ2 = 8;        // second-pass tally quantities
 
 // One interval [e_lo, e_hi) of the union energy grid: the density sum

@@ -21,6 +21,7 @@
 // one TMA bulk copy per block (cp.async.bulk + mbarrier, bounded wait).
 // FP32 kernels keep position and time at real collisions, and the energy
 // sums, as compensated float pairs; all tallies are reduced in FP64.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -303,8 +304,9 @@ struct PState {
     R nu_p, inv_nu;          // trial frequency of this particle
     R T_wend;                // windowed trial frequency: end of the current window (time since last real)
     R u0x, u0y, u0z, bux, buy, buz;  // B != 0: u0 = v_perp - vD and b x u0 at the last real collision
-    Acc<R> x, y, z, t;       // position and time at the last real collision
+    Acc<R> x, y, z, t;       // position and time at the last real collision, relative to birth
     Acc<R> se, se2;          // energy sums before / after real collisions
+    double t0;               // birth time (absolute)
     uint32_t id_lo, id_hi, k, n_real, n_null, n_fail, n_ion, n_att, status;
     bool done;
 };
@@ -512,9 +514,79 @@ __device__ __forceinline__ void init_particle(const Tab<R> &T, const RunArgs &P,
     s.n_real = s.n_null = s.n_fail = s.n_ion = s.n_att = 0;
     s.status = ST_DONE;
     s.done = false;
+    s.t0 = 0.0;
     set_b_cache(F, s);
     s.T_wend = (R)0;
     if (P.window) new_window(T, F, P, s, s.vr0, s.vr1, s.vr2, (R)0);
+}
+
+// Spawn mode: the electron in secondary slot j starts from its birth record.
+template <typename R>
+__device__ __forceinline__ void init_secondary(const Tab<R> &T, const RunArgs &P, const Fld<R> &F, PState<R> &s,
+                                               uint64_t j)
+{
+    const uint64_t id = P.bid[j];
+    s.id_lo = (uint32_t)id;
+    s.id_hi = (uint32_t)(id >> 32);
+    s.vr0 = (R)P.bvx[j];
+    s.vr1 = (R)P.bvy[j];
+    s.vr2 = (R)P.bvz[j];
+    s.T = 0;
+    s.nu_p = (R)P.nu0;
+    s.inv_nu = (R)1 / s.nu_p;
+    s.x.set(0.0);
+    s.y.set(0.0);
+    s.z.set(0.0);
+    s.t.set(0.0);
+    s.se.set(0.0);
+    s.se2.set(0.0);
+    s.k = 0;
+    s.n_real = s.n_null = s.n_fail = s.n_ion = s.n_att = 0;
+    s.status = ST_DONE;
+    s.done = false;
+    s.t0 = P.bt[j];
+    set_b_cache(F, s);
+    s.T_wend = (R)0;
+    if (P.window) new_window(T, F, P, s, s.vr0, s.vr1, s.vr2, (R)0);
+}
+
+// Id of the electron created by the ionization at `step` of electron
+// `parent`: the SplitMix64 finaliser (Steele, Lea, Flood 2014) of
+// parent * 0x9E3779B97F4A7C15 + step + 1, top bit set (never a primary id).
+__device__ __forceinline__ uint64_t secondary_id(uint64_t parent, uint32_t step)
+{
+    uint64_t z = parent * 0x9E3779B97F4A7C15ull + (uint64_t)step + 1ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return z | 0x8000000000000000ull;
+}
+
+// Appends the secondary of an ionization: one atomic per group of lanes
+// that ionize in the same step (warp-aggregated), birth record at its slot.
+template <typename R>
+__device__ __noinline__ void spawn_secondary(const RunArgs &P, const Fld<R> &F, const PState<R> &s, uint32_t step,
+                                             R es, R u_cos, R u_phi)
+{
+    namespace cg = cooperative_groups;
+    cg::coalesced_group g = cg::coalesced_threads();
+    unsigned long long base = 0;
+    if (g.thread_rank() == 0) base = atomicAdd(P.n_total, (unsigned long long)g.size());
+    base = g.shfl(base, 0);
+    const unsigned long long k = base + g.thread_rank();
+    if (k >= P.cap) {
+        atomicAdd(P.n_capped, 1u);
+        return;
+    }
+    const uint64_t j = k - P.n_primary;
+    const R ss = sqrt_(es / F.Ke), ct = (R)1 - (R)2 * u_cos, st = sqrt_(max_((R)0, (R)1 - ct * ct));
+    R sp, cp;
+    azimuth(u_phi, sp, cp);
+    P.bt[j] = s.t0 + s.t.value();
+    P.bvx[j] = (double)(ss * st * cp);
+    P.bvy[j] = (double)(ss * st * sp);
+    P.bvz[j] = (double)(ss * ct);
+    P.bid[j] = secondary_id(((uint64_t)s.id_hi << 32) | s.id_lo, step);
 }
 
 // One trial step.  Returns the decision (channel, DEC_NULL, DEC_FAIL or
@@ -531,13 +603,16 @@ __device__ __forceinline__ int trial(const Tab<R> &T, const Fld<R> &F, const Run
     const uint4 w = philox(s.id_lo, s.id_hi, step, 0u, P.key0, P.key1);
     // Eq. (3): the draw stands for 1 - R
     R Tn = s.T - log_(uni<R>(w.x)) * s.inv_nu;
-    bool cut = false;
-    if (P.t_end > 0.0 && s.t.value() + (double)Tn >= P.t_end) {
-        Tn = (R)(P.t_end - s.t.value());  // TimeBulletLimiter: the flight stops at t_end
-        cut = true;
-    }
-    const bool restart = P.window && !cut && Tn >= s.T_wend;  // the flight outlasts the window
+    // a flight that outlasts the window stops at its end (its nu' holds only there) ...
+    bool restart = P.window && Tn >= s.T_wend;
     if (restart) Tn = s.T_wend;
+    // ... unless t_end comes first: TimeBulletLimiter, the flight stops at t_end
+    bool cut = false;
+    if (P.t_end > 0.0 && s.t0 + s.t.value() + (double)Tn >= P.t_end) {
+        Tn = (R)(P.t_end - s.t0 - s.t.value());
+        cut = true;
+        restart = false;
+    }
     R v0, v1, v2, sn, omc;
     velocity_at(F, s, Tn, v0, v1, v2, sn, omc);
     const R vsq = v0 * v0 + v1 * v1 + v2 * v2;
@@ -550,7 +625,7 @@ __device__ __forceinline__ int trial(const Tab<R> &T, const Fld<R> &F, const Run
         s.x.add(dx);
         s.y.add(dy);
         s.z.add(dz);
-        s.t.set(P.t_end);
+        s.t.set(P.t_end - s.t0);
         s.vr0 = v0;
         s.vr1 = v1;
         s.vr2 = v2;
@@ -633,6 +708,10 @@ __device__ __forceinline__ int trial(const Tab<R> &T, const Fld<R> &F, const Run
                     rotate = false;
                 } else {
                     ratio = 0;  // plastic collision: the electron stops
+                    if (P.spawn) {  // ... and is removed
+                        s.status = ST_ATTACHED;
+                        s.done = true;
+                    }
                 }
             } else {
                 const R x = p.eps_k / eps;  // Eq. (9), radicand clamped at 0
@@ -640,7 +719,9 @@ __device__ __forceinline__ int trial(const Tab<R> &T, const Fld<R> &F, const Run
                 ratio = max_((R)0, (R)1 - p.mfrac * x + p.kappa2 * (sqrt_(rad) * ct - (R)1));
                 if (kind == BZ_IONIZATION) {
                     const uint4 w2 = philox(s.id_lo, s.id_hi, step, 1u, P.key0, P.key1);
-                    ratio *= (R)1 - uni<R>(w2.x);  // the secondary takes the rest
+                    const R u4 = uni<R>(w2.x);
+                    if (P.spawn) spawn_secondary(P, F, s, step, u4 * ratio * eps, uni<R>(w2.y), uni<R>(w2.z));
+                    ratio *= (R)1 - u4;  // the secondary takes the rest
                     ++s.n_ion;
                 }
             }
@@ -873,7 +954,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? BZ_SWARM_MIN_BLOCKS :
         if (B.tiles) {
             tile = B.tiles[ti];
         } else {
-            const uint64_t first = (uint64_t)ti * B.tile_size;
+            const uint64_t first = B.slot_lo + (uint64_t)ti * B.tile_size;
             const uint64_t left = B.single.n - first;
             tile = make_uint4(0u, (uint32_t)first, (uint32_t)(left < B.tile_size ? left : B.tile_size), 0u);
         }
@@ -905,7 +986,8 @@ __global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? BZ_SWARM_MIN_BLOCKS :
                     const unsigned int idx = base + __popc(need & ((1u << lane) - 1u));
                     if (idx < tile.z) {
                         slot = (uint64_t)tile.y + idx;
-                        init_particle<R>(T, P, F, s, P.id_offset + slot);
+                        if (P.spawn && slot >= P.n_primary) init_secondary<R>(T, P, F, s, slot - P.n_primary);
+                        else init_particle<R>(T, P, F, s, P.id_offset + slot);
                         have = true;
                     }
                 }
@@ -962,6 +1044,7 @@ __global__ void __launch_bounds__(kBlock) replay_kernel(const ReplayArgs A)
         s.n_real = s.n_null = s.n_fail = s.n_ion = s.n_att = 0;
         s.status = ST_DONE;
         s.done = false;
+        s.t0 = 0.0;
         set_b_cache(F, s);
         s.T_wend = (R)0;
         if (P.window) new_window(T, F, P, s, s.vr0, s.vr1, s.vr2, (R)0);
@@ -1022,39 +1105,84 @@ __device__ void block_group_reduce(double (&acc)[Q], double *out_block, uint64_t
     }
 }
 
+// Pass-1 quantities of particle i (see the layout comment below).
+__device__ __forceinline__ void pass1_contrib(const TallyArgs &A, uint64_t i, double (&c)[kQ1])
+{
+#pragma unroll
+    for (int q = 0; q < kQ1; ++q) c[q] = 0.0;
+    const double t = A.t[i];
+    const uint32_t st = A.status[i];
+    c[17] = (st != ST_DONE && st != ST_TIME && st != ST_ATTACHED) ? 1.0 : 0.0;
+    c[19] = (st == ST_TIME) ? 1.0 : 0.0;
+    c[20] = (st == ST_ATTACHED) ? 1.0 : 0.0;
+    if (!(t > 0.0)) return;
+    const double x = A.x[i], y = A.y[i], z = A.z[i];
+    const double G = (double)A.n_ion[i], D = (double)A.n_att[i];
+    c[0] = 1.0;
+    c[1] = x / t;
+    c[2] = y / t;
+    c[3] = z / t;
+    c[4] = G / z;
+    c[5] = D / z;
+    c[6] = x;
+    c[7] = y;
+    c[8] = z;
+    c[9] = t;
+    c[10] = A.se[i];
+    c[11] = A.se2[i];
+    c[12] = (double)A.n_real[i];
+    c[13] = (double)A.n_null[i];
+    c[14] = (double)A.n_fail[i];
+    c[15] = G;
+    c[16] = D;
+    c[18] = A.steps ? (double)A.steps[i] : 0.0;
+}
+
+// Batch group (id mod 32) of particle i; secondaries carry their own ids.
+__device__ __forceinline__ int group_of(const TallyArgs &A, uint64_t i)
+{
+    const uint64_t id = (A.ids && i >= A.n_primary) ? A.ids[i - A.n_primary] : A.id_offset + i;
+    return (int)(id & 31u);
+}
+
+// Groups by particle id through shared-memory atomics (spawn mode, where a
+// thread's particles do not share one group).
+template <int Q, typename Fn>
+__device__ void id_group_reduce(const TallyArgs &A, int bx, int nbx, double *out_block, Fn contrib)
+{
+    __shared__ double gs[kGroups * (kQ1 > kQ2 ? kQ1 : kQ2)];
+    for (int k = threadIdx.x; k < kGroups * Q; k += blockDim.x) gs[k] = 0.0;
+    __syncthreads();
+    const uint64_t stride = (uint64_t)nbx * blockDim.x;
+    for (uint64_t i = (uint64_t)bx * blockDim.x + threadIdx.x; i < A.n; i += stride) {
+        double c[Q];
+        contrib(i, c);
+        const int g = group_of(A, i);
+        for (int q = 0; q < Q; ++q)
+            if (c[q] != 0.0) atomicAdd(&gs[g * Q + q], c[q]);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < kGroups * Q; k += blockDim.x) out_block[k] = gs[k];
+}
+
 __device__ void tally_pass1_body(const TallyArgs &A, int bx, int nbx)
 {
+    double *out = A.part1 + (size_t)bx * kGroups * kQ1;
+    if (A.ids) {
+        id_group_reduce<kQ1>(A, bx, nbx, out, [&](uint64_t i, double(&c)[kQ1]) { pass1_contrib(A, i, c); });
+        return;
+    }
     double acc[kQ1];
 #pragma unroll
     for (int q = 0; q < kQ1; ++q) acc[q] = 0.0;
     const uint64_t stride = (uint64_t)nbx * blockDim.x;
     for (uint64_t i = (uint64_t)bx * blockDim.x + threadIdx.x; i < A.n; i += stride) {
-        const double t = A.t[i];
-        const uint32_t st = A.status[i];
-        acc[17] += (st != ST_DONE && st != ST_TIME) ? 1.0 : 0.0;
-        if (!(t > 0.0)) continue;
-        const double x = A.x[i], y = A.y[i], z = A.z[i];
-        const double G = (double)A.n_ion[i], D = (double)A.n_att[i];
-        acc[0] += 1.0;
-        acc[1] += x / t;
-        acc[2] += y / t;
-        acc[3] += z / t;
-        acc[4] += G / z;
-        acc[5] += D / z;
-        acc[6] += x;
-        acc[7] += y;
-        acc[8] += z;
-        acc[9] += t;
-        acc[10] += A.se[i];
-        acc[11] += A.se2[i];
-        acc[12] += (double)A.n_real[i];
-        acc[13] += (double)A.n_null[i];
-        acc[14] += (double)A.n_fail[i];
-        acc[15] += G;
-        acc[16] += D;
-        acc[18] += A.steps ? (double)A.steps[i] : 0.0;
+        double c[kQ1];
+        pass1_contrib(A, i, c);
+#pragma unroll
+        for (int q = 0; q < kQ1; ++q) acc[q] += c[q];
     }
-    block_group_reduce<kQ1>(acc, A.part1 + (size_t)bx * kGroups * kQ1, A.id_offset);
+    block_group_reduce<kQ1>(acc, out, A.id_offset);
 }
 
 // gsum layout: [g][0..kQ1) pass 1, [g][kQ1..kQ1+kQ2) pass 2, then summary
@@ -1093,31 +1221,46 @@ __device__ void tally_mid_body(const TallyArgs &A)
     }
 }
 
+__device__ __forceinline__ void pass2_contrib(const TallyArgs &A, uint64_t i, const double *S, double (&c)[kQ2])
+{
+#pragma unroll
+    for (int q = 0; q < kQ2; ++q) c[q] = 0.0;
+    const double t = A.t[i];
+    if (!(t > 0.0)) return;
+    const double Wx = S[0], Wy = S[1], Wz = S[2], Fx = S[3], Fy = S[4], Fz = S[5];
+    const double x = A.x[i], y = A.y[i], z = A.z[i];
+    const double dx = x - t * Wx, dy = y - t * Wy, dz = z - t * Wz;
+    const double dp2 = dx * dx + dy * dy, d2 = dp2 + dz * dz;
+    c[0] = d2 / t;
+    c[1] = dz * dz / (2.0 * t);
+    c[2] = dp2 / (4.0 * t);
+    c[3] = 2.0 * sqrt(d2);
+    c[4] = 2.0 * fabs(dz);
+    c[5] = 2.0 * sqrt(dp2);
+    const double fz = z - Fz * t, fx = x - Fx * t, fy = y - Fy * t;
+    c[6] = fz * fz;
+    c[7] = fx * fx + fy * fy;
+}
+
 __device__ void tally_pass2_body(const TallyArgs &A, int bx, int nbx)
 {
     const double *S = A.gsum + kGroups * kGS;
-    const double Wx = S[0], Wy = S[1], Wz = S[2], Fx = S[3], Fy = S[4], Fz = S[5];
+    double *out = A.part2 + (size_t)bx * kGroups * kQ2;
+    if (A.ids) {
+        id_group_reduce<kQ2>(A, bx, nbx, out, [&](uint64_t i, double(&c)[kQ2]) { pass2_contrib(A, i, S, c); });
+        return;
+    }
     double acc[kQ2];
 #pragma unroll
     for (int q = 0; q < kQ2; ++q) acc[q] = 0.0;
     const uint64_t stride = (uint64_t)nbx * blockDim.x;
     for (uint64_t i = (uint64_t)bx * blockDim.x + threadIdx.x; i < A.n; i += stride) {
-        const double t = A.t[i];
-        if (!(t > 0.0)) continue;
-        const double x = A.x[i], y = A.y[i], z = A.z[i];
-        const double dx = x - t * Wx, dy = y - t * Wy, dz = z - t * Wz;
-        const double dp2 = dx * dx + dy * dy, d2 = dp2 + dz * dz;
-        acc[0] += d2 / t;
-        acc[1] += dz * dz / (2.0 * t);
-        acc[2] += dp2 / (4.0 * t);
-        acc[3] += 2.0 * sqrt(d2);
-        acc[4] += 2.0 * fabs(dz);
-        acc[5] += 2.0 * sqrt(dp2);
-        const double fz = z - Fz * t, fx = x - Fx * t, fy = y - Fy * t;
-        acc[6] += fz * fz;
-        acc[7] += fx * fx + fy * fy;
+        double c[kQ2];
+        pass2_contrib(A, i, S, c);
+#pragma unroll
+        for (int q = 0; q < kQ2; ++q) acc[q] += c[q];
     }
-    block_group_reduce<kQ2>(acc, A.part2 + (size_t)bx * kGroups * kQ2, A.id_offset);
+    block_group_reduce<kQ2>(acc, out, A.id_offset);
 }
 
 __device__ double group_se(const double *v, const bool *has, int G)
@@ -1192,6 +1335,10 @@ __device__ void tally_final_body(const TallyArgs &A)
     o.n_ion = (uint64_t)(tot[15] + 0.5);
     o.n_att = (uint64_t)(tot[16] + 0.5);
     o.n_incomplete = (uint64_t)(tot[17] + 0.5);
+    o.n_alive = (uint64_t)(tot[19] + 0.5);
+    o.n_removed = (uint64_t)(tot[20] + 0.5);
+    o.n_spawned = A.n > A.n_primary && A.ids ? A.n - A.n_primary : 0;
+    o.n_capped = A.capped ? (uint64_t)*A.capped : 0;
     const double other = tot[18] - trials;  // steps that were neither real, null nor fail: window restarts
     o.n_window = other > 0.5 ? (uint64_t)(other + 0.5) : 0;
     o.error_flags = (int32_t)*A.err;

@@ -8,7 +8,7 @@
 
 namespace bz {
 
-enum { ST_DONE = 0, ST_TIME = 1, ST_STEPS = 2, ST_TRIAL = 3, ST_ERROR = 4 };
+enum { ST_DONE = 0, ST_TIME = 1, ST_STEPS = 2, ST_TRIAL = 3, ST_ERROR = 4, ST_ATTACHED = 5 };
 enum { DEC_WINDOW = -3, DEC_FAIL = -2, DEC_NULL = -1 };
 
 // Uniform static fields in the force frame (force on the electron along +z).
@@ -43,6 +43,15 @@ struct RunArgs {
     int32_t window;          // windowed local trial frequency
     float win_c;             // window length in units of 1/nu of the current energy bin
     double nu_floor;         // lower bound of any trial frequency [1/s]
+    // spawn mode: slots [0, n_primary) are the initial electrons; secondaries
+    // take slots from *n_total (up to cap) and their birth state from b*[slot - n_primary]
+    int32_t spawn;
+    uint64_t n_primary, cap;
+    unsigned long long *n_total;
+    unsigned int *n_capped;
+    double *bt;
+    double *bvx, *bvy, *bvz;
+    uint64_t *bid;
     Fields f;
     unsigned long long *counter;  // next particle slot
     uint32_t *err;
@@ -64,7 +73,9 @@ struct TallyArgs {
     const double *x, *y, *z, *t, *se, *se2;
     const uint32_t *n_real, *n_null, *n_fail, *n_ion, *n_att, *status;
     const uint32_t *steps;   // may be null (no window-restart count)
-    uint64_t n, id_offset;
+    const uint64_t *ids;     // spawn mode: ids of slots >= n_primary (null otherwise)
+    const unsigned int *capped;  // spawn mode: capped-ionization counter (may be null)
+    uint64_t n, id_offset, n_primary;
     double *part1, *part2;   // [blocks][kGroups][kQ1 | kQ2] scratch
     double *gsum;            // [kGroups][kQ1 + kQ2] + 8 summary values, scratch
     int32_t blocks;
@@ -81,6 +92,7 @@ struct BatchArgs {
     int32_t n_tiles;
     uint32_t tile_size;
     unsigned int *tile_counter;
+    uint64_t slot_lo;        // implicit tiles start at this slot
     RunArgs single;
 };
 

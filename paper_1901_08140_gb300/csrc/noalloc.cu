@@ -26,7 +26,7 @@ namespace {
 constexpr size_t kPart1 = (size_t)BZ_NOALLOC_MAX_BLOCKS * bz::kGroups * bz::kQ1;
 constexpr size_t kPart2 = (size_t)BZ_NOALLOC_MAX_BLOCKS * bz::kGroups * bz::kQ2;
 constexpr size_t kGsum = (size_t)bz::kGroups * (bz::kQ1 + bz::kQ2) + 8;
-static_assert(bz::kQ1 + bz::kQ2 == 27, "scratch size formula in bz.h assumes 27 quantities");
+static_assert(bz::kQ1 + bz::kQ2 == 29, "scratch size formula in bz.h assumes 29 quantities");
 static_assert(8 * (kPart1 + kPart2 + kGsum) + 256 <= BZ_NOALLOC_SCRATCH_BYTES, "scratch too small");
 
 static __device__ __align__(256) unsigned char g_scratch[BZ_NOALLOC_SCRATCH_BYTES];

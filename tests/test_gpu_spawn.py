@@ -1,0 +1,104 @@
+"""Spawn mode on the GPU: ionizations create electrons, attachments remove
+them (Sec. 2), checked against closed forms and against the oracle."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1901_08140_gb300 import bz
+from paper_1901_08140_gb300 import workloads as W
+from test_oracle_pins import _const_rate_gas
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1901_08140_gb300 import build as B
+    B.build()
+    c = bz.Context(0)
+    yield c
+    c.close()
+
+
+def _run(ctx, gases, **kw):
+    mix = bz.Mixture(ctx, gases)
+    sw = bz.run_swarm(ctx, mix, bz.make_config(**kw))
+    t = sw.tallies()
+    p = sw.particles()
+    sw.close()
+    return t, p
+
+
+@pytest.mark.parametrize("mode", [bz.BZ_TRIAL_LAZY, bz.BZ_TRIAL_WINDOW])
+def test_yule_growth_on_gpu(ctx, mode):
+    nu_i = 1e11
+    n0, t_end = 20000, 3.0 / nu_i
+    t, p = _run(ctx, [_const_rate_gas(1e12, nu_ion=nu_i)], n_electrons=n0, real_collisions=10 ** 9,
+                e_over_n_Td=50.0, seed=21, t_end_s=t_end, spawn=True, pop_cap=2_000_000, trial_mode=mode)
+    total = len(p["t"])
+    expect = n0 * math.exp(nu_i * t_end)
+    sd = math.sqrt(n0 * math.exp(nu_i * t_end) * (math.exp(nu_i * t_end) - 1))
+    assert abs(total - expect) < 4 * sd
+    assert t["n_spawned"] == total - n0 == int(p["n_ion"].sum())
+    assert t["n_alive"] == total and t["n_capped"] == 0 and t["error_flags"] == 0
+    assert np.allclose(p["t_birth"] + p["t"], t_end, rtol=1e-6, atol=0)
+    assert len(np.unique(p["id"])) == total
+
+
+def test_attachment_removes_on_gpu(ctx):
+    nu_a = 1e11
+    n0, t_end = 100000, 1.5 / nu_a
+    t, p = _run(ctx, [_const_rate_gas(1e12, nu_att=nu_a)], n_electrons=n0, real_collisions=10 ** 9,
+                e_over_n_Td=10.0, seed=5, t_end_s=t_end, spawn=True, pop_cap=n0)
+    q = math.exp(-nu_a * t_end)
+    assert abs(t["n_alive"] - n0 * q) < 4 * math.sqrt(n0 * q * (1 - q))
+    assert t["n_removed"] == n0 - t["n_alive"] == int(np.sum(p["status"] == bz.ST_ATTACHED))
+
+
+def test_spawn_fp64_matches_oracle_electron_by_electron(ctx):
+    gases = W.ar_co2_mixture()
+    kw = dict(e_over_n_Td=400.0, real_collisions=10 ** 6, seed=77, t_end_s=3e-11)
+    n0, cap = 300, 100000
+    t, p = _run(ctx, gases, n_electrons=n0, precision=64, spawn=True, pop_cap=cap, **kw)
+    m = O.Mixture(gases)
+    po = O.run_swarm_spawn(m, n=n0, pop_cap=cap, t_end=kw["t_end_s"], e_over_n_Td=kw["e_over_n_Td"],
+                           real_collisions=kw["real_collisions"], seed=kw["seed"])
+    assert len(po["id"]) > 2 * n0   # the avalanche grew
+    og = {int(i): k for k, i in enumerate(p["id"])}
+    oo = {int(i): k for k, i in enumerate(po["id"])}
+    common = set(og) & set(oo)
+    assert len(common) >= 0.95 * max(len(og), len(oo))
+    same = 0
+    for i in common:
+        a, b = og[i], oo[i]
+        if all(p[k][a] == po[k][b] for k in ("n_real", "n_null", "n_ion", "n_att", "steps", "status")):
+            same += 1
+            assert abs(p["t_birth"][a] - po["t_birth"][b]) <= 1e-9 * kw["t_end_s"]
+            assert abs(p["z"][a] - po["z"][b]) <= 1e-9 * (abs(po["z"][b]) + 1e-12)
+    assert same >= 0.95 * len(common)
+
+
+def test_population_cap(ctx):
+    nu_i = 1e11
+    t, p = _run(ctx, [_const_rate_gas(1e12, nu_ion=nu_i)], n_electrons=1000, real_collisions=10 ** 9,
+                e_over_n_Td=50.0, seed=3, t_end_s=5.0 / nu_i, spawn=True, pop_cap=20000)
+    assert len(p["t"]) == 20000 and t["n_capped"] > 0
+    assert int(p["n_ion"].sum()) == t["n_spawned"] + t["n_capped"]
+
+
+def test_avalanche_request_shape(ctx):
+    """A 1 ns avalanche in the Ar/CO2-like mixture at 300 Td from one seed of electrons."""
+    t, p = _run(ctx, W.ar_co2_mixture(), n_electrons=100, real_collisions=10 ** 9, e_over_n_Td=300.0, seed=9,
+                t_end_s=1e-9, spawn=True, pop_cap=5_000_000, trial_mode=bz.BZ_TRIAL_WINDOW)
+    assert t["n_particles"] == len(p["t"]) > 100
+    assert t["n_alive"] + t["n_removed"] + t["n_incomplete"] == len(p["t"])
+    assert t["error_flags"] == 0 and math.isfinite(t["W"]) and t["W"] > 0
+
+
+def test_batch_rejects_spawn(ctx):
+    mix = bz.Mixture(ctx, [W.argon_like()])
+    cfg = bz.make_config(n_electrons=10, real_collisions=10, e_over_n_Td=10.0, spawn=True)
+    with pytest.raises(bz.BzError):
+        bz.Batch(ctx, [mix], [cfg])
