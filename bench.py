@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serve-rates", default="250,1000,2000", help="Poisson arrival rates [req/s] of the serving run")
     ap.add_argument("--serve-seconds", type=float, default=1.0, help="arrival window of each serving run")
+    ap.add_argument("--avalanche-cap", type=int, default=100_000,
+                    help="population cap of the serving run's avalanche requests")
+    ap.add_argument("--avalanche-frac", type=float, default=0.05, help="fraction of avalanche requests")
     ap.add_argument("--trial", choices=["window", "lazy"], default="window",
                     help="trial frequency: exact windowed local bound (default) or the constant maximum")
     return ap.parse_args()
@@ -175,15 +178,19 @@ def _timed(stream, flush, steps, fn, world, dev):
     return total, outs
 
 
-def serving_runs(ctx, rates, seconds, collisions=100, pool=64, streams=3):
+def serving_runs(ctx, rates, seconds, collisions=100, pool=64, streams=3, avalanche_frac=0.05,
+                 avalanche_cap=100_000):
     """Continuous-batching request loop under Poisson arrivals: swarm sizes,
     mixtures and fields of the batched workload (a pool of compiled
-    mixtures), I real collisions per request, windowed trial frequency."""
+    mixtures), I real collisions per request, windowed trial frequency; a
+    fraction are avalanche requests (Ar/CO2 93/7, 300 Td, spawn mode, one
+    seed electron, 1 ns, population cap avalanche_cap)."""
     from paper_1901_08140_gb300 import bz, serving
     from paper_1901_08140_gb300 import workloads as W
     import numpy as np
     specs = W.batched_swarms(count=pool, real_collisions=collisions)
     mixes = [bz.Mixture(ctx, s.gases) for s in specs]
+    ava_mix = bz.Mixture(ctx, W.ar_co2_avalanche_mixture())
     backend = serving.GpuBatchBackend(ctx, n_streams=streams)
     out = []
     for k, rate in enumerate(rates):
@@ -192,13 +199,27 @@ def serving_runs(ctx, rates, seconds, collisions=100, pool=64, streams=3):
         rng = np.random.default_rng(200 + k)
         reqs = []
         for i in range(n):
+            seed = W.swarm_seed(10 ** 6 + 10 ** 4 * k + i)
+            if rng.uniform() < avalanche_frac:
+                cfg = bz.make_config(n_electrons=1, real_collisions=10 ** 9, e_over_n_Td=300.0, seed=seed,
+                                     t_end_s=1e-9, spawn=True, pop_cap=avalanche_cap,
+                                     trial_mode=bz.BZ_TRIAL_WINDOW)
+                reqs.append(serving.Request(i, ava_mix, cfg, arrival=float(arr[i]), n_electrons=1))
+                continue
             j = int(rng.integers(pool))
-            cfg = bz.config_from_spec(specs[j], trial_mode=bz.BZ_TRIAL_WINDOW, seed=W.swarm_seed(10 ** 6 + 10 ** 4 * k + i))
+            cfg = bz.config_from_spec(specs[j], trial_mode=bz.BZ_TRIAL_WINDOW, seed=seed)
             reqs.append(serving.Request(i, mixes[j], cfg, arrival=float(arr[i]), n_electrons=int(cfg.n_electrons)))
         srv = serving.Server(backend, memory_budget=60e9)
         done = srv.run(reqs, realtime=True)
         summ = serving.latency_summary(done)
-        offered = sum(r.n_electrons for r in reqs) * collisions / arr[-1] if n > 1 else float("nan")
+        ava = [r for r in done if getattr(r.cfg, "spawn", 0)]
+        plain = [r for r in done if not getattr(r.cfg, "spawn", 0)]
+        offered = sum(r.n_electrons for r in plain) * collisions / arr[-1] if n > 1 else float("nan")
+        if ava:
+            summ["avalanche"] = {"requests": len(ava),
+                                 "p99_ms": float(np.percentile([r.latency for r in ava], 99) * 1e3),
+                                 "mean_final_population": float(np.mean([r.tallies["n_particles"] for r in ava]))}
+        offered += sum(r.tallies["n_real"] for r in ava) / arr[-1] if n > 1 else 0.0
         summ.update({"rate_req_s": rate, "offered_real_collisions_per_s": offered,
                      "max_concurrent": srv.max_concurrent, "launch_groups": srv.groups})
         out.append(summ)
@@ -314,7 +335,8 @@ def run_ours(args):
     serve = None
     if not args.no_serving and rank == 0:
         rates = [float(x) for x in args.serve_rates.split(",") if x]
-        serve = serving_runs(ctx, rates, args.serve_seconds)
+        serve = serving_runs(ctx, rates, args.serve_seconds, avalanche_frac=args.avalanche_frac,
+                             avalanche_cap=args.avalanche_cap)
     if rank != 0:
         return
     cpu = None

@@ -201,8 +201,9 @@ bz_status bz_set_fields(bz_swarm_config *cfg, double e_over_n_Td, double b_T, do
  * attachment removes the electron; past pop_cap electrons, ionizations are
  * only counted.  Every electron has its own limiters (I real collisions,
  * absolute t_end) and reports position and time relative to its birth.  In
- * spawn mode the call runs generation after generation of new electrons
- * and returns when none is left (it blocks).
+ * spawn mode one persistent launch runs every electron: lanes that finish
+ * an electron take the next created one as soon as its birth record is
+ * published, until none is left; the call returns at once here too.
  * Errors: BZ_EINVAL, BZ_ENOMEM, BZ_ECUDA. */
 bz_status bz_run_swarm(bz_ctx *ctx, const bz_mixture *mix, const bz_swarm_config *cfg,
                        void *stream, bz_swarm **out);
@@ -240,6 +241,7 @@ typedef struct {
 #define BZ_ERR_TRIAL 2u         /* fixed nu' exceeded */
 #define BZ_ERR_NONFINITE 4u     /* non-finite energy met; particle stopped */
 #define BZ_ERR_MAX_TRIALS 8u    /* a particle reached max_trials */
+#define BZ_ERR_SPAWN_WAIT 16u   /* spawn mode: a lane waited > 60 s for work */
 
 /* Waits for the swarm and copies its tallies into *out.
  * Errors: BZ_ETRIAL (fixed mode exceeded), BZ_ETIMEOUT, BZ_ECUDA. */

@@ -413,7 +413,8 @@ bz_status bz_run_swarm(bz_ctx *ctx, const bz_mixture *mix, const bz_swarm_config
     const uint64_t cap = spawn ? (cfg->pop_cap ? cfg->pop_cap : 64 * n) : n;  // electron slots
     if (cap > 0xFFFFFFFFull) return fail(BZ_EINVAL, "a swarm holds at most 2^32-1 electrons");
     const int block = 256;
-    int bps = bz::batch_occupancy(cfg->precision, ch_smem, block, a.stage_bytes);
+    int bps = spawn ? bz::spawn_occupancy(cfg->precision, ch_smem, block, a.stage_bytes)
+                    : bz::batch_occupancy(cfg->precision, ch_smem, block, a.stage_bytes);
     if (bps < 1) return fail(BZ_ECUDA, "step kernel cannot be resident with these tables");
     if (cfg->blocks_per_sm > 0 && cfg->blocks_per_sm < bps) bps = cfg->blocks_per_sm;
     const uint64_t grid64 = (uint64_t)ctx->sm_count * bps;
@@ -435,7 +436,8 @@ bz_status bz_run_swarm(bz_ctx *ctx, const bz_mixture *mix, const bz_swarm_config
     const size_t o_se = take(8 * m), o_se2 = take(8 * m);
     const size_t o_vx = take(4 * m), o_vy = take(4 * m), o_vz = take(4 * m), o_nup = take(4 * m);
     const size_t o_u[7] = {take(4 * m), take(4 * m), take(4 * m), take(4 * m), take(4 * m), take(4 * m), take(4 * m)};
-    const size_t o_ctr = take(32);  // tile counter, error word, capped counter, electron counter
+    // tile counter, error word, capped counter; spawn mode: electrons, pending, ticket
+    const size_t o_ctr = take(48);
     const uint64_t nb = spawn ? cap - n : 0;
     const size_t o_bt = take(8 * nb), o_bid = take(8 * nb), o_bv = take(24 * nb);
     const size_t o_p1 = take(sizeof(double) * tblocks * bz::kGroups * bz::kQ1);
@@ -459,6 +461,8 @@ bz_status bz_run_swarm(bz_ctx *ctx, const bz_mixture *mix, const bz_swarm_config
     s->err = (uint32_t *)(M + o_ctr + 8);
     unsigned int *n_capped = (unsigned int *)(M + o_ctr + 12);
     unsigned long long *n_total = (unsigned long long *)(M + o_ctr + 16);
+    unsigned long long *pending = (unsigned long long *)(M + o_ctr + 24);
+    unsigned long long *ticket = (unsigned long long *)(M + o_ctr + 32);
     s->bt = (double *)(M + o_bt);
     s->bid = (uint64_t *)(M + o_bid);
     s->tallies_dev = (bz_tallies *)(M + o_tal);
@@ -474,7 +478,7 @@ bz_status bz_run_swarm(bz_ctx *ctx, const bz_mixture *mix, const bz_swarm_config
         return cuda_fail(e, "swarm set-up");
     }
     for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaEventCreate(&s->ev[i]);
-    if (e == cudaSuccess) e = cudaMemsetAsync(M + o_ctr, 0, 32, s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(M + o_ctr, 0, 48, s->stream);
     a.counter = nullptr;
     a.err = s->err;
     a.out = s->p;
@@ -482,51 +486,41 @@ bz_status bz_run_swarm(bz_ctx *ctx, const bz_mixture *mix, const bz_swarm_config
     a.n_primary = n;
     a.cap = cap;
     a.n_total = n_total;
+    a.pending = pending;
     a.n_capped = n_capped;
     a.bt = s->bt;
     a.bid = s->bid;
     a.bvx = (double *)(M + o_bv);
     a.bvy = a.bvx + nb;
     a.bvz = a.bvy + nb;
-    bz::BatchArgs ba;
-    memset(&ba, 0, sizeof ba);
-    ba.tile_counter = counter;
-    ba.single = a;
-    // tiles over slots [lo, hi): one launch, or in spawn mode one per
-    // generation of newly created electrons until none is left
-    auto launch_range = [&](uint64_t lo, uint64_t hi) {
-        const uint32_t tile = tile_size_for(hi - lo, grid64, 8);
-        const uint64_t n_tiles = (hi - lo + tile - 1) / tile;
+    const unsigned long long init[2] = {n, n};  // spawn mode: electrons, pending
+    if (spawn) {
+        // unpublished birth records read as id 0
+        a.counter = ticket;
+        if (e == cudaSuccess && nb) e = cudaMemsetAsync(s->bid, 0, 8 * nb, s->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(n_total, init, sizeof init, cudaMemcpyHostToDevice, s->stream);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(s->ev[0], s->stream);
+    if (!spawn) {
+        // tiles over all slots, one launch
+        bz::BatchArgs ba;
+        memset(&ba, 0, sizeof ba);
+        ba.tile_counter = counter;
+        ba.single = a;
+        const uint32_t tile = tile_size_for(n, grid64, 8);
+        const uint64_t n_tiles = (n + tile - 1) / tile;
         ba.n_tiles = (int32_t)n_tiles;
         ba.tile_size = tile;
-        ba.slot_lo = lo;
-        ba.single.n = hi;
+        ba.slot_lo = 0;
         const int grid = (int)(grid64 < n_tiles ? grid64 : n_tiles);
-        cudaError_t r = cudaMemsetAsync(counter, 0, sizeof(unsigned int), s->stream);
-        if (r == cudaSuccess) r = bz::launch_batch(cfg->precision, ch_smem, ba, a.stage_bytes, grid, block, s->stream);
-        return r;
-    };
-    if (e == cudaSuccess) e = cudaEventRecord(s->ev[0], s->stream);
-    uint64_t total = n;
-    if (!spawn) {
-        if (e == cudaSuccess) e = launch_range(0, n);
+        if (e == cudaSuccess && n_tiles > 0)
+            e = bz::launch_batch(cfg->precision, ch_smem, ba, a.stage_bytes, grid, block, s->stream);
     } else {
-        unsigned long long init = n, now = n;
-        if (e == cudaSuccess) e = cudaMemcpyAsync(n_total, &init, sizeof init, cudaMemcpyHostToDevice, s->stream);
-        uint64_t lo = 0, hi = n;
-        for (uint64_t gen = 0; e == cudaSuccess && hi > lo; ++gen) {
-            if (gen > 1000000) {
-                e = cudaErrorLaunchTimeout;
-                break;
-            }
-            e = launch_range(lo, hi);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(&now, n_total, sizeof now, cudaMemcpyDeviceToHost, s->stream);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-            lo = hi;
-            hi = now < cap ? now : cap;
-        }
-        total = hi;
-        s->n = total;
+        // every electron, created ones included, in one persistent launch
+        uint64_t want = (cap + block - 1) / block;
+        if (want < (uint64_t)ctx->sm_count) want = ctx->sm_count;
+        const int grid = (int)(grid64 < want ? grid64 : want);
+        if (e == cudaSuccess) e = bz::launch_spawn(cfg->precision, ch_smem, a, a.stage_bytes, grid, block, s->stream);
     }
     if (e == cudaSuccess) e = cudaEventRecord(s->ev[1], s->stream);
     bz::TallyArgs t;
@@ -535,7 +529,8 @@ bz_status bz_run_swarm(bz_ctx *ctx, const bz_mixture *mix, const bz_swarm_config
     t.n_real = s->p.n_real; t.n_null = s->p.n_null; t.n_fail = s->p.n_fail; t.n_ion = s->p.n_ion;
     t.n_att = s->p.n_att; t.status = s->p.status;
     t.steps = s->p.steps;
-    t.n = total;
+    t.n = spawn ? cap : n;
+    t.n_dev = spawn ? n_total : nullptr;
     t.n_primary = n;
     t.ids = spawn ? s->bid : nullptr;
     t.capped = spawn ? n_capped : nullptr;
@@ -588,12 +583,19 @@ bz_status bz_query_tallies(bz_swarm *sw, bz_tallies *out)
     return finish_tallies(sw, out);
 }
 
+// Electrons in a finished swarm (spawn mode: the primaries and the created ones).
+static uint64_t swarm_count(const bz_swarm *sw)
+{
+    if (!sw->cfg.spawn) return sw->n;
+    return sw->n_primary + sw->tallies_host->n_spawned;
+}
+
 bz_status bz_read_particles(bz_swarm *sw, const bz_particles *o)
 {
     if (!sw || !o) return fail(BZ_EINVAL, "null argument");
     cudaError_t e = cudaEventSynchronize(sw->done);
     if (e != cudaSuccess) return cuda_fail(e, "swarm");
-    const size_t n = sw->n;
+    const size_t n = sw->n = swarm_count(sw);
     struct { void *dst; const void *src; size_t bytes; } cp[] = {
         {o->x, sw->p.x, 8 * n}, {o->y, sw->p.y, 8 * n}, {o->z, sw->p.z, 8 * n}, {o->t, sw->p.t, 8 * n},
         {o->sum_e, sw->p.se, 8 * n}, {o->sum_e2, sw->p.se2, 8 * n}, {o->vx, sw->p.vx, 4 * n},
@@ -625,7 +627,7 @@ bz_status bz_swarm_size(bz_swarm *sw, uint64_t *n)
     if (!sw || !n) return fail(BZ_EINVAL, "null argument");
     cudaError_t e = cudaEventSynchronize(sw->done);
     if (e != cudaSuccess) return cuda_fail(e, "swarm");
-    *n = sw->n;
+    *n = sw->n = swarm_count(sw);
     return BZ_OK;
 }
 

@@ -525,12 +525,13 @@ template <typename R>
 __device__ __forceinline__ void init_secondary(const Tab<R> &T, const RunArgs &P, const Fld<R> &F, PState<R> &s,
                                                uint64_t j)
 {
-    const uint64_t id = P.bid[j];
+    // the record was published by another SM: read it from L2
+    const uint64_t id = __ldcg(P.bid + j);
     s.id_lo = (uint32_t)id;
     s.id_hi = (uint32_t)(id >> 32);
-    s.vr0 = (R)P.bvx[j];
-    s.vr1 = (R)P.bvy[j];
-    s.vr2 = (R)P.bvz[j];
+    s.vr0 = (R)__ldcg(P.bvx + j);
+    s.vr1 = (R)__ldcg(P.bvy + j);
+    s.vr2 = (R)__ldcg(P.bvz + j);
     s.T = 0;
     s.nu_p = (R)P.nu0;
     s.inv_nu = (R)1 / s.nu_p;
@@ -544,7 +545,7 @@ __device__ __forceinline__ void init_secondary(const Tab<R> &T, const RunArgs &P
     s.n_real = s.n_null = s.n_fail = s.n_ion = s.n_att = 0;
     s.status = ST_DONE;
     s.done = false;
-    s.t0 = P.bt[j];
+    s.t0 = __ldcg(P.bt + j);
     set_b_cache(F, s);
     s.T_wend = (R)0;
     if (P.window) new_window(T, F, P, s, s.vr0, s.vr1, s.vr2, (R)0);
@@ -562,8 +563,22 @@ __device__ __forceinline__ uint64_t secondary_id(uint64_t parent, uint32_t step)
     return z | 0x8000000000000000ull;
 }
 
+__device__ __forceinline__ void st_release(uint64_t *p, uint64_t v)
+{
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ uint64_t ld_acquire(const uint64_t *p)
+{
+    uint64_t v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
 // Appends the secondary of an ionization: one atomic per group of lanes
-// that ionize in the same step (warp-aggregated), birth record at its slot.
+// that ionize in the same step (warp-aggregated) takes their slots and
+// counts them as pending before any of them can finish; the birth record
+// is written at the slot and published by storing the id last (release).
 template <typename R>
 __device__ __noinline__ void spawn_secondary(const RunArgs &P, const Fld<R> &F, const PState<R> &s, uint32_t step,
                                              R es, R u_cos, R u_phi)
@@ -571,7 +586,12 @@ __device__ __noinline__ void spawn_secondary(const RunArgs &P, const Fld<R> &F, 
     namespace cg = cooperative_groups;
     cg::coalesced_group g = cg::coalesced_threads();
     unsigned long long base = 0;
-    if (g.thread_rank() == 0) base = atomicAdd(P.n_total, (unsigned long long)g.size());
+    if (g.thread_rank() == 0) {
+        base = atomicAdd(P.n_total, (unsigned long long)g.size());
+        const unsigned long long made = base >= P.cap ? 0ull : min((unsigned long long)g.size(), P.cap - base);
+        if (made) atomicAdd(P.pending, made);
+    }
+    g.sync();
     base = g.shfl(base, 0);
     const unsigned long long k = base + g.thread_rank();
     if (k >= P.cap) {
@@ -586,7 +606,7 @@ __device__ __noinline__ void spawn_secondary(const RunArgs &P, const Fld<R> &F, 
     P.bvx[j] = (double)(ss * st * cp);
     P.bvy[j] = (double)(ss * st * sp);
     P.bvz[j] = (double)(ss * ct);
-    P.bid[j] = secondary_id(((uint64_t)s.id_hi << 32) | s.id_lo, step);
+    st_release(P.bid + j, secondary_id(((uint64_t)s.id_hi << 32) | s.id_lo, step));
 }
 
 // One trial step.  Returns the decision (channel, DEC_NULL, DEC_FAIL or
@@ -986,8 +1006,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? BZ_SWARM_MIN_BLOCKS :
                     const unsigned int idx = base + __popc(need & ((1u << lane) - 1u));
                     if (idx < tile.z) {
                         slot = (uint64_t)tile.y + idx;
-                        if (P.spawn && slot >= P.n_primary) init_secondary<R>(T, P, F, s, slot - P.n_primary);
-                        else init_particle<R>(T, P, F, s, P.id_offset + slot);
+                        init_particle<R>(T, P, F, s, P.id_offset + slot);
                         have = true;
                     }
                 }
@@ -1010,6 +1029,128 @@ __global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? BZ_SWARM_MIN_BLOCKS :
             }
         }
         __syncthreads();
+    }
+}
+
+__device__ __forceinline__ uint64_t ld_acquire_ull(const unsigned long long *p)
+{
+    uint64_t v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// A warp that has no electron to run gives up after this long without one.
+constexpr uint64_t kSpawnWaitNs = 60ull * 1000000000ull;
+
+// Spawn mode (ChildrenBulletLimiter, Sec. 3.2): one persistent launch runs
+// the primaries and every electron created from them.  A lane without an
+// electron holds a ticket k, a slot handed out in increasing order by one
+// warp-aggregated atomic.  Slot k < n_primary is a primary; a created slot
+// starts once its birth record is published (id != 0, acquire).  Every
+// created electron is counted as pending before its parent can finish and
+// uncounted when it finishes, so once pending reads 0 nothing more can be
+// created: a ticket whose record is still missing is void, and so is every
+// later one.  Tickets are taken only by lanes that are running, and every
+// slot below the largest ticket has a holder, so a waiting lane waits only
+// on electrons that are being run.
+template <typename R, bool CH_SMEM>
+__global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? BZ_SWARM_MIN_BLOCKS : 1)
+    spawn_kernel(const __grid_constant__ RunArgs P)
+{
+    extern __shared__ __align__(128) uint8_t smem[];
+    __shared__ __align__(8) uint64_t mbar;
+    if (!stage_tables(P.blob, smem, P.stage_bytes, &mbar, P.err)) return;
+    const Tab<R> T = make_tab<R>(smem, P.blob, P.lay, CH_SMEM);
+    const Fld<R> F = make_fld<R>(P.f);
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    PState<R> s;
+    bool have = false, ticket = false, over = false;
+    uint64_t k = 0, wait_since = 0;
+    uint32_t nap = 64;
+    for (;;) {
+        const bool idle = !have && !ticket && !over;
+        const unsigned want = __ballot_sync(FULL, idle);
+        if (want) {
+            const int leader = __ffs(want) - 1;
+            unsigned long long base = 0;
+            if (lane == leader) base = atomicAdd(P.counter, (unsigned long long)__popc(want));
+            base = __shfl_sync(FULL, base, leader);
+            if (idle) {
+                k = base + __popc(want & ((1u << lane) - 1u));
+                ticket = true;
+            }
+        }
+        bool ready = false;
+        if (ticket) {
+            if (k >= P.cap) {
+                ticket = false;
+                over = true;
+            } else {
+                ready = k < P.n_primary || ld_acquire(P.bid + (k - P.n_primary)) != 0;
+            }
+        }
+        const unsigned blocked = __ballot_sync(FULL, ticket && !ready);
+        if (blocked) {
+            const int first = __ffs(blocked) - 1;
+            unsigned long long pend = 1;
+            if (lane == first) pend = ld_acquire_ull(P.pending);
+            pend = __shfl_sync(FULL, pend, first);
+            __syncwarp(FULL);  // orders the other lanes' loads after that acquire
+            if (pend == 0 && ticket && !ready) {
+                // every record was published before the last electron finished
+                ready = ld_acquire(P.bid + (k - P.n_primary)) != 0;
+                if (!ready) {
+                    ticket = false;
+                    over = true;
+                }
+            }
+        }
+        if (ready) {
+            if (k < P.n_primary) init_particle<R>(T, P, F, s, P.id_offset + k);
+            else init_secondary<R>(T, P, F, s, k - P.n_primary);
+            have = true;
+            ticket = false;
+        }
+        if (!__any_sync(FULL, have)) {
+            if (__all_sync(FULL, over)) break;
+            const uint64_t now = global_ns();
+            if (wait_since == 0) {
+                wait_since = now;
+            } else if (now - wait_since > kSpawnWaitNs) {
+                if (lane == 0) atomicOr(P.err, BZ_ERR_SPAWN_WAIT);
+                break;
+            }
+            __nanosleep(nap);
+            nap = nap < 8192 ? 2 * nap : nap;
+            continue;
+        }
+        wait_since = 0;
+        nap = 64;
+#pragma unroll 1
+        for (int it = 0; it < 8 && have; ++it) {
+            if (s.k >= P.max_trials) {
+                s.status = ST_STEPS;
+                s.done = true;
+                atomicOr(P.err, BZ_ERR_MAX_TRIALS);
+            } else {
+                R ei, ef;
+                trial<R, CH_SMEM>(T, F, P, s, ei, ef);
+            }
+            if (s.done) {
+                write_particle<R>(P, s, k);
+                __threadfence();
+                atomicAdd(P.pending, ~0ull);  // this electron is finished
+                have = false;
+            }
+        }
     }
 }
 
@@ -1138,6 +1279,14 @@ __device__ __forceinline__ void pass1_contrib(const TallyArgs &A, uint64_t i, do
     c[18] = A.steps ? (double)A.steps[i] : 0.0;
 }
 
+// Particles to reduce: in spawn mode the population the step kernel left.
+__device__ __forceinline__ uint64_t tally_n(const TallyArgs &A)
+{
+    if (!A.n_dev) return A.n;
+    const uint64_t v = *A.n_dev;
+    return v < A.n ? v : A.n;
+}
+
 // Batch group (id mod 32) of particle i; secondaries carry their own ids.
 __device__ __forceinline__ int group_of(const TallyArgs &A, uint64_t i)
 {
@@ -1153,8 +1302,8 @@ __device__ void id_group_reduce(const TallyArgs &A, int bx, int nbx, double *out
     __shared__ double gs[kGroups * (kQ1 > kQ2 ? kQ1 : kQ2)];
     for (int k = threadIdx.x; k < kGroups * Q; k += blockDim.x) gs[k] = 0.0;
     __syncthreads();
-    const uint64_t stride = (uint64_t)nbx * blockDim.x;
-    for (uint64_t i = (uint64_t)bx * blockDim.x + threadIdx.x; i < A.n; i += stride) {
+    const uint64_t stride = (uint64_t)nbx * blockDim.x, n = tally_n(A);
+    for (uint64_t i = (uint64_t)bx * blockDim.x + threadIdx.x; i < n; i += stride) {
         double c[Q];
         contrib(i, c);
         const int g = group_of(A, i);
@@ -1175,8 +1324,8 @@ __device__ void tally_pass1_body(const TallyArgs &A, int bx, int nbx)
     double acc[kQ1];
 #pragma unroll
     for (int q = 0; q < kQ1; ++q) acc[q] = 0.0;
-    const uint64_t stride = (uint64_t)nbx * blockDim.x;
-    for (uint64_t i = (uint64_t)bx * blockDim.x + threadIdx.x; i < A.n; i += stride) {
+    const uint64_t stride = (uint64_t)nbx * blockDim.x, n = tally_n(A);
+    for (uint64_t i = (uint64_t)bx * blockDim.x + threadIdx.x; i < n; i += stride) {
         double c[kQ1];
         pass1_contrib(A, i, c);
 #pragma unroll
@@ -1253,8 +1402,8 @@ __device__ void tally_pass2_body(const TallyArgs &A, int bx, int nbx)
     double acc[kQ2];
 #pragma unroll
     for (int q = 0; q < kQ2; ++q) acc[q] = 0.0;
-    const uint64_t stride = (uint64_t)nbx * blockDim.x;
-    for (uint64_t i = (uint64_t)bx * blockDim.x + threadIdx.x; i < A.n; i += stride) {
+    const uint64_t stride = (uint64_t)nbx * blockDim.x, n = tally_n(A);
+    for (uint64_t i = (uint64_t)bx * blockDim.x + threadIdx.x; i < n; i += stride) {
         double c[kQ2];
         pass2_contrib(A, i, S, c);
 #pragma unroll
@@ -1337,7 +1486,8 @@ __device__ void tally_final_body(const TallyArgs &A)
     o.n_incomplete = (uint64_t)(tot[17] + 0.5);
     o.n_alive = (uint64_t)(tot[19] + 0.5);
     o.n_removed = (uint64_t)(tot[20] + 0.5);
-    o.n_spawned = A.n > A.n_primary && A.ids ? A.n - A.n_primary : 0;
+    const uint64_t n = tally_n(A);
+    o.n_spawned = n > A.n_primary && A.ids ? n - A.n_primary : 0;
     o.n_capped = A.capped ? (uint64_t)*A.capped : 0;
     const double other = tot[18] - trials;  // steps that were neither real, null nor fail: window restarts
     o.n_window = other > 0.5 ? (uint64_t)(other + 0.5) : 0;
@@ -1418,6 +1568,44 @@ cudaError_t launch_batch(int precision, bool ch_smem, const BatchArgs &a, size_t
     }
 #undef BZ_LAUNCH
     return cudaGetLastError();
+}
+
+cudaError_t launch_spawn(int precision, bool ch_smem, const RunArgs &a, size_t smem, int grid, int block,
+                         cudaStream_t s)
+{
+    if (block != kBlock) return cudaErrorInvalidValue;
+    cudaError_t e;
+#define BZ_LAUNCH(R, C)                                                        \
+    do {                                                                       \
+        e = prep_smem(spawn_kernel<R, C>, smem);                               \
+        if (e != cudaSuccess) return e;                                        \
+        spawn_kernel<R, C><<<grid, block, smem, s>>>(a);                       \
+    } while (0)
+    if (precision == 64) {
+        if (ch_smem) BZ_LAUNCH(double, true); else BZ_LAUNCH(double, false);
+    } else {
+        if (ch_smem) BZ_LAUNCH(float, true); else BZ_LAUNCH(float, false);
+    }
+#undef BZ_LAUNCH
+    return cudaGetLastError();
+}
+
+int spawn_occupancy(int precision, bool ch_smem, int block, size_t smem)
+{
+    int n = 0;
+    cudaError_t e;
+#define BZ_OCC(R, C)                                                                        \
+    do {                                                                                    \
+        prep_smem(spawn_kernel<R, C>, smem);                                                \
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, spawn_kernel<R, C>, block, smem); \
+    } while (0)
+    if (precision == 64) {
+        if (ch_smem) BZ_OCC(double, true); else BZ_OCC(double, false);
+    } else {
+        if (ch_smem) BZ_OCC(float, true); else BZ_OCC(float, false);
+    }
+#undef BZ_OCC
+    return e == cudaSuccess ? n : 0;
 }
 
 int batch_occupancy(int precision, bool ch_smem, int block, size_t smem)

@@ -44,16 +44,18 @@ struct RunArgs {
     float win_c;             // window length in units of 1/nu of the current energy bin
     double nu_floor;         // lower bound of any trial frequency [1/s]
     // spawn mode: slots [0, n_primary) are the initial electrons; secondaries
-    // take slots from *n_total (up to cap) and their birth state from b*[slot - n_primary]
+    // take slots from *n_total (up to cap) and their birth state from
+    // b*[slot - n_primary]; bid[] != 0 marks a published birth record
     int32_t spawn;
     uint64_t n_primary, cap;
     unsigned long long *n_total;
+    unsigned long long *pending;  // electrons created and not finished
     unsigned int *n_capped;
     double *bt;
     double *bvx, *bvy, *bvz;
     uint64_t *bid;
     Fields f;
-    unsigned long long *counter;  // next particle slot
+    unsigned long long *counter;  // spawn mode: next slot ticket
     uint32_t *err;
     ParticlesDev out;
 };
@@ -76,6 +78,7 @@ struct TallyArgs {
     const uint64_t *ids;     // spawn mode: ids of slots >= n_primary (null otherwise)
     const unsigned int *capped;  // spawn mode: capped-ionization counter (may be null)
     uint64_t n, id_offset, n_primary;
+    const unsigned long long *n_dev;  // spawn mode: particles = min(*n_dev, n) (may be null)
     double *part1, *part2;   // [blocks][kGroups][kQ1 | kQ2] scratch
     double *gsum;            // [kGroups][kQ1 + kQ2] + 8 summary values, scratch
     int32_t blocks;
@@ -102,6 +105,11 @@ cudaError_t launch_philox(int64_t n, const uint32_t *ctr, uint64_t key, uint32_t
 cudaError_t launch_tallies(const TallyArgs &a, cudaStream_t s);
 cudaError_t launch_batch(int precision, bool ch_smem, const BatchArgs &a, size_t smem, int grid, int block,
                          cudaStream_t s);
+// Spawn mode: one persistent launch runs the primaries and every electron
+// created from them (slots handed out as tickets from a.counter).
+cudaError_t launch_spawn(int precision, bool ch_smem, const RunArgs &a, size_t smem, int grid, int block,
+                         cudaStream_t s);
+int spawn_occupancy(int precision, bool ch_smem, int block, size_t smem);
 // Blocks of `block` threads that fit on one SM with `smem` bytes of tables.
 int batch_occupancy(int precision, bool ch_smem, int block, size_t smem);
 // Tallies of n_swarms swarms; args_dev is a device array of TallyArgs.

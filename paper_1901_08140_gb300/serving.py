@@ -29,6 +29,7 @@ import numpy as np
 # device bytes per electron of a swarm (results in SoA) and per swarm (tally scratch)
 BYTES_PER_ELECTRON = 92
 BYTES_PER_SWARM = 2 << 20
+BYTES_PER_BIRTH = 40   # spawn mode: birth record of a created electron
 
 
 @dataclasses.dataclass
@@ -48,7 +49,9 @@ class Request:
         return self.done - self.arrival
 
     def device_bytes(self) -> int:
-        return BYTES_PER_ELECTRON * self.n_electrons + BYTES_PER_SWARM
+        cap = int(getattr(self.cfg, "pop_cap", 0) or 0) if getattr(self.cfg, "spawn", 0) else 0
+        n = max(self.n_electrons, cap)
+        return (BYTES_PER_ELECTRON + (BYTES_PER_BIRTH if cap else 0)) * n + BYTES_PER_SWARM
 
 
 class GpuBackend:
@@ -83,8 +86,31 @@ class GpuBackend:
         handle.close()
 
 
+class _SwarmRun:
+    """A request launched on its own as a swarm (spawn mode: an avalanche)."""
+
+    def __init__(self, bz, ctx, req, stream):
+        self.bz = bz
+        self.sw = bz.Swarm(ctx, req.mixture, req.cfg, stream)
+
+    def poll(self) -> Optional[List[Dict[str, float]]]:
+        import ctypes as C
+        t = self.bz.bz_tallies()
+        st = self.bz.lib().bz_query_tallies(self.sw.h, C.byref(t))
+        if st == self.bz.BZ_ENOTREADY:
+            return None
+        out = self.bz._tally_dict(t)
+        out["status"] = st
+        return [out]
+
+    def close(self) -> None:
+        self.sw.close()
+
+
 class GpuBatchBackend:
-    """Launches groups of requests as one batched launch of libbz.so per slot."""
+    """Launches groups of requests as one batched launch of libbz.so per slot;
+    spawn-mode requests (avalanches) run alone, each in its own persistent
+    launch on the slot's stream."""
 
     def __init__(self, ctx, n_streams: int = 4):
         import torch
@@ -98,12 +124,20 @@ class GpuBatchBackend:
     def slots(self) -> int:
         return len(self.streams)
 
+    @staticmethod
+    def alone(req: Request) -> bool:
+        return bool(getattr(req.cfg, "spawn", 0))
+
     def launch_group(self, reqs: Sequence[Request], slot: int):
+        if len(reqs) == 1 and self.alone(reqs[0]):
+            return _SwarmRun(self.bz, self.ctx, reqs[0], self.streams[slot])
         b = self.bz.Batch(self.ctx, [r.mixture for r in reqs], [r.cfg for r in reqs], use_graph=False)
         b.launch(self.streams[slot])
         return b
 
     def poll_group(self, handle) -> Optional[List[Dict[str, float]]]:
+        if isinstance(handle, _SwarmRun):
+            return handle.poll()
         if not handle.ready():
             return None
         return handle.tallies(check=False)
@@ -156,11 +190,16 @@ class Server:
             # admit in arrival order while a slot and memory are free
             while queue and free and self.in_use + queue[0].device_bytes() <= self.budget:
                 group, need = [], 0.0
+                alone = getattr(self.backend, "alone", lambda r: False)
                 while (queue and len(group) < self.max_group
                        and self.in_use + need + queue[0].device_bytes() <= self.budget):
+                    if group and alone(queue[0]):
+                        break          # runs on its own
                     r = queue.popleft()
                     need += r.device_bytes()
                     group.append(r)
+                    if alone(r):
+                        break
                 slot = free.pop()
                 t_adm = self.clock() - t0
                 for r in group:

@@ -264,6 +264,11 @@ def ar_co2_mixture(n_total: float = N_STP_293) -> List[Gas]:
     return [argon_like(0.9 * n_total), co2_like(0.1 * n_total)]
 
 
+def ar_co2_avalanche_mixture(n_total: float = N_STP_293) -> List[Gas]:
+    """Ar/CO2 93/7, the mixture of the paper's avalanche timing (Sec. 8)."""
+    return [argon_like(0.93 * n_total), co2_like(0.07 * n_total)]
+
+
 def ar_co2_swarm(n_electrons: int = 1_000_000, real_collisions: int = 1000) -> SwarmSpec:
     """Ar/CO2 90/10, E/N = 100 Td, B = 1 T perpendicular to E."""
     return SwarmSpec(ar_co2_mixture(), 100.0, 1.0, math.pi / 2, n_electrons, real_collisions,

@@ -88,6 +88,32 @@ def test_population_cap(ctx):
     assert int(p["n_ion"].sum()) == t["n_spawned"] + t["n_capped"]
 
 
+def test_population_cap_at_the_start(ctx):
+    """pop_cap equal to the primaries: every ionization is capped, none is created."""
+    nu_i = 1e11
+    t, p = _run(ctx, [_const_rate_gas(1e12, nu_ion=nu_i)], n_electrons=5000, real_collisions=10 ** 9,
+                e_over_n_Td=50.0, seed=4, t_end_s=2.0 / nu_i, spawn=True, pop_cap=5000)
+    assert len(p["t"]) == 5000 and t["n_spawned"] == 0
+    assert t["n_capped"] == int(p["n_ion"].sum()) > 0
+
+
+def test_spawn_is_reproducible_run_to_run(ctx):
+    """Lanes take created electrons in whatever order they are published, yet
+    each electron's history depends only on its id: two runs agree."""
+    kw = dict(n_electrons=4, real_collisions=10 ** 9, e_over_n_Td=300.0, seed=31, t_end_s=0.25e-9, spawn=True,
+              pop_cap=10 ** 6, trial_mode=bz.BZ_TRIAL_WINDOW)
+    t1, p1 = _run(ctx, W.ar_co2_avalanche_mixture(), **kw)
+    t2, p2 = _run(ctx, W.ar_co2_avalanche_mixture(), **kw)
+    assert len(p1["id"]) > 100 and t1["n_capped"] == 0
+    o1, o2 = np.argsort(p1["id"]), np.argsort(p2["id"])
+    assert np.array_equal(p1["id"][o1], p2["id"][o2])
+    for k in ("n_real", "n_null", "n_ion", "n_att", "steps", "status", "x", "z", "t", "t_birth"):
+        assert np.array_equal(p1[k][o1], p2[k][o2]), k
+    for k in ("n_particles", "n_real", "n_ion", "n_spawned", "n_alive"):
+        assert t1[k] == t2[k]
+    assert t1["W"] == pytest.approx(t2["W"], rel=1e-12, abs=0.0)
+
+
 def test_avalanche_request_shape(ctx):
     """A 1 ns avalanche in the Ar/CO2-like mixture at 300 Td from one seed of electrons."""
     t, p = _run(ctx, W.ar_co2_mixture(), n_electrons=100, real_collisions=10 ** 9, e_over_n_Td=300.0, seed=9,

@@ -95,6 +95,34 @@ def test_queued_requests_are_launched_together_within_budget():
     assert srv.peak_in_use <= budget and len(done) == 7
 
 
+class FakeAloneBackend(FakeGroupBackend):
+    """Requests with cfg == "alone" must be launched on their own."""
+
+    @staticmethod
+    def alone(req):
+        return req.cfg == "alone"
+
+
+def test_requests_that_run_alone_are_not_grouped():
+    be = FakeAloneBackend(slots=2, polls=10)
+    reqs = _reqs([100] * 6, [0.0] * 6)
+    reqs[2].cfg = "alone"
+    reqs[3].cfg = "alone"
+    srv = S.Server(be, memory_budget=1e12, clock=Clock(), idle_sleep=0, max_group=8)
+    done = srv.run(reqs, realtime=False)
+    groups = [e[1] for e in be.log if e[0] == "group"]
+    assert groups[:2] == [(0, 1), (2,)]
+    assert (3,) in groups and sorted(r for g in groups for r in g) == list(range(6))
+    assert len(done) == 6
+
+
+def test_spawn_requests_reserve_memory_for_the_population_cap():
+    class Cfg:
+        spawn, pop_cap = 1, 10 ** 6
+    r = S.Request(0, None, Cfg(), n_electrons=1)
+    assert r.device_bytes() == (S.BYTES_PER_ELECTRON + S.BYTES_PER_BIRTH) * 10 ** 6 + S.BYTES_PER_SWARM
+
+
 def test_oversized_request_is_rejected():
     srv = S.Server(FakeBackend(), memory_budget=1e6, clock=Clock(), idle_sleep=0)
     with pytest.raises(ValueError):
@@ -140,3 +168,40 @@ def test_results_are_the_same_alone_and_in_the_mix():
             a = alone[r.rid]
             for k in ("W", "eps", "D_L", "D_T", "n_real", "n_null", "n_window"):
                 assert r.tallies[k] == a[k], (r.rid, k)
+
+
+@pytest.mark.gpu
+def test_avalanche_requests_alone_and_in_the_mix():
+    """Spawn-mode requests run on worker threads beside batched swarms; the
+    population they reach (integer counts, fixed by the ids' random numbers)
+    is the same as when each runs alone."""
+    from paper_1901_08140_gb300 import build as B
+    B.build()
+    from paper_1901_08140_gb300 import bz
+    from paper_1901_08140_gb300 import workloads as W
+    ctx = bz.Context(0)
+    specs = W.batched_swarms(count=8, real_collisions=100, max_electrons=20000)
+    mixes = [bz.Mixture(ctx, s.gases) for s in specs]
+    cfgs = [bz.config_from_spec(s, trial_mode=bz.BZ_TRIAL_WINDOW) for s in specs]
+    ava = bz.Mixture(ctx, W.ar_co2_mixture())
+    for i in range(3):
+        mixes.insert(2 + 3 * i, ava)
+        cfgs.insert(2 + 3 * i, bz.make_config(n_electrons=4, real_collisions=10 ** 9, e_over_n_Td=250.0,
+                                              seed=W.swarm_seed(70 + i), t_end_s=0.2e-9, spawn=True,
+                                              pop_cap=10 ** 6, trial_mode=bz.BZ_TRIAL_WINDOW))
+    alone = []
+    for m, c in zip(mixes, cfgs):
+        sw = bz.run_swarm(ctx, m, c)
+        alone.append(sw.tallies())
+        sw.close()
+    assert all(alone[2 + 3 * i]["n_spawned"] > 0 for i in range(3))
+    reqs = [S.Request(i, m, c, arrival=a, n_electrons=int(c.n_electrons))
+            for i, (m, c, a) in enumerate(zip(mixes, cfgs, np.linspace(0.0, 0.01, len(cfgs))))]
+    srv = S.Server(S.GpuBatchBackend(ctx, n_streams=3), memory_budget=60e9, max_group=4)
+    done = srv.run(reqs, realtime=True)
+    assert len(done) == len(reqs)
+    for r in done:
+        a = alone[r.rid]
+        for k in ("n_particles", "n_real", "n_ion", "n_att", "n_spawned", "n_alive", "n_capped"):
+            assert r.tallies[k] == a[k], (r.rid, k)
+        assert r.tallies["eps"] == pytest.approx(a["eps"], rel=1e-12, abs=0.0)
