@@ -268,6 +268,122 @@ void or_majorant(or_mixture *m, double eps_cap)
     m->eps_at_max = best_eps;
 }
 
+/* Maximum of nu over [a, b] -- the per-bin maximum of BinnedTrialFrequency
+ * (Sec. 6.3) -- by the same piecewise analysis as the majorant: between two
+ * consecutive breakpoints inside [a, b] with no channel in its power-law
+ * tail, nu = sqrt(eps) (A + B eps) up to a constant, maximal at an end or at
+ * eps* = -A/(3B); pieces with a tail are sampled densely and refined. */
+double or_range_max(const or_mixture *m, double a, double b)
+{
+    if (!(a >= 0.0)) a = 0.0;
+    if (!(b > a)) return or_nu(m, a);
+    int total = 2;
+    for (int c = 0; c < m->n_ch; ++c) total += m->ch[c].n + 1;
+    double *bp = (double *)malloc(sizeof(double) * (size_t)total);
+    int nb = 0;
+    bp[nb++] = a;
+    bp[nb++] = b;
+    for (int c = 0; c < m->n_ch; ++c) {
+        for (int i = 0; i < m->ch[c].n; ++i)
+            if (m->ch[c].e[i] > a && m->ch[c].e[i] < b) bp[nb++] = m->ch[c].e[i];
+        if (m->ch[c].kind != OR_ELASTIC && m->ch[c].threshold > a && m->ch[c].threshold < b)
+            bp[nb++] = m->ch[c].threshold;
+    }
+    qsort(bp, (size_t)nb, sizeof(double), cmp_double);
+    int u = 0;
+    for (int i = 0; i < nb; ++i)
+        if (u == 0 || bp[i] != bp[u - 1]) bp[u++] = bp[i];
+    nb = u;
+    double best = 0.0, dummy = 0.0;
+    const double k = sqrt(2.0 * OR_QE / OR_ME);
+    for (int i = 0; i + 1 < nb; ++i) {
+        double lo = bp[i], hi = bp[i + 1], w = hi - lo;
+        int tail = 0;
+        for (int c = 0; c < m->n_ch; ++c)
+            if (m->ch[c].e[m->ch[c].n - 1] < hi) tail = 1;
+        if (!tail) {
+            double e1 = lo + w / 3.0, e2 = lo + 2.0 * w / 3.0;
+            double s1 = or_density_sum(m, e1), s2 = or_density_sum(m, e2);
+            double B = (s2 - s1) / (e2 - e1), A = s1 - B * e1;
+            double cand[3] = {lo, hi, (B != 0.0) ? -A / (3.0 * B) : lo};
+            for (int j = 0; j < 3; ++j) {
+                double x = cand[j];
+                if (!(x >= lo && x <= hi)) continue;
+                double v = k * linear_piece_value(A, B, x);
+                if (v > best) best = v;
+            }
+        } else {
+            const int NS = 1024;
+            int arg = 0;
+            double vmax = -1.0;
+            for (int j = 0; j <= NS; ++j) {
+                double v = or_nu(m, lo + w * (double)j / NS);
+                if (v > vmax) { vmax = v; arg = j; }
+            }
+            double x0 = lo + w * (double)(arg > 0 ? arg - 1 : 0) / NS;
+            double x3 = lo + w * (double)(arg < NS ? arg + 1 : NS) / NS;
+            const double g = 0.6180339887498949;
+            double x1 = x3 - g * (x3 - x0), x2 = x0 + g * (x3 - x0);
+            double f1 = or_nu(m, x1), f2 = or_nu(m, x2);
+            for (int it = 0; it < 200 && (x3 - x0) > 1e-14 * x3; ++it) {
+                if (f1 < f2) { x0 = x1; x1 = x2; f1 = f2; x2 = x0 + g * (x3 - x0); f2 = or_nu(m, x2); }
+                else { x3 = x2; x2 = x1; f2 = f1; x1 = x3 - g * (x3 - x0); f1 = or_nu(m, x1); }
+            }
+            consider(m, lo + w * (double)arg / NS, &best, &dummy);
+            consider(m, x1, &best, &dummy);
+            consider(m, x2, &best, &dummy);
+            consider(m, lo, &best, &dummy);
+            consider(m, hi, &best, &dummy);
+        }
+    }
+    free(bp);
+    return best;
+}
+
+/* BinnedTrialFrequency (Sec. 6.3): bins_per_decade log-uniform bins per
+ * decade of energy, bin j = [10^(j/B), 10^((j+1)/B)) with j = floor(B log10 eps);
+ * the trial frequency of an energy is the maximum of nu over its bin. */
+static int binned_index(int B, double eps) { return (int)floor((double)B * log10(eps)); }
+
+double or_binned_max(const or_mixture *m, int B, int j)
+{
+    return or_range_max(m, pow(10.0, (double)j / B), pow(10.0, (double)(j + 1) / B));
+}
+
+/* Bin maxima of the bins that hold the mixture's tables, computed once per
+ * run; other bins are computed when met. */
+typedef struct {
+    int B, j0, n;
+    double *max;
+} or_binned;
+
+static void binned_setup(const or_mixture *m, int B, or_binned *bt)
+{
+    bt->B = B;
+    bt->n = 0;
+    bt->max = NULL;
+    if (B <= 0) return;
+    double lo = INFINITY, hi = 0.0;
+    for (int c = 0; c < m->n_ch; ++c) {
+        const or_channel *ch = &m->ch[c];
+        for (int i = 0; i < ch->n; ++i)
+            if (ch->e[i] > 0.0) { lo = fmin(lo, ch->e[i]); hi = fmax(hi, ch->e[i]); }
+    }
+    if (!(hi > 0.0)) return;
+    bt->j0 = binned_index(B, lo) - 1;
+    bt->n = binned_index(B, hi * 1e3) + 2 - bt->j0;   /* and three decades of tails */
+    bt->max = (double *)malloc(sizeof(double) * (size_t)bt->n);
+    for (int i = 0; i < bt->n; ++i) bt->max[i] = or_binned_max(m, B, bt->j0 + i);
+}
+
+static double binned_nu(const or_mixture *m, const or_binned *bt, double eps)
+{
+    if (!(eps > 0.0)) return 0.0;
+    int j = binned_index(bt->B, eps);
+    if (j >= bt->j0 && j < bt->j0 + bt->n) return bt->max[j - bt->j0];
+    return or_binned_max(m, bt->B, j);
+}
+
 /* Mixture from flat arrays (tables are copied). Returns 0 or -1 on bad input. */
 int or_mixture_create(int n_gas, const double *gas_mass, const double *gas_density, const int *gas_angular,
                       int n_ch, const int *ch_gas, const int *ch_kind, const double *ch_threshold,
@@ -449,7 +565,16 @@ typedef struct {
     int attach_keep_state;    /* 1: a dummy attachment leaves the electron unchanged */
     int spawn;                /* 1: ionizations create electrons, attachments remove them */
     uint64_t pop_cap;         /* spawn mode: at most this many electrons in all */
+    int strategy;             /* trial frequency (Sec. 6): 0 constant (Lazy / given / Fixed),
+                                 1 VariableTrialFrequency, 2 BinnedTrialFrequency */
+    double zeta;              /* Variable: nu' = (1 + zeta) nu(eps) */
+    uint32_t grace;           /* Variable, Binned: collisions between two queries of nu' */
+    int bins_per_decade;      /* Binned */
 } or_config;
+
+#define OR_TF_CONST 0
+#define OR_TF_VARIABLE 1
+#define OR_TF_BINNED 2
 
 /* Identifier of the electron that the ionization at `step` of electron
  * `parent` creates: the SplitMix64 finaliser (Steele, Lea, Flood 2014) of
@@ -538,14 +663,31 @@ typedef struct {
 /* Runs one electron from birth (time t0, velocity v0; t0 = 0 and a
  * Maxwellian start for primaries) to its limiters.  Positions and times are
  * kept relative to birth; the time limit is absolute. */
-static void run_particle_from(const or_mixture *m, const or_config *cf, const or_field *f, uint64_t id, double t0,
-                              const double *v0, const or_particles *P, int64_t slot, or_spawns *sp)
+/* Trial frequency of the adaptive strategies (Sec. 6) at energy eps:
+ * Variable (1 + zeta) nu(eps), Binned the maximum of nu over the bin of eps;
+ * neither below 1e-9 of the Lazy majorant (nu vanishes at eps = 0). */
+static double adaptive_nu(const or_mixture *m, const or_config *cf, const or_binned *bt, double eps)
+{
+    double floor_nu = 1e-9 * m->nu_max;
+    if (cf->strategy == OR_TF_VARIABLE) return (1.0 + cf->zeta) * fmax(or_nu(m, eps), floor_nu);
+    return fmax(binned_nu(m, bt, eps), floor_nu);
+}
+
+static void run_particle_from(const or_mixture *m, const or_config *cf, const or_field *f, const or_binned *bt,
+                              uint64_t id, double t0, const double *v0, const or_particles *P, int64_t slot,
+                              or_spawns *sp)
 {
     double x[3] = {0.0, 0.0, 0.0}, v[3], t = 0.0;
     if (v0) { v[0] = v0[0]; v[1] = v0[1]; v[2] = v0[2]; }
     else init_velocity(cf, id, v);
     double sx[3] = {0, 0, 0}, sv[3] = {v[0], v[1], v[2]}, st = 0.0; /* last real collision */
-    double nu_p = cf->nu_trial;
+    /* Sec. 6: the adaptive strategies query nu' at the start, keep it for
+     * `grace` collisions (null or real), query again, and on a fail go back
+     * to the last real collision and query with the fail's energy. */
+    const int adaptive = cf->strategy == OR_TF_VARIABLE || cf->strategy == OR_TF_BINNED;
+    double nu_p = adaptive ? adaptive_nu(m, cf, bt, energy_of(v)) : cf->nu_trial;
+    uint32_t grace_left = cf->grace;
+    int retried = 0; /* Binned: nu' comes from a retry after a fail */
     double sum_e = 0.0, sum_e2 = 0.0;
     uint32_t n_real = 0, n_null = 0, n_fail = 0, n_ion = 0, n_att = 0, k = 0, status = OR_ST_DONE;
     while (n_real < cf->real_collisions) {
@@ -568,13 +710,31 @@ static void run_particle_from(const or_mixture *m, const or_config *cf, const or
         if (nu > nu_p) { /* fail: Sec. 6 -- back to the last real collision */
             ++n_fail;
             if (cf->fixed) { status = OR_ST_TRIAL; break; }
+            if (cf->strategy == OR_TF_BINNED) {
+                /* retry with the larger maximum of the two bins; a fail
+                 * under that nu' (before a real collision or a new query)
+                 * is an error */
+                if (retried) { status = OR_ST_TRIAL; break; }
+                retried = 1;
+            }
             for (int i = 0; i < 3; ++i) { x[i] = sx[i]; v[i] = sv[i]; }
             t = st;
-            nu_p = fmax(nu_p, 1.25 * nu);
+            if (cf->strategy == OR_TF_VARIABLE) nu_p = adaptive_nu(m, cf, bt, eps);
+            else if (cf->strategy == OR_TF_BINNED) nu_p = fmax(nu_p, adaptive_nu(m, cf, bt, eps));
+            else nu_p = fmax(nu_p, 1.25 * nu);
+            grace_left = cf->grace;
             continue;
         }
         double r = u[1] * nu_p;
-        if (r > nu) { ++n_null; continue; } /* Eq. (4) */
+        if (r > nu) { /* Eq. (4) */
+            ++n_null;
+            if (adaptive && --grace_left == 0) {
+                nu_p = adaptive_nu(m, cf, bt, eps);
+                grace_left = cf->grace;
+                retried = 0;
+            }
+            continue;
+        }
         int c = or_select_channel(m, eps, r);
         double eps_f, sec_v[3];
         int ion, att;
@@ -593,6 +753,13 @@ static void run_particle_from(const or_mixture *m, const or_config *cf, const or
         if (cf->spawn && att && !cf->attach_keep_state) { status = OR_ST_ATTACHED; break; }
         for (int i = 0; i < 3; ++i) { sx[i] = x[i]; sv[i] = v[i]; }
         st = t;
+        if (adaptive) {
+            retried = 0;
+            if (--grace_left == 0) {
+                nu_p = adaptive_nu(m, cf, bt, energy_of(v));
+                grace_left = cf->grace;
+            }
+        }
     }
     P->x[slot] = x[0]; P->y[slot] = x[1]; P->z[slot] = x[2]; P->t[slot] = t;
     P->vx[slot] = v[0]; P->vy[slot] = v[1]; P->vz[slot] = v[2];
@@ -601,16 +768,11 @@ static void run_particle_from(const or_mixture *m, const or_config *cf, const or
     P->n_ion[slot] = n_ion; P->n_att[slot] = n_att; P->steps[slot] = k; P->status[slot] = status;
 }
 
-static void run_particle(const or_mixture *m, const or_config *cf, const or_field *f, uint64_t id,
-                         const or_particles *P, int64_t slot)
-{
-    run_particle_from(m, cf, f, id, 0.0, NULL, P, slot, NULL);
-}
-
 typedef struct {
     const or_mixture *m;
     const or_config *cf;
     const or_field *f;
+    const or_binned *bt;
     const or_particles *P;
     uint64_t id0;
     int64_t begin, end;
@@ -619,8 +781,25 @@ typedef struct {
 static void *run_range(void *arg)
 {
     const or_job *j = (const or_job *)arg;
-    for (int64_t i = j->begin; i < j->end; ++i) run_particle(j->m, j->cf, j->f, j->id0 + (uint64_t)i, j->P, i);
+    for (int64_t i = j->begin; i < j->end; ++i)
+        run_particle_from(j->m, j->cf, j->f, j->bt, j->id0 + (uint64_t)i, 0.0, NULL, j->P, i, NULL);
     return NULL;
+}
+
+/* Checks the strategy's parameters; builds the Binned tables. */
+static int strategy_setup(const or_mixture *m, const or_config *c, or_binned *bt)
+{
+    bt->n = 0;
+    bt->max = NULL;
+    if (c->strategy == OR_TF_CONST) return 0;
+    if (c->strategy != OR_TF_VARIABLE && c->strategy != OR_TF_BINNED) return -1;
+    if (c->grace < 1 || c->fixed) return -1;
+    if (c->strategy == OR_TF_VARIABLE && !(c->zeta >= 0.0)) return -1;
+    if (c->strategy == OR_TF_BINNED) {
+        if (c->bins_per_decade < 1) return -1;
+        binned_setup(m, c->bins_per_decade, bt);
+    }
+    return 0;
 }
 
 /* Spawn mode: primaries id0 .. id0+n-1 first, then every secondary in the
@@ -642,6 +821,8 @@ int64_t or_run_swarm_spawn(const or_mixture *m, const or_config *cf, uint64_t id
     field_setup(&f, c.e_over_n_Td, m->n_total, c.b_T, c.b_angle_rad);
     int64_t room = cap - n;
     if (room < 0) return -1;
+    or_binned bt;
+    if (strategy_setup(m, &c, &bt) != 0) return -2;
     or_spawns sp;
     sp.ids = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(room + 1));
     sp.t_birth = (double *)malloc(sizeof(double) * (size_t)(room + 1));
@@ -651,18 +832,19 @@ int64_t or_run_swarm_spawn(const or_mixture *m, const or_config *cf, uint64_t id
     for (int64_t i = 0; i < n; ++i) {
         ids_out[i] = id0 + (uint64_t)i;
         t_birth_out[i] = 0.0;
-        run_particle_from(m, &c, &f, ids_out[i], 0.0, NULL, &P, i, &sp);
+        run_particle_from(m, &c, &f, &bt, ids_out[i], 0.0, NULL, &P, i, &sp);
     }
     for (int64_t k = 0; k < sp.n; ++k) {
         int64_t slot = n + k;
         ids_out[slot] = sp.ids[k];
         t_birth_out[slot] = sp.t_birth[k];
-        run_particle_from(m, &c, &f, sp.ids[k], sp.t_birth[k], sp.v_birth + 3 * k, &P, slot, &sp);
+        run_particle_from(m, &c, &f, &bt, sp.ids[k], sp.t_birth[k], sp.v_birth + 3 * k, &P, slot, &sp);
     }
     int64_t total = n + sp.n;
     free(sp.ids);
     free(sp.t_birth);
     free(sp.v_birth);
+    free(bt.max);
     return total;
 }
 
@@ -679,6 +861,8 @@ int or_run_swarm(const or_mixture *m, const or_config *cf, uint64_t id0, int64_t
     if (c.max_trials == 0) c.max_trials = 0x7FFFFFFFu;
     or_field f;
     field_setup(&f, c.e_over_n_Td, m->n_total, c.b_T, c.b_angle_rad);
+    or_binned bt;
+    if (strategy_setup(m, &c, &bt) != 0) return -1;
     if (n_threads < 1) n_threads = 1;
     if (n_threads > 256) n_threads = 256;
     pthread_t th[256];
@@ -688,12 +872,13 @@ int or_run_swarm(const or_mixture *m, const or_config *cf, uint64_t id0, int64_t
     for (int i = 0; i < n_threads; ++i) {
         int64_t b = (int64_t)i * per, e = b + per < n ? b + per : n;
         if (b >= e) break;
-        jobs[i] = (or_job){m, &c, &f, &P, id0, b, e};
+        jobs[i] = (or_job){m, &c, &f, &bt, &P, id0, b, e};
         if (n_threads == 1) { run_range(&jobs[i]); continue; }
         pthread_create(&th[i], NULL, run_range, &jobs[i]);
         ++launched;
     }
     for (int i = 0; i < launched; ++i) pthread_join(th[i], NULL);
+    free(bt.max);
     return 0;
 }
 

@@ -46,7 +46,12 @@ class _Config(C.Structure):
                 ("nu_trial", C.c_double), ("fixed", C.c_int), ("real_collisions", C.c_uint32),
                 ("t_end", C.c_double), ("eps0_mean_eV", C.c_double), ("seed", C.c_uint64),
                 ("max_trials", C.c_uint64), ("attach_keep_state", C.c_int), ("spawn", C.c_int),
-                ("pop_cap", C.c_uint64)]
+                ("pop_cap", C.c_uint64), ("strategy", C.c_int), ("zeta", C.c_double), ("grace", C.c_uint32),
+                ("bins_per_decade", C.c_int)]
+
+
+# trial frequency strategies of Sec. 6 (besides the constant one)
+TF_CONST, TF_VARIABLE, TF_BINNED = 0, 1, 2
 
 
 def lib():
@@ -94,6 +99,10 @@ def lib():
             [_dp] * 10 + [_u32p] * 7 + [_u64p, _dp]
         L.or_sigma_many.argtypes = [C.c_void_p, C.c_int, C.c_int64, _dp, _dp]
         L.or_initial_velocity_many.argtypes = [C.c_double, C.c_uint64, C.c_uint64, C.c_int64, _dp]
+        L.or_range_max.restype = C.c_double
+        L.or_range_max.argtypes = [C.c_void_p, C.c_double, C.c_double]
+        L.or_binned_max.restype = C.c_double
+        L.or_binned_max.argtypes = [C.c_void_p, C.c_int, C.c_int]
         _lib = L
     return _lib
 
@@ -180,6 +189,14 @@ class Mixture:
     def select_channel(self, eps: float, r: float) -> int:
         return lib().or_select_channel(self.h, float(eps), float(r))
 
+    def range_max(self, a: float, b: float) -> float:
+        """Maximum of nu over [a, b] eV."""
+        return lib().or_range_max(self.h, float(a), float(b))
+
+    def binned_max(self, bins_per_decade: int, j: int) -> float:
+        """Maximum of nu over bin j = [10^(j/B), 10^((j+1)/B)) (BinnedTrialFrequency)."""
+        return lib().or_binned_max(self.h, int(bins_per_decade), int(j))
+
 
 def cos_theta(angular: int, eps_eV: float, R: float) -> float:
     return lib().or_cos_theta(int(angular), float(eps_eV), float(R))
@@ -220,10 +237,12 @@ def initial_velocities(eps0_mean_eV: float, seed: int, id0: int, n: int) -> np.n
 
 
 def _config(e_over_n_Td, b_T, b_angle_rad, real_collisions, seed, eps0_mean_eV, nu_trial, fixed, t_end,
-            max_trials, attach_keep_state, spawn=False, pop_cap=0) -> _Config:
+            max_trials, attach_keep_state, spawn=False, pop_cap=0, strategy=TF_CONST, zeta=0.25, grace=5000,
+            bins_per_decade=8) -> _Config:
     return _Config(float(e_over_n_Td), float(b_T), float(b_angle_rad), float(nu_trial), int(bool(fixed)),
                    int(real_collisions), float(t_end), float(eps0_mean_eV), int(seed) & 0xFFFFFFFFFFFFFFFF,
-                   int(max_trials), int(bool(attach_keep_state)), int(bool(spawn)), int(pop_cap))
+                   int(max_trials), int(bool(attach_keep_state)), int(bool(spawn)), int(pop_cap), int(strategy),
+                   float(zeta), int(grace), int(bins_per_decade))
 
 
 def secondary_id(parent: int, step: int) -> int:
@@ -232,10 +251,12 @@ def secondary_id(parent: int, step: int) -> int:
 
 def run_swarm_spawn(mix: Mixture, *, e_over_n_Td: float, real_collisions: int, n: int, seed: int, pop_cap: int,
                     b_T: float = 0.0, b_angle_rad: float = 0.0, id0: int = 0, eps0_mean_eV: float = 0.1,
-                    nu_trial: float = 0.0, t_end: float = 0.0, max_trials: int = 0) -> Dict[str, np.ndarray]:
-    """Spawn mode: ionizations create electrons, attachments remove them."""
+                    nu_trial: float = 0.0, t_end: float = 0.0, max_trials: int = 0,
+                    **strategy) -> Dict[str, np.ndarray]:
+    """Spawn mode: ionizations create electrons, attachments remove them.
+    ``strategy``: strategy=TF_VARIABLE | TF_BINNED with zeta, grace, bins_per_decade."""
     cf = _config(e_over_n_Td, b_T, b_angle_rad, real_collisions, seed, eps0_mean_eV, nu_trial, False, t_end,
-                 max_trials, False, spawn=True, pop_cap=pop_cap)
+                 max_trials, False, spawn=True, pop_cap=pop_cap, **strategy)
     names_d = ["x", "y", "z", "t", "vx", "vy", "vz", "sum_e", "sum_e2", "nu_p"]
     names_u = ["n_real", "n_null", "n_fail", "n_ion", "n_att", "steps", "status"]
     out = {k: np.zeros(pop_cap, dtype=np.float64) for k in names_d}
@@ -245,8 +266,10 @@ def run_swarm_spawn(mix: Mixture, *, e_over_n_Td: float, real_collisions: int, n
     total = lib().or_run_swarm_spawn(mix.h, C.byref(cf), int(id0), int(n), int(pop_cap),
                                      *[_p(out[k], _dp) for k in names_d], *[_p(out[k], _u32p) for k in names_u],
                                      _p(ids, _u64p), _p(tb, _dp))
-    if total < 0:
+    if total == -1:
         raise ValueError("pop_cap below the number of primaries")
+    if total < 0:
+        raise ValueError("invalid trial frequency strategy")
     res = {k: v[:total] for k, v in out.items()}
     res["id"] = ids[:total]
     res["t_birth"] = tb[:total]
@@ -256,10 +279,11 @@ def run_swarm_spawn(mix: Mixture, *, e_over_n_Td: float, real_collisions: int, n
 def run_swarm(mix: Mixture, *, e_over_n_Td: float, real_collisions: int, n: int, seed: int,
               b_T: float = 0.0, b_angle_rad: float = 0.0, id0: int = 0, eps0_mean_eV: float = 0.1,
               nu_trial: float = 0.0, fixed: bool = False, t_end: float = 0.0, threads: int = 1,
-              max_trials: int = 0, attach_keep_state: bool = False) -> Dict[str, np.ndarray]:
-    """Runs particles id0..id0+n-1 to I real collisions; per-particle outputs."""
+              max_trials: int = 0, attach_keep_state: bool = False, **strategy) -> Dict[str, np.ndarray]:
+    """Runs particles id0..id0+n-1 to I real collisions; per-particle outputs.
+    ``strategy``: strategy=TF_VARIABLE | TF_BINNED with zeta, grace, bins_per_decade (Sec. 6)."""
     cf = _config(e_over_n_Td, b_T, b_angle_rad, real_collisions, seed, eps0_mean_eV, nu_trial, fixed, t_end,
-                 max_trials, attach_keep_state)
+                 max_trials, attach_keep_state, **strategy)
     names_d = ["x", "y", "z", "t", "vx", "vy", "vz", "sum_e", "sum_e2", "nu_p"]
     names_u = ["n_real", "n_null", "n_fail", "n_ion", "n_att", "steps", "status"]
     out = {k: np.zeros(n, dtype=np.float64) for k in names_d}
@@ -267,8 +291,10 @@ def run_swarm(mix: Mixture, *, e_over_n_Td: float, real_collisions: int, n: int,
     if n == 0:
         out["id"] = np.zeros(0, dtype=np.uint64)
         return out
-    lib().or_run_swarm(mix.h, C.byref(cf), int(id0), int(n), int(threads),
-                       *[_p(out[k], _dp) for k in names_d], *[_p(out[k], _u32p) for k in names_u])
+    rc = lib().or_run_swarm(mix.h, C.byref(cf), int(id0), int(n), int(threads),
+                            *[_p(out[k], _dp) for k in names_d], *[_p(out[k], _u32p) for k in names_u])
+    if rc != 0:
+        raise ValueError("invalid trial frequency strategy")
     out["id"] = np.arange(id0, id0 + n, dtype=np.uint64)
     return out
 

@@ -556,3 +556,123 @@ def test_secondary_ids_follow_the_splitmix64_finaliser():
         return (z ^ (z >> 31)) | 2 ** 63
     for parent, step in [(0, 0), (1, 7), (2 ** 40 + 3, 123456), (2 ** 63 + 9, 2 ** 32 - 1)]:
         assert O.secondary_id(parent, step) == mix(parent, step)
+
+
+# --------------------------------------------------------------------------
+# The paper's adaptive trial frequencies (Sec. 6.3 Binned, Sec. 6.4 Variable)
+# --------------------------------------------------------------------------
+def _sampled_max(m, gases, a, b, n=200001):
+    """max of nu over [a, b] by dense sampling plus every table point inside."""
+    xs = np.linspace(a, b, n)
+    pts = [np.asarray(ch.energy_eV) for g in gases for ch in g.channels]
+    inner = np.concatenate([p[(p >= a) & (p <= b)] for p in pts] + [xs])
+    return float(m.nu_many(inner).max())
+
+
+def test_range_max_matches_brute_force():
+    rng = np.random.default_rng(17)
+    for gases in ([W.argon_like()], W.ar_co2_mixture(), [W.batched_gases()[3], W.batched_gases()[5]]):
+        m = O.Mixture(gases)
+        for _ in range(12):
+            a = float(10 ** rng.uniform(-3.5, 2.3))
+            b = a * float(10 ** rng.uniform(0.01, 0.8))
+            got, ref = m.range_max(a, b), _sampled_max(m, gases, a, b)
+            # exact maximum: never below a sampled value, and the samples come close to it
+            assert got >= ref * (1 - 1e-12)
+            assert got <= ref * (1 + 2e-6)
+        # a bin of BinnedTrialFrequency is the range [10^(j/B), 10^((j+1)/B))
+        for B, j in ((8, -9), (8, 5), (3, 2), (1, 1)):
+            assert m.binned_max(B, j) == m.range_max(10 ** (j / B), 10 ** ((j + 1) / B))
+
+
+def _maxwell_run(**strategy):
+    spec = W.maxwell_swarm(n_electrons=4000, real_collisions=600)
+    gas = spec.gases[0]
+    m = O.Mixture(spec.gases)
+    p = O.run_swarm(m, e_over_n_Td=spec.e_over_n_Td, real_collisions=spec.real_collisions, n=spec.n_electrons,
+                    seed=spec.seed, eps0_mean_eV=spec.eps0_mean_eV, threads=O.cpu_count(), **strategy)
+    return spec, gas, m, p
+
+
+def test_variable_trial_frequency_on_a_constant_frequency_gas():
+    """With nu constant, nu' = (1 + zeta) nu never fails and the process is
+    exact: the efficiency (Eq. 28) is 1/(1 + zeta) and the transport
+    coefficients keep their closed forms."""
+    zeta = 0.25
+    spec, gas, m, p = _maxwell_run(strategy=O.TF_VARIABLE, zeta=zeta, grace=7)
+    assert np.all(p["n_real"] == 600) and np.all(p["n_fail"] == 0)
+    trials = p["n_real"].sum() + p["n_null"].sum()
+    eff = p["n_real"].sum() / trials
+    se = math.sqrt(eff * (1 - eff) / trials)
+    assert abs(eff - 1 / (1 + zeta)) < 5 * se
+    nu = 1e12
+    E = spec.e_over_n_Td * 1e-21 * gas.number_density_m3
+    vd = QE * E / (ME * nu)
+    tr = T.swarm_tallies(p, spec.e_over_n_Td, gas.number_density_m3)
+    assert abs(tr["W"] - vd) < 3.5 * tr["W_se"]
+    kappa = 2 * ME * gas.mass_kg / (ME + gas.mass_kg) ** 2
+    mean_eps, _, _ = _maxwell_closed_forms(600, 0.1, nu, kappa, vd)
+    assert abs(tr["eps"] - mean_eps) < 3.5 * tr["eps_se"]
+
+
+def test_binned_trial_frequency_on_a_constant_frequency_gas():
+    """Bins of a constant-frequency gas all hold the same maximum (up to the
+    table's interpolation ripple), so nu' = nu (1 + O(1e-5))."""
+    spec, gas, m, p = _maxwell_run(strategy=O.TF_BINNED, bins_per_decade=8, grace=11)
+    assert np.all(p["status"] == O.ST_DONE)
+    eff = p["n_real"].sum() / (p["n_real"].sum() + p["n_null"].sum() + p["n_fail"].sum())
+    assert eff > 0.9999
+    E = spec.e_over_n_Td * 1e-21 * gas.number_density_m3
+    vd = QE * E / (ME * 1e12)
+    tr = T.swarm_tallies(p, spec.e_over_n_Td, gas.number_density_m3)
+    assert abs(tr["W"] - vd) < 3.5 * tr["W_se"]
+
+
+def _energy(p):
+    return 0.5 * ME * (p["vx"] ** 2 + p["vy"] ** 2 + p["vz"] ** 2) / QE
+
+
+def test_adaptive_queries_follow_the_strategy_rules():
+    """Grace counts null and real collisions alike (Sec. 6); with a grace of
+    one, nu' is queried after every collision, so the last query happens
+    right after the last real collision, at the energy the electron leaves
+    with: Variable gives (1 + zeta) nu(eps), Binned the maximum over eps's bin."""
+    m = O.Mixture(W.ar_co2_mixture())
+    kw = dict(e_over_n_Td=20.0, real_collisions=60, n=300, seed=5, threads=O.cpu_count())
+    p = O.run_swarm(m, strategy=O.TF_VARIABLE, zeta=0.4, grace=1, **kw)
+    ok = p["status"] == O.ST_DONE
+    eps = _energy(p)[ok]
+    floor = 1e-9 * m.nu_max
+    want = 1.4 * np.maximum(m.nu_many(eps), floor)
+    assert ok.sum() > 250
+    assert np.allclose(p["nu_p"][ok], want, rtol=1e-12, atol=0.0)
+    # Binned: whatever the grace, nu' is always one bin's maximum (a query
+    # takes the bin of the current energy, a retry the larger of two bins)
+    p = O.run_swarm(m, strategy=O.TF_BINNED, bins_per_decade=4, grace=25, max_trials=200000, **kw)
+    assert (p["status"] == O.ST_DONE).sum() > 150
+    maxima = {max(m.binned_max(4, j), floor) for j in range(-16, 12)}
+    assert all(v in maxima for v in p["nu_p"])
+
+
+def test_binned_second_fail_before_a_real_collision_is_an_error():
+    """Sec. 6.3: after a fail the flight is retried with the larger of the two
+    bins' maxima; if it fails again the run stops with an error.  With one
+    bin per decade at a strong field, electrons cross bins often."""
+    m = O.Mixture([W.argon_like()])
+    p = O.run_swarm(m, e_over_n_Td=300.0, real_collisions=400, n=400, seed=8, threads=O.cpu_count(),
+                    strategy=O.TF_BINNED, bins_per_decade=1, grace=1000, max_trials=200000)
+    err = p["status"] == O.ST_TRIAL
+    assert err.any() and (~err).any()
+    assert np.all(p["n_fail"][err] >= 2)
+    # every nu' left behind is one bin's maximum (a retry takes the larger of two)
+    maxima = {m.binned_max(1, j) for j in range(-6, 4)}
+    assert all(v in maxima for v in p["nu_p"])
+
+
+def test_invalid_strategies_are_rejected():
+    m = O.Mixture([W.argon_like()])
+    kw = dict(e_over_n_Td=10.0, real_collisions=5, n=4, seed=1)
+    for bad in (dict(strategy=O.TF_VARIABLE, zeta=-0.1), dict(strategy=O.TF_BINNED, bins_per_decade=0),
+                dict(strategy=O.TF_VARIABLE, grace=0), dict(strategy=7)):
+        with pytest.raises(ValueError):
+            O.run_swarm(m, **kw, **bad)
