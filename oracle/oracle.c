@@ -355,6 +355,7 @@ double or_binned_max(const or_mixture *m, int B, int j)
 typedef struct {
     int B, j0, n;
     double *max;
+    double nu_first;  /* floor of the adaptive nu' */
 } or_binned;
 
 static void binned_setup(const or_mixture *m, int B, or_binned *bt)
@@ -663,12 +664,26 @@ typedef struct {
 /* Runs one electron from birth (time t0, velocity v0; t0 = 0 and a
  * Maxwellian start for primaries) to its limiters.  Positions and times are
  * kept relative to birth; the time limit is absolute. */
+/* nu at the lowest positive energy of any table or threshold. */
+static double nu_at_first_point(const or_mixture *m)
+{
+    double lo = INFINITY;
+    for (int c = 0; c < m->n_ch; ++c) {
+        const or_channel *ch = &m->ch[c];
+        for (int i = 0; i < ch->n; ++i)
+            if (ch->e[i] > 0.0) lo = fmin(lo, ch->e[i]);
+        if (ch->kind != OR_ELASTIC && ch->threshold > 0.0) lo = fmin(lo, ch->threshold);
+    }
+    return isfinite(lo) ? or_nu(m, lo) : 0.0;
+}
+
 /* Trial frequency of the adaptive strategies (Sec. 6) at energy eps:
  * Variable (1 + zeta) nu(eps), Binned the maximum of nu over the bin of eps;
- * neither below 1e-9 of the Lazy majorant (nu vanishes at eps = 0). */
+ * neither below nu at the lowest table energy (nu vanishes at eps = 0, and
+ * the tables say nothing below their first point). */
 static double adaptive_nu(const or_mixture *m, const or_config *cf, const or_binned *bt, double eps)
 {
-    double floor_nu = 1e-9 * m->nu_max;
+    double floor_nu = fmax(1e-9 * m->nu_max, bt->nu_first);
     if (cf->strategy == OR_TF_VARIABLE) return (1.0 + cf->zeta) * fmax(or_nu(m, eps), floor_nu);
     return fmax(binned_nu(m, bt, eps), floor_nu);
 }
@@ -709,16 +724,17 @@ static void run_particle_from(const or_mixture *m, const or_config *cf, const or
         double nu = or_nu(m, eps);
         if (nu > nu_p) { /* fail: Sec. 6 -- back to the last real collision */
             ++n_fail;
-            if (cf->fixed) { status = OR_ST_TRIAL; break; }
+            int error = cf->fixed; /* FixedTrialFrequency: a fail is an error */
             if (cf->strategy == OR_TF_BINNED) {
                 /* retry with the larger maximum of the two bins; a fail
                  * under that nu' (before a real collision or a new query)
                  * is an error */
-                if (retried) { status = OR_ST_TRIAL; break; }
+                error = retried;
                 retried = 1;
             }
             for (int i = 0; i < 3; ++i) { x[i] = sx[i]; v[i] = sv[i]; }
             t = st;
+            if (error) { status = OR_ST_TRIAL; break; } /* stopped at its last valid state */
             if (cf->strategy == OR_TF_VARIABLE) nu_p = adaptive_nu(m, cf, bt, eps);
             else if (cf->strategy == OR_TF_BINNED) nu_p = fmax(nu_p, adaptive_nu(m, cf, bt, eps));
             else nu_p = fmax(nu_p, 1.25 * nu);
@@ -791,6 +807,7 @@ static int strategy_setup(const or_mixture *m, const or_config *c, or_binned *bt
 {
     bt->n = 0;
     bt->max = NULL;
+    bt->nu_first = nu_at_first_point(m);
     if (c->strategy == OR_TF_CONST) return 0;
     if (c->strategy != OR_TF_VARIABLE && c->strategy != OR_TF_BINNED) return -1;
     if (c->grace < 1 || c->fixed) return -1;

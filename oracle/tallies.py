@@ -56,6 +56,12 @@ def _estimates(x, y, z, t, sum_e, sum_e2, n_real, n_ion, n_att, W_vec) -> Dict[s
 
 
 def swarm_tallies(p: Dict[str, np.ndarray], e_over_n_Td: float, n_total: float, groups: int = 32) -> Dict[str, float]:
+    # Eqs. (15)-(27) divide by each particle's time: a particle that never
+    # moved (t = 0, e.g. stopped by an error at its first trial) has no
+    # defined ratio and is left out
+    moved = np.asarray(p["t"], dtype=np.float64) > 0.0
+    if not np.all(moved):
+        p = {k: (np.asarray(v)[moved] if np.ndim(v) == 1 and len(v) == len(moved) else v) for k, v in p.items()}
     x, y, z, t = (np.asarray(p[k], dtype=np.float64) for k in ("x", "y", "z", "t"))
     sum_e, sum_e2 = np.asarray(p["sum_e"], np.float64), np.asarray(p["sum_e2"], np.float64)
     n_real = np.asarray(p["n_real"], np.float64)

@@ -637,12 +637,16 @@ def test_adaptive_queries_follow_the_strategy_rules():
     one, nu' is queried after every collision, so the last query happens
     right after the last real collision, at the energy the electron leaves
     with: Variable gives (1 + zeta) nu(eps), Binned the maximum over eps's bin."""
-    m = O.Mixture(W.ar_co2_mixture())
+    gases = W.ar_co2_mixture()
+    m = O.Mixture(gases)
     kw = dict(e_over_n_Td=20.0, real_collisions=60, n=300, seed=5, threads=O.cpu_count())
     p = O.run_swarm(m, strategy=O.TF_VARIABLE, zeta=0.4, grace=1, **kw)
     ok = p["status"] == O.ST_DONE
     eps = _energy(p)[ok]
-    floor = 1e-9 * m.nu_max
+    # floor: nu at the lowest positive table energy or threshold
+    first = min(min(e for e in ch.energy_eV if e > 0) for g in gases for ch in g.channels)
+    first = min([first] + [ch.threshold_eV for g in gases for ch in g.channels if ch.threshold_eV > 0])
+    floor = max(1e-9 * m.nu_max, m.nu(first))
     want = 1.4 * np.maximum(m.nu_many(eps), floor)
     assert ok.sum() > 250
     assert np.allclose(p["nu_p"][ok], want, rtol=1e-12, atol=0.0)
@@ -665,7 +669,8 @@ def test_binned_second_fail_before_a_real_collision_is_an_error():
     assert err.any() and (~err).any()
     assert np.all(p["n_fail"][err] >= 2)
     # every nu' left behind is one bin's maximum (a retry takes the larger of two)
-    maxima = {m.binned_max(1, j) for j in range(-6, 4)}
+    floor = m.nu(1e-3)   # nu at the lowest table energy
+    maxima = {max(m.binned_max(1, j), floor) for j in range(-6, 6)}
     assert all(v in maxima for v in p["nu_p"])
 
 
