@@ -34,7 +34,7 @@
 extern "C" {
 #endif
 
-#define BZ_ABI_VERSION 1
+#define BZ_ABI_VERSION 2
 
 typedef enum {
     BZ_OK = 0,
@@ -58,7 +58,25 @@ typedef enum { BZ_ANG_ISOTROPIC = 0, BZ_ANG_SCREENED_COULOMB = 1 } bz_angular;
  *            E and B, per-bin maxima of nu); a flight that outlasts the window
  *            restarts at its end (exact by memorylessness).  Same statistics as
  *            LAZY with far fewer null collisions. */
-typedef enum { BZ_TRIAL_LAZY = 0, BZ_TRIAL_FIXED = 1, BZ_TRIAL_WINDOW = 2 } bz_trial_mode;
+/* Trial frequency nu' (Sec. 6).  LAZY: the exact maximum of nu over the
+ * tables (a fail -- nu > nu' past the tables -- goes back to the last real
+ * collision and raises the particle's nu' to 1.25 nu).  FIXED: nu_trial, a
+ * fail is an error.  WINDOW: a local majorant over the energies reachable
+ * before the end of a short time window, renewed at window ends and real
+ * collisions (exact, never fails).  VARIABLE (Sec. 6.4): nu' = (1 + zeta)
+ * nu(eps), queried at the start, after every `grace` collisions (null or
+ * real) and on a fail.  BINNED (Sec. 6.3): nu' = the maximum of nu over the
+ * energy bin of eps (bins_per_decade bins per decade), queried likewise; a
+ * fail retries with the larger maximum of the two bins, and a fail under
+ * that retry value is an error (BZ_ERR_TRIAL).  VARIABLE and BINNED follow
+ * the paper and are not exact: a fail goes back to the last real collision. */
+typedef enum {
+    BZ_TRIAL_LAZY = 0,
+    BZ_TRIAL_FIXED = 1,
+    BZ_TRIAL_WINDOW = 2,
+    BZ_TRIAL_VARIABLE = 3,
+    BZ_TRIAL_BINNED = 4
+} bz_trial_mode;
 
 typedef struct bz_ctx bz_ctx;
 typedef struct bz_mixture bz_mixture;
@@ -178,10 +196,14 @@ typedef struct {
     int32_t spawn;            /* 1: ionizations create electrons, attachments remove them (Sec. 2) */
     int32_t reserved0;
     uint64_t pop_cap;         /* spawn mode: at most this many electrons in all; 0: 64 x n_electrons */
+    double zeta;              /* VARIABLE: overhead, nu' = (1 + zeta) nu(eps); >= 0 */
+    uint32_t grace;           /* VARIABLE, BINNED: collisions between queries of nu'; >= 1 */
+    int32_t bins_per_decade;  /* BINNED: 1, 2, 4, 8, 16 or 32 */
 } bz_swarm_config;
 
 /* Fills *cfg with defaults: N = 1e4, I = 1000, FP32, lazy mode, Maxwellian
- * start with mean 0.1 eV, no time limit, seed 1901081400, fields zero. */
+ * start with mean 0.1 eV, no time limit, seed 1901081400, fields zero;
+ * zeta = 0.25, grace = 5000, bins_per_decade = 8. */
 void bz_config_defaults(bz_swarm_config *cfg);
 
 /* Sets the fields of a configuration: reduced field E/N [Td] (E = (E/N) N
@@ -238,7 +260,7 @@ typedef struct {
 } bz_tallies;
 
 #define BZ_ERR_STAGE_TIMEOUT 1u /* table staging wait gave up */
-#define BZ_ERR_TRIAL 2u         /* fixed nu' exceeded */
+#define BZ_ERR_TRIAL 2u         /* fixed nu' exceeded, or a BINNED retry failed again */
 #define BZ_ERR_NONFINITE 4u     /* non-finite energy met; particle stopped */
 #define BZ_ERR_MAX_TRIALS 8u    /* a particle reached max_trials */
 #define BZ_ERR_SPAWN_WAIT 16u   /* spawn mode: a lane waited > 60 s for work */

@@ -21,9 +21,10 @@ import numpy as np
 from . import build as _build
 
 BZ_OK, BZ_EINVAL, BZ_ENOMEM, BZ_EBUDGET, BZ_ETRIAL, BZ_ETIMEOUT, BZ_ECUDA, BZ_ECANCEL, BZ_ENOTREADY = range(9)
-BZ_TRIAL_LAZY, BZ_TRIAL_FIXED, BZ_TRIAL_WINDOW = 0, 1, 2
+BZ_TRIAL_LAZY, BZ_TRIAL_FIXED, BZ_TRIAL_WINDOW, BZ_TRIAL_VARIABLE, BZ_TRIAL_BINNED = 0, 1, 2, 3, 4
 DEC_WINDOW, DEC_FAIL, DEC_NULL = -3, -2, -1
 ST_DONE, ST_TIME, ST_STEPS, ST_TRIAL, ST_ERROR, ST_ATTACHED = 0, 1, 2, 3, 4, 5
+BZ_ERR_STAGE_TIMEOUT, BZ_ERR_TRIAL, BZ_ERR_NONFINITE, BZ_ERR_MAX_TRIALS, BZ_ERR_SPAWN_WAIT = 1, 2, 4, 8, 16
 
 
 class BzError(RuntimeError):
@@ -65,7 +66,8 @@ class bz_swarm_config(C.Structure):
                 ("eps0_mean_eV", C.c_double), ("t_end_s", C.c_double), ("max_trials", C.c_uint64),
                 ("seed", C.c_uint64), ("id_offset", C.c_uint64), ("block_threads", C.c_int32),
                 ("blocks_per_sm", C.c_int32), ("window_c", C.c_double), ("spawn", C.c_int32),
-                ("reserved0", C.c_int32), ("pop_cap", C.c_uint64)]
+                ("reserved0", C.c_int32), ("pop_cap", C.c_uint64), ("zeta", C.c_double),
+                ("grace", C.c_uint32), ("bins_per_decade", C.c_int32)]
 
 
 _TALLY_DOUBLES = ["W", "W_se", "Wx", "Wy", "W_flux", "lorentz_angle", "mu", "mu_N", "mu_0", "eps", "eps_se",
@@ -333,7 +335,8 @@ def make_config(*, n_electrons: int, real_collisions: int, e_over_n_Td: float, b
                 b_angle_rad: float = 0.0, precision: int = 32, seed: int = 1901081400, eps0_mean_eV: float = 0.1,
                 trial_mode: int = BZ_TRIAL_LAZY, nu_trial: float = 0.0, t_end_s: float = 0.0, max_trials: int = 0,
                 id_offset: int = 0, attach_keep_state: bool = False, blocks_per_sm: int = 0,
-                window_c: float = 0.0, spawn: bool = False, pop_cap: int = 0) -> bz_swarm_config:
+                window_c: float = 0.0, spawn: bool = False, pop_cap: int = 0, zeta: float = 0.25,
+                grace: int = 5000, bins_per_decade: int = 8) -> bz_swarm_config:
     cfg = bz_swarm_config()
     lib().bz_config_defaults(C.byref(cfg))
     _check(lib().bz_set_fields(C.byref(cfg), float(e_over_n_Td), float(b_T), float(b_angle_rad)))
@@ -352,6 +355,9 @@ def make_config(*, n_electrons: int, real_collisions: int, e_over_n_Td: float, b
     cfg.window_c = float(window_c)
     cfg.spawn = int(bool(spawn))
     cfg.pop_cap = int(pop_cap)
+    cfg.zeta = float(zeta)
+    cfg.grace = int(grace)
+    cfg.bins_per_decade = int(bins_per_decade)
     return cfg
 
 

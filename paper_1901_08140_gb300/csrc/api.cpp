@@ -62,7 +62,7 @@ struct bz_batch {
     bz_ctx *ctx;
     int32_t n;
     int precision;
-    bool ch_smem, use_graph;
+    bool ch_smem, use_graph, adapt;
     size_t smem;
     int grid, n_tiles, max_tblocks;
     std::vector<uint64_t> n_el, id_offset;
@@ -205,6 +205,13 @@ bz::Fields make_fields(const bz_swarm_config &cfg, double n_total)
     return f;
 }
 
+// The paper's adaptive trial frequencies (Sec. 6), run by the ADAPT
+// instance of the step kernel.
+bool adaptive(const bz_swarm_config *cfg)
+{
+    return cfg->trial_mode == BZ_TRIAL_VARIABLE || cfg->trial_mode == BZ_TRIAL_BINNED;
+}
+
 bz_status validate_config(const bz_swarm_config *cfg)
 {
     if (!cfg) return fail(BZ_EINVAL, "null configuration");
@@ -213,8 +220,15 @@ bz_status validate_config(const bz_swarm_config *cfg)
     if (cfg->real_collisions < 1) return fail(BZ_EINVAL, "real_collisions must be >= 1");
     if (!(cfg->e_over_n_Td >= 0.0) || !isfinite(cfg->e_over_n_Td)) return fail(BZ_EINVAL, "bad E/N");
     if (!(cfg->b_T >= 0.0) || !isfinite(cfg->b_T) || !isfinite(cfg->b_angle_rad)) return fail(BZ_EINVAL, "bad B");
-    if (cfg->trial_mode != BZ_TRIAL_LAZY && cfg->trial_mode != BZ_TRIAL_FIXED && cfg->trial_mode != BZ_TRIAL_WINDOW)
-        return fail(BZ_EINVAL, "bad trial mode");
+    if (cfg->trial_mode < BZ_TRIAL_LAZY || cfg->trial_mode > BZ_TRIAL_BINNED) return fail(BZ_EINVAL, "bad trial mode");
+    if (adaptive(cfg)) {
+        if (!(cfg->zeta >= 0.0) || !isfinite(cfg->zeta)) return fail(BZ_EINVAL, "zeta must be finite and >= 0");
+        if (cfg->grace < 1) return fail(BZ_EINVAL, "grace must be >= 1");
+        if (cfg->trial_mode == BZ_TRIAL_BINNED && (cfg->bins_per_decade < 1 || cfg->bins_per_decade > 32 ||
+                                                   (cfg->bins_per_decade & (cfg->bins_per_decade - 1))))
+            return fail(BZ_EINVAL, "bins_per_decade must be 1, 2, 4, 8, 16 or 32");
+        if (cfg->spawn) return fail(BZ_EINVAL, "spawn mode runs with the lazy, fixed or windowed trial frequency");
+    }
     if (!(cfg->window_c >= 0.0) || !isfinite(cfg->window_c)) return fail(BZ_EINVAL, "window_c must be >= 0");
     if (cfg->trial_mode == BZ_TRIAL_FIXED && !(cfg->nu_trial > 0.0)) return fail(BZ_EINVAL, "fixed mode needs nu_trial > 0");
     if (!(cfg->eps0_mean_eV >= 0.0) || !isfinite(cfg->eps0_mean_eV)) return fail(BZ_EINVAL, "bad eps0_mean_eV");
@@ -254,6 +268,16 @@ bz_status prepare_run(const bz_mixture *mix, const bz_swarm_config *cfg, bz::Run
     a->win_c = (float)(cfg->window_c > 0.0 ? cfg->window_c : 2.0);
     a->nu_floor = 1e-9 * mix->cm.nu_max;
     a->f = make_fields(*cfg, mix->cm.n_total);
+    a->tf = cfg->trial_mode == BZ_TRIAL_VARIABLE ? bz::TF_VARIABLE
+            : cfg->trial_mode == BZ_TRIAL_BINNED ? bz::TF_BINNED : bz::TF_NONE;
+    a->tf_zeta1 = 1.0 + cfg->zeta;
+    // the adaptive nu' is never below nu at the lowest table energy (nu
+    // vanishes at rest, and the tables say nothing below their first point)
+    if (a->tf != bz::TF_NONE) a->nu_floor = std::max(a->nu_floor, a->lay.nu_first);
+    a->tf_grace = cfg->grace;
+    a->tf_B = cfg->bins_per_decade;
+    if (a->tf == bz::TF_BINNED && (a->lay.bins_per_decade % cfg->bins_per_decade) != 0)
+        return fail(BZ_EINVAL, "bins_per_decade must divide the mixture's compiled bins per decade");
     return BZ_OK;
 }
 
@@ -382,6 +406,9 @@ void bz_config_defaults(bz_swarm_config *cfg)
     cfg->trial_mode = BZ_TRIAL_LAZY;
     cfg->eps0_mean_eV = 0.1;
     cfg->seed = 1901081400ull;
+    cfg->zeta = 0.25;
+    cfg->grace = 5000;
+    cfg->bins_per_decade = 8;
 }
 
 bz_status bz_set_fields(bz_swarm_config *cfg, double e_over_n_Td, double b_T, double b_angle_rad)
@@ -414,7 +441,8 @@ bz_status bz_run_swarm(bz_ctx *ctx, const bz_mixture *mix, const bz_swarm_config
     if (cap > 0xFFFFFFFFull) return fail(BZ_EINVAL, "a swarm holds at most 2^32-1 electrons");
     const int block = 256;
     int bps = spawn ? bz::spawn_occupancy(cfg->precision, ch_smem, block, a.stage_bytes)
-                    : bz::batch_occupancy(cfg->precision, ch_smem, block, a.stage_bytes);
+                    : bz::batch_occupancy(cfg->precision, ch_smem, adaptive(cfg), block, a.stage_bytes);
+    if (bps < 0) return cuda_fail((cudaError_t)(-bps), "occupancy of the step kernel");
     if (bps < 1) return fail(BZ_ECUDA, "step kernel cannot be resident with these tables");
     if (cfg->blocks_per_sm > 0 && cfg->blocks_per_sm < bps) bps = cfg->blocks_per_sm;
     const uint64_t grid64 = (uint64_t)ctx->sm_count * bps;
@@ -514,7 +542,7 @@ bz_status bz_run_swarm(bz_ctx *ctx, const bz_mixture *mix, const bz_swarm_config
         ba.slot_lo = 0;
         const int grid = (int)(grid64 < n_tiles ? grid64 : n_tiles);
         if (e == cudaSuccess && n_tiles > 0)
-            e = bz::launch_batch(cfg->precision, ch_smem, ba, a.stage_bytes, grid, block, s->stream);
+            e = bz::launch_batch(cfg->precision, ch_smem, adaptive(cfg), ba, a.stage_bytes, grid, block, s->stream);
     } else {
         // every electron, created ones included, in one persistent launch
         uint64_t want = (cap + block - 1) / block;
@@ -562,7 +590,7 @@ static bz_status finish_tallies(bz_swarm *sw, bz_tallies *out)
 {
     *out = *sw->tallies_host;
     if (out->error_flags & BZ_ERR_STAGE_TIMEOUT) return fail(BZ_ETIMEOUT, "table staging timed out");
-    if (out->error_flags & BZ_ERR_TRIAL) return fail(BZ_ETRIAL, "fixed trial frequency exceeded");
+    if (out->error_flags & BZ_ERR_TRIAL) return fail(BZ_ETRIAL, "trial frequency exceeded (fixed mode, or a binned retry that failed again)");
     return BZ_OK;
 }
 
@@ -675,7 +703,7 @@ static cudaError_t batch_part(bz_batch *b, int part, cudaStream_t s)
         a.tiles = b->tiles;
         a.n_tiles = b->n_tiles;
         a.tile_counter = b->tile_counter;
-        if (e == cudaSuccess) e = bz::launch_batch(b->precision, b->ch_smem, a, b->smem, b->grid, 256, s);
+        if (e == cudaSuccess) e = bz::launch_batch(b->precision, b->ch_smem, b->adapt, a, b->smem, b->grid, 256, s);
         return e;
     }
     e = bz::launch_tallies_multi(b->targs, b->n, b->max_tblocks, s);
@@ -708,6 +736,8 @@ bz_status bz_create_batch(bz_ctx *ctx, int32_t n, const bz_mixture *const *mixtu
         if (!mixtures[i]) return fail(BZ_EINVAL, "null mixture");
         if (cfgs[i].precision != precision) return fail(BZ_EINVAL, "all swarms of a batch need the same precision");
         if (cfgs[i].spawn) return fail(BZ_EINVAL, "spawn-mode swarms run through bz_run_swarm");
+        if (adaptive(&cfgs[i]) != adaptive(&cfgs[0]))
+            return fail(BZ_EINVAL, "a batch holds either VARIABLE / BINNED swarms or swarms of the other modes");
         if (cfgs[i].n_electrons > 0xFFFFFFFFull) return fail(BZ_EINVAL, "a batched swarm holds at most 2^32-1 electrons");
     }
     cudaError_t e = cudaSetDevice(ctx->device);
@@ -717,6 +747,7 @@ bz_status bz_create_batch(bz_ctx *ctx, int32_t n, const bz_mixture *const *mixtu
     b->ctx = ctx;
     b->n = n;
     b->precision = precision;
+    b->adapt = adaptive(&cfgs[0]);
     b->use_graph = opts ? opts->use_graph != 0 : true;
     // tables of every mixture must fit; channel tables go to shared memory only if all fit
     b->ch_smem = true;
@@ -735,7 +766,7 @@ bz_status bz_create_batch(bz_ctx *ctx, int32_t n, const bz_mixture *const *mixtu
         desc[i].stage_bytes = b->ch_smem ? desc[i].lay.stage_all : desc[i].lay.stage_tables;
         b->smem = std::max(b->smem, (size_t)desc[i].stage_bytes);
     }
-    int bps = bz::batch_occupancy(precision, b->ch_smem, 256, b->smem);
+    int bps = bz::batch_occupancy(precision, b->ch_smem, b->adapt, 256, b->smem);
     if (bps < 1) {
         delete b;
         return fail(BZ_ECUDA, "batch kernel cannot be resident with these tables");
@@ -842,7 +873,7 @@ bz_status bz_create_batch(bz_ctx *ctx, int32_t n, const bz_mixture *const *mixtu
     }
     if (b->use_graph) {
         // make sure the kernels' shared-memory limits are set before capture
-        bz::batch_occupancy(precision, b->ch_smem, 256, b->smem);
+        bz::batch_occupancy(precision, b->ch_smem, b->adapt, 256, b->smem);
         for (int part = 0; part < 2 && e == cudaSuccess; ++part) {
             e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
             cudaError_t e1 = (e == cudaSuccess) ? batch_part(b, part, b->cap) : e;
@@ -884,7 +915,7 @@ bz_status bz_batch_read_tallies(bz_batch *b, bz_tallies *out)
     for (int i = 0; i < b->n; ++i) {
         out[i] = b->tallies_host[i];
         if (out[i].error_flags & BZ_ERR_STAGE_TIMEOUT) st = fail(BZ_ETIMEOUT, "table staging timed out");
-        else if ((out[i].error_flags & BZ_ERR_TRIAL) && st == BZ_OK) st = fail(BZ_ETRIAL, "fixed trial frequency exceeded");
+        else if ((out[i].error_flags & BZ_ERR_TRIAL) && st == BZ_OK) st = fail(BZ_ETRIAL, "trial frequency exceeded (fixed mode, or a binned retry that failed again)");
     }
     return st;
 }
@@ -969,6 +1000,7 @@ bz_status bz_step_replay(bz_ctx *ctx, const bz_mixture *mix, const bz_swarm_conf
     if (!state_in_dev || !ids_dev || !steps_dev || !state_out_dev || !decision_dev || !eps_dev)
         return fail(BZ_EINVAL, "null buffer");
     if (cfg->precision != 32 && cfg->precision != 64) return fail(BZ_EINVAL, "precision must be 32 or 64");
+    if (adaptive(cfg)) return fail(BZ_EINVAL, "single steps replay the lazy, fixed or windowed trial frequency");
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
     bz::ReplayArgs r;

@@ -69,6 +69,10 @@ struct Layout {
     float bin_lo, inv_binw;  // log2 energy of the first bin edge, bins per unit log2
     double nu_low;           // max nu over [0, 2^bin_lo]
     double g_top;            // last union point [eV]
+    // bin edges lie on the lattice 10^(j / bins_per_decade), the first at
+    // j = bin_j0; low_sqrt: below it nu = nu_low sqrt(eps / 2^bin_lo)
+    int32_t bin_j0, bins_per_decade, low_sqrt;
+    double nu_first;         // nu at the first positive union point (floor of the adaptive nu')
     // per-gas density sums per record ({val, slope}, n_rec x n_gases, global
     // memory) and each gas's channel range, for a two-level channel search
     uint32_t off_gval;

@@ -76,6 +76,12 @@ __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
 __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
 __device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsqrt_(double x) { return rsqrt(x); }
+__device__ __forceinline__ float log10_(float x) { return log10f(x); }
+__device__ __forceinline__ double log10_(double x) { return log10(x); }
+__device__ __forceinline__ float exp10_(float x) { return exp10f(x); }
+__device__ __forceinline__ double exp10_(double x) { return exp10(x); }
+__device__ __forceinline__ float floor_(float x) { return floorf(x); }
+__device__ __forceinline__ double floor_(double x) { return floor(x); }
 __device__ __forceinline__ void sincos_(float x, float *s, float *c) { sincosf(x, s, c); }
 __device__ __forceinline__ void sincos_(double x, double *s, double *c) { sincos(x, s, c); }
 __device__ __forceinline__ void sincospi_(float x, float *s, float *c) { sincospif(x, s, c); }
@@ -309,6 +315,8 @@ struct PState {
     double t0;               // birth time (absolute)
     uint32_t id_lo, id_hi, k, n_real, n_null, n_fail, n_ion, n_att, status;
     bool done;
+    uint32_t grace;          // adaptive trial frequencies: collisions left before the next query
+    bool retried;            // BINNED: nu' comes from a retry after a fail
 };
 
 template <typename R>
@@ -485,6 +493,80 @@ __device__ __forceinline__ void new_window(const Tab<R> &T, const Fld<R> &F, con
     s.T_wend = t0 + dt;
 }
 
+// BinnedTrialFrequency (Sec. 6.3): the maximum of nu over the energy bin of
+// eps, bin j = [10^(j/B), 10^((j+1)/B)) with j = floor(B log10 eps).  The
+// compiled bins lie on the lattice 10^(i/fpd) and B divides fpd, so bin j is
+// the run of compiled bins [j fpd/B, (j+1) fpd/B): its maximum comes from
+// two entries of the sparse table.  Below the compiled bins nu grows as
+// sqrt(eps) (a constant density sum) when the layout says so, else nu_low
+// bounds it; above them the power-law tails are bounded per channel.
+template <typename R>
+__device__ R binned_max(const Tab<R> &T, const RunArgs &P, R eps)
+{
+    if (!(eps > (R)0)) return (R)0;
+    const int fpd = P.lay.bins_per_decade, B = P.tf_B, m = fpd / B, j0 = P.lay.bin_j0;
+    const int j = (int)floor_((R)B * log10_(eps));
+    int lo = j * m - j0;
+    const int hi = lo + m - 1;
+    if (hi < 0) {
+        if (!P.lay.low_sqrt) return T.nu_low;
+        // nu_low is nu at the first compiled edge 10^(j0/fpd)
+        return T.nu_low * exp10_((R)0.5 * ((R)(j + 1) / (R)B - (R)j0 / (R)fpd));
+    }
+    if (lo < 0) lo = 0;  // the part below is dominated by the first compiled bin
+    R mx = (R)0;
+    if (lo < T.n_bins) {
+        const int h = hi < T.n_bins ? hi : T.n_bins - 1;
+        const int l = 31 - __clz(h - lo + 1);
+        const R *lev = T.binmax + (size_t)l * T.n_bins;
+        mx = max_(lev[lo], lev[h - (1 << l) + 1]);
+    }
+    if (hi >= T.n_bins) {
+        const R a = max_(exp10_((R)(j0 + T.n_bins) / (R)fpd), exp10_((R)j / (R)B));
+        mx = max_(mx, tail_bound(T, a, exp10_((R)(j + 1) / (R)B)));
+    }
+    return mx;
+}
+
+// nu' of the adaptive strategies at energy eps where nu = nu(eps) is known
+// (Sec. 6): VARIABLE (1 + zeta) nu, BINNED the maximum over eps's bin; not
+// below nu_floor, nu at the lowest table energy (nu vanishes at rest).
+template <typename R>
+__device__ __forceinline__ R adaptive_nu(const Tab<R> &T, const RunArgs &P, R eps, R nu)
+{
+    if (P.tf == TF_VARIABLE) return (R)P.tf_zeta1 * max_(nu, (R)P.nu_floor);
+    return max_(binned_max(T, P, eps), (R)P.nu_floor);
+}
+
+// nu(eps) from the tables (Eq. 2), for queries at an energy the step has
+// not evaluated.
+template <typename R>
+__device__ __forceinline__ R nu_at(const Tab<R> &T, const Fld<R> &F, R eps)
+{
+    int ri;
+    R elo;
+    return sqrt_(eps / F.Ke) * density(T, eps, ri, elo);
+}
+
+template <typename R>
+__device__ __forceinline__ R density_at(const Tab<R> &T, R eps)
+{
+    int ri;
+    R elo;
+    return density(T, eps, ri, elo);
+}
+
+// First query of an electron's nu' (VARIABLE, BINNED) at its start.
+template <typename R>
+__device__ __forceinline__ void adaptive_start(const Tab<R> &T, const Fld<R> &F, const RunArgs &P, PState<R> &s)
+{
+    const R eps = F.Ke * (s.vr0 * s.vr0 + s.vr1 * s.vr1 + s.vr2 * s.vr2);
+    s.nu_p = adaptive_nu(T, P, eps, P.tf == TF_VARIABLE ? nu_at(T, F, eps) : (R)0);
+    s.inv_nu = (R)1 / s.nu_p;
+    s.grace = P.tf_grace;
+    s.retried = false;
+}
+
 template <typename R>
 __device__ __forceinline__ void init_particle(const Tab<R> &T, const RunArgs &P, const Fld<R> &F, PState<R> &s,
                                               uint64_t id)
@@ -615,7 +697,7 @@ __device__ __noinline__ void spawn_secondary(const RunArgs &P, const Fld<R> &F, 
 // every lane, and every lane that needs a new trial-frequency window (window
 // end, real collision, fail) computes it at one common point after the
 // branches, so divergent lanes do not repeat that code.
-template <typename R, bool CH_SMEM>
+template <typename R, bool CH_SMEM, bool ADAPT = false>
 __device__ __forceinline__ int trial(const Tab<R> &T, const Fld<R> &F, const RunArgs &P, PState<R> &s, R &eps_i,
                                      R &eps_f)
 {
@@ -679,7 +761,15 @@ __device__ __forceinline__ int trial(const Tab<R> &T, const Fld<R> &F, const Run
                 return DEC_FAIL;
             }
             ++s.n_fail;
-            if (P.fixed) {  // FixedTrialFrequency (Sec. 6.1): an error
+            bool error = P.fixed;  // FixedTrialFrequency (Sec. 6.1): an error
+            if constexpr (ADAPT) {
+                // BinnedTrialFrequency (Sec. 6.3): one retry, then an error
+                if (P.tf == TF_BINNED) {
+                    error = s.retried;
+                    s.retried = true;
+                }
+            }
+            if (error) {
                 atomicOr(P.err, BZ_ERR_TRIAL);
                 s.status = ST_TRIAL;
                 s.done = true;
@@ -696,6 +786,14 @@ __device__ __forceinline__ int trial(const Tab<R> &T, const Fld<R> &F, const Run
             ++s.n_null;
             s.T = Tn;
             dec = DEC_NULL;
+            if constexpr (ADAPT) {
+                if (--s.grace == 0) {  // end of the grace period: query nu' here
+                    s.nu_p = adaptive_nu(T, P, eps, nu);
+                    s.inv_nu = (R)1 / s.nu_p;
+                    s.grace = P.tf_grace;
+                    s.retried = false;
+                }
+            }
         } else {
             // ---- real collision ----
             const int c = select_channel<R, CH_SMEM>(T, ri, elo, eps, r * inv_sp);
@@ -803,13 +901,28 @@ __device__ __forceinline__ int trial(const Tab<R> &T, const Fld<R> &F, const Run
             w1 = s.vr1;
             w2 = s.vr2;
             dec = c;
+            if constexpr (ADAPT) {
+                s.retried = false;
+                if (--s.grace == 0) {  // query at the energy the electron leaves with
+                    s.nu_p = adaptive_nu(T, P, eps_f, P.tf == TF_VARIABLE ? nsp * density_at(T, eps_f) : (R)0);
+                    s.inv_nu = (R)1 / s.nu_p;
+                    s.grace = P.tf_grace;
+                }
+            }
         }
     }
     if (need_window) {
         new_window(T, F, P, s, w0, w1, w2, wt0);
     }
     if (dec == DEC_FAIL) {
-        s.nu_p = max_(s.nu_p, (R)1.25 * nu_fail);
+        if constexpr (ADAPT) {
+            // VARIABLE: (1 + zeta) nu at the fail; BINNED: the larger of the two bins' maxima
+            const R q = adaptive_nu(T, P, eps, nu_fail);
+            s.nu_p = (P.tf == TF_VARIABLE) ? q : max_(s.nu_p, q);
+            s.grace = P.tf_grace;
+        } else {
+            s.nu_p = max_(s.nu_p, (R)1.25 * nu_fail);
+        }
         s.inv_nu = (R)1 / s.nu_p;
     }
     return dec;
@@ -942,7 +1055,7 @@ __device__ bool restage_tables(const uint8_t *src, uint8_t *dst, uint32_t bytes,
 // one it holds, runs the tile's electrons with per-lane refill (a lane that
 // finishes an electron takes the next one of the tile), and synchronises
 // before the next tile.
-template <typename R, bool CH_SMEM>
+template <typename R, bool CH_SMEM, bool ADAPT>
 __global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? BZ_SWARM_MIN_BLOCKS : 1)
     batch_kernel(const __grid_constant__ BatchArgs B)
 {
@@ -1007,6 +1120,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? BZ_SWARM_MIN_BLOCKS :
                     if (idx < tile.z) {
                         slot = (uint64_t)tile.y + idx;
                         init_particle<R>(T, P, F, s, P.id_offset + slot);
+                        if constexpr (ADAPT) adaptive_start(T, F, P, s);
                         have = true;
                     }
                 }
@@ -1020,7 +1134,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? BZ_SWARM_MIN_BLOCKS :
                     atomicOr(P.err, BZ_ERR_MAX_TRIALS);
                 } else {
                     R ei, ef;
-                    trial<R, CH_SMEM>(T, F, P, s, ei, ef);
+                    trial<R, CH_SMEM, ADAPT>(T, F, P, s, ei, ef);
                 }
                 if (s.done) {
                     write_particle<R>(P, s, slot);
@@ -1543,29 +1657,47 @@ __global__ void tally_final_multi(const TallyArgs *As) { tally_final_body(As[blo
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
+// Lets `kernel` take up to the device's opt-in shared memory per block minus
+// its static shared memory (dynamic plus static above 48 KB needs the
+// opt-in); the limit only ever rises to that one value, so concurrent
+// launches of the same kernel with different table sizes cannot race on it.
 template <typename K>
 static cudaError_t prep_smem(K kernel, size_t smem)
 {
-    if (smem > 48 * 1024) return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    return cudaSuccess;
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kernel);
+    if (e != cudaSuccess) return e;
+    const int limit = optin - (int)fa.sharedSizeBytes;
+    if ((long long)smem > (long long)limit) return cudaErrorInvalidValue;
+    if (fa.maxDynamicSharedSizeBytes < limit)
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, limit);
+    return e;
 }
 
-cudaError_t launch_batch(int precision, bool ch_smem, const BatchArgs &a, size_t smem, int grid, int block,
-                         cudaStream_t s)
+cudaError_t launch_batch(int precision, bool ch_smem, bool adapt, const BatchArgs &a, size_t smem, int grid,
+                         int block, cudaStream_t s)
 {
     if (block != kBlock) return cudaErrorInvalidValue;
     cudaError_t e;
-#define BZ_LAUNCH(R, C)                                                        \
+#define BZ_LAUNCH(R, C, A)                                                     \
     do {                                                                       \
-        e = prep_smem(batch_kernel<R, C>, smem);                               \
+        e = prep_smem(batch_kernel<R, C, A>, smem);                            \
         if (e != cudaSuccess) return e;                                        \
-        batch_kernel<R, C><<<grid, block, smem, s>>>(a);                       \
+        batch_kernel<R, C, A><<<grid, block, smem, s>>>(a);                    \
+    } while (0)
+#define BZ_LAUNCH2(R, C) \
+    do {                 \
+        if (adapt) BZ_LAUNCH(R, C, true); else BZ_LAUNCH(R, C, false); \
     } while (0)
     if (precision == 64) {
-        if (ch_smem) BZ_LAUNCH(double, true); else BZ_LAUNCH(double, false);
+        if (ch_smem) BZ_LAUNCH2(double, true); else BZ_LAUNCH2(double, false);
     } else {
-        if (ch_smem) BZ_LAUNCH(float, true); else BZ_LAUNCH(float, false);
+        if (ch_smem) BZ_LAUNCH2(float, true); else BZ_LAUNCH2(float, false);
     }
+#undef BZ_LAUNCH2
 #undef BZ_LAUNCH
     return cudaGetLastError();
 }
@@ -1608,22 +1740,28 @@ int spawn_occupancy(int precision, bool ch_smem, int block, size_t smem)
     return e == cudaSuccess ? n : 0;
 }
 
-int batch_occupancy(int precision, bool ch_smem, int block, size_t smem)
+int batch_occupancy(int precision, bool ch_smem, bool adapt, int block, size_t smem)
 {
     int n = 0;
     cudaError_t e;
-#define BZ_OCC(R, C)                                                                        \
-    do {                                                                                    \
-        prep_smem(batch_kernel<R, C>, smem);                                                \
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<R, C>, block, smem); \
+#define BZ_OCC(R, C, A)                                                                            \
+    do {                                                                                           \
+        e = prep_smem(batch_kernel<R, C, A>, smem);                                                \
+        if (e == cudaSuccess)                                                                      \
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<R, C, A>, block, smem); \
+    } while (0)
+#define BZ_OCC2(R, C) \
+    do {              \
+        if (adapt) BZ_OCC(R, C, true); else BZ_OCC(R, C, false); \
     } while (0)
     if (precision == 64) {
-        if (ch_smem) BZ_OCC(double, true); else BZ_OCC(double, false);
+        if (ch_smem) BZ_OCC2(double, true); else BZ_OCC2(double, false);
     } else {
-        if (ch_smem) BZ_OCC(float, true); else BZ_OCC(float, false);
+        if (ch_smem) BZ_OCC2(float, true); else BZ_OCC2(float, false);
     }
+#undef BZ_OCC2
 #undef BZ_OCC
-    return e == cudaSuccess ? n : 0;
+    return e == cudaSuccess ? n : -(int)e;
 }
 
 cudaError_t launch_tallies_multi(const TallyArgs *args_dev, int n_swarms, int max_blocks, cudaStream_t s)

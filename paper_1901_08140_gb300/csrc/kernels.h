@@ -10,6 +10,7 @@ namespace bz {
 
 enum { ST_DONE = 0, ST_TIME = 1, ST_STEPS = 2, ST_TRIAL = 3, ST_ERROR = 4, ST_ATTACHED = 5 };
 enum { DEC_WINDOW = -3, DEC_FAIL = -2, DEC_NULL = -1 };
+enum { TF_NONE = 0, TF_VARIABLE = 1, TF_BINNED = 2 };
 
 // Uniform static fields in the force frame (force on the electron along +z).
 struct Fields {
@@ -43,6 +44,12 @@ struct RunArgs {
     int32_t window;          // windowed local trial frequency
     float win_c;             // window length in units of 1/nu of the current energy bin
     double nu_floor;         // lower bound of any trial frequency [1/s]
+    // the paper's adaptive trial frequencies (Sec. 6): tf = TF_VARIABLE or
+    // TF_BINNED (0 otherwise), run by the ADAPT instance of the step kernel
+    int32_t tf;
+    double tf_zeta1;         // VARIABLE: 1 + zeta
+    uint32_t tf_grace;       // collisions between queries of nu'
+    int32_t tf_B;            // BINNED: bins per decade (divides lay.bins_per_decade)
     // spawn mode: slots [0, n_primary) are the initial electrons; secondaries
     // take slots from *n_total (up to cap) and their birth state from
     // b*[slot - n_primary]; bid[] != 0 marks a published birth record
@@ -103,15 +110,18 @@ struct BatchArgs {
 cudaError_t launch_replay(int precision, bool ch_smem, const ReplayArgs &a, int grid, int block, cudaStream_t s);
 cudaError_t launch_philox(int64_t n, const uint32_t *ctr, uint64_t key, uint32_t *out, cudaStream_t s);
 cudaError_t launch_tallies(const TallyArgs &a, cudaStream_t s);
-cudaError_t launch_batch(int precision, bool ch_smem, const BatchArgs &a, size_t smem, int grid, int block,
-                         cudaStream_t s);
+// adapt: the instance that runs the paper's adaptive trial frequencies (every
+// swarm of the launch must then use one; the other instance runs the rest).
+cudaError_t launch_batch(int precision, bool ch_smem, bool adapt, const BatchArgs &a, size_t smem, int grid,
+                         int block, cudaStream_t s);
 // Spawn mode: one persistent launch runs the primaries and every electron
 // created from them (slots handed out as tickets from a.counter).
 cudaError_t launch_spawn(int precision, bool ch_smem, const RunArgs &a, size_t smem, int grid, int block,
                          cudaStream_t s);
 int spawn_occupancy(int precision, bool ch_smem, int block, size_t smem);
 // Blocks of `block` threads that fit on one SM with `smem` bytes of tables.
-int batch_occupancy(int precision, bool ch_smem, int block, size_t smem);
+// (a negative value is minus the CUDA error of the query)
+int batch_occupancy(int precision, bool ch_smem, bool adapt, int block, size_t smem);
 // Tallies of n_swarms swarms; args_dev is a device array of TallyArgs.
 cudaError_t launch_tallies_multi(const TallyArgs *args_dev, int n_swarms, int max_blocks, cudaStream_t s);
 int tally_blocks(uint64_t n, int sm_count);

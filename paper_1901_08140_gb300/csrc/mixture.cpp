@@ -84,8 +84,11 @@ struct Bins {
     std::vector<double> max;   // per-bin maxima, then the sparse-table levels: level l holds
     int levels;                // the max over bins [b, b + 2^l) at [l * n_bins + b]
     int n_bins;
+    int j0, per_decade;        // first edge 10^(j0 / per_decade)
     float lo, inv_w;
     double nu_low;
+    double nu_first;  // nu at the first positive union point
+    bool low_sqrt;
 };
 
 template <typename R>
@@ -177,6 +180,10 @@ void emit(const std::vector<Chan> &ch, const std::vector<double> &g, const std::
     lay->bin_lo = bins.lo;
     lay->inv_binw = bins.inv_w;
     lay->nu_low = bins.nu_low;
+    lay->bin_j0 = bins.j0;
+    lay->bins_per_decade = bins.per_decade;
+    lay->low_sqrt = bins.low_sqrt ? 1 : 0;
+    lay->nu_first = bins.nu_first;
     lay->g_top = g.back();
 }
 
@@ -387,29 +394,52 @@ bz_status compile_mixture(const bz_gas *gases, int32_t n_gases, const bz_mixture
         }
         return m * (1.0 + 1e-9);
     };
+    // Bins are 1/fpd decade wide with edges on the lattice 10^(j/fpd)
+    // (fpd = 32, halved while the tables would need more than 1024 bins), from
+    // the edge at or below the first positive union point to three decades
+    // above the last one, so that the maxima are exact in the tails too.
     Bins bins;
     {
-        double Lb0 = L0, Lb1 = log2(g[P - 1] > 0.0 ? g[P - 1] : 1.0);
-        int nbins = (Lb1 > Lb0) ? (int)ceil((Lb1 - Lb0) / log2(10.0) * 32.0) : 1;
-        nbins = std::min(std::max(nbins, 1), 1024);
-        double bw = (Lb1 > Lb0) ? (Lb1 - Lb0) / nbins : 0.0;
+        const double d0 = (ipos < P) ? log10(g[ipos]) : 0.0, d1 = log10(g[P - 1] > 0.0 ? g[P - 1] : 1.0) + 3.0;
+        int fpd = 32, j0 = 0, nbins = 1;
+        for (;;) {
+            j0 = (int)floor(fpd * d0);
+            int j1 = (int)ceil(fpd * d1);
+            if (j1 <= j0) j1 = j0 + 1;
+            nbins = j1 - j0;
+            if (nbins <= 1024 || fpd == 1) break;
+            fpd /= 2;
+        }
+        nbins = std::min(nbins, 1024);
+        auto edge = [&](int j) { return pow(10.0, (double)j / fpd); };
         int levels = 1;
         while ((1 << levels) <= nbins) ++levels;
         bins.n_bins = nbins;
         bins.levels = levels;
+        bins.j0 = j0;
+        bins.per_decade = fpd;
         bins.max.assign((size_t)levels * nbins, 0.0);
-        for (int b = 0; b < nbins; ++b) {
-            double a = exp2(Lb0 + b * bw), e = (b == nbins - 1) ? g[P - 1] : exp2(Lb0 + (b + 1) * bw);
-            bins.max[b] = range_max(a, e);
-        }
+        for (int b = 0; b < nbins; ++b) bins.max[b] = range_max(edge(j0 + b), edge(j0 + b + 1));
         // sparse table for O(1) range maxima
         for (int l = 1; l < levels; ++l)
             for (int b = 0; b + (1 << l) <= nbins; ++b)
                 bins.max[(size_t)l * nbins + b] = std::max(bins.max[(size_t)(l - 1) * nbins + b],
                                                            bins.max[(size_t)(l - 1) * nbins + b + (1 << (l - 1))]);
-        bins.lo = (float)Lb0;
-        bins.inv_w = (bw > 0.0) ? (float)(1.0 / bw) : 0.0f;
-        bins.nu_low = range_max(0.0, exp2(Lb0));
+        bins.lo = (float)((double)j0 / fpd * log2(10.0));
+        bins.inv_w = (float)(fpd / log2(10.0));
+        bins.nu_low = range_max(0.0, edge(j0));
+        // below the first union point the density sum is constant, so there
+        // nu grows as sqrt(eps)
+        bins.low_sqrt = g[0] > 0.0 && edge(j0) <= g[0];
+        // record ipos + 1 starts at the first positive union point
+        if (ipos < P) {
+            const double e1 = g[ipos];
+            const int i1 = ipos + 1;
+            const double hi1 = (i1 < n_rec - 1) ? g[i1] : 2.0 * e1 + 1.0;
+            bins.nu_first = speed_of(e1) * (i1 < first_tail ? Slo[i1] : record_density(ch, e1, hi1, e1));
+        } else {
+            bins.nu_first = 0.0;
+        }
     }
 
     emit<float>(ch, g, Slo, Ssl, cv, cs, bucket, cp, first_tail, log2_lo, inv_bw, bins, &out->blob32, &out->lay32);

@@ -128,6 +128,12 @@ class GpuBatchBackend:
     def alone(req: Request) -> bool:
         return bool(getattr(req.cfg, "spawn", 0))
 
+    @staticmethod
+    def group_key(req: Request) -> int:
+        """Requests share a launch only with requests of the same step-kernel
+        instance: the paper's adaptive trial frequencies run in their own."""
+        return int(getattr(req.cfg, "trial_mode", 0) in (3, 4))
+
     def launch_group(self, reqs: Sequence[Request], slot: int):
         if len(reqs) == 1 and self.alone(reqs[0]):
             return _SwarmRun(self.bz, self.ctx, reqs[0], self.streams[slot])
@@ -191,10 +197,11 @@ class Server:
             while queue and free and self.in_use + queue[0].device_bytes() <= self.budget:
                 group, need = [], 0.0
                 alone = getattr(self.backend, "alone", lambda r: False)
+                key = getattr(self.backend, "group_key", lambda r: 0)
                 while (queue and len(group) < self.max_group
                        and self.in_use + need + queue[0].device_bytes() <= self.budget):
-                    if group and alone(queue[0]):
-                        break          # runs on its own
+                    if group and (alone(queue[0]) or key(queue[0]) != key(group[0])):
+                        break          # runs on its own, or in another kernel instance
                     r = queue.popleft()
                     need += r.device_bytes()
                     group.append(r)

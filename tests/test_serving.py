@@ -116,6 +116,22 @@ def test_requests_that_run_alone_are_not_grouped():
     assert len(done) == 6
 
 
+def test_groups_hold_one_kernel_instance():
+    class KeyBackend(FakeGroupBackend):
+        @staticmethod
+        def group_key(req):
+            return req.cfg
+
+    be = KeyBackend(slots=1, polls=3)
+    reqs = _reqs([100] * 6, [0.0] * 6)
+    for r, k in zip(reqs, [0, 0, 1, 1, 0, 1]):
+        r.cfg = k
+    srv = S.Server(be, memory_budget=1e12, clock=Clock(), idle_sleep=0, max_group=8)
+    srv.run(reqs, realtime=False)
+    groups = [e[1] for e in be.log if e[0] == "group"]
+    assert groups == [(0, 1), (2, 3), (4,), (5,)]
+
+
 def test_spawn_requests_reserve_memory_for_the_population_cap():
     class Cfg:
         spawn, pop_cap = 1, 10 ** 6
