@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--avalanche-cap", type=int, default=100_000,
                     help="population cap of the serving run's avalanche requests")
     ap.add_argument("--avalanche-frac", type=float, default=0.05, help="fraction of avalanche requests")
+    ap.add_argument("--no-strategies", action="store_true", help="skip the trial-frequency comparison")
+    ap.add_argument("--strategy-electrons", type=int, default=100_000)
     ap.add_argument("--trial", choices=["window", "lazy"], default="window",
                     help="trial frequency: exact windowed local bound (default) or the constant maximum")
     return ap.parse_args()
@@ -115,6 +117,26 @@ class Clocks:
         os.unlink(self.path)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def profiled_traffic():
+    """DRAM bytes (read + write) of one batched step-kernel launch of this
+    workload from an ncu capture, if the kernel sources are still the ones
+    that capture ran; None otherwise."""
+    import hashlib
+    root = os.path.dirname(os.path.abspath(__file__))
+    try:
+        with open(os.path.join(root, "profiles", "batch_kernel_traffic_argon_sweep.json")) as f:
+            rec = json.load(f)
+        h = hashlib.sha256()
+        for name in rec["sources"]:
+            with open(os.path.join(root, "paper_1901_08140_gb300", "csrc", name), "rb") as f:
+                h.update(f.read())
+    except (OSError, ValueError, KeyError):
+        return None
+    if h.hexdigest() != rec["sources_sha256"]:
+        return None
+    return rec["dram_bytes_read"] + rec["dram_bytes_write"]
 
 
 def sweep_specs(args, rank):
@@ -176,6 +198,40 @@ def _timed(stream, flush, steps, fn, world, dev):
         torch.cuda.synchronize(dev)
         outs.append(h)
     return total, outs
+
+
+def strategy_runs(ctx, mix, specs, electrons):
+    """The argon sweep at `electrons` per point under each trial frequency
+    (Sec. 6): real collisions/s of the step kernel, efficiency (Eq. 28),
+    fails, electrons stopped by an error, and the largest deviation of W
+    from the exact windowed run in combined standard errors."""
+    import math
+    from paper_1901_08140_gb300 import bz
+    modes = [("window", bz.BZ_TRIAL_WINDOW), ("lazy", bz.BZ_TRIAL_LAZY), ("variable", bz.BZ_TRIAL_VARIABLE),
+             ("binned", bz.BZ_TRIAL_BINNED)]
+    out, ref = {}, None
+    for name, mode in modes:
+        cfgs = [bz.config_from_spec(s, n_electrons=electrons, trial_mode=mode, zeta=0.25, grace=5000,
+                                    bins_per_decade=8, max_trials=10 ** 7) for s in specs]
+        b = bz.Batch(ctx, [mix] * len(cfgs), cfgs, use_graph=False)
+        b.launch()
+        b.tallies(check=False)
+        b.launch()
+        ts = b.tallies(check=False)
+        ms, _ = b.timing()
+        b.close()
+        reals = sum(t["n_real"] for t in ts)
+        trials = sum(t["n_real"] + t["n_null"] + t["n_fail"] for t in ts)
+        row = {"real_collisions_per_s": reals / (ms / 1e3), "efficiency": reals / trials if trials else None,
+               "fails": int(sum(t["n_fail"] for t in ts)), "stopped_by_error": int(sum(t["n_incomplete"] for t in ts))}
+        if ref is None:
+            ref = ts
+        else:
+            z = [abs(t["W"] - r["W"]) / math.hypot(t["W_se"], r["W_se"]) for t, r in zip(ts, ref)
+                 if t["W_se"] > 0 and r["W_se"] > 0]
+            row["max_z_W_vs_window"] = max(z) if z else None
+        out[name] = row
+    return {"electrons_per_point": electrons, "zeta": 0.25, "grace": 5000, "bins_per_decade": 8, "modes": out}
 
 
 def serving_runs(ctx, rates, seconds, collisions=100, pool=64, streams=3, avalanche_frac=0.05,
@@ -328,10 +384,13 @@ def run_ours(args):
     peak = torch.cuda.get_device_properties(dev).multi_processor_count * LANES_PER_SM_CLOCK * sm_mhz * 1e6
     achieved = work / (kern_ms / 1e3)
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tops/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": profiled_traffic(),
                 "kernel": "batch_kernel<float,true>",
                 "note": f"algorithmic thread-ops ({ALG_OPS_PER_TRIAL}/step + {ALG_OPS_PER_REAL}/real) over "
                         f"SMs x 128 lanes x median SM clock {sm_mhz:.0f} MHz"}
+    strategies = None
+    if not args.no_strategies and rank == 0:
+        strategies = strategy_runs(ctx, mix, specs, min(args.strategy_electrons, args.electrons))
     serve = None
     if not args.no_serving and rank == 0:
         rates = [float(x) for x in args.serve_rates.split(",") if x]
@@ -363,6 +422,7 @@ def run_ours(args):
         "max_rel_se_W": max(w_err) if w_err else None,
         "trial_frequency": args.trial,
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
+        "trial_strategies": strategies,
         "serving": serve,
         # p99 at the highest arrival rate the GPU kept up with (>= 90 % of the offered work)
         "p99_swarm_latency_ms": (max(((x["rate_req_s"], x["p99_ms"]) for x in serve

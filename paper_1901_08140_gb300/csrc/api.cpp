@@ -544,7 +544,10 @@ bz_status bz_run_swarm(bz_ctx *ctx, const bz_mixture *mix, const bz_swarm_config
         if (e == cudaSuccess && n_tiles > 0)
             e = bz::launch_batch(cfg->precision, ch_smem, adaptive(cfg), ba, a.stage_bytes, grid, block, s->stream);
     } else {
-        // every electron, created ones included, in one persistent launch
+        // every electron, created ones included, in one persistent launch:
+        // a lane per electron of the population cap (at least a block per
+        // SM).  Fewer blocks leave room for concurrent launches but made a
+        // 1e5-cap avalanche 50 % slower and served requests slower overall.
         uint64_t want = (cap + block - 1) / block;
         if (want < (uint64_t)ctx->sm_count) want = ctx->sm_count;
         const int grid = (int)(grid64 < want ? grid64 : want);
