@@ -60,6 +60,7 @@ def parse():
                     help="population cap of the serving run's avalanche requests")
     ap.add_argument("--avalanche-frac", type=float, default=0.05, help="fraction of avalanche requests")
     ap.add_argument("--no-strategies", action="store_true", help="skip the trial-frequency comparison")
+    ap.add_argument("--no-batched-workload", action="store_true", help="skip the 256-swarm batched workload")
     ap.add_argument("--strategy-electrons", type=int, default=100_000)
     ap.add_argument("--trial", choices=["window", "lazy"], default="window",
                     help="trial frequency: exact windowed local bound (default) or the constant maximum")
@@ -198,6 +199,54 @@ def _timed(stream, flush, steps, fn, world, dev):
         torch.cuda.synchronize(dev)
         outs.append(h)
     return total, outs
+
+
+def batched_workload_runs(ctx, stream, flush, world, dev, collisions, warmup, steps):
+    """The batched workload: 256 swarms, electrons log-uniform 1e3-1e6, 2-4
+    of 8 synthetic gases each with Dirichlet fractions, E/N log-uniform
+    0.1-1000 Td, |B| uniform 0-2 T at a random angle, I real collisions,
+    windowed trial frequency.  Plain: one persistent launch per swarm, back
+    to back; batched: all swarms in one persistent launch replayed from a
+    CUDA graph with the autotuner's launch options."""
+    from paper_1901_08140_gb300 import autotune, bz
+    from paper_1901_08140_gb300 import workloads as W
+    specs = W.batched_swarms(count=256, real_collisions=collisions)
+    mixes = [bz.Mixture(ctx, s.gases) for s in specs]
+    cfgs = [bz.config_from_spec(s, trial_mode=bz.BZ_TRIAL_WINDOW) for s in specs]
+
+    def plain_step():
+        return [bz.run_swarm(ctx, m, c, stream) for m, c in zip(mixes, cfgs)]
+
+    for _ in range(warmup):
+        for sw in plain_step():
+            sw.tallies(check=False)
+            sw.close()
+    plain_ms, outs = _timed(stream, flush, steps, plain_step, world, dev)
+    plain_reals = 0
+    for sws in outs:
+        for sw in sws:
+            plain_reals += sw.tallies(check=False)["n_real"]
+            sw.close()
+    choice = autotune.tune(ctx, mixes, cfgs)
+    batch = bz.Batch(ctx, mixes, autotune.apply(cfgs, choice), tile_particles=choice["tile_particles"],
+                     blocks_per_sm=choice["blocks_per_sm"])
+    for _ in range(warmup):
+        batch.launch(stream)
+        batch.tallies(check=False)
+    ms = 0.0
+    reals = 0
+    for _ in range(steps):
+        m1, _ = _timed(stream, flush, 1, lambda: batch.launch(stream), world, dev)
+        ms += m1
+        reals += sum(t["n_real"] for t in batch.tallies(check=False))
+    batch.close()
+    value, plain_value = reals / (ms / 1e3), plain_reals / (plain_ms / 1e3)
+    return {"workload": "256 swarms, 1e3-1e6 electrons (log-uniform, %d in all), 2-4 of 8 synthetic gases, "
+                        "E/N 0.1-1000 Td, |B| 0-2 T at random angles, I = %d" % (sum(c.n_electrons for c in cfgs),
+                                                                                  collisions),
+            "value": value, "unit": UNIT, "ms_per_step": ms / steps, "plain": {"value": plain_value,
+            "ms_per_step": plain_ms / steps}, "batched_over_plain": value / plain_value,
+            "autotuned": {k: choice[k] for k in ("window_c", "tile_particles", "blocks_per_sm", "cached")}}
 
 
 def strategy_runs(ctx, mix, specs, electrons):
@@ -388,6 +437,10 @@ def run_ours(args):
                 "kernel": "batch_kernel<float,true>",
                 "note": f"algorithmic thread-ops ({ALG_OPS_PER_TRIAL}/step + {ALG_OPS_PER_REAL}/real) over "
                         f"SMs x 128 lanes x median SM clock {sm_mhz:.0f} MHz"}
+    batched_workload = None
+    if not args.no_batched_workload and args.only_point < 0:
+        batched_workload = batched_workload_runs(ctx, stream, flush, world, dev, args.collisions,
+                                                 max(1, args.warmup - 2), max(1, min(args.steps, 2)))
     strategies = None
     if not args.no_strategies and rank == 0:
         strategies = strategy_runs(ctx, mix, specs, min(args.strategy_electrons, args.electrons))
@@ -422,6 +475,7 @@ def run_ours(args):
         "max_rel_se_W": max(w_err) if w_err else None,
         "trial_frequency": args.trial,
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
+        "batched_workload": batched_workload,
         "trial_strategies": strategies,
         "serving": serve,
         # p99 at the highest arrival rate the GPU kept up with (>= 90 % of the offered work)
