@@ -45,7 +45,7 @@
 #define OR_PI 3.14159265358979323846
 
 enum { OR_ELASTIC = 0, OR_EXCITATION = 1, OR_ATTACHMENT = 2, OR_IONIZATION = 3 };
-enum { OR_ISOTROPIC = 0, OR_SCREENED_COULOMB = 1 };
+enum { OR_ISOTROPIC = 0, OR_SCREENED_COULOMB = 1, OR_ANG_XI = 2 };
 enum { OR_DEC_FAIL = -2, OR_DEC_NULL = -1 };
 enum { OR_ST_DONE = 0, OR_ST_TIME = 1, OR_ST_STEPS = 2, OR_ST_TRIAL = 3, OR_ST_ERROR = 4, OR_ST_ATTACHED = 5 };
 
@@ -101,6 +101,8 @@ typedef struct {
 typedef struct {
     double M, n;
     int angular;
+    int n_el;          /* xi form: the total elastic cross section table */
+    double *e_el, *s_el;
 } or_gas;
 
 typedef struct {
@@ -117,14 +119,11 @@ typedef struct {
  * power law sigma = A eps^K through the last two points, Eqs. (12)-(14).
  * Where either of the two points is zero the power law is undefined and the
  * last value is continued. */
-double or_sigma(const or_mixture *m, int c, double eps)
+static double table_sigma(int kind, double threshold, const double *e, const double *s, int n, double eps)
 {
-    const or_channel *ch = &m->ch[c];
-    const double *e = ch->e, *s = ch->s;
-    int n = ch->n;
-    if (ch->kind != OR_ELASTIC) {
-        if (eps < ch->threshold) return 0.0;
-        if (eps < e[0]) return s[0] * (eps - ch->threshold) / (e[0] - ch->threshold);
+    if (kind != OR_ELASTIC) {
+        if (eps < threshold) return 0.0;
+        if (eps < e[0]) return s[0] * (eps - threshold) / (e[0] - threshold);
     } else if (eps < e[0]) {
         return s[0];
     }
@@ -143,6 +142,20 @@ double or_sigma(const or_mixture *m, int c, double eps)
         if (e[mid] <= eps) lo = mid; else hi = mid;
     }
     return s[lo] + (s[hi] - s[lo]) * (eps - e[lo]) / (e[hi] - e[lo]);
+}
+
+double or_sigma(const or_mixture *m, int c, double eps)
+{
+    const or_channel *ch = &m->ch[c];
+    return table_sigma(ch->kind, ch->threshold, ch->e, ch->s, ch->n, eps);
+}
+
+/* Total elastic cross section of gas g (xi form), extended like an elastic
+ * table (Sec. 2.2). */
+static double sigma_el_total(const or_mixture *m, int g, double eps)
+{
+    const or_gas *G = &m->gas[g];
+    return table_sigma(OR_ELASTIC, 0.0, G->e_el, G->s_el, G->n_el, eps);
 }
 
 /* Eq. (2): nu(eps) = sqrt(2 eps / m) * sum_k n_k (sigma_k + sum_i sigma_ki).
@@ -385,11 +398,15 @@ static double binned_nu(const or_mixture *m, const or_binned *bt, double eps)
     return or_binned_max(m, bt->B, j);
 }
 
-/* Mixture from flat arrays (tables are copied). Returns 0 or -1 on bad input. */
+void or_mixture_destroy(or_mixture *m);
+
+/* Mixture from flat arrays (tables are copied). Returns 0 or -1 on bad input
+ * (an xi-form gas needs its total elastic cross section table). */
 int or_mixture_create(int n_gas, const double *gas_mass, const double *gas_density, const int *gas_angular,
                       int n_ch, const int *ch_gas, const int *ch_kind, const double *ch_threshold,
                       const int64_t *ch_offset, const int *ch_n, const double *energy, const double *sigma,
-                      double eps_cap, or_mixture **out)
+                      const int64_t *gas_el_offset, const int *gas_el_n, const double *el_energy,
+                      const double *el_sigma, double eps_cap, or_mixture **out)
 {
     *out = NULL;
     if (n_gas <= 0 || n_ch <= 0) return -1;
@@ -404,6 +421,15 @@ int or_mixture_create(int n_gas, const double *gas_mass, const double *gas_densi
         m->gas[g].n = gas_density[g];
         m->gas[g].angular = gas_angular[g];
         m->n_total += gas_density[g];
+        int ne = gas_el_n ? gas_el_n[g] : 0;
+        if (gas_angular[g] == OR_ANG_XI && ne < 1) { or_mixture_destroy(m); return -1; }
+        m->gas[g].n_el = ne;
+        if (ne > 0) {
+            m->gas[g].e_el = (double *)malloc(sizeof(double) * (size_t)ne);
+            m->gas[g].s_el = (double *)malloc(sizeof(double) * (size_t)ne);
+            memcpy(m->gas[g].e_el, el_energy + gas_el_offset[g], sizeof(double) * (size_t)ne);
+            memcpy(m->gas[g].s_el, el_sigma + gas_el_offset[g], sizeof(double) * (size_t)ne);
+        }
     }
     for (int c = 0; c < n_ch; ++c) {
         or_channel *ch = &m->ch[c];
@@ -426,6 +452,7 @@ void or_mixture_destroy(or_mixture *m)
 {
     if (!m) return;
     for (int c = 0; c < m->n_ch; ++c) { free(m->ch[c].e); free(m->ch[c].s); }
+    for (int g = 0; g < m->n_gas; ++g) { free(m->gas[g].e_el); free(m->gas[g].s_el); }
     free(m->ch);
     free(m->gas);
     free(m);
@@ -446,6 +473,56 @@ double or_cos_theta(int angular, double eps_eV, double R)
         return 1.0 - 2.0 * R / (1.0 + 8.0 * e * (1.0 - R));
     }
     return 1.0 - 2.0 * R;
+}
+
+/* Right-hand side of the xi equation (Eq. 7): the ratio sigma_mt/sigma_el
+ * that the xi form (Eq. 6) yields,
+ *   r(xi) = (1 - xi)/(2 xi^2) ((1 + xi) ln((1 + xi)/(1 - xi)) - 2 xi),
+ * 1 at xi = 0 (isotropic), 2 at xi = -1, 0 at xi = 1.  Near 0 the bracket
+ * cancels to O(xi^2); there the same function is summed from its Taylor
+ * series, 1 - 2 sum_k xi^(2k+1) / ((2k+1)(2k+3)), obtained by expanding the
+ * logarithm. */
+double or_xi_ratio(double xi)
+{
+    if (fabs(xi) < 0.05) {
+        double sum = 0.0, p = xi; /* xi^(2k+1) */
+        for (int k = 0; k < 40; ++k) {
+            sum += p / ((2.0 * k + 1.0) * (2.0 * k + 3.0));
+            p *= xi * xi;
+        }
+        return 1.0 - 2.0 * sum;
+    }
+    double L = log((1.0 + xi) / (1.0 - xi));
+    return (1.0 - xi) / (2.0 * xi * xi) * ((1.0 + xi) * L - 2.0 * xi);
+}
+
+/* xi with or_xi_ratio(xi) = r, by bisection on (-1, 1), where the ratio falls
+ * monotonically from 2 to 0; r outside (0, 2) gives the nearer end. */
+double or_xi_solve(double r)
+{
+    double lo = -1.0, hi = 1.0;
+    for (int it = 0; it < 200 && hi - lo > 1e-16; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (or_xi_ratio(mid) > r) lo = mid;
+        else hi = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+/* Eq. (6): cos theta of the xi form for non-polar molecules. */
+double or_cos_theta_xi(double xi, double R) { return 1.0 - 2.0 * R * (1.0 - xi) / (1.0 + xi * (1.0 - 2.0 * R)); }
+
+/* xi of gas g at energy eps (Eq. 7): from the ratio of its momentum-transfer
+ * cross section (the sum of its elastic channels) to its total elastic one;
+ * 0 (isotropic) where the total elastic cross section vanishes. */
+double or_gas_xi(const or_mixture *m, int g, double eps)
+{
+    if (m->gas[g].n_el < 1) return 0.0; /* no total elastic table: isotropic */
+    double smt = 0.0;
+    for (int k = 0; k < m->n_ch; ++k)
+        if (m->ch[k].gas == g && m->ch[k].kind == OR_ELASTIC) smt += or_sigma(m, k, eps);
+    double sel = sigma_el_total(m, g, eps);
+    return sel > 0.0 ? or_xi_solve(smt / sel) : 0.0;
 }
 
 /* Eq. (8) delta_energy_ela: eps_f/eps_i for an elastic collision. */
@@ -616,7 +693,8 @@ static void collide(const or_mixture *m, const or_config *cf, uint64_t id, uint3
 {
     const or_channel *ch = &m->ch[c];
     const or_gas *g = &m->gas[ch->gas];
-    double cos_t = or_cos_theta(g->angular, eps, u[2]);
+    double cos_t = (g->angular == OR_ANG_XI) ? or_cos_theta_xi(or_gas_xi(m, ch->gas, eps), u[2])
+                                             : or_cos_theta(g->angular, eps, u[2]);
     double phi = 2.0 * OR_PI * u[3];
     double ratio;
     *ion = 0;

@@ -64,7 +64,15 @@ def lib():
         L.or_uniform.argtypes = [C.c_uint32]
         L.or_mixture_create.restype = C.c_int
         L.or_mixture_create.argtypes = [C.c_int, _dp, _dp, _i32p, C.c_int, _i32p, _i32p, _dp, _i64p, _i32p,
-                                        _dp, _dp, C.c_double, C.POINTER(C.c_void_p)]
+                                        _dp, _dp, _i64p, _i32p, _dp, _dp, C.c_double, C.POINTER(C.c_void_p)]
+        L.or_xi_ratio.restype = C.c_double
+        L.or_xi_ratio.argtypes = [C.c_double]
+        L.or_xi_solve.restype = C.c_double
+        L.or_xi_solve.argtypes = [C.c_double]
+        L.or_cos_theta_xi.restype = C.c_double
+        L.or_cos_theta_xi.argtypes = [C.c_double, C.c_double]
+        L.or_gas_xi.restype = C.c_double
+        L.or_gas_xi.argtypes = [C.c_void_p, C.c_int, C.c_double]
         L.or_mixture_destroy.argtypes = [C.c_void_p]
         for f in ("or_mixture_nu_max", "or_mixture_eps_at_max", "or_mixture_n_total"):
             getattr(L, f).restype = C.c_double
@@ -136,7 +144,8 @@ class Mixture:
                                      _p(f["gas_angular"], _i32p), len(f["ch_gas"]), _p(f["ch_gas"], _i32p),
                                      _p(f["ch_kind"], _i32p), _p(f["ch_threshold"], _dp), _p(f["ch_offset"], _i64p),
                                      _p(f["ch_n"], _i32p), _p(f["energy"], _dp), _p(f["sigma"], _dp),
-                                     float(eps_cap), C.byref(h))
+                                     _p(f["gas_el_offset"], _i64p), _p(f["gas_el_n"], _i32p),
+                                     _p(f["el_energy"], _dp), _p(f["el_sigma"], _dp), float(eps_cap), C.byref(h))
         if rc != 0:
             raise ValueError("oracle rejected the mixture")
         self.h = h
@@ -189,6 +198,10 @@ class Mixture:
     def select_channel(self, eps: float, r: float) -> int:
         return lib().or_select_channel(self.h, float(eps), float(r))
 
+    def gas_xi(self, g: int, eps: float) -> float:
+        """xi of gas g at eps (Eq. 7) from sigma_mt / sigma_el."""
+        return lib().or_gas_xi(self.h, int(g), float(eps))
+
     def range_max(self, a: float, b: float) -> float:
         """Maximum of nu over [a, b] eV."""
         return lib().or_range_max(self.h, float(a), float(b))
@@ -200,6 +213,19 @@ class Mixture:
 
 def cos_theta(angular: int, eps_eV: float, R: float) -> float:
     return lib().or_cos_theta(int(angular), float(eps_eV), float(R))
+
+
+def xi_ratio(xi: float) -> float:
+    """sigma_mt / sigma_el produced by the xi form (right side of Eq. 7)."""
+    return lib().or_xi_ratio(float(xi))
+
+
+def xi_solve(r: float) -> float:
+    return lib().or_xi_solve(float(r))
+
+
+def cos_theta_xi(xi: float, R: float) -> float:
+    return lib().or_cos_theta_xi(float(xi), float(R))
 
 
 def ratio_elastic(m: float, M: float, cos_t: float) -> float:

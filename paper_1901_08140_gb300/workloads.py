@@ -20,7 +20,7 @@ from __future__ import annotations
 
 import dataclasses
 import math
-from typing import List, Sequence
+from typing import List, Optional, Sequence, Tuple
 
 import numpy as np
 
@@ -37,7 +37,7 @@ N_STP_293 = 101325.0 / (BOLTZMANN * 293.15)
 SEED = 1901081400
 
 ELASTIC, EXCITATION, ATTACHMENT, IONIZATION = 0, 1, 2, 3
-ISOTROPIC, SCREENED_COULOMB = 0, 1
+ISOTROPIC, SCREENED_COULOMB, XI_FORM = 0, 1, 2
 
 
 def splitmix64(x: int) -> int:
@@ -69,6 +69,9 @@ class Gas:
     number_density_m3: float
     angular: int
     channels: List[Channel]
+    # XI_FORM gases: the total elastic cross section (energy [eV], sigma [m^2]);
+    # the elastic channel's table is the momentum-transfer cross section
+    sigma_el: Optional[Tuple[np.ndarray, np.ndarray]] = None
 
     def with_density(self, n: float) -> "Gas":
         return dataclasses.replace(self, number_density_m3=float(n))
@@ -153,9 +156,12 @@ def _on_grid(grid: np.ndarray, th: float, lo: float = 0.0, hi: float = np.inf) -
     return np.concatenate([[th], pts])
 
 
-def co2_like(n: float = N_STP_293, points: int = 500) -> Gas:
+def co2_like(n: float = N_STP_293, points: int = 500, xi_form: bool = False) -> Gas:
     """20 channels; every table lives on the gas's 500-point log grid
-    (1e-3 - 100 eV), inelastic ones from their threshold upwards."""
+    (1e-3 - 100 eV), inelastic ones from their threshold upwards.  With
+    xi_form the gas scatters by the xi form of a non-polar molecule, with a
+    total elastic cross section sigma_el = sigma_mt (1 + eps / 5 eV), so
+    that scattering turns forward as the energy grows."""
     grid = np.geomspace(1e-3, 100.0, points)
     s_el = 1e-20 + 9e-20 / (1.0 + (grid / 0.5) ** 0.8)
     chans = [Channel(ELASTIC, 0.0, grid, s_el)]
@@ -179,6 +185,9 @@ def co2_like(n: float = N_STP_293, points: int = 500) -> Gas:
     e = _on_grid(grid, ip)
     s = 2e-20 * (e - ip) / (100.0 - ip)
     chans.append(Channel(IONIZATION, ip, e, s))
+    if xi_form:
+        return Gas("co2-like-xi", 44.01 * ATOMIC_MASS_UNIT, n, XI_FORM, chans,
+                   sigma_el=(grid.copy(), s_el * (1.0 + grid / 5.0)))
     return Gas("co2-like", 44.01 * ATOMIC_MASS_UNIT, n, ISOTROPIC, chans)
 
 
@@ -306,13 +315,26 @@ def flatten_gases(gases: Sequence[Gas]):
     g_mass, g_dens, g_ang, g_first, g_nch = [], [], [], [], []
     c_gas, c_kind, c_th, c_off, c_n = [], [], [], [], []
     e_all, s_all = [], []
+    el_off, el_n, el_e, el_s = [], [], [], []
     off = 0
+    el_at = 0
     for gi, g in enumerate(gases):
         g_mass.append(g.mass_kg)
         g_dens.append(g.number_density_m3)
         g_ang.append(g.angular)
         g_first.append(len(c_gas))
         g_nch.append(len(g.channels))
+        if g.sigma_el is not None:
+            ee = np.ascontiguousarray(g.sigma_el[0], dtype=np.float64)
+            ss = np.ascontiguousarray(g.sigma_el[1], dtype=np.float64)
+            el_off.append(el_at)
+            el_n.append(len(ee))
+            el_e.append(ee)
+            el_s.append(ss)
+            el_at += len(ee)
+        else:
+            el_off.append(el_at)
+            el_n.append(0)
         for ch in g.channels:
             e = np.ascontiguousarray(ch.energy_eV, dtype=np.float64)
             s = np.ascontiguousarray(ch.sigma_m2, dtype=np.float64)
@@ -333,4 +355,6 @@ def flatten_gases(gases: Sequence[Gas]):
         ch_n=np.array(c_n, dtype=np.int32),
         energy=np.concatenate(e_all) if e_all else np.zeros(0),
         sigma=np.concatenate(s_all) if s_all else np.zeros(0),
+        gas_el_offset=np.array(el_off, dtype=np.int64), gas_el_n=np.array(el_n, dtype=np.int32),
+        el_energy=np.concatenate(el_e) if el_e else np.zeros(1), el_sigma=np.concatenate(el_s) if el_s else np.zeros(1),
     )

@@ -681,3 +681,83 @@ def test_invalid_strategies_are_rejected():
                 dict(strategy=O.TF_VARIABLE, grace=0), dict(strategy=7)):
         with pytest.raises(ValueError):
             O.run_swarm(m, **kw, **bad)
+
+
+# --------------------------------------------------------------------------
+# xi form of the scattering angle for non-polar molecules (Eqs. 6-7)
+# --------------------------------------------------------------------------
+def test_xi_form_mean_deflection_is_the_cross_section_ratio():
+    """The xi form is built so that the mean of 1 - cos(theta) under Eq. 6
+    equals sigma_mt / sigma_el, the right side of Eq. 7 (substituting
+    u = 1 + xi - 2 xi R makes the integral elementary).  Quadrature of the
+    sampler over R therefore pins both equations against each other."""
+    from scipy import integrate
+    for xi in (-0.95, -0.6, -0.2, -0.01, 0.003, 0.04, 0.06, 0.3, 0.7, 0.95, 0.999):
+        mean, err = integrate.quad(lambda R: 1.0 - O.cos_theta_xi(xi, R), 0.0, 1.0, epsabs=0.0, epsrel=1e-12,
+                                   limit=200)
+        assert O.xi_ratio(xi) == pytest.approx(mean, rel=1e-10, abs=0.0), xi
+
+
+def test_xi_form_limits():
+    # isotropic at xi = 0; the ratio falls monotonically from 2 (backward) to 0 (forward)
+    for R in (0.0, 0.1, 0.5, 0.9):
+        assert O.cos_theta_xi(0.0, R) == 1.0 - 2.0 * R
+    assert O.xi_ratio(0.0) == 1.0
+    xs = np.linspace(-0.999, 0.999, 2001)
+    r = np.array([O.xi_ratio(x) for x in xs])
+    assert np.all(np.diff(r) < 0) and r[0] < 2.0 and r[-1] > 0.0
+    assert O.xi_ratio(-1 + 1e-12) == pytest.approx(2.0, abs=1e-9)
+    assert O.xi_ratio(1 - 1e-12) == pytest.approx(0.0, abs=1e-9)
+    # the series (|xi| < 0.05) and the closed form meet smoothly
+    assert O.xi_ratio(0.0499999) == pytest.approx(O.xi_ratio(0.0500001), abs=1e-6)
+    # every cos(theta) is a cosine
+    for xi in (-0.99, -0.5, 0.5, 0.99):
+        c = [O.cos_theta_xi(xi, R) for R in np.linspace(0.0, 1.0, 101)]
+        assert min(c) >= -1.0 - 1e-12 and max(c) <= 1.0 + 1e-12
+
+
+def test_xi_solve_and_gas_xi():
+    for r in (1e-4, 0.05, 0.4, 0.999, 1.0, 1.3, 1.9, 1.9999):
+        xi = O.xi_solve(r)
+        assert O.xi_ratio(xi) == pytest.approx(r, rel=1e-12, abs=1e-14)
+    assert abs(O.xi_solve(1.0)) < 1e-15
+    # the xi-form CO2-like gas: sigma_el = sigma_mt (1 + eps / 5 eV), so r = 1 / (1 + eps / 5)
+    gases = [W.argon_like(0.9 * W.N_STP_293), W.co2_like(0.1 * W.N_STP_293, xi_form=True)]
+    m = O.Mixture(gases)
+    # the table points of both cross sections coincide, so the ratio is exact at them
+    grid = gases[1].sigma_el[0]
+    for eps in (grid[0], grid[137], grid[350], grid[-1]):
+        assert O.xi_ratio(m.gas_xi(1, eps)) == pytest.approx(1.0 / (1.0 + eps / 5.0), rel=1e-9, abs=0.0)
+    # below the tables both extend with their first values (Sec. 2.2)
+    assert m.gas_xi(1, 1e-5) == m.gas_xi(1, grid[0])
+    assert m.gas_xi(0, 3.0) == 0.0            # argon has no total elastic table: isotropic
+
+
+def test_xi_gas_with_equal_cross_sections_scatters_isotropically():
+    """sigma_el = sigma_mt gives xi = 0, the isotropic law: a swarm in that gas
+    follows the isotropic one collision for collision."""
+    base = W.co2_like()
+    grid, s_mt = base.channels[0].energy_eV, base.channels[0].sigma_m2
+    xi_gas = W.Gas("co2-xi-iso", base.mass_kg, base.number_density_m3, W.XI_FORM, base.channels,
+                   sigma_el=(grid, s_mt))
+    kw = dict(e_over_n_Td=40.0, real_collisions=200, n=300, seed=9, threads=O.cpu_count())
+    a = O.run_swarm(O.Mixture([base]), **kw)
+    b = O.run_swarm(O.Mixture([xi_gas]), **kw)
+    same = np.ones(300, bool)
+    for k in ("n_real", "n_null", "n_fail", "n_att", "steps"):
+        same &= a[k] == b[k]
+    assert same.mean() > 0.99
+    assert np.allclose(a["z"][same], b["z"][same], rtol=1e-9, atol=1e-18)
+
+
+def test_xi_form_forward_scattering_raises_the_drift_velocity():
+    """Where sigma_el > sigma_mt the xi form scatters forward (xi > 0): with
+    the momentum-transfer cross section fixed, forward scattering keeps more
+    of the momentum gained from the field, so electrons drift at least as
+    fast as with isotropic scattering (a sanity check, not a closed form)."""
+    kw = dict(e_over_n_Td=60.0, real_collisions=300, n=3000, seed=12, threads=O.cpu_count())
+    iso = O.run_swarm(O.Mixture([W.co2_like()]), **kw)
+    fwd = O.run_swarm(O.Mixture([W.co2_like(xi_form=True)]), **kw)
+    ti = T.swarm_tallies(iso, 60.0, W.N_STP_293)
+    tf = T.swarm_tallies(fwd, 60.0, W.N_STP_293)
+    assert tf["W"] > ti["W"] - 3 * math.hypot(ti["W_se"], tf["W_se"])
