@@ -34,7 +34,7 @@
 extern "C" {
 #endif
 
-#define BZ_ABI_VERSION 2
+#define BZ_ABI_VERSION 3
 
 typedef enum {
     BZ_OK = 0,
@@ -49,7 +49,11 @@ typedef enum {
 } bz_status;
 
 typedef enum { BZ_ELASTIC = 0, BZ_EXCITATION = 1, BZ_ATTACHMENT = 2, BZ_IONIZATION = 3 } bz_kind;
-typedef enum { BZ_ANG_ISOTROPIC = 0, BZ_ANG_SCREENED_COULOMB = 1 } bz_angular;
+/* Scattering angle (Sec. 2): isotropic; screened Coulomb (Eq. 5, atoms);
+ * XI, the xi form of non-polar molecules (Eq. 6), whose xi solves Eq. 7
+ * for the ratio of the gas's momentum-transfer cross section (its one
+ * elastic channel) to its total elastic cross section (bz_gas.sigma_el_m2). */
+typedef enum { BZ_ANG_ISOTROPIC = 0, BZ_ANG_SCREENED_COULOMB = 1, BZ_ANG_XI = 2 } bz_angular;
 /* Trial frequency nu' of the null-collision flights (Sec. 6):
  *  LAZY   -- one constant nu' = exact max of nu over [0, eps_cap] (Sec. 6.2);
  *  FIXED  -- the caller's constant nu_trial; exceeding it is an error (Sec. 6.1);
@@ -126,8 +130,15 @@ typedef struct {
     double mass_kg;           /* > 0 */
     double number_density_m3; /* > 0 */
     int32_t angular;          /* bz_angular of every channel of this gas */
-    int32_t n_channels;       /* >= 1 */
+    int32_t n_channels;       /* >= 1; BZ_ANG_XI: exactly one BZ_ELASTIC channel */
     const bz_channel *channels;
+    /* BZ_ANG_XI only (ignored otherwise): the total elastic cross section,
+     * host, el_n_points >= 1, energies strictly increasing, extended like
+     * an elastic table (Sec. 2.2) */
+    int32_t el_n_points;
+    int32_t reserved;
+    const double *el_energy_eV;
+    const double *sigma_el_m2;
 } bz_gas;
 
 typedef struct {
@@ -161,6 +172,8 @@ typedef struct {
     int32_t channels_in_smem;
     int32_t first_tail_record;
     int32_t table_bytes;      /* device bytes of the compiled tables (FP32 + FP64 copies) */
+    int32_t n_xi_gases;       /* gases with the xi form of the angle */
+    int32_t reserved;
 } bz_mixture_info;
 
 bz_status bz_mixture_get_info(const bz_mixture *mix, bz_mixture_info *out);

@@ -43,7 +43,9 @@ class bz_channel(C.Structure):
 
 class bz_gas(C.Structure):
     _fields_ = [("mass_kg", C.c_double), ("number_density_m3", C.c_double), ("angular", C.c_int32),
-                ("n_channels", C.c_int32), ("channels", C.POINTER(bz_channel))]
+                ("n_channels", C.c_int32), ("channels", C.POINTER(bz_channel)), ("el_n_points", C.c_int32),
+                ("reserved", C.c_int32), ("el_energy_eV", C.POINTER(C.c_double)),
+                ("sigma_el_m2", C.POINTER(C.c_double))]
 
 
 class bz_mixture_opts(C.Structure):
@@ -56,7 +58,7 @@ class bz_mixture_info(C.Structure):
                 ("eps_cap", C.c_double), ("n_total", C.c_double), ("n_gases", C.c_int32),
                 ("n_channels", C.c_int32), ("n_records", C.c_int32), ("n_buckets", C.c_int32),
                 ("smem_bytes", C.c_int32), ("channels_in_smem", C.c_int32), ("first_tail_record", C.c_int32),
-                ("table_bytes", C.c_int32)]
+                ("table_bytes", C.c_int32), ("n_xi_gases", C.c_int32), ("reserved", C.c_int32)]
 
 
 class bz_swarm_config(C.Structure):
@@ -287,6 +289,14 @@ def _gas_structs(gases):
                                 e.ctypes.data_as(C.POINTER(C.c_double)), s.ctypes.data_as(C.POINTER(C.c_double)))
         keep.append(chs)
         gs[i] = bz_gas(float(g.mass_kg), float(g.number_density_m3), int(g.angular), len(g.channels), chs)
+        el = getattr(g, "sigma_el", None)
+        if el is not None:
+            ee = np.ascontiguousarray(el[0], dtype=np.float64)
+            es = np.ascontiguousarray(el[1], dtype=np.float64)
+            keep += [ee, es]
+            gs[i].el_n_points = len(ee)
+            gs[i].el_energy_eV = ee.ctypes.data_as(C.POINTER(C.c_double))
+            gs[i].sigma_el_m2 = es.ctypes.data_as(C.POINTER(C.c_double))
     return gs, keep
 
 

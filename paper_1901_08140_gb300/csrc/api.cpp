@@ -62,7 +62,7 @@ struct bz_batch {
     bz_ctx *ctx;
     int32_t n;
     int precision;
-    bool ch_smem, use_graph, adapt;
+    bool ch_smem, use_graph, ext;
     size_t smem;
     int grid, n_tiles, max_tblocks;
     std::vector<uint64_t> n_el, id_offset;
@@ -210,6 +210,13 @@ bz::Fields make_fields(const bz_swarm_config &cfg, double n_total)
 bool adaptive(const bz_swarm_config *cfg)
 {
     return cfg->trial_mode == BZ_TRIAL_VARIABLE || cfg->trial_mode == BZ_TRIAL_BINNED;
+}
+
+// Swarms that need the feature instance of the step kernel: the paper's
+// adaptive trial frequencies, or a mixture with an xi-form gas.
+bool ext_instance(const bz_mixture *mix, const bz_swarm_config *cfg)
+{
+    return adaptive(cfg) || mix->cm.info.n_xi_gases > 0;
 }
 
 bz_status validate_config(const bz_swarm_config *cfg)
@@ -441,7 +448,7 @@ bz_status bz_run_swarm(bz_ctx *ctx, const bz_mixture *mix, const bz_swarm_config
     if (cap > 0xFFFFFFFFull) return fail(BZ_EINVAL, "a swarm holds at most 2^32-1 electrons");
     const int block = 256;
     int bps = spawn ? bz::spawn_occupancy(cfg->precision, ch_smem, block, a.stage_bytes)
-                    : bz::batch_occupancy(cfg->precision, ch_smem, adaptive(cfg), block, a.stage_bytes);
+                    : bz::batch_occupancy(cfg->precision, ch_smem, ext_instance(mix, cfg), block, a.stage_bytes);
     if (bps < 0) return cuda_fail((cudaError_t)(-bps), "occupancy of the step kernel");
     if (bps < 1) return fail(BZ_ECUDA, "step kernel cannot be resident with these tables");
     if (cfg->blocks_per_sm > 0 && cfg->blocks_per_sm < bps) bps = cfg->blocks_per_sm;
@@ -542,7 +549,8 @@ bz_status bz_run_swarm(bz_ctx *ctx, const bz_mixture *mix, const bz_swarm_config
         ba.slot_lo = 0;
         const int grid = (int)(grid64 < n_tiles ? grid64 : n_tiles);
         if (e == cudaSuccess && n_tiles > 0)
-            e = bz::launch_batch(cfg->precision, ch_smem, adaptive(cfg), ba, a.stage_bytes, grid, block, s->stream);
+            e = bz::launch_batch(cfg->precision, ch_smem, ext_instance(mix, cfg), ba, a.stage_bytes, grid, block,
+                                 s->stream);
     } else {
         // every electron, created ones included, in one persistent launch:
         // a lane per electron of the population cap (at least a block per
@@ -706,7 +714,7 @@ static cudaError_t batch_part(bz_batch *b, int part, cudaStream_t s)
         a.tiles = b->tiles;
         a.n_tiles = b->n_tiles;
         a.tile_counter = b->tile_counter;
-        if (e == cudaSuccess) e = bz::launch_batch(b->precision, b->ch_smem, b->adapt, a, b->smem, b->grid, 256, s);
+        if (e == cudaSuccess) e = bz::launch_batch(b->precision, b->ch_smem, b->ext, a, b->smem, b->grid, 256, s);
         return e;
     }
     e = bz::launch_tallies_multi(b->targs, b->n, b->max_tblocks, s);
@@ -736,11 +744,12 @@ bz_status bz_create_batch(bz_ctx *ctx, int32_t n, const bz_mixture *const *mixtu
     for (int i = 0; i < n; ++i) {
         bz_status st = validate_config(&cfgs[i]);
         if (st != BZ_OK) return st;
-        if (!mixtures[i]) return fail(BZ_EINVAL, "null mixture");
+        if (!mixtures[i] || !mixtures[0]) return fail(BZ_EINVAL, "null mixture");
         if (cfgs[i].precision != precision) return fail(BZ_EINVAL, "all swarms of a batch need the same precision");
         if (cfgs[i].spawn) return fail(BZ_EINVAL, "spawn-mode swarms run through bz_run_swarm");
-        if (adaptive(&cfgs[i]) != adaptive(&cfgs[0]))
-            return fail(BZ_EINVAL, "a batch holds either VARIABLE / BINNED swarms or swarms of the other modes");
+        if (ext_instance(mixtures[i], &cfgs[i]) != ext_instance(mixtures[0], &cfgs[0]))
+            return fail(BZ_EINVAL, "a batch holds either swarms with VARIABLE / BINNED trial frequencies or xi-form "
+                                   "gases, or swarms with neither");
         if (cfgs[i].n_electrons > 0xFFFFFFFFull) return fail(BZ_EINVAL, "a batched swarm holds at most 2^32-1 electrons");
     }
     cudaError_t e = cudaSetDevice(ctx->device);
@@ -750,7 +759,7 @@ bz_status bz_create_batch(bz_ctx *ctx, int32_t n, const bz_mixture *const *mixtu
     b->ctx = ctx;
     b->n = n;
     b->precision = precision;
-    b->adapt = adaptive(&cfgs[0]);
+    b->ext = ext_instance(mixtures[0], &cfgs[0]);
     b->use_graph = opts ? opts->use_graph != 0 : true;
     // tables of every mixture must fit; channel tables go to shared memory only if all fit
     b->ch_smem = true;
@@ -769,7 +778,7 @@ bz_status bz_create_batch(bz_ctx *ctx, int32_t n, const bz_mixture *const *mixtu
         desc[i].stage_bytes = b->ch_smem ? desc[i].lay.stage_all : desc[i].lay.stage_tables;
         b->smem = std::max(b->smem, (size_t)desc[i].stage_bytes);
     }
-    int bps = bz::batch_occupancy(precision, b->ch_smem, b->adapt, 256, b->smem);
+    int bps = bz::batch_occupancy(precision, b->ch_smem, b->ext, 256, b->smem);
     if (bps < 1) {
         delete b;
         return fail(BZ_ECUDA, "batch kernel cannot be resident with these tables");
@@ -876,7 +885,7 @@ bz_status bz_create_batch(bz_ctx *ctx, int32_t n, const bz_mixture *const *mixtu
     }
     if (b->use_graph) {
         // make sure the kernels' shared-memory limits are set before capture
-        bz::batch_occupancy(precision, b->ch_smem, b->adapt, 256, b->smem);
+        bz::batch_occupancy(precision, b->ch_smem, b->ext, 256, b->smem);
         for (int part = 0; part < 2 && e == cudaSuccess; ++part) {
             e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
             cudaError_t e1 = (e == cudaSuccess) ? batch_part(b, part, b->cap) : e;

@@ -31,7 +31,8 @@ struct alignas(4 * sizeof(R)) Rec {
     R e_lo, e_hi, S_lo, slope;
 };
 
-// Per-channel constants.  bits: kind | angular << 4 | tail_zero << 8.
+// Per-channel constants.  bits: kind | angular << 4 | tail_zero << 8, and
+// for xi-form gases gas << 12 | (the gas's elastic channel) << 16.
 // Tail: n sigma(eps) = exp(tail_logc + tail_K ln eps) for eps >= e_last.
 template <typename R>
 struct alignas(16) ChParam {
@@ -77,6 +78,10 @@ struct Layout {
     // memory) and each gas's channel range, for a two-level channel search
     uint32_t off_gval;
     int32_t n_gases;
+    // xi-form gases (Eqs. 6-7): the total elastic cross section per record
+    // and gas ({val, slope}, n_rec x n_gases) and per gas its tail constants
+    // (ChParam: e_last, tail_logc, tail_K, bits & 0x100 = no tail), global memory
+    uint32_t off_elval, off_elp;
     int16_t gas_first[kMaxGases], gas_count[kMaxGases];
 };
 

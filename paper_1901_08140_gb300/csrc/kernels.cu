@@ -274,6 +274,78 @@ __device__ __forceinline__ int select_channel(const Tab<R> &T, int ri, R e_lo, R
     return last;  // rounding left the sum a hair short of S: last channel that is open
 }
 
+// Right side of Eq. 7, r(xi) = (1 - xi)/(2 xi^2) ((1 + xi) ln((1 + xi)/(1 - xi)) - 2 xi),
+// and its derivative; for |xi| < 0.2, where the bracket cancels, from the
+// series 1 - 2 sum_k xi^(2k+1) / ((2k+1)(2k+3)) (the logarithm expanded).
+template <typename R>
+__device__ __forceinline__ void xi_ratio(R xi, R &f, R &df)
+{
+    if (fabs(xi) < (R)0.2) {
+        const R x2 = xi * xi;
+        R p = 1, s = 0, ds = 0;
+#pragma unroll
+        for (int k = 0; k < 14; ++k) {
+            ds += p / (R)(2 * k + 3);
+            s += p * xi / (R)((2 * k + 1) * (2 * k + 3));
+            p *= x2;
+        }
+        f = (R)1 - (R)2 * s;
+        df = (R)-2 * ds;
+    } else {
+        const R L = log_(((R)1 + xi) / ((R)1 - xi));
+        const R A = ((R)1 + xi) * L - (R)2 * xi;
+        f = ((R)1 - xi) * A / ((R)2 * xi * xi);
+        df = ((R)2 - L) / xi - ((R)1 - xi) * A / (xi * xi * xi);
+    }
+}
+
+// xi with r(xi) = r: Newton steps kept inside a bisection bracket of
+// (-1, 1), on which r falls from 2 to 0.
+template <typename R>
+__device__ __forceinline__ R xi_solve(R r)
+{
+    const R lim = (sizeof(R) == 4) ? (R)0.9999 : (R)0.99999999;
+    R lo = -lim, hi = lim;
+    R x = min_(max_((R)1.5 * ((R)1 - r), (R)-0.9), (R)0.9);
+    const R tol = (sizeof(R) == 4) ? (R)1e-6 : (R)1e-14;
+    for (int it = 0; it < 80; ++it) {
+        R f, df;
+        xi_ratio(x, f, df);
+        const R d = f - r;
+        if (d > (R)0) lo = x;  // r falls with xi: the root lies above
+        else hi = x;
+        R xn = x - d / df;
+        if (!(xn > lo && xn < hi)) xn = (R)0.5 * (lo + hi);
+        const bool done = fabs(xn - x) <= tol;
+        x = xn;
+        if (done || hi - lo <= tol) break;
+    }
+    return x;
+}
+
+// Eq. 6 for a channel of an xi-form gas: xi from the ratio of the gas's
+// momentum-transfer cross section (its elastic channel) to its total
+// elastic one at eps, both read on record ri (or from their tails).
+template <typename R, bool CH_SMEM>
+__device__ __noinline__ R xi_cos_theta(const Tab<R> &T, const RunArgs &P, int bits, int ri, R e_lo, R eps, R u)
+{
+    const int g = (bits >> 12) & 15, cel = (bits >> 16) & 0xFFFF;
+    const R de = eps - e_lo;
+    const ChVal<R> cv = load_chval(T.chval + (size_t)ri * T.n_ch + cel, CH_SMEM);
+    R smt = cv.val + cv.slope * de;
+    const ChParam<R> pm = T.chp[cel];
+    if (e_lo >= pm.e_last && !(pm.bits & 0x100)) smt += exp_(pm.tail_logc + pm.tail_K * log_(eps));
+    const ChVal<R> *elv = (const ChVal<R> *)(P.blob + P.lay.off_elval);
+    const ChParam<R> *elp = (const ChParam<R> *)(P.blob + P.lay.off_elp);
+    const ChVal<R> ev = load_chval(elv + (size_t)ri * T.n_gases + g, false);
+    R sel = ev.val + ev.slope * de;
+    const R e_last = __ldg(&elp[g].e_last);
+    if (e_lo >= e_last && !(__ldg(&elp[g].bits) & 0x100))
+        sel += exp_(__ldg(&elp[g].tail_logc) + __ldg(&elp[g].tail_K) * log_(eps));
+    const R xi = (sel > (R)0) ? xi_solve(smt / sel) : (R)0;
+    return (R)1 - (R)2 * u * ((R)1 - xi) / ((R)1 + xi * ((R)1 - (R)2 * u));
+}
+
 template <typename R>
 struct Fld {
     R a, b0, b1, b2, w, inv_w, vD0, vD1, vD2, vDn, a_par, Ke;
@@ -697,7 +769,7 @@ __device__ __noinline__ void spawn_secondary(const RunArgs &P, const Fld<R> &F, 
 // every lane, and every lane that needs a new trial-frequency window (window
 // end, real collision, fail) computes it at one common point after the
 // branches, so divergent lanes do not repeat that code.
-template <typename R, bool CH_SMEM, bool ADAPT = false>
+template <typename R, bool CH_SMEM, bool EXT = false>
 __device__ __forceinline__ int trial(const Tab<R> &T, const Fld<R> &F, const RunArgs &P, PState<R> &s, R &eps_i,
                                      R &eps_f)
 {
@@ -762,7 +834,7 @@ __device__ __forceinline__ int trial(const Tab<R> &T, const Fld<R> &F, const Run
             }
             ++s.n_fail;
             bool error = P.fixed;  // FixedTrialFrequency (Sec. 6.1): an error
-            if constexpr (ADAPT) {
+            if constexpr (EXT) {
                 // BinnedTrialFrequency (Sec. 6.3): one retry, then an error
                 if (P.tf == TF_BINNED) {
                     error = s.retried;
@@ -786,8 +858,8 @@ __device__ __forceinline__ int trial(const Tab<R> &T, const Fld<R> &F, const Run
             ++s.n_null;
             s.T = Tn;
             dec = DEC_NULL;
-            if constexpr (ADAPT) {
-                if (--s.grace == 0) {  // end of the grace period: query nu' here
+            if constexpr (EXT) {
+                if (P.tf != TF_NONE && --s.grace == 0) {  // end of the grace period: query nu' here
                     s.nu_p = adaptive_nu(T, P, eps, nu);
                     s.inv_nu = (R)1 / s.nu_p;
                     s.grace = P.tf_grace;
@@ -810,8 +882,11 @@ __device__ __forceinline__ int trial(const Tab<R> &T, const Fld<R> &F, const Run
             const ChParam<R> p = T.chp[c];
             const int kind = p.bits & 15;
             R ct;
-            if ((p.bits >> 4) & 15) {  // Eq. (5), eps in Hartree
+            const int ang = (p.bits >> 4) & 15;
+            if (ang == BZ_ANG_SCREENED_COULOMB) {  // Eq. (5), eps in Hartree
                 ct = (R)1 - (R)2 * u2 / ((R)1 + (R)8 * (eps * (R)(1.0 / kHartreeEv)) * ((R)1 - u2));
+            } else if (EXT && ang == BZ_ANG_XI) {  // Eqs. (6)-(7)
+                ct = xi_cos_theta<R, CH_SMEM>(T, P, p.bits, ri, elo, eps, u2);
             } else {
                 ct = (R)1 - (R)2 * u2;
             }
@@ -901,9 +976,9 @@ __device__ __forceinline__ int trial(const Tab<R> &T, const Fld<R> &F, const Run
             w1 = s.vr1;
             w2 = s.vr2;
             dec = c;
-            if constexpr (ADAPT) {
+            if constexpr (EXT) {
                 s.retried = false;
-                if (--s.grace == 0) {  // query at the energy the electron leaves with
+                if (P.tf != TF_NONE && --s.grace == 0) {  // query at the energy the electron leaves with
                     s.nu_p = adaptive_nu(T, P, eps_f, P.tf == TF_VARIABLE ? nsp * density_at(T, eps_f) : (R)0);
                     s.inv_nu = (R)1 / s.nu_p;
                     s.grace = P.tf_grace;
@@ -915,7 +990,7 @@ __device__ __forceinline__ int trial(const Tab<R> &T, const Fld<R> &F, const Run
         new_window(T, F, P, s, w0, w1, w2, wt0);
     }
     if (dec == DEC_FAIL) {
-        if constexpr (ADAPT) {
+        if (EXT && P.tf != TF_NONE) {
             // VARIABLE: (1 + zeta) nu at the fail; BINNED: the larger of the two bins' maxima
             const R q = adaptive_nu(T, P, eps, nu_fail);
             s.nu_p = (P.tf == TF_VARIABLE) ? q : max_(s.nu_p, q);
@@ -1055,7 +1130,7 @@ __device__ bool restage_tables(const uint8_t *src, uint8_t *dst, uint32_t bytes,
 // one it holds, runs the tile's electrons with per-lane refill (a lane that
 // finishes an electron takes the next one of the tile), and synchronises
 // before the next tile.
-template <typename R, bool CH_SMEM, bool ADAPT>
+template <typename R, bool CH_SMEM, bool EXT>
 __global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? BZ_SWARM_MIN_BLOCKS : 1)
     batch_kernel(const __grid_constant__ BatchArgs B)
 {
@@ -1120,7 +1195,9 @@ __global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? BZ_SWARM_MIN_BLOCKS :
                     if (idx < tile.z) {
                         slot = (uint64_t)tile.y + idx;
                         init_particle<R>(T, P, F, s, P.id_offset + slot);
-                        if constexpr (ADAPT) adaptive_start(T, F, P, s);
+                        if constexpr (EXT) {
+                            if (P.tf != TF_NONE) adaptive_start(T, F, P, s);
+                        }
                         have = true;
                     }
                 }
@@ -1134,7 +1211,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? BZ_SWARM_MIN_BLOCKS :
                     atomicOr(P.err, BZ_ERR_MAX_TRIALS);
                 } else {
                     R ei, ef;
-                    trial<R, CH_SMEM, ADAPT>(T, F, P, s, ei, ef);
+                    trial<R, CH_SMEM, EXT>(T, F, P, s, ei, ef);
                 }
                 if (s.done) {
                     write_particle<R>(P, s, slot);
@@ -1256,7 +1333,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? BZ_SWARM_MIN_BLOCKS :
                 atomicOr(P.err, BZ_ERR_MAX_TRIALS);
             } else {
                 R ei, ef;
-                trial<R, CH_SMEM>(T, F, P, s, ei, ef);
+                trial<R, CH_SMEM, true>(T, F, P, s, ei, ef);
             }
             if (s.done) {
                 write_particle<R>(P, s, k);
@@ -1304,7 +1381,7 @@ __global__ void __launch_bounds__(kBlock) replay_kernel(const ReplayArgs A)
         s.T_wend = (R)0;
         if (P.window) new_window(T, F, P, s, s.vr0, s.vr1, s.vr2, (R)0);
         R ei, ef;
-        const int dec = trial<R, CH_SMEM>(T, F, P, s, ei, ef);
+        const int dec = trial<R, CH_SMEM, true>(T, F, P, s, ei, ef);
         // state at the trial point: last real collision advanced by s.T
         R v0, v1, v2, sn, omc, dx, dy, dz;
         velocity_at(F, s, s.T, v0, v1, v2, sn, omc);
@@ -1677,7 +1754,7 @@ static cudaError_t prep_smem(K kernel, size_t smem)
     return e;
 }
 
-cudaError_t launch_batch(int precision, bool ch_smem, bool adapt, const BatchArgs &a, size_t smem, int grid,
+cudaError_t launch_batch(int precision, bool ch_smem, bool ext, const BatchArgs &a, size_t smem, int grid,
                          int block, cudaStream_t s)
 {
     if (block != kBlock) return cudaErrorInvalidValue;
@@ -1690,7 +1767,7 @@ cudaError_t launch_batch(int precision, bool ch_smem, bool adapt, const BatchArg
     } while (0)
 #define BZ_LAUNCH2(R, C) \
     do {                 \
-        if (adapt) BZ_LAUNCH(R, C, true); else BZ_LAUNCH(R, C, false); \
+        if (ext) BZ_LAUNCH(R, C, true); else BZ_LAUNCH(R, C, false); \
     } while (0)
     if (precision == 64) {
         if (ch_smem) BZ_LAUNCH2(double, true); else BZ_LAUNCH2(double, false);
@@ -1740,7 +1817,7 @@ int spawn_occupancy(int precision, bool ch_smem, int block, size_t smem)
     return e == cudaSuccess ? n : 0;
 }
 
-int batch_occupancy(int precision, bool ch_smem, bool adapt, int block, size_t smem)
+int batch_occupancy(int precision, bool ch_smem, bool ext, int block, size_t smem)
 {
     int n = 0;
     cudaError_t e;
@@ -1752,7 +1829,7 @@ int batch_occupancy(int precision, bool ch_smem, bool adapt, int block, size_t s
     } while (0)
 #define BZ_OCC2(R, C) \
     do {              \
-        if (adapt) BZ_OCC(R, C, true); else BZ_OCC(R, C, false); \
+        if (ext) BZ_OCC(R, C, true); else BZ_OCC(R, C, false); \
     } while (0)
     if (precision == 64) {
         if (ch_smem) BZ_OCC2(double, true); else BZ_OCC2(double, false);

@@ -91,12 +91,20 @@ struct Bins {
     bool low_sqrt;
 };
 
+// Total elastic cross section of an xi-form gas (Eqs. 6-7): per record and
+// gas its density-weighted value and slope (zero for other gases and in the
+// tail), and per gas its tail constants.
+struct ElTabs {
+    std::vector<std::vector<double>> val, slope;  // [n_rec][n_gases]
+    std::vector<ChParam<double>> tail;            // [n_gases]
+};
+
 template <typename R>
 void emit(const std::vector<Chan> &ch, const std::vector<double> &g, const std::vector<double> &Slo,
           const std::vector<double> &Ssl, const std::vector<std::vector<double>> &cv,
           const std::vector<std::vector<double>> &cs, const std::vector<uint16_t> &bucket,
           const std::vector<ChParam<double>> &cp, int first_tail, float log2_lo, float inv_bw, const Bins &bins,
-          std::vector<uint8_t> *blob, Layout *lay)
+          const ElTabs &el, std::vector<uint8_t> *blob, Layout *lay)
 {
     const int n_rec = (int)Slo.size(), n_ch = (int)ch.size(), nb = (int)bucket.size();
     const int n_bins = bins.n_bins, n_bin_vals = (int)bins.max.size();
@@ -109,7 +117,9 @@ void emit(const std::vector<Chan> &ch, const std::vector<double> &g, const std::
     size_t off_gval = pad16(off_chval + sizeof(ChVal<R>) * (size_t)n_rec * n_ch);
     int n_gases = 0;
     for (const Chan &c : ch) n_gases = std::max(n_gases, c.gas + 1);
-    size_t total = pad16(off_gval + sizeof(ChVal<R>) * (size_t)n_rec * n_gases);
+    size_t off_elval = pad16(off_gval + sizeof(ChVal<R>) * (size_t)n_rec * n_gases);
+    size_t off_elp = pad16(off_elval + sizeof(ChVal<R>) * (size_t)n_rec * n_gases);
+    size_t total = pad16(off_elp + sizeof(ChParam<R>) * (size_t)n_gases);
     blob->assign(total, 0);
     Rec<R> *rec = (Rec<R> *)(blob->data() + off_rec);
     for (int i = 0; i < n_rec; ++i) {
@@ -152,6 +162,22 @@ void emit(const std::vector<Chan> &ch, const std::vector<double> &g, const std::
             gv[(size_t)i * n_gases + gI].slope = (R)ss[gI];
         }
     }
+    ChVal<R> *ev = (ChVal<R> *)(blob->data() + off_elval);
+    for (int i = 0; i < n_rec; ++i)
+        for (int gI = 0; gI < n_gases; ++gI) {
+            ev[(size_t)i * n_gases + gI].val = (R)el.val[i][gI];
+            ev[(size_t)i * n_gases + gI].slope = (R)el.slope[i][gI];
+        }
+    ChParam<R> *ep = (ChParam<R> *)(blob->data() + off_elp);
+    for (int gI = 0; gI < n_gases; ++gI) {
+        ep[gI].kappa2 = ep[gI].mfrac = ep[gI].minv = ep[gI].eps_k = (R)0;
+        ep[gI].e_last = (R)el.tail[gI].e_last;
+        ep[gI].tail_logc = (R)el.tail[gI].tail_logc;
+        ep[gI].tail_K = (R)el.tail[gI].tail_K;
+        ep[gI].bits = el.tail[gI].bits;
+    }
+    lay->off_elval = (uint32_t)off_elval;
+    lay->off_elp = (uint32_t)off_elp;
     lay->off_gval = (uint32_t)off_gval;
     lay->n_gases = n_gases;
     for (int gI = 0; gI < kMaxGases; ++gI) {
@@ -198,6 +224,7 @@ bz_status compile_mixture(const bz_gas *gases, int32_t n_gases, const bz_mixture
     if (n_gases > kMaxGases) { *err = "at most 16 gases per mixture"; return BZ_EINVAL; }
     std::vector<Chan> ch;
     std::vector<ChParam<double>> cp;
+    std::vector<Chan> eltab;  // per gas (xi form: the total elastic table; else empty)
     double n_total = 0.0, emax = 0.0;
     const double m = kMe;
     for (int gi = 0; gi < n_gases; ++gi) {
@@ -206,9 +233,37 @@ bz_status compile_mixture(const bz_gas *gases, int32_t n_gases, const bz_mixture
         if (!(G.number_density_m3 > 0.0) || !finite(G.number_density_m3)) {
             *err = "gas number density must be > 0"; return BZ_EINVAL;
         }
-        if (G.angular != BZ_ANG_ISOTROPIC && G.angular != BZ_ANG_SCREENED_COULOMB) {
+        if (G.angular != BZ_ANG_ISOTROPIC && G.angular != BZ_ANG_SCREENED_COULOMB && G.angular != BZ_ANG_XI) {
             *err = "unknown angular model"; return BZ_EINVAL;
         }
+        Chan elc;  // xi form: the total elastic cross section, as an elastic table
+        elc.kind = BZ_ELASTIC;
+        elc.gas = gi;
+        elc.th = 0.0;
+        elc.n = G.number_density_m3;
+        elc.tail_zero = true;
+        elc.tail_K = 0.0;
+        if (G.angular == BZ_ANG_XI) {
+            int n_el_ch = 0;
+            for (int c = 0; c < G.n_channels && G.channels; ++c) n_el_ch += G.channels[c].kind == BZ_ELASTIC;
+            if (n_el_ch != 1) { *err = "an xi-form gas needs exactly one elastic channel"; return BZ_EINVAL; }
+            if (G.el_n_points < 1 || !G.el_energy_eV || !G.sigma_el_m2) {
+                *err = "an xi-form gas needs its total elastic cross section"; return BZ_EINVAL;
+            }
+            elc.e.assign(G.el_energy_eV, G.el_energy_eV + G.el_n_points);
+            elc.s.assign(G.sigma_el_m2, G.sigma_el_m2 + G.el_n_points);
+            for (int i = 0; i < G.el_n_points; ++i) {
+                if (!finite(elc.e[i]) || elc.e[i] < 0.0 || !finite(elc.s[i]) || elc.s[i] < 0.0 ||
+                    (i > 0 && !(elc.e[i] > elc.e[i - 1]))) {
+                    *err = "bad total elastic cross-section table"; return BZ_EINVAL;
+                }
+            }
+            const size_t n = elc.e.size();
+            elc.tail_zero = elc.s[n - 1] == 0.0;
+            if (n >= 2 && elc.s[n - 1] > 0.0 && elc.s[n - 2] > 0.0)
+                elc.tail_K = log(elc.s[n - 1] / elc.s[n - 2]) / log(elc.e[n - 1] / elc.e[n - 2]);
+        }
+        eltab.push_back(std::move(elc));
         if (G.n_channels < 1 || !G.channels) { *err = "a gas needs at least one channel"; return BZ_EINVAL; }
         n_total += G.number_density_m3;
         const double M = G.mass_kg;
@@ -259,6 +314,17 @@ bz_status compile_mixture(const bz_gas *gases, int32_t n_gases, const bz_mixture
         g.insert(g.end(), c.e.begin(), c.e.end());
         if (c.kind != BZ_ELASTIC) g.push_back(c.th);
     }
+    for (const Chan &c : eltab) g.insert(g.end(), c.e.begin(), c.e.end());
+    // xi-form gases: each channel names its gas and the gas's elastic channel
+    if (n_ch > 0xFFFF) { *err = "at most 65535 channels"; return BZ_EINVAL; }
+    for (int j = 0; j < n_ch; ++j) {
+        const int gI = ch[j].gas;
+        if (gases[gI].angular != BZ_ANG_XI) continue;
+        int el = 0;
+        for (int k = 0; k < n_ch; ++k)
+            if (ch[k].gas == gI && ch[k].kind == BZ_ELASTIC) el = k;
+        cp[j].bits |= (gI << 12) | (el << 16);
+    }
     std::sort(g.begin(), g.end());
     g.erase(std::unique(g.begin(), g.end()), g.end());
     const int P = (int)g.size();
@@ -285,6 +351,30 @@ bz_status compile_mixture(const bz_gas *gases, int32_t n_gases, const bz_mixture
         Slo[i] = S;
         Ssl[i] = sl;
         if (any_tail && i < first_tail) first_tail = i;
+    }
+    // xi-form gases: the total elastic cross section on the same records
+    ElTabs elt;
+    elt.val.assign(n_rec, std::vector<double>(n_gases, 0.0));
+    elt.slope = elt.val;
+    elt.tail.assign(n_gases, ChParam<double>());
+    for (int gI = 0; gI < n_gases; ++gI) {
+        ChParam<double> &t = elt.tail[gI];
+        memset(&t, 0, sizeof t);
+        t.bits = 0x100;  // no tail
+        const Chan &c = eltab[gI];
+        if (gases[gI].angular != BZ_ANG_XI) continue;
+        for (int i = 0; i + 1 < n_rec; ++i) {
+            double lo = (i == 0) ? 0.0 : g[i - 1];
+            double mid = (i == 0) ? 0.5 * g[0] : 0.5 * (lo + g[i]);
+            double a, b;
+            if (!piece(c, mid, &a, &b)) continue;
+            elt.val[i][gI] = c.n * (a + b * lo);
+            elt.slope[i][gI] = c.n * b;
+        }
+        t.e_last = c.e.back();
+        t.tail_K = c.tail_K;
+        t.tail_logc = c.tail_zero ? 0.0 : log(c.n * c.s.back()) - c.tail_K * log(c.e.back());
+        t.bits = c.tail_zero ? 0x100 : 0;
     }
     // exact maximum of nu over [0, eps_cap]
     double cap = (opts && opts->eps_cap_eV > 0.0) ? opts->eps_cap_eV : emax;
@@ -442,13 +532,16 @@ bz_status compile_mixture(const bz_gas *gases, int32_t n_gases, const bz_mixture
         }
     }
 
-    emit<float>(ch, g, Slo, Ssl, cv, cs, bucket, cp, first_tail, log2_lo, inv_bw, bins, &out->blob32, &out->lay32);
-    emit<double>(ch, g, Slo, Ssl, cv, cs, bucket, cp, first_tail, log2_lo, inv_bw, bins, &out->blob64, &out->lay64);
+    emit<float>(ch, g, Slo, Ssl, cv, cs, bucket, cp, first_tail, log2_lo, inv_bw, bins, elt, &out->blob32,
+                &out->lay32);
+    emit<double>(ch, g, Slo, Ssl, cv, cs, bucket, cp, first_tail, log2_lo, inv_bw, bins, elt, &out->blob64,
+                 &out->lay64);
     out->n_total = n_total;
     out->nu_max = best;
     out->nu_trial = best * (1.0 + guard);
     bz_mixture_info &I = out->info;
     memset(&I, 0, sizeof I);
+    for (int gI = 0; gI < n_gases; ++gI) I.n_xi_gases += gases[gI].angular == BZ_ANG_XI;
     I.nu_max = best;
     I.nu_trial = out->nu_trial;
     I.eps_at_max = best_eps;

@@ -131,8 +131,10 @@ class GpuBatchBackend:
     @staticmethod
     def group_key(req: Request) -> int:
         """Requests share a launch only with requests of the same step-kernel
-        instance: the paper's adaptive trial frequencies run in their own."""
-        return int(getattr(req.cfg, "trial_mode", 0) in (3, 4))
+        instance: the paper's adaptive trial frequencies and mixtures with
+        xi-form gases run in the feature instance."""
+        info = getattr(req.mixture, "info", None) or {}
+        return int(getattr(req.cfg, "trial_mode", 0) in (3, 4) or info.get("n_xi_gases", 0) > 0)
 
     def launch_group(self, reqs: Sequence[Request], slot: int):
         if len(reqs) == 1 and self.alone(reqs[0]):

@@ -40,7 +40,7 @@ def test_every_declared_symbol_is_exported(L):
     missing = [n for n in names if n not in exported]
     assert not missing, missing
     assert set(names) == set(bz.SIGNATURES)
-    assert L.bz_abi_version() == 2
+    assert L.bz_abi_version() == 3
 
 
 def test_struct_layouts_match_the_header(tmp_path):
@@ -128,6 +128,20 @@ def _bad(kind="ok"):
     elif kind == "density":
         dens = -1.0
     return [W.Gas("bad", mass, dens, W.ISOTROPIC, [W.Channel(k, th, e, s)])]
+
+
+def test_xi_form_gases_compile_and_validate():
+    n = W.N_STP_293
+    info = bz.compile_info([W.argon_like(0.9 * n), W.co2_like(0.1 * n, xi_form=True)])
+    assert info["n_xi_gases"] == 1 and info["n_gases"] == 2
+    base = W.co2_like()
+    no_table = W.Gas("xi", base.mass_kg, base.number_density_m3, W.XI_FORM, base.channels)
+    two_elastic = W.Gas("xi", base.mass_kg, base.number_density_m3, W.XI_FORM,
+                        base.channels + [base.channels[0]], sigma_el=(base.channels[0].energy_eV,
+                                                                     base.channels[0].sigma_m2))
+    for gas in (no_table, two_elastic):
+        with pytest.raises(bz.BzError):
+            bz.compile_info([gas])
 
 
 @pytest.mark.parametrize("kind", ["nonmono", "neg", "nan", "below_threshold", "mass", "density"])
