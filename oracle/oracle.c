@@ -43,6 +43,7 @@
 #define OR_HARTREE_EV 27.211386245988
 #define OR_TD 1e-21                /* 1 Townsend [V m^2] */
 #define OR_PI 3.14159265358979323846
+#define OR_KB 1.380649e-23         /* Boltzmann constant [J/K] */
 
 enum { OR_ELASTIC = 0, OR_EXCITATION = 1, OR_ATTACHMENT = 2, OR_IONIZATION = 3 };
 enum { OR_ISOTROPIC = 0, OR_SCREENED_COULOMB = 1, OR_ANG_XI = 2 };
@@ -648,6 +649,7 @@ typedef struct {
     double zeta;              /* Variable: nu' = (1 + zeta) nu(eps) */
     uint32_t grace;           /* Variable, Binned: collisions between two queries of nu' */
     int bins_per_decade;      /* Binned */
+    double gas_T;             /* > 0: gas temperature [K]: targets move (Sec. 2.1); 0: targets at rest */
 } or_config;
 
 #define OR_TF_CONST 0
@@ -688,6 +690,47 @@ static void init_velocity(const or_config *cf, uint64_t id, double v[3])
  * For an ionization, sec_v receives the secondary's velocity (the ejected
  * electron takes the fraction w0 of the energy left after Eq. (9) and
  * leaves isotropically: cos = 1 - 2 w1, azimuth 2 pi w2). */
+/* Sec. 2.1: a collision with a moving target, worked in the centre-of-
+ * momentum frame.  v1, v2: bullet and target velocities (mass m, M); the
+ * bullet's velocity relative to the centre of momentum keeps its length less
+ * what the energy loss eps_k [eV] takes,
+ *   |v1' - Vcm|^2 = |v1 - Vcm|^2 - 2 eps_k M / ((m + M) m),
+ * (clamped at 0) and turns by (cos_t, phi) about its own direction; the
+ * target takes the opposite momentum in that frame. */
+void or_thermal_collide(const double v1[3], const double v2[3], double m, double M, double eps_k, double cos_t,
+                        double phi, double v1_out[3], double v2_out[3])
+{
+    double vcm[3], g[3];
+    for (int i = 0; i < 3; ++i) {
+        vcm[i] = (m * v1[i] + M * v2[i]) / (m + M);
+        g[i] = v1[i] - vcm[i];
+    }
+    double gn = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+    double d[3] = {0.0, 0.0, 1.0};
+    if (gn > 0.0) { d[0] = g[0] / gn; d[1] = g[1] / gn; d[2] = g[2] / gn; }
+    double gp = sqrt(fmax(0.0, gn * gn - 2.0 * eps_k * OR_QE * M / ((m + M) * m)));
+    double nd[3];
+    or_rotate(d, cos_t, phi, nd);
+    for (int i = 0; i < 3; ++i) {
+        v1_out[i] = vcm[i] + gp * nd[i];
+        if (v2_out) v2_out[i] = vcm[i] - (m / M) * gp * nd[i];
+    }
+}
+
+/* Target velocity of the real collision at `step` (Sec. 2.1): Maxwell-
+ * Boltzmann at temperature T, each component normal with variance kT/M
+ * (Box-Muller on the fourth draw of the step, sub-counter 3). */
+static void target_velocity(const or_config *cf, uint64_t id, uint32_t step, double M, double v2[3])
+{
+    double w[4];
+    draw4(cf->seed, id, step, 3u, w);
+    double st = sqrt(OR_KB * cf->gas_T / M);
+    double r0 = sqrt(-2.0 * log(w[0])), r1 = sqrt(-2.0 * log(w[2]));
+    v2[0] = st * r0 * cos(2.0 * OR_PI * w[1]);
+    v2[1] = st * r0 * sin(2.0 * OR_PI * w[1]);
+    v2[2] = st * r1 * cos(2.0 * OR_PI * w[3]);
+}
+
 static void collide(const or_mixture *m, const or_config *cf, uint64_t id, uint32_t step, int c, double eps,
                     const double u[4], double v[3], double *eps_f, int *ion, int *att, double sec_v[3])
 {
@@ -699,6 +742,30 @@ static void collide(const or_mixture *m, const or_config *cf, uint64_t id, uint3
     double ratio;
     *ion = 0;
     *att = 0;
+    if (cf->gas_T > 0.0 && ch->kind != OR_ATTACHMENT) {
+        /* Sec. 2.1: moving targets; the lab energy after the collision, then
+         * for an ionization the split with the secondary as below */
+        double v2[3], v1p[3];
+        target_velocity(cf, id, step, g->M, v2);
+        or_thermal_collide(v, v2, OR_ME, g->M, ch->kind == OR_ELASTIC ? 0.0 : ch->threshold, cos_t, phi, v1p, NULL);
+        double ef = 0.5 * OR_ME * (v1p[0] * v1p[0] + v1p[1] * v1p[1] + v1p[2] * v1p[2]) / OR_QE;
+        double keep = 1.0;
+        if (ch->kind == OR_IONIZATION) {
+            double w[4];
+            draw4(cf->seed, id, step, 1u, w);
+            double es = w[0] * ef;
+            double ss = sqrt(2.0 * es * OR_QE / OR_ME), cs = 1.0 - 2.0 * w[1], sn = sqrt(fmax(0.0, 1.0 - cs * cs));
+            sec_v[0] = ss * sn * cos(2.0 * OR_PI * w[2]);
+            sec_v[1] = ss * sn * sin(2.0 * OR_PI * w[2]);
+            sec_v[2] = ss * cs;
+            keep = 1.0 - w[0];
+            *ion = 1;
+        }
+        double sk = sqrt(keep);
+        for (int i = 0; i < 3; ++i) v[i] = v1p[i] * sk;
+        *eps_f = keep * ef;
+        return;
+    }
     if (ch->kind == OR_ELASTIC) {
         ratio = or_ratio_elastic(OR_ME, g->M, cos_t);
     } else if (ch->kind == OR_ATTACHMENT) {

@@ -47,7 +47,7 @@ class _Config(C.Structure):
                 ("t_end", C.c_double), ("eps0_mean_eV", C.c_double), ("seed", C.c_uint64),
                 ("max_trials", C.c_uint64), ("attach_keep_state", C.c_int), ("spawn", C.c_int),
                 ("pop_cap", C.c_uint64), ("strategy", C.c_int), ("zeta", C.c_double), ("grace", C.c_uint32),
-                ("bins_per_decade", C.c_int)]
+                ("bins_per_decade", C.c_int), ("gas_T", C.c_double)]
 
 
 # trial frequency strategies of Sec. 6 (besides the constant one)
@@ -107,6 +107,8 @@ def lib():
             [_dp] * 10 + [_u32p] * 7 + [_u64p, _dp]
         L.or_sigma_many.argtypes = [C.c_void_p, C.c_int, C.c_int64, _dp, _dp]
         L.or_initial_velocity_many.argtypes = [C.c_double, C.c_uint64, C.c_uint64, C.c_int64, _dp]
+        L.or_thermal_collide.argtypes = [_dp, _dp, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
+                                         _dp, _dp]
         L.or_range_max.restype = C.c_double
         L.or_range_max.argtypes = [C.c_void_p, C.c_double, C.c_double]
         L.or_binned_max.restype = C.c_double
@@ -215,6 +217,16 @@ def cos_theta(angular: int, eps_eV: float, R: float) -> float:
     return lib().or_cos_theta(int(angular), float(eps_eV), float(R))
 
 
+def thermal_collide(v1, v2, m: float, M: float, eps_k: float, cos_t: float, phi: float):
+    """One collision with a moving target in the centre-of-momentum frame (Sec. 2.1)."""
+    a = np.ascontiguousarray(v1, dtype=np.float64)
+    b = np.ascontiguousarray(v2, dtype=np.float64)
+    o1, o2 = np.zeros(3), np.zeros(3)
+    lib().or_thermal_collide(_p(a, _dp), _p(b, _dp), float(m), float(M), float(eps_k), float(cos_t), float(phi),
+                             _p(o1, _dp), _p(o2, _dp))
+    return o1, o2
+
+
 def xi_ratio(xi: float) -> float:
     """sigma_mt / sigma_el produced by the xi form (right side of Eq. 7)."""
     return lib().or_xi_ratio(float(xi))
@@ -264,11 +276,11 @@ def initial_velocities(eps0_mean_eV: float, seed: int, id0: int, n: int) -> np.n
 
 def _config(e_over_n_Td, b_T, b_angle_rad, real_collisions, seed, eps0_mean_eV, nu_trial, fixed, t_end,
             max_trials, attach_keep_state, spawn=False, pop_cap=0, strategy=TF_CONST, zeta=0.25, grace=5000,
-            bins_per_decade=8) -> _Config:
+            bins_per_decade=8, gas_T=0.0) -> _Config:
     return _Config(float(e_over_n_Td), float(b_T), float(b_angle_rad), float(nu_trial), int(bool(fixed)),
                    int(real_collisions), float(t_end), float(eps0_mean_eV), int(seed) & 0xFFFFFFFFFFFFFFFF,
                    int(max_trials), int(bool(attach_keep_state)), int(bool(spawn)), int(pop_cap), int(strategy),
-                   float(zeta), int(grace), int(bins_per_decade))
+                   float(zeta), int(grace), int(bins_per_decade), float(gas_T))
 
 
 def secondary_id(parent: int, step: int) -> int:

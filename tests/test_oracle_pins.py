@@ -761,3 +761,77 @@ def test_xi_form_forward_scattering_raises_the_drift_velocity():
     ti = T.swarm_tallies(iso, 60.0, W.N_STP_293)
     tf = T.swarm_tallies(fwd, 60.0, W.N_STP_293)
     assert tf["W"] > ti["W"] - 3 * math.hypot(ti["W_se"], tf["W_se"])
+
+
+# --------------------------------------------------------------------------
+# Moving targets (Sec. 2.1): collisions in the centre-of-momentum frame
+# --------------------------------------------------------------------------
+KB = 1.380649e-23
+
+
+def test_thermal_collision_conserves_momentum_and_energy():
+    rng = np.random.default_rng(5)
+    for M_over_m in (1.0, 10.0, 7.3e4):
+        m, M = ME, ME * M_over_m
+        for eps_k in (0.0, 0.4):
+            v1 = rng.normal(0, 1e6, 3)
+            v2 = rng.normal(0, 3e3, 3)
+            ct, phi = float(rng.uniform(-1, 1)), float(rng.uniform(0, 2 * math.pi))
+            a, b = O.thermal_collide(v1, v2, m, M, eps_k, ct, phi)
+            p0, p1 = m * v1 + M * v2, m * a + M * b
+            assert np.allclose(p1, p0, rtol=0, atol=1e-12 * np.abs(p0).max())
+            e0 = 0.5 * m * v1 @ v1 + 0.5 * M * v2 @ v2
+            e1 = 0.5 * m * a @ a + 0.5 * M * b @ b
+            assert e1 == pytest.approx(e0 - eps_k * QE, rel=1e-12, abs=0.0)
+            # the centre-of-momentum frame turns the bullet by theta
+            vcm = p0 / (m + M)
+            g0, g1 = v1 - vcm, a - vcm
+            assert g0 @ g1 / (np.linalg.norm(g0) * np.linalg.norm(g1)) == pytest.approx(ct, abs=1e-12)
+
+
+def _thermal_gas():
+    # constant collision frequency nu = 1e12/s, target mass 10 m (light, so the mass factors show)
+    return W.maxwell_gas(nu=1e12, mass_ratio=0.1)
+
+
+def test_thermal_equilibrium_at_zero_field():
+    """Without a field, electrons among targets at temperature T relax to the
+    Maxwellian at T (a constant collision frequency keeps detailed balance):
+    mean energy 3/2 kT, energies distributed as Gamma(3/2, kT)."""
+    temp = 293.15
+    kT = KB * temp / QE
+    m = O.Mixture([_thermal_gas()])
+    p = O.run_swarm(m, e_over_n_Td=0.0, real_collisions=300, n=6000, seed=17, threads=O.cpu_count(), gas_T=temp)
+    eps = 0.5 * ME * (p["vx"] ** 2 + p["vy"] ** 2 + p["vz"] ** 2) / QE
+    assert abs(eps.mean() - 1.5 * kT) < 4 * eps.std() / math.sqrt(len(eps))
+    assert stats.kstest(eps / kT, stats.gamma(1.5).cdf).pvalue > 1e-3
+    # targets at rest instead: the electrons keep cooling (20 collisions take
+    # the 0.1 eV start to ~3 meV, well below 3/2 kT)
+    q = O.run_swarm(m, e_over_n_Td=0.0, real_collisions=20, n=2000, seed=17, threads=O.cpu_count())
+    assert (0.5 * ME * (q["vx"] ** 2 + q["vy"] ** 2 + q["vz"] ** 2) / QE).mean() < 0.5 * kT
+
+
+def test_thermal_drift_and_mean_energy_closed_forms():
+    """Constant collision frequency, isotropic scattering in the centre-of-
+    momentum frame, targets at T: momentum balance gives v_d = eE/(mu nu)
+    (mu the reduced mass); per collision <d eps> = -kappa (eps - 3/2 kT) with
+    kappa = 2 m M / (m + M)^2, so <eps> = 3/2 kT + (eE)^2 / (mu nu^2 kappa)."""
+    temp, nu = 293.15, 1e12
+    gas = _thermal_gas()
+    M = gas.mass_kg
+    mu, kappa = ME * M / (ME + M), 2 * ME * M / (ME + M) ** 2
+    eon = 10.0
+    E = eon * 1e-21 * gas.number_density_m3
+    p = O.run_swarm(O.Mixture([gas]), e_over_n_Td=eon, real_collisions=1000, n=6000, seed=19,
+                    threads=O.cpu_count(), gas_T=temp)
+    t = OT_tallies(p, eon, gas.number_density_m3)
+    vd = QE * E / (mu * nu)
+    mean_eps = 1.5 * KB * temp / QE + (QE * E) ** 2 / (mu * nu ** 2 * kappa) / QE
+    assert abs(t["W"] - vd) < 3.5 * t["W_se"]
+    assert abs(t["eps"] - mean_eps) < 3.5 * t["eps_se"]
+    # and the mass factor matters: the heavy-target formula is several SE away
+    assert abs(t["W"] - QE * E / (ME * nu)) > 5 * t["W_se"]
+
+
+def OT_tallies(p, eon, n):
+    return T.swarm_tallies(p, eon, n)
