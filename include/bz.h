@@ -34,7 +34,7 @@
 extern "C" {
 #endif
 
-#define BZ_ABI_VERSION 3
+#define BZ_ABI_VERSION 4
 
 typedef enum {
     BZ_OK = 0,
@@ -212,6 +212,9 @@ typedef struct {
     double zeta;              /* VARIABLE: overhead, nu' = (1 + zeta) nu(eps); >= 0 */
     uint32_t grace;           /* VARIABLE, BINNED: collisions between queries of nu'; >= 1 */
     int32_t bins_per_decade;  /* BINNED: 1, 2, 4, 8, 16 or 32 */
+    double gas_temperature_K; /* > 0: the targets move, Maxwell-Boltzmann at this temperature, and every
+                                 collision but attachment is worked in the centre-of-momentum frame
+                                 (Sec. 2.1); 0: targets at rest (Eqs. 8-9) */
 } bz_swarm_config;
 
 /* Fills *cfg with defaults: N = 1e4, I = 1000, FP32, lazy mode, Maxwellian

@@ -69,7 +69,7 @@ class bz_swarm_config(C.Structure):
                 ("seed", C.c_uint64), ("id_offset", C.c_uint64), ("block_threads", C.c_int32),
                 ("blocks_per_sm", C.c_int32), ("window_c", C.c_double), ("spawn", C.c_int32),
                 ("reserved0", C.c_int32), ("pop_cap", C.c_uint64), ("zeta", C.c_double),
-                ("grace", C.c_uint32), ("bins_per_decade", C.c_int32)]
+                ("grace", C.c_uint32), ("bins_per_decade", C.c_int32), ("gas_temperature_K", C.c_double)]
 
 
 _TALLY_DOUBLES = ["W", "W_se", "Wx", "Wy", "W_flux", "lorentz_angle", "mu", "mu_N", "mu_0", "eps", "eps_se",
@@ -346,7 +346,7 @@ def make_config(*, n_electrons: int, real_collisions: int, e_over_n_Td: float, b
                 trial_mode: int = BZ_TRIAL_LAZY, nu_trial: float = 0.0, t_end_s: float = 0.0, max_trials: int = 0,
                 id_offset: int = 0, attach_keep_state: bool = False, blocks_per_sm: int = 0,
                 window_c: float = 0.0, spawn: bool = False, pop_cap: int = 0, zeta: float = 0.25,
-                grace: int = 5000, bins_per_decade: int = 8) -> bz_swarm_config:
+                grace: int = 5000, bins_per_decade: int = 8, gas_temperature_K: float = 0.0) -> bz_swarm_config:
     cfg = bz_swarm_config()
     lib().bz_config_defaults(C.byref(cfg))
     _check(lib().bz_set_fields(C.byref(cfg), float(e_over_n_Td), float(b_T), float(b_angle_rad)))
@@ -368,6 +368,7 @@ def make_config(*, n_electrons: int, real_collisions: int, e_over_n_Td: float, b
     cfg.zeta = float(zeta)
     cfg.grace = int(grace)
     cfg.bins_per_decade = int(bins_per_decade)
+    cfg.gas_temperature_K = float(gas_temperature_K)
     return cfg
 
 

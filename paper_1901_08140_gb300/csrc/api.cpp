@@ -213,10 +213,10 @@ bool adaptive(const bz_swarm_config *cfg)
 }
 
 // Swarms that need the feature instance of the step kernel: the paper's
-// adaptive trial frequencies, or a mixture with an xi-form gas.
+// adaptive trial frequencies, a mixture with an xi-form gas, or moving targets.
 bool ext_instance(const bz_mixture *mix, const bz_swarm_config *cfg)
 {
-    return adaptive(cfg) || mix->cm.info.n_xi_gases > 0;
+    return adaptive(cfg) || mix->cm.info.n_xi_gases > 0 || cfg->gas_temperature_K > 0.0;
 }
 
 bz_status validate_config(const bz_swarm_config *cfg)
@@ -240,6 +240,8 @@ bz_status validate_config(const bz_swarm_config *cfg)
     if (cfg->trial_mode == BZ_TRIAL_FIXED && !(cfg->nu_trial > 0.0)) return fail(BZ_EINVAL, "fixed mode needs nu_trial > 0");
     if (!(cfg->eps0_mean_eV >= 0.0) || !isfinite(cfg->eps0_mean_eV)) return fail(BZ_EINVAL, "bad eps0_mean_eV");
     if (!(cfg->t_end_s >= 0.0) || !isfinite(cfg->t_end_s)) return fail(BZ_EINVAL, "bad t_end_s");
+    if (!(cfg->gas_temperature_K >= 0.0) || !isfinite(cfg->gas_temperature_K))
+        return fail(BZ_EINVAL, "gas_temperature_K must be finite and >= 0");
     if (cfg->max_trials > 0xFFFFFFFFull) return fail(BZ_EINVAL, "max_trials must fit 32 bits");
     if (cfg->block_threads != 0 && cfg->block_threads != 256) return fail(BZ_EINVAL, "block_threads must be 0 or 256");
     if (cfg->blocks_per_sm < 0) return fail(BZ_EINVAL, "blocks_per_sm must be >= 0");
@@ -278,6 +280,7 @@ bz_status prepare_run(const bz_mixture *mix, const bz_swarm_config *cfg, bz::Run
     a->tf = cfg->trial_mode == BZ_TRIAL_VARIABLE ? bz::TF_VARIABLE
             : cfg->trial_mode == BZ_TRIAL_BINNED ? bz::TF_BINNED : bz::TF_NONE;
     a->tf_zeta1 = 1.0 + cfg->zeta;
+    a->kT_m = 1.380649e-23 * cfg->gas_temperature_K / bz::kMe;  // Boltzmann constant [J/K]
     // the adaptive nu' is never below nu at the lowest table energy (nu
     // vanishes at rest, and the tables say nothing below their first point)
     if (a->tf != bz::TF_NONE) a->nu_floor = std::max(a->nu_floor, a->lay.nu_first);

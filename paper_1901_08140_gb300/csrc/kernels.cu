@@ -763,6 +763,68 @@ __device__ __noinline__ void spawn_secondary(const RunArgs &P, const Fld<R> &F, 
     st_release(P.bid + j, secondary_id(((uint64_t)s.id_hi << 32) | s.id_lo, step));
 }
 
+// Sec. 2.1: a collision with a moving target, in the centre-of-momentum
+// frame.  The target's velocity is Maxwell-Boltzmann at the gas temperature
+// (each component normal with variance kT/M; Box-Muller on the step's
+// fourth draw, sub-counter 3); the bullet's velocity relative to the centre
+// of momentum keeps its length less what the energy loss eps_k takes,
+// |g'|^2 = |g|^2 - 2 eps_k M / ((m + M) m), and turns by (ct, azimuth u)
+// about its own direction, with the azimuth origin of the lab rotation.
+// m/(m+M) comes from kappa2 / (2 M/(m+M)), which does not cancel in FP32.
+template <typename R>
+__device__ __noinline__ void thermal_collide(const RunArgs &P, uint32_t id_lo, uint32_t id_hi, uint32_t step,
+                                             const ChParam<R> &p, bool elastic, R v0, R v1, R v2, R ct, R u, R Ke,
+                                             R &o0, R &o1, R &o2)
+{
+    const uint4 w = philox(id_lo, id_hi, step, 3u, P.key0, P.key1);
+    const R a = p.mfrac, b = p.kappa2 / ((R)2 * p.mfrac);  // M/(m+M), m/(m+M)
+    const R st = sqrt_((R)P.kT_m * (b / a));              // sqrt(kT/M) = sqrt(kT/m * m/M)
+    const R r0 = sqrt_((R)-2 * log_(uni<R>(w.x))), r1 = sqrt_((R)-2 * log_(uni<R>(w.z)));
+    R s1, c1, s3, c3;
+    sincospi_((R)2 * uni<R>(w.y), &s1, &c1);
+    sincospi_((R)2 * uni<R>(w.w), &s3, &c3);
+    const R V0 = st * r0 * c1, V1 = st * r0 * s1, V2 = st * r1 * c3;
+    const R c0 = b * v0 + a * V0, cc1 = b * v1 + a * V1, c2 = b * v2 + a * V2;  // centre of momentum
+    const R g0 = v0 - c0, g1 = v1 - cc1, g2 = v2 - c2;
+    const R gsq = g0 * g0 + g1 * g1 + g2 * g2;
+    R d0 = 0, d1 = 0, d2 = 1;
+    if (gsq > (R)0) {
+        const R ig = rsqrt_(gsq);
+        d0 = g0 * ig;
+        d1 = g1 * ig;
+        d2 = g2 * ig;
+    }
+    const R ek = elastic ? (R)0 : p.eps_k;
+    const R gp = sqrt_(max_((R)0, gsq - ek * a / Ke));  // 2 eps_k QE M/((m+M) m) = eps_k a / Ke
+    // azimuth origin e1 = (x x d)/|x x d|, x the axis of the smallest |d_i|
+    const R ax = fabs(d0), ay = fabs(d1), az = fabs(d2);
+    R e0, e1, e2;
+    if (ax <= ay && ax <= az) {
+        e0 = 0;
+        e1 = -d2;
+        e2 = d1;
+    } else if (ay <= az) {
+        e0 = d2;
+        e1 = 0;
+        e2 = -d0;
+    } else {
+        e0 = -d1;
+        e1 = d0;
+        e2 = 0;
+    }
+    const R ie = rsqrt_(e0 * e0 + e1 * e1 + e2 * e2);
+    e0 *= ie;
+    e1 *= ie;
+    e2 *= ie;
+    const R f0 = d1 * e2 - d2 * e1, f1 = d2 * e0 - d0 * e2, f2 = d0 * e1 - d1 * e0;
+    const R sn = sqrt_(max_((R)0, (R)1 - ct * ct));
+    R sp3, cp3;
+    azimuth(u, sp3, cp3);
+    o0 = c0 + gp * (ct * d0 + sn * (cp3 * e0 + sp3 * f0));
+    o1 = cc1 + gp * (ct * d1 + sn * (cp3 * e1 + sp3 * f1));
+    o2 = c2 + gp * (ct * d2 + sn * (cp3 * e2 + sp3 * f2));
+}
+
 // One trial step.  Returns the decision (channel, DEC_NULL, DEC_FAIL or
 // DEC_WINDOW); eps_i / eps_f receive the energy before and after a real
 // collision.  The velocity at the end of the flight is computed once for
@@ -892,7 +954,29 @@ __device__ __forceinline__ int trial(const Tab<R> &T, const Fld<R> &F, const Run
             }
             R ratio;
             bool rotate = true;
-            if (kind == BZ_ELASTIC) {
+            bool moved = false;  // moving targets: the new velocity is set directly
+            R e_after = 0;
+            if (EXT && P.kT_m > 0.0 && kind != BZ_ATTACHMENT) {
+                R t0, t1, t2;
+                thermal_collide<R>(P, s.id_lo, s.id_hi, step, p, kind == BZ_ELASTIC, v0, v1, v2, ct, uni<R>(w.w),
+                                   F.Ke, t0, t1, t2);
+                const R efl = F.Ke * (t0 * t0 + t1 * t1 + t2 * t2);
+                R keep = 1;
+                if (kind == BZ_IONIZATION) {  // the secondary takes u4 of the lab energy
+                    const uint4 w2 = philox(s.id_lo, s.id_hi, step, 1u, P.key0, P.key1);
+                    const R u4 = uni<R>(w2.x);
+                    if (P.spawn) spawn_secondary(P, F, s, step, u4 * efl, uni<R>(w2.y), uni<R>(w2.z));
+                    keep = (R)1 - u4;
+                    ++s.n_ion;
+                }
+                const R sk = sqrt_(keep);
+                s.vr0 = t0 * sk;
+                s.vr1 = t1 * sk;
+                s.vr2 = t2 * sk;
+                e_after = keep * efl;
+                ratio = 0;
+                moved = true;
+            } else if (kind == BZ_ELASTIC) {
                 ratio = (R)1 - p.kappa2 * ((R)1 - ct);  // Eq. (8)
             } else if (kind == BZ_ATTACHMENT) {
                 ++s.n_att;
@@ -919,7 +1003,8 @@ __device__ __forceinline__ int trial(const Tab<R> &T, const Fld<R> &F, const Run
                 }
             }
             const R nsp = sp * sqrt_(ratio);
-            if (rotate) {
+            if (moved) {
+            } else if (rotate) {
                 R d0 = v0 * inv_sp, d1 = v1 * inv_sp, d2 = v2 * inv_sp;
                 if (!(vsq > (R)0)) {
                     d0 = 0;
@@ -959,7 +1044,7 @@ __device__ __forceinline__ int trial(const Tab<R> &T, const Fld<R> &F, const Run
                 s.vr2 = v2;
             }
             set_b_cache(F, s);
-            eps_f = ratio * eps;
+            eps_f = moved ? e_after : ratio * eps;
             s.se.add(eps);
             s.se2.add(eps_f);
             if (++s.n_real >= P.I) s.done = true;

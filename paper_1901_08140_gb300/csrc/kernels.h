@@ -50,6 +50,7 @@ struct RunArgs {
     double tf_zeta1;         // VARIABLE: 1 + zeta
     uint32_t tf_grace;       // collisions between queries of nu'
     int32_t tf_B;            // BINNED: bins per decade (divides lay.bins_per_decade)
+    double kT_m;             // > 0: moving targets (Sec. 2.1), k T / m_e [(m/s)^2]; 0: targets at rest
     // spawn mode: slots [0, n_primary) are the initial electrons; secondaries
     // take slots from *n_total (up to cap) and their birth state from
     // b*[slot - n_primary]; bid[] != 0 marks a published birth record

@@ -134,7 +134,8 @@ class GpuBatchBackend:
         instance: the paper's adaptive trial frequencies and mixtures with
         xi-form gases run in the feature instance."""
         info = getattr(req.mixture, "info", None) or {}
-        return int(getattr(req.cfg, "trial_mode", 0) in (3, 4) or info.get("n_xi_gases", 0) > 0)
+        return int(getattr(req.cfg, "trial_mode", 0) in (3, 4) or info.get("n_xi_gases", 0) > 0
+                   or getattr(req.cfg, "gas_temperature_K", 0.0) > 0.0)
 
     def launch_group(self, reqs: Sequence[Request], slot: int):
         if len(reqs) == 1 and self.alone(reqs[0]):

@@ -40,7 +40,7 @@ def test_every_declared_symbol_is_exported(L):
     missing = [n for n in names if n not in exported]
     assert not missing, missing
     assert set(names) == set(bz.SIGNATURES)
-    assert L.bz_abi_version() == 3
+    assert L.bz_abi_version() == 4
 
 
 def test_struct_layouts_match_the_header(tmp_path):
@@ -63,7 +63,7 @@ def test_config_defaults_and_field_validation(L):
     L.bz_config_defaults(C.byref(cfg))
     assert cfg.precision == 32 and cfg.real_collisions == 1000 and cfg.seed == 1901081400
     assert cfg.eps0_mean_eV == 0.1 and cfg.trial_mode == bz.BZ_TRIAL_LAZY
-    assert (cfg.zeta, cfg.grace, cfg.bins_per_decade) == (0.25, 5000, 8)
+    assert (cfg.zeta, cfg.grace, cfg.bins_per_decade, cfg.gas_temperature_K) == (0.25, 5000, 8, 0.0)
     assert L.bz_set_fields(C.byref(cfg), 10.0, 1.0, 0.5) == bz.BZ_OK
     assert (cfg.e_over_n_Td, cfg.b_T, cfg.b_angle_rad) == (10.0, 1.0, 0.5)
     for bad in [(-1.0, 0.0, 0.0), (float("nan"), 0.0, 0.0), (1.0, -2.0, 0.0), (1.0, 1.0, float("inf"))]:

@@ -811,11 +811,37 @@ def test_thermal_equilibrium_at_zero_field():
     assert (0.5 * ME * (q["vx"] ** 2 + q["vy"] ** 2 + q["vz"] ** 2) / QE).mean() < 0.5 * kT
 
 
+def thermal_expectations(I, eps0_eV, nu, E, M, temp):
+    """Exact means for a constant collision frequency, isotropic scattering in
+    the centre-of-momentum frame and targets at temperature T, started from
+    an isotropic distribution of mean energy eps0 (zero mean velocity).  Per
+    collision the mean velocity becomes m/(m+M) of its value (the target's
+    mean is 0, the centre-of-momentum velocity keeps the rest) and
+    <eps'> = (1 - kappa) eps + kappa 3/2 kT, kappa = 2 m M / (m + M)^2; an
+    exponential flight of mean 1/nu from velocity u adds u/nu + a/nu^2 to z
+    and m a u / nu + m a^2 / nu^2 to the energy (<tau^2> = 2/nu^2).  Returns
+    (E[sum z] / E[sum t], mean energy before a collision [eV]); their steady
+    states are v_d = eE/(mu nu) and 3/2 kT + (eE)^2/(mu nu^2 kappa)."""
+    a = QE * E / ME
+    b = ME / (ME + M)
+    kappa = 2 * ME * M / (ME + M) ** 2
+    u, ea, Z, eb_sum = 0.0, eps0_eV * QE, 0.0, 0.0
+    for _ in range(I):
+        Z += u / nu + a / nu ** 2
+        eb = ea + ME * a * u / nu + ME * a * a / nu ** 2
+        eb_sum += eb
+        u = b * (u + a / nu)
+        ea = (1 - kappa) * eb + kappa * 1.5 * KB * temp
+    return Z / (I / nu), eb_sum / I / QE
+
+
 def test_thermal_drift_and_mean_energy_closed_forms():
     """Constant collision frequency, isotropic scattering in the centre-of-
     momentum frame, targets at T: momentum balance gives v_d = eE/(mu nu)
     (mu the reduced mass); per collision <d eps> = -kappa (eps - 3/2 kT) with
-    kappa = 2 m M / (m + M)^2, so <eps> = 3/2 kT + (eE)^2 / (mu nu^2 kappa)."""
+    kappa = 2 m M / (m + M)^2, so <eps> = 3/2 kT + (eE)^2 / (mu nu^2 kappa).
+    The ratio-of-sums drift and the collision-averaged energy are compared
+    with the exact means of the transient from the start (above)."""
     temp, nu = 293.15, 1e12
     gas = _thermal_gas()
     M = gas.mass_kg
@@ -827,10 +853,12 @@ def test_thermal_drift_and_mean_energy_closed_forms():
     t = OT_tallies(p, eon, gas.number_density_m3)
     vd = QE * E / (mu * nu)
     mean_eps = 1.5 * KB * temp / QE + (QE * E) ** 2 / (mu * nu ** 2 * kappa) / QE
-    assert abs(t["W"] - vd) < 3.5 * t["W_se"]
-    assert abs(t["eps"] - mean_eps) < 3.5 * t["eps_se"]
+    w_exp, e_exp = thermal_expectations(1000, 0.1, nu, E, M, temp)
+    assert w_exp == pytest.approx(vd, rel=2e-3, abs=0.0) and e_exp == pytest.approx(mean_eps, rel=2e-3, abs=0.0)
+    assert abs(t["W_flux"] - w_exp) < 3.5 * t["W_se"]
+    assert abs(t["eps"] - e_exp) < 3.5 * t["eps_se"]
     # and the mass factor matters: the heavy-target formula is several SE away
-    assert abs(t["W"] - QE * E / (ME * nu)) > 5 * t["W_se"]
+    assert abs(t["W_flux"] - QE * E / (ME * nu)) > 5 * t["W_se"]
 
 
 def OT_tallies(p, eon, n):
