@@ -34,6 +34,10 @@ constexpr int kBlock = 256;
 #ifndef BZ_SWARM_MIN_BLOCKS
 #define BZ_SWARM_MIN_BLOCKS 3  // FP32: resident blocks per SM the register allocation must allow
 #endif
+// The lean FP32 step kernel is also built for 4 resident blocks per SM (64
+// registers, a few more spills); a launch takes it when its tables leave
+// room for 4 blocks, where it is faster, and the 3-block build otherwise.
+constexpr int kMinBlocksWide = 4;
 constexpr uint32_t kStageChunk = 32768;
 constexpr uint32_t kWaitLimit = 1u << 24;
 
@@ -734,7 +738,7 @@ __device__ __forceinline__ uint64_t ld_acquire(const uint64_t *p)
 // counts them as pending before any of them can finish; the birth record
 // is written at the slot and published by storing the id last (release).
 template <typename R>
-__device__ __noinline__ void spawn_secondary(const RunArgs &P, const Fld<R> &F, const PState<R> &s, uint32_t step,
+__device__ __noinline__ void spawn_secondary(const RunArgs &P, R Ke, double t_birth, uint64_t parent, uint32_t step,
                                              R es, R u_cos, R u_phi)
 {
     namespace cg = cooperative_groups;
@@ -753,14 +757,14 @@ __device__ __noinline__ void spawn_secondary(const RunArgs &P, const Fld<R> &F, 
         return;
     }
     const uint64_t j = k - P.n_primary;
-    const R ss = sqrt_(es / F.Ke), ct = (R)1 - (R)2 * u_cos, st = sqrt_(max_((R)0, (R)1 - ct * ct));
+    const R ss = sqrt_(es / Ke), ct = (R)1 - (R)2 * u_cos, st = sqrt_(max_((R)0, (R)1 - ct * ct));
     R sp, cp;
     azimuth(u_phi, sp, cp);
-    P.bt[j] = s.t0 + s.t.value();
+    P.bt[j] = t_birth;
     P.bvx[j] = (double)(ss * st * cp);
     P.bvy[j] = (double)(ss * st * sp);
     P.bvz[j] = (double)(ss * ct);
-    st_release(P.bid + j, secondary_id(((uint64_t)s.id_hi << 32) | s.id_lo, step));
+    st_release(P.bid + j, secondary_id(parent, step));
 }
 
 // Sec. 2.1: a collision with a moving target, in the centre-of-momentum
@@ -965,7 +969,9 @@ __device__ __forceinline__ int trial(const Tab<R> &T, const Fld<R> &F, const Run
                 if (kind == BZ_IONIZATION) {  // the secondary takes u4 of the lab energy
                     const uint4 w2 = philox(s.id_lo, s.id_hi, step, 1u, P.key0, P.key1);
                     const R u4 = uni<R>(w2.x);
-                    if (P.spawn) spawn_secondary(P, F, s, step, u4 * efl, uni<R>(w2.y), uni<R>(w2.z));
+                    if (P.spawn)
+                        spawn_secondary(P, F.Ke, s.t0 + s.t.value(), ((uint64_t)s.id_hi << 32) | s.id_lo, step,
+                                        u4 * efl, uni<R>(w2.y), uni<R>(w2.z));
                     keep = (R)1 - u4;
                     ++s.n_ion;
                 }
@@ -997,7 +1003,9 @@ __device__ __forceinline__ int trial(const Tab<R> &T, const Fld<R> &F, const Run
                 if (kind == BZ_IONIZATION) {
                     const uint4 w2 = philox(s.id_lo, s.id_hi, step, 1u, P.key0, P.key1);
                     const R u4 = uni<R>(w2.x);
-                    if (P.spawn) spawn_secondary(P, F, s, step, u4 * ratio * eps, uni<R>(w2.y), uni<R>(w2.z));
+                    if (P.spawn)
+                        spawn_secondary(P, F.Ke, s.t0 + s.t.value(), ((uint64_t)s.id_hi << 32) | s.id_lo, step,
+                                        u4 * ratio * eps, uni<R>(w2.y), uni<R>(w2.z));
                     ratio *= (R)1 - u4;  // the secondary takes the rest
                     ++s.n_ion;
                 }
@@ -1215,9 +1223,8 @@ __device__ bool restage_tables(const uint8_t *src, uint8_t *dst, uint32_t bytes,
 // one it holds, runs the tile's electrons with per-lane refill (a lane that
 // finishes an electron takes the next one of the tile), and synchronises
 // before the next tile.
-template <typename R, bool CH_SMEM, bool EXT>
-__global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? BZ_SWARM_MIN_BLOCKS : 1)
-    batch_kernel(const __grid_constant__ BatchArgs B)
+template <typename R, bool CH_SMEM, bool EXT, int MINB>
+__global__ void __launch_bounds__(kBlock, MINB) batch_kernel(const __grid_constant__ BatchArgs B)
 {
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ __align__(8) uint64_t mbar;
@@ -1839,27 +1846,51 @@ static cudaError_t prep_smem(K kernel, size_t smem)
     return e;
 }
 
+// Blocks of the step kernel <R, C, E, MINB> resident per SM with `smem`
+// bytes of tables (a negative value is minus the CUDA error of the query).
+template <typename R, bool C, bool E, int MINB>
+static int occupancy_of(int block, size_t smem)
+{
+    int n = 0;
+    cudaError_t e = prep_smem(batch_kernel<R, C, E, MINB>, smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<R, C, E, MINB>, block, smem);
+    return e == cudaSuccess ? n : -(int)e;
+}
+
+// The lean FP32 kernel runs its 4-block build when 4 of its blocks fit.
+template <bool C>
+static bool wide_fits(int block, size_t smem)
+{
+    return occupancy_of<float, C, false, kMinBlocksWide>(block, smem) >= kMinBlocksWide;
+}
+
 cudaError_t launch_batch(int precision, bool ch_smem, bool ext, const BatchArgs &a, size_t smem, int grid,
                          int block, cudaStream_t s)
 {
     if (block != kBlock) return cudaErrorInvalidValue;
     cudaError_t e;
-#define BZ_LAUNCH(R, C, A)                                                     \
+#define BZ_LAUNCH(R, C, E, M)                                                  \
     do {                                                                       \
-        e = prep_smem(batch_kernel<R, C, A>, smem);                            \
+        e = prep_smem(batch_kernel<R, C, E, M>, smem);                         \
         if (e != cudaSuccess) return e;                                        \
-        batch_kernel<R, C, A><<<grid, block, smem, s>>>(a);                    \
-    } while (0)
-#define BZ_LAUNCH2(R, C) \
-    do {                 \
-        if (ext) BZ_LAUNCH(R, C, true); else BZ_LAUNCH(R, C, false); \
+        batch_kernel<R, C, E, M><<<grid, block, smem, s>>>(a);                 \
     } while (0)
     if (precision == 64) {
-        if (ch_smem) BZ_LAUNCH2(double, true); else BZ_LAUNCH2(double, false);
+        if (ch_smem) {
+            if (ext) BZ_LAUNCH(double, true, true, 1); else BZ_LAUNCH(double, true, false, 1);
+        } else {
+            if (ext) BZ_LAUNCH(double, false, true, 1); else BZ_LAUNCH(double, false, false, 1);
+        }
+    } else if (ext) {
+        if (ch_smem) BZ_LAUNCH(float, true, true, BZ_SWARM_MIN_BLOCKS);
+        else BZ_LAUNCH(float, false, true, BZ_SWARM_MIN_BLOCKS);
+    } else if (ch_smem) {
+        if (wide_fits<true>(block, smem)) BZ_LAUNCH(float, true, false, kMinBlocksWide);
+        else BZ_LAUNCH(float, true, false, BZ_SWARM_MIN_BLOCKS);
     } else {
-        if (ch_smem) BZ_LAUNCH2(float, true); else BZ_LAUNCH2(float, false);
+        if (wide_fits<false>(block, smem)) BZ_LAUNCH(float, false, false, kMinBlocksWide);
+        else BZ_LAUNCH(float, false, false, BZ_SWARM_MIN_BLOCKS);
     }
-#undef BZ_LAUNCH2
 #undef BZ_LAUNCH
     return cudaGetLastError();
 }
@@ -1904,26 +1935,17 @@ int spawn_occupancy(int precision, bool ch_smem, int block, size_t smem)
 
 int batch_occupancy(int precision, bool ch_smem, bool ext, int block, size_t smem)
 {
-    int n = 0;
-    cudaError_t e;
-#define BZ_OCC(R, C, A)                                                                            \
-    do {                                                                                           \
-        e = prep_smem(batch_kernel<R, C, A>, smem);                                                \
-        if (e == cudaSuccess)                                                                      \
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<R, C, A>, block, smem); \
-    } while (0)
-#define BZ_OCC2(R, C) \
-    do {              \
-        if (ext) BZ_OCC(R, C, true); else BZ_OCC(R, C, false); \
-    } while (0)
     if (precision == 64) {
-        if (ch_smem) BZ_OCC2(double, true); else BZ_OCC2(double, false);
-    } else {
-        if (ch_smem) BZ_OCC2(float, true); else BZ_OCC2(float, false);
+        if (ch_smem) return ext ? occupancy_of<double, true, true, 1>(block, smem)
+                                : occupancy_of<double, true, false, 1>(block, smem);
+        return ext ? occupancy_of<double, false, true, 1>(block, smem) : occupancy_of<double, false, false, 1>(block, smem);
     }
-#undef BZ_OCC2
-#undef BZ_OCC
-    return e == cudaSuccess ? n : -(int)e;
+    if (ext) return ch_smem ? occupancy_of<float, true, true, BZ_SWARM_MIN_BLOCKS>(block, smem)
+                            : occupancy_of<float, false, true, BZ_SWARM_MIN_BLOCKS>(block, smem);
+    if (ch_smem) return wide_fits<true>(block, smem) ? kMinBlocksWide
+                                                    : occupancy_of<float, true, false, BZ_SWARM_MIN_BLOCKS>(block, smem);
+    return wide_fits<false>(block, smem) ? kMinBlocksWide
+                                         : occupancy_of<float, false, false, BZ_SWARM_MIN_BLOCKS>(block, smem);
 }
 
 cudaError_t launch_tallies_multi(const TallyArgs *args_dev, int n_swarms, int max_blocks, cudaStream_t s)
