@@ -35,8 +35,11 @@ constexpr int kBlock = 256;
 #define BZ_SWARM_MIN_BLOCKS 3  // FP32: resident blocks per SM the register allocation must allow
 #endif
 // The lean FP32 step kernel is also built for 4 resident blocks per SM (64
-// registers, a few more spills); a launch takes it when its tables leave
-// room for 4 blocks, where it is faster, and the 3-block build otherwise.
+// registers, more spills).  A launch takes it when the caller allows it and
+// the tables leave room for 4 blocks.  Measured on GB300: +6 % on a
+// single-gas sweep, but -3 % on a two-gas mixture with B and -11 % on
+// avalanches, whose longer real-collision path pays for the spills -- so
+// callers allow it for single-gas mixtures only.
 constexpr int kMinBlocksWide = 4;
 constexpr uint32_t kStageChunk = 32768;
 constexpr uint32_t kWaitLimit = 1u << 24;
@@ -1343,9 +1346,8 @@ constexpr uint64_t kSpawnWaitNs = 60ull * 1000000000ull;
 // later one.  Tickets are taken only by lanes that are running, and every
 // slot below the largest ticket has a holder, so a waiting lane waits only
 // on electrons that are being run.
-template <typename R, bool CH_SMEM>
-__global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? BZ_SWARM_MIN_BLOCKS : 1)
-    spawn_kernel(const __grid_constant__ RunArgs P)
+template <typename R, bool CH_SMEM, bool EXT, int MINB>
+__global__ void __launch_bounds__(kBlock, MINB) spawn_kernel(const __grid_constant__ RunArgs P)
 {
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ __align__(8) uint64_t mbar;
@@ -1425,7 +1427,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? BZ_SWARM_MIN_BLOCKS :
                 atomicOr(P.err, BZ_ERR_MAX_TRIALS);
             } else {
                 R ei, ef;
-                trial<R, CH_SMEM, true>(T, F, P, s, ei, ef);
+                trial<R, CH_SMEM, EXT>(T, F, P, s, ei, ef);
             }
             if (s.done) {
                 write_particle<R>(P, s, k);
@@ -1859,13 +1861,13 @@ static int occupancy_of(int block, size_t smem)
 
 // The lean FP32 kernel runs its 4-block build when 4 of its blocks fit.
 template <bool C>
-static bool wide_fits(int block, size_t smem)
+static bool wide_fits(bool allow, int block, size_t smem)
 {
-    return occupancy_of<float, C, false, kMinBlocksWide>(block, smem) >= kMinBlocksWide;
+    return allow && occupancy_of<float, C, false, kMinBlocksWide>(block, smem) >= kMinBlocksWide;
 }
 
-cudaError_t launch_batch(int precision, bool ch_smem, bool ext, const BatchArgs &a, size_t smem, int grid,
-                         int block, cudaStream_t s)
+cudaError_t launch_batch(int precision, bool ch_smem, bool ext, bool wide, const BatchArgs &a, size_t smem,
+                         int grid, int block, cudaStream_t s)
 {
     if (block != kBlock) return cudaErrorInvalidValue;
     cudaError_t e;
@@ -1885,55 +1887,80 @@ cudaError_t launch_batch(int precision, bool ch_smem, bool ext, const BatchArgs 
         if (ch_smem) BZ_LAUNCH(float, true, true, BZ_SWARM_MIN_BLOCKS);
         else BZ_LAUNCH(float, false, true, BZ_SWARM_MIN_BLOCKS);
     } else if (ch_smem) {
-        if (wide_fits<true>(block, smem)) BZ_LAUNCH(float, true, false, kMinBlocksWide);
+        if (wide_fits<true>(wide, block, smem)) BZ_LAUNCH(float, true, false, kMinBlocksWide);
         else BZ_LAUNCH(float, true, false, BZ_SWARM_MIN_BLOCKS);
     } else {
-        if (wide_fits<false>(block, smem)) BZ_LAUNCH(float, false, false, kMinBlocksWide);
+        if (wide_fits<false>(wide, block, smem)) BZ_LAUNCH(float, false, false, kMinBlocksWide);
         else BZ_LAUNCH(float, false, false, BZ_SWARM_MIN_BLOCKS);
     }
 #undef BZ_LAUNCH
     return cudaGetLastError();
 }
 
-cudaError_t launch_spawn(int precision, bool ch_smem, const RunArgs &a, size_t smem, int grid, int block,
-                         cudaStream_t s)
+// Blocks of spawn_kernel<R, C, E, MINB> resident per SM (negative: minus the CUDA error).
+template <typename R, bool C, bool E, int MINB>
+static int spawn_occupancy_of(int block, size_t smem)
+{
+    int n = 0;
+    cudaError_t e = prep_smem(spawn_kernel<R, C, E, MINB>, smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, spawn_kernel<R, C, E, MINB>, block, smem);
+    return e == cudaSuccess ? n : -(int)e;
+}
+
+template <bool C>
+static bool spawn_wide_fits(bool allow, int block, size_t smem)
+{
+    return allow && spawn_occupancy_of<float, C, false, kMinBlocksWide>(block, smem) >= kMinBlocksWide;
+}
+
+cudaError_t launch_spawn(int precision, bool ch_smem, bool ext, bool wide, const RunArgs &a, size_t smem, int grid,
+                         int block, cudaStream_t s)
 {
     if (block != kBlock) return cudaErrorInvalidValue;
     cudaError_t e;
-#define BZ_LAUNCH(R, C)                                                        \
+#define BZ_LAUNCH(R, C, E, M)                                                  \
     do {                                                                       \
-        e = prep_smem(spawn_kernel<R, C>, smem);                               \
+        e = prep_smem(spawn_kernel<R, C, E, M>, smem);                         \
         if (e != cudaSuccess) return e;                                        \
-        spawn_kernel<R, C><<<grid, block, smem, s>>>(a);                       \
+        spawn_kernel<R, C, E, M><<<grid, block, smem, s>>>(a);                 \
     } while (0)
     if (precision == 64) {
-        if (ch_smem) BZ_LAUNCH(double, true); else BZ_LAUNCH(double, false);
+        if (ch_smem) {
+            if (ext) BZ_LAUNCH(double, true, true, 1); else BZ_LAUNCH(double, true, false, 1);
+        } else {
+            if (ext) BZ_LAUNCH(double, false, true, 1); else BZ_LAUNCH(double, false, false, 1);
+        }
+    } else if (ext) {
+        if (ch_smem) BZ_LAUNCH(float, true, true, BZ_SWARM_MIN_BLOCKS);
+        else BZ_LAUNCH(float, false, true, BZ_SWARM_MIN_BLOCKS);
+    } else if (ch_smem) {
+        if (spawn_wide_fits<true>(wide, block, smem)) BZ_LAUNCH(float, true, false, kMinBlocksWide);
+        else BZ_LAUNCH(float, true, false, BZ_SWARM_MIN_BLOCKS);
     } else {
-        if (ch_smem) BZ_LAUNCH(float, true); else BZ_LAUNCH(float, false);
+        if (spawn_wide_fits<false>(wide, block, smem)) BZ_LAUNCH(float, false, false, kMinBlocksWide);
+        else BZ_LAUNCH(float, false, false, BZ_SWARM_MIN_BLOCKS);
     }
 #undef BZ_LAUNCH
     return cudaGetLastError();
 }
 
-int spawn_occupancy(int precision, bool ch_smem, int block, size_t smem)
+int spawn_occupancy(int precision, bool ch_smem, bool ext, bool wide, int block, size_t smem)
 {
-    int n = 0;
-    cudaError_t e;
-#define BZ_OCC(R, C)                                                                        \
-    do {                                                                                    \
-        prep_smem(spawn_kernel<R, C>, smem);                                                \
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, spawn_kernel<R, C>, block, smem); \
-    } while (0)
     if (precision == 64) {
-        if (ch_smem) BZ_OCC(double, true); else BZ_OCC(double, false);
-    } else {
-        if (ch_smem) BZ_OCC(float, true); else BZ_OCC(float, false);
+        if (ch_smem) return ext ? spawn_occupancy_of<double, true, true, 1>(block, smem)
+                                : spawn_occupancy_of<double, true, false, 1>(block, smem);
+        return ext ? spawn_occupancy_of<double, false, true, 1>(block, smem)
+                   : spawn_occupancy_of<double, false, false, 1>(block, smem);
     }
-#undef BZ_OCC
-    return e == cudaSuccess ? n : 0;
+    if (ext) return ch_smem ? spawn_occupancy_of<float, true, true, BZ_SWARM_MIN_BLOCKS>(block, smem)
+                            : spawn_occupancy_of<float, false, true, BZ_SWARM_MIN_BLOCKS>(block, smem);
+    if (ch_smem) return spawn_wide_fits<true>(wide, block, smem) ? kMinBlocksWide
+                        : spawn_occupancy_of<float, true, false, BZ_SWARM_MIN_BLOCKS>(block, smem);
+    return spawn_wide_fits<false>(wide, block, smem) ? kMinBlocksWide
+                                               : spawn_occupancy_of<float, false, false, BZ_SWARM_MIN_BLOCKS>(block, smem);
 }
 
-int batch_occupancy(int precision, bool ch_smem, bool ext, int block, size_t smem)
+int batch_occupancy(int precision, bool ch_smem, bool ext, bool wide, int block, size_t smem)
 {
     if (precision == 64) {
         if (ch_smem) return ext ? occupancy_of<double, true, true, 1>(block, smem)
@@ -1942,9 +1969,9 @@ int batch_occupancy(int precision, bool ch_smem, bool ext, int block, size_t sme
     }
     if (ext) return ch_smem ? occupancy_of<float, true, true, BZ_SWARM_MIN_BLOCKS>(block, smem)
                             : occupancy_of<float, false, true, BZ_SWARM_MIN_BLOCKS>(block, smem);
-    if (ch_smem) return wide_fits<true>(block, smem) ? kMinBlocksWide
+    if (ch_smem) return wide_fits<true>(wide, block, smem) ? kMinBlocksWide
                                                     : occupancy_of<float, true, false, BZ_SWARM_MIN_BLOCKS>(block, smem);
-    return wide_fits<false>(block, smem) ? kMinBlocksWide
+    return wide_fits<false>(wide, block, smem) ? kMinBlocksWide
                                          : occupancy_of<float, false, false, BZ_SWARM_MIN_BLOCKS>(block, smem);
 }
 
