@@ -62,7 +62,7 @@ struct bz_batch {
     bz_ctx *ctx;
     int32_t n;
     int precision;
-    bool ch_smem, use_graph, ext, wide;
+    bool ch_smem, use_graph, ext, wide, bfield;
     size_t smem;
     int grid, n_tiles, max_tblocks;
     std::vector<uint64_t> n_el, id_offset;
@@ -451,8 +451,11 @@ bz_status bz_run_swarm(bz_ctx *ctx, const bz_mixture *mix, const bz_swarm_config
     if (cap > 0xFFFFFFFFull) return fail(BZ_EINVAL, "a swarm holds at most 2^32-1 electrons");
     const int block = 256;
     const bool wide = mix->cm.info.n_gases == 1;  // the 4-block build pays off for one gas only
-    int bps = spawn ? bz::spawn_occupancy(cfg->precision, ch_smem, ext_instance(mix, cfg), wide, block, a.stage_bytes)
-                    : bz::batch_occupancy(cfg->precision, ch_smem, ext_instance(mix, cfg), wide, block, a.stage_bytes);
+    const bool bfield = cfg->b_T > 0.0;
+    int bps = spawn ? bz::spawn_occupancy(cfg->precision, ch_smem, ext_instance(mix, cfg), wide, bfield, block,
+                                          a.stage_bytes)
+                    : bz::batch_occupancy(cfg->precision, ch_smem, ext_instance(mix, cfg), wide, bfield, block,
+                                          a.stage_bytes);
     if (bps < 0) return cuda_fail((cudaError_t)(-bps), "occupancy of the step kernel");
     if (bps < 1) return fail(BZ_ECUDA, "step kernel cannot be resident with these tables");
     if (cfg->blocks_per_sm > 0 && cfg->blocks_per_sm < bps) bps = cfg->blocks_per_sm;
@@ -553,8 +556,8 @@ bz_status bz_run_swarm(bz_ctx *ctx, const bz_mixture *mix, const bz_swarm_config
         ba.slot_lo = 0;
         const int grid = (int)(grid64 < n_tiles ? grid64 : n_tiles);
         if (e == cudaSuccess && n_tiles > 0)
-            e = bz::launch_batch(cfg->precision, ch_smem, ext_instance(mix, cfg), wide, ba, a.stage_bytes, grid,
-                                 block, s->stream);
+            e = bz::launch_batch(cfg->precision, ch_smem, ext_instance(mix, cfg), wide, bfield, ba, a.stage_bytes,
+                                 grid, block, s->stream);
     } else {
         // every electron, created ones included, in one persistent launch:
         // a lane per electron of the population cap (at least a block per
@@ -563,8 +566,8 @@ bz_status bz_run_swarm(bz_ctx *ctx, const bz_mixture *mix, const bz_swarm_config
         uint64_t want = (cap + block - 1) / block;
         if (want < (uint64_t)ctx->sm_count) want = ctx->sm_count;
         const int grid = (int)(grid64 < want ? grid64 : want);
-        if (e == cudaSuccess) e = bz::launch_spawn(cfg->precision, ch_smem, ext_instance(mix, cfg), wide, a, a.stage_bytes, grid,
-                                                  block, s->stream);
+        if (e == cudaSuccess) e = bz::launch_spawn(cfg->precision, ch_smem, ext_instance(mix, cfg), wide, bfield, a,
+                                                  a.stage_bytes, grid, block, s->stream);
     }
     if (e == cudaSuccess) e = cudaEventRecord(s->ev[1], s->stream);
     bz::TallyArgs t;
@@ -719,7 +722,7 @@ static cudaError_t batch_part(bz_batch *b, int part, cudaStream_t s)
         a.tiles = b->tiles;
         a.n_tiles = b->n_tiles;
         a.tile_counter = b->tile_counter;
-        if (e == cudaSuccess) e = bz::launch_batch(b->precision, b->ch_smem, b->ext, b->wide, a, b->smem, b->grid, 256, s);
+        if (e == cudaSuccess) e = bz::launch_batch(b->precision, b->ch_smem, b->ext, b->wide, b->bfield, a, b->smem, b->grid, 256, s);
         return e;
     }
     e = bz::launch_tallies_multi(b->targs, b->n, b->max_tblocks, s);
@@ -767,6 +770,8 @@ bz_status bz_create_batch(bz_ctx *ctx, int32_t n, const bz_mixture *const *mixtu
     b->ext = ext_instance(mixtures[0], &cfgs[0]);
     b->wide = true;  // the 4-block build pays off when every mixture has one gas
     for (int i = 0; i < n; ++i) b->wide = b->wide && mixtures[i]->cm.info.n_gases == 1;
+    b->bfield = false;  // the lean build without the field's paths when no swarm has B
+    for (int i = 0; i < n; ++i) b->bfield = b->bfield || cfgs[i].b_T > 0.0;
     b->use_graph = opts ? opts->use_graph != 0 : true;
     // tables of every mixture must fit; channel tables go to shared memory only if all fit
     b->ch_smem = true;
@@ -785,7 +790,7 @@ bz_status bz_create_batch(bz_ctx *ctx, int32_t n, const bz_mixture *const *mixtu
         desc[i].stage_bytes = b->ch_smem ? desc[i].lay.stage_all : desc[i].lay.stage_tables;
         b->smem = std::max(b->smem, (size_t)desc[i].stage_bytes);
     }
-    int bps = bz::batch_occupancy(precision, b->ch_smem, b->ext, b->wide, 256, b->smem);
+    int bps = bz::batch_occupancy(precision, b->ch_smem, b->ext, b->wide, b->bfield, 256, b->smem);
     if (bps < 1) {
         delete b;
         return fail(BZ_ECUDA, "batch kernel cannot be resident with these tables");
@@ -892,7 +897,7 @@ bz_status bz_create_batch(bz_ctx *ctx, int32_t n, const bz_mixture *const *mixtu
     }
     if (b->use_graph) {
         // make sure the kernels' shared-memory limits are set before capture
-        bz::batch_occupancy(precision, b->ch_smem, b->ext, b->wide, 256, b->smem);
+        bz::batch_occupancy(precision, b->ch_smem, b->ext, b->wide, b->bfield, 256, b->smem);
         for (int part = 0; part < 2 && e == cudaSuccess; ++part) {
             e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
             cudaError_t e1 = (e == cudaSuccess) ? batch_part(b, part, b->cap) : e;

@@ -398,10 +398,10 @@ struct PState {
     bool retried;            // BINNED: nu' comes from a retry after a fail
 };
 
-template <typename R>
+template <typename R, bool BF = true>
 __device__ __forceinline__ void set_b_cache(const Fld<R> &F, PState<R> &s)
 {
-    if (!F.has_b) return;
+    if (!BF || !F.has_b) return;
     const R vpar = s.vr0 * F.b0 + s.vr1 * F.b1 + s.vr2 * F.b2;
     s.u0x = s.vr0 - vpar * F.b0 - F.vD0;
     s.u0y = s.vr1 - vpar * F.b1 - F.vD1;
@@ -418,11 +418,11 @@ __device__ __forceinline__ void set_b_cache(const Fld<R> &F, PState<R> &s)
 //   v(T) = v_r + a_par T b - u0 (1 - cos wT) + (b x u0) sin wT,
 // so that rounding stays relative to the change even when |vD| >> |v|.
 // Returns sn = sin wT and omc = 1 - cos wT (without cancellation).
-template <typename R>
+template <typename R, bool BF = true>
 __device__ __forceinline__ void velocity_at(const Fld<R> &F, const PState<R> &s, R T, R &v0, R &v1, R &v2, R &sn,
                                             R &omc)
 {
-    if (F.has_b) {
+    if (BF && F.has_b) {
         R cs;
         sincos_(F.w * T, &sn, &cs);
         omc = (cs > (R)0) ? sn * sn / ((R)1 + cs) : (R)1 - cs;
@@ -457,11 +457,11 @@ __device__ __forceinline__ R sin_minus_x(R x, R sn)
 
 // Displacement after time T since the last real collision:
 //   dx = v_r T + a_par T^2/2 b + [u0 (sin wT - wT) + (b x u0)(1 - cos wT)] / w.
-template <typename R>
+template <typename R, bool BF = true>
 __device__ __forceinline__ void displacement(const Fld<R> &F, const PState<R> &s, R T, R sn, R omc, R &dx, R &dy,
                                              R &dz)
 {
-    if (F.has_b) {
+    if (BF && F.has_b) {
         const R smx = sin_minus_x(F.w * T, sn);
         const R hp = (R)0.5 * F.a_par * T * T;
         dx = s.vr0 * T + hp * F.b0 + (s.u0x * smx + s.bux * omc) * F.inv_w;
@@ -537,7 +537,7 @@ __device__ __forceinline__ R window_majorant(const Tab<R> &T, R e_lo, R e_hi)
 // |v|^2 lies between v_par^2 + (|vD| - |u0|)^2 and v_par^2 + (|vD| + |u0|)^2;
 // the window then only has to bound the change of v_par, and the tighter of
 // the two bounds is used.
-template <typename R>
+template <typename R, bool BF = true>
 __device__ __forceinline__ void new_window(const Tab<R> &T, const Fld<R> &F, const RunArgs &P, PState<R> &s, R v0,
                                            R v1, R v2, R t0)
 {
@@ -548,7 +548,7 @@ __device__ __forceinline__ void new_window(const Tab<R> &T, const Fld<R> &F, con
     R dt = (R)P.win_c / nub;
     const R grow_max = (R)0.25 * speed + T.s_min;
     R s_hi, s_lo;
-    if (F.has_b) {
+    if (BF && F.has_b) {
         const R u0n = sqrt_(s.u0x * s.u0x + s.u0y * s.u0y + s.u0z * s.u0z);
         const R apar = fabs(F.a_par);
         if (apar * dt > grow_max) dt = grow_max / apar;
@@ -646,7 +646,7 @@ __device__ __forceinline__ void adaptive_start(const Tab<R> &T, const Fld<R> &F,
     s.retried = false;
 }
 
-template <typename R>
+template <typename R, bool BF = true>
 __device__ __forceinline__ void init_particle(const Tab<R> &T, const RunArgs &P, const Fld<R> &F, PState<R> &s,
                                               uint64_t id)
 {
@@ -676,13 +676,13 @@ __device__ __forceinline__ void init_particle(const Tab<R> &T, const RunArgs &P,
     s.status = ST_DONE;
     s.done = false;
     s.t0 = 0.0;
-    set_b_cache(F, s);
+    set_b_cache<R, BF>(F, s);
     s.T_wend = (R)0;
-    if (P.window) new_window(T, F, P, s, s.vr0, s.vr1, s.vr2, (R)0);
+    if (P.window) new_window<R, BF>(T, F, P, s, s.vr0, s.vr1, s.vr2, (R)0);
 }
 
 // Spawn mode: the electron in secondary slot j starts from its birth record.
-template <typename R>
+template <typename R, bool BF = true>
 __device__ __forceinline__ void init_secondary(const Tab<R> &T, const RunArgs &P, const Fld<R> &F, PState<R> &s,
                                                uint64_t j)
 {
@@ -707,9 +707,9 @@ __device__ __forceinline__ void init_secondary(const Tab<R> &T, const RunArgs &P
     s.status = ST_DONE;
     s.done = false;
     s.t0 = __ldcg(P.bt + j);
-    set_b_cache(F, s);
+    set_b_cache<R, BF>(F, s);
     s.T_wend = (R)0;
-    if (P.window) new_window(T, F, P, s, s.vr0, s.vr1, s.vr2, (R)0);
+    if (P.window) new_window<R, BF>(T, F, P, s, s.vr0, s.vr1, s.vr2, (R)0);
 }
 
 // Id of the electron created by the ionization at `step` of electron
@@ -838,7 +838,7 @@ __device__ __noinline__ void thermal_collide(const RunArgs &P, uint32_t id_lo, u
 // every lane, and every lane that needs a new trial-frequency window (window
 // end, real collision, fail) computes it at one common point after the
 // branches, so divergent lanes do not repeat that code.
-template <typename R, bool CH_SMEM, bool EXT = false>
+template <typename R, bool CH_SMEM, bool EXT = false, bool BF = true>
 __device__ __forceinline__ int trial(const Tab<R> &T, const Fld<R> &F, const RunArgs &P, PState<R> &s, R &eps_i,
                                      R &eps_f)
 {
@@ -857,14 +857,14 @@ __device__ __forceinline__ int trial(const Tab<R> &T, const Fld<R> &F, const Run
         restart = false;
     }
     R v0, v1, v2, sn, omc;
-    velocity_at(F, s, Tn, v0, v1, v2, sn, omc);
+    velocity_at<R, BF>(F, s, Tn, v0, v1, v2, sn, omc);
     const R vsq = v0 * v0 + v1 * v1 + v2 * v2;
     const R eps = F.Ke * vsq;
     eps_i = eps;
     eps_f = 0;
     if (cut) {
         R dx, dy, dz;
-        displacement(F, s, Tn, sn, omc, dx, dy, dz);
+        displacement<R, BF>(F, s, Tn, sn, omc, dx, dy, dz);
         s.x.add(dx);
         s.y.add(dy);
         s.z.add(dz);
@@ -940,7 +940,7 @@ __device__ __forceinline__ int trial(const Tab<R> &T, const Fld<R> &F, const Run
             const int c = select_channel<R, CH_SMEM>(T, ri, elo, eps, r * inv_sp);
             {
                 R dx, dy, dz;
-                displacement(F, s, Tn, sn, omc, dx, dy, dz);
+                displacement<R, BF>(F, s, Tn, sn, omc, dx, dy, dz);
                 s.x.add(dx);
                 s.y.add(dy);
                 s.z.add(dz);
@@ -1054,7 +1054,7 @@ __device__ __forceinline__ int trial(const Tab<R> &T, const Fld<R> &F, const Run
                 s.vr1 = v1;
                 s.vr2 = v2;
             }
-            set_b_cache(F, s);
+            set_b_cache<R, BF>(F, s);
             eps_f = moved ? e_after : ratio * eps;
             s.se.add(eps);
             s.se2.add(eps_f);
@@ -1083,7 +1083,7 @@ __device__ __forceinline__ int trial(const Tab<R> &T, const Fld<R> &F, const Run
         }
     }
     if (need_window) {
-        new_window(T, F, P, s, w0, w1, w2, wt0);
+        new_window<R, BF>(T, F, P, s, w0, w1, w2, wt0);
     }
     if (dec == DEC_FAIL) {
         if (EXT && P.tf != TF_NONE) {
@@ -1226,7 +1226,7 @@ __device__ bool restage_tables(const uint8_t *src, uint8_t *dst, uint32_t bytes,
 // one it holds, runs the tile's electrons with per-lane refill (a lane that
 // finishes an electron takes the next one of the tile), and synchronises
 // before the next tile.
-template <typename R, bool CH_SMEM, bool EXT, int MINB>
+template <typename R, bool CH_SMEM, bool EXT, int MINB, bool BF>
 __global__ void __launch_bounds__(kBlock, MINB) batch_kernel(const __grid_constant__ BatchArgs B)
 {
     extern __shared__ __align__(128) uint8_t smem[];
@@ -1289,7 +1289,7 @@ __global__ void __launch_bounds__(kBlock, MINB) batch_kernel(const __grid_consta
                     const unsigned int idx = base + __popc(need & ((1u << lane) - 1u));
                     if (idx < tile.z) {
                         slot = (uint64_t)tile.y + idx;
-                        init_particle<R>(T, P, F, s, P.id_offset + slot);
+                        init_particle<R, BF>(T, P, F, s, P.id_offset + slot);
                         if constexpr (EXT) {
                             if (P.tf != TF_NONE) adaptive_start(T, F, P, s);
                         }
@@ -1306,7 +1306,7 @@ __global__ void __launch_bounds__(kBlock, MINB) batch_kernel(const __grid_consta
                     atomicOr(P.err, BZ_ERR_MAX_TRIALS);
                 } else {
                     R ei, ef;
-                    trial<R, CH_SMEM, EXT>(T, F, P, s, ei, ef);
+                    trial<R, CH_SMEM, EXT, BF>(T, F, P, s, ei, ef);
                 }
                 if (s.done) {
                     write_particle<R>(P, s, slot);
@@ -1346,7 +1346,7 @@ constexpr uint64_t kSpawnWaitNs = 60ull * 1000000000ull;
 // later one.  Tickets are taken only by lanes that are running, and every
 // slot below the largest ticket has a holder, so a waiting lane waits only
 // on electrons that are being run.
-template <typename R, bool CH_SMEM, bool EXT, int MINB>
+template <typename R, bool CH_SMEM, bool EXT, int MINB, bool BF>
 __global__ void __launch_bounds__(kBlock, MINB) spawn_kernel(const __grid_constant__ RunArgs P)
 {
     extern __shared__ __align__(128) uint8_t smem[];
@@ -1399,8 +1399,8 @@ __global__ void __launch_bounds__(kBlock, MINB) spawn_kernel(const __grid_consta
             }
         }
         if (ready) {
-            if (k < P.n_primary) init_particle<R>(T, P, F, s, P.id_offset + k);
-            else init_secondary<R>(T, P, F, s, k - P.n_primary);
+            if (k < P.n_primary) init_particle<R, BF>(T, P, F, s, P.id_offset + k);
+            else init_secondary<R, BF>(T, P, F, s, k - P.n_primary);
             have = true;
             ticket = false;
         }
@@ -1427,7 +1427,7 @@ __global__ void __launch_bounds__(kBlock, MINB) spawn_kernel(const __grid_consta
                 atomicOr(P.err, BZ_ERR_MAX_TRIALS);
             } else {
                 R ei, ef;
-                trial<R, CH_SMEM, EXT>(T, F, P, s, ei, ef);
+                trial<R, CH_SMEM, EXT, BF>(T, F, P, s, ei, ef);
             }
             if (s.done) {
                 write_particle<R>(P, s, k);
@@ -1848,131 +1848,90 @@ static cudaError_t prep_smem(K kernel, size_t smem)
     return e;
 }
 
-// Blocks of the step kernel <R, C, E, MINB> resident per SM with `smem`
-// bytes of tables (a negative value is minus the CUDA error of the query).
-template <typename R, bool C, bool E, int MINB>
-static int occupancy_of(int block, size_t smem)
+// Launching and occupancy of one build of a step kernel.
+template <typename K, typename A>
+static cudaError_t go(K kernel, const A &a, size_t smem, int grid, int block, cudaStream_t s)
+{
+    cudaError_t e = prep_smem(kernel, smem);
+    if (e != cudaSuccess) return e;
+    kernel<<<grid, block, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+// Blocks of `kernel` resident per SM (negative: minus the CUDA error of the query).
+template <typename K>
+static int occ(K kernel, int block, size_t smem)
 {
     int n = 0;
-    cudaError_t e = prep_smem(batch_kernel<R, C, E, MINB>, smem);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<R, C, E, MINB>, block, smem);
+    cudaError_t e = prep_smem(kernel, smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, block, smem);
     return e == cudaSuccess ? n : -(int)e;
 }
 
-// The lean FP32 kernel runs its 4-block build when 4 of its blocks fit.
-template <bool C>
-static bool wide_fits(bool allow, int block, size_t smem)
+template <typename R, bool C, bool E, int M, bool B, bool SPAWN>
+static auto kernel_of()
 {
-    return allow && occupancy_of<float, C, false, kMinBlocksWide>(block, smem) >= kMinBlocksWide;
+    if constexpr (SPAWN) return &spawn_kernel<R, C, E, M, B>;
+    else return &batch_kernel<R, C, E, M, B>;
 }
 
-cudaError_t launch_batch(int precision, bool ch_smem, bool ext, bool wide, const BatchArgs &a, size_t smem,
+// Calls fn with the build of the step kernel (batch or spawn) that a launch
+// uses: FP64 and the feature build (ext) are general; the lean FP32 build
+// comes without the magnetic-field paths where the launch has no field
+// (bf false), and in its 4-block form where the caller allows it and 4
+// blocks fit.
+template <bool SPAWN, typename Fn>
+static auto dispatch(int precision, bool ch, bool ext, bool bf, bool wide, int block, size_t smem, Fn fn)
+{
+    if (precision == 64) {
+        if (ch) return ext ? fn(kernel_of<double, true, true, 1, true, SPAWN>())
+                           : fn(kernel_of<double, true, false, 1, true, SPAWN>());
+        return ext ? fn(kernel_of<double, false, true, 1, true, SPAWN>())
+                   : fn(kernel_of<double, false, false, 1, true, SPAWN>());
+    }
+    if (ext) return ch ? fn(kernel_of<float, true, true, BZ_SWARM_MIN_BLOCKS, true, SPAWN>())
+                       : fn(kernel_of<float, false, true, BZ_SWARM_MIN_BLOCKS, true, SPAWN>());
+#define BZ_LEAN(C, B)                                                                 \
+    do {                                                                              \
+        auto k4 = kernel_of<float, C, false, kMinBlocksWide, B, SPAWN>();            \
+        if (wide && occ(k4, block, smem) >= kMinBlocksWide) return fn(k4);          \
+        return fn(kernel_of<float, C, false, BZ_SWARM_MIN_BLOCKS, B, SPAWN>());      \
+    } while (0)
+    if (ch) {
+        if (bf) BZ_LEAN(true, true);
+        BZ_LEAN(true, false);
+    }
+    if (bf) BZ_LEAN(false, true);
+    BZ_LEAN(false, false);
+#undef BZ_LEAN
+}
+
+cudaError_t launch_batch(int precision, bool ch_smem, bool ext, bool wide, bool bfield, const BatchArgs &a,
+                         size_t smem, int grid, int block, cudaStream_t s)
+{
+    if (block != kBlock) return cudaErrorInvalidValue;
+    return dispatch<false>(precision, ch_smem, ext, bfield, wide, block, smem,
+                           [&](auto k) { return go(k, a, smem, grid, block, s); });
+}
+
+int batch_occupancy(int precision, bool ch_smem, bool ext, bool wide, bool bfield, int block, size_t smem)
+{
+    return dispatch<false>(precision, ch_smem, ext, bfield, wide, block, smem,
+                           [&](auto k) { return occ(k, block, smem); });
+}
+
+cudaError_t launch_spawn(int precision, bool ch_smem, bool ext, bool wide, bool bfield, const RunArgs &a, size_t smem,
                          int grid, int block, cudaStream_t s)
 {
     if (block != kBlock) return cudaErrorInvalidValue;
-    cudaError_t e;
-#define BZ_LAUNCH(R, C, E, M)                                                  \
-    do {                                                                       \
-        e = prep_smem(batch_kernel<R, C, E, M>, smem);                         \
-        if (e != cudaSuccess) return e;                                        \
-        batch_kernel<R, C, E, M><<<grid, block, smem, s>>>(a);                 \
-    } while (0)
-    if (precision == 64) {
-        if (ch_smem) {
-            if (ext) BZ_LAUNCH(double, true, true, 1); else BZ_LAUNCH(double, true, false, 1);
-        } else {
-            if (ext) BZ_LAUNCH(double, false, true, 1); else BZ_LAUNCH(double, false, false, 1);
-        }
-    } else if (ext) {
-        if (ch_smem) BZ_LAUNCH(float, true, true, BZ_SWARM_MIN_BLOCKS);
-        else BZ_LAUNCH(float, false, true, BZ_SWARM_MIN_BLOCKS);
-    } else if (ch_smem) {
-        if (wide_fits<true>(wide, block, smem)) BZ_LAUNCH(float, true, false, kMinBlocksWide);
-        else BZ_LAUNCH(float, true, false, BZ_SWARM_MIN_BLOCKS);
-    } else {
-        if (wide_fits<false>(wide, block, smem)) BZ_LAUNCH(float, false, false, kMinBlocksWide);
-        else BZ_LAUNCH(float, false, false, BZ_SWARM_MIN_BLOCKS);
-    }
-#undef BZ_LAUNCH
-    return cudaGetLastError();
+    return dispatch<true>(precision, ch_smem, ext, bfield, wide, block, smem,
+                          [&](auto k) { return go(k, a, smem, grid, block, s); });
 }
 
-// Blocks of spawn_kernel<R, C, E, MINB> resident per SM (negative: minus the CUDA error).
-template <typename R, bool C, bool E, int MINB>
-static int spawn_occupancy_of(int block, size_t smem)
+int spawn_occupancy(int precision, bool ch_smem, bool ext, bool wide, bool bfield, int block, size_t smem)
 {
-    int n = 0;
-    cudaError_t e = prep_smem(spawn_kernel<R, C, E, MINB>, smem);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, spawn_kernel<R, C, E, MINB>, block, smem);
-    return e == cudaSuccess ? n : -(int)e;
-}
-
-template <bool C>
-static bool spawn_wide_fits(bool allow, int block, size_t smem)
-{
-    return allow && spawn_occupancy_of<float, C, false, kMinBlocksWide>(block, smem) >= kMinBlocksWide;
-}
-
-cudaError_t launch_spawn(int precision, bool ch_smem, bool ext, bool wide, const RunArgs &a, size_t smem, int grid,
-                         int block, cudaStream_t s)
-{
-    if (block != kBlock) return cudaErrorInvalidValue;
-    cudaError_t e;
-#define BZ_LAUNCH(R, C, E, M)                                                  \
-    do {                                                                       \
-        e = prep_smem(spawn_kernel<R, C, E, M>, smem);                         \
-        if (e != cudaSuccess) return e;                                        \
-        spawn_kernel<R, C, E, M><<<grid, block, smem, s>>>(a);                 \
-    } while (0)
-    if (precision == 64) {
-        if (ch_smem) {
-            if (ext) BZ_LAUNCH(double, true, true, 1); else BZ_LAUNCH(double, true, false, 1);
-        } else {
-            if (ext) BZ_LAUNCH(double, false, true, 1); else BZ_LAUNCH(double, false, false, 1);
-        }
-    } else if (ext) {
-        if (ch_smem) BZ_LAUNCH(float, true, true, BZ_SWARM_MIN_BLOCKS);
-        else BZ_LAUNCH(float, false, true, BZ_SWARM_MIN_BLOCKS);
-    } else if (ch_smem) {
-        if (spawn_wide_fits<true>(wide, block, smem)) BZ_LAUNCH(float, true, false, kMinBlocksWide);
-        else BZ_LAUNCH(float, true, false, BZ_SWARM_MIN_BLOCKS);
-    } else {
-        if (spawn_wide_fits<false>(wide, block, smem)) BZ_LAUNCH(float, false, false, kMinBlocksWide);
-        else BZ_LAUNCH(float, false, false, BZ_SWARM_MIN_BLOCKS);
-    }
-#undef BZ_LAUNCH
-    return cudaGetLastError();
-}
-
-int spawn_occupancy(int precision, bool ch_smem, bool ext, bool wide, int block, size_t smem)
-{
-    if (precision == 64) {
-        if (ch_smem) return ext ? spawn_occupancy_of<double, true, true, 1>(block, smem)
-                                : spawn_occupancy_of<double, true, false, 1>(block, smem);
-        return ext ? spawn_occupancy_of<double, false, true, 1>(block, smem)
-                   : spawn_occupancy_of<double, false, false, 1>(block, smem);
-    }
-    if (ext) return ch_smem ? spawn_occupancy_of<float, true, true, BZ_SWARM_MIN_BLOCKS>(block, smem)
-                            : spawn_occupancy_of<float, false, true, BZ_SWARM_MIN_BLOCKS>(block, smem);
-    if (ch_smem) return spawn_wide_fits<true>(wide, block, smem) ? kMinBlocksWide
-                        : spawn_occupancy_of<float, true, false, BZ_SWARM_MIN_BLOCKS>(block, smem);
-    return spawn_wide_fits<false>(wide, block, smem) ? kMinBlocksWide
-                                               : spawn_occupancy_of<float, false, false, BZ_SWARM_MIN_BLOCKS>(block, smem);
-}
-
-int batch_occupancy(int precision, bool ch_smem, bool ext, bool wide, int block, size_t smem)
-{
-    if (precision == 64) {
-        if (ch_smem) return ext ? occupancy_of<double, true, true, 1>(block, smem)
-                                : occupancy_of<double, true, false, 1>(block, smem);
-        return ext ? occupancy_of<double, false, true, 1>(block, smem) : occupancy_of<double, false, false, 1>(block, smem);
-    }
-    if (ext) return ch_smem ? occupancy_of<float, true, true, BZ_SWARM_MIN_BLOCKS>(block, smem)
-                            : occupancy_of<float, false, true, BZ_SWARM_MIN_BLOCKS>(block, smem);
-    if (ch_smem) return wide_fits<true>(wide, block, smem) ? kMinBlocksWide
-                                                    : occupancy_of<float, true, false, BZ_SWARM_MIN_BLOCKS>(block, smem);
-    return wide_fits<false>(wide, block, smem) ? kMinBlocksWide
-                                         : occupancy_of<float, false, false, BZ_SWARM_MIN_BLOCKS>(block, smem);
+    return dispatch<true>(precision, ch_smem, ext, bfield, wide, block, smem,
+                          [&](auto k) { return occ(k, block, smem); });
 }
 
 cudaError_t launch_tallies_multi(const TallyArgs *args_dev, int n_swarms, int max_blocks, cudaStream_t s)

@@ -115,17 +115,19 @@ cudaError_t launch_tallies(const TallyArgs &a, cudaStream_t s);
 // form of the angle; the lean instance (the hot path of Lazy, Fixed and
 // windowed swarms in mixtures without xi-form gases) compiles without them.
 // wide: the 4-block build of the lean FP32 kernel may be taken (where its
-// blocks fit); callers allow it for single-gas mixtures.
-cudaError_t launch_batch(int precision, bool ch_smem, bool ext, bool wide, const BatchArgs &a, size_t smem,
-                         int grid, int block, cudaStream_t s);
+// blocks fit); callers allow it for single-gas mixtures.  bfield: some swarm
+// of the launch has a magnetic field (else the lean build without the
+// field's paths runs).
+cudaError_t launch_batch(int precision, bool ch_smem, bool ext, bool wide, bool bfield, const BatchArgs &a,
+                         size_t smem, int grid, int block, cudaStream_t s);
 // Spawn mode: one persistent launch runs the primaries and every electron
 // created from them (slots handed out as tickets from a.counter).
-cudaError_t launch_spawn(int precision, bool ch_smem, bool ext, bool wide, const RunArgs &a, size_t smem, int grid,
-                         int block, cudaStream_t s);
-int spawn_occupancy(int precision, bool ch_smem, bool ext, bool wide, int block, size_t smem);
+cudaError_t launch_spawn(int precision, bool ch_smem, bool ext, bool wide, bool bfield, const RunArgs &a, size_t smem,
+                         int grid, int block, cudaStream_t s);
+int spawn_occupancy(int precision, bool ch_smem, bool ext, bool wide, bool bfield, int block, size_t smem);
 // Blocks of `block` threads that fit on one SM with `smem` bytes of tables.
 // (a negative value is minus the CUDA error of the query)
-int batch_occupancy(int precision, bool ch_smem, bool ext, bool wide, int block, size_t smem);
+int batch_occupancy(int precision, bool ch_smem, bool ext, bool wide, bool bfield, int block, size_t smem);
 // Tallies of n_swarms swarms; args_dev is a device array of TallyArgs.
 cudaError_t launch_tallies_multi(const TallyArgs *args_dev, int n_swarms, int max_blocks, cudaStream_t s);
 int tally_blocks(uint64_t n, int sm_count);

@@ -129,13 +129,16 @@ class GpuBatchBackend:
         return bool(getattr(req.cfg, "spawn", 0))
 
     @staticmethod
-    def group_key(req: Request) -> int:
-        """Requests share a launch only with requests of the same step-kernel
-        instance: the paper's adaptive trial frequencies and mixtures with
-        xi-form gases run in the feature instance."""
+    def group_key(req: Request):
+        """Requests share a launch only with requests that run the same build
+        of the step kernel alone, so that every result is the one the
+        request gets alone: the feature build (the paper's adaptive trial
+        frequencies, xi-form gases, moving targets) or the lean one, and in
+        the lean one with or without a magnetic field."""
         info = getattr(req.mixture, "info", None) or {}
-        return int(getattr(req.cfg, "trial_mode", 0) in (3, 4) or info.get("n_xi_gases", 0) > 0
-                   or getattr(req.cfg, "gas_temperature_K", 0.0) > 0.0)
+        ext = (getattr(req.cfg, "trial_mode", 0) in (3, 4) or info.get("n_xi_gases", 0) > 0
+               or getattr(req.cfg, "gas_temperature_K", 0.0) > 0.0)
+        return (bool(ext), bool(ext or getattr(req.cfg, "b_T", 0.0) > 0.0))
 
     def launch_group(self, reqs: Sequence[Request], slot: int):
         if len(reqs) == 1 and self.alone(reqs[0]):

@@ -36,8 +36,12 @@ def _items(ctx):
 
 
 @pytest.mark.parametrize("use_graph", [True, False])
-def test_batch_equals_individual_runs(ctx, use_graph):
-    items = _items(ctx)
+@pytest.mark.parametrize("field", [True, False])
+def test_batch_equals_individual_runs(ctx, use_graph, field):
+    """A batch runs one build of the step kernel; batches whose swarms all
+    have (or all lack) a magnetic field run the build each swarm runs alone,
+    so every value is the same bit for bit."""
+    items = [(m, c) for m, c in _items(ctx) if (c.b_T > 0) == field]
     batch = bz.Batch(ctx, [m for m, _ in items], [c for _, c in items], tile_particles=512, use_graph=use_graph)
     batch.launch()
     bt = batch.tallies()
@@ -54,6 +58,27 @@ def test_batch_equals_individual_runs(ctx, use_graph):
         assert bt[i]["n_real"] == t["n_real"] and bt[i]["error_flags"] == 0
     km, tm = batch.timing()
     assert km > 0 and tm > 0
+    batch.close()
+
+
+def test_mixed_field_batch(ctx):
+    """Swarms without a field batched with swarms with one run the field's
+    build: the field swarms match their runs alone bit for bit, the others
+    to FP32 rounding along their trajectories (statistics within errors)."""
+    items = _items(ctx)
+    batch = bz.Batch(ctx, [m for m, _ in items], [c for _, c in items], tile_particles=512)
+    batch.launch()
+    bt = batch.tallies()
+    for i, (mix, cfg) in enumerate(items):
+        sw = bz.run_swarm(ctx, mix, cfg)
+        t = sw.tallies()
+        sw.close()
+        assert bt[i]["n_real"] == t["n_real"]
+        if cfg.b_T > 0:
+            assert bt[i]["W"] == t["W"] and bt[i]["n_null"] == t["n_null"], i
+        elif cfg.n_electrons > 100:
+            for k in ("W", "eps"):
+                assert abs(bt[i][k] - t[k]) <= 3 * math.hypot(bt[i][k + "_se"], t[k + "_se"]), (i, k)
     batch.close()
 
 
