@@ -24,7 +24,7 @@ from . import bz
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_autotune_cache.json")
 
 DEFAULT = {"window_c": 2.0, "tile_particles": 0, "blocks_per_sm": 0}
-WINDOW_C = [1.0, 1.5, 2.0, 3.0]
+WINDOW_C = [1.0, 1.5, 2.0, 3.0, 4.0]
 TILES = [0, 512, 1024, 2048, 4096]
 BLOCKS = [0, 2, 1]
 

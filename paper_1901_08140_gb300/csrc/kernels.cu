@@ -487,10 +487,15 @@ __device__ __forceinline__ void displacement(const Fld<R> &F, const PState<R> &s
 // (Eqs. 3-4), with fewer null collisions.
 // ---------------------------------------------------------------------------
 template <typename R>
+__device__ __forceinline__ float bin_pos(const Tab<R> &T, R eps)
+{
+    return (__log2f((float)eps) - T.bin_lo) * T.inv_binw;
+}
+
+template <typename R>
 __device__ __forceinline__ int bin_of(const Tab<R> &T, R eps)
 {
-    float fb = (__log2f((float)eps) - T.bin_lo) * T.inv_binw;
-    fb = fminf(fmaxf(fb, -1.0f), (float)T.n_bins);
+    const float fb = fminf(fmaxf(bin_pos(T, eps), -1.0f), (float)T.n_bins);
     return (int)floorf(fb);  // -1 below the first bin, n_bins above the last
 }
 
@@ -512,7 +517,11 @@ __device__ __noinline__ R tail_bound(const Tab<R> &T, R a, R b)
 template <typename R>
 __device__ __forceinline__ R window_majorant(const Tab<R> &T, R e_lo, R e_hi)
 {
-    int bl = bin_of(T, e_lo) - 1, bh = bin_of(T, e_hi) + 1;
+    // Bins met by [e_lo, e_hi], the positions widened by 1/32 of a bin (0.2 %
+    // in energy): many times the FP32 rounding of the positions, of the
+    // energy bounds and of the energies the flight then reaches.
+    const float pl = fmaxf(bin_pos(T, e_lo) - 0.03125f, -1.0f), ph = fminf(bin_pos(T, e_hi) + 0.03125f, (float)T.n_bins);
+    int bl = (int)floorf(pl), bh = (int)floorf(ph);
     R m = 0;
     if (bl < 0) {
         m = T.nu_low;
