@@ -547,8 +547,8 @@ __device__ __forceinline__ R window_majorant(const Tab<R> &T, R e_lo, R e_hi)
 // the window then only has to bound the change of v_par, and the tighter of
 // the two bounds is used.
 template <typename R, bool BF = true>
-__device__ __forceinline__ void new_window(const Tab<R> &T, const Fld<R> &F, const RunArgs &P, PState<R> &s, R v0,
-                                           R v1, R v2, R t0)
+__device__ __forceinline__ void window_of(const Tab<R> &T, const Fld<R> &F, const RunArgs &P, const PState<R> &s, R v0,
+                                          R v1, R v2, R t0, R &nu_p, R &inv_nu, R &t_wend)
 {
     const R speed = sqrt_(v0 * v0 + v1 * v1 + v2 * v2);
     const R eps = F.Ke * speed * speed;
@@ -576,9 +576,16 @@ __device__ __forceinline__ void new_window(const Tab<R> &T, const Fld<R> &F, con
         s_lo = max_((R)0, speed - grow);
     }
     const R m = max_(window_majorant(T, F.Ke * s_lo * s_lo, F.Ke * s_hi * s_hi) * (R)(1.0 + 1e-5), (R)P.nu_floor);
-    s.nu_p = m;
-    s.inv_nu = (R)1 / m;
-    s.T_wend = t0 + dt;
+    nu_p = m;
+    inv_nu = (R)1 / m;
+    t_wend = t0 + dt;
+}
+
+template <typename R, bool BF = true>
+__device__ __forceinline__ void new_window(const Tab<R> &T, const Fld<R> &F, const RunArgs &P, PState<R> &s, R v0,
+                                           R v1, R v2, R t0)
+{
+    window_of<R, BF>(T, F, P, s, v0, v1, v2, t0, s.nu_p, s.inv_nu, s.T_wend);
 }
 
 // BinnedTrialFrequency (Sec. 6.3): the maximum of nu over the energy bin of
@@ -886,8 +893,10 @@ __device__ __forceinline__ int trial(const Tab<R> &T, const Fld<R> &F, const Run
         s.done = true;
         return DEC_NULL;
     }
+    // No branch below returns early: every lane of the warp meets again
+    // before the window, which they then compute together.
     int dec;
-    bool need_window = false;
+    bool need_window = false, stop = false;
     R wt0 = 0, nu_fail = 0;
     R w0 = v0, w1 = v1, w2 = v2;  // velocity at the start of a new window
     if (restart) {
@@ -904,34 +913,34 @@ __device__ __forceinline__ int trial(const Tab<R> &T, const Fld<R> &F, const Run
         const R nu = sp * S;
         const R r = uni<R>(w.y) * s.nu_p;
         if (!(nu <= s.nu_p)) {
+            dec = DEC_FAIL;
             if (!(nu == nu)) {  // non-finite state: stop this particle, flag it
                 atomicOr(P.err, BZ_ERR_NONFINITE);
                 s.status = ST_ERROR;
-                s.done = true;
-                return DEC_FAIL;
-            }
-            ++s.n_fail;
-            bool error = P.fixed;  // FixedTrialFrequency (Sec. 6.1): an error
-            if constexpr (EXT) {
-                // BinnedTrialFrequency (Sec. 6.3): one retry, then an error
-                if (P.tf == TF_BINNED) {
-                    error = s.retried;
-                    s.retried = true;
+                stop = true;
+            } else {
+                ++s.n_fail;
+                bool error = P.fixed;  // FixedTrialFrequency (Sec. 6.1): an error
+                if constexpr (EXT) {
+                    // BinnedTrialFrequency (Sec. 6.3): one retry, then an error
+                    if (P.tf == TF_BINNED) {
+                        error = s.retried;
+                        s.retried = true;
+                    }
+                }
+                if (error) {
+                    atomicOr(P.err, BZ_ERR_TRIAL);
+                    s.status = ST_TRIAL;
+                    stop = true;
+                } else {
+                    s.T = 0;  // fail (Sec. 6): back to the last real collision
+                    nu_fail = nu;
+                    need_window = P.window;
+                    w0 = s.vr0;
+                    w1 = s.vr1;
+                    w2 = s.vr2;
                 }
             }
-            if (error) {
-                atomicOr(P.err, BZ_ERR_TRIAL);
-                s.status = ST_TRIAL;
-                s.done = true;
-                return DEC_FAIL;
-            }
-            s.T = 0;  // fail (Sec. 6): back to the last real collision
-            nu_fail = nu;
-            need_window = P.window;
-            w0 = s.vr0;
-            w1 = s.vr1;
-            w2 = s.vr2;
-            dec = DEC_FAIL;
         } else if (r > nu) {  // Eq. (4): null collision
             ++s.n_null;
             s.T = Tn;
@@ -1091,8 +1100,20 @@ __device__ __forceinline__ int trial(const Tab<R> &T, const Fld<R> &F, const Run
             }
         }
     }
-    if (need_window) {
-        new_window<R, BF>(T, F, P, s, w0, w1, w2, wt0);
+    if (P.window) {
+        // taken by every lane (the warp is whole again here), kept by those
+        // that start a window: after a restart, a real collision or a fail
+        R m, im, we;
+        window_of<R, BF>(T, F, P, s, w0, w1, w2, wt0, m, im, we);
+        if (need_window) {
+            s.nu_p = m;
+            s.inv_nu = im;
+            s.T_wend = we;
+        }
+    }
+    if (stop) {
+        s.done = true;
+        return DEC_FAIL;
     }
     if (dec == DEC_FAIL) {
         if (EXT && P.tf != TF_NONE) {
