@@ -420,11 +420,13 @@ bz_status compile_mixture(const bz_gas *gases, int32_t n_gases, const bz_mixture
         }
     }
     double guard = (opts && opts->majorant_guard >= 0.0) ? opts->majorant_guard : 1e-6;
-    // bucket index over log2 energy of the positive union points
+    // bucket index over log2 energy of the positive union points: four
+    // buckets per record, so that the walk from a bucket's first record to
+    // the one holding eps rarely takes a step (a step costs the whole warp)
     int ipos = 0;
     while (ipos < P && g[ipos] <= 0.0) ++ipos;
     double L0 = (ipos < P) ? log2(g[ipos]) : 0.0, L1 = log2(g[P - 1] > 0.0 ? g[P - 1] : 1.0);
-    int nb = std::min(std::max(2 * P, 64), 65535);
+    int nb = std::min(std::max(4 * P, 64), 65535);
     double w = (L1 > L0) ? (L1 - L0) / nb : 0.0;
     if (w == 0.0) nb = 1;
     std::vector<uint16_t> bucket(nb);
