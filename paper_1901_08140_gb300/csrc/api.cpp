@@ -284,6 +284,8 @@ bz_status prepare_run(const bz_mixture *mix, const bz_swarm_config *cfg, bz::Run
     // the adaptive nu' is never below nu at the lowest table energy (nu
     // vanishes at rest, and the tables say nothing below their first point)
     if (a->tf != bz::TF_NONE) a->nu_floor = std::max(a->nu_floor, a->lay.nu_first);
+    a->nu_floor32 = (float)a->nu_floor;
+    a->timed = a->t_end > 0.0;
     a->tf_grace = cfg->grace;
     a->tf_B = cfg->bins_per_decade;
     if (a->tf == bz::TF_BINNED && (a->lay.bins_per_decade % cfg->bins_per_decade) != 0)

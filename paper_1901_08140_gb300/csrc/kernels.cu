@@ -114,9 +114,12 @@ __device__ __forceinline__ void azimuth(double u, double &sn, double &cs) { sinc
 template <typename R>
 struct Acc;
 // FP32: increments go into a short float sum `s` (one add each) that fold()
-// moves into the compensated pair (hi, lo) with TwoSum every few additions;
-// the short sum holds at most 16 increments, so its own rounding stays at
-// the level of one increment's.
+// moves into the compensated pair (hi, lo) with TwoSum every 64 additions.
+// Each add to the short sum rounds by at most 2^-24 |s| <= 2^-18 of the
+// largest increment, so over a run the sum carries at most 2^-18 relative
+// error (much less on average, the roundings being of both signs), and the
+// pair adds nothing more.  A fold costs the whole warp while one or two of
+// its lanes need it, so it is kept rare.
 template <>
 struct Acc<float> {
     float hi, lo, s;
@@ -392,11 +395,22 @@ struct PState {
     Acc<R> x, y, z, t;       // position and time at the last real collision, relative to birth
     Acc<R> se, se2;          // energy sums before / after real collisions
     double t0;               // birth time (absolute)
+    R t_left;                // FP32 runs with t_end: time from the last real collision to t_end
     uint32_t id_lo, id_hi, k, n_real, n_null, n_fail, n_ion, n_att, status;
     bool done;
     uint32_t grace;          // adaptive trial frequencies: collisions left before the next query
     bool retried;            // BINNED: nu' comes from a retry after a fail
 };
+
+// Time left until t_end, from the last real collision.  The FP32 step keeps it
+// in FP32 and takes the flight time of each real collision off it; it is set
+// exactly (in FP64) at birth and again at every fold of the time sum, so it
+// carries at most 64 FP32 roundings of the remaining time.
+template <typename R>
+__device__ __forceinline__ void set_t_left(const RunArgs &P, PState<R> &s)
+{
+    if (P.timed) s.t_left = (R)(P.t_end - s.t0 - s.t.value());
+}
 
 template <typename R, bool BF = true>
 __device__ __forceinline__ void set_b_cache(const Fld<R> &F, PState<R> &s)
@@ -486,6 +500,16 @@ __device__ __forceinline__ void displacement(const Fld<R> &F, const PState<R> &s
 // exponential flight this samples the same process as a constant nu'
 // (Eqs. 3-4), with fewer null collisions.
 // ---------------------------------------------------------------------------
+// The lower bound of any trial frequency in the step's precision.  GB300 runs
+// FP64 at a small fraction of the FP32 rate, so the FP32 step takes the FP32
+// copy the host made rather than converting the double on every trial.
+template <typename R>
+__device__ __forceinline__ R nu_floor_of(const RunArgs &P);
+template <>
+__device__ __forceinline__ float nu_floor_of<float>(const RunArgs &P) { return P.nu_floor32; }
+template <>
+__device__ __forceinline__ double nu_floor_of<double>(const RunArgs &P) { return P.nu_floor; }
+
 template <typename R>
 __device__ __forceinline__ float bin_pos(const Tab<R> &T, R eps)
 {
@@ -553,7 +577,7 @@ __device__ __forceinline__ void window_of(const Tab<R> &T, const Fld<R> &F, cons
     const R speed = sqrt_(v0 * v0 + v1 * v1 + v2 * v2);
     const R eps = F.Ke * speed * speed;
     const int b = bin_of(T, eps);
-    const R nub = max_((b < 0) ? T.nu_low : T.binmax[b < T.n_bins ? b : T.n_bins - 1], (R)P.nu_floor);
+    const R nub = max_((b < 0) ? T.nu_low : T.binmax[b < T.n_bins ? b : T.n_bins - 1], nu_floor_of<R>(P));
     R dt = (R)P.win_c / nub;
     const R grow_max = (R)0.25 * speed + T.s_min;
     R s_hi, s_lo;
@@ -575,7 +599,7 @@ __device__ __forceinline__ void window_of(const Tab<R> &T, const Fld<R> &F, cons
         s_hi = speed + grow;
         s_lo = max_((R)0, speed - grow);
     }
-    const R m = max_(window_majorant(T, F.Ke * s_lo * s_lo, F.Ke * s_hi * s_hi) * (R)(1.0 + 1e-5), (R)P.nu_floor);
+    const R m = max_(window_majorant(T, F.Ke * s_lo * s_lo, F.Ke * s_hi * s_hi) * (R)(1.0 + 1e-5), nu_floor_of<R>(P));
     nu_p = m;
     inv_nu = (R)1 / m;
     t_wend = t0 + dt;
@@ -629,8 +653,8 @@ __device__ R binned_max(const Tab<R> &T, const RunArgs &P, R eps)
 template <typename R>
 __device__ __forceinline__ R adaptive_nu(const Tab<R> &T, const RunArgs &P, R eps, R nu)
 {
-    if (P.tf == TF_VARIABLE) return (R)P.tf_zeta1 * max_(nu, (R)P.nu_floor);
-    return max_(binned_max(T, P, eps), (R)P.nu_floor);
+    if (P.tf == TF_VARIABLE) return (R)P.tf_zeta1 * max_(nu, nu_floor_of<R>(P));
+    return max_(binned_max(T, P, eps), nu_floor_of<R>(P));
 }
 
 // nu(eps) from the tables (Eq. 2), for queries at an energy the step has
@@ -692,6 +716,7 @@ __device__ __forceinline__ void init_particle(const Tab<R> &T, const RunArgs &P,
     s.status = ST_DONE;
     s.done = false;
     s.t0 = 0.0;
+    set_t_left(P, s);
     set_b_cache<R, BF>(F, s);
     s.T_wend = (R)0;
     if (P.window) new_window<R, BF>(T, F, P, s, s.vr0, s.vr1, s.vr2, (R)0);
@@ -723,6 +748,7 @@ __device__ __forceinline__ void init_secondary(const Tab<R> &T, const RunArgs &P
     s.status = ST_DONE;
     s.done = false;
     s.t0 = __ldcg(P.bt + j);
+    set_t_left(P, s);
     set_b_cache<R, BF>(F, s);
     s.T_wend = (R)0;
     if (P.window) new_window<R, BF>(T, F, P, s, s.vr0, s.vr1, s.vr2, (R)0);
@@ -867,10 +893,17 @@ __device__ __forceinline__ int trial(const Tab<R> &T, const Fld<R> &F, const Run
     if (restart) Tn = s.T_wend;
     // ... unless t_end comes first: TimeBulletLimiter, the flight stops at t_end
     bool cut = false;
-    if (P.t_end > 0.0 && s.t0 + s.t.value() + (double)Tn >= P.t_end) {
-        Tn = (R)(P.t_end - s.t0 - s.t.value());
-        cut = true;
-        restart = false;
+    if (P.timed) {
+        bool over;
+        if constexpr (sizeof(R) == 4)
+            over = Tn >= s.t_left;  // no FP64 work per trial in the FP32 step
+        else
+            over = s.t0 + s.t.value() + (double)Tn >= P.t_end;
+        if (over) {
+            Tn = (R)(P.t_end - s.t0 - s.t.value());
+            cut = true;
+            restart = false;
+        }
     }
     R v0, v1, v2, sn, omc;
     velocity_at<R, BF>(F, s, Tn, v0, v1, v2, sn, omc);
@@ -963,6 +996,7 @@ __device__ __forceinline__ int trial(const Tab<R> &T, const Fld<R> &F, const Run
                 s.y.add(dy);
                 s.z.add(dz);
                 s.t.add(Tn);
+                if (sizeof(R) == 4 && P.timed) s.t_left -= Tn;
                 s.T = 0;
             }
             const R u2 = uni<R>(w.z);
@@ -1077,13 +1111,14 @@ __device__ __forceinline__ int trial(const Tab<R> &T, const Fld<R> &F, const Run
             s.se.add(eps);
             s.se2.add(eps_f);
             if (++s.n_real >= P.I) s.done = true;
-            if ((s.n_real & 15u) == 0u) {
+            if ((s.n_real & 63u) == 0u) {
                 s.x.fold();
                 s.y.fold();
                 s.z.fold();
                 s.t.fold();
                 s.se.fold();
                 s.se2.fold();
+                set_t_left(P, s);
             }
             need_window = P.window;
             w0 = s.vr0;
@@ -1501,6 +1536,7 @@ __global__ void __launch_bounds__(kBlock) replay_kernel(const ReplayArgs A)
         s.status = ST_DONE;
         s.done = false;
         s.t0 = 0.0;
+        set_t_left(P, s);
         set_b_cache(F, s);
         s.T_wend = (R)0;
         if (P.window) new_window(T, F, P, s, s.vr0, s.vr1, s.vr2, (R)0);

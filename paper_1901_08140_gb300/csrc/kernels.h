@@ -44,6 +44,8 @@ struct RunArgs {
     int32_t window;          // windowed local trial frequency
     float win_c;             // window length in units of 1/nu of the current energy bin
     double nu_floor;         // lower bound of any trial frequency [1/s]
+    float nu_floor32;        // nu_floor rounded to FP32, and
+    int32_t timed;           // t_end > 0: the FP32 step reads these and does no FP64 work per trial
     // the paper's adaptive trial frequencies (Sec. 6): tf = TF_VARIABLE or
     // TF_BINNED (0 otherwise), run by the ADAPT instance of the step kernel
     int32_t tf;
