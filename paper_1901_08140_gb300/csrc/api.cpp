@@ -281,6 +281,8 @@ bz_status prepare_run(const bz_mixture *mix, const bz_swarm_config *cfg, bz::Run
             : cfg->trial_mode == BZ_TRIAL_BINNED ? bz::TF_BINNED : bz::TF_NONE;
     a->tf_zeta1 = 1.0 + cfg->zeta;
     a->kT_m = 1.380649e-23 * cfg->gas_temperature_K / bz::kMe;  // Boltzmann constant [J/K]
+    a->kT_m32 = (float)a->kT_m;
+    a->thermal = a->kT_m > 0.0;
     // the adaptive nu' is never below nu at the lowest table energy (nu
     // vanishes at rest, and the tables say nothing below their first point)
     if (a->tf != bz::TF_NONE) a->nu_floor = std::max(a->nu_floor, a->lay.nu_first);
@@ -452,8 +454,10 @@ bz_status bz_run_swarm(bz_ctx *ctx, const bz_mixture *mix, const bz_swarm_config
     const uint64_t cap = spawn ? (cfg->pop_cap ? cfg->pop_cap : 64 * n) : n;  // electron slots
     if (cap > 0xFFFFFFFFull) return fail(BZ_EINVAL, "a swarm holds at most 2^32-1 electrons");
     const int block = 256;
-    const bool wide = mix->cm.info.n_gases == 1;  // the 4-block build pays off for one gas only
     const bool bfield = cfg->b_T > 0.0;
+    // the 4-block build: for every mixture without B; with B (more registers
+    // live, more spills at 64) only for one gas
+    const bool wide = !bfield || mix->cm.info.n_gases == 1;
     int bps = spawn ? bz::spawn_occupancy(cfg->precision, ch_smem, ext_instance(mix, cfg), wide, bfield, block,
                                           a.stage_bytes)
                     : bz::batch_occupancy(cfg->precision, ch_smem, ext_instance(mix, cfg), wide, bfield, block,
@@ -770,10 +774,10 @@ bz_status bz_create_batch(bz_ctx *ctx, int32_t n, const bz_mixture *const *mixtu
     b->n = n;
     b->precision = precision;
     b->ext = ext_instance(mixtures[0], &cfgs[0]);
-    b->wide = true;  // the 4-block build pays off when every mixture has one gas
-    for (int i = 0; i < n; ++i) b->wide = b->wide && mixtures[i]->cm.info.n_gases == 1;
     b->bfield = false;  // the lean build without the field's paths when no swarm has B
     for (int i = 0; i < n; ++i) b->bfield = b->bfield || cfgs[i].b_T > 0.0;
+    b->wide = true;  // the 4-block build: without B, or when every mixture has one gas
+    for (int i = 0; i < n; ++i) b->wide = b->wide && (!b->bfield || mixtures[i]->cm.info.n_gases == 1);
     b->use_graph = opts ? opts->use_graph != 0 : true;
     // tables of every mixture must fit; channel tables go to shared memory only if all fit
     b->ch_smem = true;

@@ -37,9 +37,10 @@ constexpr int kBlock = 256;
 // The lean FP32 step kernel is also built for 4 resident blocks per SM (64
 // registers, more spills).  A launch takes it when the caller allows it and
 // the tables leave room for 4 blocks.  Measured on GB300: +6 % on a
-// single-gas sweep, but -3 % on a two-gas mixture with B and -11 % on
-// avalanches, whose longer real-collision path pays for the spills -- so
-// callers allow it for single-gas mixtures only.
+// single-gas sweep, +6 % on a two-gas mixture without B and +27 % on
+// avalanches, but -10 % on two-gas mixtures with B, whose field paths keep
+// more registers live -- so callers allow it without B, and with B for
+// single-gas mixtures only.
 constexpr int kMinBlocksWide = 4;
 constexpr uint32_t kStageChunk = 32768;
 constexpr uint32_t kWaitLimit = 1u << 24;
@@ -509,6 +510,12 @@ template <>
 __device__ __forceinline__ float nu_floor_of<float>(const RunArgs &P) { return P.nu_floor32; }
 template <>
 __device__ __forceinline__ double nu_floor_of<double>(const RunArgs &P) { return P.nu_floor; }
+template <typename R>
+__device__ __forceinline__ R kT_m_of(const RunArgs &P);
+template <>
+__device__ __forceinline__ float kT_m_of<float>(const RunArgs &P) { return P.kT_m32; }
+template <>
+__device__ __forceinline__ double kT_m_of<double>(const RunArgs &P) { return P.kT_m; }
 
 template <typename R>
 __device__ __forceinline__ float bin_pos(const Tab<R> &T, R eps)
@@ -827,7 +834,7 @@ __device__ __noinline__ void thermal_collide(const RunArgs &P, uint32_t id_lo, u
 {
     const uint4 w = philox(id_lo, id_hi, step, 3u, P.key0, P.key1);
     const R a = p.mfrac, b = p.kappa2 / ((R)2 * p.mfrac);  // M/(m+M), m/(m+M)
-    const R st = sqrt_((R)P.kT_m * (b / a));              // sqrt(kT/M) = sqrt(kT/m * m/M)
+    const R st = sqrt_(kT_m_of<R>(P) * (b / a));              // sqrt(kT/M) = sqrt(kT/m * m/M)
     const R r0 = sqrt_((R)-2 * log_(uni<R>(w.x))), r1 = sqrt_((R)-2 * log_(uni<R>(w.z)));
     R s1, c1, s3, c3;
     sincospi_((R)2 * uni<R>(w.y), &s1, &c1);
@@ -1015,7 +1022,7 @@ __device__ __forceinline__ int trial(const Tab<R> &T, const Fld<R> &F, const Run
             bool rotate = true;
             bool moved = false;  // moving targets: the new velocity is set directly
             R e_after = 0;
-            if (EXT && P.kT_m > 0.0 && kind != BZ_ATTACHMENT) {
+            if (EXT && P.thermal && kind != BZ_ATTACHMENT) {
                 R t0, t1, t2;
                 thermal_collide<R>(P, s.id_lo, s.id_hi, step, p, kind == BZ_ELASTIC, v0, v1, v2, ct, uni<R>(w.w),
                                    F.Ke, t0, t1, t2);

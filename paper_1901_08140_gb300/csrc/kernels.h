@@ -53,6 +53,8 @@ struct RunArgs {
     uint32_t tf_grace;       // collisions between queries of nu'
     int32_t tf_B;            // BINNED: bins per decade (divides lay.bins_per_decade)
     double kT_m;             // > 0: moving targets (Sec. 2.1), k T / m_e [(m/s)^2]; 0: targets at rest
+    float kT_m32;            // kT_m rounded to FP32, and
+    int32_t thermal;         // kT_m > 0, for the FP32 step
     // spawn mode: slots [0, n_primary) are the initial electrons; secondaries
     // take slots from *n_total (up to cap) and their birth state from
     // b*[slot - n_primary]; bid[] != 0 marks a published birth record
