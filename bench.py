@@ -434,7 +434,7 @@ def run_ours(args):
     achieved = work / (kern_ms / 1e3)
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tops/s",
                 "frac": achieved / peak, "traffic": profiled_traffic(),
-                "kernel": "batch_kernel (lean FP32 build; 4 blocks/SM where single-gas tables fit)",
+                "kernel": "batch_kernel (lean FP32 build without field paths; 4 blocks/SM where the tables fit)",
                 "note": f"algorithmic thread-ops ({ALG_OPS_PER_TRIAL}/step + {ALG_OPS_PER_REAL}/real) over "
                         f"SMs x 128 lanes x median SM clock {sm_mhz:.0f} MHz"}
     batched_workload = None
