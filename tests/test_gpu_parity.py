@@ -320,6 +320,24 @@ def test_degenerate_and_limit_cases(ctx):
     assert t["error_flags"] & 8 and t["n_incomplete"] == 100
 
 
+@pytest.mark.parametrize("mode", [bz.BZ_TRIAL_LAZY, bz.BZ_TRIAL_WINDOW])
+def test_time_limited_counts_are_poisson_fp32(ctx, mode):
+    """With a constant collision frequency nu the real collisions an electron
+    makes before t_end are Poisson(nu t_end) (Eqs. 3-4).  The FP32 step tests
+    each flight against the remaining time kept in FP32 (set exactly at birth
+    and every 64 real collisions): the mean count must hold to its statistical
+    error, and every electron must stop at t_end exactly."""
+    from test_oracle_pins import _const_rate_gas
+    nu, t_end, n = 1e12, 1e-9, 20000
+    t, p, _ = _gpu_swarm(ctx, [_const_rate_gas(nu)], n_electrons=n, real_collisions=10 ** 6, e_over_n_Td=50.0,
+                         seed=8, t_end_s=t_end, trial_mode=mode)
+    lam = nu * t_end
+    assert t["error_flags"] == 0
+    assert np.all(p["status"] == bz.ST_TIME) and np.allclose(p["t"], t_end, rtol=1e-12, atol=0)
+    assert abs(p["n_real"].mean() - lam) < 4 * math.sqrt(lam / n), (p["n_real"].mean(), lam)
+    assert abs(p["n_real"].var() / lam - 1) < 0.05
+
+
 def test_fixed_trial_frequency_exceeded_is_an_error(ctx):
     mix = bz.Mixture(ctx, [W.argon_like()])
     cfg = bz.make_config(n_electrons=1000, real_collisions=100, e_over_n_Td=300.0, seed=1,
