@@ -202,6 +202,21 @@ bz::Fields make_fields(const bz_swarm_config &cfg, double n_total)
         f.vD[2] = 0.0;
     }
     f.a_par = f.a * f.b[2];
+    bz::Fields32 &g = f.f32;
+    g.a = (float)f.a;
+    g.b0 = (float)f.b[0];
+    g.b1 = (float)f.b[1];
+    g.b2 = (float)f.b[2];
+    g.w = (float)f.w;
+    g.inv_w = f.has_b ? (float)(1.0 / f.w) : 0.0f;
+    g.vD0 = (float)f.vD[0];
+    g.vD1 = (float)f.vD[1];
+    g.vD2 = (float)f.vD[2];
+    g.vDn = (float)sqrt(f.vD[0] * f.vD[0] + f.vD[1] * f.vD[1] + f.vD[2] * f.vD[2]);
+    g.a_par = (float)f.a_par;
+    g.Ke = (float)(0.5 * bz::kMe / bz::kQe);
+    g.inv_a = f.a > 0.0 ? (float)(1.0 / f.a) : 0.0f;
+    g.inv_apar = f.a_par != 0.0 ? (float)(1.0 / fabs(f.a_par)) : 0.0f;
     return f;
 }
 

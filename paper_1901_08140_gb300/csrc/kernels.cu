@@ -83,6 +83,11 @@ __device__ __forceinline__ double exp_(double x) { return exp(x); }
 __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
 __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
 __device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
+// Division where the quotient may be a few ulp off (a window's length, which
+// any positive value makes exact; 1/nu'): the FP32 form takes the hardware
+// reciprocal (2 ulp), FP64 divides exactly.
+__device__ __forceinline__ float fdiv_(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double fdiv_(double a, double b) { return a / b; }
 __device__ __forceinline__ double rsqrt_(double x) { return rsqrt(x); }
 __device__ __forceinline__ float log10_(float x) { return log10f(x); }
 __device__ __forceinline__ double log10_(double x) { return log10(x); }
@@ -360,6 +365,7 @@ __device__ __noinline__ R xi_cos_theta(const Tab<R> &T, const RunArgs &P, int bi
 template <typename R>
 struct Fld {
     R a, b0, b1, b2, w, inv_w, vD0, vD1, vD2, vDn, a_par, Ke;
+    R inv_a, inv_apar;  // 1/a and 1/|a_par| (0 where those vanish)
     int has_b;
 };
 
@@ -367,8 +373,26 @@ template <typename R>
 __device__ __forceinline__ Fld<R> make_fld(const Fields &f)
 {
     Fld<R> F;
-    F.a = (R)f.a;
     F.has_b = f.has_b;
+    if constexpr (sizeof(R) == 4) {  // the host's FP32 copies
+        const Fields32 &g = f.f32;
+        F.a = g.a;
+        F.b0 = g.b0;
+        F.b1 = g.b1;
+        F.b2 = g.b2;
+        F.w = g.w;
+        F.inv_w = g.inv_w;
+        F.vD0 = g.vD0;
+        F.vD1 = g.vD1;
+        F.vD2 = g.vD2;
+        F.vDn = g.vDn;
+        F.a_par = g.a_par;
+        F.Ke = g.Ke;
+        F.inv_a = g.inv_a;
+        F.inv_apar = g.inv_apar;
+        return F;
+    }
+    F.a = (R)f.a;
     F.b0 = (R)f.b[0];
     F.b1 = (R)f.b[1];
     F.b2 = (R)f.b[2];
@@ -380,6 +404,8 @@ __device__ __forceinline__ Fld<R> make_fld(const Fields &f)
     F.vDn = (R)sqrt(f.vD[0] * f.vD[0] + f.vD[1] * f.vD[1] + f.vD[2] * f.vD[2]);
     F.a_par = (R)f.a_par;
     F.Ke = (R)(0.5 * kMe / kQe);  // eV per (m/s)^2
+    F.inv_a = f.a > 0.0 ? (R)(1.0 / f.a) : (R)0;
+    F.inv_apar = f.a_par != 0.0 ? (R)(1.0 / fabs(f.a_par)) : (R)0;
     return F;
 }
 
@@ -585,13 +611,13 @@ __device__ __forceinline__ void window_of(const Tab<R> &T, const Fld<R> &F, cons
     const R eps = F.Ke * speed * speed;
     const int b = bin_of(T, eps);
     const R nub = max_((b < 0) ? T.nu_low : T.binmax[b < T.n_bins ? b : T.n_bins - 1], nu_floor_of<R>(P));
-    R dt = (R)P.win_c / nub;
+    R dt = fdiv_((R)P.win_c, nub);  // any positive length is exact
     const R grow_max = (R)0.25 * speed + T.s_min;
     R s_hi, s_lo;
     if (BF && F.has_b) {
         const R u0n = sqrt_(s.u0x * s.u0x + s.u0y * s.u0y + s.u0z * s.u0z);
         const R apar = fabs(F.a_par);
-        if (apar * dt > grow_max) dt = grow_max / apar;
+        if (apar * dt > grow_max) dt = grow_max * F.inv_apar;
         R wdt = F.w * dt;
         if (wdt > (R)2) wdt = (R)2;
         const R grow = apar * dt + u0n * wdt;  // |v(t) - v(t0)| <= |a_par| dt + |u0| min(2, w dt)
@@ -601,14 +627,14 @@ __device__ __forceinline__ void window_of(const Tab<R> &T, const Fld<R> &F, cons
         s_hi = min_(speed + grow, sqrt_(vp_hi * vp_hi + g_hi * g_hi));
         s_lo = max_(max_((R)0, speed - grow), sqrt_(vp_lo * vp_lo + g_lo * g_lo));
     } else {
-        if (F.a * dt > grow_max) dt = grow_max / F.a;
+        if (F.a * dt > grow_max) dt = grow_max * F.inv_a;
         const R grow = F.a * dt;
         s_hi = speed + grow;
         s_lo = max_((R)0, speed - grow);
     }
     const R m = max_(window_majorant(T, F.Ke * s_lo * s_lo, F.Ke * s_hi * s_hi) * (R)(1.0 + 1e-5), nu_floor_of<R>(P));
     nu_p = m;
-    inv_nu = (R)1 / m;
+    inv_nu = fdiv_((R)1, m);  // 2 ulp in FP32: the flights' rate is nu' to ~1e-7
     t_wend = t0 + dt;
 }
 

@@ -13,6 +13,14 @@ enum { DEC_WINDOW = -3, DEC_FAIL = -2, DEC_NULL = -1 };
 enum { TF_NONE = 0, TF_VARIABLE = 1, TF_BINNED = 2 };
 
 // Uniform static fields in the force frame (force on the electron along +z).
+// The field constants rounded to FP32 by the host, for the FP32 step: it
+// reads them as they are and never converts from FP64 in the loop (GB300
+// runs FP64, conversions included, at a small fraction of the FP32 rate).
+struct Fields32 {
+    float a, b0, b1, b2, w, inv_w, vD0, vD1, vD2, vDn, a_par, Ke;
+    float inv_a, inv_apar;  // 1/a and 1/|a_par| (0 where those vanish)
+};
+
 struct Fields {
     double a;        // eE/m [m/s^2]
     int32_t has_b;
@@ -20,6 +28,7 @@ struct Fields {
     double w;        // e|B|/m [rad/s]
     double vD[3];    // E x B drift (b x a z)/w
     double a_par;    // a (z . b)
+    Fields32 f32;
 };
 
 struct ParticlesDev {
