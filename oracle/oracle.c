@@ -766,6 +766,25 @@ static void collide(const or_mixture *m, const or_config *cf, uint64_t id, uint3
         *eps_f = keep * ef;
         return;
     }
+    /* The scattered direction.  Isotropic scattering (Sec. 2) sends the
+     * electron in a direction uniform on the sphere whatever its incident
+     * one, so that direction is taken in the lab frame from the same two
+     * draws (polar cosine cos_t, azimuth phi), and Eqs. (8)-(9) take the
+     * cosine between the incident and the new direction; the other angular
+     * models turn the incident direction by (cos_t, phi). */
+    double speed = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    double d[3] = {0.0, 0.0, 1.0};
+    if (speed > 0.0) { d[0] = v[0] / speed; d[1] = v[1] / speed; d[2] = v[2] / speed; }
+    double nd[3];
+    if (g->angular == OR_ISOTROPIC) {
+        double st = sqrt(fmax(0.0, 1.0 - cos_t * cos_t));
+        nd[0] = st * cos(phi);
+        nd[1] = st * sin(phi);
+        nd[2] = cos_t;
+        cos_t = d[0] * nd[0] + d[1] * nd[1] + d[2] * nd[2];
+    } else {
+        or_rotate(d, cos_t, phi, nd);
+    }
     if (ch->kind == OR_ELASTIC) {
         ratio = or_ratio_elastic(OR_ME, g->M, cos_t);
     } else if (ch->kind == OR_ATTACHMENT) {
@@ -786,11 +805,6 @@ static void collide(const or_mixture *m, const or_config *cf, uint64_t id, uint3
             *ion = 1;
         }
     }
-    double speed = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-    double d[3] = {0.0, 0.0, 1.0};
-    if (speed > 0.0) { d[0] = v[0] / speed; d[1] = v[1] / speed; d[2] = v[2] / speed; }
-    double nd[3];
-    or_rotate(d, cos_t, phi, nd);
     double sp = speed * sqrt(ratio);
     v[0] = sp * nd[0]; v[1] = sp * nd[1]; v[2] = sp * nd[2];
     *eps_f = ratio * eps;
