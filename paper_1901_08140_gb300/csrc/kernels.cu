@@ -1044,6 +1044,22 @@ __device__ __forceinline__ int trial(const Tab<R> &T, const Fld<R> &F, const Run
             } else {
                 ct = (R)1 - (R)2 * u2;
             }
+            // Isotropic scattering sends the electron in a direction uniform on
+            // the sphere whatever its incident one: the direction is drawn in
+            // the lab frame (polar cosine ct, the azimuth from w.w), which
+            // needs no frame about the incident direction, and Eqs. (8)-(9)
+            // take its cosine to the incident direction.
+            const bool lab = ang == BZ_ANG_ISOTROPIC && !(EXT && P.thermal && kind != BZ_ATTACHMENT);
+            R n0 = 0, n1 = 0, n2 = 0;
+            if (lab) {
+                const R st = sqrt_(max_((R)0, (R)1 - ct * ct));
+                R sp3, cp3;
+                azimuth(uni<R>(w.w), sp3, cp3);
+                n0 = st * cp3;
+                n1 = st * sp3;
+                n2 = ct;
+                ct = vsq > (R)0 ? (v0 * n0 + v1 * n1 + v2 * n2) * inv_sp : n2;
+            }
             R ratio;
             bool rotate = true;
             bool moved = false;  // moving targets: the new velocity is set directly
@@ -1100,6 +1116,10 @@ __device__ __forceinline__ int trial(const Tab<R> &T, const Fld<R> &F, const Run
             }
             const R nsp = sp * sqrt_(ratio);
             if (moved) {
+            } else if (rotate && lab) {
+                s.vr0 = nsp * n0;
+                s.vr1 = nsp * n1;
+                s.vr2 = nsp * n2;
             } else if (rotate) {
                 R d0 = v0 * inv_sp, d1 = v1 * inv_sp, d2 = v2 * inv_sp;
                 if (!(vsq > (R)0)) {

@@ -75,14 +75,24 @@ def test_fp32_statistics_match_the_fp64_oracle(ctx):
 
 
 def test_equal_cross_sections_scatter_isotropically(ctx):
-    """sigma_el = sigma_mt gives xi = 0: the same histories as isotropic scattering."""
+    """sigma_el = sigma_mt gives xi = 0, where Eq. 6 is the isotropic law.  The
+    isotropic gas draws its new direction in the lab frame and the xi gas
+    turns the incident one, so the swarms agree in distribution (every
+    statistic within 3.5 combined SE) and first flights agree to rounding."""
     base = W.co2_like()
     grid, s_mt = base.channels[0].energy_eV, base.channels[0].sigma_m2
     iso_xi = W.Gas("xi-iso", base.mass_kg, base.number_density_m3, W.XI_FORM, base.channels, sigma_el=(grid, s_mt))
-    kw = dict(n_electrons=1500, precision=64, e_over_n_Td=40.0, real_collisions=200, seed=63)
-    _, a, _ = _gpu(ctx, [base], **kw)
-    _, b, _ = _gpu(ctx, [iso_xi], **kw)
-    assert _paired(a, b).mean() > 0.99
+    kw = dict(n_electrons=20000, e_over_n_Td=40.0, real_collisions=200, seed=63)
+    ta, _, _ = _gpu(ctx, [base], **kw)
+    tb, _, _ = _gpu(ctx, [iso_xi], **kw)
+    for k in ["W", "eps", "eps_after", "D_L", "D_T"]:
+        assert abs(ta[k] - tb[k]) <= 3.5 * math.hypot(ta[k + "_se"], tb[k + "_se"]), k
+    one = dict(kw, n_electrons=3000, real_collisions=1, precision=64)
+    _, a, _ = _gpu(ctx, [base], **one)
+    _, b, _ = _gpu(ctx, [iso_xi], **one)
+    same = _paired(a, b)   # the two gases run different builds (lean, feature): FP64 rounding may differ
+    assert same.mean() > 0.999
+    assert np.allclose(a["z"][same], b["z"][same], rtol=1e-12, atol=1e-18)
 
 
 def test_batches_spawn_and_validation(ctx):
