@@ -35,7 +35,7 @@ UNIT = "real collisions/s"
 # Algorithmic thread operations of one trial step and the extra of a real
 # collision (counted from the method's arithmetic; see the design notes).
 ALG_OPS_PER_TRIAL = 95
-ALG_OPS_PER_REAL = 110
+ALG_OPS_PER_REAL = 90
 SM_COUNT_NOMINAL = 152
 LANES_PER_SM_CLOCK = 4 * 32     # 4 schedulers x 32 lanes issue per clock
 
