@@ -520,7 +520,7 @@ __device__ __forceinline__ void displacement(const Fld<R> &F, const PState<R> &s
 // with speed |v|, the speed stays within |v| +- g with g = a dt (B = 0) or
 // g = |a_par| dt + |u0| min(2, w dt) (B != 0: |u(t) - u(t0)| = 2|u0||sin(w(t-t0)/2)|),
 // so the maximum of nu over the energies [eps(|v|-g), eps(|v|+g)] -- read
-// from per-bin maxima of nu, one bin of margin on each side, plus a bound
+// from per-bin maxima of nu, 1/32 of a bin of margin on each side, plus a bound
 // of the power-law tails above the last union point -- is a trial frequency
 // that holds for the whole window.  A flight longer than the window stops
 // at its end and a new window starts there: by the memorylessness of the

@@ -128,9 +128,9 @@ cudaError_t launch_tallies(const TallyArgs &a, cudaStream_t s);
 // form of the angle; the lean instance (the hot path of Lazy, Fixed and
 // windowed swarms in mixtures without xi-form gases) compiles without them.
 // wide: the 4-block build of the lean FP32 kernel may be taken (where its
-// blocks fit); callers allow it for single-gas mixtures.  bfield: some swarm
-// of the launch has a magnetic field (else the lean build without the
-// field's paths runs).
+// blocks fit); callers allow it without B, and with B for single-gas
+// mixtures.  bfield: some swarm of the launch has a magnetic field (else the
+// lean build without the field's paths runs).
 cudaError_t launch_batch(int precision, bool ch_smem, bool ext, bool wide, bool bfield, const BatchArgs &a,
                          size_t smem, int grid, int block, cudaStream_t s);
 // Spawn mode: one persistent launch runs the primaries and every electron
