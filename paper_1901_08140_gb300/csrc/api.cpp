@@ -279,6 +279,10 @@ bz_status prepare_run(const bz_mixture *mix, const bz_swarm_config *cfg, bz::Run
         return fail(BZ_EBUDGET, "mixture tables exceed the shared memory of one block");
     a->key0 = (uint32_t)cfg->seed;
     a->key1 = (uint32_t)(cfg->seed >> 32);
+    for (uint32_t r = 0; r < 10; ++r) {  // Philox round keys, read by the step instead of stepped
+        a->rk[2 * r] = a->key0 + r * 0x9E3779B9u;
+        a->rk[2 * r + 1] = a->key1 + r * 0xBB67AE85u;
+    }
     a->id_offset = cfg->id_offset;
     a->n = cfg->n_electrons;
     a->I = cfg->real_collisions;

@@ -68,6 +68,25 @@ __device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, u
     return make_uint4(c0, c1, c2, c3);
 }
 
+// The same generator with the round keys read from the swarm's parameters
+// (precomputed by the host) instead of stepped in registers on every call:
+// the step draws once per trial, and the 20 key additions were a few per
+// cent of its instructions.
+__device__ __forceinline__ uint4 philox_rk(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, const uint32_t *rk)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+        const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+        const uint32_t n0 = hi1 ^ c1 ^ rk[2 * r], n2 = hi0 ^ c3 ^ rk[2 * r + 1];
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+    }
+    return make_uint4(c0, c1, c2, c3);
+}
+
 // ((w >> 9) + 1/2) 2^-23: an odd multiple of 2^-24 in (0,1), exact in FP32.
 template <typename R>
 __device__ __forceinline__ R uni(uint32_t w)
@@ -918,7 +937,7 @@ __device__ __forceinline__ int trial(const Tab<R> &T, const Fld<R> &F, const Run
                                      R &eps_f)
 {
     const uint32_t step = s.k++;
-    const uint4 w = philox(s.id_lo, s.id_hi, step, 0u, P.key0, P.key1);
+    const uint4 w = philox_rk(s.id_lo, s.id_hi, step, 0u, P.rk);
     // Eq. (3): the draw stands for 1 - R
     R Tn = s.T - log_(uni<R>(w.x)) * s.inv_nu;
     // a flight that outlasts the window stops at its end (its nu' holds only there) ...
@@ -1071,7 +1090,7 @@ __device__ __forceinline__ int trial(const Tab<R> &T, const Fld<R> &F, const Run
                 const R efl = F.Ke * (t0 * t0 + t1 * t1 + t2 * t2);
                 R keep = 1;
                 if (kind == BZ_IONIZATION) {  // the secondary takes u4 of the lab energy
-                    const uint4 w2 = philox(s.id_lo, s.id_hi, step, 1u, P.key0, P.key1);
+                    const uint4 w2 = philox_rk(s.id_lo, s.id_hi, step, 1u, P.rk);
                     const R u4 = uni<R>(w2.x);
                     if (P.spawn)
                         spawn_secondary(P, F.Ke, s.t0 + s.t.value(), ((uint64_t)s.id_hi << 32) | s.id_lo, step,
@@ -1105,7 +1124,7 @@ __device__ __forceinline__ int trial(const Tab<R> &T, const Fld<R> &F, const Run
                 const R rad = max_((R)0, (R)1 - p.minv * x);
                 ratio = max_((R)0, (R)1 - p.mfrac * x + p.kappa2 * (sqrt_(rad) * ct - (R)1));
                 if (kind == BZ_IONIZATION) {
-                    const uint4 w2 = philox(s.id_lo, s.id_hi, step, 1u, P.key0, P.key1);
+                    const uint4 w2 = philox_rk(s.id_lo, s.id_hi, step, 1u, P.rk);
                     const R u4 = uni<R>(w2.x);
                     if (P.spawn)
                         spawn_secondary(P, F.Ke, s.t0 + s.t.value(), ((uint64_t)s.id_hi << 32) | s.id_lo, step,

@@ -42,6 +42,7 @@ struct RunArgs {
     Layout lay;
     uint32_t stage_bytes;    // prefix of the blob staged into shared memory
     uint32_t key0, key1;     // Philox key (swarm seed)
+    uint32_t rk[20];         // its round keys: key + r (0x9E3779B9, 0xBB67AE85), r = 0..9
     uint64_t id_offset, n;
     uint32_t I;              // real collisions per particle
     int32_t fixed;           // fixed trial frequency: a fail stops the particle
