@@ -140,6 +140,14 @@ def profiled_traffic():
     return rec["dram_bytes_read"] + rec["dram_bytes_write"]
 
 
+def workload_name(args):
+    """The workload both arms name in their JSON line (the same swarms; how
+    each arm samples them is in its own keys)."""
+    return (f"Argon-like E/N sweep: {args.points} log points 1-1000 Td x {args.electrons} electrons x "
+            f"{args.collisions} real collisions, FP32 flights, FP64 tallies, {args.trial} trial frequency, B = 0"
+            + (f" (point {args.only_point} only)" if args.only_point >= 0 else ""))
+
+
 def sweep_specs(args, rank):
     from paper_1901_08140_gb300 import workloads as W
     specs = W.argon_sweep(n_electrons=args.electrons, real_collisions=args.collisions, points=args.points)
@@ -458,10 +466,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"Argon-like E/N sweep: {args.points} log points 1-1000 Td x "
-                               f"{args.electrons} electrons x {args.collisions} real collisions, "
-                               f"FP32 flights, FP64 tallies, {args.trial} trial frequency, B = 0"
-                               + (f" (point {args.only_point} only)" if args.only_point >= 0 else ""),
+        "config": {"workload": workload_name(args),
                    "mode": "batched: all swarms in one persistent launch replayed from a CUDA graph",
                    "swarms": len(specs), "electrons_per_swarm": args.electrons, "real_collisions": args.collisions,
                    "l2": "flushed between steps (256 MiB write)", "parallelism": f"dp{world} (particle ids)",
@@ -517,15 +522,12 @@ def run_reference(args):
     dt = time.perf_counter() - t0
     value = reals / dt
     sample = (f"per step: all {len(specs)} E/N points x {block} electrons x I={specs[0].real_collisions} "
-              f"(FP64 oracle, {cores} threads)")
+              f"(FP64 oracle, Lazy exact trial frequency, {cores} threads)")
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-        "config": {"workload": f"Argon-like E/N sweep: {args.points} log points 1-1000 Td x "
-                               f"{args.electrons} electrons x {args.collisions} real collisions, "
-                               "FP32 flights, FP64 tallies, lazy exact trial frequency, B = 0",
-                   "sample": sample},
+        "config": {"workload": workload_name(args), "sample": sample},
         "trial_collisions_per_s": trials / dt,
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
