@@ -22,6 +22,11 @@ constexpr int kMaxGases = 16;  // gases per mixture
 constexpr int kGroups = 32;   // batch groups for standard errors (id mod 32)
 constexpr int kQ1 = 21;       // first-pass tally quantities
 constexpr int kQ2 = 8;        // second-pass tally quantities
+// Shared-memory budgets of a mixture's staged tables: three FP32 step blocks
+// of 256 threads per SM (each also holds ~2 KB of static and reserved shared
+// memory out of a GB300 SM's 228 KB), and one FP64 block.
+constexpr size_t kStageBudget32 = 72 * 1024;
+constexpr size_t kStageBudget64 = 200 * 1024;
 
 // One interval [e_lo, e_hi) of the union energy grid: the density sum
 // S(eps) = sum n_k sigma_kj(eps) of all channels not in their power-law
@@ -53,19 +58,31 @@ struct alignas(2 * sizeof(R)) ChVal {
 };
 
 // Where each section of a compiled mixture sits in its device blob.  The
-// blob is [records | buckets | channel params | bin maxima | channel
-// values]; the prefix up to stage_tables (or stage_all) is copied into
-// shared memory.  Bin maxima: the maximum of nu(eps) over each of n_bins
-// log-uniform energy bins from 2^bin_lo to the last union point (windowed
-// trial frequency); nu_low is the maximum below the first bin.
+// blob is [records | buckets | channel params | bin maxima | channel values
+// | per-gas sums | xi tables | cumulative channel values]; the prefix up to
+// stage_tables (or stage_all) is copied into shared memory.  Bin maxima: the
+// maximum of nu(eps) over each of n_bins log-uniform energy bins from
+// 2^bin_lo to the last union point (windowed trial frequency); nu_low is the
+// maximum below the first bin.  The compiler sizes the bucket index (1 to 4
+// entries per record) and decides whether the bin maxima are staged so that
+// stage_tables fits a shared-memory budget (the step kernels then keep
+// three blocks per SM); bin maxima outside the staged prefix are read from
+// global memory through L1.
 struct Layout {
     int32_t n_rec, n_buckets, n_ch, first_tail_rec;
     float log2_lo, inv_bw;
     uint32_t off_bucket, off_chp, off_chval;
-    uint32_t stage_tables;   // bytes of records + buckets + channel params + bin maxima
-    uint32_t stage_all;      // + channel values
+    uint32_t stage_tables;   // bytes of records + buckets + channel params (+ bin maxima when they fit)
+    uint32_t stage_all;      // everything but the cumulative channel values
     uint32_t total;
     uint32_t off_bin;
+    uint32_t bin_end;        // off_bin + bytes of the bin maxima: staged iff the staged prefix reaches it
+    // cumulative channel values per record ({val, slope}, n_rec x n_ch, in
+    // the order of Eq. 2): entry j is the sum of channels 0..j, searched by
+    // bisection on real collisions when the channel values are not staged
+    uint32_t off_cum;
+    int32_t buckets_per_record;
+    double s_min;            // speed at the first bin edge [m/s]
     int32_t n_bins, bin_levels;  // sparse table: level l at [l * n_bins + b] = max over bins [b, b + 2^l)
     float bin_lo, inv_binw;  // log2 energy of the first bin edge, bins per unit log2
     double nu_low;           // max nu over [0, 2^bin_lo]
@@ -95,6 +112,15 @@ struct CompiledMixture {
 
 // Sets the calling thread's message returned by bz_last_error (api.cpp).
 void set_last_error(const std::string &msg);
+
+// Context and configuration queries shared by the C ABI's translation units
+// (api.cpp): the context's CUDA device; the checks bz_run_swarm applies to a
+// configuration (BZ_OK or BZ_EINVAL with the message set); whether a swarm
+// runs in the step kernel's feature instance (the paper's adaptive trial
+// frequencies, xi-form gases or moving targets).
+int ctx_device(const bz_ctx *ctx);
+bz_status check_config(const bz_swarm_config *cfg);
+bool needs_feature_instance(const bz_mixture *mix, const bz_swarm_config *cfg);
 
 // Host mixture compiler (mixture.cpp).  Returns BZ_OK or an error with *err.
 bz_status compile_mixture(const bz_gas *gases, int32_t n_gases, const bz_mixture_opts *opts,

@@ -184,35 +184,43 @@ struct Tab {
     const uint16_t *bucket;
     const ChParam<R> *chp;
     const ChVal<R> *chval;
+    const ChVal<R> *cum;   // cumulative channel values (global memory)
     const R *binmax;  // sparse table of per-bin maxima (level-major)
     const ChVal<R> *gval;  // per-record, per-gas density sums (global memory)
     const Layout *lay;     // gas channel ranges
     int n_rec, n_buckets, n_ch, first_tail, n_bins, n_gases;
+    int ch_steps;          // bisection steps over n_ch channels: ceil(log2 n_ch)
     float log2_lo, inv_bw, bin_lo, inv_binw;
     R nu_low, g_top, s_min;  // s_min: speed at the first bin edge [m/s]
 };
 
+// Table views of a mixture: the staged prefix (`staged` bytes) in shared
+// memory, the rest in global memory.  Every constant comes from the host's
+// layout, so setting up a tile does no FP64 arithmetic.
 template <typename R>
-__device__ __forceinline__ Tab<R> make_tab(const uint8_t *smem, const uint8_t *blob, const Layout &L, bool ch_smem)
+__device__ __forceinline__ Tab<R> make_tab(const uint8_t *smem, const uint8_t *blob, const Layout &L, bool ch_smem,
+                                           uint32_t staged)
 {
     Tab<R> T;
     T.rec = (const Rec<R> *)smem;
     T.bucket = (const uint16_t *)(smem + L.off_bucket);
     T.chp = (const ChParam<R> *)(smem + L.off_chp);
     T.chval = (const ChVal<R> *)((ch_smem ? smem : blob) + L.off_chval);
+    T.cum = (const ChVal<R> *)(blob + L.off_cum);
     T.n_rec = L.n_rec;
     T.n_buckets = L.n_buckets;
     T.n_ch = L.n_ch;
+    T.ch_steps = L.n_ch > 1 ? 32 - __clz(L.n_ch - 1) : 0;
     T.first_tail = L.first_tail_rec;
     T.log2_lo = L.log2_lo;
     T.inv_bw = L.inv_bw;
-    T.binmax = (const R *)(smem + L.off_bin);
+    T.binmax = (const R *)((staged >= L.bin_end ? smem : blob) + L.off_bin);
     T.n_bins = L.n_bins;
     T.bin_lo = L.bin_lo;
     T.inv_binw = L.inv_binw;
     T.nu_low = (R)L.nu_low;
     T.g_top = (R)L.g_top;
-    T.s_min = (R)sqrt(exp2((double)L.bin_lo) * 2.0 * kQe / kMe);
+    T.s_min = (R)L.s_min;
     T.gval = (const ChVal<R> *)(blob + L.off_gval);
     T.lay = &L;
     T.n_gases = L.n_gases;
@@ -250,24 +258,67 @@ __device__ __forceinline__ R density(const Tab<R> &T, R eps, int &ri, R &e_lo)
     return S;
 }
 
+// One {val, slope} pair: from shared memory, or from global memory in one
+// 8-byte (FP32) or 16-byte (FP64) read-only load.
+__device__ __forceinline__ ChVal<float> ldg_chval(const ChVal<float> *p)
+{
+    const float2 v = __ldg(reinterpret_cast<const float2 *>(p));
+    ChVal<float> c;
+    c.val = v.x;
+    c.slope = v.y;
+    return c;
+}
+__device__ __forceinline__ ChVal<double> ldg_chval(const ChVal<double> *p)
+{
+    const double2 v = __ldg(reinterpret_cast<const double2 *>(p));
+    ChVal<double> c;
+    c.val = v.x;
+    c.slope = v.y;
+    return c;
+}
+
 template <typename R>
 __device__ __forceinline__ ChVal<R> load_chval(const ChVal<R> *p, bool ch_smem)
 {
     if (ch_smem) return *p;
-    ChVal<R> v;
-    v.val = __ldg(&p->val);
-    v.slope = __ldg(&p->slope);
-    return v;
+    return ldg_chval(p);
 }
 
 // First channel whose cumulative density reaches `target` (= R nu'/|v|),
 // in the order of Eq. (2): gas by gas, channel by channel.  Outside the
 // power-law tails the search is two-level: per-gas sums find the gas, then
 // that gas's channels are scanned (the same cumulative partition).
+//
+// Where the channel values are not staged (many channels, read through L1
+// from global memory), the search runs on the record's cumulative values
+// instead: the first j whose cumulative value reaches the target, found by
+// bisection in ceil(log2 n_ch) steps.  The step count depends on the mixture
+// only, so the lanes of a warp that collide run the search together (a
+// channel-by-channel scan would keep the warp for its slowest lane), and
+// each step is one 8-byte load.  (A 16-ary search tree with two levels took
+// two trips to L2 instead of up to eight, but read four times the bytes and
+// needed more registers: 12 % slower on the 256-swarm workload.)  The
+// target is first clamped to the record's total: where rounding leaves it a
+// hair above, the search lands on the last channel that adds to the total
+// (the first entry equal to it).
 template <typename R, bool CH_SMEM>
 __device__ __forceinline__ int select_channel(const Tab<R> &T, int ri, R e_lo, R eps, R target)
 {
     const R de = eps - e_lo;
+    if (!CH_SMEM && ri < T.first_tail) {
+        const ChVal<R> *row = T.cum + (size_t)ri * T.n_ch;
+        const ChVal<R> top = ldg_chval(row + T.n_ch - 1);
+        target = min_(target, top.val + top.slope * de);
+        int base = 0, len = T.n_ch;
+        // the answer lies in [base, base + len): each step halves len
+        for (int k = 0; k < T.ch_steps; ++k) {
+            const int half = len >> 1;
+            const ChVal<R> c = ldg_chval(row + base + half - 1);
+            if (c.val + c.slope * de < target) base += half;
+            len -= half;
+        }
+        return base;
+    }
     if (ri < T.first_tail && T.n_gases > 1) {
         const ChVal<R> *grow = T.gval + (size_t)ri * T.n_gases;
         R cum = 0;
@@ -555,6 +606,20 @@ template <>
 __device__ __forceinline__ float nu_floor_of<float>(const RunArgs &P) { return P.nu_floor32; }
 template <>
 __device__ __forceinline__ double nu_floor_of<double>(const RunArgs &P) { return P.nu_floor; }
+// The Maxwellian start's per-component spread and the starting nu', in the
+// step's precision (the FP32 step reads the host's FP32 copies).
+template <typename R>
+__device__ __forceinline__ R v0_scale_of(const RunArgs &P);
+template <>
+__device__ __forceinline__ float v0_scale_of<float>(const RunArgs &P) { return P.v0_scale32; }
+template <>
+__device__ __forceinline__ double v0_scale_of<double>(const RunArgs &P) { return P.v0_scale; }
+template <typename R>
+__device__ __forceinline__ R nu0_of(const RunArgs &P);
+template <>
+__device__ __forceinline__ float nu0_of<float>(const RunArgs &P) { return P.nu0_32; }
+template <>
+__device__ __forceinline__ double nu0_of<double>(const RunArgs &P) { return P.nu0; }
 template <typename R>
 __device__ __forceinline__ R kT_m_of(const RunArgs &P);
 template <>
@@ -746,7 +811,7 @@ __device__ __forceinline__ void init_particle(const Tab<R> &T, const RunArgs &P,
     s.id_hi = (uint32_t)(id >> 32);
     const uint4 w = philox(s.id_lo, s.id_hi, 0u, 2u, P.key0, P.key1);
     // isotropic Maxwellian with mean energy eps0 = 3/2 kT (Box-Muller)
-    const R sv = (R)sqrt((2.0 / 3.0) * P.eps0_mean * kQe / kMe);
+    const R sv = v0_scale_of<R>(P);
     const R r0 = sqrt_((R)-2 * log_(uni<R>(w.x))), r1 = sqrt_((R)-2 * log_(uni<R>(w.z)));
     R s1, c1, s3, c3;
     sincospi_((R)2 * uni<R>(w.y), &s1, &c1);
@@ -755,7 +820,7 @@ __device__ __forceinline__ void init_particle(const Tab<R> &T, const RunArgs &P,
     s.vr1 = sv * r0 * s1;
     s.vr2 = sv * r1 * c3;
     s.T = 0;
-    s.nu_p = (R)P.nu0;
+    s.nu_p = nu0_of<R>(P);
     s.inv_nu = (R)1 / s.nu_p;
     s.x.set(0.0);
     s.y.set(0.0);
@@ -787,7 +852,7 @@ __device__ __forceinline__ void init_secondary(const Tab<R> &T, const RunArgs &P
     s.vr1 = (R)__ldcg(P.bvy + j);
     s.vr2 = (R)__ldcg(P.bvz + j);
     s.T = 0;
-    s.nu_p = (R)P.nu0;
+    s.nu_p = nu0_of<R>(P);
     s.inv_nu = (R)1 / s.nu_p;
     s.x.set(0.0);
     s.y.set(0.0);
@@ -1409,7 +1474,7 @@ __global__ void __launch_bounds__(kBlock, MINB) batch_kernel(const __grid_consta
             phase ^= 1u;
             staged = P.blob;
         }
-        const Tab<R> T = make_tab<R>(smem, P.blob, P.lay, CH_SMEM);
+        const Tab<R> T = make_tab<R>(smem, P.blob, P.lay, CH_SMEM, P.stage_bytes);
         const Fld<R> F = make_fld<R>(P.f);
         PState<R> s;
         bool have = false, exhausted = false;
@@ -1489,7 +1554,7 @@ __global__ void __launch_bounds__(kBlock, MINB) spawn_kernel(const __grid_consta
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ __align__(8) uint64_t mbar;
     if (!stage_tables(P.blob, smem, P.stage_bytes, &mbar, P.err)) return;
-    const Tab<R> T = make_tab<R>(smem, P.blob, P.lay, CH_SMEM);
+    const Tab<R> T = make_tab<R>(smem, P.blob, P.lay, CH_SMEM, P.stage_bytes);
     const Fld<R> F = make_fld<R>(P.f);
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -1583,7 +1648,7 @@ __global__ void __launch_bounds__(kBlock) replay_kernel(const ReplayArgs A)
     __shared__ __align__(8) uint64_t mbar;
     const RunArgs &P = A.run;
     if (!stage_tables(P.blob, smem, P.stage_bytes, &mbar, P.err)) return;
-    const Tab<R> T = make_tab<R>(smem, P.blob, P.lay, CH_SMEM);
+    const Tab<R> T = make_tab<R>(smem, P.blob, P.lay, CH_SMEM, P.stage_bytes);
     const Fld<R> F = make_fld<R>(P.f);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < A.n; i += (int64_t)gridDim.x * blockDim.x) {
         const double *in = A.state_in + 8 * i;

@@ -49,6 +49,8 @@ struct RunArgs {
     int32_t attach_keep;
     double nu0;              // starting trial frequency
     double eps0_mean;        // Maxwellian start, mean energy [eV]
+    double v0_scale;         // sqrt(2 eps0_mean / (3 m)) [m/s]: the Maxwellian's per-component spread
+    float v0_scale32, nu0_32;  // it and nu0 rounded to FP32 by the host, for the FP32 step
     double t_end;            // > 0: time limit [s]
     uint64_t max_trials;
     int32_t window;          // windowed local trial frequency

@@ -99,27 +99,76 @@ struct ElTabs {
     std::vector<ChParam<double>> tail;            // [n_gases]
 };
 
-template <typename R>
-void emit(const std::vector<Chan> &ch, const std::vector<double> &g, const std::vector<double> &Slo,
-          const std::vector<double> &Ssl, const std::vector<std::vector<double>> &cv,
-          const std::vector<std::vector<double>> &cs, const std::vector<uint16_t> &bucket,
-          const std::vector<ChParam<double>> &cp, int first_tail, float log2_lo, float inv_bw, const Bins &bins,
-          const ElTabs &el, std::vector<uint8_t> *blob, Layout *lay)
+// Log-energy bucket index with k buckets per union point (record i holds
+// [g[i-1], g[i]) for i >= 1, [0, g[0]) for i = 0).
+struct BucketIndex {
+    std::vector<uint16_t> bucket;
+    float log2_lo, inv_bw;
+};
+
+BucketIndex bucket_index(const std::vector<double> &g, int k)
 {
-    const int n_rec = (int)Slo.size(), n_ch = (int)ch.size(), nb = (int)bucket.size();
+    const int P = (int)g.size();
+    int ipos = 0;
+    while (ipos < P && g[ipos] <= 0.0) ++ipos;
+    double L0 = (ipos < P) ? log2(g[ipos]) : 0.0, L1 = log2(g[P - 1] > 0.0 ? g[P - 1] : 1.0);
+    int nb = std::min(std::max(k * P, 64), 65535);
+    double w = (L1 > L0) ? (L1 - L0) / nb : 0.0;
+    if (w == 0.0) nb = 1;
+    BucketIndex B;
+    B.bucket.resize(nb);
+    for (int b = 0; b < nb; ++b) {
+        double e = exp2(L0 + b * w);
+        B.bucket[b] = (uint16_t)(std::upper_bound(g.begin(), g.end(), e) - g.begin());
+    }
+    B.log2_lo = (float)L0;
+    B.inv_bw = (w > 0.0) ? (float)(1.0 / w) : 0.0f;
+    return B;
+}
+
+// Emits the blob of one precision.  The bucket index takes as many entries
+// per record (4, 3, 2 or 1) as let records + buckets + channel params + bin
+// maxima fit `budget` bytes of shared memory; if none does, the bin maxima
+// stay in global memory and the densest index that fits is taken.  Four per
+// record land the walk on the right record almost always (a walk step costs
+// the whole warp); fewer keep large mixtures at three blocks per SM.
+template <typename R>
+bool emit(const std::vector<Chan> &ch, const std::vector<double> &g, const std::vector<double> &Slo,
+          const std::vector<double> &Ssl, const std::vector<std::vector<double>> &cv,
+          const std::vector<std::vector<double>> &cs, const std::vector<ChParam<double>> &cp, int first_tail,
+          const Bins &bins, const ElTabs &el, size_t budget, std::vector<uint8_t> *blob, Layout *lay,
+          std::string *err_out)
+{
+    const int n_rec = (int)Slo.size(), n_ch = (int)ch.size();
     const int n_bins = bins.n_bins, n_bin_vals = (int)bins.max.size();
     auto pad16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
     size_t off_rec = 0;
-    size_t off_bucket = pad16(off_rec + sizeof(Rec<R>) * n_rec);
+    const size_t off_bucket = pad16(off_rec + sizeof(Rec<R>) * n_rec);
+    auto prefix = [&](int k, bool with_bins) {
+        const int nb = std::min(std::max(k * (int)g.size(), 64), 65535);
+        const size_t ob = pad16(pad16(off_bucket + sizeof(uint16_t) * nb) + sizeof(ChParam<R>) * n_ch);
+        return with_bins ? ob + sizeof(R) * n_bin_vals : ob;
+    };
+    int k = 0;
+    for (int kk = 4; kk >= 1 && !k; --kk)
+        if (prefix(kk, true) <= budget) k = kk;
+    for (int kk = 4; kk >= 1 && !k; --kk)
+        if (prefix(kk, false) <= budget) k = kk;
+    if (!k) k = 1;
+    const BucketIndex BI = bucket_index(g, k);
+    const std::vector<uint16_t> &bucket = BI.bucket;
+    const int nb = (int)bucket.size();
     size_t off_chp = pad16(off_bucket + sizeof(uint16_t) * nb);
     size_t off_bin = pad16(off_chp + sizeof(ChParam<R>) * n_ch);
-    size_t off_chval = pad16(off_bin + sizeof(R) * n_bin_vals);
+    const size_t bin_end = off_bin + sizeof(R) * n_bin_vals;
+    size_t off_chval = pad16(bin_end);
     size_t off_gval = pad16(off_chval + sizeof(ChVal<R>) * (size_t)n_rec * n_ch);
     int n_gases = 0;
     for (const Chan &c : ch) n_gases = std::max(n_gases, c.gas + 1);
     size_t off_elval = pad16(off_gval + sizeof(ChVal<R>) * (size_t)n_rec * n_gases);
     size_t off_elp = pad16(off_elval + sizeof(ChVal<R>) * (size_t)n_rec * n_gases);
-    size_t total = pad16(off_elp + sizeof(ChParam<R>) * (size_t)n_gases);
+    size_t off_cum = pad16(off_elp + sizeof(ChParam<R>) * (size_t)n_gases);
+    size_t total = pad16(off_cum + sizeof(ChVal<R>) * (size_t)n_rec * n_ch);
     blob->assign(total, 0);
     Rec<R> *rec = (Rec<R> *)(blob->data() + off_rec);
     for (int i = 0; i < n_rec; ++i) {
@@ -188,19 +237,36 @@ void emit(const std::vector<Chan> &ch, const std::vector<double> &g, const std::
         lay->gas_first[ch[j].gas] = (int16_t)j;
         lay->gas_count[ch[j].gas] += 1;
     }
+    // cumulative channel values: running FP64 sums in the order of Eq. 2,
+    // rounded once, so that entry j reaches the record's density sum at j =
+    // n_ch - 1 and never decreases where a channel adds nothing
+    ChVal<R> *cu = (ChVal<R> *)(blob->data() + off_cum);
+    for (int i = 0; i < n_rec; ++i) {
+        double a = 0.0, b = 0.0;
+        for (int j = 0; j < n_ch; ++j) {
+            a += cv[i][j];
+            b += cs[i][j];
+            cu[(size_t)i * n_ch + j].val = (R)a;
+            cu[(size_t)i * n_ch + j].slope = (R)b;
+        }
+    }
     lay->n_rec = n_rec;
     lay->n_buckets = nb;
     lay->n_ch = n_ch;
     lay->first_tail_rec = first_tail;
-    lay->log2_lo = log2_lo;
-    lay->inv_bw = inv_bw;
+    lay->log2_lo = BI.log2_lo;
+    lay->inv_bw = BI.inv_bw;
+    lay->buckets_per_record = k;
     lay->off_bucket = (uint32_t)off_bucket;
     lay->off_chp = (uint32_t)off_chp;
     lay->off_chval = (uint32_t)off_chval;
-    lay->stage_tables = (uint32_t)off_chval;
-    lay->stage_all = (uint32_t)total;
+    lay->stage_tables = (uint32_t)(bin_end <= budget ? bin_end : off_bin);
+    lay->stage_all = (uint32_t)off_cum;
     lay->total = (uint32_t)total;
     lay->off_bin = (uint32_t)off_bin;
+    lay->bin_end = (uint32_t)bin_end;
+    lay->off_cum = (uint32_t)off_cum;
+    lay->s_min = sqrt(exp2((double)bins.lo) * 2.0 * kQe / kMe);
     lay->n_bins = n_bins;
     lay->bin_levels = bins.levels;
     lay->bin_lo = bins.lo;
@@ -211,6 +277,7 @@ void emit(const std::vector<Chan> &ch, const std::vector<double> &g, const std::
     lay->low_sqrt = bins.low_sqrt ? 1 : 0;
     lay->nu_first = bins.nu_first;
     lay->g_top = g.back();
+    return true;
 }
 
 bool finite(double x) { return std::isfinite(x); }
@@ -420,23 +487,8 @@ bz_status compile_mixture(const bz_gas *gases, int32_t n_gases, const bz_mixture
         }
     }
     double guard = (opts && opts->majorant_guard >= 0.0) ? opts->majorant_guard : 1e-6;
-    // bucket index over log2 energy of the positive union points: four
-    // buckets per record, so that the walk from a bucket's first record to
-    // the one holding eps rarely takes a step (a step costs the whole warp)
-    int ipos = 0;
+    int ipos = 0;  // first positive union point
     while (ipos < P && g[ipos] <= 0.0) ++ipos;
-    double L0 = (ipos < P) ? log2(g[ipos]) : 0.0, L1 = log2(g[P - 1] > 0.0 ? g[P - 1] : 1.0);
-    int nb = std::min(std::max(4 * P, 64), 65535);
-    double w = (L1 > L0) ? (L1 - L0) / nb : 0.0;
-    if (w == 0.0) nb = 1;
-    std::vector<uint16_t> bucket(nb);
-    for (int b = 0; b < nb; ++b) {
-        double e = exp2(L0 + b * w);
-        // record i holds [g[i-1], g[i]) for i >= 1, [0, g[0]) for i = 0
-        int i = (int)(std::upper_bound(g.begin(), g.end(), e) - g.begin());
-        bucket[b] = (uint16_t)i;
-    }
-    float log2_lo = (float)L0, inv_bw = (w > 0.0) ? (float)(1.0 / w) : 0.0f;
 
     // Maximum of nu over each log-uniform energy bin (32 per decade) between
     // the first positive union point and the last one, exact per record:
@@ -534,10 +586,13 @@ bz_status compile_mixture(const bz_gas *gases, int32_t n_gases, const bz_mixture
         }
     }
 
-    emit<float>(ch, g, Slo, Ssl, cv, cs, bucket, cp, first_tail, log2_lo, inv_bw, bins, elt, &out->blob32,
-                &out->lay32);
-    emit<double>(ch, g, Slo, Ssl, cv, cs, bucket, cp, first_tail, log2_lo, inv_bw, bins, elt, &out->blob64,
-                 &out->lay64);
+    // shared-memory budgets of the staged tables: three FP32 blocks per SM
+    // (72 KB each on a GB300's 228 KB), one FP64 block
+    const size_t budget32 = (opts && opts->smem_budget > 0) ? (size_t)opts->smem_budget : kStageBudget32;
+    if (!emit<float>(ch, g, Slo, Ssl, cv, cs, cp, first_tail, bins, elt, budget32, &out->blob32, &out->lay32, err) ||
+        !emit<double>(ch, g, Slo, Ssl, cv, cs, cp, first_tail, bins, elt, kStageBudget64, &out->blob64, &out->lay64,
+                      err))
+        return BZ_EINVAL;
     out->n_total = n_total;
     out->nu_max = best;
     out->nu_trial = best * (1.0 + guard);
@@ -552,7 +607,7 @@ bz_status compile_mixture(const bz_gas *gases, int32_t n_gases, const bz_mixture
     I.n_gases = n_gases;
     I.n_channels = n_ch;
     I.n_records = n_rec;
-    I.n_buckets = nb;
+    I.n_buckets = out->lay32.n_buckets;
     I.first_tail_record = first_tail;
     return BZ_OK;
 }
