@@ -6,6 +6,7 @@ plausible slip (dropped term, wrong sign, swapped operand, wrong index) in
 the corresponding oracle function fails.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -46,6 +47,60 @@ def test_philox_uniformity_and_independence():
     # every 32-bit output bit is balanced
     bits = ((w[:, :, None] >> np.arange(32, dtype=np.uint64)) & 1).reshape(-1, 32).mean(axis=0)
     assert np.all(np.abs(bits - 0.5) < 5 * 0.5 / math.sqrt(w.size))
+
+
+def _curand_host_philox(seed: int, n_blocks: int) -> np.ndarray:
+    """The first n_blocks x 4 words of cuRAND's host-side Philox4_32_10
+    generator seeded with `seed` (NVIDIA's implementation of the same
+    published generator), or None where libcurand is not installed."""
+    import ctypes
+    import ctypes.util
+    paths = [os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "lib64", "libcurand.so"),
+             ctypes.util.find_library("curand")]
+    lib = None
+    for p in paths:
+        try:
+            lib = ctypes.CDLL(p) if p else None
+        except OSError:
+            lib = None
+        if lib is not None:
+            break
+    if lib is None:
+        return None
+    gen = ctypes.c_void_p()
+    CURAND_RNG_PSEUDO_PHILOX4_32_10 = 161
+    assert lib.curandCreateGeneratorHost(ctypes.byref(gen), CURAND_RNG_PSEUDO_PHILOX4_32_10) == 0
+    try:
+        assert lib.curandSetPseudoRandomGeneratorSeed(gen, ctypes.c_ulonglong(seed)) == 0
+        out = np.zeros(4 * n_blocks, np.uint32)
+        assert lib.curandGenerate(gen, out.ctypes.data_as(ctypes.c_void_p), ctypes.c_size_t(out.size)) == 0
+    finally:
+        lib.curandDestroyGenerator(gen)
+    return out.reshape(-1, 4)
+
+
+def test_philox_identity_against_curand():
+    """Known answers of Philox4x32-10 (Salmon et al. 2011) from an
+    implementation that is not this project's: cuRAND's host generator.
+    Seeded with s, its block k is Philox at counter (k div 65536, 0, k mod
+    65536, 0) under the key (s mod 2^32, s div 2^32).  Over two sweeps of
+    the third counter word and three keys this fixes the multipliers, the
+    Weyl constants of the key schedule, the word permutation of a round and
+    the number of rounds: swapping two multipliers or two high words, or a
+    wrong Weyl constant, changes every block."""
+    n = 2 * 65536 + 8
+    for seed in (0, 0x0123456789ABCDEF, 0xFFFFFFFFFFFFFFFF):
+        ref = _curand_host_philox(seed, n)
+        if ref is None:
+            pytest.skip("libcurand is not installed")
+        key = [seed & 0xFFFFFFFF, seed >> 32]
+        rng = np.random.default_rng(seed & 0xFFFF)
+        ks = np.concatenate([np.arange(0, 64), np.arange(65530, 65542), np.arange(131068, n),
+                             rng.integers(0, n, 400)])
+        for k in ks:
+            k = int(k)
+            got = O.philox([k // 65536, 0, k % 65536, 0], key)
+            assert np.array_equal(got, ref[k]), (seed, k, got, ref[k])
 
 
 def test_philox_counter_and_key_avalanche():
