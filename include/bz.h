@@ -34,7 +34,7 @@
 extern "C" {
 #endif
 
-#define BZ_ABI_VERSION 4
+#define BZ_ABI_VERSION 5
 
 typedef enum {
     BZ_OK = 0,
@@ -356,6 +356,81 @@ bz_status bz_batch_read_particles(bz_batch *b, int32_t i, const bz_particles *ou
 /* Device time of the last launch: the batch kernel and the tally kernels [ms]. */
 bz_status bz_batch_timing(bz_batch *b, double *step_ms, double *tally_ms);
 void bz_destroy_batch(bz_batch *b);
+
+/* ------------------------------------------------------------------------
+ * Serving: a request loop with continuous batching.  The paper has no
+ * counterpart (its drifter runs one swarm per process, Sec. 7); this is the
+ * form in which many independent swarm requests share one GPU.
+ *
+ * Requests (a compiled mixture and a configuration, as for bz_run_swarm)
+ * are queued in submission order.  A worker thread of the server owns
+ * n_slots launch slots, one non-blocking CUDA stream each.  Whenever a slot
+ * is free it takes queued requests in order -- as many as fit the
+ * device-memory budget, at most max_group, all of one step-kernel class
+ * (precision; the feature instance or the lean one; the lean one with or
+ * without the magnetic field's paths) -- and runs them as one batched
+ * persistent launch (bz_create_batch); a spawn-mode request runs alone
+ * (bz_run_swarm).  Launches are polled without blocking, so requests that
+ * arrive while others run are admitted as soon as a slot and memory free up.
+ * A request's tallies equal those of bz_run_swarm with its configuration.
+ *
+ * Device bytes of a request, counted against the budget while it runs:
+ * 92 per electron slot (its results), 40 per created electron's birth
+ * record in spawn mode (pop_cap - n_electrons), plus 2 MiB.
+ * ------------------------------------------------------------------------ */
+typedef struct bz_server bz_server;
+
+typedef struct {
+    double memory_budget_bytes; /* device bytes running requests may hold at once; <= 0: 60e9 */
+    int32_t n_slots;            /* concurrent launches; <= 0: 3 */
+    int32_t max_group;          /* requests per batched launch; <= 0: 512 */
+    int32_t simulate;           /* 0: run on the context's GPU.  n > 0: host-only scheduling test -- no
+                                   device is touched, ctx and mixtures may be NULL, a launch ends after
+                                   n polls of the worker and reports n_particles and n_real only */
+    int32_t reserved;
+} bz_server_opts;
+
+typedef struct {
+    double t_submit, t_admit, t_done; /* seconds since the server was created (monotonic clock) */
+    uint64_t launch;                  /* index of the launch that ran the request (0, 1, ...) */
+    int32_t group_size;               /* requests in that launch */
+    int32_t status;                   /* bz_status of the request's run */
+} bz_request_info;
+
+typedef struct {
+    uint64_t submitted, completed, cancelled, launches;
+    int32_t queued, running, max_running, reserved; /* requests waiting / on the GPU / most at once */
+    double bytes_in_use, peak_bytes_in_use;         /* device bytes held by running requests */
+} bz_server_stats;
+
+/* Creates a server on ctx's device and starts its worker thread.  The
+ * context (and the mixtures of submitted requests) must outlive the
+ * server.  Errors: BZ_EINVAL, BZ_ENOMEM, BZ_ECUDA (stream creation). */
+bz_status bz_server_create(bz_ctx *ctx, const bz_server_opts *opts, bz_server **out);
+/* Queues a request and returns its id (> 0) at once.  The configuration is
+ * copied.  Errors: BZ_EINVAL (as bz_run_swarm's checks), BZ_EBUDGET (the
+ * request alone needs more device memory than the budget: it could never
+ * run). */
+bz_status bz_submit(bz_server *s, const bz_mixture *mix, const bz_swarm_config *cfg, uint64_t *request_id);
+/* Non-blocking: BZ_ENOTREADY while the request is queued or running.  When
+ * it has run, copies its tallies into *out and its times into *info (either
+ * may be NULL), forgets the request and returns the run's status (BZ_OK, or
+ * the error its launch reported).  BZ_ECANCEL if it was cancelled (the id is
+ * then forgotten); BZ_EINVAL for an unknown or already delivered id. */
+bz_status bz_poll(bz_server *s, uint64_t request_id, bz_tallies *out, bz_request_info *info);
+/* Cancels a request: a queued one never starts; a running one's launch goes
+ * on with the rest of its group and its result is dropped (its memory is
+ * released when the launch ends); a finished one's result is dropped.
+ * bz_poll then reports BZ_ECANCEL.  Errors: BZ_EINVAL (unknown id). */
+bz_status bz_cancel(bz_server *s, uint64_t request_id);
+/* Holds (paused != 0) or resumes admission: while held, queued requests
+ * wait and launches already running go on (draining, maintenance, or a set
+ * of submissions that should be grouped together).  Errors: BZ_EINVAL. */
+bz_status bz_server_pause(bz_server *s, int32_t paused);
+bz_status bz_server_get_stats(bz_server *s, bz_server_stats *out);
+/* Stops the server: queued requests are cancelled, running launches are
+ * waited for, and every undelivered result is dropped. */
+void bz_server_destroy(bz_server *s);
 
 /* ------------------------------------------------------------------------
  * Allocation-free tally reduction.  The paper has no counterpart: this entry

@@ -110,6 +110,23 @@ class bz_batch_opts(C.Structure):
                 ("reserved", C.c_int32)]
 
 
+class bz_server_opts(C.Structure):
+    _fields_ = [("memory_budget_bytes", C.c_double), ("n_slots", C.c_int32), ("max_group", C.c_int32),
+                ("simulate", C.c_int32), ("reserved", C.c_int32)]
+
+
+class bz_request_info(C.Structure):
+    _fields_ = [("t_submit", C.c_double), ("t_admit", C.c_double), ("t_done", C.c_double),
+                ("launch", C.c_uint64), ("group_size", C.c_int32), ("status", C.c_int32)]
+
+
+class bz_server_stats(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("cancelled", C.c_uint64),
+                ("launches", C.c_uint64), ("queued", C.c_int32), ("running", C.c_int32),
+                ("max_running", C.c_int32), ("reserved", C.c_int32), ("bytes_in_use", C.c_double),
+                ("peak_bytes_in_use", C.c_double)]
+
+
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 
@@ -155,6 +172,13 @@ SIGNATURES = {
     "bz_destroy_batch": (None, [C.c_void_p]),
     "bz_reduce_tallies_noalloc": (C.c_int, [C.POINTER(bz_particle_arrays), C.c_uint64, C.c_uint64, C.c_double,
                                             C.c_double, C.c_double, C.c_void_p, C.c_void_p]),
+    "bz_server_create": (C.c_int, [C.c_void_p, C.POINTER(bz_server_opts), C.POINTER(C.c_void_p)]),
+    "bz_submit": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(bz_swarm_config), C.POINTER(C.c_uint64)]),
+    "bz_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(bz_tallies), C.POINTER(bz_request_info)]),
+    "bz_cancel": (C.c_int, [C.c_void_p, C.c_uint64]),
+    "bz_server_pause": (C.c_int, [C.c_void_p, C.c_int32]),
+    "bz_server_get_stats": (C.c_int, [C.c_void_p, C.POINTER(bz_server_stats)]),
+    "bz_server_destroy": (None, [C.c_void_p]),
     "bz_step_replay": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(bz_swarm_config), C.c_int64, C.c_void_p,
                                  C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "bz_philox": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p]),
@@ -212,6 +236,13 @@ def bz_batch_read_particles(b, i, out): return lib().bz_batch_read_particles(b, 
 def bz_batch_timing(b, a, c): return lib().bz_batch_timing(b, a, c)
 def bz_destroy_batch(b): return lib().bz_destroy_batch(b)
 def bz_reduce_tallies_noalloc(*a): return lib().bz_reduce_tallies_noalloc(*a)
+def bz_server_create(ctx, opts, out): return lib().bz_server_create(ctx, opts, out)
+def bz_submit(srv, mix, cfg, rid): return lib().bz_submit(srv, mix, cfg, rid)
+def bz_poll(srv, rid, out, info): return lib().bz_poll(srv, rid, out, info)
+def bz_cancel(srv, rid): return lib().bz_cancel(srv, rid)
+def bz_server_pause(srv, paused): return lib().bz_server_pause(srv, paused)
+def bz_server_get_stats(srv, out): return lib().bz_server_get_stats(srv, out)
+def bz_server_destroy(srv): return lib().bz_server_destroy(srv)
 def bz_step_replay(*a): return lib().bz_step_replay(*a)
 def bz_philox(*a): return lib().bz_philox(*a)
 

@@ -290,6 +290,9 @@ bz_status prepare_run(const bz_mixture *mix, const bz_swarm_config *cfg, bz::Run
     a->attach_keep = cfg->attach_keep_state != 0;
     a->nu0 = (cfg->nu_trial > 0.0) ? cfg->nu_trial : mix->cm.nu_trial;
     a->eps0_mean = cfg->eps0_mean_eV;
+    a->v0_scale = sqrt((2.0 / 3.0) * cfg->eps0_mean_eV * bz::kQe / bz::kMe);
+    a->v0_scale32 = (float)a->v0_scale;
+    a->nu0_32 = (float)a->nu0;
     a->t_end = cfg->t_end_s;
     a->max_trials = cfg->max_trials ? cfg->max_trials : 0x7FFFFFFFull;
     a->window = cfg->trial_mode == BZ_TRIAL_WINDOW;
@@ -317,6 +320,9 @@ bz_status prepare_run(const bz_mixture *mix, const bz_swarm_config *cfg, bz::Run
 }  // namespace
 
 void bz::set_last_error(const std::string &msg) { g_err = msg; }
+int bz::ctx_device(const bz_ctx *ctx) { return ctx->device; }
+bz_status bz::check_config(const bz_swarm_config *cfg) { return validate_config(cfg); }
+bool bz::needs_feature_instance(const bz_mixture *mix, const bz_swarm_config *cfg) { return ext_instance(mix, cfg); }
 
 extern "C" {
 
@@ -384,10 +390,13 @@ bz_status bz_create_gas_mixture(bz_ctx *ctx, const bz_gas *gases, int32_t n_gase
         return cuda_fail(e, "copy of the mixture tables");
     }
     const int mode = opts ? opts->channels_in_smem : -1;
-    int budget = (opts && opts->smem_budget > 0) ? opts->smem_budget : 96 * 1024;
+    // channel values go to shared memory when the whole staged blob fits the
+    // budget the tables were compiled for (three FP32 blocks per SM)
+    int budget = (opts && opts->smem_budget > 0) ? opts->smem_budget : (int)bz::kStageBudget32;
     if (budget > ctx->smem_optin - 1024) budget = ctx->smem_optin - 1024;
+    int budget64 = std::min((int)bz::kStageBudget64, ctx->smem_optin - 1024);
     m->ch_smem32 = mode == 1 ? true : mode == 0 ? false : (int)m->cm.lay32.stage_all <= budget;
-    m->ch_smem64 = mode == 1 ? true : mode == 0 ? false : (int)m->cm.lay64.stage_all <= budget;
+    m->ch_smem64 = mode == 1 ? true : mode == 0 ? false : (int)m->cm.lay64.stage_all <= budget64;
     if (m->ch_smem32 && (int)m->cm.lay32.stage_all > ctx->smem_optin - 1024) m->ch_smem32 = false;
     if (m->ch_smem64 && (int)m->cm.lay64.stage_all > ctx->smem_optin - 1024) m->ch_smem64 = false;
     m->cm.info.channels_in_smem = m->ch_smem32 ? 1 : 0;

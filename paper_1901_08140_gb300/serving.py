@@ -1,41 +1,31 @@
-"""Serving loop: swarm requests with continuous batching on one GPU.
+"""Serving: swarm requests with continuous batching on one GPU.
 
-Requests (a compiled mixture plus a swarm configuration) arrive over time.
-Whenever a launch slot (one of S CUDA streams) is free, the server takes
-the queued requests in arrival order, as many as fit the device-memory
-admission budget (and a group-size cap), and launches them together as one
-batched persistent launch on that slot; it polls completions without
-blocking.  Groups on different slots run concurrently, so requests that
-arrive while others are on the GPU are admitted as soon as a slot and
-memory free up and their work overlaps on the device.  Each swarm's
-results depend only on its configuration (counter-based random numbers
-keyed by the swarm seed and particle ids, one step kernel for every launch
-form), so a request's tallies are the same alone and in the mix.
-
-The scheduling logic is independent of the GPU: a backend object launches,
-polls and releases swarms (``GpuBackend`` drives libbz.so; the tests drive
-the same server with a host-only fake to check admission and ordering).
+The request loop itself is native (``bz_server_*``, ``bz_submit``,
+``bz_poll``, ``bz_cancel`` in libbz.so): a worker thread admits queued
+requests in arrival order into free launch slots as device memory allows,
+batches requests of one step-kernel class into one persistent launch per
+slot, runs avalanche (spawn-mode) requests alone, and polls completions
+without blocking.  This module only marshals: ``Server.run`` submits each
+request at its arrival time and collects the results with the server's own
+timestamps.
 """
 from __future__ import annotations
 
-import collections
+import ctypes as C
 import dataclasses
 import math
 import time
-from typing import Callable, Deque, Dict, List, Optional, Sequence
+from typing import Dict, List, Optional, Sequence
 
 import numpy as np
 
-# device bytes per electron of a swarm (results in SoA) and per swarm (tally scratch)
-BYTES_PER_ELECTRON = 92
-BYTES_PER_SWARM = 2 << 20
-BYTES_PER_BIRTH = 40   # spawn mode: birth record of a created electron
+from . import bz
 
 
 @dataclasses.dataclass
 class Request:
     rid: int
-    mixture: object                 # a compiled mixture (bz.Mixture) or backend-specific handle
+    mixture: object                 # a compiled mixture (bz.Mixture), or None on a simulated server
     cfg: object                     # bz.bz_swarm_config
     arrival: float = 0.0            # seconds after the start of the run
     n_electrons: int = 0
@@ -43,208 +33,105 @@ class Request:
     done: Optional[float] = None
     tallies: Optional[Dict[str, float]] = None
     status: int = 0
+    launch: int = -1
+    group_size: int = 0
 
     @property
     def latency(self) -> float:
         return self.done - self.arrival
 
-    def device_bytes(self) -> int:
-        cap = int(getattr(self.cfg, "pop_cap", 0) or 0) if getattr(self.cfg, "spawn", 0) else 0
-        n = max(self.n_electrons, cap)
-        return (BYTES_PER_ELECTRON + (BYTES_PER_BIRTH if cap else 0)) * n + BYTES_PER_SWARM
-
-
-class GpuBackend:
-    """Launches requests as swarms of libbz.so on a pool of CUDA streams."""
-
-    def __init__(self, ctx, n_streams: int = 16):
-        import torch
-        from . import bz
-        self.bz = bz
-        self.ctx = ctx
-        dev = torch.device("cuda", ctx.device)
-        self.streams = [torch.cuda.Stream(device=dev) for _ in range(n_streams)]
-
-    @property
-    def slots(self) -> int:
-        return len(self.streams)
-
-    def launch(self, req: Request, slot: int):
-        return self.bz.Swarm(self.ctx, req.mixture, req.cfg, self.streams[slot])
-
-    def poll(self, handle) -> Optional[Dict[str, float]]:
-        t = self.bz.bz_tallies()
-        import ctypes as C
-        st = self.bz.lib().bz_query_tallies(handle.h, C.byref(t))
-        if st == self.bz.BZ_ENOTREADY:
-            return None
-        out = self.bz._tally_dict(t)
-        out["status"] = st
-        return out
-
-    def release(self, handle) -> None:
-        handle.close()
-
-
-class _SwarmRun:
-    """A request launched on its own as a swarm (spawn mode: an avalanche)."""
-
-    def __init__(self, bz, ctx, req, stream):
-        self.bz = bz
-        self.sw = bz.Swarm(ctx, req.mixture, req.cfg, stream)
-
-    def poll(self) -> Optional[List[Dict[str, float]]]:
-        import ctypes as C
-        t = self.bz.bz_tallies()
-        st = self.bz.lib().bz_query_tallies(self.sw.h, C.byref(t))
-        if st == self.bz.BZ_ENOTREADY:
-            return None
-        out = self.bz._tally_dict(t)
-        out["status"] = st
-        return [out]
-
-    def close(self) -> None:
-        self.sw.close()
-
-
-class GpuBatchBackend:
-    """Launches groups of requests as one batched launch of libbz.so per slot;
-    spawn-mode requests (avalanches) run alone, each in its own persistent
-    launch on the slot's stream."""
-
-    def __init__(self, ctx, n_streams: int = 4):
-        import torch
-        from . import bz
-        self.bz = bz
-        self.ctx = ctx
-        dev = torch.device("cuda", ctx.device)
-        self.streams = [torch.cuda.Stream(device=dev) for _ in range(n_streams)]
-
-    @property
-    def slots(self) -> int:
-        return len(self.streams)
-
-    @staticmethod
-    def alone(req: Request) -> bool:
-        return bool(getattr(req.cfg, "spawn", 0))
-
-    @staticmethod
-    def group_key(req: Request):
-        """Requests share a launch only with requests that run the same build
-        of the step kernel alone, so that every result is the one the
-        request gets alone: the feature build (the paper's adaptive trial
-        frequencies, xi-form gases, moving targets) or the lean one, and in
-        the lean one with or without a magnetic field."""
-        info = getattr(req.mixture, "info", None) or {}
-        ext = (getattr(req.cfg, "trial_mode", 0) in (3, 4) or info.get("n_xi_gases", 0) > 0
-               or getattr(req.cfg, "gas_temperature_K", 0.0) > 0.0)
-        return (bool(ext), bool(ext or getattr(req.cfg, "b_T", 0.0) > 0.0))
-
-    def launch_group(self, reqs: Sequence[Request], slot: int):
-        if len(reqs) == 1 and self.alone(reqs[0]):
-            return _SwarmRun(self.bz, self.ctx, reqs[0], self.streams[slot])
-        b = self.bz.Batch(self.ctx, [r.mixture for r in reqs], [r.cfg for r in reqs], use_graph=False)
-        b.launch(self.streams[slot])
-        return b
-
-    def poll_group(self, handle) -> Optional[List[Dict[str, float]]]:
-        if isinstance(handle, _SwarmRun):
-            return handle.poll()
-        if not handle.ready():
-            return None
-        return handle.tallies(check=False)
-
-    def release_group(self, handle) -> None:
-        handle.close()
-
 
 class Server:
-    """Continuous-batching request loop with memory-budget admission.
+    """A bz_server: continuous-batching request loop of libbz.so.
 
-    With a backend that launches groups (``launch_group``), each free slot
-    takes up to ``max_group`` queued requests at once; otherwise one request
-    per slot.
+    simulate = n > 0 runs the scheduling on the host only (no device; a launch
+    ends after n polls of the worker), for tests on machines without a GPU.
     """
 
-    def __init__(self, backend, memory_budget: float = 60e9, clock: Callable[[], float] = time.perf_counter,
-                 idle_sleep: float = 2e-5, max_group: int = 512):
-        self.backend = backend
-        self.budget = float(memory_budget)
-        self.clock = clock
-        self.idle_sleep = idle_sleep
-        self.max_group = max_group if hasattr(backend, "launch_group") else 1
-        self.in_use = 0.0
-        self.peak_in_use = 0.0
-        self.max_concurrent = 0
-        self.groups = 0
+    def __init__(self, ctx=None, memory_budget: float = 60e9, n_slots: int = 3, max_group: int = 512,
+                 simulate: int = 0):
+        opts = bz.bz_server_opts(float(memory_budget), int(n_slots), int(max_group), int(simulate), 0)
+        h = C.c_void_p()
+        bz._check(bz.lib().bz_server_create(ctx.h if ctx is not None else None, C.byref(opts), C.byref(h)))
+        self.h = h
+        self.ctx = ctx
 
-    def run(self, requests: Sequence[Request], realtime: bool = True) -> List[Request]:
-        """Serves `requests` (sorted by arrival); returns them completed.
+    def submit(self, mixture, cfg) -> int:
+        rid = C.c_uint64()
+        bz._check(bz.lib().bz_submit(self.h, mixture.h if mixture is not None else None, C.byref(cfg),
+                                     C.byref(rid)))
+        return int(rid.value)
 
-        With realtime=True a request becomes visible at its arrival time on
-        the wall clock; otherwise all are visible at once (throughput mode).
-        """
+    def poll(self, rid: int):
+        """None while queued or running; else (status, tallies, info)."""
+        t, info = bz.bz_tallies(), bz.bz_request_info()
+        st = bz.lib().bz_poll(self.h, C.c_uint64(rid), C.byref(t), C.byref(info))
+        if st == bz.BZ_ENOTREADY:
+            return None
+        if st == bz.BZ_EINVAL:
+            bz._check(st)
+        out = bz._tally_dict(t)
+        out["status"] = st
+        return st, out, {k: getattr(info, k) for k, _ in bz.bz_request_info._fields_}
+
+    def pause(self, paused: bool = True) -> None:
+        """Holds (or resumes) admission; running launches go on."""
+        bz._check(bz.lib().bz_server_pause(self.h, int(bool(paused))))
+
+    def cancel(self, rid: int) -> None:
+        bz._check(bz.lib().bz_cancel(self.h, C.c_uint64(rid)))
+
+    def stats(self) -> Dict[str, float]:
+        s = bz.bz_server_stats()
+        bz._check(bz.lib().bz_server_get_stats(self.h, C.byref(s)))
+        return {k: getattr(s, k) for k, _ in bz.bz_server_stats._fields_}
+
+    def run(self, requests: Sequence[Request], realtime: bool = True, poll_sleep: float = 2e-5) -> List[Request]:
+        """Submits `requests` at their arrival times (all at once when
+        realtime is False) and returns them completed; their admission and
+        completion times are the server's, counted from their arrival."""
         reqs = sorted(requests, key=lambda r: (r.arrival, r.rid))
-        for r in reqs:
-            if r.device_bytes() > self.budget:
-                raise ValueError(f"request {r.rid} needs {r.device_bytes()} bytes, above the admission budget")
-        pending: Deque[Request] = collections.deque(reqs)
-        queue: Deque[Request] = collections.deque()
-        free = list(range(self.backend.slots))[::-1]
-        running: Dict[int, tuple] = {}   # slot -> (requests, handle)
-        t0 = self.clock()
+        if not reqs:
+            return []
+        t0 = time.perf_counter()
+        waiting: Dict[int, Request] = {}
         done: List[Request] = []
-        grouped = self.max_group > 1
-        while pending or queue or running:
-            now = self.clock() - t0
-            while pending and (not realtime or pending[0].arrival <= now):
-                queue.append(pending.popleft())
-            # admit in arrival order while a slot and memory are free
-            while queue and free and self.in_use + queue[0].device_bytes() <= self.budget:
-                group, need = [], 0.0
-                alone = getattr(self.backend, "alone", lambda r: False)
-                key = getattr(self.backend, "group_key", lambda r: 0)
-                while (queue and len(group) < self.max_group
-                       and self.in_use + need + queue[0].device_bytes() <= self.budget):
-                    if group and (alone(queue[0]) or key(queue[0]) != key(group[0])):
-                        break          # runs on its own, or in another kernel instance
-                    r = queue.popleft()
-                    need += r.device_bytes()
-                    group.append(r)
-                    if alone(r):
-                        break
-                slot = free.pop()
-                t_adm = self.clock() - t0
-                for r in group:
-                    r.admitted = t_adm
-                h = self.backend.launch_group(group, slot) if grouped else self.backend.launch(group[0], slot)
-                running[slot] = (group, h)
-                self.groups += 1
-                self.in_use += need
-                self.peak_in_use = max(self.peak_in_use, self.in_use)
-                self.max_concurrent = max(self.max_concurrent, sum(len(g) for g, _ in running.values()))
-            progressed = False
-            for slot in list(running):
-                group, h = running[slot]
-                res = self.backend.poll_group(h) if grouped else self.backend.poll(h)
+        i = 0
+        while i < len(reqs) or waiting:
+            now = time.perf_counter() - t0
+            while i < len(reqs) and (not realtime or reqs[i].arrival <= now):
+                r = reqs[i]
+                waiting[self.submit(r.mixture, r.cfg)] = r
+                i += 1
+            for rid in list(waiting):
+                res = self.poll(rid)
                 if res is None:
                     continue
-                t_done = self.clock() - t0
-                if not grouped:
-                    res = [res]
-                for r, t in zip(group, res):
-                    r.done = t_done
-                    r.tallies = t
-                    r.status = int(t.get("status", 0))
-                    self.in_use -= r.device_bytes()
-                    done.append(r)
-                (self.backend.release_group if grouped else self.backend.release)(h)
-                del running[slot]
-                free.append(slot)
-                progressed = True
-            if not progressed and self.idle_sleep > 0:
-                time.sleep(self.idle_sleep)
+                st, t, info = res
+                r = waiting.pop(rid)
+                # latency on the server's clock: from submission (at arrival) to completion
+                r.status, r.tallies = int(st), t
+                r.admitted = r.arrival + (info["t_admit"] - info["t_submit"])
+                r.done = r.arrival + (info["t_done"] - info["t_submit"])
+                r.launch, r.group_size = int(info["launch"]), int(info["group_size"])
+                done.append(r)
+            if waiting and poll_sleep > 0:
+                time.sleep(poll_sleep)
         return done
+
+    def close(self):
+        if getattr(self, "h", None):
+            bz.lib().bz_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        import sys
+        if sys.is_finalizing():
+            return
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def poisson_arrivals(rate: float, count: int, seed: int = 1) -> np.ndarray:

@@ -1,155 +1,166 @@
-"""Serving loop: host-side admission and ordering with a fake backend (CPU),
-and on the GPU each request's result alone and in the mix."""
+"""Serving through the C ABI (bz_server_create, bz_submit, bz_poll,
+bz_cancel): admission, grouping, ordering, cancellation and admission
+overflow on a simulated server (host only, no device), and on the GPU each
+request's result alone and in the mix."""
+import time
+
 import numpy as np
 import pytest
 
+from paper_1901_08140_gb300 import build as B
+from paper_1901_08140_gb300 import bz
 from paper_1901_08140_gb300 import serving as S
 
-
-class FakeBackend:
-    """Completes a launch a fixed number of polls after it starts."""
-
-    def __init__(self, slots=3, polls=5):
-        self._slots = slots
-        self.polls = polls
-        self.log = []
-
-    @property
-    def slots(self):
-        return self._slots
-
-    def launch(self, req, slot):
-        self.log.append(("launch", req.rid, slot))
-        return {"req": req, "left": self.polls}
-
-    def poll(self, h):
-        h["left"] -= 1
-        if h["left"] > 0:
-            return None
-        return {"n_real": h["req"].n_electrons, "status": 0}
-
-    def release(self, h):
-        self.log.append(("release", h["req"].rid))
+MIB = 1 << 20
 
 
-class FakeGroupBackend(FakeBackend):
-    def launch_group(self, reqs, slot):
-        self.log.append(("group", tuple(r.rid for r in reqs), slot))
-        return {"reqs": list(reqs), "left": self.polls}
-
-    def poll_group(self, h):
-        h["left"] -= 1
-        if h["left"] > 0:
-            return None
-        return [{"n_real": r.n_electrons, "status": 0} for r in h["reqs"]]
-
-    def release_group(self, h):
-        self.log.append(("release", tuple(r.rid for r in h["reqs"])))
+@pytest.fixture(scope="module")
+def L():
+    B.build()
+    return bz.lib()
 
 
-class Clock:
-    def __init__(self):
-        self.t = 0.0
-
-    def __call__(self):
-        self.t += 1e-3
-        return self.t
+def _cfg(n=1000, **kw):
+    return bz.make_config(n_electrons=n, real_collisions=10, e_over_n_Td=10.0, **kw)
 
 
-def _reqs(sizes, arrivals):
-    return [S.Request(i, None, None, arrival=a, n_electrons=n) for i, (n, a) in enumerate(zip(sizes, arrivals))]
+def _bytes(n):
+    return 92 * n + 2 * MIB
 
 
-def test_admission_respects_slots_and_budget():
-    be = FakeBackend(slots=3)
-    budget = S.BYTES_PER_ELECTRON * 2500 + 2 * S.BYTES_PER_SWARM
-    srv = S.Server(be, memory_budget=budget, clock=Clock(), idle_sleep=0)
-    done = srv.run(_reqs([1000, 1000, 1000, 500, 2000], [0, 0, 0, 0, 0]), realtime=False)
-    assert sorted(r.rid for r in done) == [0, 1, 2, 3, 4]
-    assert srv.max_concurrent <= 3
-    assert srv.peak_in_use <= budget
-    # admission is in arrival order: request 3 starts only after request 0 or 1 ends
-    launches = [e for e in be.log if e[0] == "launch"]
-    assert [e[1] for e in launches] == [0, 1, 2, 3, 4]
-    assert all(r.done > r.admitted >= r.arrival for r in done)
+def _wait_all(srv, ids, timeout=20.0):
+    out, t0 = {}, time.time()
+    while len(out) < len(ids):
+        for rid in ids:
+            if rid in out:
+                continue
+            r = srv.poll(rid)
+            if r is not None:
+                out[rid] = r
+        assert time.time() - t0 < timeout, "the simulated server did not finish"
+        time.sleep(1e-4)
+    return out
 
 
-def test_requests_arriving_while_others_run_are_admitted_at_once():
-    be = FakeBackend(slots=4, polls=50)
-    srv = S.Server(be, memory_budget=1e12, clock=Clock(), idle_sleep=0)
-    done = srv.run(_reqs([10, 10, 10], [0.0, 0.005, 0.010]), realtime=True)
+def test_admission_respects_slots_budget_and_order(L):
+    budget = _bytes(1000) * 2 + _bytes(500)  # two 1000-electron requests and a 500 one at once
+    srv = S.Server(None, memory_budget=budget, n_slots=3, max_group=1, simulate=200)
+    ids = [srv.submit(None, _cfg(n)) for n in (1000, 1000, 1000, 500, 2000)]
+    res = _wait_all(srv, ids)
+    st = srv.stats()
+    assert st["completed"] == 5 and st["max_running"] <= 3
+    assert st["peak_bytes_in_use"] <= budget
+    # admission in submission order: launches are numbered in the order of the ids
+    launches = [res[i][2]["launch"] for i in ids]
+    assert launches == sorted(launches) and len(set(launches)) == 5
+    # the third 1000-electron request had to wait for memory: admitted after another one ended
+    assert res[ids[2]][2]["t_admit"] >= min(res[ids[0]][2]["t_done"], res[ids[1]][2]["t_done"])
+    for rid, n in zip(ids, (1000, 1000, 1000, 500, 2000)):
+        st_, t, info = res[rid]
+        assert st_ == bz.BZ_OK and t["n_particles"] == n and t["n_real"] == 10 * n
+        assert info["t_done"] >= info["t_admit"] >= info["t_submit"]
+    srv.close()
+
+
+def test_queued_requests_share_a_launch_within_budget(L):
+    budget = _bytes(1000) * 3
+    srv = S.Server(None, memory_budget=budget, n_slots=2, max_group=8, simulate=50)
+    srv.pause()
+    ids = [srv.submit(None, _cfg(1000)) for _ in range(7)]
+    srv.pause(False)
+    res = _wait_all(srv, ids)
+    groups = {}
+    for rid in ids:
+        groups.setdefault(res[rid][2]["launch"], []).append(rid)
+    sizes = [len(groups[k]) for k in sorted(groups)]
+    assert sizes[0] == 3 and sum(sizes) == 7          # as many as the memory budget allows
+    assert all(res[rid][2]["group_size"] == len(g) for g in groups.values() for rid in g)
+    assert srv.stats()["peak_bytes_in_use"] <= budget
+    srv.close()
+
+
+def test_groups_hold_one_kernel_class_and_avalanches_run_alone(L):
+    srv = S.Server(None, memory_budget=1e12, n_slots=1, max_group=8, simulate=20)
+    cfgs = [_cfg(), _cfg(), _cfg(b_T=1.0), _cfg(b_T=0.5), _cfg(spawn=True, pop_cap=10 ** 4), _cfg(), _cfg(),
+            _cfg(precision=64), _cfg(precision=64)]
+    srv.pause()
+    ids = [srv.submit(None, c) for c in cfgs]
+    srv.pause(False)
+    res = _wait_all(srv, ids)
+    launch = [res[i][2]["launch"] for i in ids]
+    # [0, 1] lean without B, [2, 3] with B, [4] spawn alone, [5, 6], [7, 8] FP64
+    assert launch == [0, 0, 1, 1, 2, 3, 3, 4, 4]
+    srv.close()
+
+
+def test_cancel_queued_running_and_finished_requests(L):
+    srv = S.Server(None, memory_budget=1e12, n_slots=1, max_group=1, simulate=2000)
+    a, b, c = (srv.submit(None, _cfg()) for _ in range(3))
+    t0 = time.time()
+    while srv.stats()["running"] == 0:     # a starts, b and c wait for the only slot
+        assert time.time() - t0 < 5
+        time.sleep(1e-4)
+    srv.cancel(b)                           # queued: never starts
+    srv.cancel(a)                           # running: its result is dropped
+    assert srv.poll(a)[0] == bz.BZ_ECANCEL and srv.poll(b)[0] == bz.BZ_ECANCEL
+    res = _wait_all(srv, [c])
+    assert res[c][0] == bz.BZ_OK
+    st = srv.stats()
+    assert st["cancelled"] == 2 and st["completed"] == 1 and st["launches"] == 2
+    assert st["bytes_in_use"] == 0 and st["running"] == 0
+    d = srv.submit(None, _cfg())
+    t0 = time.time()
+    while srv.stats()["completed"] < 2:
+        assert time.time() - t0 < 10
+        time.sleep(1e-4)
+    srv.cancel(d)                           # finished but not delivered: dropped
+    assert srv.poll(d)[0] == bz.BZ_ECANCEL
+    with pytest.raises(bz.BzError) as ei:   # delivered ids are forgotten
+        srv.poll(d)
+    assert ei.value.status == bz.BZ_EINVAL
+    with pytest.raises(bz.BzError):
+        srv.cancel(12345)
+    srv.close()
+
+
+def test_admission_overflow_is_rejected_at_submission(L):
+    srv = S.Server(None, memory_budget=1e6, n_slots=2, simulate=5)
+    with pytest.raises(bz.BzError) as ei:
+        srv.submit(None, _cfg(10 ** 6))
+    assert ei.value.status == bz.BZ_EBUDGET
+    # spawn requests hold memory for their population cap
+    with pytest.raises(bz.BzError) as ei:
+        srv.submit(None, _cfg(1, spawn=True, pop_cap=10 ** 5))
+    assert ei.value.status == bz.BZ_EBUDGET
+    with pytest.raises(bz.BzError) as ei:     # invalid configurations never queue
+        srv.submit(None, _cfg(0))
+    assert ei.value.status == bz.BZ_EINVAL
+    assert srv.stats()["submitted"] == 0
+    srv.close()
+
+
+def test_destroy_cancels_what_is_queued(L):
+    srv = S.Server(None, memory_budget=1e12, n_slots=1, max_group=1, simulate=500)
+    for _ in range(5):
+        srv.submit(None, _cfg())
+    srv.close()   # returns after the running launch ends; nothing leaks or hangs
+
+
+def test_run_in_real_time_admits_arrivals_while_others_run(L):
+    srv = S.Server(None, memory_budget=1e12, n_slots=4, max_group=1, simulate=3000)
+    reqs = [S.Request(i, None, _cfg(), arrival=a, n_electrons=1000) for i, a in enumerate([0.0, 0.005, 0.01])]
+    done = srv.run(reqs, realtime=True)
     by = {r.rid: r for r in done}
-    # the later requests start before the first one finished
     assert by[1].admitted < by[0].done and by[2].admitted < by[0].done
-    assert srv.max_concurrent == 3
-
-
-def test_queued_requests_are_launched_together_within_budget():
-    be = FakeGroupBackend(slots=2, polls=20)
-    budget = S.BYTES_PER_ELECTRON * 3000 + 3 * S.BYTES_PER_SWARM
-    srv = S.Server(be, memory_budget=budget, clock=Clock(), idle_sleep=0, max_group=8)
-    done = srv.run(_reqs([1000] * 7, [0.0] * 7), realtime=False)
-    groups = [e[1] for e in be.log if e[0] == "group"]
-    assert groups[0] == (0, 1, 2)              # as many as the memory budget allows
-    assert sorted(r for g in groups for r in g) == list(range(7))
-    assert srv.peak_in_use <= budget and len(done) == 7
-
-
-class FakeAloneBackend(FakeGroupBackend):
-    """Requests with cfg == "alone" must be launched on their own."""
-
-    @staticmethod
-    def alone(req):
-        return req.cfg == "alone"
-
-
-def test_requests_that_run_alone_are_not_grouped():
-    be = FakeAloneBackend(slots=2, polls=10)
-    reqs = _reqs([100] * 6, [0.0] * 6)
-    reqs[2].cfg = "alone"
-    reqs[3].cfg = "alone"
-    srv = S.Server(be, memory_budget=1e12, clock=Clock(), idle_sleep=0, max_group=8)
-    done = srv.run(reqs, realtime=False)
-    groups = [e[1] for e in be.log if e[0] == "group"]
-    assert groups[:2] == [(0, 1), (2,)]
-    assert (3,) in groups and sorted(r for g in groups for r in g) == list(range(6))
-    assert len(done) == 6
-
-
-def test_groups_hold_one_kernel_instance():
-    class KeyBackend(FakeGroupBackend):
-        @staticmethod
-        def group_key(req):
-            return req.cfg
-
-    be = KeyBackend(slots=1, polls=3)
-    reqs = _reqs([100] * 6, [0.0] * 6)
-    for r, k in zip(reqs, [0, 0, 1, 1, 0, 1]):
-        r.cfg = k
-    srv = S.Server(be, memory_budget=1e12, clock=Clock(), idle_sleep=0, max_group=8)
-    srv.run(reqs, realtime=False)
-    groups = [e[1] for e in be.log if e[0] == "group"]
-    assert groups == [(0, 1), (2, 3), (4,), (5,)]
-
-
-def test_spawn_requests_reserve_memory_for_the_population_cap():
-    class Cfg:
-        spawn, pop_cap = 1, 10 ** 6
-    r = S.Request(0, None, Cfg(), n_electrons=1)
-    assert r.device_bytes() == (S.BYTES_PER_ELECTRON + S.BYTES_PER_BIRTH) * 10 ** 6 + S.BYTES_PER_SWARM
-
-
-def test_oversized_request_is_rejected():
-    srv = S.Server(FakeBackend(), memory_budget=1e6, clock=Clock(), idle_sleep=0)
-    with pytest.raises(ValueError):
-        srv.run(_reqs([10 ** 7], [0.0]))
+    assert srv.stats()["max_running"] == 3
+    srv.close()
 
 
 def test_poisson_arrivals_and_summary():
     a = S.poisson_arrivals(1000.0, 20000, seed=3)
     gaps = np.diff(a)
     assert abs(gaps.mean() - 1e-3) < 3e-5 and np.all(gaps > 0)
-    rs = _reqs([1] * 3, [0.0, 0.1, 0.2])
+    rs = [S.Request(i, None, None, arrival=x, n_electrons=1) for i, x in enumerate([0.0, 0.1, 0.2])]
     for r, d in zip(rs, [0.05, 0.2, 0.4]):
         r.done = d
         r.tallies = {"n_real": 10}
@@ -159,10 +170,10 @@ def test_poisson_arrivals_and_summary():
 
 @pytest.mark.gpu
 def test_results_are_the_same_alone_and_in_the_mix():
-    from paper_1901_08140_gb300 import build as B
-    B.build()
-    from paper_1901_08140_gb300 import bz
+    """Through bz_submit / bz_poll: each request's tallies equal those of the
+    swarm run alone (bz_run_swarm), bit for bit."""
     from paper_1901_08140_gb300 import workloads as W
+    B.build()
     ctx = bz.Context(0)
     specs = W.batched_swarms(count=24, real_collisions=100, max_electrons=30000)
     mixes = [bz.Mixture(ctx, s.gases) for s in specs]
@@ -173,28 +184,27 @@ def test_results_are_the_same_alone_and_in_the_mix():
         sw = bz.run_swarm(ctx, m, c)
         alone.append(sw.tallies())
         sw.close()
-    for backend, arrivals in ((S.GpuBackend(ctx, n_streams=8), [0.0] * len(cfgs)),
-                              (S.GpuBatchBackend(ctx, n_streams=3), list(np.linspace(0.0, 0.02, len(cfgs))))):
+    for slots, arrivals in ((8, [0.0] * len(cfgs)), (3, list(np.linspace(0.0, 0.02, len(cfgs))))):
         reqs = [S.Request(i, m, c, arrival=a, n_electrons=int(c.n_electrons))
                 for i, (m, c, a) in enumerate(zip(mixes, cfgs, arrivals))]
-        srv = S.Server(backend, memory_budget=60e9, max_group=6)
+        srv = S.Server(ctx, memory_budget=60e9, n_slots=slots, max_group=6)
         done = srv.run(reqs, realtime=True)
-        assert srv.max_concurrent > 1 and len(done) == len(reqs)
+        assert srv.stats()["max_running"] > 1 and len(done) == len(reqs)
         for r in done:
             a = alone[r.rid]
+            assert r.status == bz.BZ_OK
             for k in ("W", "eps", "D_L", "D_T", "n_real", "n_null", "n_window"):
                 assert r.tallies[k] == a[k], (r.rid, k)
+        srv.close()
 
 
 @pytest.mark.gpu
 def test_avalanche_requests_alone_and_in_the_mix():
-    """Spawn-mode requests run on worker threads beside batched swarms; the
-    population they reach (integer counts, fixed by the ids' random numbers)
-    is the same as when each runs alone."""
-    from paper_1901_08140_gb300 import build as B
-    B.build()
-    from paper_1901_08140_gb300 import bz
+    """Spawn-mode requests run in launches of their own beside batched swarms;
+    the population they reach (integer counts, fixed by the ids' random
+    numbers) is the same as when each runs alone."""
     from paper_1901_08140_gb300 import workloads as W
+    B.build()
     ctx = bz.Context(0)
     specs = W.batched_swarms(count=8, real_collisions=100, max_electrons=20000)
     mixes = [bz.Mixture(ctx, s.gases) for s in specs]
@@ -213,7 +223,7 @@ def test_avalanche_requests_alone_and_in_the_mix():
     assert all(alone[2 + 3 * i]["n_spawned"] > 0 for i in range(3))
     reqs = [S.Request(i, m, c, arrival=a, n_electrons=int(c.n_electrons))
             for i, (m, c, a) in enumerate(zip(mixes, cfgs, np.linspace(0.0, 0.01, len(cfgs))))]
-    srv = S.Server(S.GpuBatchBackend(ctx, n_streams=3), memory_budget=60e9, max_group=4)
+    srv = S.Server(ctx, memory_budget=60e9, n_slots=3, max_group=4)
     done = srv.run(reqs, realtime=True)
     assert len(done) == len(reqs)
     for r in done:
@@ -221,3 +231,33 @@ def test_avalanche_requests_alone_and_in_the_mix():
         for k in ("n_particles", "n_real", "n_ion", "n_att", "n_spawned", "n_alive", "n_capped"):
             assert r.tallies[k] == a[k], (r.rid, k)
         assert r.tallies["eps"] == pytest.approx(a["eps"], rel=1e-12, abs=0.0)
+    srv.close()
+
+
+@pytest.mark.gpu
+def test_cancel_on_the_gpu_drops_only_the_cancelled_request():
+    from paper_1901_08140_gb300 import workloads as W
+    B.build()
+    ctx = bz.Context(0)
+    specs = W.batched_swarms(count=6, real_collisions=200, max_electrons=50000)
+    mixes = [bz.Mixture(ctx, s.gases) for s in specs]
+    cfgs = [bz.config_from_spec(s, trial_mode=bz.BZ_TRIAL_WINDOW) for s in specs]
+    srv = S.Server(ctx, memory_budget=60e9, n_slots=1, max_group=2)
+    srv.pause()
+    ids = [srv.submit(m, c) for m, c in zip(mixes, cfgs)]
+    srv.cancel(ids[1])
+    srv.pause(False)
+    while srv.stats()["running"] == 0:
+        time.sleep(1e-4)
+    srv.cancel(ids[0])
+    res = _wait_all(srv, ids, timeout=120)
+    for k, rid in enumerate(ids):
+        if k in (0, 1):
+            assert res[rid][0] == bz.BZ_ECANCEL
+        else:
+            sw = bz.run_swarm(ctx, mixes[k], cfgs[k])
+            a = sw.tallies()
+            sw.close()
+            assert res[rid][0] == bz.BZ_OK and res[rid][1]["W"] == a["W"] and res[rid][1]["n_real"] == a["n_real"]
+    assert srv.stats()["bytes_in_use"] == 0
+    srv.close()
