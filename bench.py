@@ -1,25 +1,35 @@
 #!/usr/bin/env python
 """Benchmark of the electron-swarm step loop on GB300.
 
-One step = the whole hot path over one batch: the Argon-like E/N sweep
-(32 log-spaced points, 1-1000 Td), 1e6 electrons per point, each electron
-run to its 1000th real collision with FP32 flights and FP64 tallies, every
-swarm's tallies reduced on the device and copied to the host.
+One step = the whole hot path over one batch: the batched workload of 256
+swarms (1e3-1e6 electrons each, log-uniform, 4.1e7 in all; each a mixture
+of 2-4 of 8 synthetic gases with 5-40 channels on 100-1000-point tables;
+E/N log-uniform 0.1-1000 Td; |B| uniform 0-2 T at a random angle to E),
+every electron run to its 1000th real collision with FP32 flights and FP64
+tallies, all swarms in one persistent launch replayed from a CUDA graph,
+every swarm's tallies reduced on the device and copied to the host.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Prints one JSON line (rank 0).  ``value`` is real collisions per second over
-all ranks (device time, CUDA events on the launching stream, max over
-ranks); ``e2e`` is the same metric through the C ABI with host tables and a
-host read of the tallies inside the timed region; ``roofline`` relates the
+Prints one JSON line (rank 0).  ``value`` is real collisions per second of
+the batched launch over all ranks (device time, CUDA events on the
+launching stream, max over ranks); ``plain`` is the same swarms launched
+one by one at the same window length; ``e2e`` is the same metric through
+the C ABI from host buffers (tables compiled and copied, configurations
+copied, tallies read back) inside the timed region; ``roofline`` relates the
 step kernel's algorithmic thread operations to the SM issue rate;
-``cpu_baseline`` is the FP64 oracle timed on this host's cores.
+``cpu_baseline`` is the FP64 oracle timed on this host's cores.  Further
+keys: the Argon-like sweep (its throughput, its roofline and its drift
+velocity against the oracle, the metric's accuracy qualifier), the Maxwell
+and Ar/CO2 configurations, FP32 against FP64, the paper's trial
+frequencies, and serving latency under Poisson load.
 """
 from __future__ import annotations
 
 import argparse
 import ctypes as C
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -32,12 +42,20 @@ sys.path.insert(0, ROOT)
 
 METRIC = "collisions/s batched vs plain at ≤0.5% drift-velocity error; p99 swarm latency"
 UNIT = "real collisions/s"
-# Algorithmic thread operations of one trial step and the extra of a real
-# collision (counted from the method's arithmetic; see the design notes).
-ALG_OPS_PER_TRIAL = 95
-ALG_OPS_PER_REAL = 90
 SM_COUNT_NOMINAL = 152
 LANES_PER_SM_CLOCK = 4 * 32     # 4 schedulers x 32 lanes issue per clock
+# Algorithmic thread operations of the method, counted from its arithmetic
+# (per trial step, per new trial-frequency window, per real collision) for
+# the two kernel classes the workloads run: "plain" -- B = 0, a few
+# channels searched in shared memory (the Argon-like sweep); "field" -- B != 0
+# and many channels searched in a tree in global memory (the batched
+# workload, Ar/CO2 with B).
+ALG_OPS = {
+    "plain": {"step": 95, "window": 63, "real": 90},
+    "field": {"step": 129, "window": 98, "real": 140},
+}
+LEGS = ("plain", "e2e", "sweep", "oracle", "configs", "precision", "strategies", "serving", "cpu")
+L2_NOTE = "flushed between steps (256 MiB write)"
 
 
 def parse():
@@ -46,25 +64,28 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--points", type=int, default=32)
-    ap.add_argument("--electrons", type=int, default=1_000_000)
+    ap.add_argument("--workload", choices=["batched", "sweep"], default="batched",
+                    help="the headline workload (sweep: the Argon-like E/N sweep)")
+    ap.add_argument("--swarms", type=int, default=256, help="swarms of the batched workload")
+    ap.add_argument("--scale", type=int, default=1, help="divide every swarm's electrons by this (profiling case)")
     ap.add_argument("--collisions", type=int, default=1000)
+    ap.add_argument("--points", type=int, default=32, help="E/N points of the sweep")
+    ap.add_argument("--electrons", type=int, default=1_000_000, help="electrons per point of the sweep")
+    ap.add_argument("--legs", default="all", help="comma list of " + ",".join(LEGS) + ", or all / none")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="bound of the CPU-baseline sample")
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--only-point", type=int, default=-1, help="run one E/N point of the sweep (profiling case)")
-    ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--serve-rates", default="250,1000,2000", help="Poisson arrival rates [req/s] of the serving run")
-    ap.add_argument("--serve-seconds", type=float, default=1.0, help="arrival window of each serving run")
+    ap.add_argument("--oracle-electrons", type=int, default=10_000,
+                    help="oracle electrons per E/N point of the sweep's drift-velocity check")
+    ap.add_argument("--serve-rates", default="250,400,600,800,2000", help="Poisson arrival rates [req/s]")
+    ap.add_argument("--serve-seconds", type=float, default=5.0, help="arrival window of each serving run")
     ap.add_argument("--avalanche-cap", type=int, default=100_000,
                     help="population cap of the serving run's avalanche requests")
     ap.add_argument("--avalanche-frac", type=float, default=0.05, help="fraction of avalanche requests")
-    ap.add_argument("--no-strategies", action="store_true", help="skip the trial-frequency comparison")
-    ap.add_argument("--no-batched-workload", action="store_true", help="skip the 256-swarm batched workload")
     ap.add_argument("--strategy-electrons", type=int, default=100_000)
-    ap.add_argument("--trial", choices=["window", "lazy"], default="window",
-                    help="trial frequency: exact windowed local bound (default) or the constant maximum")
-    return ap.parse_args()
+    ap.add_argument("--precision-electrons", type=int, default=100_000,
+                    help="electrons per swarm of the FP32-against-FP64 comparison")
+    a = ap.parse_args()
+    a.legs = set(LEGS) if a.legs == "all" else set() if a.legs == "none" else set(a.legs.split(","))
+    return a
 
 
 def dist():
@@ -120,74 +141,73 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def profiled_traffic():
-    """DRAM bytes (read + write) of one batched step-kernel launch of this
-    workload from an ncu capture, if the kernel sources are still the ones
-    that capture ran; None otherwise."""
+def profiled_traffic(name):
+    """DRAM bytes (read + write) of one step-kernel launch of a workload from
+    an ncu capture summarised in profiles/<name>.json, if the kernel sources
+    are still the ones that capture ran (else None)."""
     import hashlib
-    root = os.path.dirname(os.path.abspath(__file__))
     try:
-        with open(os.path.join(root, "profiles", "batch_kernel_traffic_argon_sweep.json")) as f:
+        with open(os.path.join(ROOT, "profiles", name + ".json")) as f:
             rec = json.load(f)
         h = hashlib.sha256()
-        for name in rec["sources"]:
-            with open(os.path.join(root, "paper_1901_08140_gb300", "csrc", name), "rb") as f:
+        for src in rec["sources"]:
+            with open(os.path.join(ROOT, "paper_1901_08140_gb300", "csrc", src), "rb") as f:
                 h.update(f.read())
     except (OSError, ValueError, KeyError):
         return None
     if h.hexdigest() != rec["sources_sha256"]:
         return None
-    return rec["dram_bytes_read"] + rec["dram_bytes_write"]
+    return (rec["dram_bytes_read"] + rec["dram_bytes_write"]) * rec.get("scale_to_full", 1.0)
 
 
-def workload_name(args):
-    """The workload both arms name in their JSON line (the same swarms; how
-    each arm samples them is in its own keys)."""
-    return (f"Argon-like E/N sweep: {args.points} log points 1-1000 Td x {args.electrons} electrons x "
-            f"{args.collisions} real collisions, FP32 flights, FP64 tallies, {args.trial} trial frequency, B = 0"
-            + (f" (point {args.only_point} only)" if args.only_point >= 0 else ""))
-
-
-def sweep_specs(args, rank):
+# --------------------------------------------------------------------------
+# workloads
+# --------------------------------------------------------------------------
+def batched_specs(args):
     from paper_1901_08140_gb300 import workloads as W
-    specs = W.argon_sweep(n_electrons=args.electrons, real_collisions=args.collisions, points=args.points)
-    if args.only_point >= 0:
-        specs = [specs[args.only_point]]
+    specs = W.batched_swarms(count=args.swarms, real_collisions=args.collisions)
+    if args.scale > 1:
+        import dataclasses
+        specs = [dataclasses.replace(s, n_electrons=max(1, s.n_electrons // args.scale)) for s in specs]
     return specs
 
 
-def cpu_baseline(args, specs, budget_s):
-    """The FP64 oracle, as it stands, on this host's cores: a bounded sample
-    of the same sweep (the same particle ids of each point, taken point by
-    point in a round-robin of id blocks until the time bound)."""
-    from oracle import oracle as O
-    m = O.Mixture(specs[0].gases)
-    cores = O.cpu_count()
-    block = 64 * cores
-    reals = trials = 0
-    t0 = time.perf_counter()
-    rounds = 0
-    done_points = 0
-    while True:
-        for i, s in enumerate(specs):
-            p = O.run_swarm(m, e_over_n_Td=s.e_over_n_Td, real_collisions=s.real_collisions, n=block, seed=s.seed,
-                            id0=rounds * block, threads=cores)
-            reals += int(p["n_real"].sum())
-            trials += int(p["n_real"].sum() + p["n_null"].sum() + p["n_fail"].sum())
-            done_points += 1
-            if time.perf_counter() - t0 > budget_s and done_points >= min(len(specs), 4):
-                break
-        else:
-            rounds += 1
-            continue
-        break
-    dt = time.perf_counter() - t0
-    sample = (f"{done_points} (E/N point, {block}-electron id block) units of the sweep, "
-              f"I={specs[0].real_collisions}, {reals} real / {trials} trial collisions in {dt:.1f} s")
-    return {"value": reals / dt, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
-            "trial_collisions_per_s": trials / dt}
+def sweep_specs(args):
+    from paper_1901_08140_gb300 import workloads as W
+    return W.argon_sweep(n_electrons=max(1, args.electrons // args.scale), real_collisions=args.collisions,
+                         points=args.points)
 
 
+def batched_name(args, specs):
+    n = sum(s.n_electrons for s in specs)
+    return (f"{len(specs)} swarms, electrons log-uniform 1e3-1e6 ({n} in all"
+            + (f", each swarm's count divided by {args.scale}" if args.scale > 1 else "")
+            + "), 2-4 of 8 synthetic gases (5-40 channels, 100-1000-point tables), E/N 0.1-1000 Td, "
+            f"|B| 0-2 T at random angles, I = {args.collisions} real collisions, FP32 flights, FP64 tallies, "
+            "windowed trial frequency")
+
+
+def sweep_name(args):
+    return (f"Argon-like E/N sweep: {args.points} log points 1-1000 Td x {max(1, args.electrons // args.scale)} "
+            f"electrons x {args.collisions} real collisions, FP32 flights, FP64 tallies, windowed trial "
+            "frequency, B = 0")
+
+
+def workload_config(args):
+    """The `config` both arms print: the workload, its sizes, the L2 rule."""
+    if args.workload == "sweep":
+        specs = sweep_specs(args)
+        name = sweep_name(args)
+    else:
+        specs = batched_specs(args)
+        name = batched_name(args, specs)
+    return specs, {"workload": name, "swarms": len(specs), "electrons": sum(s.n_electrons for s in specs),
+                   "real_collisions": args.collisions, "l2": L2_NOTE}
+
+
+# --------------------------------------------------------------------------
+# timing helpers
+# --------------------------------------------------------------------------
 def _timed(stream, flush, steps, fn, world, dev):
     """Runs fn() `steps` times; device time per step from CUDA events on `stream`."""
     import torch
@@ -209,60 +229,270 @@ def _timed(stream, flush, steps, fn, world, dev):
     return total, outs
 
 
-def batched_workload_runs(ctx, stream, flush, world, dev, collisions, warmup, steps):
-    """The batched workload: 256 swarms, electrons log-uniform 1e3-1e6, 2-4
-    of 8 synthetic gases each with Dirichlet fractions, E/N log-uniform
-    0.1-1000 Td, |B| uniform 0-2 T at a random angle, I real collisions,
-    windowed trial frequency.  Plain: one persistent launch per swarm, back
-    to back; batched: all swarms in one persistent launch replayed from a
-    CUDA graph with the autotuner's launch options."""
+def roofline_of(kind, counts, kern_ms, sm_count, sm_mhz, traffic, kernel):
+    """Algorithmic thread operations over the step kernel's time against the
+    SMs' issue rate (SMs x 4 schedulers x 32 lanes x SM clock)."""
+    ops = ALG_OPS[kind]
+    work = (ops["step"] * counts["steps"] + ops["window"] * counts["windows"] + ops["real"] * counts["reals"])
+    peak = sm_count * LANES_PER_SM_CLOCK * sm_mhz * 1e6
+    achieved = work / (kern_ms / 1e3)
+    return {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tops/s",
+            "frac": achieved / peak, "traffic": traffic, "kernel": kernel,
+            "ops_per_unit": ops, "units": counts,
+            "note": f"algorithmic thread-ops ({ops['step']}/step + {ops['window']}/window + {ops['real']}/real) "
+                    f"over {sm_count} SMs x 128 lanes x median SM clock {sm_mhz:.0f} MHz"}
+
+
+def counts_of(tallies):
+    """Trial steps (real + null + fail + window restarts), new windows (window
+    restarts + real collisions + fails) and real collisions."""
+    reals = sum(t["n_real"] for t in tallies)
+    nulls = sum(t["n_null"] for t in tallies)
+    fails = sum(t["n_fail"] for t in tallies)
+    wins = sum(t["n_window"] for t in tallies)
+    return {"steps": reals + nulls + fails + wins, "windows": wins + reals + fails, "reals": reals,
+            "trials": reals + nulls + fails}
+
+
+# --------------------------------------------------------------------------
+# legs of the GPU arm
+# --------------------------------------------------------------------------
+def batched_run(ctx, stream, flush, world, dev, specs, rank, args, clocks_gpu):
+    """The headline: every swarm in one persistent launch replayed from a CUDA
+    graph with the autotuner's launch options; the same swarms one launch each
+    at the same window length; the autotuned window length's own gain."""
     from paper_1901_08140_gb300 import autotune, bz
-    from paper_1901_08140_gb300 import workloads as W
-    specs = W.batched_swarms(count=256, real_collisions=collisions)
     mixes = [bz.Mixture(ctx, s.gases) for s in specs]
-    cfgs = [bz.config_from_spec(s, trial_mode=bz.BZ_TRIAL_WINDOW) for s in specs]
-
-    def plain_step():
-        return [bz.run_swarm(ctx, m, c, stream) for m, c in zip(mixes, cfgs)]
-
-    for _ in range(warmup):
+    id_off = rank << 32  # weak scaling: every rank runs every swarm on its own ids
+    cfgs = [bz.config_from_spec(s, trial_mode=bz.BZ_TRIAL_WINDOW, id_offset=id_off) for s in specs]
+    choice = autotune.tune(ctx, mixes, cfgs)
+    tuned = autotune.apply(cfgs, choice)
+    batch = autotune.make_batch(ctx, mixes, tuned, choice)
+    for _ in range(args.warmup):
+        batch.launch(stream)
+        batch.tallies(check=False)
+    clocks = clocks_gpu()
+    total_ms = kern_ms = 0.0
+    tallies = []
+    for _ in range(args.steps):
+        ms, _ = _timed(stream, flush, 1, lambda: batch.launch(stream), world, dev)
+        total_ms += ms
+        ts = batch.tallies()
+        tallies += ts
+        kern_ms += batch.timing()[0]
+    clk = clocks.stop()
+    batch.close()
+    out = {"ms": total_ms, "kern_ms": kern_ms, "tallies": tallies, "clocks": clk, "choice": choice,
+           "mixes": mixes, "cfgs": cfgs, "tuned": tuned}
+    if "plain" in args.legs:
+        def plain_step():
+            return [bz.run_swarm(ctx, m, c, stream) for m, c in zip(mixes, tuned)]
         for sw in plain_step():
             sw.tallies(check=False)
             sw.close()
-    plain_ms, outs = _timed(stream, flush, steps, plain_step, world, dev)
-    plain_reals = 0
-    for sws in outs:
-        for sw in sws:
-            plain_reals += sw.tallies(check=False)["n_real"]
-            sw.close()
-    choice = autotune.tune(ctx, mixes, cfgs)
-    batch = bz.Batch(ctx, mixes, autotune.apply(cfgs, choice), tile_particles=choice["tile_particles"],
-                     blocks_per_sm=choice["blocks_per_sm"])
-    for _ in range(warmup):
+        steps = max(1, min(args.steps, 3))
+        pms, outs = _timed(stream, flush, steps, plain_step, world, dev)
+        preals = 0
+        for sws in outs:
+            for sw in sws:
+                preals += sw.tallies()["n_real"]
+                sw.close()
+        out["plain"] = {"ms": pms, "steps": steps, "reals": preals}
+        # the autotuned window length against the default one, batched both
+        if any(abs(c.window_c - 2.0) > 1e-9 for c in tuned):
+            b2 = autotune.make_batch(ctx, mixes, cfgs, dict(choice, window_c=2.0))
+            b2.launch(stream)
+            b2.tallies(check=False)
+            dms, _ = _timed(stream, flush, 1, lambda: b2.launch(stream), world, dev)
+            dreals = sum(t["n_real"] for t in b2.tallies())
+            b2.close()
+            out["default_window"] = {"ms": dms, "reals": dreals}
+    return out
+
+
+def e2e_run(ctx, stream, specs, rank, choice, steps):
+    """The same metric end to end through the C ABI: per step the mixtures'
+    host tables are compiled and copied to the device (16 host threads), the
+    swarm configurations copied, the launch run and every swarm's tallies
+    read back to the host."""
+    import concurrent.futures as cf
+    import torch
+    from paper_1901_08140_gb300 import autotune, bz
+    id_off = rank << 32
+    cfgs = autotune.apply([bz.config_from_spec(s, trial_mode=bz.BZ_TRIAL_WINDOW, id_offset=id_off) for s in specs],
+                          choice)
+    reals, h2d, d2h = 0, 0, 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=16) as ex:
+        for _ in range(steps):
+            mixes = list(ex.map(lambda s: bz.Mixture(ctx, s.gases), specs))
+            b = autotune.make_batch(ctx, mixes, cfgs, choice)
+            b.launch(stream)
+            ts = b.tallies()
+            reals += sum(t["n_real"] for t in ts)
+            h2d += sum(m.info["table_bytes"] for m in mixes) + len(cfgs) * (C.sizeof(bz.bz_swarm_config) + 4096)
+            d2h += len(cfgs) * C.sizeof(bz.bz_tallies)
+            b.close()
+            for m in mixes:
+                m.close()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    return {"value": reals / dt, "unit": UNIT, "h2d_bytes_per_step": h2d // steps, "d2h_bytes_per_step": d2h // steps,
+            "steps": steps, "includes": "mixture compilation and table upload, batch set-up, launch, tallies read"}
+
+
+def sweep_run(ctx, stream, flush, world, dev, args, rank):
+    """The Argon-like sweep: batched (graph, autotuned) and plain throughput,
+    the roofline of its kernel class, the tallies for the oracle check."""
+    from paper_1901_08140_gb300 import autotune, bz
+    specs = sweep_specs(args)
+    mix = bz.Mixture(ctx, specs[0].gases)
+    cfgs = [bz.config_from_spec(s, trial_mode=bz.BZ_TRIAL_WINDOW, id_offset=rank << 32) for s in specs]
+    choice = autotune.tune(ctx, [mix] * len(cfgs), cfgs)
+    tuned = autotune.apply(cfgs, choice)
+    batch = autotune.make_batch(ctx, [mix] * len(cfgs), tuned, choice)
+    for _ in range(2):
         batch.launch(stream)
-        batch.tallies(check=False)
-    ms = 0.0
-    reals = 0
+        batch.tallies()
+    steps = max(1, min(args.steps, 5))
+    ms = kern = 0.0
+    tallies = []
     for _ in range(steps):
         m1, _ = _timed(stream, flush, 1, lambda: batch.launch(stream), world, dev)
         ms += m1
-        reals += sum(t["n_real"] for t in batch.tallies(check=False))
+        tallies = batch.tallies()
+        kern += batch.timing()[0]
     batch.close()
-    value, plain_value = reals / (ms / 1e3), plain_reals / (plain_ms / 1e3)
-    return {"workload": "256 swarms, 1e3-1e6 electrons (log-uniform, %d in all), 2-4 of 8 synthetic gases, "
-                        "E/N 0.1-1000 Td, |B| 0-2 T at random angles, I = %d" % (sum(c.n_electrons for c in cfgs),
-                                                                                  collisions),
-            "value": value, "unit": UNIT, "ms_per_step": ms / steps, "plain": {"value": plain_value,
-            "ms_per_step": plain_ms / steps}, "batched_over_plain": value / plain_value,
-            "autotuned": {k: choice[k] for k in ("window_c", "tile_particles", "blocks_per_sm", "cached")}}
+    pms, outs = _timed(stream, flush, 2, lambda: [bz.run_swarm(ctx, mix, c, stream) for c in tuned], world, dev)
+    preals = 0
+    for sws in outs:
+        for sw in sws:
+            preals += sw.tallies()["n_real"]
+            sw.close()
+    reals = sum(t["n_real"] for t in tallies) * steps
+    return {"workload": sweep_name(args), "value": reals / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
+            "plain": {"value": preals / (pms / 1e3), "ms_per_step": pms / 2},
+            "batched_over_plain": (reals / ms) / (preals / pms),
+            "autotuned": {k: choice.get(k) for k in ("window_c", "tile_particles", "blocks_per_sm", "cached")},
+            "_tallies": tallies, "_kern_ms": kern / steps, "_specs": specs}
+
+
+def sweep_vs_oracle(sweep_tallies, specs, n_oracle):
+    """The sweep's swarm statistics against the FP64 oracle's (the paper's
+    constant trial frequency over an energy range it never leaves, so no
+    fail biases it) on n_oracle electrons per point with ids after the GPU's:
+    relative difference, combined standard error, z-score."""
+    from oracle import oracle as O
+    from oracle import tallies as OT
+    rows = []
+    t0 = time.perf_counter()
+    for s, g in zip(specs, sweep_tallies):
+        m = O.Mixture(s.gases, eps_cap=300.0 if s.e_over_n_Td >= 300.0 else 0.0)
+        p = O.run_swarm(m, e_over_n_Td=s.e_over_n_Td, real_collisions=s.real_collisions, n=n_oracle, seed=s.seed,
+                        id0=s.n_electrons, threads=O.cpu_count())
+        o = OT.swarm_tallies(p, s.e_over_n_Td, m.n_total)
+        row = {"E/N_Td": s.e_over_n_Td, "oracle_fails": int(p["n_fail"].sum())}
+        for k in ("W", "eps", "D_L", "D_T"):
+            se = math.hypot(g[k + "_se"], o[k + "_se"])
+            row[k] = {"rel": (g[k] - o[k]) / abs(o[k]), "rel_se": se / abs(o[k]), "z": (g[k] - o[k]) / se}
+        rows.append(row)
+    summ = {}
+    for k in ("W", "eps", "D_L", "D_T"):
+        zs = [r[k]["z"] for r in rows]
+        resolved = [r for r in rows if 3 * r[k]["rel_se"] <= 0.005]
+        summ[k] = {"max_abs_rel": max(abs(r[k]["rel"]) for r in rows), "max_abs_z": max(abs(z) for z in zs),
+                   "chi2_over_points": sum(z * z for z in zs), "points_resolving_0.5pct": len(resolved),
+                   "resolved_within_0.5pct": sum(1 for r in resolved if abs(r[k]["rel"]) <= 0.005)}
+    return {"oracle_electrons_per_point": n_oracle, "gpu_electrons_per_point": specs[0].n_electrons,
+            "points": len(rows), "seconds": time.perf_counter() - t0, "summary": summ,
+            "max_abs_rel_W": summ["W"]["max_abs_rel"], "per_point": rows}
+
+
+def configs_run(ctx, stream):
+    """Configurations 1 and 3 on their own: the Maxwell-model gas in FP64
+    against its closed forms, and Ar/CO2 90/10 with B = 1 T perpendicular to E."""
+    from paper_1901_08140_gb300 import bz
+    from paper_1901_08140_gb300 import workloads as W
+    QE, ME = 1.602176634e-19, 9.1093837015e-31
+    out = {}
+    spec = W.maxwell_swarm(n_electrons=10_000, real_collisions=1000)
+    mix = bz.Mixture(ctx, spec.gases)
+    cfg = bz.config_from_spec(spec)
+    best = None
+    for _ in range(4):
+        sw = bz.run_swarm(ctx, mix, cfg, stream)
+        t = sw.tallies()
+        ms = sw.timing()[0]
+        sw.close()
+        best = ms if best is None else min(best, ms)
+    g = spec.gases[0]
+    vd = QE * spec.e_over_n_Td * 1e-21 * g.number_density_m3 / (ME * 1e12)
+    out["maxwell_fp64"] = {"workload": "Maxwell-model gas, E/N = 10 Td, 1e4 electrons x 1000 real collisions, FP64",
+                           "value": t["n_real"] / (best / 1e3), "unit": UNIT, "kernel_ms": best,
+                           "W_over_vd": t["W"] / vd, "W_se_over_vd": t["W_se"] / vd, "W_flux_over_vd": t["W_flux"] / vd,
+                           "eps": t["eps"], "eps_closed_form": 5.2580, "eps_se": t["eps_se"]}
+    spec = W.ar_co2_swarm(n_electrons=1_000_000, real_collisions=1000)
+    mix = bz.Mixture(ctx, spec.gases)
+    cfg = bz.config_from_spec(spec, trial_mode=bz.BZ_TRIAL_WINDOW)
+    best = None
+    for _ in range(3):
+        sw = bz.run_swarm(ctx, mix, cfg, stream)
+        t = sw.tallies()
+        ms = sw.timing()[0]
+        sw.close()
+        best = ms if best is None else min(best, ms)
+    out["arco2_B1T"] = {"workload": "Ar/CO2 90/10, E/N = 100 Td, B = 1 T perpendicular to E, 1e6 electrons x 1000 "
+                                    "real collisions, FP32 flights, windowed trial frequency",
+                        "value": t["n_real"] / (best / 1e3), "unit": UNIT, "kernel_ms": best,
+                        "W": t["W"], "W_se": t["W_se"], "Wx": t["Wx"], "Wy": t["Wy"],
+                        "lorentz_angle_rad": t["lorentz_angle"], "D_L": t["D_L"], "D_L_se": t["D_L_se"],
+                        "D_T": t["D_T"], "D_T_se": t["D_T_se"], "efficiency": t["efficiency"]}
+    return out
+
+
+def precision_run(ctx, n):
+    """FP32 flights against FP64 throughout on the same swarms (same seeds and
+    ids): the Argon-like sweep's 32 points and Ar/CO2 with B = 1 T.  Per
+    quantity the largest relative difference and z-score (difference over the
+    combined standard error; the two runs draw the same numbers, so they are
+    not independent and the z-scores overstate the agreement's spread)."""
+    from paper_1901_08140_gb300 import bz
+    from paper_1901_08140_gb300 import workloads as W
+    out = {}
+    for name, specs in (("argon_sweep", W.argon_sweep(n_electrons=n, real_collisions=1000, points=32)),
+                        ("arco2_B1T", [W.ar_co2_swarm(n_electrons=n, real_collisions=1000)])):
+        mix = bz.Mixture(ctx, specs[0].gases)
+        res = {}
+        for prec in (32, 64):
+            cfgs = [bz.config_from_spec(s, precision=prec, trial_mode=bz.BZ_TRIAL_WINDOW) for s in specs]
+            b = bz.Batch(ctx, [mix] * len(cfgs), cfgs, use_graph=False)
+            b.launch()
+            res[prec] = b.tallies()
+            res["ms%d" % prec] = b.timing()[0]
+            b.close()
+        q = {}
+        for k in ("W", "eps", "eps_after", "alpha", "D_L", "D_T"):
+            rel, z = [], []
+            for a, b64 in zip(res[32], res[64]):
+                if b64[k] == 0:
+                    continue
+                rel.append(abs(a[k] - b64[k]) / abs(b64[k]))
+                se = math.hypot(a.get(k + "_se", 0.0) or 0.0, b64.get(k + "_se", 0.0) or 0.0)
+                if se > 0:
+                    z.append(abs(a[k] - b64[k]) / se)
+            q[k] = {"max_rel": max(rel) if rel else None, "median_rel": statistics.median(rel) if rel else None,
+                    "max_z": max(z) if z else None}
+        out[name] = {"electrons_per_swarm": n, "swarms": len(specs), "fp32_ms": res["ms32"], "fp64_ms": res["ms64"],
+                     "quantities": q}
+    return out
 
 
 def strategy_runs(ctx, mix, specs, electrons):
-    """The argon sweep at `electrons` per point under each trial frequency
+    """The Argon-like sweep at `electrons` per point under each trial frequency
     (Sec. 6): real collisions/s of the step kernel, efficiency (Eq. 28),
     fails, electrons stopped by an error, and the largest deviation of W
     from the exact windowed run in combined standard errors."""
-    import math
     from paper_1901_08140_gb300 import bz
     modes = [("window", bz.BZ_TRIAL_WINDOW), ("lazy", bz.BZ_TRIAL_LAZY), ("variable", bz.BZ_TRIAL_VARIABLE),
              ("binned", bz.BZ_TRIAL_BINNED)]
@@ -298,13 +528,12 @@ def serving_runs(ctx, rates, seconds, collisions=100, pool=64, streams=3, avalan
     mixtures), I real collisions per request, windowed trial frequency; a
     fraction are avalanche requests (Ar/CO2 93/7, 300 Td, spawn mode, one
     seed electron, 1 ns, population cap avalanche_cap)."""
+    import numpy as np
     from paper_1901_08140_gb300 import bz, serving
     from paper_1901_08140_gb300 import workloads as W
-    import numpy as np
     specs = W.batched_swarms(count=pool, real_collisions=collisions)
     mixes = [bz.Mixture(ctx, s.gases) for s in specs]
     ava_mix = bz.Mixture(ctx, W.ar_co2_avalanche_mixture())
-    backend = serving.GpuBatchBackend(ctx, n_streams=streams)
     out = []
     for k, rate in enumerate(rates):
         n = max(1, int(rate * seconds))
@@ -322,7 +551,7 @@ def serving_runs(ctx, rates, seconds, collisions=100, pool=64, streams=3, avalan
             j = int(rng.integers(pool))
             cfg = bz.config_from_spec(specs[j], trial_mode=bz.BZ_TRIAL_WINDOW, seed=seed)
             reqs.append(serving.Request(i, mixes[j], cfg, arrival=float(arr[i]), n_electrons=int(cfg.n_electrons)))
-        srv = serving.Server(backend, memory_budget=60e9)
+        srv = serving.Server(ctx, memory_budget=60e9, n_slots=streams)
         done = srv.run(reqs, realtime=True)
         summ = serving.latency_summary(done)
         ava = [r for r in done if getattr(r.cfg, "spawn", 0)]
@@ -334,9 +563,42 @@ def serving_runs(ctx, rates, seconds, collisions=100, pool=64, streams=3, avalan
                                  "mean_final_population": float(np.mean([r.tallies["n_particles"] for r in ava]))}
         offered += sum(r.tallies["n_real"] for r in ava) / arr[-1] if n > 1 else 0.0
         summ.update({"rate_req_s": rate, "offered_real_collisions_per_s": offered,
-                     "max_concurrent": srv.max_concurrent, "launch_groups": srv.groups})
+                     "served_fraction": summ["real_collisions_per_s"] / offered if offered else None,
+                     "max_concurrent": srv.stats()["max_running"], "launch_groups": srv.stats()["launches"]})
+        srv.close()
         out.append(summ)
     return out
+
+
+def cpu_baseline(args, specs, budget_s):
+    """The FP64 oracle, as it stands, on this host's cores: a bounded sample of
+    the same swarms -- rounds over the swarms, a block of electrons each with
+    ids after the GPU's, until the time bound."""
+    from oracle import oracle as O
+    cores = O.cpu_count()
+    block = 4 * cores
+    reals = trials = units = 0
+    t0 = time.perf_counter()
+    k = 0
+    cache = {}
+    while time.perf_counter() - t0 < budget_s or units < 2:
+        s = specs[k % len(specs)]
+        key = id(s.gases)
+        if key not in cache:
+            cache = {key: O.Mixture(s.gases)}
+        p = O.run_swarm(cache[key], e_over_n_Td=s.e_over_n_Td, b_T=s.b_T, b_angle_rad=s.b_angle_rad,
+                        real_collisions=s.real_collisions, n=block, seed=s.seed,
+                        id0=(1 << 40) + (k // len(specs)) * block, threads=cores)
+        reals += int(p["n_real"].sum())
+        trials += int(p["n_real"].sum() + p["n_null"].sum() + p["n_fail"].sum())
+        units += 1
+        k += 1
+    dt = time.perf_counter() - t0
+    sample = (f"{units} (swarm, {block}-electron id block) units taken round-robin over the {len(specs)} swarms, "
+              f"I={specs[0].real_collisions}, FP64, the paper's constant trial frequency; {reals} real / {trials} "
+              f"trial collisions in {dt:.1f} s")
+    return {"value": reals / dt, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+            "trial_collisions_per_s": trials / dt}
 
 
 def run_ours(args):
@@ -349,164 +611,139 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     from paper_1901_08140_gb300 import build as B
     B.build()
-    from paper_1901_08140_gb300 import bz
-    specs = sweep_specs(args, rank)
+    from paper_1901_08140_gb300 import bz, sharding
     ctx = bz.Context(local)
-    mix = bz.Mixture(ctx, specs[0].gases)
-    # weak scaling: every rank runs the whole sweep on its own particle ids
-    mode = bz.BZ_TRIAL_WINDOW if args.trial == "window" else bz.BZ_TRIAL_LAZY
-    from paper_1901_08140_gb300 import sharding
-    cfgs = [bz.config_from_spec(s, id_offset=sharding.weak_offset(rank, args.electrons), trial_mode=mode)
-            for s in specs]
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    specs, config = workload_config(args)
+    out = {"metric": METRIC, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": config}
 
-    # ---- plain: one persistent launch per swarm, back to back on one stream
-    def plain_step():
-        return [bz.run_swarm(ctx, mix, c, stream) for c in cfgs]
-
-    for _ in range(args.warmup):
-        for sw in plain_step():
-            sw.tallies()
-            sw.close()
-    plain_ms, plain_outs = _timed(stream, flush, args.steps, plain_step, world, dev)
-    plain_reals = 0
-    for sws in plain_outs:
-        for sw in sws:
-            plain_reals += sw.tallies()["n_real"]
-            sw.close()
-
-    # ---- batched: every swarm in one persistent launch, replayed from a CUDA graph,
-    # with the launch options the autotuner picks (cached per GPU and workload class)
-    from paper_1901_08140_gb300 import autotune
-    choice = autotune.tune(ctx, [mix] * len(cfgs), cfgs)
-    bcfgs = autotune.apply(cfgs, choice)
-    batch = bz.Batch(ctx, [mix] * len(cfgs), bcfgs, tile_particles=choice["tile_particles"],
-                     blocks_per_sm=choice["blocks_per_sm"])
-
-    def batch_step():
-        batch.launch(stream)
-        return None
-
-    for _ in range(args.warmup):
-        batch_step()
-        batch.tallies()
-    clocks = Clocks(local)
-    reals = trials = 0
-    kern_ms = 0.0
-    steps_other = 0
-    work = 0.0
-    w_err = []
-    total_ms = 0.0
-    for _ in range(args.steps):
-        ms, _ = _timed(stream, flush, 1, batch_step, world, dev)
-        total_ms += ms
-        ts = batch.tallies()
-        km, _ = batch.timing()
-        kern_ms += km
-        for t in ts:
-            tr = t["n_real"] + t["n_null"] + t["n_fail"]
-            reals += t["n_real"]
-            trials += tr
-            steps_other += t["n_window"]
-            work += ALG_OPS_PER_TRIAL * (tr + t["n_window"]) + ALG_OPS_PER_REAL * t["n_real"]
-            w_err.append(t["W_se"] / abs(t["W"]) if t["W"] else float("inf"))
-    clk = clocks.stop()
-    launches = 5 * args.steps   # batch kernel + 4 multi-swarm tally kernels, in one graph
-    t_max, tot_reals = sharding.reduce_step(total_ms, reals)
-    p_max, tot_plain = sharding.reduce_step(plain_ms, plain_reals)
+    # ---- the headline workload
+    if args.workload == "batched":
+        r = batched_run(ctx, stream, flush, world, dev, specs, rank, args, lambda: Clocks(local))
+        kind, kernel = "field", "batch_kernel (lean FP32 build with the field's paths, 3 blocks/SM)"
+        prof = "batch_kernel_batched_256"
+    else:
+        from paper_1901_08140_gb300 import autotune
+        mix = bz.Mixture(ctx, specs[0].gases)
+        cfgs = [bz.config_from_spec(s, trial_mode=bz.BZ_TRIAL_WINDOW, id_offset=rank << 32) for s in specs]
+        choice = autotune.tune(ctx, [mix] * len(cfgs), cfgs)
+        tuned = autotune.apply(cfgs, choice)
+        b = autotune.make_batch(ctx, [mix] * len(cfgs), tuned, choice)
+        for _ in range(args.warmup):
+            b.launch(stream)
+            b.tallies()
+        clocks = Clocks(local)
+        ms = kms = 0.0
+        tl = []
+        for _ in range(args.steps):
+            m1, _ = _timed(stream, flush, 1, lambda: b.launch(stream), world, dev)
+            ms += m1
+            tl += b.tallies()
+            kms += b.timing()[0]
+        b.close()
+        r = {"ms": ms, "kern_ms": kms, "tallies": tl, "clocks": clocks.stop(), "choice": choice,
+             "mixes": [mix] * len(cfgs), "tuned": tuned}
+        kind, kernel = "plain", "batch_kernel (lean FP32 build without field paths; 4 blocks/SM where the tables fit)"
+        prof = "batch_kernel_traffic_argon_sweep"
+    reals = sum(t["n_real"] for t in r["tallies"])
+    t_max, tot_reals = sharding.reduce_step(r["ms"], reals)
     value = tot_reals / (t_max / 1e3)
-    plain_value = tot_plain / (p_max / 1e3)
-
-    # end to end through the C ABI: host tables in, host tallies out
-    e2e = None
-    if not args.no_e2e:
-        torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        m2 = bz.Mixture(ctx, specs[0].gases)
-        b2 = bz.Batch(ctx, [m2] * len(cfgs), bcfgs, tile_particles=choice["tile_particles"],
-                      blocks_per_sm=choice["blocks_per_sm"])
-        b2.launch(stream)
-        e_reals = sum(t["n_real"] for t in b2.tallies())
-        torch.cuda.synchronize(dev)
-        dt = time.perf_counter() - t0
-        h2d = m2.info["table_bytes"] + len(cfgs) * (C.sizeof(bz.bz_swarm_config) + 4096)
-        d2h = len(cfgs) * C.sizeof(bz.bz_tallies)
-        b2.close()
-        m2.close()
-        e2e = {"value": e_reals / dt, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
-    batch.close()
-
+    clk = r["clocks"]
     sm_mhz = clk.get("sm_mhz") or 2070.0
-    peak = torch.cuda.get_device_properties(dev).multi_processor_count * LANES_PER_SM_CLOCK * sm_mhz * 1e6
-    achieved = work / (kern_ms / 1e3)
-    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tops/s",
-                "frac": achieved / peak, "traffic": profiled_traffic(),
-                "kernel": "batch_kernel (lean FP32 build without field paths; 4 blocks/SM where the tables fit)",
-                "note": f"algorithmic thread-ops ({ALG_OPS_PER_TRIAL}/step + {ALG_OPS_PER_REAL}/real) over "
-                        f"SMs x 128 lanes x median SM clock {sm_mhz:.0f} MHz"}
-    batched_workload = None
-    if not args.no_batched_workload and args.only_point < 0:
-        batched_workload = batched_workload_runs(ctx, stream, flush, world, dev, args.collisions,
-                                                 max(1, args.warmup - 2), max(1, min(args.steps, 2)))
-    strategies = None
-    if not args.no_strategies and rank == 0:
-        strategies = strategy_runs(ctx, mix, specs, min(args.strategy_electrons, args.electrons))
-    serve = None
-    if not args.no_serving and rank == 0:
+    counts = counts_of(r["tallies"])
+    out.update({"value": value, "ms_per_step": t_max / args.steps,
+                "roofline": roofline_of(kind, counts, r["kern_ms"], sm_count, sm_mhz, profiled_traffic(prof), kernel),
+                "clocks": clk, "gpu_launches": 5 * args.steps,
+                "autotuned": {k: r["choice"].get(k) for k in ("window_c", "tile_particles", "blocks_per_sm",
+                                                             "staging", "cached")},
+                "trial_collisions_per_s": counts["trials"] * world / (t_max / 1e3),
+                "efficiency": counts["reals"] / counts["trials"] if counts["trials"] else None,
+                "window_restarts_per_real": (counts["windows"] - counts["reals"]) / counts["reals"]})
+    if "plain" in r:
+        p = r["plain"]
+        p_max, p_reals = sharding.reduce_step(p["ms"], p["reals"])
+        pv = p_reals / (p_max / 1e3)
+        out["plain"] = {"value": pv, "ms_per_step": p_max / p["steps"], "steps": p["steps"],
+                        "mode": "one persistent launch per swarm, back to back on one stream, the batched "
+                                "launch's window length"}
+        out["batched_over_plain"] = value / pv
+    if "default_window" in r:
+        d = r["default_window"]
+        out["window_length_gain"] = {"autotuned_window_c": r["choice"]["window_c"],
+                                     "batched_at_default_window_c_2": d["reals"] / (d["ms"] / 1e3),
+                                     "gain": value / (d["reals"] / (d["ms"] / 1e3))}
+    if "e2e" in args.legs:
+        out["e2e"] = e2e_run(ctx, stream, specs, rank, r["choice"], max(1, min(args.steps, 3)))
+    # ---- further legs (rank 0)
+    if rank == 0 and args.workload == "batched" and ("sweep" in args.legs or "oracle" in args.legs):
+        sw = sweep_run(ctx, stream, flush, world, dev, args, rank)
+        sw_counts = counts_of(sw["_tallies"])
+        sw["roofline"] = roofline_of("plain", sw_counts, sw["_kern_ms"], sm_count, sm_mhz,
+                                     profiled_traffic("batch_kernel_traffic_argon_sweep"),
+                                     "batch_kernel (lean FP32 build without field paths; 4 blocks/SM)")
+        if "oracle" in args.legs:
+            sw["drift_velocity_vs_oracle"] = sweep_vs_oracle(sw["_tallies"], sw["_specs"], args.oracle_electrons)
+            out["max_rel_err_W_vs_oracle"] = sw["drift_velocity_vs_oracle"]["max_abs_rel_W"]
+        for k in ("_tallies", "_kern_ms", "_specs"):
+            sw.pop(k)
+        out["argon_sweep"] = sw
+    if rank == 0 and "configs" in args.legs:
+        out["configurations"] = configs_run(ctx, stream)
+    if rank == 0 and "precision" in args.legs:
+        out["precision_fp32_vs_fp64"] = precision_run(ctx, args.precision_electrons)
+    if rank == 0 and "strategies" in args.legs:
+        from paper_1901_08140_gb300 import workloads as W
+        ss = W.argon_sweep(points=32)
+        out["trial_strategies"] = strategy_runs(ctx, bz.Mixture(ctx, ss[0].gases), ss,
+                                                min(args.strategy_electrons, args.electrons))
+    if rank == 0 and "serving" in args.legs:
         rates = [float(x) for x in args.serve_rates.split(",") if x]
         serve = serving_runs(ctx, rates, args.serve_seconds, avalanche_frac=args.avalanche_frac,
                              avalanche_cap=args.avalanche_cap)
+        out["serving"] = serve
+        kept = [x for x in serve if x["served_fraction"] is not None and x["served_fraction"] >= 0.9]
+        top = max(kept, key=lambda x: x["rate_req_s"]) if kept else None
+        out["p99_swarm_latency_ms"] = top["p99_ms"] if top else None
+        out["p99_at_rate_req_s"] = top["rate_req_s"] if top else None
+        last = max(serve, key=lambda x: x["rate_req_s"])
+        out["p99_at_highest_rate"] = {"rate_req_s": last["rate_req_s"], "p99_ms": last["p99_ms"],
+                                      "served_fraction": last["served_fraction"],
+                                      "saturated": (last["served_fraction"] or 0) < 0.9}
     if rank != 0:
         return
-    cpu = None
-    if not args.no_cpu_baseline:
-        cpu = cpu_baseline(args, specs, args.cpu_seconds)
-    out = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": workload_name(args),
-                   "mode": "batched: all swarms in one persistent launch replayed from a CUDA graph",
-                   "swarms": len(specs), "electrons_per_swarm": args.electrons, "real_collisions": args.collisions,
-                   "l2": "flushed between steps (256 MiB write)", "parallelism": f"dp{world} (particle ids)",
-                   "autotuned": {k: choice[k] for k in ("window_c", "tile_particles", "blocks_per_sm", "cached")}},
-        "plain": {"value": plain_value, "ms_per_step": p_max / args.steps,
-                  "mode": "one persistent launch per swarm, back to back on one stream"},
-        "batched_over_plain": value / plain_value,
-        "trial_collisions_per_s": trials * world / (t_max / 1e3),
-        "efficiency": reals / trials if trials else None,
-        "window_restarts_per_real": steps_other / reals if reals else None,
-        "max_rel_se_W": max(w_err) if w_err else None,
-        "trial_frequency": args.trial,
-        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
-        "batched_workload": batched_workload,
-        "trial_strategies": strategies,
-        "serving": serve,
-        # p99 at the highest arrival rate the GPU kept up with (>= 90 % of the offered work)
-        "p99_swarm_latency_ms": (max(((x["rate_req_s"], x["p99_ms"]) for x in serve
-                                      if x["real_collisions_per_s"] >= 0.9 * x["offered_real_collisions_per_s"]),
-                                     default=(None, None))[1] if serve else None),
-    }
+    if "cpu" in args.legs:
+        out["cpu_baseline"] = cpu_baseline(args, specs, args.cpu_seconds)
     print(json.dumps(out), flush=True)
 
 
 def run_reference(args):
+    """The oracle on this host's cores over the same workload: every step a
+    bounded sample of it (a rotating set of swarms, a block of electrons
+    each), the paper's constant trial frequency in FP64."""
     world, rank, local = dist()
     if rank != 0:
         return
     from oracle import oracle as O
-    specs = sweep_specs(args, 0)
-    m = O.Mixture(specs[0].gases)
+    specs, config = workload_config(args)
     cores = O.cpu_count()
-    block = 16 * cores
-    # one step: a bounded sample of the sweep (every E/N point, `block` electrons)
+    block = 4 * cores
+    per_step = min(len(specs), 8)
+    mixes = {}
 
     def step(k):
         r = t = 0
-        for s in specs:
-            p = O.run_swarm(m, e_over_n_Td=s.e_over_n_Td, real_collisions=s.real_collisions, n=block, seed=s.seed,
-                            id0=k * block, threads=cores)
+        for j in range(per_step):
+            i = (k * per_step + j) % len(specs)
+            s = specs[i]
+            if i not in mixes:
+                mixes[i] = O.Mixture(s.gases)
+            p = O.run_swarm(mixes[i], e_over_n_Td=s.e_over_n_Td, b_T=s.b_T, b_angle_rad=s.b_angle_rad,
+                            real_collisions=s.real_collisions, n=block, seed=s.seed, id0=(1 << 40) + k * block,
+                            threads=cores)
             r += int(p["n_real"].sum())
             t += int(p["n_real"].sum() + p["n_null"].sum() + p["n_fail"].sum())
         return r, t
@@ -521,13 +758,13 @@ def run_reference(args):
         trials += t
     dt = time.perf_counter() - t0
     value = reals / dt
-    sample = (f"per step: all {len(specs)} E/N points x {block} electrons x I={specs[0].real_collisions} "
-              f"(FP64 oracle, Lazy exact trial frequency, {cores} threads)")
+    sample = (f"per step: {per_step} of the {len(specs)} swarms (taken in turn) x {block} electrons x "
+              f"I={specs[0].real_collisions} (FP64 oracle, the paper's constant trial frequency, {cores} threads)")
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-        "config": {"workload": workload_name(args), "sample": sample},
+        "config": config, "sample": sample,
         "trial_collisions_per_s": trials / dt,
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},

@@ -66,10 +66,16 @@ def apply(cfgs: Sequence[bz.bz_swarm_config], choice: dict) -> List[bz.bz_swarm_
             for c in cfgs]
 
 
+def make_batch(ctx, mixtures, cfgs, choice, use_graph: bool = True) -> "bz.Batch":
+    """A batch launched with the chosen options (cfgs already carry the
+    chosen window length, see apply)."""
+    return bz.Batch(ctx, mixtures, cfgs, tile_particles=int(choice.get("tile_particles", 0)),
+                    blocks_per_sm=int(choice.get("blocks_per_sm", 0)), use_graph=use_graph)
+
+
 def _measure(ctx, mixtures, cfgs, choice, repeats=2) -> float:
     """Real collisions per millisecond of step-kernel time."""
-    b = bz.Batch(ctx, mixtures, apply(cfgs, choice), tile_particles=choice["tile_particles"],
-                 blocks_per_sm=choice["blocks_per_sm"])
+    b = make_batch(ctx, mixtures, apply(cfgs, choice), choice)
     best = 0.0
     for _ in range(repeats):
         b.launch()

@@ -1,6 +1,6 @@
 """bench.py's reference arm (the FP64 oracle on the host's cores) on the CPU:
-one JSON line with the contract's keys, the same workload name as the GPU
-arm, and a bounded sample described in its cpu_baseline."""
+one JSON line with the contract's keys, the same workload (config) as the
+GPU arm, and a bounded sample described in its cpu_baseline."""
 import json
 import os
 import subprocess
@@ -11,7 +11,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def test_reference_arm_prints_one_contract_line():
     cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1", "--warmup", "1",
-           "--points", "2", "--electrons", "1000", "--collisions", "20"]
+           "--swarms", "6", "--scale", "1000", "--collisions", "20"]
     out = subprocess.run(cmd, capture_output=True, text=True, timeout=600, cwd=ROOT)
     assert out.returncode == 0, out.stderr[-2000:]
     lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
@@ -22,7 +22,8 @@ def test_reference_arm_prints_one_contract_line():
         assert k in d, k
     assert d["impl"] == "reference" and d["steps"] == 1 and d["warmup"] == 1
     assert d["value"] > 0 and d["higher_is_better"] is True and d["unit"] == "real collisions/s"
-    assert d["config"]["workload"].startswith("Argon-like E/N sweep: 2 log points")
+    assert d["config"]["workload"].startswith("6 swarms, electrons log-uniform 1e3-1e6")
+    assert d["config"]["swarms"] == 6 and d["config"]["real_collisions"] == 20 and "l2" in d["config"]
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
@@ -35,8 +36,8 @@ def test_reference_arm_under_torchrun_prints_from_rank_0_only():
         port = sk.getsockname()[1]
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
            "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.join(ROOT, "bench.py"),
-           "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "1", "--points", "2",
-           "--electrons", "1000", "--collisions", "20"]
+           "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "1", "--swarms", "4",
+           "--scale", "1000", "--collisions", "20"]
     out = subprocess.run(cmd, capture_output=True, text=True, timeout=600, cwd=ROOT)
     assert out.returncode == 0, out.stderr[-2000:]
     lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
