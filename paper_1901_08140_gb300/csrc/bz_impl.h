@@ -27,6 +27,7 @@ constexpr int kQ2 = 8;        // second-pass tally quantities
 // memory out of a GB300 SM's 228 KB), and one FP64 block.
 constexpr size_t kStageBudget32 = 72 * 1024;
 constexpr size_t kStageBudget64 = 200 * 1024;
+constexpr int kGuide = 256;  // buckets of the channel-search guide
 
 // One interval [e_lo, e_hi) of the union energy grid: the density sum
 // S(eps) = sum n_k sigma_kj(eps) of all channels not in their power-law
@@ -81,6 +82,11 @@ struct Layout {
     // the order of Eq. 2): entry j is the sum of channels 0..j, searched by
     // bisection on real collisions when the channel values are not staged
     uint32_t off_cum;
+    // guide of the search (mixtures of at most 255 channels, else 0): per
+    // record r a row of kGuide bytes at off_guide + r kGuide; entry b of row r
+    // is the first channel whose cumulative value reaches b/kGuide of the
+    // density sum at the lower edge of record r (row r + 1: at its upper edge)
+    uint32_t off_guide;
     int32_t buckets_per_record;
     double s_min;            // speed at the first bin edge [m/s]
     int32_t n_bins, bin_levels;  // sparse table: level l at [l * n_bins + b] = max over bins [b, b + 2^l)

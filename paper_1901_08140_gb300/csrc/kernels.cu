@@ -185,6 +185,7 @@ struct Tab {
     const ChParam<R> *chp;
     const ChVal<R> *chval;
     const ChVal<R> *cum;   // cumulative channel values (global memory)
+    const uint8_t *guide;  // guide rows of the search (null: bisection only)
     const R *binmax;  // sparse table of per-bin maxima (level-major)
     const ChVal<R> *gval;  // per-record, per-gas density sums (global memory)
     const Layout *lay;     // gas channel ranges
@@ -207,6 +208,7 @@ __device__ __forceinline__ Tab<R> make_tab(const uint8_t *smem, const uint8_t *b
     T.chp = (const ChParam<R> *)(smem + L.off_chp);
     T.chval = (const ChVal<R> *)((ch_smem ? smem : blob) + L.off_chval);
     T.cum = (const ChVal<R> *)(blob + L.off_cum);
+    T.guide = L.off_guide ? blob + L.off_guide : nullptr;
     T.n_rec = L.n_rec;
     T.n_buckets = L.n_buckets;
     T.n_ch = L.n_ch;
@@ -291,30 +293,80 @@ __device__ __forceinline__ ChVal<R> load_chval(const ChVal<R> *p, bool ch_smem)
 //
 // Where the channel values are not staged (many channels, read through L1
 // from global memory), the search runs on the record's cumulative values
-// instead: the first j whose cumulative value reaches the target, found by
-// bisection in ceil(log2 n_ch) steps.  The step count depends on the mixture
-// only, so the lanes of a warp that collide run the search together (a
-// channel-by-channel scan would keep the warp for its slowest lane), and
-// each step is one 8-byte load.  (A 16-ary search tree with two levels took
-// two trips to L2 instead of up to eight, but read four times the bytes and
-// needed more registers: 12 % slower on the 256-swarm workload.)  The
-// target is first clamped to the record's total: where rounding leaves it a
-// hair above, the search lands on the last channel that adds to the total
-// (the first entry equal to it).
+// instead: the first j whose cumulative value reaches the target.  A guide
+// proposes where to look: the target's fraction u of the density sum S
+// names one of kGuide buckets, and each record end's guide row names the
+// first channel that reaches the bucket's lower fraction there; every
+// channel's share of the cumulative sum varies monotonically between the
+// record's ends, so the answer cannot lie below the smaller of the two ends'
+// entries (L) nor above the larger of the next bucket's (U).  One round trip
+// reads the guide bytes and the record's total, a second the cumulative
+// values at L - 1, L and L + 1; 97 % of the searches end there (256
+// buckets, the 256-swarm workload's mixtures).  The cumulative values
+// decide, not the guide: if rounding left the answer below L or above U,
+// or in a wide bucket, a bisection finishes the search, so the result is
+// always the first index reaching the target.  (Bisecting the whole row took
+// ceil(log2 n_ch) dependent trips to L2 per real collision; a 16-ary search
+// tree took two, but read four times the bytes and needed more registers:
+// 12 % slower.)  The target is first clamped to the record's total: where
+// rounding leaves it a hair above, the search lands on the last channel that
+// adds to the total (the first entry equal to it).  Every entry is evaluated
+// with the same fused multiply-add, so the clamp and the search agree.
+__device__ __forceinline__ float fma_(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fma_(double a, double b, double c) { return fma(a, b, c); }
+
+template <typename R>
+__device__ __forceinline__ R cum_at(const ChVal<R> &c, R de)
+{
+    return fma_(c.slope, de, c.val);
+}
+
+// First j in [lo, hi] whose cumulative value reaches the target, or hi
+// (whose value the caller knows to reach it).
+template <typename R>
+__device__ __noinline__ int cum_lower_bound(const ChVal<R> *row, int lo, int hi, R de, R target)
+{
+    int base = lo, len = hi - lo + 1;
+    while (len > 1) {
+        const int half = len >> 1;
+        if (cum_at(ldg_chval(row + base + half - 1), de) < target) base += half;
+        len -= half;
+    }
+    return base;
+}
+
 template <typename R, bool CH_SMEM>
-__device__ __forceinline__ int select_channel(const Tab<R> &T, int ri, R e_lo, R eps, R target)
+__device__ __forceinline__ int select_channel(const Tab<R> &T, int ri, R e_lo, R eps, R target, R S)
 {
     const R de = eps - e_lo;
     if (!CH_SMEM && ri < T.first_tail) {
-        const ChVal<R> *row = T.cum + (size_t)ri * T.n_ch;
-        const ChVal<R> top = ldg_chval(row + T.n_ch - 1);
-        target = min_(target, top.val + top.slope * de);
-        int base = 0, len = T.n_ch;
+        const int n = T.n_ch;
+        const ChVal<R> *row = T.cum + (size_t)ri * n;
+        const ChVal<R> top = ldg_chval(row + n - 1);
+        if (T.guide) {
+            const uint8_t *gl = T.guide + (size_t)ri * kGuide, *gh = gl + kGuide;
+            const float u = (S > (R)0) ? (float)(target / S) : 0.0f;
+            const int b = min(max((int)(u * (float)kGuide), 0), kGuide - 1);
+            const int L = min((int)__ldg(gl + b), (int)__ldg(gh + b));
+            const int U = (b + 1 < kGuide) ? max((int)__ldg(gl + b + 1), (int)__ldg(gh + b + 1)) : n - 1;
+            target = min_(target, cum_at(top, de));
+            const R v0 = cum_at(ldg_chval(row + L), de);
+            const R v1 = cum_at(ldg_chval(row + min(L + 1, n - 1)), de);
+            const R vm = cum_at(ldg_chval(row + max(L - 1, 0)), de);
+            if (L > 0 && !(vm < target)) return cum_lower_bound(row, 0, L - 1, de, target);  // below L (rounding)
+            if (!(v0 < target)) return L;
+            if (!(v1 < target)) return min(L + 1, n - 1);
+            // a bucket with several channels, or the answer above U by rounding
+            const int hi = min(max(U, L + 2), n - 1);
+            if (cum_at(ldg_chval(row + hi), de) < target) return cum_lower_bound(row, hi + 1, n - 1, de, target);
+            return cum_lower_bound(row, L + 2, hi, de, target);
+        }
+        target = min_(target, cum_at(top, de));
+        int base = 0, len = n;
         // the answer lies in [base, base + len): each step halves len
         for (int k = 0; k < T.ch_steps; ++k) {
             const int half = len >> 1;
-            const ChVal<R> c = ldg_chval(row + base + half - 1);
-            if (c.val + c.slope * de < target) base += half;
+            if (cum_at(ldg_chval(row + base + half - 1), de) < target) base += half;
             len -= half;
         }
         return base;
@@ -1105,7 +1157,7 @@ __device__ __forceinline__ int trial(const Tab<R> &T, const Fld<R> &F, const Run
             }
         } else {
             // ---- real collision ----
-            const int c = select_channel<R, CH_SMEM>(T, ri, elo, eps, r * inv_sp);
+            const int c = select_channel<R, CH_SMEM>(T, ri, elo, eps, r * inv_sp, S);
             {
                 R dx, dy, dz;
                 displacement<R, BF>(F, s, Tn, sn, omc, dx, dy, dz);
@@ -1534,8 +1586,6 @@ __device__ __forceinline__ uint64_t global_ns()
     return t;
 }
 
-// A warp that has no electron to run gives up after this long without one.
-constexpr uint64_t kSpawnWaitNs = 60ull * 1000000000ull;
 
 // Spawn mode (ChildrenBulletLimiter, Sec. 3.2): one persistent launch runs
 // the primaries and every electron created from them.  A lane without an
@@ -1611,7 +1661,7 @@ __global__ void __launch_bounds__(kBlock, MINB) spawn_kernel(const __grid_consta
             const uint64_t now = global_ns();
             if (wait_since == 0) {
                 wait_since = now;
-            } else if (now - wait_since > kSpawnWaitNs) {
+            } else if (now - wait_since > P.spawn_wait_ns) {  // a warp without work gives up
                 if (lane == 0) atomicOr(P.err, BZ_ERR_SPAWN_WAIT);
                 break;
             }
@@ -1824,7 +1874,35 @@ __device__ void tally_pass1_body(const TallyArgs &A, int bx, int nbx)
 
 // gsum layout: [g][0..kQ1) pass 1, [g][kQ1..kQ1+kQ2) pass 2, then summary
 // values at kGroups*(kQ1+kQ2): Wx, Wy, Wz, Wfx, Wfy, Wfz.
-constexpr int kGS = kQ1 + kQ2;
+
+}  // namespace
+
+// The swarm's drift vectors from the pass-1 group sums (gsum[g][q], row
+// stride kGS): S[0..2] = W_vec = <x/t, y/t, z/t> (Eq. 15 per component),
+// S[3..5] = the flux form (sum x, sum y, sum z) / sum t.  Host and device.
+__host__ __device__ void drift_of_groups(const double *gsum, double *S)
+{
+    double c = 0, sx = 0, sy = 0, sz = 0, X = 0, Y = 0, Z = 0, Tt = 0;
+    for (int k = 0; k < kGroups; ++k) {
+        const double *r = gsum + k * kGS;
+        c += r[0];
+        sx += r[1];
+        sy += r[2];
+        sz += r[3];
+        X += r[6];
+        Y += r[7];
+        Z += r[8];
+        Tt += r[9];
+    }
+    S[0] = c > 0 ? sx / c : 0.0;
+    S[1] = c > 0 ? sy / c : 0.0;
+    S[2] = c > 0 ? sz / c : 0.0;
+    S[3] = Tt > 0 ? X / Tt : 0.0;
+    S[4] = Tt > 0 ? Y / Tt : 0.0;
+    S[5] = Tt > 0 ? Z / Tt : 0.0;
+}
+
+namespace {
 
 __device__ void tally_mid_body(const TallyArgs &A)
 {
@@ -1835,27 +1913,7 @@ __device__ void tally_mid_body(const TallyArgs &A)
         A.gsum[g * kGS + q] = v;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double c = 0, sx = 0, sy = 0, sz = 0, X = 0, Y = 0, Z = 0, Tt = 0;
-        for (int k = 0; k < kGroups; ++k) {
-            const double *r = A.gsum + k * kGS;
-            c += r[0];
-            sx += r[1];
-            sy += r[2];
-            sz += r[3];
-            X += r[6];
-            Y += r[7];
-            Z += r[8];
-            Tt += r[9];
-        }
-        double *S = A.gsum + kGroups * kGS;
-        S[0] = c > 0 ? sx / c : 0.0;
-        S[1] = c > 0 ? sy / c : 0.0;
-        S[2] = c > 0 ? sz / c : 0.0;
-        S[3] = Tt > 0 ? X / Tt : 0.0;
-        S[4] = Tt > 0 ? Y / Tt : 0.0;
-        S[5] = Tt > 0 ? Z / Tt : 0.0;
-    }
+    if (threadIdx.x == 0) drift_of_groups(A.gsum, A.gsum + kGroups * kGS);
 }
 
 __device__ __forceinline__ void pass2_contrib(const TallyArgs &A, uint64_t i, const double *S, double (&c)[kQ2])
@@ -1900,7 +1958,9 @@ __device__ void tally_pass2_body(const TallyArgs &A, int bx, int nbx)
     block_group_reduce<kQ2>(acc, out, A.id_offset);
 }
 
-__device__ double group_se(const double *v, const bool *has, int G)
+}  // namespace
+
+__host__ __device__ static double group_se(const double *v, const bool *has, int G)
 {
     int n = 0;
     double m = 0.0;
@@ -1909,7 +1969,12 @@ __device__ double group_se(const double *v, const bool *has, int G)
             m += v[g];
             ++n;
         }
-    if (n < 2) return __longlong_as_double(0x7ff8000000000000ll);
+    if (n < 2) {
+        const unsigned long long nan_bits = 0x7ff8000000000000ull;
+        double x;
+        memcpy(&x, &nan_bits, sizeof x);
+        return x;
+    }
     m /= n;
     double s = 0.0;
     for (int g = 0; g < G; ++g)
@@ -1917,22 +1982,16 @@ __device__ double group_se(const double *v, const bool *has, int G)
     return sqrt(s / (n - 1)) / sqrt((double)n);
 }
 
-__device__ void tally_final_body(const TallyArgs &A)
+// Swarm tallies (Eqs. 15-28, the Drifter fields of Sec. 7) from the group
+// sums of both passes (gsum[g][0..kQ1) pass 1, gsum[g][kQ1..kGS) pass 2 about
+// the drift vectors S[0..5]) and the run's scalars.  Host and device.
+__host__ __device__ void tallies_of_groups(const double *gsum, const double *S, const GroupScalars &X, bz_tallies *out)
 {
-    const int g = threadIdx.x / kQ2, q = threadIdx.x % kQ2;
-    if (threadIdx.x < kGroups * kQ2) {
-        double v = 0.0;
-        for (int b = 0; b < A.blocks; ++b) v += A.part2[((size_t)b * kGroups + g) * kQ2 + q];
-        A.gsum[g * kGS + kQ1 + q] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x != 0) return;
     double tot[kGS];
     for (int k = 0; k < kGS; ++k) {
         tot[k] = 0.0;
-        for (int gg = 0; gg < kGroups; ++gg) tot[k] += A.gsum[gg * kGS + k];
+        for (int gg = 0; gg < kGroups; ++gg) tot[k] += gsum[gg * kGS + k];
     }
-    const double *S = A.gsum + kGroups * kGS;
     bz_tallies o;
     memset(&o, 0, sizeof o);
     const double N = tot[0];
@@ -1958,12 +2017,12 @@ __device__ void tally_final_body(const TallyArgs &A)
     o.D_T_flux = tot[9] > 0 ? tot[kQ1 + 7] / (4.0 * tot[9]) : 0.0;
     const double trials = tot[12] + tot[13] + tot[14];
     o.efficiency = trials > 0 ? tot[12] / trials : 0.0;
-    o.E_V_m = A.E_V_m;
-    o.n_total = A.n_total;
-    o.nu_trial = A.nu_trial;
+    o.E_V_m = X.E_V_m;
+    o.n_total = X.n_total;
+    o.nu_trial = X.nu_trial;
     o.t_mean = tot[9] * inv;
-    o.mu = A.E_V_m > 0 ? o.W / A.E_V_m : 0.0;
-    o.mu_N = o.mu * A.n_total;
+    o.mu = X.E_V_m > 0 ? o.W / X.E_V_m : 0.0;
+    o.mu_N = o.mu * X.n_total;
     o.mu_0 = o.mu_N / kLoschmidt;
     o.n_particles = (uint64_t)(N + 0.5);
     o.n_real = (uint64_t)(tot[12] + 0.5);
@@ -1974,19 +2033,18 @@ __device__ void tally_final_body(const TallyArgs &A)
     o.n_incomplete = (uint64_t)(tot[17] + 0.5);
     o.n_alive = (uint64_t)(tot[19] + 0.5);
     o.n_removed = (uint64_t)(tot[20] + 0.5);
-    const uint64_t n = tally_n(A);
-    o.n_spawned = n > A.n_primary && A.ids ? n - A.n_primary : 0;
-    o.n_capped = A.capped ? (uint64_t)*A.capped : 0;
+    o.n_spawned = X.n_spawned;
+    o.n_capped = X.n_capped;
     const double other = tot[18] - trials;  // steps that were neither real, null nor fail: window restarts
     o.n_window = other > 0.5 ? (uint64_t)(other + 0.5) : 0;
-    o.error_flags = (int32_t)*A.err;
+    o.error_flags = X.error_flags;
     // batch-mean standard errors
     bool has[kGroups];
     double v[kGroups];
-    for (int k = 0; k < kGroups; ++k) has[k] = A.gsum[k * kGS] > 0.0;
+    for (int k = 0; k < kGroups; ++k) has[k] = gsum[k * kGS] > 0.0;
     auto se_of = [&](int num, int den, double scale) {
         for (int k = 0; k < kGroups; ++k) {
-            const double *r = A.gsum + k * kGS;
+            const double *r = gsum + k * kGS;
             v[k] = has[k] && r[den] > 0 ? scale * r[num] / r[den] : 0.0;
         }
         return group_se(v, has, kGroups);
@@ -2002,7 +2060,36 @@ __device__ void tally_final_body(const TallyArgs &A)
     o.sig_se = se_of(kQ1 + 3, 0, 1.0);
     o.sig_L_se = se_of(kQ1 + 4, 0, 1.0);
     o.sig_T_se = se_of(kQ1 + 5, 0, 1.0);
-    *A.out = o;
+    *out = o;
+}
+
+namespace {
+
+// Pass 2's per-block sums added over the blocks into the group sums.
+__device__ void tally_sum2_body(const TallyArgs &A)
+{
+    const int g = threadIdx.x / kQ2, q = threadIdx.x % kQ2;
+    if (threadIdx.x < kGroups * kQ2) {
+        double v = 0.0;
+        for (int b = 0; b < A.blocks; ++b) v += A.part2[((size_t)b * kGroups + g) * kQ2 + q];
+        A.gsum[g * kGS + kQ1 + q] = v;
+    }
+}
+
+__device__ void tally_final_body(const TallyArgs &A)
+{
+    tally_sum2_body(A);
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    const uint64_t n = tally_n(A);
+    GroupScalars X;
+    X.E_V_m = A.E_V_m;
+    X.n_total = A.n_total;
+    X.nu_trial = A.nu_trial;
+    X.n_spawned = n > A.n_primary && A.ids ? n - A.n_primary : 0;
+    X.n_capped = A.capped ? (uint64_t)*A.capped : 0;
+    X.error_flags = (int32_t)*A.err;
+    tallies_of_groups(A.gsum, A.gsum + kGroups * kGS, X, A.out);
 }
 
 
@@ -2010,6 +2097,7 @@ __global__ void __launch_bounds__(kTallyBlock) tally_pass1(const TallyArgs A) { 
 __global__ void tally_mid(const TallyArgs A) { tally_mid_body(A); }
 __global__ void __launch_bounds__(kTallyBlock) tally_pass2(const TallyArgs A) { tally_pass2_body(A, blockIdx.x, gridDim.x); }
 __global__ void tally_final(const TallyArgs A) { tally_final_body(A); }
+__global__ void tally_sum2(const TallyArgs A) { tally_sum2_body(A); }
 
 // Many swarms at once: blockIdx.y (passes) or blockIdx.x (the one-block
 // steps) selects the swarm's arguments.
@@ -2183,6 +2271,16 @@ int tally_blocks(uint64_t n, int sm_count)
     if (b > cap) b = cap;
     if (b < 1) b = 1;
     return (int)b;
+}
+
+cudaError_t launch_group_sums2(const TallyArgs &a, const double *drift_host, cudaStream_t s)
+{
+    // the drift vectors go where pass 2 reads them; pass-1 group sums stay
+    cudaError_t e = cudaMemcpyAsync(a.gsum + kGroups * kGS, drift_host, 6 * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    tally_pass2<<<a.blocks, kTallyBlock, 0, s>>>(a);
+    tally_sum2<<<1, kGroups * kQ2, 0, s>>>(a);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_tallies(const TallyArgs &a, cudaStream_t s)

@@ -168,7 +168,9 @@ bool emit(const std::vector<Chan> &ch, const std::vector<double> &g, const std::
     size_t off_elval = pad16(off_gval + sizeof(ChVal<R>) * (size_t)n_rec * n_gases);
     size_t off_elp = pad16(off_elval + sizeof(ChVal<R>) * (size_t)n_rec * n_gases);
     size_t off_cum = pad16(off_elp + sizeof(ChParam<R>) * (size_t)n_gases);
-    size_t total = pad16(off_cum + sizeof(ChVal<R>) * (size_t)n_rec * n_ch);
+    const bool guided = n_ch <= 255;
+    size_t off_guide = pad16(off_cum + sizeof(ChVal<R>) * (size_t)n_rec * n_ch);
+    size_t total = pad16(off_guide + (guided ? (size_t)kGuide * (n_rec + 1) : 0));
     blob->assign(total, 0);
     Rec<R> *rec = (Rec<R> *)(blob->data() + off_rec);
     for (int i = 0; i < n_rec; ++i) {
@@ -250,6 +252,28 @@ bool emit(const std::vector<Chan> &ch, const std::vector<double> &g, const std::
             cu[(size_t)i * n_ch + j].slope = (R)b;
         }
     }
+    // guide rows: row 0 from the constant values of record 0 (below the first
+    // grid point), row r >= 1 from record r - 1's own linear pieces at its
+    // upper edge g[r - 1] -- by continuity of every channel also the lower
+    // edge of record r; record i reads rows i and i + 1
+    if (guided) {
+        uint8_t *gd = blob->data() + off_guide;
+        std::vector<double> C(n_ch);
+        for (int r = 0; r <= n_rec; ++r) {
+            const int src = r == 0 ? 0 : std::min(r - 1, n_rec - 1);
+            const double w = (r == 0 || src >= (int)g.size()) ? 0.0 : g[src] - (src == 0 ? 0.0 : g[src - 1]);
+            double a = 0.0;
+            for (int j = 0; j < n_ch; ++j) C[j] = (a += cv[src][j] + cs[src][j] * w);
+            const double tot = C[n_ch - 1];
+            int j = 0;
+            for (int b = 0; b < kGuide; ++b) {
+                const double q = tot * (double)b / kGuide;
+                while (j < n_ch - 1 && C[j] < q) ++j;
+                gd[(size_t)r * kGuide + b] = (uint8_t)(tot > 0.0 ? j : 0);
+            }
+        }
+    }
+    lay->off_guide = guided ? (uint32_t)off_guide : 0u;
     lay->n_rec = n_rec;
     lay->n_buckets = nb;
     lay->n_ch = n_ch;
