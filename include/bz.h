@@ -215,6 +215,13 @@ typedef struct {
     double gas_temperature_K; /* > 0: the targets move, Maxwell-Boltzmann at this temperature, and every
                                  collision but attachment is worked in the centre-of-momentum frame
                                  (Sec. 2.1); 0: targets at rest (Eqs. 8-9) */
+    double spawn_wait_s;      /* spawn mode: a warp with no electron to run gives up after waiting this long for a
+                                 created one (sets BZ_ERR_SPAWN_WAIT, bz_read_tallies returns BZ_ETIMEOUT);
+                                 <= 0: 60 s */
+    uint32_t hold_pending;    /* spawn mode, for tests of that bounded wait: this many electrons are counted as
+                                 pending and never arrive, so lanes that run out of work wait until spawn_wait_s;
+                                 0 in normal use */
+    int32_t reserved1;
 } bz_swarm_config;
 
 /* Fills *cfg with defaults: N = 1e4, I = 1000, FP32, lazy mode, Maxwellian
@@ -279,10 +286,12 @@ typedef struct {
 #define BZ_ERR_TRIAL 2u         /* fixed nu' exceeded, or a BINNED retry failed again */
 #define BZ_ERR_NONFINITE 4u     /* non-finite energy met; particle stopped */
 #define BZ_ERR_MAX_TRIALS 8u    /* a particle reached max_trials */
-#define BZ_ERR_SPAWN_WAIT 16u   /* spawn mode: a lane waited > 60 s for work */
+#define BZ_ERR_SPAWN_WAIT 16u   /* spawn mode: a warp waited longer than spawn_wait_s for work */
 
 /* Waits for the swarm and copies its tallies into *out.
- * Errors: BZ_ETRIAL (fixed mode exceeded), BZ_ETIMEOUT, BZ_ECUDA. */
+ * Errors: BZ_ETRIAL (fixed mode exceeded), BZ_ETIMEOUT (a bounded device
+ * wait gave up: table staging, or spawn mode's wait for created electrons;
+ * the tallies are still copied), BZ_ECUDA. */
 bz_status bz_read_tallies(bz_swarm *sw, bz_tallies *out);
 /* Non-blocking: BZ_ENOTREADY while the swarm runs, else as bz_read_tallies. */
 bz_status bz_query_tallies(bz_swarm *sw, bz_tallies *out);
@@ -356,6 +365,55 @@ bz_status bz_batch_read_particles(bz_batch *b, int32_t i, const bz_particles *ou
 /* Device time of the last launch: the batch kernel and the tally kernels [ms]. */
 bz_status bz_batch_timing(bz_batch *b, double *step_ms, double *tally_ms);
 void bz_destroy_batch(bz_batch *b);
+
+/* ------------------------------------------------------------------------
+ * Merging one swarm run in parts.  Electrons never interact (the paper
+ * neglects Coulomb forces between them, Sec. 9) and every random number is
+ * keyed by the swarm seed and the particle id, so a swarm can run as id
+ * ranges (id_offset) on several GPUs or in several launches and be merged
+ * into the tallies of one run.  The estimators of Sec. 2.3 are sums over
+ * electrons, grouped by batch group (id mod 32) for the standard errors:
+ *   pass 1: BZ_GROUP_Q1 sums per group -- count, x/t, y/t, z/t, G/z, D/z,
+ *           x, y, z, t, the energy sums, the counts of real, null and failed
+ *           trials, ionizations, attachments, incomplete electrons, steps,
+ *           electrons stopped at t_end and removed;
+ *   pass 2: BZ_GROUP_Q2 sums per group about the swarm's drift vectors --
+ *           |d|^2/t, d_z^2/(2t), |d_perp|^2/(4t), 2|d|, 2|d_z|, 2|d_perp| with
+ *           d = x - t W_vec (Eqs. 21-27), and the two flux forms' squares.
+ * Because pass 2 needs the drift of the whole swarm, a merge takes two
+ * exchanges: add every part's pass-1 sums (FP64) and derive the drift
+ * (bz_drift_from_group_sums); have every part sum pass 2 about it and add
+ * those; then bz_finalize_group_sums.  Sums are [32][Q] row-major host
+ * arrays.  The drift vector is {<x/t>, <y/t>, <z/t>, sum x/sum t,
+ * sum y/sum t, sum z/sum t}.
+ * ------------------------------------------------------------------------ */
+#define BZ_GROUPS 32
+#define BZ_GROUP_Q1 21
+#define BZ_GROUP_Q2 8
+
+typedef struct {
+    double e_over_n_Td;       /* for E in the mobility fields */
+    double n_total_m3;        /* the mixture's total number density */
+    double nu_trial;          /* copied into the result */
+    uint64_t n_spawned;       /* spawn mode: created electrons, summed over the parts */
+    uint64_t n_capped;        /* spawn mode: capped ionizations, summed over the parts */
+    int32_t error_flags;      /* the parts' error bits, or-ed */
+    int32_t reserved;
+} bz_merge_info;
+
+/* Pass-1 group sums of a finished swarm (waits for it): out[32][21]. */
+bz_status bz_swarm_group_sums1(bz_swarm *sw, double *out);
+/* Pass-2 group sums of a finished swarm about drift[6] (runs the second
+ * pass again on the swarm's stream and waits): out[32][8]. */
+bz_status bz_swarm_group_sums2(bz_swarm *sw, const double *drift, double *out);
+/* The same for swarm i of a launched batch (waits for the launch). */
+bz_status bz_batch_group_sums1(bz_batch *b, int32_t i, double *out);
+bz_status bz_batch_group_sums2(bz_batch *b, int32_t i, const double *drift, double *out);
+/* Host only: the drift vector from (summed) pass-1 group sums. */
+bz_status bz_drift_from_group_sums(const double *g1, double *drift);
+/* Host only: the tallies of (summed) pass-1 and pass-2 group sums; the
+ * same arithmetic the device reduction ends with.  Errors: BZ_EINVAL. */
+bz_status bz_finalize_group_sums(const double *g1, const double *g2, const bz_merge_info *info, bz_tallies *out);
 
 /* ------------------------------------------------------------------------
  * Serving: a request loop with continuous batching.  The paper has no
@@ -466,8 +524,11 @@ typedef struct {
  * caches it; make that first call before any stream capture.  All calls on
  * a device share the one scratch array and overwrite it, so calls whose
  * kernels overlap on the GPU (concurrent streams, or threads) race: order
- * them on one stream.  Errors: BZ_EINVAL (null pointer, n = 0),
- * BZ_EBUDGET (n > BZ_NOALLOC_MAX_PARTICLES), BZ_ECUDA. */
+ * them on one stream.  The reduction sees only the per-particle arrays,
+ * not the step kernel's error word, so the result's error_flags reads 0:
+ * the run's outcome is in the per-particle status array (BZ_ST_*).
+ * Errors: BZ_EINVAL (null pointer, n = 0), BZ_EBUDGET
+ * (n > BZ_NOALLOC_MAX_PARTICLES), BZ_ECUDA. */
 bz_status bz_reduce_tallies_noalloc(const bz_particle_arrays *in, uint64_t n, uint64_t id_offset,
                                     double e_over_n_Td, double n_total_m3, double nu_trial,
                                     bz_tallies *out_dev, void *stream);

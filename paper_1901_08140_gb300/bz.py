@@ -69,7 +69,8 @@ class bz_swarm_config(C.Structure):
                 ("seed", C.c_uint64), ("id_offset", C.c_uint64), ("block_threads", C.c_int32),
                 ("blocks_per_sm", C.c_int32), ("window_c", C.c_double), ("spawn", C.c_int32),
                 ("reserved0", C.c_int32), ("pop_cap", C.c_uint64), ("zeta", C.c_double),
-                ("grace", C.c_uint32), ("bins_per_decade", C.c_int32), ("gas_temperature_K", C.c_double)]
+                ("grace", C.c_uint32), ("bins_per_decade", C.c_int32), ("gas_temperature_K", C.c_double),
+                ("spawn_wait_s", C.c_double), ("hold_pending", C.c_uint32), ("reserved1", C.c_int32)]
 
 
 _TALLY_DOUBLES = ["W", "W_se", "Wx", "Wy", "W_flux", "lorentz_angle", "mu", "mu_N", "mu_0", "eps", "eps_se",
@@ -108,6 +109,15 @@ BZ_NOALLOC_MAX_PARTICLES = 32768 * 512
 class bz_batch_opts(C.Structure):
     _fields_ = [("tile_particles", C.c_int32), ("blocks_per_sm", C.c_int32), ("use_graph", C.c_int32),
                 ("reserved", C.c_int32)]
+
+
+class bz_merge_info(C.Structure):
+    _fields_ = [("e_over_n_Td", C.c_double), ("n_total_m3", C.c_double), ("nu_trial", C.c_double),
+                ("n_spawned", C.c_uint64), ("n_capped", C.c_uint64), ("error_flags", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+BZ_GROUPS, BZ_GROUP_Q1, BZ_GROUP_Q2 = 32, 21, 8
 
 
 class bz_server_opts(C.Structure):
@@ -172,6 +182,12 @@ SIGNATURES = {
     "bz_destroy_batch": (None, [C.c_void_p]),
     "bz_reduce_tallies_noalloc": (C.c_int, [C.POINTER(bz_particle_arrays), C.c_uint64, C.c_uint64, C.c_double,
                                             C.c_double, C.c_double, C.c_void_p, C.c_void_p]),
+    "bz_swarm_group_sums1": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "bz_swarm_group_sums2": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "bz_batch_group_sums1": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
+    "bz_batch_group_sums2": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
+    "bz_drift_from_group_sums": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "bz_finalize_group_sums": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(bz_merge_info), C.POINTER(bz_tallies)]),
     "bz_server_create": (C.c_int, [C.c_void_p, C.POINTER(bz_server_opts), C.POINTER(C.c_void_p)]),
     "bz_submit": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(bz_swarm_config), C.POINTER(C.c_uint64)]),
     "bz_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(bz_tallies), C.POINTER(bz_request_info)]),
@@ -236,6 +252,12 @@ def bz_batch_read_particles(b, i, out): return lib().bz_batch_read_particles(b, 
 def bz_batch_timing(b, a, c): return lib().bz_batch_timing(b, a, c)
 def bz_destroy_batch(b): return lib().bz_destroy_batch(b)
 def bz_reduce_tallies_noalloc(*a): return lib().bz_reduce_tallies_noalloc(*a)
+def bz_swarm_group_sums1(sw, out): return lib().bz_swarm_group_sums1(sw, out)
+def bz_swarm_group_sums2(sw, drift, out): return lib().bz_swarm_group_sums2(sw, drift, out)
+def bz_batch_group_sums1(b, i, out): return lib().bz_batch_group_sums1(b, i, out)
+def bz_batch_group_sums2(b, i, drift, out): return lib().bz_batch_group_sums2(b, i, drift, out)
+def bz_drift_from_group_sums(g1, drift): return lib().bz_drift_from_group_sums(g1, drift)
+def bz_finalize_group_sums(g1, g2, info, out): return lib().bz_finalize_group_sums(g1, g2, info, out)
 def bz_server_create(ctx, opts, out): return lib().bz_server_create(ctx, opts, out)
 def bz_submit(srv, mix, cfg, rid): return lib().bz_submit(srv, mix, cfg, rid)
 def bz_poll(srv, rid, out, info): return lib().bz_poll(srv, rid, out, info)
@@ -377,7 +399,8 @@ def make_config(*, n_electrons: int, real_collisions: int, e_over_n_Td: float, b
                 trial_mode: int = BZ_TRIAL_LAZY, nu_trial: float = 0.0, t_end_s: float = 0.0, max_trials: int = 0,
                 id_offset: int = 0, attach_keep_state: bool = False, blocks_per_sm: int = 0,
                 window_c: float = 0.0, spawn: bool = False, pop_cap: int = 0, zeta: float = 0.25,
-                grace: int = 5000, bins_per_decade: int = 8, gas_temperature_K: float = 0.0) -> bz_swarm_config:
+                grace: int = 5000, bins_per_decade: int = 8, gas_temperature_K: float = 0.0,
+                spawn_wait_s: float = 0.0, hold_pending: int = 0) -> bz_swarm_config:
     cfg = bz_swarm_config()
     lib().bz_config_defaults(C.byref(cfg))
     _check(lib().bz_set_fields(C.byref(cfg), float(e_over_n_Td), float(b_T), float(b_angle_rad)))
@@ -400,6 +423,8 @@ def make_config(*, n_electrons: int, real_collisions: int, e_over_n_Td: float, b
     cfg.grace = int(grace)
     cfg.bins_per_decade = int(bins_per_decade)
     cfg.gas_temperature_K = float(gas_temperature_K)
+    cfg.spawn_wait_s = float(spawn_wait_s)
+    cfg.hold_pending = int(hold_pending)
     return cfg
 
 
@@ -440,6 +465,19 @@ class Swarm:
         arrs, p = _particle_arrays(n)
         _check(lib().bz_read_particles(self.h, C.byref(p)))
         return arrs
+
+    def group_sums1(self) -> np.ndarray:
+        """Pass-1 group sums (32 x 21) of the finished swarm."""
+        out = np.zeros((BZ_GROUPS, BZ_GROUP_Q1))
+        _check(lib().bz_swarm_group_sums1(self.h, out.ctypes.data))
+        return out
+
+    def group_sums2(self, drift) -> np.ndarray:
+        """Pass-2 group sums (32 x 8) about the drift vector `drift` (6 values)."""
+        d = np.ascontiguousarray(drift, dtype=np.float64)
+        out = np.zeros((BZ_GROUPS, BZ_GROUP_Q2))
+        _check(lib().bz_swarm_group_sums2(self.h, d.ctypes.data, out.ctypes.data))
+        return out
 
     def timing(self):
         """(step kernel ms, tally kernels ms) from CUDA events on the swarm's stream."""
@@ -525,6 +563,17 @@ class Batch:
         _check(lib().bz_batch_timing(self.h, C.byref(a), C.byref(b)))
         return a.value, b.value
 
+    def group_sums1(self, i: int) -> np.ndarray:
+        out = np.zeros((BZ_GROUPS, BZ_GROUP_Q1))
+        _check(lib().bz_batch_group_sums1(self.h, int(i), out.ctypes.data))
+        return out
+
+    def group_sums2(self, i: int, drift) -> np.ndarray:
+        d = np.ascontiguousarray(drift, dtype=np.float64)
+        out = np.zeros((BZ_GROUPS, BZ_GROUP_Q2))
+        _check(lib().bz_batch_group_sums2(self.h, int(i), d.ctypes.data, out.ctypes.data))
+        return out
+
     def close(self):
         if getattr(self, "h", None):
             lib().bz_destroy_batch(self.h)
@@ -574,3 +623,23 @@ def philox(ctx: Context, ctr: np.ndarray, key: int, stream=None) -> np.ndarray:
 
 def run_swarm(ctx: Context, mix: Mixture, cfg: bz_swarm_config, stream=None) -> Swarm:
     return Swarm(ctx, mix, cfg, stream)
+
+
+def drift_from_group_sums(g1) -> np.ndarray:
+    """The swarm's drift vector (6 values) from summed pass-1 group sums (host only)."""
+    g = np.ascontiguousarray(g1, dtype=np.float64).reshape(BZ_GROUPS, BZ_GROUP_Q1)
+    d = np.zeros(6)
+    _check(lib().bz_drift_from_group_sums(g.ctypes.data, d.ctypes.data))
+    return d
+
+
+def finalize_group_sums(g1, g2, e_over_n_Td: float, n_total_m3: float, nu_trial: float = 0.0,
+                        n_spawned: int = 0, n_capped: int = 0, error_flags: int = 0) -> Dict[str, float]:
+    """Tallies of summed pass-1 and pass-2 group sums (host only)."""
+    a = np.ascontiguousarray(g1, dtype=np.float64).reshape(BZ_GROUPS, BZ_GROUP_Q1)
+    b = np.ascontiguousarray(g2, dtype=np.float64).reshape(BZ_GROUPS, BZ_GROUP_Q2)
+    info = bz_merge_info(float(e_over_n_Td), float(n_total_m3), float(nu_trial), int(n_spawned), int(n_capped),
+                         int(error_flags), 0)
+    t = bz_tallies()
+    _check(lib().bz_finalize_group_sums(a.ctypes.data, b.ctypes.data, C.byref(info), C.byref(t)))
+    return _tally_dict(t)

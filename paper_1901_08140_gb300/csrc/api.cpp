@@ -56,6 +56,7 @@ struct bz_swarm {
     uint64_t n_primary;
     uint64_t *bid;       // spawn mode: ids and birth times of the created electrons
     double *bt;
+    bz::TallyArgs targs; // the tally kernels' arguments (group sums for merges)
 };
 
 struct bz_batch {
@@ -81,6 +82,7 @@ struct bz_batch {
     cudaGraphExec_t exec[2];
     cudaEvent_t ev[3], done;
     bool launched;
+    std::vector<bz::TallyArgs> targs_host;  // per swarm (group sums for merges)
 };
 
 namespace {
@@ -257,6 +259,9 @@ bz_status validate_config(const bz_swarm_config *cfg)
     if (!(cfg->t_end_s >= 0.0) || !isfinite(cfg->t_end_s)) return fail(BZ_EINVAL, "bad t_end_s");
     if (!(cfg->gas_temperature_K >= 0.0) || !isfinite(cfg->gas_temperature_K))
         return fail(BZ_EINVAL, "gas_temperature_K must be finite and >= 0");
+    if (!isfinite(cfg->spawn_wait_s) || cfg->spawn_wait_s > 3600.0)
+        return fail(BZ_EINVAL, "spawn_wait_s must be finite and at most 3600");
+    if (cfg->hold_pending && !cfg->spawn) return fail(BZ_EINVAL, "hold_pending applies to spawn mode only");
     if (cfg->max_trials > 0xFFFFFFFFull) return fail(BZ_EINVAL, "max_trials must fit 32 bits");
     if (cfg->block_threads != 0 && cfg->block_threads != 256) return fail(BZ_EINVAL, "block_threads must be 0 or 256");
     if (cfg->blocks_per_sm < 0) return fail(BZ_EINVAL, "blocks_per_sm must be >= 0");
@@ -290,6 +295,7 @@ bz_status prepare_run(const bz_mixture *mix, const bz_swarm_config *cfg, bz::Run
     a->attach_keep = cfg->attach_keep_state != 0;
     a->nu0 = (cfg->nu_trial > 0.0) ? cfg->nu_trial : mix->cm.nu_trial;
     a->eps0_mean = cfg->eps0_mean_eV;
+    a->spawn_wait_ns = (uint64_t)((cfg->spawn_wait_s > 0.0 ? cfg->spawn_wait_s : 60.0) * 1e9);
     a->v0_scale = sqrt((2.0 / 3.0) * cfg->eps0_mean_eV * bz::kQe / bz::kMe);
     a->v0_scale32 = (float)a->v0_scale;
     a->nu0_32 = (float)a->nu0;
@@ -569,7 +575,8 @@ bz_status bz_run_swarm(bz_ctx *ctx, const bz_mixture *mix, const bz_swarm_config
     a.bvx = (double *)(M + o_bv);
     a.bvy = a.bvx + nb;
     a.bvz = a.bvy + nb;
-    const unsigned long long init[2] = {n, n};  // spawn mode: electrons, pending
+    // spawn mode: electrons, pending (plus the electrons a test holds pending)
+    const unsigned long long init[2] = {n, n + cfg->hold_pending};
     if (spawn) {
         // unpublished birth records read as id 0
         a.counter = ticket;
@@ -625,6 +632,7 @@ bz_status bz_run_swarm(bz_ctx *ctx, const bz_mixture *mix, const bz_swarm_config
     t.nu_trial = a.nu0;
     t.err = s->err;
     t.out = s->tallies_dev;
+    s->targs = t;
     if (e == cudaSuccess) e = bz::launch_tallies(t, s->stream);
     if (e == cudaSuccess) e = cudaEventRecord(s->ev[2], s->stream);
     if (e == cudaSuccess)
@@ -643,6 +651,7 @@ static bz_status finish_tallies(bz_swarm *sw, bz_tallies *out)
 {
     *out = *sw->tallies_host;
     if (out->error_flags & BZ_ERR_STAGE_TIMEOUT) return fail(BZ_ETIMEOUT, "table staging timed out");
+    if (out->error_flags & BZ_ERR_SPAWN_WAIT) return fail(BZ_ETIMEOUT, "spawn mode: a wait for created electrons gave up");
     if (out->error_flags & BZ_ERR_TRIAL) return fail(BZ_ETRIAL, "trial frequency exceeded (fixed mode, or a binned retry that failed again)");
     return BZ_OK;
 }
@@ -915,6 +924,7 @@ bz_status bz_create_batch(bz_ctx *ctx, int32_t n, const bz_mixture *const *mixtu
         t.err = b->errs + i;
         t.out = b->tallies_dev + i;
     }
+    b->targs_host = targs;
     e = cudaMemcpy(b->desc, desc.data(), sizeof(bz::RunArgs) * n, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->tiles, tiles.data(), sizeof(uint4) * tiles.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->targs, targs.data(), sizeof(bz::TallyArgs) * n, cudaMemcpyHostToDevice);
@@ -1045,6 +1055,96 @@ bz_status bz_batch_query(bz_batch *b)
     cudaError_t e = cudaEventQuery(b->done);
     if (e == cudaErrorNotReady) return BZ_ENOTREADY;
     if (e != cudaSuccess) return cuda_fail(e, "batch");
+    return BZ_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Group sums: merging one swarm run in parts (id ranges on several ranks or
+// launches) into one set of tallies
+// ---------------------------------------------------------------------------
+static bz_status group_sums1_of(const bz::TallyArgs &t, cudaEvent_t done, double *out)
+{
+    if (!out) return fail(BZ_EINVAL, "null output");
+    cudaError_t e = cudaEventSynchronize(done);
+    std::vector<double> g((size_t)bz::kGroups * bz::kGS);
+    if (e == cudaSuccess) e = cudaMemcpy(g.data(), t.gsum, sizeof(double) * g.size(), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "group sums");
+    for (int k = 0; k < bz::kGroups; ++k)
+        for (int q = 0; q < bz::kQ1; ++q) out[k * bz::kQ1 + q] = g[(size_t)k * bz::kGS + q];
+    return BZ_OK;
+}
+
+static bz_status group_sums2_of(const bz::TallyArgs &t, cudaEvent_t done, cudaStream_t s, const double *drift,
+                                double *out)
+{
+    if (!drift || !out) return fail(BZ_EINVAL, "null argument");
+    cudaError_t e = cudaEventSynchronize(done);
+    if (e == cudaSuccess) e = bz::launch_group_sums2(t, drift, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    std::vector<double> g((size_t)bz::kGroups * bz::kGS);
+    if (e == cudaSuccess) e = cudaMemcpy(g.data(), t.gsum, sizeof(double) * g.size(), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "group sums about the given drift");
+    for (int k = 0; k < bz::kGroups; ++k)
+        for (int q = 0; q < bz::kQ2; ++q) out[k * bz::kQ2 + q] = g[(size_t)k * bz::kGS + bz::kQ1 + q];
+    return BZ_OK;
+}
+
+bz_status bz_swarm_group_sums1(bz_swarm *sw, double *out)
+{
+    if (!sw) return fail(BZ_EINVAL, "null swarm");
+    cudaSetDevice(sw->ctx->device);
+    return group_sums1_of(sw->targs, sw->done, out);
+}
+
+bz_status bz_swarm_group_sums2(bz_swarm *sw, const double *drift, double *out)
+{
+    if (!sw) return fail(BZ_EINVAL, "null swarm");
+    cudaSetDevice(sw->ctx->device);
+    return group_sums2_of(sw->targs, sw->done, sw->stream, drift, out);
+}
+
+bz_status bz_batch_group_sums1(bz_batch *b, int32_t i, double *out)
+{
+    if (!b || i < 0 || i >= b->n || !b->launched) return fail(BZ_EINVAL, "bad batch, swarm index, or not launched");
+    cudaSetDevice(b->ctx->device);
+    return group_sums1_of(b->targs_host[i], b->done, out);
+}
+
+bz_status bz_batch_group_sums2(bz_batch *b, int32_t i, const double *drift, double *out)
+{
+    if (!b || i < 0 || i >= b->n || !b->launched) return fail(BZ_EINVAL, "bad batch, swarm index, or not launched");
+    cudaSetDevice(b->ctx->device);
+    return group_sums2_of(b->targs_host[i], b->done, (cudaStream_t)0, drift, out);
+}
+
+bz_status bz_drift_from_group_sums(const double *g1, double *drift)
+{
+    if (!g1 || !drift) return fail(BZ_EINVAL, "null argument");
+    std::vector<double> g((size_t)bz::kGroups * bz::kGS, 0.0);
+    for (int k = 0; k < bz::kGroups; ++k)
+        for (int q = 0; q < bz::kQ1; ++q) g[(size_t)k * bz::kGS + q] = g1[k * bz::kQ1 + q];
+    bz::drift_of_groups(g.data(), drift);
+    return BZ_OK;
+}
+
+bz_status bz_finalize_group_sums(const double *g1, const double *g2, const bz_merge_info *info, bz_tallies *out)
+{
+    if (!g1 || !g2 || !info || !out) return fail(BZ_EINVAL, "null argument");
+    std::vector<double> g((size_t)bz::kGroups * bz::kGS + 8, 0.0);
+    for (int k = 0; k < bz::kGroups; ++k) {
+        for (int q = 0; q < bz::kQ1; ++q) g[(size_t)k * bz::kGS + q] = g1[k * bz::kQ1 + q];
+        for (int q = 0; q < bz::kQ2; ++q) g[(size_t)k * bz::kGS + bz::kQ1 + q] = g2[k * bz::kQ2 + q];
+    }
+    double *S = g.data() + (size_t)bz::kGroups * bz::kGS;
+    bz::drift_of_groups(g.data(), S);
+    bz::GroupScalars X;
+    X.E_V_m = info->e_over_n_Td * bz::kTownsend * info->n_total_m3;
+    X.n_total = info->n_total_m3;
+    X.nu_trial = info->nu_trial;
+    X.n_spawned = info->n_spawned;
+    X.n_capped = info->n_capped;
+    X.error_flags = info->error_flags;
+    bz::tallies_of_groups(g.data(), S, X, out);
     return BZ_OK;
 }
 

@@ -80,6 +80,7 @@ struct RunArgs {
     uint64_t *bid;
     Fields f;
     unsigned long long *counter;  // spawn mode: next slot ticket
+    uint64_t spawn_wait_ns;       // spawn mode: a warp without work gives up after this long
     uint32_t *err;
     ParticlesDev out;
 };
@@ -123,10 +124,28 @@ struct BatchArgs {
     RunArgs single;
 };
 
+// Scalars of a run that its group sums do not hold.
+struct GroupScalars {
+    double E_V_m, n_total, nu_trial;
+    uint64_t n_spawned, n_capped;
+    int32_t error_flags;
+};
+
+// Group-sum layout: gsum[g * kGS + q], q < kQ1 pass 1, kQ1 <= q < kGS pass
+// 2; the drift vectors S[0..5] follow at gsum + kGroups * kGS.
+constexpr int kGS = kQ1 + kQ2;
+// The swarm's drift vectors from pass-1 group sums, and the tallies from
+// both passes' group sums (kernels.cu; host and device).
+__host__ __device__ void drift_of_groups(const double *gsum, double *S);
+__host__ __device__ void tallies_of_groups(const double *gsum, const double *S, const GroupScalars &X, bz_tallies *out);
+
 // Launch helpers (kernels.cu).  precision is 32 or 64.
 cudaError_t launch_replay(int precision, bool ch_smem, const ReplayArgs &a, int grid, int block, cudaStream_t s);
 cudaError_t launch_philox(int64_t n, const uint32_t *ctr, uint64_t key, uint32_t *out, cudaStream_t s);
 cudaError_t launch_tallies(const TallyArgs &a, cudaStream_t s);
+// Pass 2 of a finished run's tallies about the given drift vectors
+// (drift_host[6], as S above), summed into the group sums' pass-2 columns.
+cudaError_t launch_group_sums2(const TallyArgs &a, const double *drift_host, cudaStream_t s);
 // ext: the instance with the paper's adaptive trial frequencies and the xi
 // form of the angle; the lean instance (the hot path of Lazy, Fixed and
 // windowed swarms in mixtures without xi-form gases) compiles without them.
