@@ -128,3 +128,35 @@ def test_batch_rejects_spawn(ctx):
     cfg = bz.make_config(n_electrons=10, real_collisions=10, e_over_n_Td=10.0, spawn=True)
     with pytest.raises(bz.BzError):
         bz.Batch(ctx, [mix], [cfg])
+
+
+def test_spawn_wait_gives_up_after_its_limit(ctx):
+    """A failure made on the host: one electron is counted as pending but is
+    never created, so lanes that run out of work keep waiting for it.  After
+    spawn_wait_s the kernel gives up, flags BZ_ERR_SPAWN_WAIT, and returns:
+    bz_read_tallies reports BZ_ETIMEOUT, every electron that existed was run
+    (the counts equal the same swarm's run without the reservation), and the
+    context stays usable."""
+    import time
+    mix = bz.Mixture(ctx, W.ar_co2_avalanche_mixture())
+    kw = dict(n_electrons=64, real_collisions=10 ** 9, e_over_n_Td=300.0, seed=W.swarm_seed(91), t_end_s=0.05e-9,
+              spawn=True, pop_cap=10 ** 4, trial_mode=bz.BZ_TRIAL_WINDOW)
+    ref = bz.run_swarm(ctx, mix, bz.make_config(**kw))
+    tr = ref.tallies()
+    ref.close()
+    t0 = time.time()
+    sw = bz.run_swarm(ctx, mix, bz.make_config(spawn_wait_s=0.2, hold_pending=1, **kw))
+    with pytest.raises(bz.BzError) as ei:
+        sw.tallies()
+    elapsed = time.time() - t0
+    assert ei.value.status == bz.BZ_ETIMEOUT
+    t = sw.tallies(check=False)
+    sw.close()
+    assert t["error_flags"] & bz.BZ_ERR_SPAWN_WAIT
+    assert 0.2 <= elapsed < 30.0
+    for k in ("n_particles", "n_real", "n_ion", "n_spawned", "n_alive"):
+        assert t[k] == tr[k], k
+    # the context still runs work
+    ok = bz.run_swarm(ctx, mix, bz.make_config(n_electrons=1000, real_collisions=20, e_over_n_Td=50.0))
+    assert ok.tallies()["n_real"] == 20000
+    ok.close()
