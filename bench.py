@@ -51,8 +51,8 @@ LANES_PER_SM_CLOCK = 4 * 32     # 4 schedulers x 32 lanes issue per clock
 # and many channels searched in a tree in global memory (the batched
 # workload, Ar/CO2 with B).
 ALG_OPS = {
-    "plain": {"step": 95, "window": 63, "real": 90},
-    "field": {"step": 129, "window": 98, "real": 140},
+    "plain": {"step": 95, "window": 61, "real": 67},
+    "field": {"step": 128, "window": 86, "real": 135},
 }
 LEGS = ("plain", "e2e", "sweep", "oracle", "configs", "precision", "strategies", "serving", "cpu")
 L2_NOTE = "flushed between steps (256 MiB write)"
@@ -86,6 +86,20 @@ def parse():
     a = ap.parse_args()
     a.legs = set(LEGS) if a.legs == "all" else set() if a.legs == "none" else set(a.legs.split(","))
     return a
+
+
+def _jsonable(o):
+    """numpy scalars and arrays as plain JSON values."""
+    import numpy as np
+    if isinstance(o, np.bool_):
+        return bool(o)
+    if isinstance(o, np.integer):
+        return int(o)
+    if isinstance(o, np.floating):
+        return float(o)
+    if isinstance(o, np.ndarray):
+        return o.tolist()
+    raise TypeError(f"{type(o).__name__} is not JSON serializable")
 
 
 def dist():
@@ -374,7 +388,7 @@ def sweep_run(ctx, stream, flush, world, dev, args, rank):
     return {"workload": sweep_name(args), "value": reals / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
             "plain": {"value": preals / (pms / 1e3), "ms_per_step": pms / 2},
             "batched_over_plain": (reals / ms) / (preals / pms),
-            "autotuned": {k: choice.get(k) for k in ("window_c", "tile_particles", "blocks_per_sm", "cached")},
+            "autotuned": {k: choice.get(k) for k in ("window_c", "tiles_per_block", "blocks_per_sm", "cached")},
             "_tallies": tallies, "_kern_ms": kern / steps, "_specs": specs}
 
 
@@ -658,8 +672,7 @@ def run_ours(args):
     out.update({"value": value, "ms_per_step": t_max / args.steps,
                 "roofline": roofline_of(kind, counts, r["kern_ms"], sm_count, sm_mhz, profiled_traffic(prof), kernel),
                 "clocks": clk, "gpu_launches": 5 * args.steps,
-                "autotuned": {k: r["choice"].get(k) for k in ("window_c", "tile_particles", "blocks_per_sm",
-                                                             "staging", "cached")},
+                "autotuned": {k: r["choice"].get(k) for k in ("window_c", "tiles_per_block", "blocks_per_sm", "cached")},
                 "trial_collisions_per_s": counts["trials"] * world / (t_max / 1e3),
                 "efficiency": counts["reals"] / counts["trials"] if counts["trials"] else None,
                 "window_restarts_per_real": (counts["windows"] - counts["reals"]) / counts["reals"]})
@@ -712,12 +725,12 @@ def run_ours(args):
         last = max(serve, key=lambda x: x["rate_req_s"])
         out["p99_at_highest_rate"] = {"rate_req_s": last["rate_req_s"], "p99_ms": last["p99_ms"],
                                       "served_fraction": last["served_fraction"],
-                                      "saturated": (last["served_fraction"] or 0) < 0.9}
+                                      "saturated": bool((last["served_fraction"] or 0) < 0.9)}
     if rank != 0:
         return
     if "cpu" in args.legs:
         out["cpu_baseline"] = cpu_baseline(args, specs, args.cpu_seconds)
-    print(json.dumps(out), flush=True)
+    print(json.dumps(out, default=_jsonable), flush=True)
 
 
 def run_reference(args):
@@ -769,7 +782,7 @@ def run_reference(args):
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
-    print(json.dumps(out), flush=True)
+    print(json.dumps(out, default=_jsonable), flush=True)
 
 
 def main():

@@ -2,14 +2,16 @@
 
 Picks, for a batch of swarms, the launch options that maximise real
 collisions per second of device time: the trial-frequency window length
-(``window_c``, windowed mode only; any value samples the same process), the
-tile size and the resident blocks per SM.  It times candidates by
-coordinate descent on a reduced copy of the batch -- every swarm keeps its
-electrons, mixture and fields but runs fewer real collisions per electron,
-so tiles and load balance look like the full batch's -- and caches the
-result in a JSON file keyed by the GPU name and a signature of the workload
-(swarm count, electron count and trial-mode mix), so later runs of the same
-class skip the search.
+(``window_c``, windowed mode only; any value samples the same process),
+the tile size, expressed as tiles per resident block so that the choice
+carries over between a copy of the batch and the batch itself, and the
+resident blocks per SM.  It times candidates by coordinate descent on a
+reduced copy of the batch -- every swarm keeps its mixture, fields and real
+collisions per electron but runs a quarter of its electrons, so an
+electron's history and a tile's work look like the full batch's -- and
+caches the result in a JSON file keyed by the GPU name and a signature of
+the workload (swarm count, electron count, trial modes, precision), so later
+runs of the same class skip the search.
 """
 from __future__ import annotations
 
@@ -23,10 +25,12 @@ from . import bz
 
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_autotune_cache.json")
 
-DEFAULT = {"window_c": 2.0, "tile_particles": 0, "blocks_per_sm": 0}
-WINDOW_C = [1.0, 1.5, 2.0, 3.0, 4.0]
-TILES = [0, 512, 1024, 2048, 4096]
-BLOCKS = [0, 2, 1]
+DEFAULT = {"window_c": 2.0, "tiles_per_block": 16, "blocks_per_sm": 0}
+WINDOW_C = [1.0, 1.5, 2.0, 3.0]
+TILES_PER_BLOCK = [4, 8, 16, 32]
+BLOCKS = [0, 2]
+SM_COUNT = 152
+RESIDENT_BLOCKS = 3   # the FP32 step kernel's blocks per SM when its tables fit
 
 
 def signature(cfgs: Sequence[bz.bz_swarm_config]) -> str:
@@ -66,16 +70,25 @@ def apply(cfgs: Sequence[bz.bz_swarm_config], choice: dict) -> List[bz.bz_swarm_
             for c in cfgs]
 
 
-def make_batch(ctx, mixtures, cfgs, choice, use_graph: bool = True) -> "bz.Batch":
+def tile_size(cfgs: Sequence[bz.bz_swarm_config], choice: dict, sm_count: int = SM_COUNT) -> int:
+    """Electrons per tile for `tiles_per_block` tiles per resident block
+    (rounded up to 256, at least 256)."""
+    total = sum(int(c.n_electrons) for c in cfgs)
+    bps = int(choice.get("blocks_per_sm", 0)) or RESIDENT_BLOCKS
+    t = math.ceil(total / (sm_count * bps * int(choice.get("tiles_per_block", 16))))
+    return max(256, (t + 255) // 256 * 256)
+
+
+def make_batch(ctx, mixtures, cfgs, choice, use_graph: bool = True, sm_count: int = SM_COUNT) -> "bz.Batch":
     """A batch launched with the chosen options (cfgs already carry the
     chosen window length, see apply)."""
-    return bz.Batch(ctx, mixtures, cfgs, tile_particles=int(choice.get("tile_particles", 0)),
+    return bz.Batch(ctx, mixtures, cfgs, tile_particles=tile_size(cfgs, choice, sm_count),
                     blocks_per_sm=int(choice.get("blocks_per_sm", 0)), use_graph=use_graph)
 
 
-def _measure(ctx, mixtures, cfgs, choice, repeats=2) -> float:
-    """Real collisions per millisecond of step-kernel time."""
-    b = make_batch(ctx, mixtures, apply(cfgs, choice), choice)
+def _measure(ctx, mixtures, cfgs, choice, sm_count, repeats=2) -> float:
+    """Real collisions per millisecond of step-kernel time (best of `repeats`)."""
+    b = make_batch(ctx, mixtures, apply(cfgs, choice), choice, sm_count=sm_count)
     best = 0.0
     for _ in range(repeats):
         b.launch()
@@ -86,27 +99,28 @@ def _measure(ctx, mixtures, cfgs, choice, repeats=2) -> float:
     return best
 
 
-def tune(ctx, mixtures: Sequence, cfgs: Sequence[bz.bz_swarm_config], scale: float = 0.1,
+def tune(ctx, mixtures: Sequence, cfgs: Sequence[bz.bz_swarm_config], scale: float = 0.25,
          use_cache: bool = True, cache_path: str = CACHE, gpu_name: Optional[str] = None) -> dict:
     """Best launch options for this batch (cached per GPU and workload class)."""
+    import torch
     if gpu_name is None:
-        import torch
         gpu_name = torch.cuda.get_device_name(ctx.device)
+    sm_count = torch.cuda.get_device_properties(ctx.device).multi_processor_count
     key = f"{gpu_name}|{signature(cfgs)}"
     cache = load_cache(cache_path) if use_cache else {}
-    if key in cache:
+    if key in cache and "tiles_per_block" in cache[key]:
         return dict(cache[key], cached=True)
-    small = [_copy_cfg(c, real_collisions=max(20, int(c.real_collisions * scale))) for c in cfgs]
+    small = [_copy_cfg(c, n_electrons=max(256, int(c.n_electrons * scale))) for c in cfgs]
     best = dict(DEFAULT)
-    best_rate = _measure(ctx, mixtures, small, best)
+    best_rate = _measure(ctx, mixtures, small, best, sm_count)
     windowed = any(c.trial_mode == bz.BZ_TRIAL_WINDOW for c in cfgs)
-    for name, values in (("window_c", WINDOW_C if windowed else []), ("tile_particles", TILES),
+    for name, values in (("window_c", WINDOW_C if windowed else []), ("tiles_per_block", TILES_PER_BLOCK),
                          ("blocks_per_sm", BLOCKS)):
         for v in values:
             if v == best[name]:
                 continue
             cand = dict(best, **{name: v})
-            r = _measure(ctx, mixtures, small, cand)
+            r = _measure(ctx, mixtures, small, cand, sm_count)
             if r > best_rate * 1.01:
                 best, best_rate = cand, r
     best["rate_per_ms"] = best_rate

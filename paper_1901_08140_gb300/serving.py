@@ -50,11 +50,16 @@ class Server:
 
     def __init__(self, ctx=None, memory_budget: float = 60e9, n_slots: int = 3, max_group: int = 512,
                  simulate: int = 0):
+        # the server's worker thread allocates every launch's memory; it does
+        # so through a context of its own on the same device that uses CUDA's
+        # stream-ordered allocator, so a native thread never calls back into
+        # Python (mixtures of any context on that device may be submitted)
+        self.ctx = bz.Context(ctx.device, torch_allocator=False) if ctx is not None and not simulate else None
         opts = bz.bz_server_opts(float(memory_budget), int(n_slots), int(max_group), int(simulate), 0)
         h = C.c_void_p()
-        bz._check(bz.lib().bz_server_create(ctx.h if ctx is not None else None, C.byref(opts), C.byref(h)))
+        bz._check(bz.lib().bz_server_create(self.ctx.h if self.ctx is not None else None, C.byref(opts),
+                                            C.byref(h)))
         self.h = h
-        self.ctx = ctx
 
     def submit(self, mixture, cfg) -> int:
         rid = C.c_uint64()
@@ -123,6 +128,9 @@ class Server:
         if getattr(self, "h", None):
             bz.lib().bz_server_destroy(self.h)
             self.h = None
+        if getattr(self, "ctx", None) is not None:
+            self.ctx.close()
+            self.ctx = None
 
     def __del__(self):
         import sys

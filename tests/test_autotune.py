@@ -17,7 +17,7 @@ def test_signature_and_apply(L):
                            trial_mode=bz.BZ_TRIAL_WINDOW if i % 2 else bz.BZ_TRIAL_LAZY) for i in range(4)]
     sig = autotune.signature(cfgs)
     assert sig == "n4-e13-m0.2-p32"
-    out = autotune.apply(cfgs, {"window_c": 3.0, "tile_particles": 0, "blocks_per_sm": 0})
+    out = autotune.apply(cfgs, {"window_c": 3.0, "tiles_per_block": 16, "blocks_per_sm": 0})
     assert [c.window_c for c in out] == [0.0, 3.0, 0.0, 3.0]
     assert [c.window_c for c in cfgs] == [0.0, 0.0, 0.0, 0.0]   # inputs untouched
 
@@ -25,8 +25,16 @@ def test_signature_and_apply(L):
 def test_cache_round_trip(tmp_path, L):
     path = str(tmp_path / "cache.json")
     assert autotune.load_cache(path) == {}
-    autotune.store_cache({"gpu|sig": {"window_c": 1.5, "tile_particles": 512, "blocks_per_sm": 2}}, path)
-    assert autotune.load_cache(path)["gpu|sig"]["tile_particles"] == 512
+    autotune.store_cache({"gpu|sig": {"window_c": 1.5, "tiles_per_block": 8, "blocks_per_sm": 2}}, path)
+    assert autotune.load_cache(path)["gpu|sig"]["tiles_per_block"] == 8
+
+
+def test_tile_size_from_tiles_per_block(L):
+    cfgs = [bz.make_config(n_electrons=n, real_collisions=10, e_over_n_Td=1.0) for n in (10 ** 6, 3 * 10 ** 5)]
+    # 1.3e6 electrons over 152 SMs x 3 blocks x 16 tiles: 179 -> 256 (the floor); x 1 tile: 2851 -> 3072
+    assert autotune.tile_size(cfgs, {"tiles_per_block": 16, "blocks_per_sm": 0}) == 256
+    assert autotune.tile_size(cfgs, {"tiles_per_block": 1, "blocks_per_sm": 0}) == 3072
+    assert autotune.tile_size(cfgs, {"tiles_per_block": 1, "blocks_per_sm": 2}) == 4352
 
 
 @pytest.mark.gpu
@@ -40,8 +48,7 @@ def test_tune_a_small_batch(tmp_path, L):
     assert choice["cached"] is False and choice["window_c"] in autotune.WINDOW_C
     again = autotune.tune(ctx, [mix] * 4, cfgs, cache_path=path)
     assert again["cached"] is True and again["window_c"] == choice["window_c"]
-    b = bz.Batch(ctx, [mix] * 4, autotune.apply(cfgs, choice), tile_particles=choice["tile_particles"],
-                 blocks_per_sm=choice["blocks_per_sm"])
+    b = autotune.make_batch(ctx, [mix] * 4, autotune.apply(cfgs, choice), choice)
     b.launch()
     assert all(t["n_real"] == 20000 * 200 and t["error_flags"] == 0 for t in b.tallies())
     b.close()
