@@ -23,13 +23,22 @@
  * Random numbers come from Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11),
  * implemented here from its published definition.
  *
- * Readings of points the paper leaves open (each is listed with its reason in
- * the design notes): force axis +z with W > 0; the flight uniform is used
- * directly as 1-R; fail => revert and raise the particle's trial frequency to
- * 1.25 nu; radicand of Eq. (9) clamped at 0; the ionization remainder is split
- * uniformly between primary and secondary; a dummy attachment leaves the
- * electron at rest; an inelastic table that starts above its threshold rises
- * linearly from (threshold, 0).
+ * Readings of points the paper leaves open, each with its reason:
+ *   - the electric force on the electron points along +z, so W > 0 (the
+ *     worked example of Sec. 7 prints a positive drift velocity);
+ *   - the flight's uniform is used directly as 1-R (both are uniform on
+ *     (0,1), and this spares a subtraction that would round);
+ *   - a fail reverts the electron to its last real collision and raises its
+ *     trial frequency to 1.25 nu (Sec. 6 names reverting and a 25 % margin);
+ *   - the radicand of Eq. (9) is clamped at 0 (it is negative only in the
+ *     kinematically closed band just above the threshold);
+ *   - the ionization remainder is split uniformly between primary and
+ *     secondary (the paper says only that it is shared);
+ *   - a dummy attachment leaves the electron at rest (a plastic collision
+ *     keeps no kinetic energy);
+ *   - an inelastic table that starts above its threshold rises linearly
+ *     from (threshold, 0) (Sec. 2.2 sets the cross section to zero below
+ *     the threshold and interpolates linearly).
  */
 #include <math.h>
 #include <pthread.h>
