@@ -83,6 +83,9 @@ def parse():
     ap.add_argument("--strategy-electrons", type=int, default=100_000)
     ap.add_argument("--precision-electrons", type=int, default=100_000,
                     help="electrons per swarm of the FP32-against-FP64 comparison")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="the autotuner's default launch options instead of a search (profiling runs)")
+    ap.add_argument("--only-point", type=int, default=-1, help="sweep workload: one E/N point (profiling case)")
     a = ap.parse_args()
     a.legs = set(LEGS) if a.legs == "all" else set() if a.legs == "none" else set(a.legs.split(","))
     return a
@@ -188,8 +191,9 @@ def batched_specs(args):
 
 def sweep_specs(args):
     from paper_1901_08140_gb300 import workloads as W
-    return W.argon_sweep(n_electrons=max(1, args.electrons // args.scale), real_collisions=args.collisions,
-                         points=args.points)
+    specs = W.argon_sweep(n_electrons=max(1, args.electrons // args.scale), real_collisions=args.collisions,
+                          points=args.points)
+    return [specs[args.only_point]] if args.only_point >= 0 else specs
 
 
 def batched_name(args, specs):
@@ -204,7 +208,15 @@ def batched_name(args, specs):
 def sweep_name(args):
     return (f"Argon-like E/N sweep: {args.points} log points 1-1000 Td x {max(1, args.electrons // args.scale)} "
             f"electrons x {args.collisions} real collisions, FP32 flights, FP64 tallies, windowed trial "
-            "frequency, B = 0")
+            "frequency, B = 0" + (f" (point {args.only_point} only)" if args.only_point >= 0 else ""))
+
+
+def tuned(ctx, mixes, cfgs, args):
+    """The autotuner's choice for this batch, or its default options with --no-tune."""
+    from paper_1901_08140_gb300 import autotune
+    if args.no_tune:
+        return dict(autotune.DEFAULT, cached=None)
+    return autotune.tune(ctx, mixes, cfgs)
 
 
 def workload_config(args):
@@ -279,9 +291,9 @@ def batched_run(ctx, stream, flush, world, dev, specs, rank, args, clocks_gpu):
     mixes = [bz.Mixture(ctx, s.gases) for s in specs]
     id_off = rank << 32  # weak scaling: every rank runs every swarm on its own ids
     cfgs = [bz.config_from_spec(s, trial_mode=bz.BZ_TRIAL_WINDOW, id_offset=id_off) for s in specs]
-    choice = autotune.tune(ctx, mixes, cfgs)
-    tuned = autotune.apply(cfgs, choice)
-    batch = autotune.make_batch(ctx, mixes, tuned, choice)
+    choice = tuned(ctx, mixes, cfgs, args)
+    tuned_cfgs = autotune.apply(cfgs, choice)
+    batch = autotune.make_batch(ctx, mixes, tuned_cfgs, choice)
     for _ in range(args.warmup):
         batch.launch(stream)
         batch.tallies(check=False)
@@ -295,12 +307,14 @@ def batched_run(ctx, stream, flush, world, dev, specs, rank, args, clocks_gpu):
         tallies += ts
         kern_ms += batch.timing()[0]
     clk = clocks.stop()
+    merged = merged_over_ranks(batch, mixes, cfgs, world) if world > 1 else None
     batch.close()
     out = {"ms": total_ms, "kern_ms": kern_ms, "tallies": tallies, "clocks": clk, "choice": choice,
-           "mixes": mixes, "cfgs": cfgs, "tuned": tuned}
+           "merged": merged,
+           "mixes": mixes, "cfgs": cfgs, "tuned": tuned_cfgs}
     if "plain" in args.legs:
         def plain_step():
-            return [bz.run_swarm(ctx, m, c, stream) for m, c in zip(mixes, tuned)]
+            return [bz.run_swarm(ctx, m, c, stream) for m, c in zip(mixes, tuned_cfgs)]
         for sw in plain_step():
             sw.tallies(check=False)
             sw.close()
@@ -313,7 +327,7 @@ def batched_run(ctx, stream, flush, world, dev, specs, rank, args, clocks_gpu):
                 sw.close()
         out["plain"] = {"ms": pms, "steps": steps, "reals": preals}
         # the autotuned window length against the default one, batched both
-        if any(abs(c.window_c - 2.0) > 1e-9 for c in tuned):
+        if any(abs(c.window_c - 2.0) > 1e-9 for c in tuned_cfgs):
             b2 = autotune.make_batch(ctx, mixes, cfgs, dict(choice, window_c=2.0))
             b2.launch(stream)
             b2.tallies(check=False)
@@ -322,6 +336,21 @@ def batched_run(ctx, stream, flush, world, dev, specs, rank, args, clocks_gpu):
             b2.close()
             out["default_window"] = {"ms": dms, "reals": dreals}
     return out
+
+
+def merged_over_ranks(batch, mixes, cfgs, world):
+    """Every swarm's tallies merged over the ranks (each ran its own ids of
+    every swarm): the FP64 group sums summed in two all-reduces, so each rank
+    holds one set of tallies per swarm over all ranks' electrons."""
+    from paper_1901_08140_gb300 import sharding
+    out = []
+    for i, (m, c) in enumerate(zip(mixes, cfgs)):
+        t = sharding.merge_tallies(batch.group_sums1(i), lambda d, i=i: batch.group_sums2(i, d), c.e_over_n_Td,
+                                   m.info["n_total"], m.info["nu_trial"])
+        out.append(t)
+    return {"swarms": len(out), "ranks": world, "electrons": int(sum(t["n_particles"] for t in out)),
+            "W_first_swarms": [t["W"] for t in out[:4]], "W_se_first_swarms": [t["W_se"] for t in out[:4]],
+            "D_L_first_swarms": [t["D_L"] for t in out[:4]], "D_T_first_swarms": [t["D_T"] for t in out[:4]]}
 
 
 def e2e_run(ctx, stream, specs, rank, choice, steps):
@@ -363,9 +392,9 @@ def sweep_run(ctx, stream, flush, world, dev, args, rank):
     specs = sweep_specs(args)
     mix = bz.Mixture(ctx, specs[0].gases)
     cfgs = [bz.config_from_spec(s, trial_mode=bz.BZ_TRIAL_WINDOW, id_offset=rank << 32) for s in specs]
-    choice = autotune.tune(ctx, [mix] * len(cfgs), cfgs)
-    tuned = autotune.apply(cfgs, choice)
-    batch = autotune.make_batch(ctx, [mix] * len(cfgs), tuned, choice)
+    choice = tuned(ctx, [mix] * len(cfgs), cfgs, args)
+    tuned_cfgs = autotune.apply(cfgs, choice)
+    batch = autotune.make_batch(ctx, [mix] * len(cfgs), tuned_cfgs, choice)
     for _ in range(2):
         batch.launch(stream)
         batch.tallies()
@@ -378,7 +407,7 @@ def sweep_run(ctx, stream, flush, world, dev, args, rank):
         tallies = batch.tallies()
         kern += batch.timing()[0]
     batch.close()
-    pms, outs = _timed(stream, flush, 2, lambda: [bz.run_swarm(ctx, mix, c, stream) for c in tuned], world, dev)
+    pms, outs = _timed(stream, flush, 2, lambda: [bz.run_swarm(ctx, mix, c, stream) for c in tuned_cfgs], world, dev)
     preals = 0
     for sws in outs:
         for sw in sws:
@@ -644,9 +673,9 @@ def run_ours(args):
         from paper_1901_08140_gb300 import autotune
         mix = bz.Mixture(ctx, specs[0].gases)
         cfgs = [bz.config_from_spec(s, trial_mode=bz.BZ_TRIAL_WINDOW, id_offset=rank << 32) for s in specs]
-        choice = autotune.tune(ctx, [mix] * len(cfgs), cfgs)
-        tuned = autotune.apply(cfgs, choice)
-        b = autotune.make_batch(ctx, [mix] * len(cfgs), tuned, choice)
+        choice = tuned(ctx, [mix] * len(cfgs), cfgs, args)
+        tuned_cfgs = autotune.apply(cfgs, choice)
+        b = autotune.make_batch(ctx, [mix] * len(cfgs), tuned_cfgs, choice)
         for _ in range(args.warmup):
             b.launch(stream)
             b.tallies()
@@ -660,7 +689,7 @@ def run_ours(args):
             kms += b.timing()[0]
         b.close()
         r = {"ms": ms, "kern_ms": kms, "tallies": tl, "clocks": clocks.stop(), "choice": choice,
-             "mixes": [mix] * len(cfgs), "tuned": tuned}
+             "mixes": [mix] * len(cfgs), "tuned": tuned_cfgs}
         kind, kernel = "plain", "batch_kernel (lean FP32 build without field paths; 4 blocks/SM where the tables fit)"
         prof = "batch_kernel_traffic_argon_sweep"
     reals = sum(t["n_real"] for t in r["tallies"])
@@ -676,6 +705,8 @@ def run_ours(args):
                 "trial_collisions_per_s": counts["trials"] * world / (t_max / 1e3),
                 "efficiency": counts["reals"] / counts["trials"] if counts["trials"] else None,
                 "window_restarts_per_real": (counts["windows"] - counts["reals"]) / counts["reals"]})
+    if r.get("merged"):
+        out["merged_tallies"] = r["merged"]
     if "plain" in r:
         p = r["plain"]
         p_max, p_reals = sharding.reduce_step(p["ms"], p["reals"])

@@ -7,8 +7,9 @@ the tile size, expressed as tiles per resident block so that the choice
 carries over between a copy of the batch and the batch itself, and the
 resident blocks per SM.  It times candidates by coordinate descent on a
 reduced copy of the batch -- every swarm keeps its mixture, fields and real
-collisions per electron but runs a quarter of its electrons, so an
-electron's history and a tile's work look like the full batch's -- and
+collisions per electron but runs half of its electrons, so an electron's
+history looks like the full batch's -- checks the winner against the
+defaults on the batch itself, and
 caches the result in a JSON file keyed by the GPU name and a signature of
 the workload (swarm count, electron count, trial modes, precision), so later
 runs of the same class skip the search.
@@ -99,9 +100,15 @@ def _measure(ctx, mixtures, cfgs, choice, sm_count, repeats=2) -> float:
     return best
 
 
-def tune(ctx, mixtures: Sequence, cfgs: Sequence[bz.bz_swarm_config], scale: float = 0.25,
-         use_cache: bool = True, cache_path: str = CACHE, gpu_name: Optional[str] = None) -> dict:
-    """Best launch options for this batch (cached per GPU and workload class)."""
+def tune(ctx, mixtures: Sequence, cfgs: Sequence[bz.bz_swarm_config], scale: float = 0.5,
+         use_cache: bool = True, cache_path: str = CACHE, gpu_name: Optional[str] = None,
+         margin: float = 0.02) -> dict:
+    """Best launch options for this batch (cached per GPU and workload class).
+
+    A candidate replaces the current best only if it is faster by more than
+    `margin` on the reduced copy; at the end the choice and the defaults are
+    timed once each on the batch itself and the faster is kept, so the
+    tuner never settles on options slower than the defaults."""
     import torch
     if gpu_name is None:
         gpu_name = torch.cuda.get_device_name(ctx.device)
@@ -121,9 +128,16 @@ def tune(ctx, mixtures: Sequence, cfgs: Sequence[bz.bz_swarm_config], scale: flo
                 continue
             cand = dict(best, **{name: v})
             r = _measure(ctx, mixtures, small, cand, sm_count)
-            if r > best_rate * 1.01:
+            if r > best_rate * (1.0 + margin):
                 best, best_rate = cand, r
-    best["rate_per_ms"] = best_rate
+    best["rate_per_ms_reduced"] = best_rate
+    if any(best[k] != DEFAULT[k] for k in DEFAULT):
+        full_best = _measure(ctx, mixtures, cfgs, best, sm_count, repeats=1)
+        full_default = _measure(ctx, mixtures, cfgs, DEFAULT, sm_count, repeats=1)
+        if full_default >= full_best:
+            best = dict(DEFAULT, rate_per_ms_reduced=best_rate, rejected=dict(best))
+        best["rate_per_ms"] = max(full_best, full_default)
+        best["default_rate_per_ms"] = full_default
     cache[key] = best
     if use_cache:
         store_cache(cache, cache_path)
