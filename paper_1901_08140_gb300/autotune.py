@@ -26,7 +26,10 @@ from . import bz
 
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_autotune_cache.json")
 
-DEFAULT = {"window_c": 2.0, "tiles_per_block": 16, "blocks_per_sm": 0}
+# window_c 1.5 and 16 tiles per block: the fastest point of a full-size sweep of
+# the 256-swarm workload on GB300 (window_c 1.0 / 1.5 / 2.0 / 3.0: 2.94 / 2.90 /
+# 2.99 / 3.18 s; 8 / 16 / 32 tiles per block: 2.98 / 2.90 / 2.91 s)
+DEFAULT = {"window_c": 1.5, "tiles_per_block": 16, "blocks_per_sm": 0}
 WINDOW_C = [1.0, 1.5, 2.0, 3.0]
 TILES_PER_BLOCK = [4, 8, 16, 32]
 BLOCKS = [0, 2]

@@ -302,10 +302,15 @@ def test_maxwell_model_closed_forms_on_gpu_fp64(ctx):
     assert abs(DL_hat - DL) < 3 * se_L
 
 
-def test_full_size_argon_swarm_sampled_against_oracle(ctx):
-    """The workload the benchmark times (one E/N point of the Argon-like
-    sweep, 1e6 electrons x 1000 real collisions, FP32), checked on particles
-    the oracle recomputes one by one, plus size-independent invariants."""
+def test_full_size_lazy_swarm_sampled_against_oracle(ctx):
+    """One E/N point of the Argon-like sweep at full size (1e6 electrons x
+    1000 real collisions, FP32) with the paper's constant trial frequency,
+    whose draws the oracle shares: 48 electrons recomputed one by one by the
+    oracle, plus size-independent invariants.  (The windowed form that the
+    benchmark times draws other numbers than a constant nu' and is compared
+    with the oracle statistically, at full size, in test_gpu_sweep_oracle.)
+    FP32 histories drift from FP64 ones by ~sqrt(I) x 1e-6 (R34): the flight
+    times sum draws only, the energy sums follow the trajectory."""
     spec = W.argon_sweep(points=32)[8]
     t, p, mix = _gpu_swarm(ctx, spec.gases, **_cfg_kw(spec))
     assert t["n_particles"] == spec.n_electrons and t["error_flags"] == 0 and t["n_incomplete"] == 0

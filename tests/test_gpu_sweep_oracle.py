@@ -75,6 +75,13 @@ def test_windowed_sweep_as_timed_against_oracle(ctx):
     batch = bz.Batch(ctx, [mix] * len(cfgs), cfgs)  # one persistent launch from a CUDA graph
     batch.launch()
     tg = batch.tallies()
+    # every electron of the launch, at the lowest, a middle and the highest field
+    for i in (0, 16, 31):
+        p = batch.particles(i)
+        assert np.all(p["status"] == bz.ST_DONE) and np.all(p["n_real"] == specs[i].real_collisions)
+        assert np.all(p["t"] > 0) and np.all(np.isfinite(p["z"])) and np.all(np.isfinite(p["sum_e"]))
+        assert np.all(p["n_fail"] == 0)                     # the windowed trial frequency never fails
+        assert np.all(p["steps"] >= p["n_real"] + p["n_null"])
     batch.close()
     chi2 = {k: 0.0 for k in QUANTITIES}
     rows, worst = [], {k: (0.0, 0.0) for k in QUANTITIES}
