@@ -34,8 +34,10 @@ struct Chan {
 };
 
 // Linear piece a + b eps of channel c on an interval whose midpoint is m;
-// returns false if the channel is in its right extension there.
-bool piece(const Chan &c, double m, double *a, double *b)
+// returns false if the channel is in its right extension there.  *k is a
+// hint of the table interval (e[k-1] <= m < e[k]); it only moves forward, so
+// a caller that visits increasing m finds every interval in amortised O(1).
+bool piece(const Chan &c, double m, double *a, double *b, size_t *k)
 {
     const std::vector<double> &e = c.e, &s = c.s;
     size_t n = e.size();
@@ -50,32 +52,38 @@ bool piece(const Chan &c, double m, double *a, double *b)
     } else if (m < e[0]) {
         *a = s[0]; *b = 0.0; return true;
     }
-    size_t k = (size_t)(std::upper_bound(e.begin(), e.end(), m) - e.begin());  // e[k-1] <= m < e[k]
-    if (k == 0) k = 1;
-    if (k >= n) k = n - 1;
-    double e0 = e[k - 1], e1 = e[k], s0 = s[k - 1], s1 = s[k];
+    if (*k > n || (*k > 0 && e[*k - 1] > m)) *k = 0;  // the hint ran past m: search again
+    while (*k < n && e[*k] <= m) ++*k;                // e[k-1] <= m < e[k]
+    size_t i = *k;
+    if (i == 0) i = 1;
+    if (i >= n) i = n - 1;
+    double e0 = e[i - 1], e1 = e[i], s0 = s[i - 1], s1 = s[i];
     *b = (s1 - s0) / (e1 - e0);
     *a = s0 - *b * e0;
     return true;
 }
 
-double tail_value(const Chan &c, double eps)
+bool piece(const Chan &c, double m, double *a, double *b)
 {
-    double sl = c.s.back();
-    if (c.tail_zero) return 0.0;
-    return c.n * sl * pow(eps / c.e.back(), c.tail_K);
+    if (m > c.e.back()) return false;  // the right extension: no search needed
+    size_t k = (size_t)(std::upper_bound(c.e.begin(), c.e.end(), m) - c.e.begin());
+    return piece(c, m, a, b, &k);
 }
 
 double speed_of(double eps) { return sqrt(2.0 * eps * kQe / kMe); }
 
-// Exact density sum at eps in record (a, b): linear part plus active tails.
-double record_density(const std::vector<Chan> &ch, double a, double b, double eps)
+// Exact density sum at eps in record (a, b): linear part plus active tails,
+// n sigma = exp(tail_logc + K ln eps) (tail_logc per channel, host FP64).
+double record_density(const std::vector<Chan> &ch, const std::vector<double> &tail_logc, double a, double b,
+                      double eps)
 {
     double mid = 0.5 * (a + b), S = 0.0;
-    for (const Chan &c : ch) {
+    const double le = log(eps);
+    for (size_t j = 0; j < ch.size(); ++j) {
+        const Chan &c = ch[j];
         double pa, pb;
         if (piece(c, mid, &pa, &pb)) S += c.n * (pa + pb * eps);
-        else S += tail_value(c, eps);
+        else if (!c.tail_zero) S += exp(tail_logc[j] + c.tail_K * le);
     }
     return S;
 }
@@ -117,9 +125,11 @@ BucketIndex bucket_index(const std::vector<double> &g, int k)
     if (w == 0.0) nb = 1;
     BucketIndex B;
     B.bucket.resize(nb);
+    size_t i = 0;  // record of bucket b's lower edge e: g[i-1] <= e < g[i]; e grows with b
     for (int b = 0; b < nb; ++b) {
         double e = exp2(L0 + b * w);
-        B.bucket[b] = (uint16_t)(std::upper_bound(g.begin(), g.end(), e) - g.begin());
+        while (i < g.size() && g[i] <= e) ++i;
+        B.bucket[b] = (uint16_t)i;
     }
     B.log2_lo = (float)L0;
     B.inv_bw = (w > 0.0) ? (float)(1.0 / w) : 0.0f;
@@ -399,6 +409,8 @@ bz_status compile_mixture(const bz_gas *gases, int32_t n_gases, const bz_mixture
         }
     }
     const int n_ch = (int)ch.size();
+    std::vector<double> tail_logc(n_ch);
+    for (int j = 0; j < n_ch; ++j) tail_logc[j] = cp[j].tail_logc;
     // union grid of all table energies and inelastic thresholds
     std::vector<double> g;
     for (const Chan &c : ch) {
@@ -424,6 +436,7 @@ bz_status compile_mixture(const bz_gas *gases, int32_t n_gases, const bz_mixture
     std::vector<double> Slo(n_rec), Ssl(n_rec);
     std::vector<std::vector<double>> cv(n_rec, std::vector<double>(n_ch, 0.0)), cs = cv;
     int first_tail = n_rec - 1;
+    std::vector<size_t> cursor(n_ch, 0);  // per channel: its table interval, moving up with the records
     for (int i = 0; i < n_rec; ++i) {
         double lo = (i == 0) ? 0.0 : g[i - 1];
         double hi = (i < n_rec - 1) ? g[i] : lo * 2.0 + 1.0;
@@ -433,7 +446,7 @@ bz_status compile_mixture(const bz_gas *gases, int32_t n_gases, const bz_mixture
         bool any_tail = false;
         for (int j = 0; j < n_ch; ++j) {
             double a, b;
-            if (i == n_rec - 1 || !piece(ch[j], mid, &a, &b)) { any_tail = true; continue; }
+            if (i == n_rec - 1 || !piece(ch[j], mid, &a, &b, &cursor[j])) { any_tail = true; continue; }
             cv[i][j] = ch[j].n * (a + b * lo);
             cs[i][j] = ch[j].n * b;
             S += cv[i][j];
@@ -488,7 +501,7 @@ bz_status compile_mixture(const bz_gas *gases, int32_t n_gases, const bz_mixture
             }
         } else {
             double rhi = (i < n_rec - 1) ? g[i] : hi;
-            auto f = [&](double x) { return speed_of(x) * record_density(ch, lo, rhi, x); };
+            auto f = [&](double x) { return speed_of(x) * record_density(ch, tail_logc, lo, rhi, x); };
             const int NS = 2048;
             int arg = 0;
             double vm = -1.0;
@@ -531,7 +544,7 @@ bz_status compile_mixture(const bz_gas *gases, int32_t n_gases, const bz_mixture
             return m;
         }
         double rhi = (i < n_rec - 1) ? g[i] : b;
-        auto f = [&](double x) { return speed_of(x) * record_density(ch, rlo, rhi, x); };
+        auto f = [&](double x) { return speed_of(x) * record_density(ch, tail_logc, rlo, rhi, x); };
         const int NS = 256;
         int arg = 0;
         double vm = -1.0;
@@ -604,7 +617,7 @@ bz_status compile_mixture(const bz_gas *gases, int32_t n_gases, const bz_mixture
             const double e1 = g[ipos];
             const int i1 = ipos + 1;
             const double hi1 = (i1 < n_rec - 1) ? g[i1] : 2.0 * e1 + 1.0;
-            bins.nu_first = speed_of(e1) * (i1 < first_tail ? Slo[i1] : record_density(ch, e1, hi1, e1));
+            bins.nu_first = speed_of(e1) * (i1 < first_tail ? Slo[i1] : record_density(ch, tail_logc, e1, hi1, e1));
         } else {
             bins.nu_first = 0.0;
         }
