@@ -34,7 +34,7 @@
 extern "C" {
 #endif
 
-#define BZ_ABI_VERSION 5
+#define BZ_ABI_VERSION 6
 
 typedef enum {
     BZ_OK = 0,
@@ -221,7 +221,13 @@ typedef struct {
     uint32_t hold_pending;    /* spawn mode, for tests of that bounded wait: this many electrons are counted as
                                  pending and never arrive, so lanes that run out of work wait until spawn_wait_s;
                                  0 in normal use */
-    int32_t reserved1;
+    uint32_t hold_stage;      /* tests of the table staging wait: 1 = once a block's tables are in, it waits on
+                                 a further copy that is never issued, so the wait runs out after stage_wait_s
+                                 (BZ_ERR_STAGE_TIMEOUT; the read returns BZ_ETIMEOUT) with no copy in flight;
+                                 0 in normal use */
+    double stage_wait_s;      /* a block gives up waiting for its tables (TMA bulk copy into shared memory) after
+                                 this long, sets BZ_ERR_STAGE_TIMEOUT and exits once no copy is in flight (at most
+                                 1 s more); <= 0: 10 s; at most 3600 */
 } bz_swarm_config;
 
 /* Fills *cfg with defaults: N = 1e4, I = 1000, FP32, lazy mode, Maxwellian
@@ -341,7 +347,8 @@ void bz_destroy_swarm(bz_swarm *sw);
 typedef struct bz_batch bz_batch;
 
 typedef struct {
-    int32_t tile_particles;   /* electrons per tile; <= 0: about 16 tiles per resident block */
+    int32_t tile_particles;   /* electrons per tile at most (the last tiles shrink to 256 as the work left
+                                 runs out); <= 0: about 16 tiles per resident block */
     int32_t blocks_per_sm;    /* <= 0: as many as fit */
     int32_t use_graph;        /* 1: CUDA graph (default when opts is NULL), 0: plain launches */
     int32_t reserved;

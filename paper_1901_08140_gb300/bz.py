@@ -70,7 +70,8 @@ class bz_swarm_config(C.Structure):
                 ("blocks_per_sm", C.c_int32), ("window_c", C.c_double), ("spawn", C.c_int32),
                 ("reserved0", C.c_int32), ("pop_cap", C.c_uint64), ("zeta", C.c_double),
                 ("grace", C.c_uint32), ("bins_per_decade", C.c_int32), ("gas_temperature_K", C.c_double),
-                ("spawn_wait_s", C.c_double), ("hold_pending", C.c_uint32), ("reserved1", C.c_int32)]
+                ("spawn_wait_s", C.c_double), ("hold_pending", C.c_uint32), ("hold_stage", C.c_uint32),
+                ("stage_wait_s", C.c_double)]
 
 
 _TALLY_DOUBLES = ["W", "W_se", "Wx", "Wy", "W_flux", "lorentz_angle", "mu", "mu_N", "mu_0", "eps", "eps_se",
@@ -400,7 +401,8 @@ def make_config(*, n_electrons: int, real_collisions: int, e_over_n_Td: float, b
                 id_offset: int = 0, attach_keep_state: bool = False, blocks_per_sm: int = 0,
                 window_c: float = 0.0, spawn: bool = False, pop_cap: int = 0, zeta: float = 0.25,
                 grace: int = 5000, bins_per_decade: int = 8, gas_temperature_K: float = 0.0,
-                spawn_wait_s: float = 0.0, hold_pending: int = 0) -> bz_swarm_config:
+                spawn_wait_s: float = 0.0, hold_pending: int = 0, stage_wait_s: float = 0.0,
+                hold_stage: int = 0) -> bz_swarm_config:
     cfg = bz_swarm_config()
     lib().bz_config_defaults(C.byref(cfg))
     _check(lib().bz_set_fields(C.byref(cfg), float(e_over_n_Td), float(b_T), float(b_angle_rad)))
@@ -425,6 +427,8 @@ def make_config(*, n_electrons: int, real_collisions: int, e_over_n_Td: float, b
     cfg.gas_temperature_K = float(gas_temperature_K)
     cfg.spawn_wait_s = float(spawn_wait_s)
     cfg.hold_pending = int(hold_pending)
+    cfg.stage_wait_s = float(stage_wait_s)
+    cfg.hold_stage = int(hold_stage)
     return cfg
 
 

@@ -262,6 +262,9 @@ bz_status validate_config(const bz_swarm_config *cfg)
     if (!isfinite(cfg->spawn_wait_s) || cfg->spawn_wait_s > 3600.0)
         return fail(BZ_EINVAL, "spawn_wait_s must be finite and at most 3600");
     if (cfg->hold_pending && !cfg->spawn) return fail(BZ_EINVAL, "hold_pending applies to spawn mode only");
+    if (!isfinite(cfg->stage_wait_s) || cfg->stage_wait_s > 3600.0)
+        return fail(BZ_EINVAL, "stage_wait_s must be finite and at most 3600");
+    if (cfg->hold_stage > 1) return fail(BZ_EINVAL, "hold_stage must be 0 or 1");
     if (cfg->max_trials > 0xFFFFFFFFull) return fail(BZ_EINVAL, "max_trials must fit 32 bits");
     if (cfg->block_threads != 0 && cfg->block_threads != 256) return fail(BZ_EINVAL, "block_threads must be 0 or 256");
     if (cfg->blocks_per_sm < 0) return fail(BZ_EINVAL, "blocks_per_sm must be >= 0");
@@ -296,6 +299,8 @@ bz_status prepare_run(const bz_mixture *mix, const bz_swarm_config *cfg, bz::Run
     a->nu0 = (cfg->nu_trial > 0.0) ? cfg->nu_trial : mix->cm.nu_trial;
     a->eps0_mean = cfg->eps0_mean_eV;
     a->spawn_wait_ns = (uint64_t)((cfg->spawn_wait_s > 0.0 ? cfg->spawn_wait_s : 60.0) * 1e9);
+    a->stage_wait_ns = (uint64_t)((cfg->stage_wait_s > 0.0 ? cfg->stage_wait_s : 10.0) * 1e9);
+    a->stage_hold = cfg->hold_stage;
     a->v0_scale = sqrt((2.0 / 3.0) * cfg->eps0_mean_eV * bz::kQe / bz::kMe);
     a->v0_scale32 = (float)a->v0_scale;
     a->nu0_32 = (float)a->nu0;
@@ -847,11 +852,23 @@ bz_status bz_create_batch(bz_ctx *ctx, int32_t n, const bz_mixture *const *mixtu
     std::vector<int> order(n);
     for (int i = 0; i < n; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return desc[x].blob < desc[y].blob; });
+    // Blocks take tiles in list order, so the launch ends when the last
+    // tiles taken end.  Tiles keep the full size while a quarter of an even
+    // share of the work left exceeds it, then shrink with the work left
+    // (guided self-scheduling) down to 256 electrons: a block that runs out of
+    // tiles waits at most about one short tile for the others, whatever the
+    // cost of the mixtures that happen to come last in the list.
+    const uint64_t blocks = (uint64_t)ctx->sm_count * bps;
     std::vector<uint4> tiles;
+    uint64_t left = total;
     for (int i : order)
-        for (uint64_t s0 = 0; s0 < cfgs[i].n_electrons; s0 += tile) {
-            uint64_t c = std::min<uint64_t>(tile, cfgs[i].n_electrons - s0);
+        for (uint64_t s0 = 0; s0 < cfgs[i].n_electrons;) {
+            uint64_t want = left / (4 * blocks);
+            want = std::min<uint64_t>(std::max<uint64_t>((want + 255) / 256 * 256, 256), tile);
+            const uint64_t c = std::min<uint64_t>(want, cfgs[i].n_electrons - s0);
             tiles.push_back(make_uint4((unsigned)i, (unsigned)s0, (unsigned)c, 0u));
+            s0 += c;
+            left -= c;
         }
     b->n_tiles = (int)tiles.size();
     b->grid = std::min(ctx->sm_count * bps, b->n_tiles);

@@ -44,6 +44,7 @@ constexpr int kBlock = 256;
 constexpr int kMinBlocksWide = 4;
 constexpr uint32_t kStageChunk = 32768;
 constexpr uint32_t kWaitLimit = 1u << 24;
+constexpr uint64_t kDrainNs = 1000000000ull;  // 1 s for a staging copy in flight after a timeout
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of the
@@ -1382,6 +1383,13 @@ __device__ __forceinline__ void write_particle(const RunArgs &P, const PState<R>
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint32_t mb, uint32_t parity)
 {
     uint32_t ok;
@@ -1395,7 +1403,61 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t mb, uint32_t parity)
     return ok != 0;
 }
 
-__device__ bool stage_tables(const uint8_t *src, uint8_t *dst, uint32_t bytes, uint64_t *mbar, uint32_t *err)
+// Waits for phase `parity` of the block's mbarrier, at most wait_ns of the
+// global timer (and at most kWaitLimit polls).  On a timeout in any thread
+// the block sets BZ_ERR_STAGE_TIMEOUT, waits (bounded by kDrainNs) for a
+// copy still in flight, so that none lands after the block has exited, and
+// returns false.
+__device__ bool stage_wait(uint32_t mb, uint32_t parity, uint64_t wait_ns, uint32_t *err)
+{
+    bool ok = mbar_try_wait(mb, parity);
+    if (!ok) {
+        const uint64_t t0 = global_ns();
+        for (uint32_t it = 0; it < kWaitLimit && !ok && global_ns() - t0 < wait_ns; ++it)
+            ok = mbar_try_wait(mb, parity);
+    }
+    if (__syncthreads_or(!ok)) {
+        if (threadIdx.x == 0) atomicOr(err, BZ_ERR_STAGE_TIMEOUT);
+        bool done = ok;
+        const uint64_t t1 = global_ns();
+        for (uint32_t it = 0; it < kWaitLimit && !done && global_ns() - t1 < kDrainNs; ++it)
+            done = mbar_try_wait(mb, parity);
+        __syncthreads();
+        return false;
+    }
+    return true;
+}
+
+// Tests of the bounded staging wait (stage_hold): once the tables are in,
+// thread 0 opens the next phase expecting 16 bytes that no copy sends, and
+// the block waits on it.  No copy is in flight, so the wait can only run out.
+__device__ bool stage_hold_wait(uint32_t mb, uint32_t parity, uint64_t wait_ns, uint32_t *err)
+{
+    if (threadIdx.x == 0)
+        asm volatile(
+            "{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(mb),
+            "r"(16u)
+            : "memory");
+    return stage_wait(mb, parity, wait_ns, err);
+}
+
+__device__ void issue_stage_copy(const uint8_t *src, uint8_t *dst, uint32_t bytes, uint32_t mb)
+{
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(mb),
+                 "r"(bytes)
+                 : "memory");
+    const uint32_t d = smem_u32(dst);
+    for (uint32_t off = 0; off < bytes; off += kStageChunk) {
+        const uint32_t sz = (bytes - off < kStageChunk) ? bytes - off : kStageChunk;
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(d + off),
+            "l"(src + off), "r"(sz), "r"(mb)
+            : "memory");
+    }
+}
+
+__device__ bool stage_tables(const uint8_t *src, uint8_t *dst, uint32_t bytes, uint64_t *mbar, uint64_t wait_ns,
+                             uint32_t hold, uint32_t *err)
 {
     const uint32_t mb = smem_u32(mbar);
     if (threadIdx.x == 0) {
@@ -1405,32 +1467,9 @@ __device__ bool stage_tables(const uint8_t *src, uint8_t *dst, uint32_t bytes, u
     }
     __syncthreads();
     if (bytes == 0) return true;
-    if (threadIdx.x == 0) {
-        asm volatile(
-            "{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(mb),
-            "r"(bytes)
-            : "memory");
-        const uint32_t d = smem_u32(dst);
-        for (uint32_t off = 0; off < bytes; off += kStageChunk) {
-            const uint32_t sz = (bytes - off < kStageChunk) ? bytes - off : kStageChunk;
-            asm volatile(
-                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                    d + off),
-                "l"(src + off), "r"(sz), "r"(mb)
-                : "memory");
-        }
-    }
-    bool ok = false;
-    for (uint32_t it = 0; it < kWaitLimit && !ok; ++it) ok = mbar_try_wait(mb, 0);
-    const int failed = __syncthreads_or(!ok);
-    if (failed) {
-        if (threadIdx.x == 0) atomicOr(err, BZ_ERR_STAGE_TIMEOUT);
-        // wait (bounded) for the copy still in flight before the block exits
-        bool done = ok;
-        for (uint32_t it = 0; it < kWaitLimit && !done; ++it) done = mbar_try_wait(mb, 0);
-        __syncthreads();
-        return false;
-    }
+    if (threadIdx.x == 0) issue_stage_copy(src, dst, bytes, mb);
+    if (!stage_wait(mb, 0, wait_ns, err)) return false;
+    if (hold) return stage_hold_wait(mb, 1, wait_ns, err);
     return true;
 }
 
@@ -1440,35 +1479,16 @@ __device__ bool stage_tables(const uint8_t *src, uint8_t *dst, uint32_t bytes, u
 // Re-stages the tables of a new mixture into shared memory through the
 // block's mbarrier (already initialised), waiting on phase `parity`.
 __device__ bool restage_tables(const uint8_t *src, uint8_t *dst, uint32_t bytes, uint32_t mb, uint32_t parity,
-                               uint32_t *err)
+                               uint64_t wait_ns, uint32_t hold, uint32_t *err)
 {
     if (threadIdx.x == 0) {
         // the generic-proxy reads of the previous tables are ordered before
         // the asynchronous copy that overwrites them
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile(
-            "{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(mb),
-            "r"(bytes)
-            : "memory");
-        const uint32_t d = smem_u32(dst);
-        for (uint32_t off = 0; off < bytes; off += kStageChunk) {
-            const uint32_t sz = (bytes - off < kStageChunk) ? bytes - off : kStageChunk;
-            asm volatile(
-                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                    d + off),
-                "l"(src + off), "r"(sz), "r"(mb)
-                : "memory");
-        }
+        issue_stage_copy(src, dst, bytes, mb);
     }
-    bool ok = false;
-    for (uint32_t it = 0; it < kWaitLimit && !ok; ++it) ok = mbar_try_wait(mb, parity);
-    if (__syncthreads_or(!ok)) {
-        if (threadIdx.x == 0) atomicOr(err, BZ_ERR_STAGE_TIMEOUT);
-        bool done = ok;
-        for (uint32_t it = 0; it < kWaitLimit && !done; ++it) done = mbar_try_wait(mb, parity);
-        __syncthreads();
-        return false;
-    }
+    if (!stage_wait(mb, parity, wait_ns, err)) return false;
+    if (hold) return stage_hold_wait(mb, parity ^ 1u, wait_ns, err);
     return true;
 }
 
@@ -1522,7 +1542,8 @@ __global__ void __launch_bounds__(kBlock, MINB) batch_kernel(const __grid_consta
         }
         __syncthreads();
         if (P.blob != staged) {
-            if (!restage_tables(P.blob, smem, P.stage_bytes, mb, phase, P.err)) return;
+            if (!restage_tables(P.blob, smem, P.stage_bytes, mb, phase, P.stage_wait_ns, P.stage_hold, P.err))
+                return;
             phase ^= 1u;
             staged = P.blob;
         }
@@ -1579,12 +1600,6 @@ __device__ __forceinline__ uint64_t ld_acquire_ull(const unsigned long long *p)
     return v;
 }
 
-__device__ __forceinline__ uint64_t global_ns()
-{
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
 
 
 // Spawn mode (ChildrenBulletLimiter, Sec. 3.2): one persistent launch runs
@@ -1603,7 +1618,7 @@ __global__ void __launch_bounds__(kBlock, MINB) spawn_kernel(const __grid_consta
 {
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ __align__(8) uint64_t mbar;
-    if (!stage_tables(P.blob, smem, P.stage_bytes, &mbar, P.err)) return;
+    if (!stage_tables(P.blob, smem, P.stage_bytes, &mbar, P.stage_wait_ns, P.stage_hold, P.err)) return;
     const Tab<R> T = make_tab<R>(smem, P.blob, P.lay, CH_SMEM, P.stage_bytes);
     const Fld<R> F = make_fld<R>(P.f);
     const unsigned FULL = 0xffffffffu;
@@ -1697,7 +1712,7 @@ __global__ void __launch_bounds__(kBlock) replay_kernel(const ReplayArgs A)
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ __align__(8) uint64_t mbar;
     const RunArgs &P = A.run;
-    if (!stage_tables(P.blob, smem, P.stage_bytes, &mbar, P.err)) return;
+    if (!stage_tables(P.blob, smem, P.stage_bytes, &mbar, P.stage_wait_ns, P.stage_hold, P.err)) return;
     const Tab<R> T = make_tab<R>(smem, P.blob, P.lay, CH_SMEM, P.stage_bytes);
     const Fld<R> F = make_fld<R>(P.f);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < A.n; i += (int64_t)gridDim.x * blockDim.x) {

@@ -81,6 +81,9 @@ struct RunArgs {
     Fields f;
     unsigned long long *counter;  // spawn mode: next slot ticket
     uint64_t spawn_wait_ns;       // spawn mode: a warp without work gives up after this long
+    uint64_t stage_wait_ns;       // a block gives up waiting for its tables after this long
+    uint32_t stage_hold;          // tests of that wait: a second phase that no copy completes
+    uint32_t pad0;
     uint32_t *err;
     ParticlesDev out;
 };

@@ -135,6 +135,12 @@ def test_admission_overflow_is_rejected_at_submission(L):
     with pytest.raises(bz.BzError) as ei:     # invalid configurations never queue
         srv.submit(None, _cfg(0))
     assert ei.value.status == bz.BZ_EINVAL
+    # ... among them bounded-wait settings out of range
+    for bad in (dict(stage_wait_s=float("nan")), dict(stage_wait_s=4000.0), dict(hold_stage=2),
+                dict(spawn_wait_s=float("inf")), dict(hold_pending=1)):
+        with pytest.raises(bz.BzError) as ei:
+            srv.submit(None, _cfg(10, **bad))
+        assert ei.value.status == bz.BZ_EINVAL, bad
     assert srv.stats()["submitted"] == 0
     srv.close()
 
