@@ -77,6 +77,7 @@ def parse():
                     help="oracle electrons per E/N point of the sweep's drift-velocity check")
     ap.add_argument("--serve-rates", default="250,400,600,800,2000", help="Poisson arrival rates [req/s]")
     ap.add_argument("--serve-seconds", type=float, default=5.0, help="arrival window of each serving run")
+    ap.add_argument("--serve-slots", type=int, default=3, help="launch slots (streams) of the serving loop")
     ap.add_argument("--avalanche-cap", type=int, default=100_000,
                     help="population cap of the serving run's avalanche requests")
     ap.add_argument("--avalanche-frac", type=float, default=0.05, help="fraction of avalanche requests")
@@ -614,7 +615,7 @@ def serving_runs(ctx, rates, seconds, collisions=100, pool=64, streams=3, avalan
                                  "p99_ms": float(np.percentile([r.latency for r in ava], 99) * 1e3),
                                  "mean_final_population": float(np.mean([r.tallies["n_particles"] for r in ava]))}
         offered += sum(r.tallies["n_real"] for r in ava) / arr[-1] if n > 1 else 0.0
-        summ.update({"rate_req_s": rate, "offered_real_collisions_per_s": offered,
+        summ.update({"rate_req_s": rate, "slots": streams, "offered_real_collisions_per_s": offered,
                      "served_fraction": summ["real_collisions_per_s"] / offered if offered else None,
                      "max_concurrent": srv.stats()["max_running"], "launch_groups": srv.stats()["launches"]})
         srv.close()
@@ -755,8 +756,8 @@ def run_ours(args):
                                                 min(args.strategy_electrons, args.electrons))
     if rank == 0 and "serving" in args.legs:
         rates = [float(x) for x in args.serve_rates.split(",") if x]
-        serve = serving_runs(ctx, rates, args.serve_seconds, avalanche_frac=args.avalanche_frac,
-                             avalanche_cap=args.avalanche_cap)
+        serve = serving_runs(ctx, rates, args.serve_seconds, streams=args.serve_slots,
+                             avalanche_frac=args.avalanche_frac, avalanche_cap=args.avalanche_cap)
         out["serving"] = serve
         kept = [x for x in serve if x["served_fraction"] is not None and x["served_fraction"] >= 0.9]
         top = max(kept, key=lambda x: x["rate_req_s"]) if kept else None
