@@ -731,7 +731,7 @@ def run_ours(args):
                                      "batched_at_default_window_c_2": d["reals"] / (d["ms"] / 1e3),
                                      "gain": value / (d["reals"] / (d["ms"] / 1e3))}
     if "e2e" in args.legs:
-        out["e2e"] = e2e_run(ctx, stream, specs, rank, r["choice"], max(1, min(args.steps, 3)))
+        out["e2e"] = e2e_run(ctx, stream, specs, rank, r["choice"], min(max(args.steps, 2), 5))
     # ---- further legs (rank 0)
     if rank == 0 and args.workload == "batched" and ("sweep" in args.legs or "oracle" in args.legs):
         sw = sweep_run(ctx, stream, flush, world, dev, args, rank)

@@ -89,9 +89,14 @@ __device__ __forceinline__ uint4 philox_rk(uint32_t c0, uint32_t c1, uint32_t c2
 }
 
 // ((w >> 9) + 1/2) 2^-23: an odd multiple of 2^-24 in (0,1), exact in FP32.
+// FP32 builds it from the bits, with no integer conversion: 1 + k 2^-23
+// (k = w >> 9 as the mantissa of an exponent-0 float) minus 1 - 2^-24 is
+// (2k + 1) 2^-24 exactly, since that difference is representable -- the
+// same value for every k.
 template <typename R>
 __device__ __forceinline__ R uni(uint32_t w)
 {
+    if constexpr (sizeof(R) == 4) return __int_as_float(0x3f800000u | (w >> 9)) - 0.99999994f;
     return ((R)(w >> 9) + (R)0.5) * (R)(1.0 / 8388608.0);
 }
 
@@ -104,8 +109,10 @@ __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
 __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
 __device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
 // Division where the quotient may be a few ulp off (a window's length, which
-// any positive value makes exact; 1/nu'): the FP32 form takes the hardware
-// reciprocal (2 ulp), FP64 divides exactly.
+// any positive value makes exact; 1/nu'; 1 - cos under B, the inelastic
+// energy ratio and the screened-Coulomb angle, whose denominators lie in
+// [1, 2^126)): the FP32 form takes the hardware reciprocal (2 ulp), FP64
+// divides exactly.
 __device__ __forceinline__ float fdiv_(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ double fdiv_(double a, double b) { return a / b; }
 __device__ __forceinline__ double rsqrt_(double x) { return rsqrt(x); }
@@ -589,7 +596,7 @@ __device__ __forceinline__ void velocity_at(const Fld<R> &F, const PState<R> &s,
     if (BF && F.has_b) {
         R cs;
         sincos_(F.w * T, &sn, &cs);
-        omc = (cs > (R)0) ? sn * sn / ((R)1 + cs) : (R)1 - cs;
+        omc = (cs > (R)0) ? fdiv_(sn * sn, (R)1 + cs) : (R)1 - cs;  // 1 - cos, no cancellation
         const R ap = F.a_par * T;
         v0 = s.vr0 + ap * F.b0 - s.u0x * omc + s.bux * sn;
         v1 = s.vr1 + ap * F.b1 - s.u0y * omc + s.buy * sn;
@@ -1175,7 +1182,7 @@ __device__ __forceinline__ int trial(const Tab<R> &T, const Fld<R> &F, const Run
             R ct;
             const int ang = (p.bits >> 4) & 15;
             if (ang == BZ_ANG_SCREENED_COULOMB) {  // Eq. (5), eps in Hartree
-                ct = (R)1 - (R)2 * u2 / ((R)1 + (R)8 * (eps * (R)(1.0 / kHartreeEv)) * ((R)1 - u2));
+                ct = (R)1 - fdiv_((R)2 * u2, (R)1 + (R)8 * (eps * (R)(1.0 / kHartreeEv)) * ((R)1 - u2));
             } else if (EXT && ang == BZ_ANG_XI) {  // Eqs. (6)-(7)
                 ct = xi_cos_theta<R, CH_SMEM>(T, P, p.bits, ri, elo, eps, u2);
             } else {
@@ -1238,7 +1245,7 @@ __device__ __forceinline__ int trial(const Tab<R> &T, const Fld<R> &F, const Run
                     }
                 }
             } else {
-                const R x = p.eps_k / eps;  // Eq. (9), radicand clamped at 0
+                const R x = fdiv_(p.eps_k, eps);  // Eq. (9), radicand clamped at 0
                 const R rad = max_((R)0, (R)1 - p.minv * x);
                 ratio = max_((R)0, (R)1 - p.mfrac * x + p.kappa2 * (sqrt_(rad) * ct - (R)1));
                 if (kind == BZ_IONIZATION) {
