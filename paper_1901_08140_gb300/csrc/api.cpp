@@ -116,6 +116,38 @@ void dev_free(bz_ctx *c, void *p, size_t bytes, cudaStream_t s)
     else cudaFreeAsync(p, s);
 }
 
+// Host-blocking copies that wait for nothing else.  cudaMemcpy runs on the
+// legacy default stream, which first waits for all work queued there -- a
+// caller's launch on that stream included, so a mixture compiled while the
+// previous step runs would wait for it.  These copies take a non-blocking
+// stream of their own and wait for that stream alone.
+struct SyncCopies {
+    cudaStream_t s = nullptr;
+    cudaError_t e = cudaSuccess;
+    SyncCopies() { e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking); }
+    SyncCopies(const SyncCopies &) = delete;
+    SyncCopies &operator=(const SyncCopies &) = delete;
+    void add(void *dst, const void *src, size_t bytes, cudaMemcpyKind kind)
+    {
+        if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(dst, src, bytes, kind, s);
+    }
+    cudaError_t wait()
+    {
+        if (s) {
+            const cudaError_t w = cudaStreamSynchronize(s);
+            if (e == cudaSuccess) e = w;
+        }
+        return e;
+    }
+    ~SyncCopies()
+    {
+        if (s) {
+            cudaStreamSynchronize(s);
+            cudaStreamDestroy(s);
+        }
+    }
+};
+
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Electrons per tile: ~n / (blocks x per_block), rounded up to a multiple of
@@ -384,16 +416,23 @@ bz_status bz_create_gas_mixture(bz_ctx *ctx, const bz_gas *gases, int32_t n_gase
     cudaSetDevice(ctx->device);
     m->bytes32 = m->cm.blob32.size();
     m->bytes64 = m->cm.blob64.size();
-    m->blob32 = (uint8_t *)dev_alloc(ctx, m->bytes32, 0);
-    m->blob64 = (uint8_t *)dev_alloc(ctx, m->bytes64, 0);
+    SyncCopies up;
+    // the library's own pool allocates in the order of the copy stream; a
+    // caller's allocator takes its usual stream (the tables are freed only
+    // after a device-wide synchronisation)
+    const cudaStream_t as = ctx->custom_alloc ? (cudaStream_t)0 : up.s;
+    m->blob32 = (uint8_t *)dev_alloc(ctx, m->bytes32, as);
+    m->blob64 = (uint8_t *)dev_alloc(ctx, m->bytes64, as);
     if (!m->blob32 || !m->blob64) {
-        dev_free(ctx, m->blob32, m->bytes32, 0);
-        dev_free(ctx, m->blob64, m->bytes64, 0);
+        up.wait();
+        dev_free(ctx, m->blob32, m->bytes32, as);
+        dev_free(ctx, m->blob64, m->bytes64, as);
         delete m;
         return fail(BZ_ENOMEM, "device allocation of the mixture tables");
     }
-    cudaError_t e = cudaMemcpy(m->blob32, m->cm.blob32.data(), m->bytes32, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(m->blob64, m->cm.blob64.data(), m->bytes64, cudaMemcpyHostToDevice);
+    up.add(m->blob32, m->cm.blob32.data(), m->bytes32, cudaMemcpyHostToDevice);
+    up.add(m->blob64, m->cm.blob64.data(), m->bytes64, cudaMemcpyHostToDevice);
+    cudaError_t e = up.wait();
     if (e != cudaSuccess) {
         dev_free(ctx, m->blob32, m->bytes32, 0);
         dev_free(ctx, m->blob64, m->bytes64, 0);
@@ -698,22 +737,19 @@ bz_status bz_read_particles(bz_swarm *sw, const bz_particles *o)
         {o->n_real, sw->p.n_real, 4 * n}, {o->n_null, sw->p.n_null, 4 * n}, {o->n_fail, sw->p.n_fail, 4 * n},
         {o->n_ion, sw->p.n_ion, 4 * n}, {o->n_att, sw->p.n_att, 4 * n}, {o->steps, sw->p.steps, 4 * n},
         {o->status, sw->p.status, 4 * n}};
-    for (auto &c : cp) {
-        if (!c.dst) continue;
-        if ((e = cudaMemcpy(c.dst, c.src, c.bytes, cudaMemcpyDeviceToHost)) != cudaSuccess)
-            return cuda_fail(e, "copy of particle state");
-    }
+    SyncCopies rd;
+    for (auto &c : cp)
+        if (c.dst) rd.add(c.dst, c.src, c.bytes, cudaMemcpyDeviceToHost);
     const uint64_t np = sw->n_primary < n ? sw->n_primary : n;
     if (o->id) {
         for (uint64_t i = 0; i < np; ++i) o->id[i] = sw->cfg.id_offset + i;
-        if (n > np && (e = cudaMemcpy(o->id + np, sw->bid, 8 * (n - np), cudaMemcpyDeviceToHost)) != cudaSuccess)
-            return cuda_fail(e, "copy of particle ids");
+        if (n > np) rd.add(o->id + np, sw->bid, 8 * (n - np), cudaMemcpyDeviceToHost);
     }
     if (o->t_birth) {
         for (uint64_t i = 0; i < np; ++i) o->t_birth[i] = 0.0;
-        if (n > np && (e = cudaMemcpy(o->t_birth + np, sw->bt, 8 * (n - np), cudaMemcpyDeviceToHost)) != cudaSuccess)
-            return cuda_fail(e, "copy of birth times");
+        if (n > np) rd.add(o->t_birth + np, sw->bt, 8 * (n - np), cudaMemcpyDeviceToHost);
     }
+    if ((e = rd.wait()) != cudaSuccess) return cuda_fail(e, "copy of particle state");
     return BZ_OK;
 }
 
@@ -895,7 +931,9 @@ bz_status bz_create_batch(bz_ctx *ctx, int32_t n, const bz_mixture *const *mixtu
         o_gs[i] = take(sizeof(double) * (bz::kGroups * (bz::kQ1 + bz::kQ2) + 8));
     }
     b->bytes = off;
-    b->mem = (uint8_t *)dev_alloc(ctx, b->bytes, 0);
+    // the set-up copies; the library's own pool allocates in their stream's order
+    SyncCopies up;
+    b->mem = (uint8_t *)dev_alloc(ctx, b->bytes, ctx->custom_alloc ? (cudaStream_t)0 : up.s);
     if (!b->mem) {
         delete b;
         return fail(BZ_ENOMEM, "device allocation of the batch");
@@ -942,9 +980,10 @@ bz_status bz_create_batch(bz_ctx *ctx, int32_t n, const bz_mixture *const *mixtu
         t.out = b->tallies_dev + i;
     }
     b->targs_host = targs;
-    e = cudaMemcpy(b->desc, desc.data(), sizeof(bz::RunArgs) * n, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(b->tiles, tiles.data(), sizeof(uint4) * tiles.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(b->targs, targs.data(), sizeof(bz::TallyArgs) * n, cudaMemcpyHostToDevice);
+    up.add(b->desc, desc.data(), sizeof(bz::RunArgs) * n, cudaMemcpyHostToDevice);
+    up.add(b->tiles, tiles.data(), sizeof(uint4) * tiles.size(), cudaMemcpyHostToDevice);
+    up.add(b->targs, targs.data(), sizeof(bz::TallyArgs) * n, cudaMemcpyHostToDevice);
+    e = up.wait();
     if (e == cudaSuccess) {
         b->tallies_host = (bz_tallies *)pinned_block(ctx, sizeof(bz_tallies) * n, &b->tallies_cap);
         if (!b->tallies_host) e = cudaErrorMemoryAllocation;
@@ -1018,10 +1057,11 @@ bz_status bz_batch_read_particles(bz_batch *b, int32_t i, const bz_particles *o)
         {o->nu_p, p.nup, 4 * m}, {o->n_real, p.n_real, 4 * m}, {o->n_null, p.n_null, 4 * m},
         {o->n_fail, p.n_fail, 4 * m}, {o->n_ion, p.n_ion, 4 * m}, {o->n_att, p.n_att, 4 * m},
         {o->steps, p.steps, 4 * m}, {o->status, p.status, 4 * m}};
-    for (auto &c : cp) {
-        if (!c.dst) continue;
-        if ((e = cudaMemcpy(c.dst, c.src, c.bytes, cudaMemcpyDeviceToHost)) != cudaSuccess)
-            return cuda_fail(e, "copy of particle state");
+    {
+        SyncCopies rd;
+        for (auto &c : cp)
+            if (c.dst) rd.add(c.dst, c.src, c.bytes, cudaMemcpyDeviceToHost);
+        if ((e = rd.wait()) != cudaSuccess) return cuda_fail(e, "copy of particle state");
     }
     for (uint64_t k = 0; k < m; ++k) {
         if (o->id) o->id[k] = b->id_offset[i] + k;
@@ -1084,7 +1124,11 @@ static bz_status group_sums1_of(const bz::TallyArgs &t, cudaEvent_t done, double
     if (!out) return fail(BZ_EINVAL, "null output");
     cudaError_t e = cudaEventSynchronize(done);
     std::vector<double> g((size_t)bz::kGroups * bz::kGS);
-    if (e == cudaSuccess) e = cudaMemcpy(g.data(), t.gsum, sizeof(double) * g.size(), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) {
+        SyncCopies rd;
+        rd.add(g.data(), t.gsum, sizeof(double) * g.size(), cudaMemcpyDeviceToHost);
+        e = rd.wait();
+    }
     if (e != cudaSuccess) return cuda_fail(e, "group sums");
     for (int k = 0; k < bz::kGroups; ++k)
         for (int q = 0; q < bz::kQ1; ++q) out[k * bz::kQ1 + q] = g[(size_t)k * bz::kGS + q];
@@ -1099,7 +1143,11 @@ static bz_status group_sums2_of(const bz::TallyArgs &t, cudaEvent_t done, cudaSt
     if (e == cudaSuccess) e = bz::launch_group_sums2(t, drift, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     std::vector<double> g((size_t)bz::kGroups * bz::kGS);
-    if (e == cudaSuccess) e = cudaMemcpy(g.data(), t.gsum, sizeof(double) * g.size(), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) {
+        SyncCopies rd;
+        rd.add(g.data(), t.gsum, sizeof(double) * g.size(), cudaMemcpyDeviceToHost);
+        e = rd.wait();
+    }
     if (e != cudaSuccess) return cuda_fail(e, "group sums about the given drift");
     for (int k = 0; k < bz::kGroups; ++k)
         for (int q = 0; q < bz::kQ2; ++q) out[k * bz::kQ2 + q] = g[(size_t)k * bz::kGS + bz::kQ1 + q];
