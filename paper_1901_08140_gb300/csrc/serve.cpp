@@ -3,10 +3,11 @@
 //
 // Requests (a compiled mixture and a swarm configuration) are queued in
 // arrival order.  A worker thread owns S launch slots (one non-blocking CUDA
-// stream each).  Whenever a slot is free it takes the queued requests in
-// arrival order -- as many as fit the device-memory admission budget, up to
-// a group cap, all of one step-kernel class -- and runs them together as one
-// batched persistent launch on that slot (bz_create_batch/bz_launch_batch);
+// stream each).  Whenever a slot is free it takes the request at the head of
+// the queue and, in arrival order, further queued requests of its step-kernel
+// class, looking past requests of other classes -- as many as fit the
+// device-memory admission budget, up to a group cap -- and runs them together
+// as one batched persistent launch on that slot (bz_create_batch/bz_launch_batch);
 // a spawn-mode request (an avalanche) runs alone as its own persistent
 // launch (bz_run_swarm).  Running launches are polled without blocking, so
 // requests that arrive while others are on the GPU are admitted as soon as a
@@ -196,6 +197,10 @@ bool poll(bz_server *s, Launch &L, std::vector<bz_tallies> *t, std::vector<bz_st
     return true;  // the launch failed to start: its statuses are set already
 }
 
+// How deep admission looks past the head of the queue for requests of the
+// head's class.
+constexpr size_t kLookahead = 4096;
+
 void work(bz_server *s)
 {
     if (s->ctx && s->opts.simulate <= 0) cudaSetDevice(bz::ctx_device(s->ctx));
@@ -217,11 +222,23 @@ void work(bz_server *s)
             std::vector<bz_swarm_config> cfgs;
             bool alone = false;
             const double tn = now_s(s);
-            while (!s->queue.empty() && (int)L.ids.size() < s->opts.max_group) {
-                Req &r = s->reqs[s->queue.front()];
+            // The head first; then, in arrival order, queued requests of the
+            // head's step-kernel class from further down the queue (at most
+            // kLookahead entries deep), so that a request of another class in
+            // between -- an avalanche, which runs alone -- does not cut the
+            // launch short.  The head is always admitted first, so no request
+            // waits behind a later one of its own class; one of another class
+            // waits at most for this launch to be formed.
+            size_t scanned = 0;
+            for (auto it = s->queue.begin();
+                 it != s->queue.end() && (int)L.ids.size() < s->opts.max_group && scanned < kLookahead; ++scanned) {
+                Req &r = s->reqs[*it];
+                if (!L.ids.empty() && (r.alone || r.key != s->reqs[L.ids[0]].key)) {
+                    ++it;
+                    continue;
+                }
                 if (s->st.bytes_in_use + L.bytes + r.bytes > s->opts.memory_budget_bytes) break;
-                if (!L.ids.empty() && (r.alone || r.key != s->reqs[L.ids[0]].key)) break;
-                s->queue.pop_front();
+                it = s->queue.erase(it);
                 r.state = RUNNING;
                 r.t_admit = tn;
                 r.launch = s->st.launches;

@@ -88,8 +88,10 @@ def test_groups_hold_one_kernel_class_and_avalanches_run_alone(L):
     srv.pause(False)
     res = _wait_all(srv, ids)
     launch = [res[i][2]["launch"] for i in ids]
-    # [0, 1] lean without B, [2, 3] with B, [4] spawn alone, [5, 6], [7, 8] FP64
-    assert launch == [0, 0, 1, 1, 2, 3, 3, 4, 4]
+    # the head's class is gathered past other classes: [0, 1, 5, 6] lean without B,
+    # [2, 3] with B, [4] spawn alone, [7, 8] FP64 -- each launch led by the oldest
+    # request still queued
+    assert launch == [0, 0, 1, 1, 2, 0, 0, 3, 3]
     srv.close()
 
 
