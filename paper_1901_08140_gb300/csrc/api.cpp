@@ -649,7 +649,13 @@ bz_status bz_run_swarm(bz_ctx *ctx, const bz_mixture *mix, const bz_swarm_config
         // unpublished birth records read as id 0
         a.counter = ticket;
         if (e == cudaSuccess && nb) e = cudaMemsetAsync(s->bid, 0, 8 * nb, s->stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(n_total, init, sizeof init, cudaMemcpyHostToDevice, s->stream);
+        // staged in the swarm's pinned tally slot (its tallies arrive there
+        // later in stream order): a copy from pageable memory would first wait
+        // for the stream's earlier work
+        static_assert(sizeof(bz_tallies) >= sizeof init, "tally slot too small");
+        memcpy(s->tallies_host, init, sizeof init);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(n_total, s->tallies_host, sizeof init, cudaMemcpyHostToDevice, s->stream);
     }
     if (e == cudaSuccess) e = cudaEventRecord(s->ev[0], s->stream);
     if (!spawn) {
