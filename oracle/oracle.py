@@ -5,8 +5,8 @@ benchmark's CPU-baseline leg use it; the product path never does.
 
 Parity status of the oracle's functions (each pinned by a ``-m "not gpu"``
 test against something other than itself):
-  philox / uniform      statistical pins (uniformity, independence); the
-                        method asks only for uniform R in [0,1) (Eqs. 3-5)
+  philox / uniform      known answers of cuRAND's host Philox4_32_10
+                        generator; uniformity, independence, avalanche
   sigma (tables+ext.)   hand-worked cases of Sec. 2.2, Eqs. (12)-(14)
   nu, select_channel    Eq. (2) against channel ratios (chi-square)
   majorant              brute-force maximum on a dense grid
@@ -16,8 +16,11 @@ test against something other than itself):
   move                  brute-force RK4 integration of the Lorentz force
   run_swarm             closed forms of the constant-frequency Maxwell model
                         (drift velocity, mean energy, D_L, D_T)
-  ionization split, dummy attachment   readings of Sec. 2, pinned only by
-                        energy accounting (parity unpinned in absolute terms)
+  ionization split      closed-form moments of one ionizing collision (Eq. 9
+                        with the uniform split of the remaining energy): mean,
+                        second moment, correlation with the scattering cosine
+  dummy attachment      the reading of Sec. 2 (a plastic collision: the
+                        electron stops), checked directly
 """
 from __future__ import annotations
 

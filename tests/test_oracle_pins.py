@@ -486,6 +486,47 @@ def test_ionization_split_and_attachment_energy_accounting():
     assert np.all(eio[att, 1] == 0.0) and np.all(out[att, 3:6] == 0.0)
 
 
+def test_ionization_energy_moments_match_eq9_closed_forms():
+    """One ionizing collision from a mono-energetic start (Eq. 9 with the
+    ionization threshold as epsilon_k, then the uniform split of reading R9),
+    against moments written from the equation, not from the oracle's code.
+    With the new direction isotropic (cos theta uniform on [-1, 1]), the
+    energy ratio is A + B cos theta, A = 1 - M/(m+M) x - 2mM/(m+M)^2,
+    B = 2mM/(m+M)^2 sqrt(1 - (m+M)/M x), x = IP/eps0, and the primary keeps
+    (1 - U) of it: E[eps'] = eps0 A / 2, E[eps'^2] = eps0^2 (A^2 + B^2/3) / 3,
+    E[eps' cos theta] = eps0 B / 6.  A light target (M = 4 m) makes every
+    term of Eq. 9 a visible share of the mean; a dropped term, a wrong sign of
+    the angular term or a split other than a uniform fraction fails."""
+    M_t, ip, eps0, n = 4 * ME, 15.0, 50.0, 200_000
+    e = np.geomspace(ip, 1e4, 2001)
+    v = np.sqrt(2 * e * QE / ME)
+    nd = W.N_STP_293
+    gas = W.Gas("ion4", M_t, nd, W.ISOTROPIC, [W.Channel(W.IONIZATION, ip, e, 1e12 / (nd * v))])
+    m = O.Mixture([gas])
+    rng = np.random.default_rng(77)
+    d = rng.normal(size=(n, 3))
+    d /= np.linalg.norm(d, axis=1)[:, None]
+    speed = math.sqrt(2 * eps0 * QE / ME)
+    state = np.zeros((n, 8))
+    state[:, 3:6] = d * speed
+    state[:, 7] = m.nu(eps0) * (1 + 1e-9)
+    out, dec, eio = O.step_replay(m, state, np.arange(n, dtype=np.uint64), np.full(n, 5, np.uint32),
+                                  e_over_n_Td=0.0, seed=2024)
+    real = dec >= 0
+    assert real.mean() > 0.999
+    ef = 0.5 * ME * np.sum(out[real, 3:6] ** 2, axis=1) / QE
+    vn = out[real, 3:6] / np.linalg.norm(out[real, 3:6], axis=1)[:, None]
+    ct = np.sum(vn * d[real], axis=1)
+    x = ip / eps0
+    kappa = 2 * ME * M_t / (ME + M_t) ** 2
+    A = 1 - M_t / (ME + M_t) * x - kappa
+    B = kappa * math.sqrt(1 - x / (M_t / (ME + M_t)))
+    for sample, expect in ((ef, eps0 * A / 2), (ef ** 2, eps0 ** 2 * (A * A + B * B / 3) / 3),
+                           (ef * ct, eps0 * B / 6), (ct, 0.0), (ct ** 2, 1.0 / 3.0)):
+        se = sample.std() / math.sqrt(len(sample))
+        assert abs(sample.mean() - expect) < 4 * se, (sample.mean(), expect, se)
+
+
 def test_isotropic_scattering_kinematics():
     """Isotropic elastic scattering (Sec. 2, Eq. 8) through the whole trial
     step: whatever the incident direction, the new one is uniform on the
