@@ -54,7 +54,7 @@ ALG_OPS = {
     "plain": {"step": 95, "window": 61, "real": 67},
     "field": {"step": 128, "window": 86, "real": 135},
 }
-LEGS = ("plain", "e2e", "sweep", "oracle", "configs", "precision", "strategies", "serving", "cpu")
+LEGS = ("plain", "e2e", "sweep", "oracle", "configs", "precision", "strategies", "avalanche", "serving", "cpu")
 L2_NOTE = "flushed between steps (256 MiB write)"
 
 
@@ -81,6 +81,8 @@ def parse():
     ap.add_argument("--avalanche-cap", type=int, default=100_000,
                     help="population cap of the serving run's avalanche requests")
     ap.add_argument("--avalanche-frac", type=float, default=0.05, help="fraction of avalanche requests")
+    ap.add_argument("--avalanche-caps", default="1e5,1e7,1e8",
+                    help="population caps of the avalanche leg (one seed electron each, run alone)")
     ap.add_argument("--strategy-electrons", type=int, default=100_000)
     ap.add_argument("--precision-electrons", type=int, default=100_000,
                     help="electrons per swarm of the FP32-against-FP64 comparison")
@@ -574,6 +576,36 @@ def strategy_runs(ctx, mix, specs, electrons):
     return {"electrons_per_point": electrons, "zeta": 0.25, "grace": 5000, "bins_per_decade": 8, "modes": out}
 
 
+def avalanche_runs(ctx, stream, caps):
+    """Avalanches alone (the serving workload's avalanche request): one seed
+    electron at 300 Td in Ar/CO2 93/7, spawn mode, 1 ns, windowed trial
+    frequency, growth capped at each population in `caps`; latency on the
+    host clock from the launch to the tallies, and the step kernel's time."""
+    from paper_1901_08140_gb300 import bz
+    from paper_1901_08140_gb300 import workloads as W
+    mix = bz.Mixture(ctx, W.ar_co2_avalanche_mixture())
+
+    def cfg(cap, k):
+        return bz.make_config(n_electrons=1, real_collisions=10 ** 9, e_over_n_Td=300.0, seed=W.swarm_seed(5000 + k),
+                              t_end_s=1e-9, spawn=True, pop_cap=int(cap), trial_mode=bz.BZ_TRIAL_WINDOW)
+    warm = bz.run_swarm(ctx, mix, cfg(1000, 0), stream)
+    warm.tallies()
+    warm.close()
+    out = []
+    for k, cap in enumerate(caps):
+        t0 = time.perf_counter()
+        sw = bz.run_swarm(ctx, mix, cfg(cap, k + 1), stream)
+        t = sw.tallies()
+        lat = time.perf_counter() - t0
+        kms = sw.timing()[0]
+        sw.close()
+        out.append({"pop_cap": int(cap), "latency_ms": lat * 1e3, "kernel_ms": kms,
+                    "final_population": int(t["n_particles"]), "real_collisions": int(t["n_real"]),
+                    "real_collisions_per_s": t["n_real"] / (kms / 1e3) if kms > 0 else None,
+                    "capped_ionizations": int(t.get("n_capped", 0))})
+    return out
+
+
 def serving_runs(ctx, rates, seconds, collisions=100, pool=64, streams=3, avalanche_frac=0.05,
                  avalanche_cap=100_000):
     """Continuous-batching request loop under Poisson arrivals: swarm sizes,
@@ -754,6 +786,10 @@ def run_ours(args):
         ss = W.argon_sweep(points=32)
         out["trial_strategies"] = strategy_runs(ctx, bz.Mixture(ctx, ss[0].gases), ss,
                                                 min(args.strategy_electrons, args.electrons))
+    if rank == 0 and "avalanche" in args.legs:
+        caps = [float(x) for x in args.avalanche_caps.split(",") if x]
+        out["avalanche"] = {"workload": "one seed electron, 300 Td, Ar/CO2 93/7, spawn mode, t_end 1 ns, windowed "
+                                        "trial frequency, run alone", "runs": avalanche_runs(ctx, stream, caps)}
     if rank == 0 and "serving" in args.legs:
         rates = [float(x) for x in args.serve_rates.split(",") if x]
         serve = serving_runs(ctx, rates, args.serve_seconds, streams=args.serve_slots,
