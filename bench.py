@@ -78,6 +78,7 @@ def parse():
     ap.add_argument("--serve-rates", default="250,400,600,800,2000", help="Poisson arrival rates [req/s]")
     ap.add_argument("--serve-seconds", type=float, default=5.0, help="arrival window of each serving run")
     ap.add_argument("--serve-slots", type=int, default=3, help="launch slots (streams) of the serving loop")
+    ap.add_argument("--serve-max-group", type=int, default=512, help="requests per launch at most")
     ap.add_argument("--avalanche-cap", type=int, default=100_000,
                     help="population cap of the serving run's avalanche requests")
     ap.add_argument("--avalanche-frac", type=float, default=0.05, help="fraction of avalanche requests")
@@ -607,7 +608,7 @@ def avalanche_runs(ctx, stream, caps):
 
 
 def serving_runs(ctx, rates, seconds, collisions=100, pool=64, streams=3, avalanche_frac=0.05,
-                 avalanche_cap=100_000):
+                 avalanche_cap=100_000, max_group=512):
     """Continuous-batching request loop under Poisson arrivals: swarm sizes,
     mixtures and fields of the batched workload (a pool of compiled
     mixtures), I real collisions per request, windowed trial frequency; a
@@ -636,7 +637,7 @@ def serving_runs(ctx, rates, seconds, collisions=100, pool=64, streams=3, avalan
             j = int(rng.integers(pool))
             cfg = bz.config_from_spec(specs[j], trial_mode=bz.BZ_TRIAL_WINDOW, seed=seed)
             reqs.append(serving.Request(i, mixes[j], cfg, arrival=float(arr[i]), n_electrons=int(cfg.n_electrons)))
-        srv = serving.Server(ctx, memory_budget=60e9, n_slots=streams)
+        srv = serving.Server(ctx, memory_budget=60e9, n_slots=streams, max_group=max_group)
         done = srv.run(reqs, realtime=True)
         summ = serving.latency_summary(done)
         ava = [r for r in done if getattr(r.cfg, "spawn", 0)]
@@ -647,7 +648,8 @@ def serving_runs(ctx, rates, seconds, collisions=100, pool=64, streams=3, avalan
                                  "p99_ms": float(np.percentile([r.latency for r in ava], 99) * 1e3),
                                  "mean_final_population": float(np.mean([r.tallies["n_particles"] for r in ava]))}
         offered += sum(r.tallies["n_real"] for r in ava) / arr[-1] if n > 1 else 0.0
-        summ.update({"rate_req_s": rate, "slots": streams, "offered_real_collisions_per_s": offered,
+        summ.update({"rate_req_s": rate, "slots": streams, "max_group": max_group,
+                     "offered_real_collisions_per_s": offered,
                      "served_fraction": summ["real_collisions_per_s"] / offered if offered else None,
                      "max_concurrent": srv.stats()["max_running"], "launch_groups": srv.stats()["launches"]})
         srv.close()
@@ -793,7 +795,8 @@ def run_ours(args):
     if rank == 0 and "serving" in args.legs:
         rates = [float(x) for x in args.serve_rates.split(",") if x]
         serve = serving_runs(ctx, rates, args.serve_seconds, streams=args.serve_slots,
-                             avalanche_frac=args.avalanche_frac, avalanche_cap=args.avalanche_cap)
+                             avalanche_frac=args.avalanche_frac, avalanche_cap=args.avalanche_cap,
+                             max_group=args.serve_max_group)
         out["serving"] = serve
         kept = [x for x in serve if x["served_fraction"] is not None and x["served_fraction"] >= 0.9]
         top = max(kept, key=lambda x: x["rate_req_s"]) if kept else None
