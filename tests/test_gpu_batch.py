@@ -103,3 +103,40 @@ def test_batch_rejects_mixed_precision(ctx):
     with pytest.raises(bz.BzError) as ei:
         bz.Batch(ctx, [m for m, _ in items], cfgs)
     assert ei.value.status == bz.BZ_EINVAL
+
+
+def test_set_up_does_not_wait_for_a_running_launch(ctx):
+    """The library's set-up copies (a mixture's tables, a batch's descriptors)
+    run on a stream of their own: while a launch runs on the legacy default
+    stream, compiling and uploading a mixture and setting up a batch return
+    before it ends (the overlap the end-to-end loop relies on)."""
+    import time
+    specs = W.argon_sweep(n_electrons=1_000_000, real_collisions=1000, points=32)
+    mix = bz.Mixture(ctx, specs[0].gases)
+    cfgs = [bz.config_from_spec(s, trial_mode=bz.BZ_TRIAL_WINDOW) for s in specs]
+    other = W.batched_swarms(count=2)[1]
+    ocfg = bz.config_from_spec(other, n_electrons=1000, real_collisions=10, trial_mode=bz.BZ_TRIAL_WINDOW)
+    # warm the allocators' caches with the same sizes first: a fresh pinned or
+    # device allocation may itself wait for the device
+    for _ in range(2):
+        m = bz.Mixture(ctx, other.gases)
+        b = bz.Batch(ctx, [m], [ocfg])
+        b.close()
+        m.close()
+    big = bz.Batch(ctx, [mix] * len(cfgs), cfgs)
+    big.launch()
+    t0 = time.perf_counter()
+    m2 = bz.Mixture(ctx, other.gases)
+    b2 = bz.Batch(ctx, [m2], [ocfg])
+    dt = time.perf_counter() - t0
+    running = not big.ready()
+    big.tallies()
+    ms = big.timing()[0]
+    b2.launch()
+    t2 = b2.tallies()[0]
+    assert running, f"the {ms:.0f} ms launch ended before the set-up returned ({dt * 1e3:.0f} ms)"
+    assert dt < 0.5 * ms / 1e3
+    assert t2["n_real"] == 10 * 1000
+    b2.close()
+    m2.close()
+    big.close()
