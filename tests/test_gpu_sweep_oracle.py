@@ -16,6 +16,11 @@ agree in every swarm statistic within their standard errors.
   sum of squared z-scores of each quantity over the 32 points below the
   0.999 quantile of chi-square with 32 degrees of freedom, and within 0.5 %
   wherever the two samples resolve 0.5 % (3 combined SE below it).
+* The 256-swarm batched workload exactly as the benchmark launches it (one
+  persistent launch from a CUDA graph, the autotuner's default options):
+  four of its swarms -- 3-4 gases, 30-300 Td, |B| >= 0.3 T at an oblique
+  angle, at least 1e5 electrons -- against 8000 oracle electrons each, W,
+  <eps>, D_L and D_T within 4 combined standard errors (16 comparisons).
 * Four configurations at high statistics (1e7 GPU and 1e6 oracle electrons
   x 100 real collisions): three points of the sweep and the Ar/CO2 90/10
   mixture with B = 1 T perpendicular to E, all four in one batched launch:
@@ -139,3 +144,31 @@ def test_high_statistics_against_oracle_within_half_percent(ctx):
             assert abs(z) <= 3.0, (nm, k, g[k], o[k], z)
             assert abs(rel) <= 0.005, (nm, k, rel)
     print("\nhigh statistics vs oracle (rel, rel SE, z):", report)
+
+
+def test_batched_workload_as_timed_against_oracle(ctx):
+    from paper_1901_08140_gb300 import autotune
+    specs = W.batched_swarms(count=256, real_collisions=1000)
+    mixes = [bz.Mixture(ctx, sp.gases) for sp in specs]
+    cfgs = autotune.apply([bz.config_from_spec(sp, trial_mode=bz.BZ_TRIAL_WINDOW) for sp in specs],
+                          autotune.DEFAULT)
+    batch = autotune.make_batch(ctx, mixes, cfgs, autotune.DEFAULT)
+    batch.launch()
+    tg = batch.tallies()
+    batch.close()
+    assert all(t["error_flags"] == 0 for t in tg)
+    assert sum(t["n_real"] for t in tg) == 1000 * sum(sp.n_electrons for sp in specs)
+    picked = [i for i, sp in enumerate(specs) if 30.0 <= sp.e_over_n_Td <= 300.0 and len(sp.gases) >= 3
+              and sp.b_T >= 0.3 and sp.n_electrons >= 100_000][:4]
+    assert len(picked) == 4
+    report = {}
+    for i in picked:
+        sp = specs[i]
+        # oracle ids follow the GPU's: two independent samples of one swarm
+        o = oracle_tallies(sp.gases, sp.e_over_n_Td, sp.b_T, sp.b_angle_rad, 8000, 1000, sp.seed,
+                           id0=sp.n_electrons)
+        for k in QUANTITIES:
+            rel, rse, z = compare(tg[i], o, k)
+            report[(i, k)] = (round(rel, 5), round(z, 2))
+            assert abs(z) <= 4.0, (i, k, tg[i][k], o[k], z)
+    print("\nbatched workload vs oracle (rel, z):", report)
