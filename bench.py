@@ -19,8 +19,9 @@ the C ABI from host buffers (tables compiled and copied, configurations
 copied, tallies read back) inside the timed region; ``roofline`` relates the
 step kernel's algorithmic thread operations to the SM issue rate;
 ``cpu_baseline`` is the FP64 oracle timed on this host's cores.  Further
-keys: the Argon-like sweep (its throughput, its roofline and its drift
-velocity against the oracle, the metric's accuracy qualifier), the Maxwell
+keys: four swarms of the batched workload against the oracle, the
+Argon-like sweep (its throughput, its roofline and its drift velocity
+against the oracle, the metric's accuracy qualifier), the Maxwell
 and Ar/CO2 configurations, FP32 against FP64, the paper's trial
 frequencies, and serving latency under Poisson load.
 """
@@ -465,6 +466,35 @@ def sweep_vs_oracle(sweep_tallies, specs, n_oracle):
             "max_abs_rel_W": summ["W"]["max_abs_rel"], "per_point": rows}
 
 
+def batched_vs_oracle(tallies, specs, n_oracle=8000, count=4):
+    """Swarms of the timed batched workload (3-4 gases, 30-300 Td, |B| >= 0.3 T,
+    at least 1e5 electrons: the first `count` of them) against the FP64
+    oracle on n_oracle electrons each, ids after the GPU's: relative
+    difference, combined standard error, z-score."""
+    from oracle import oracle as O
+    from oracle import tallies as OT
+    picked = [i for i, s in enumerate(specs) if 30.0 <= s.e_over_n_Td <= 300.0 and len(s.gases) >= 3
+              and s.b_T >= 0.3 and s.n_electrons >= 100_000][:count]
+    rows = []
+    t0 = time.perf_counter()
+    for i in picked:
+        s, g = specs[i], tallies[i]
+        m = O.Mixture(s.gases)
+        p = O.run_swarm(m, e_over_n_Td=s.e_over_n_Td, b_T=s.b_T, b_angle_rad=s.b_angle_rad,
+                        real_collisions=s.real_collisions, n=n_oracle, seed=s.seed, id0=s.n_electrons,
+                        threads=O.cpu_count())
+        o = OT.swarm_tallies(p, s.e_over_n_Td, m.n_total)
+        row = {"swarm": i, "E/N_Td": s.e_over_n_Td, "B_T": s.b_T, "gases": len(s.gases), "gpu_electrons": s.n_electrons,
+               "oracle_fails": int(p["n_fail"].sum())}
+        for k in ("W", "eps", "D_L", "D_T"):
+            se = math.hypot(g[k + "_se"], o[k + "_se"])
+            row[k] = {"rel": (g[k] - o[k]) / abs(o[k]), "rel_se": se / abs(o[k]), "z": (g[k] - o[k]) / se}
+        rows.append(row)
+    return {"oracle_electrons_per_swarm": n_oracle, "seconds": time.perf_counter() - t0,
+            "max_abs_z": max(abs(r[k]["z"]) for r in rows for k in ("W", "eps", "D_L", "D_T")),
+            "max_abs_rel_W": max(abs(r["W"]["rel"]) for r in rows), "per_swarm": rows}
+
+
 def configs_run(ctx, stream):
     """Configurations 1 and 3 on their own: the Maxwell-model gas in FP64
     against its closed forms, and Ar/CO2 90/10 with B = 1 T perpendicular to E."""
@@ -767,6 +797,8 @@ def run_ours(args):
     if "e2e" in args.legs:
         out["e2e"] = e2e_run(ctx, stream, specs, rank, r["choice"], min(max(args.steps, 2), 5))
     # ---- further legs (rank 0)
+    if rank == 0 and args.workload == "batched" and "oracle" in args.legs and args.scale == 1:
+        out["batched_vs_oracle"] = batched_vs_oracle(r["tallies"][-len(specs):], specs)
     if rank == 0 and args.workload == "batched" and ("sweep" in args.legs or "oracle" in args.legs):
         sw = sweep_run(ctx, stream, flush, world, dev, args, rank)
         sw_counts = counts_of(sw["_tallies"])
