@@ -342,7 +342,14 @@ void bz_destroy_swarm(bz_swarm *sw);
  * changes.  The launch, the FP64 tallies of every swarm and the copy of
  * the tallies to the host are captured once in a CUDA graph and replayed
  * by bz_launch_batch.  Every swarm's results equal those of bz_run_swarm
- * with the same configuration.
+ * with the same configuration when the batch's swarms all have a magnetic
+ * field or all lack one, and their mixtures all stage their channel tables
+ * in shared memory or all leave them in global memory
+ * (bz_mixture_info.channels_in_smem).  Otherwise the batch runs the field's
+ * build, or searches every mixture's cumulative channel table in global
+ * memory, and a swarm that runs differently alone matches its run alone to
+ * FP32 rounding (a channel choice differs only where a draw falls within
+ * rounding of a channel boundary).
  * ------------------------------------------------------------------------ */
 typedef struct bz_batch bz_batch;
 

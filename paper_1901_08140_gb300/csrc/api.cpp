@@ -390,6 +390,7 @@ void bz::set_last_error(const std::string &msg) { g_err = msg; }
 int bz::ctx_device(const bz_ctx *ctx) { return ctx->device; }
 bz_status bz::check_config(const bz_swarm_config *cfg) { return validate_config(cfg); }
 bool bz::needs_feature_instance(const bz_mixture *mix, const bz_swarm_config *cfg) { return ext_instance(mix, cfg); }
+bool bz::stages_channels(const bz_mixture *mix, int precision) { return precision == 64 ? mix->ch_smem64 : mix->ch_smem32; }
 
 extern "C" {
 

@@ -127,6 +127,9 @@ void set_last_error(const std::string &msg);
 int ctx_device(const bz_ctx *ctx);
 bz_status check_config(const bz_swarm_config *cfg);
 bool needs_feature_instance(const bz_mixture *mix, const bz_swarm_config *cfg);
+// Whether a launch of this mixture alone stages its channel tables in shared
+// memory (the CH_SMEM instance of the step kernel) at this precision.
+bool stages_channels(const bz_mixture *mix, int precision);
 
 // Host mixture compiler (mixture.cpp).  Returns BZ_OK or an error with *err.
 bz_status compile_mixture(const bz_gas *gases, int32_t n_gases, const bz_mixture_opts *opts,

@@ -5,7 +5,8 @@
 // arrival order.  A worker thread owns S launch slots (one non-blocking CUDA
 // stream each).  Whenever a slot is free it takes the request at the head of
 // the queue and, in arrival order, further queued requests of its step-kernel
-// class, looking past requests of other classes -- as many as fit the
+// class (precision, feature instance, field paths, channel tables staged or
+// not), looking past requests of other classes -- as many as fit the
 // device-memory admission budget, up to a group cap -- and runs them together
 // as one batched persistent launch on that slot (bz_create_batch/bz_launch_batch);
 // a spawn-mode request (an avalanche) runs alone as its own persistent
@@ -114,7 +115,12 @@ int kernel_key(const bz_mixture *mix, const bz_swarm_config &c, bool simulated)
                                   c.gas_temperature_K > 0.0)
                                : bz::needs_feature_instance(mix, &c);
     const bool bf = ext || c.b_T > 0.0;
-    return (c.precision == 64 ? 4 : 0) | (ext ? 2 : 0) | (bf ? 1 : 0);
+    // a batch stages channel tables only if every mixture does; one that would
+    // stage them alone then searches the cumulative table in L2 instead, which
+    // can choose differently where a draw falls within FP32 rounding of a
+    // channel boundary -- so such requests form a class of their own
+    const bool ch = !simulated && mix && bz::stages_channels(mix, c.precision);
+    return (c.precision == 64 ? 4 : 0) | (ext ? 2 : 0) | (bf ? 1 : 0) | (ch ? 8 : 0);
 }
 
 // Results of a finished launch (lock held): every request of the launch gets
