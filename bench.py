@@ -163,10 +163,9 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def profiled_traffic(name):
-    """DRAM bytes (read + write) of one step-kernel launch of a workload from
-    an ncu capture summarised in profiles/<name>.json, if the kernel sources
-    are still the ones that capture ran (else None)."""
+def _profile_record(name):
+    """profiles/<name>.json if the kernel sources are still the ones its ncu
+    capture ran (else None)."""
     import hashlib
     try:
         with open(os.path.join(ROOT, "profiles", name + ".json")) as f:
@@ -177,9 +176,32 @@ def profiled_traffic(name):
                 h.update(f.read())
     except (OSError, ValueError, KeyError):
         return None
-    if h.hexdigest() != rec["sources_sha256"]:
+    return rec if h.hexdigest() == rec["sources_sha256"] else None
+
+
+def profiled_traffic(name):
+    """DRAM bytes (read + write) of one step-kernel launch of a workload from
+    an ncu capture summarised in profiles/<name>.json, if the kernel sources
+    are still the ones that capture ran (else None)."""
+    rec = _profile_record(name)
+    if rec is None:
         return None
     return (rec["dram_bytes_read"] + rec["dram_bytes_write"]) * rec.get("scale_to_full", 1.0)
+
+
+def shared_memory_roofline(case, reals, kern_ms, sm_count, sm_mhz):
+    """Shared-memory pipe use of a launch: shared-memory wavefronts per real
+    collision from the ncu capture of the workload's reduced case
+    (profiles/batch_kernel_smem.json) times this launch's real collisions,
+    over the peak of one 128-byte wavefront per SM per clock."""
+    rec = _profile_record("batch_kernel_smem")
+    if rec is None or case not in rec["cases"]:
+        return None
+    per_real = rec["cases"][case]["wavefronts_per_real"]
+    achieved = per_real * reals * 128.0 / (kern_ms / 1e3)
+    peak = sm_count * 128.0 * sm_mhz * 1e6
+    return {"achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TB/s", "frac": achieved / peak,
+            "wavefronts_per_real": per_real, "source": rec["cases"][case]["command"]}
 
 
 # --------------------------------------------------------------------------
@@ -774,6 +796,8 @@ def run_ours(args):
     counts = counts_of(r["tallies"])
     out.update({"value": value, "ms_per_step": t_max / args.steps,
                 "roofline": roofline_of(kind, counts, r["kern_ms"], sm_count, sm_mhz, profiled_traffic(prof), kernel),
+                "shared_memory": shared_memory_roofline("batched" if args.workload == "batched" else "sweep",
+                                                        counts["reals"], r["kern_ms"], sm_count, sm_mhz),
                 "clocks": clk, "gpu_launches": 5 * args.steps,
                 "autotuned": {k: r["choice"].get(k) for k in ("window_c", "tiles_per_block", "blocks_per_sm", "cached")},
                 "trial_collisions_per_s": counts["trials"] * world / (t_max / 1e3),
@@ -805,6 +829,7 @@ def run_ours(args):
         sw["roofline"] = roofline_of("plain", sw_counts, sw["_kern_ms"], sm_count, sm_mhz,
                                      profiled_traffic("batch_kernel_traffic_argon_sweep"),
                                      "batch_kernel (lean FP32 build without field paths; 4 blocks/SM)")
+        sw["shared_memory"] = shared_memory_roofline("sweep", sw_counts["reals"], sw["_kern_ms"], sm_count, sm_mhz)
         if "oracle" in args.legs:
             sw["drift_velocity_vs_oracle"] = sweep_vs_oracle(sw["_tallies"], sw["_specs"], args.oracle_electrons)
             out["max_rel_err_W_vs_oracle"] = sw["drift_velocity_vs_oracle"]["max_abs_rel_W"]
