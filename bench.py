@@ -78,6 +78,8 @@ def parse():
                     help="oracle electrons per E/N point of the sweep's drift-velocity check")
     ap.add_argument("--serve-rates", default="250,400,600,800,2000", help="Poisson arrival rates [req/s]")
     ap.add_argument("--serve-seconds", type=float, default=5.0, help="arrival window of each serving run")
+    ap.add_argument("--serve-rates-i1000", default="25,50,75,100",
+                    help="Poisson arrival rates [req/s] of the serving sweep at I = 1000 real collisions per request")
     ap.add_argument("--serve-slots", type=int, default=3, help="launch slots (streams) of the serving loop")
     ap.add_argument("--serve-max-group", type=int, default=512, help="requests per launch at most")
     ap.add_argument("--avalanche-cap", type=int, default=100_000,
@@ -855,6 +857,12 @@ def run_ours(args):
                              avalanche_frac=args.avalanche_frac, avalanche_cap=args.avalanche_cap,
                              max_group=args.serve_max_group)
         out["serving"] = serve
+        # the same loop at the workload's own I = 1000 (ten times the work per request)
+        rates_long = [float(x) for x in args.serve_rates_i1000.split(",") if x]
+        if rates_long:
+            out["serving_I1000"] = serving_runs(ctx, rates_long, args.serve_seconds, collisions=1000,
+                                                streams=args.serve_slots, avalanche_frac=args.avalanche_frac,
+                                                avalanche_cap=args.avalanche_cap, max_group=args.serve_max_group)
         kept = [x for x in serve if x["served_fraction"] is not None and x["served_fraction"] >= 0.9]
         top = max(kept, key=lambda x: x["rate_req_s"]) if kept else None
         out["p99_swarm_latency_ms"] = top["p99_ms"] if top else None
