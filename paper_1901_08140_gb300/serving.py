@@ -29,6 +29,7 @@ class Request:
     cfg: object                     # bz.bz_swarm_config
     arrival: float = 0.0            # seconds after the start of the run
     n_electrons: int = 0
+    submitted: Optional[float] = None  # when the loop handed it to the server (>= arrival)
     admitted: Optional[float] = None
     done: Optional[float] = None
     tallies: Optional[Dict[str, float]] = None
@@ -93,8 +94,10 @@ class Server:
 
     def run(self, requests: Sequence[Request], realtime: bool = True, poll_sleep: float = 2e-5) -> List[Request]:
         """Submits `requests` at their arrival times (all at once when
-        realtime is False) and returns them completed; their admission and
-        completion times are the server's, counted from their arrival."""
+        realtime is False) and returns them completed.  A request's admission
+        and completion are the server's times after its submission, added to
+        the moment this loop submitted it, so a latency (completion minus
+        arrival) includes any delay of the loop in submitting."""
         reqs = sorted(requests, key=lambda r: (r.arrival, r.rid))
         if not reqs:
             return []
@@ -107,6 +110,7 @@ class Server:
             while i < len(reqs) and (not realtime or reqs[i].arrival <= now):
                 r = reqs[i]
                 waiting[self.submit(r.mixture, r.cfg)] = r
+                r.submitted = max(time.perf_counter() - t0, r.arrival) if realtime else r.arrival
                 i += 1
             for rid in list(waiting):
                 res = self.poll(rid)
@@ -114,10 +118,10 @@ class Server:
                     continue
                 st, t, info = res
                 r = waiting.pop(rid)
-                # latency on the server's clock: from submission (at arrival) to completion
+                # the server's clock from submission on, this loop's before
                 r.status, r.tallies = int(st), t
-                r.admitted = r.arrival + (info["t_admit"] - info["t_submit"])
-                r.done = r.arrival + (info["t_done"] - info["t_submit"])
+                r.admitted = r.submitted + (info["t_admit"] - info["t_submit"])
+                r.done = r.submitted + (info["t_done"] - info["t_submit"])
                 r.launch, r.group_size = int(info["launch"]), int(info["group_size"])
                 done.append(r)
             if waiting and poll_sleep > 0:
@@ -151,6 +155,8 @@ def latency_summary(done: Sequence[Request], duration: Optional[float] = None) -
     lat = np.array([r.latency for r in done])
     reals = sum(int(r.tallies["n_real"]) for r in done if r.tallies)
     span = duration if duration is not None else max(r.done for r in done) - min(r.arrival for r in done)
+    lag = np.array([(r.submitted if r.submitted is not None else r.arrival) - r.arrival for r in done])
     return {"requests": len(done), "p50_ms": float(np.percentile(lat, 50) * 1e3),
             "p99_ms": float(np.percentile(lat, 99) * 1e3), "mean_ms": float(lat.mean() * 1e3),
-            "real_collisions_per_s": reals / span if span > 0 else math.nan, "span_s": span}
+            "real_collisions_per_s": reals / span if span > 0 else math.nan, "span_s": span,
+            "submit_lag_p99_ms": float(np.percentile(lag, 99) * 1e3), "submit_lag_max_ms": float(lag.max() * 1e3)}
