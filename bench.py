@@ -418,7 +418,8 @@ def e2e_run(ctx, stream, specs, rank, choice, steps):
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     return {"value": reals / dt, "unit": UNIT, "h2d_bytes_per_step": h2d // steps, "d2h_bytes_per_step": d2h // steps,
-            "steps": steps, "includes": "mixture compilation and table upload, batch set-up, launch, tallies read",
+            "steps": steps, "includes": "mixture compilation and table upload (from pinned host staging), batch set-up, launch, "
+                        "tallies read (into pinned host memory)",
             "pipelined": "the next step's mixtures are compiled and uploaded and its batch set up while the "
                          "current step's launch runs; the first step's set-up is timed alone"}
 

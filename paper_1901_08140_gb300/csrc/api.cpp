@@ -237,6 +237,30 @@ void pinned_block_release(bz_ctx *c, void *p, size_t cap)
     c->pin_blocks.emplace_back(cap, p);
 }
 
+// Host staging in page-locked memory from the context's pool, so that uploads
+// start from pinned memory (one DMA) rather than from pageable vectors.  The
+// block returns to the pool when the stage is destroyed: declare the stage
+// before the SyncCopies whose copies read it, so that those copies are waited
+// for first.
+struct PinnedStage {
+    bz_ctx *c;
+    uint8_t *p = nullptr;
+    size_t cap = 0, used = 0;
+    PinnedStage(bz_ctx *ctx, size_t bytes) : c(ctx) { p = (uint8_t *)pinned_block(ctx, bytes, &cap); }
+    PinnedStage(const PinnedStage &) = delete;
+    PinnedStage &operator=(const PinnedStage &) = delete;
+    ~PinnedStage() { pinned_block_release(c, p, cap); }
+    // the pinned copy of `bytes` at `src`, or `src` itself if the pool had no room
+    const void *put(const void *src, size_t bytes)
+    {
+        if (!p || used + bytes > cap) return src;
+        uint8_t *d = p + used;
+        memcpy(d, src, bytes);
+        used = (used + bytes + 15) & ~(size_t)15;
+        return d;
+    }
+};
+
 void ctx_release(bz_ctx *c)
 {
     if (c->refs.fetch_sub(1) == 1) delete c;
@@ -441,6 +465,7 @@ bz_status bz_create_gas_mixture(bz_ctx *ctx, const bz_gas *gases, int32_t n_gase
     cudaSetDevice(ctx->device);
     m->bytes32 = m->cm.blob32.size();
     m->bytes64 = m->cm.blob64.size();
+    PinnedStage stage(ctx, m->bytes32 + m->bytes64 + 32);
     SyncCopies up;
     // the library's own pool allocates in the order of the copy stream; a
     // caller's allocator takes its usual stream (the tables are freed only
@@ -455,8 +480,8 @@ bz_status bz_create_gas_mixture(bz_ctx *ctx, const bz_gas *gases, int32_t n_gase
         delete m;
         return fail(BZ_ENOMEM, "device allocation of the mixture tables");
     }
-    up.add(m->blob32, m->cm.blob32.data(), m->bytes32, cudaMemcpyHostToDevice);
-    up.add(m->blob64, m->cm.blob64.data(), m->bytes64, cudaMemcpyHostToDevice);
+    up.add(m->blob32, stage.put(m->cm.blob32.data(), m->bytes32), m->bytes32, cudaMemcpyHostToDevice);
+    up.add(m->blob64, stage.put(m->cm.blob64.data(), m->bytes64), m->bytes64, cudaMemcpyHostToDevice);
     cudaError_t e = up.wait();
     if (e != cudaSuccess) {
         dev_free(ctx, m->blob32, m->bytes32, 0);
@@ -950,7 +975,9 @@ bz_status bz_create_batch(bz_ctx *ctx, int32_t n, const bz_mixture *const *mixtu
         o_gs[i] = take(sizeof(double) * (bz::kGroups * (bz::kQ1 + bz::kQ2) + 8));
     }
     b->bytes = off;
-    // the set-up copies; the library's own pool allocates in their stream's order
+    // the set-up copies, from pinned staging; the library's own pool allocates
+    // in their stream's order
+    PinnedStage stage(ctx, sizeof(bz::RunArgs) * n + sizeof(uint4) * tiles.size() + sizeof(bz::TallyArgs) * n + 48);
     SyncCopies up;
     b->mem = (uint8_t *)dev_alloc(ctx, b->bytes, ctx->custom_alloc ? (cudaStream_t)0 : up.s);
     if (!b->mem) {
@@ -999,9 +1026,11 @@ bz_status bz_create_batch(bz_ctx *ctx, int32_t n, const bz_mixture *const *mixtu
         t.out = b->tallies_dev + i;
     }
     b->targs_host = targs;
-    up.add(b->desc, desc.data(), sizeof(bz::RunArgs) * n, cudaMemcpyHostToDevice);
-    up.add(b->tiles, tiles.data(), sizeof(uint4) * tiles.size(), cudaMemcpyHostToDevice);
-    up.add(b->targs, targs.data(), sizeof(bz::TallyArgs) * n, cudaMemcpyHostToDevice);
+    up.add(b->desc, stage.put(desc.data(), sizeof(bz::RunArgs) * n), sizeof(bz::RunArgs) * n, cudaMemcpyHostToDevice);
+    up.add(b->tiles, stage.put(tiles.data(), sizeof(uint4) * tiles.size()), sizeof(uint4) * tiles.size(),
+           cudaMemcpyHostToDevice);
+    up.add(b->targs, stage.put(targs.data(), sizeof(bz::TallyArgs) * n), sizeof(bz::TallyArgs) * n,
+           cudaMemcpyHostToDevice);
     e = up.wait();
     if (e == cudaSuccess) {
         b->tallies_host = (bz_tallies *)pinned_block(ctx, sizeof(bz_tallies) * n, &b->tallies_cap);
