@@ -240,12 +240,21 @@ def sweep_name(args):
             "frequency, B = 0" + (f" (point {args.only_point} only)" if args.only_point >= 0 else ""))
 
 
-def tuned(ctx, mixes, cfgs, args):
-    """The autotuner's choice for this batch, or its default options with --no-tune."""
+def tuned(ctx, mixes, cfgs, args, shared=True):
+    """The autotuner's choice for this batch, or its default options with
+    --no-tune.  With several ranks and shared=True, rank 0 tunes and every
+    rank takes its choice (the legs that follow must agree across ranks)."""
     from paper_1901_08140_gb300 import autotune
     if args.no_tune:
         return dict(autotune.DEFAULT, cached=None)
-    return autotune.tune(ctx, mixes, cfgs)
+    import torch.distributed as dist
+    multi = shared and dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1
+    choice = autotune.tune(ctx, mixes, cfgs) if not multi or dist.get_rank() == 0 else None
+    if multi:
+        box = [choice]
+        dist.broadcast_object_list(box, src=0)
+        choice = box[0]
+    return choice
 
 
 def workload_config(args):
@@ -397,6 +406,8 @@ def e2e_run(ctx, stream, specs, rank, choice, steps):
                           choice)
     reals, h2d, d2h = 0, 0, 0
     torch.cuda.synchronize()
+    if torch.distributed.is_available() and torch.distributed.is_initialized():
+        torch.distributed.barrier()
     t0 = time.perf_counter()
     with cf.ThreadPoolExecutor(max_workers=16) as ex:
         def prepare():
@@ -417,7 +428,15 @@ def e2e_run(ctx, stream, specs, rank, choice, steps):
                 m.close()
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
-    return {"value": reals / dt, "unit": UNIT, "h2d_bytes_per_step": h2d // steps, "d2h_bytes_per_step": d2h // steps,
+    # whole job: every rank's real collisions over the slowest rank's time,
+    # every rank's bytes
+    from paper_1901_08140_gb300 import sharding
+    t_max, reals = sharding.reduce_step(dt * 1e3, reals)
+    _, h2d = sharding.reduce_step(0.0, h2d)
+    _, d2h = sharding.reduce_step(0.0, d2h)
+    dt = t_max / 1e3
+    return {"value": reals / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d) // steps,
+            "d2h_bytes_per_step": int(d2h) // steps,
             "steps": steps, "includes": "mixture compilation and table upload (from pinned host staging), batch set-up, launch, "
                         "tallies read (into pinned host memory)",
             "pipelined": "the next step's mixtures are compiled and uploaded and its batch set up while the "
@@ -431,7 +450,7 @@ def sweep_run(ctx, stream, flush, world, dev, args, rank):
     specs = sweep_specs(args)
     mix = bz.Mixture(ctx, specs[0].gases)
     cfgs = [bz.config_from_spec(s, trial_mode=bz.BZ_TRIAL_WINDOW, id_offset=rank << 32) for s in specs]
-    choice = tuned(ctx, [mix] * len(cfgs), cfgs, args)
+    choice = tuned(ctx, [mix] * len(cfgs), cfgs, args, shared=False)  # rank 0 alone
     tuned_cfgs = autotune.apply(cfgs, choice)
     batch = autotune.make_batch(ctx, [mix] * len(cfgs), tuned_cfgs, choice)
     for _ in range(2):
@@ -827,7 +846,7 @@ def run_ours(args):
     if rank == 0 and args.workload == "batched" and "oracle" in args.legs and args.scale == 1:
         out["batched_vs_oracle"] = batched_vs_oracle(r["tallies"][-len(specs):], specs)
     if rank == 0 and args.workload == "batched" and ("sweep" in args.legs or "oracle" in args.legs):
-        sw = sweep_run(ctx, stream, flush, world, dev, args, rank)
+        sw = sweep_run(ctx, stream, flush, 1, dev, args, rank)  # rank 0 alone: no barrier
         sw_counts = counts_of(sw["_tallies"])
         sw["roofline"] = roofline_of("plain", sw_counts, sw["_kern_ms"], sm_count, sm_mhz,
                                      profiled_traffic("batch_kernel_traffic_argon_sweep"),
