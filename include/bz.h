@@ -361,10 +361,11 @@ typedef struct {
     int32_t reserved;
 } bz_batch_opts;
 
-/* Prepares a batch of n swarms: mixtures[i] and cfgs[i] as for
- * bz_run_swarm (all the same precision).  Allocates the device state of all
- * swarms once.  Errors: BZ_EINVAL, BZ_EBUDGET (tables too large for shared
- * memory), BZ_ENOMEM, BZ_ECUDA. */
+/* Prepares a batch of n swarms (1 <= n <= 65535): mixtures[i] and cfgs[i]
+ * as for bz_run_swarm (all the same precision, no spawn mode; either every
+ * swarm or none needs the feature instance).  Allocates the device state of
+ * all swarms once.  Errors: BZ_EINVAL, BZ_EBUDGET (tables too large for
+ * shared memory), BZ_ENOMEM, BZ_ECUDA. */
 bz_status bz_create_batch(bz_ctx *ctx, int32_t n, const bz_mixture *const *mixtures, const bz_swarm_config *cfgs,
                           const bz_batch_opts *opts, bz_batch **out);
 /* Runs the batch on `stream` (asynchronous); may be called again after the

@@ -890,6 +890,8 @@ bz_status bz_create_batch(bz_ctx *ctx, int32_t n, const bz_mixture *const *mixtu
     if (!ctx || !out || !mixtures || !cfgs) return fail(BZ_EINVAL, "null argument");
     *out = nullptr;
     if (n < 1) return fail(BZ_EINVAL, "a batch needs at least one swarm");
+    // the tally kernels take one grid row per swarm
+    if (n > 65535) return fail(BZ_EINVAL, "a batch holds at most 65535 swarms");
     const int precision = cfgs[0].precision;
     for (int i = 0; i < n; ++i) {
         bz_status st = validate_config(&cfgs[i]);

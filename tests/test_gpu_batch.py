@@ -131,6 +131,11 @@ def test_batch_rejects_mixed_precision(ctx):
     with pytest.raises(bz.BzError) as ei:
         bz.Batch(ctx, [m for m, _ in items], cfgs)
     assert ei.value.status == bz.BZ_EINVAL
+    # one tally grid row per swarm: at most 65535 swarms
+    m, c = items[0]
+    with pytest.raises(bz.BzError) as ei:
+        bz.Batch(ctx, [m] * 65536, [c] * 65536)
+    assert ei.value.status == bz.BZ_EINVAL
 
 
 def test_set_up_does_not_wait_for_a_running_launch(ctx):
