@@ -455,8 +455,8 @@ typedef struct bz_server bz_server;
 
 typedef struct {
     double memory_budget_bytes; /* device bytes running requests may hold at once; <= 0: 60e9 */
-    int32_t n_slots;            /* concurrent launches; <= 0: 3 */
-    int32_t max_group;          /* requests per batched launch; <= 0: 512 */
+    int32_t n_slots;            /* concurrent launches, at most 64; <= 0: 3 */
+    int32_t max_group;          /* requests per batched launch, at most 65535; <= 0: 512 */
     int32_t simulate;           /* 0: run on the context's GPU.  n > 0: host-only scheduling test -- no
                                    device is touched, ctx and mixtures may be NULL, a launch ends after
                                    n polls of the worker and reports n_particles and n_real only */

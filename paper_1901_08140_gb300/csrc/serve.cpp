@@ -337,6 +337,8 @@ bz_status bz_server_create(bz_ctx *ctx, const bz_server_opts *opts, bz_server **
     if (!(o.memory_budget_bytes > 0.0)) o.memory_budget_bytes = 60e9;
     if (o.n_slots <= 0) o.n_slots = 3;
     if (o.max_group <= 0) o.max_group = 512;
+    if (o.max_group > 65535) return fail_msg(BZ_EINVAL, "max_group is at most 65535 (a batch's limit)");
+    if (o.n_slots > 64) return fail_msg(BZ_EINVAL, "n_slots is at most 64");
     if (o.simulate < 0) return fail_msg(BZ_EINVAL, "simulate must be >= 0");
     if (o.simulate == 0 && !ctx) return fail_msg(BZ_EINVAL, "a server on the GPU needs a context");
     bz_server *s = new (std::nothrow) bz_server();

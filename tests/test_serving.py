@@ -147,6 +147,15 @@ def test_admission_overflow_is_rejected_at_submission(L):
     srv.close()
 
 
+def test_server_options_out_of_range_are_rejected(L):
+    for kw in (dict(max_group=70000), dict(n_slots=65), dict(simulate=-1)):
+        opts = dict(memory_budget=1e9, n_slots=2, max_group=8, simulate=5)
+        opts.update(kw)
+        with pytest.raises(bz.BzError) as ei:
+            S.Server(None, **opts)
+        assert ei.value.status == bz.BZ_EINVAL, kw
+
+
 def test_destroy_cancels_what_is_queued(L):
     srv = S.Server(None, memory_budget=1e12, n_slots=1, max_group=1, simulate=500)
     for _ in range(5):
