@@ -558,8 +558,10 @@ bz_status bz_reduce_tallies_noalloc(const bz_particle_arrays *in, uint64_t n, ui
  * (id, steps[i], 0), flies, and takes the fail / null / real decision.
  * Outputs: state_out_dev[8 n] the state after the step; decision_dev[n] the
  * global channel index, -1 null, -2 fail; eps_dev[2 n] the energy before and
- * after the collision.  Uses cfg's fields, precision, seed and trial mode.
- * Asynchronous on `stream`. */
+ * after the collision.  Uses cfg's fields, precision, seed and trial mode
+ * (cfg is validated as for bz_run_swarm).  Asynchronous on `stream`.
+ * Errors: BZ_EINVAL (null pointer, n < 0, an invalid configuration, the
+ * VARIABLE or BINNED trial frequency), BZ_EBUDGET, BZ_ENOMEM, BZ_ECUDA. */
 bz_status bz_step_replay(bz_ctx *ctx, const bz_mixture *mix, const bz_swarm_config *cfg, int64_t n,
                          const double *state_in_dev, const uint64_t *ids_dev, const uint32_t *steps_dev,
                          double *state_out_dev, int32_t *decision_dev, double *eps_dev, void *stream);

@@ -1272,7 +1272,8 @@ bz_status bz_step_replay(bz_ctx *ctx, const bz_mixture *mix, const bz_swarm_conf
     if (n == 0) return BZ_OK;
     if (!state_in_dev || !ids_dev || !steps_dev || !state_out_dev || !decision_dev || !eps_dev)
         return fail(BZ_EINVAL, "null buffer");
-    if (cfg->precision != 32 && cfg->precision != 64) return fail(BZ_EINVAL, "precision must be 32 or 64");
+    bz_status vs = validate_config(cfg);
+    if (vs != BZ_OK) return vs;
     if (adaptive(cfg)) return fail(BZ_EINVAL, "single steps replay the lazy, fixed or windowed trial frequency");
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
