@@ -34,7 +34,7 @@
 extern "C" {
 #endif
 
-#define BZ_ABI_VERSION 6
+#define BZ_ABI_VERSION 7
 
 typedef enum {
     BZ_OK = 0,
@@ -358,7 +358,10 @@ typedef struct {
                                  runs out); <= 0: about 16 tiles per resident block */
     int32_t blocks_per_sm;    /* <= 0: as many as fit */
     int32_t use_graph;        /* 1: CUDA graph (default when opts is NULL), 0: plain launches */
-    int32_t reserved;
+    int32_t channels_in_l2;   /* table-staging policy: 1 = every mixture's channels are chosen from its cumulative
+                                 table in global memory, even where its channel coefficients would fit shared
+                                 memory (smaller staged prefix; results then match runs alone to FP32 rounding
+                                 of channel boundaries); 0 = stage them where every mixture's fit */
 } bz_batch_opts;
 
 /* Prepares a batch of n swarms (1 <= n <= 65535): mixtures[i] and cfgs[i]

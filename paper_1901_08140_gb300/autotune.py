@@ -4,8 +4,11 @@ Picks, for a batch of swarms, the launch options that maximise real
 collisions per second of device time: the trial-frequency window length
 (``window_c``, windowed mode only; any value samples the same process),
 the tile size, expressed as tiles per resident block so that the choice
-carries over between a copy of the batch and the batch itself, and the
-resident blocks per SM.  It times candidates by coordinate descent on a
+carries over between a copy of the batch and the batch itself (it sets how
+many electrons each lane runs, one after another, per tile), the resident
+blocks per SM, and the table-staging policy where every mixture could stage
+its channel tables (staged, or all channel choices from the cumulative
+tables in global memory).  It times candidates by coordinate descent on a
 reduced copy of the batch -- every swarm keeps its mixture, fields and real
 collisions per electron but runs half of its electrons, so an electron's
 history looks like the full batch's -- checks the winner against the
@@ -29,7 +32,7 @@ CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_autotune_cach
 # window_c 1.5 and 16 tiles per block: the fastest point of a full-size sweep of
 # the 256-swarm workload on GB300 (window_c 1.0 / 1.5 / 2.0 / 3.0: 2.94 / 2.90 /
 # 2.99 / 3.18 s; 8 / 16 / 32 tiles per block: 2.98 / 2.90 / 2.91 s)
-DEFAULT = {"window_c": 1.5, "tiles_per_block": 16, "blocks_per_sm": 0}
+DEFAULT = {"window_c": 1.5, "tiles_per_block": 16, "blocks_per_sm": 0, "channels_in_l2": False}
 WINDOW_C = [1.0, 1.5, 2.0, 3.0]
 TILES_PER_BLOCK = [4, 8, 16, 32]
 BLOCKS = [0, 2]
@@ -87,7 +90,8 @@ def make_batch(ctx, mixtures, cfgs, choice, use_graph: bool = True, sm_count: in
     """A batch launched with the chosen options (cfgs already carry the
     chosen window length, see apply)."""
     return bz.Batch(ctx, mixtures, cfgs, tile_particles=tile_size(cfgs, choice, sm_count),
-                    blocks_per_sm=int(choice.get("blocks_per_sm", 0)), use_graph=use_graph)
+                    blocks_per_sm=int(choice.get("blocks_per_sm", 0)), use_graph=use_graph,
+                    channels_in_l2=bool(choice.get("channels_in_l2", False)))
 
 
 def _measure(ctx, mixtures, cfgs, choice, sm_count, repeats=2) -> float:
@@ -118,14 +122,16 @@ def tune(ctx, mixtures: Sequence, cfgs: Sequence[bz.bz_swarm_config], scale: flo
     sm_count = torch.cuda.get_device_properties(ctx.device).multi_processor_count
     key = f"{gpu_name}|{signature(cfgs)}"
     cache = load_cache(cache_path) if use_cache else {}
-    if key in cache and "tiles_per_block" in cache[key]:
+    if key in cache and "channels_in_l2" in cache[key]:
         return dict(cache[key], cached=True)
     small = [_copy_cfg(c, n_electrons=max(256, int(c.n_electrons * scale))) for c in cfgs]
     best = dict(DEFAULT)
     best_rate = _measure(ctx, mixtures, small, best, sm_count)
     windowed = any(c.trial_mode == bz.BZ_TRIAL_WINDOW for c in cfgs)
+    # the staging policy matters only where every mixture would stage its channel tables
+    staged = all(m.info.get("channels_in_smem") for m in mixtures) and all(int(c.precision) == 32 for c in cfgs)
     for name, values in (("window_c", WINDOW_C if windowed else []), ("tiles_per_block", TILES_PER_BLOCK),
-                         ("blocks_per_sm", BLOCKS)):
+                         ("blocks_per_sm", BLOCKS), ("channels_in_l2", [False, True] if staged else [])):
         for v in values:
             if v == best[name]:
                 continue

@@ -929,6 +929,8 @@ bz_status bz_create_batch(bz_ctx *ctx, int32_t n, const bz_mixture *const *mixtu
         }
         b->ch_smem = b->ch_smem && ch;
     }
+    // staging policy: every mixture's channel choice from its cumulative table in global memory
+    if (opts && opts->channels_in_l2) b->ch_smem = false;
     b->smem = 0;
     for (int i = 0; i < n; ++i) {
         desc[i].stage_bytes = b->ch_smem ? desc[i].lay.stage_all : desc[i].lay.stage_tables;

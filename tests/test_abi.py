@@ -40,7 +40,7 @@ def test_every_declared_symbol_is_exported(L):
     missing = [n for n in names if n not in exported]
     assert not missing, missing
     assert set(names) == set(bz.SIGNATURES)
-    assert L.bz_abi_version() == 6
+    assert L.bz_abi_version() == 7
 
 
 def test_struct_layouts_match_the_header(tmp_path):

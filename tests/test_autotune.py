@@ -46,6 +46,7 @@ def test_tune_a_small_batch(tmp_path, L):
     path = str(tmp_path / "c.json")
     choice = autotune.tune(ctx, [mix] * 4, cfgs, cache_path=path)
     assert choice["cached"] is False and choice["window_c"] in autotune.WINDOW_C
+    assert mix.info["channels_in_smem"] == 1 and choice["channels_in_l2"] in (False, True)
     again = autotune.tune(ctx, [mix] * 4, cfgs, cache_path=path)
     assert again["cached"] is True and again["window_c"] == choice["window_c"]
     b = autotune.make_batch(ctx, [mix] * 4, autotune.apply(cfgs, choice), choice)

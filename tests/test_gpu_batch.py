@@ -110,6 +110,35 @@ def test_mixed_staging_batch(ctx):
     batch.close()
 
 
+def test_channel_tables_in_l2_policy(ctx):
+    """The staging policy that keeps every channel table in global memory
+    (the cumulative-table search) runs the same swarms: equal counts,
+    swarm statistics within their errors, and equal to a batch whose
+    mixtures cannot stage their channels bit for bit."""
+    items = [(m, c) for m, c in _items(ctx) if c.b_T == 0]
+    staged = [(m, c) for m, c in items if m.info["channels_in_smem"]]
+    a = bz.Batch(ctx, [m for m, _ in staged], [c for _, c in staged], tile_particles=512)
+    b = bz.Batch(ctx, [m for m, _ in staged], [c for _, c in staged], tile_particles=512, channels_in_l2=True)
+    a.launch()
+    b.launch()
+    ta, tb = a.tallies(), b.tallies()
+    for i, (_, cfg) in enumerate(staged):
+        assert ta[i]["n_real"] == tb[i]["n_real"] and ta[i]["n_particles"] == tb[i]["n_particles"]
+        if cfg.n_electrons > 100:
+            for k in ("W", "eps"):
+                assert abs(ta[i][k] - tb[i][k]) <= 3 * math.hypot(ta[i][k + "_se"], tb[i][k + "_se"]), (i, k)
+    a.close()
+    b.close()
+    # a mixed batch already searches in global memory: the policy changes nothing there
+    c = bz.Batch(ctx, [m for m, _ in items], [c for _, c in items], tile_particles=512)
+    d = bz.Batch(ctx, [m for m, _ in items], [c for _, c in items], tile_particles=512, channels_in_l2=True)
+    c.launch()
+    d.launch()
+    assert [t["W"] for t in c.tallies()] == [t["W"] for t in d.tallies()]
+    c.close()
+    d.close()
+
+
 def test_batch_relaunch_is_reproducible(ctx):
     items = _items(ctx)
     batch = bz.Batch(ctx, [m for m, _ in items], [c for _, c in items])
