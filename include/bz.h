@@ -34,7 +34,7 @@
 extern "C" {
 #endif
 
-#define BZ_ABI_VERSION 7
+#define BZ_ABI_VERSION 8
 
 typedef enum {
     BZ_OK = 0,
@@ -203,7 +203,8 @@ typedef struct {
     uint64_t max_trials;      /* per particle, 0: 2^31 - 1 */
     uint64_t seed;            /* Philox key of the swarm */
     uint64_t id_offset;       /* first particle id: ids id_offset .. id_offset + N - 1 */
-    int32_t block_threads;    /* launch shape, 0: auto */
+    int32_t block_threads;    /* threads per block: 0 or 256; 128, 384 or 768 for FP32 swarms without spawn
+                                 mode whose mixture and trial mode run the lean step kernel (same results) */
     int32_t blocks_per_sm;    /* 0: auto (occupancy) */
     double window_c;          /* WINDOW mode: window = window_c / nu of the current energy bin; 0: 2 */
     int32_t spawn;            /* 1: ionizations create electrons, attachments remove them (Sec. 2) */
@@ -362,6 +363,10 @@ typedef struct {
                                  table in global memory, even where its channel coefficients would fit shared
                                  memory (smaller staged prefix; results then match runs alone to FP32 rounding
                                  of channel boundaries); 0 = stage them where every mixture's fit */
+    int32_t block_threads;    /* threads per block: 0 or 256; 128, 384 or 768 for FP32 batches of the lean step
+                                 kernel (no VARIABLE / BINNED trial frequency, no xi-form gas), at the register cap
+                                 of the 256-thread build (6 x 128, 2 x 384 or 1 x 768 threads per SM).  Results do
+                                 not depend on it; other values: BZ_EINVAL */
 } bz_batch_opts;
 
 /* Prepares a batch of n swarms (1 <= n <= 65535): mixtures[i] and cfgs[i]

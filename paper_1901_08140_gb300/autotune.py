@@ -6,9 +6,11 @@ collisions per second of device time: the trial-frequency window length
 the tile size, expressed as tiles per resident block so that the choice
 carries over between a copy of the batch and the batch itself (it sets how
 many electrons each lane runs, one after another, per tile), the resident
-blocks per SM, and the table-staging policy where every mixture could stage
-its channel tables (staged, or all channel choices from the cumulative
-tables in global memory).  It times candidates by coordinate descent on a
+blocks per SM, the threads per block (256, or 128 / 384 / 768 at the same
+register cap where the batch runs the lean FP32 kernel), and the
+table-staging policy where every mixture could stage its channel tables
+(staged, or all channel choices from the cumulative tables in global
+memory).  It times candidates by coordinate descent on a
 reduced copy of the batch -- every swarm keeps its mixture, fields and real
 collisions per electron but runs half of its electrons, so an electron's
 history looks like the full batch's -- checks the winner against the
@@ -32,12 +34,13 @@ CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_autotune_cach
 # window_c 1.5 and 16 tiles per block: the fastest point of a full-size sweep of
 # the 256-swarm workload on GB300 (window_c 1.0 / 1.5 / 2.0 / 3.0: 2.94 / 2.90 /
 # 2.99 / 3.18 s; 8 / 16 / 32 tiles per block: 2.98 / 2.90 / 2.91 s)
-DEFAULT = {"window_c": 1.5, "tiles_per_block": 16, "blocks_per_sm": 0, "channels_in_l2": False}
+DEFAULT = {"window_c": 1.5, "tiles_per_block": 16, "blocks_per_sm": 0, "channels_in_l2": False, "block_threads": 256}
 WINDOW_C = [1.0, 1.5, 2.0, 3.0]
 TILES_PER_BLOCK = [4, 8, 16, 32]
 BLOCKS = [0, 2]
+BLOCK_THREADS = [256, 128, 384, 768]
 SM_COUNT = 152
-RESIDENT_BLOCKS = 3   # the FP32 step kernel's blocks per SM when its tables fit
+RESIDENT_BLOCKS = 3   # the FP32 step kernel's blocks of 256 threads per SM when its tables fit
 
 
 def signature(cfgs: Sequence[bz.bz_swarm_config]) -> str:
@@ -81,7 +84,7 @@ def tile_size(cfgs: Sequence[bz.bz_swarm_config], choice: dict, sm_count: int = 
     """Electrons per tile for `tiles_per_block` tiles per resident block
     (rounded up to 256, at least 256)."""
     total = sum(int(c.n_electrons) for c in cfgs)
-    bps = int(choice.get("blocks_per_sm", 0)) or RESIDENT_BLOCKS
+    bps = int(choice.get("blocks_per_sm", 0)) or RESIDENT_BLOCKS * 256 // int(choice.get("block_threads", 256))
     t = math.ceil(total / (sm_count * bps * int(choice.get("tiles_per_block", 16))))
     return max(256, (t + 255) // 256 * 256)
 
@@ -91,7 +94,8 @@ def make_batch(ctx, mixtures, cfgs, choice, use_graph: bool = True, sm_count: in
     chosen window length, see apply)."""
     return bz.Batch(ctx, mixtures, cfgs, tile_particles=tile_size(cfgs, choice, sm_count),
                     blocks_per_sm=int(choice.get("blocks_per_sm", 0)), use_graph=use_graph,
-                    channels_in_l2=bool(choice.get("channels_in_l2", False)))
+                    channels_in_l2=bool(choice.get("channels_in_l2", False)),
+                    block_threads=int(choice.get("block_threads", 256)))
 
 
 def _measure(ctx, mixtures, cfgs, choice, sm_count, repeats=2) -> float:
@@ -122,7 +126,7 @@ def tune(ctx, mixtures: Sequence, cfgs: Sequence[bz.bz_swarm_config], scale: flo
     sm_count = torch.cuda.get_device_properties(ctx.device).multi_processor_count
     key = f"{gpu_name}|{signature(cfgs)}"
     cache = load_cache(cache_path) if use_cache else {}
-    if key in cache and "channels_in_l2" in cache[key]:
+    if key in cache and "block_threads" in cache[key]:
         return dict(cache[key], cached=True)
     small = [_copy_cfg(c, n_electrons=max(256, int(c.n_electrons * scale))) for c in cfgs]
     best = dict(DEFAULT)
@@ -130,8 +134,13 @@ def tune(ctx, mixtures: Sequence, cfgs: Sequence[bz.bz_swarm_config], scale: flo
     windowed = any(c.trial_mode == bz.BZ_TRIAL_WINDOW for c in cfgs)
     # the staging policy matters only where every mixture would stage its channel tables
     staged = all(m.info.get("channels_in_smem") for m in mixtures) and all(int(c.precision) == 32 for c in cfgs)
+    # other block sizes are built for the lean FP32 kernel only
+    lean = (all(int(c.precision) == 32 for c in cfgs)
+            and all(int(c.trial_mode) not in (bz.BZ_TRIAL_VARIABLE, bz.BZ_TRIAL_BINNED) for c in cfgs)
+            and not any(m.info.get("n_xi_gases") for m in mixtures))
     for name, values in (("window_c", WINDOW_C if windowed else []), ("tiles_per_block", TILES_PER_BLOCK),
-                         ("blocks_per_sm", BLOCKS), ("channels_in_l2", [False, True] if staged else [])):
+                         ("blocks_per_sm", BLOCKS), ("channels_in_l2", [False, True] if staged else []),
+                         ("block_threads", BLOCK_THREADS if lean else [])):
         for v in values:
             if v == best[name]:
                 continue

@@ -109,7 +109,7 @@ BZ_NOALLOC_MAX_PARTICLES = 32768 * 512
 
 class bz_batch_opts(C.Structure):
     _fields_ = [("tile_particles", C.c_int32), ("blocks_per_sm", C.c_int32), ("use_graph", C.c_int32),
-                ("channels_in_l2", C.c_int32)]
+                ("channels_in_l2", C.c_int32), ("block_threads", C.c_int32)]
 
 
 class bz_merge_info(C.Structure):
@@ -529,11 +529,12 @@ class Batch:
 
     def __init__(self, ctx: Context, mixtures: Sequence["Mixture"], cfgs: Sequence[bz_swarm_config],
                  tile_particles: int = 0, blocks_per_sm: int = 0, use_graph: bool = True,
-                 channels_in_l2: bool = False):
+                 channels_in_l2: bool = False, block_threads: int = 0):
         self.ctx, self.mixtures, self.n = ctx, list(mixtures), len(cfgs)
         self.cfgs = (bz_swarm_config * self.n)(*cfgs)
         mh = (C.c_void_p * self.n)(*[m.h.value for m in mixtures])
-        opts = bz_batch_opts(int(tile_particles), int(blocks_per_sm), int(bool(use_graph)), int(bool(channels_in_l2)))
+        opts = bz_batch_opts(int(tile_particles), int(blocks_per_sm), int(bool(use_graph)), int(bool(channels_in_l2)),
+                             int(block_threads))
         h = C.c_void_p()
         _check(lib().bz_create_batch(ctx.h, self.n, mh, self.cfgs, C.byref(opts), C.byref(h)))
         self.h = h

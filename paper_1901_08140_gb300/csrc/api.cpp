@@ -65,7 +65,7 @@ struct bz_batch {
     int precision;
     bool ch_smem, use_graph, ext, wide, bfield;
     size_t smem;
-    int grid, n_tiles, max_tblocks;
+    int block, grid, n_tiles, max_tblocks;
     std::vector<uint64_t> n_el, id_offset;
     std::vector<bz::ParticlesDev> p;
     uint8_t *mem;
@@ -346,7 +346,11 @@ bz_status validate_config(const bz_swarm_config *cfg)
         return fail(BZ_EINVAL, "stage_wait_s must be finite and at most 3600");
     if (cfg->hold_stage > 1) return fail(BZ_EINVAL, "hold_stage must be 0 or 1");
     if (cfg->max_trials > 0xFFFFFFFFull) return fail(BZ_EINVAL, "max_trials must fit 32 bits");
-    if (cfg->block_threads != 0 && cfg->block_threads != 256) return fail(BZ_EINVAL, "block_threads must be 0 or 256");
+    if (cfg->block_threads != 0 && cfg->block_threads != 128 && cfg->block_threads != 256 &&
+        cfg->block_threads != 384 && cfg->block_threads != 768)
+        return fail(BZ_EINVAL, "block_threads must be 0, 128, 256, 384 or 768");
+    if (cfg->block_threads != 0 && cfg->block_threads != 256 && (cfg->precision != 32 || cfg->spawn))
+        return fail(BZ_EINVAL, "blocks of 128, 384 or 768 threads run FP32 swarms without spawn mode only");
     if (cfg->blocks_per_sm < 0) return fail(BZ_EINVAL, "blocks_per_sm must be >= 0");
     if (cfg->spawn != 0 && cfg->spawn != 1) return fail(BZ_EINVAL, "spawn must be 0 or 1");
     if (cfg->spawn && cfg->pop_cap && cfg->pop_cap < cfg->n_electrons)
@@ -581,11 +585,14 @@ bz_status bz_run_swarm(bz_ctx *ctx, const bz_mixture *mix, const bz_swarm_config
     const bool spawn = cfg->spawn != 0;
     const uint64_t cap = spawn ? (cfg->pop_cap ? cfg->pop_cap : 64 * n) : n;  // electron slots
     if (cap > 0xFFFFFFFFull) return fail(BZ_EINVAL, "a swarm holds at most 2^32-1 electrons");
-    const int block = 256;
+    const int block = cfg->block_threads ? cfg->block_threads : 256;
+    if (block != 256 && ext_instance(mix, cfg))
+        return fail(BZ_EINVAL, "blocks of 128, 384 or 768 threads run the lean step kernel only (no VARIABLE / "
+                               "BINNED trial frequency, no xi-form gases)");
     const bool bfield = cfg->b_T > 0.0;
     // the 4-block build: for every mixture without B; with B (more registers
-    // live, more spills at 64) only for one gas
-    const bool wide = !bfield || mix->cm.info.n_gases == 1;
+    // live, more spills at 64) only for one gas; blocks of 256 threads only
+    const bool wide = block == 256 && (!bfield || mix->cm.info.n_gases == 1);
     int bps = spawn ? bz::spawn_occupancy(cfg->precision, ch_smem, ext_instance(mix, cfg), wide, bfield, block,
                                           a.stage_bytes)
                     : bz::batch_occupancy(cfg->precision, ch_smem, ext_instance(mix, cfg), wide, bfield, block,
@@ -864,7 +871,7 @@ static cudaError_t batch_part(bz_batch *b, int part, cudaStream_t s)
         a.tiles = b->tiles;
         a.n_tiles = b->n_tiles;
         a.tile_counter = b->tile_counter;
-        if (e == cudaSuccess) e = bz::launch_batch(b->precision, b->ch_smem, b->ext, b->wide, b->bfield, a, b->smem, b->grid, 256, s);
+        if (e == cudaSuccess) e = bz::launch_batch(b->precision, b->ch_smem, b->ext, b->wide, b->bfield, a, b->smem, b->grid, b->block, s);
         return e;
     }
     e = bz::launch_tallies_multi(b->targs, b->n, b->max_tblocks, s);
@@ -914,7 +921,17 @@ bz_status bz_create_batch(bz_ctx *ctx, int32_t n, const bz_mixture *const *mixtu
     b->ext = ext_instance(mixtures[0], &cfgs[0]);
     b->bfield = false;  // the lean build without the field's paths when no swarm has B
     for (int i = 0; i < n; ++i) b->bfield = b->bfield || cfgs[i].b_T > 0.0;
-    b->wide = true;  // the 4-block build: without B, or when every mixture has one gas
+    b->block = (opts && opts->block_threads > 0) ? opts->block_threads : 256;
+    if (b->block != 256 && b->block != 128 && b->block != 384 && b->block != 768) {
+        delete b;
+        return fail(BZ_EINVAL, "block_threads must be 0, 128, 256, 384 or 768");
+    }
+    if (b->block != 256 && (precision != 32 || b->ext)) {
+        delete b;
+        return fail(BZ_EINVAL, "blocks of 128, 384 or 768 threads run the lean FP32 step kernel only");
+    }
+    // the 4-block build: without B, or when every mixture has one gas; blocks of 256 threads only
+    b->wide = b->block == 256;
     for (int i = 0; i < n; ++i) b->wide = b->wide && (!b->bfield || mixtures[i]->cm.info.n_gases == 1);
     b->use_graph = opts ? opts->use_graph != 0 : true;
     // tables of every mixture must fit; channel tables go to shared memory only if all fit
@@ -936,7 +953,7 @@ bz_status bz_create_batch(bz_ctx *ctx, int32_t n, const bz_mixture *const *mixtu
         desc[i].stage_bytes = b->ch_smem ? desc[i].lay.stage_all : desc[i].lay.stage_tables;
         b->smem = std::max(b->smem, (size_t)desc[i].stage_bytes);
     }
-    int bps = bz::batch_occupancy(precision, b->ch_smem, b->ext, b->wide, b->bfield, 256, b->smem);
+    int bps = bz::batch_occupancy(precision, b->ch_smem, b->ext, b->wide, b->bfield, b->block, b->smem);
     if (bps < 1) {
         delete b;
         return fail(BZ_ECUDA, "batch kernel cannot be resident with these tables");
@@ -1049,7 +1066,7 @@ bz_status bz_create_batch(bz_ctx *ctx, int32_t n, const bz_mixture *const *mixtu
     }
     if (b->use_graph) {
         // make sure the kernels' shared-memory limits are set before capture
-        bz::batch_occupancy(precision, b->ch_smem, b->ext, b->wide, b->bfield, 256, b->smem);
+        bz::batch_occupancy(precision, b->ch_smem, b->ext, b->wide, b->bfield, b->block, b->smem);
         for (int part = 0; part < 2 && e == cudaSuccess; ++part) {
             e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
             cudaError_t e1 = (e == cudaSuccess) ? batch_part(b, part, b->cap) : e;

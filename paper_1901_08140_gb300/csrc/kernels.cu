@@ -42,6 +42,14 @@ constexpr int kBlock = 256;
 // more registers live -- so callers allow it without B, and with B for
 // single-gas mixtures only.
 constexpr int kMinBlocksWide = 4;
+// The lean FP32 batch kernel is also built for blocks of 128, 384 and 768
+// threads at the register cap of the default build (3 x 256 threads per SM:
+// 6 x 128, 2 x 384, 1 x 768): fewer, larger blocks hold fewer copies of the
+// staged tables (more of the SM's shared memory is left to L1, which caches
+// the channel tables read from global memory) but wait on more warps at the
+// end of each tile.
+template <int BS>
+constexpr int blocks_at_default_cap() { return BZ_SWARM_MIN_BLOCKS * kBlock / BS; }
 constexpr uint32_t kStageChunk = 32768;
 constexpr uint32_t kWaitLimit = 1u << 24;
 constexpr uint64_t kDrainNs = 1000000000ull;  // 1 s for a staging copy in flight after a timeout
@@ -1507,8 +1515,8 @@ __device__ bool restage_tables(const uint8_t *src, uint8_t *dst, uint32_t bytes,
 // one it holds, runs the tile's electrons with per-lane refill (a lane that
 // finishes an electron takes the next one of the tile), and synchronises
 // before the next tile.
-template <typename R, bool CH_SMEM, bool EXT, int MINB, bool BF>
-__global__ void __launch_bounds__(kBlock, MINB) batch_kernel(const __grid_constant__ BatchArgs B)
+template <typename R, bool CH_SMEM, bool EXT, int MINB, bool BF, int BS = kBlock>
+__global__ void __launch_bounds__(BS, MINB) batch_kernel(const __grid_constant__ BatchArgs B)
 {
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ __align__(8) uint64_t mbar;
@@ -2188,6 +2196,24 @@ static auto kernel_of()
     else return &batch_kernel<R, C, E, M, B>;
 }
 
+// Block sizes a launch may take: 256 for every build; 128, 384 and 768 for
+// the lean FP32 batch kernel.
+static bool block_supported(int precision, bool ext, bool spawn, int block)
+{
+    if (block == kBlock) return true;
+    return (block == 128 || block == 384 || block == 768) && precision == 32 && !ext && !spawn;
+}
+
+template <int BS, typename Fn>
+static auto lean_block_build(bool ch, bool bf, Fn fn)
+{
+    constexpr int M = blocks_at_default_cap<BS>();
+    if (ch) return bf ? fn(&batch_kernel<float, true, false, M, true, BS>)
+                      : fn(&batch_kernel<float, true, false, M, false, BS>);
+    return bf ? fn(&batch_kernel<float, false, false, M, true, BS>)
+              : fn(&batch_kernel<float, false, false, M, false, BS>);
+}
+
 // Calls fn with the build of the step kernel (batch or spawn) that a launch
 // uses: FP64 and the feature build (ext) are general; the lean FP32 build
 // comes without the magnetic-field paths where the launch has no field
@@ -2196,6 +2222,12 @@ static auto kernel_of()
 template <bool SPAWN, typename Fn>
 static auto dispatch(int precision, bool ch, bool ext, bool bf, bool wide, int block, size_t smem, Fn fn)
 {
+    // (callers check block_supported first)
+    if constexpr (!SPAWN) {
+        if (block == 128) return lean_block_build<128>(ch, bf, fn);
+        if (block == 384) return lean_block_build<384>(ch, bf, fn);
+        if (block == 768) return lean_block_build<768>(ch, bf, fn);
+    }
     if (precision == 64) {
         if (ch) return ext ? fn(kernel_of<double, true, true, 1, true, SPAWN>())
                            : fn(kernel_of<double, true, false, 1, true, SPAWN>());
@@ -2222,13 +2254,14 @@ static auto dispatch(int precision, bool ch, bool ext, bool bf, bool wide, int b
 cudaError_t launch_batch(int precision, bool ch_smem, bool ext, bool wide, bool bfield, const BatchArgs &a,
                          size_t smem, int grid, int block, cudaStream_t s)
 {
-    if (block != kBlock) return cudaErrorInvalidValue;
+    if (!block_supported(precision, ext, false, block)) return cudaErrorInvalidValue;
     return dispatch<false>(precision, ch_smem, ext, bfield, wide, block, smem,
                            [&](auto k) { return go(k, a, smem, grid, block, s); });
 }
 
 int batch_occupancy(int precision, bool ch_smem, bool ext, bool wide, bool bfield, int block, size_t smem)
 {
+    if (!block_supported(precision, ext, false, block)) return -(int)cudaErrorInvalidValue;
     return dispatch<false>(precision, ch_smem, ext, bfield, wide, block, smem,
                            [&](auto k) { return occ(k, block, smem); });
 }
@@ -2243,6 +2276,7 @@ cudaError_t launch_spawn(int precision, bool ch_smem, bool ext, bool wide, bool 
 
 int spawn_occupancy(int precision, bool ch_smem, bool ext, bool wide, bool bfield, int block, size_t smem)
 {
+    if (block != kBlock) return -(int)cudaErrorInvalidValue;
     return dispatch<true>(precision, ch_smem, ext, bfield, wide, block, smem,
                           [&](auto k) { return occ(k, block, smem); });
 }

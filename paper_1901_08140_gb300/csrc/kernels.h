@@ -155,7 +155,9 @@ cudaError_t launch_group_sums2(const TallyArgs &a, const double *drift_host, cud
 // wide: the 4-block build of the lean FP32 kernel may be taken (where its
 // blocks fit); callers allow it without B, and with B for single-gas
 // mixtures.  bfield: some swarm of the launch has a magnetic field (else the
-// lean build without the field's paths runs).
+// lean build without the field's paths runs).  block: 256 threads, or 128,
+// 384 or 768 for the lean FP32 build (precision 32, not ext; never the
+// 4-block build); any other value returns cudaErrorInvalidValue.
 cudaError_t launch_batch(int precision, bool ch_smem, bool ext, bool wide, bool bfield, const BatchArgs &a,
                          size_t smem, int grid, int block, cudaStream_t s);
 // Spawn mode: one persistent launch runs the primaries and every electron

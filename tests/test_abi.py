@@ -40,19 +40,20 @@ def test_every_declared_symbol_is_exported(L):
     missing = [n for n in names if n not in exported]
     assert not missing, missing
     assert set(names) == set(bz.SIGNATURES)
-    assert L.bz_abi_version() == 7
+    assert L.bz_abi_version() == 8
 
 
 def test_struct_layouts_match_the_header(tmp_path):
     prog = tmp_path / "sizes.c"
-    prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "bz.h"\nint main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n",'
-                    'sizeof(bz_channel),sizeof(bz_gas),sizeof(bz_mixture_opts),sizeof(bz_mixture_info),'
+    prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "bz.h"\nint main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n",'
+                    'sizeof(bz_batch_opts),offsetof(bz_batch_opts,block_threads),sizeof(bz_channel),sizeof(bz_gas),sizeof(bz_mixture_opts),sizeof(bz_mixture_info),'
                     'sizeof(bz_swarm_config),sizeof(bz_tallies),sizeof(bz_particles),sizeof(bz_allocator),'
                     'offsetof(bz_tallies,n_particles),offsetof(bz_swarm_config,seed));return 0;}\n')
     exe = tmp_path / "sizes"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
     got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
-    want = [C.sizeof(bz.bz_channel), C.sizeof(bz.bz_gas), C.sizeof(bz.bz_mixture_opts), C.sizeof(bz.bz_mixture_info),
+    want = [C.sizeof(bz.bz_batch_opts), bz.bz_batch_opts.block_threads.offset, C.sizeof(bz.bz_channel),
+            C.sizeof(bz.bz_gas), C.sizeof(bz.bz_mixture_opts), C.sizeof(bz.bz_mixture_info),
             C.sizeof(bz.bz_swarm_config), C.sizeof(bz.bz_tallies), C.sizeof(bz.bz_particles),
             C.sizeof(bz.bz_allocator), bz.bz_tallies.n_particles.offset, bz.bz_swarm_config.seed.offset]
     assert got == want

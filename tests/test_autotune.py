@@ -35,6 +35,9 @@ def test_tile_size_from_tiles_per_block(L):
     assert autotune.tile_size(cfgs, {"tiles_per_block": 16, "blocks_per_sm": 0}) == 256
     assert autotune.tile_size(cfgs, {"tiles_per_block": 1, "blocks_per_sm": 0}) == 3072
     assert autotune.tile_size(cfgs, {"tiles_per_block": 1, "blocks_per_sm": 2}) == 4352
+    # blocks of 128 threads: 6 resident per SM, tiles of half the electrons (1426 -> 1536); 384: 2 per SM
+    assert autotune.tile_size(cfgs, {"tiles_per_block": 1, "blocks_per_sm": 0, "block_threads": 128}) == 1536
+    assert autotune.tile_size(cfgs, {"tiles_per_block": 1, "blocks_per_sm": 0, "block_threads": 384}) == 4352
 
 
 @pytest.mark.gpu
@@ -47,6 +50,7 @@ def test_tune_a_small_batch(tmp_path, L):
     choice = autotune.tune(ctx, [mix] * 4, cfgs, cache_path=path)
     assert choice["cached"] is False and choice["window_c"] in autotune.WINDOW_C
     assert mix.info["channels_in_smem"] == 1 and choice["channels_in_l2"] in (False, True)
+    assert choice["block_threads"] in autotune.BLOCK_THREADS
     again = autotune.tune(ctx, [mix] * 4, cfgs, cache_path=path)
     assert again["cached"] is True and again["window_c"] == choice["window_c"]
     b = autotune.make_batch(ctx, [mix] * 4, autotune.apply(cfgs, choice), choice)

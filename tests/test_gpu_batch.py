@@ -1,5 +1,6 @@
 """Batched swarms (one persistent launch over many swarms, CUDA graph):
 every swarm's results equal those of its own bz_run_swarm."""
+import ctypes as C
 import math
 
 import numpy as np
@@ -63,6 +64,66 @@ def test_batch_equals_individual_runs(ctx, use_graph, field, staged):
     km, tm = batch.timing()
     assert km > 0 and tm > 0
     batch.close()
+
+
+@pytest.mark.parametrize("block", [128, 384, 768])
+@pytest.mark.parametrize("field", [True, False])
+@pytest.mark.parametrize("staged", [True, False])
+def test_block_sizes_give_the_same_results(ctx, block, field, staged):
+    """Blocks of 128, 384 or 768 threads run the same step kernel at the same
+    register cap: electrons are independent and every draw is keyed by the
+    electron's id, so every value equals the 256-thread launch's bit for bit,
+    batched and alone."""
+    items = [(m, c) for m, c in _items(ctx)
+             if (c.b_T > 0) == field and bool(m.info["channels_in_smem"]) == staged]
+    ref = bz.Batch(ctx, [m for m, _ in items], [c for _, c in items], tile_particles=512)
+    ref.launch()
+    rt = ref.tallies()
+    got = bz.Batch(ctx, [m for m, _ in items], [c for _, c in items], tile_particles=512, block_threads=block)
+    got.launch()
+    gt = got.tallies()
+    for i, (mix, cfg) in enumerate(items):
+        p, q = ref.particles(i), got.particles(i)
+        for k in ["x", "y", "z", "t", "sum_e", "sum_e2", "n_real", "n_null", "n_fail", "n_ion", "n_att", "steps"]:
+            assert np.array_equal(p[k], q[k]), (i, k)
+        for k in ["W", "eps", "D_L", "D_T", "W_se", "alpha", "efficiency"]:
+            assert gt[i][k] == rt[i][k] or (math.isnan(rt[i][k]) and math.isnan(gt[i][k])), (i, k)
+        assert gt[i]["error_flags"] == 0
+    mix, cfg = items[-1]
+    alone = bz.run_swarm(ctx, mix, _with(cfg, block_threads=block))
+    pa = alone.particles()
+    alone.close()
+    q = got.particles(len(items) - 1)
+    for k in ["x", "t", "sum_e", "n_real", "n_null", "steps"]:
+        assert np.array_equal(pa[k], q[k]), k
+    ref.close()
+    got.close()
+
+
+def _with(cfg, **over):
+    """A copy of a swarm configuration with some fields replaced."""
+    out = bz.bz_swarm_config()
+    C.memmove(C.byref(out), C.byref(cfg), C.sizeof(bz.bz_swarm_config))
+    for k, v in over.items():
+        setattr(out, k, v)
+    return out
+
+
+def test_unsupported_block_sizes_are_rejected(ctx):
+    mix, cfg = _items(ctx)[3]
+    for bad in (64, 192, 512, 1024):
+        with pytest.raises(bz.BzError, match="block_threads"):
+            bz.Batch(ctx, [mix], [cfg], block_threads=bad)
+        with pytest.raises(bz.BzError, match="block_threads"):
+            bz.run_swarm(ctx, mix, _with(cfg, block_threads=bad))
+    c64 = _with(cfg, precision=64)
+    with pytest.raises(bz.BzError, match="128, 384 or 768"):
+        bz.Batch(ctx, [mix], [c64], block_threads=128)
+    with pytest.raises(bz.BzError, match="128, 384 or 768"):
+        bz.run_swarm(ctx, mix, _with(c64, block_threads=384))
+    cv = _with(cfg, trial_mode=bz.BZ_TRIAL_VARIABLE)
+    with pytest.raises(bz.BzError, match="128, 384 or 768"):
+        bz.Batch(ctx, [mix], [cv], block_threads=128)
 
 
 def test_mixed_field_batch(ctx):
