@@ -93,6 +93,10 @@ def parse():
     ap.add_argument("--no-tune", action="store_true",
                     help="the autotuner's default launch options instead of a search (profiling runs)")
     ap.add_argument("--only-point", type=int, default=-1, help="sweep workload: one E/N point (profiling case)")
+    ap.add_argument("--block-threads", type=int, default=0,
+                    help="with --no-tune: threads per block of the headline launch (profiling runs)")
+    ap.add_argument("--smem-budget", type=int, default=0,
+                    help="with --no-tune: table budget per block the headline's mixtures are compiled for")
     a = ap.parse_args()
     a.legs = set(LEGS) if a.legs == "all" else set() if a.legs == "none" else set(a.legs.split(","))
     return a
@@ -181,23 +185,31 @@ def _profile_record(name):
     return rec if h.hexdigest() == rec["sources_sha256"] else None
 
 
-def profiled_traffic(name):
+def _same_launch(rec, launch):
+    """The captured launch had this block size and table budget."""
+    base = {"block_threads": 256, "smem_budget": 0}
+    return launch is None or all(int(rec.get("launch", {}).get(k, base[k])) == int(v or base[k])
+                                 for k, v in launch.items())
+
+
+def profiled_traffic(name, launch=None):
     """DRAM bytes (read + write) of one step-kernel launch of a workload from
     an ncu capture summarised in profiles/<name>.json, if the kernel sources
-    are still the ones that capture ran (else None)."""
+    are still the ones that capture ran and the capture launched the same
+    block size and table budget (else None)."""
     rec = _profile_record(name)
-    if rec is None:
+    if rec is None or not _same_launch(rec, launch):
         return None
     return (rec["dram_bytes_read"] + rec["dram_bytes_write"]) * rec.get("scale_to_full", 1.0)
 
 
-def shared_memory_roofline(case, reals, kern_ms, sm_count, sm_mhz):
+def shared_memory_roofline(case, reals, kern_ms, sm_count, sm_mhz, launch=None):
     """Shared-memory pipe use of a launch: shared-memory wavefronts per real
     collision from the ncu capture of the workload's reduced case
-    (profiles/batch_kernel_smem.json) times this launch's real collisions,
-    over the peak of one 128-byte wavefront per SM per clock."""
+    (profiles/batch_kernel_smem.json, same launch form) times this launch's
+    real collisions, over the peak of one 128-byte wavefront per SM per clock."""
     rec = _profile_record("batch_kernel_smem")
-    if rec is None or case not in rec["cases"]:
+    if rec is None or case not in rec["cases"] or not _same_launch(rec["cases"][case], launch):
         return None
     per_real = rec["cases"][case]["wavefronts_per_real"]
     achieved = per_real * reals * 128.0 / (kern_ms / 1e3)
@@ -240,16 +252,25 @@ def sweep_name(args):
             "frequency, B = 0" + (f" (point {args.only_point} only)" if args.only_point >= 0 else ""))
 
 
-def tuned(ctx, mixes, cfgs, args, shared=True):
+def tuned(ctx, mixes, cfgs, args, shared=True, gas_lists=None, headline=False):
     """The autotuner's choice for this batch, or its default options with
-    --no-tune.  With several ranks and shared=True, rank 0 tunes and every
-    rank takes its choice (the legs that follow must agree across ranks)."""
+    --no-tune (for the headline launch, --block-threads / --smem-budget
+    override them).  With several
+    ranks and shared=True, rank 0 tunes and every rank takes its choice (the
+    legs that follow must agree across ranks).  With gas_lists the tuner may
+    choose a table budget; the batch then runs on mixtures compiled for it."""
     from paper_1901_08140_gb300 import autotune
     if args.no_tune:
-        return dict(autotune.DEFAULT, cached=None)
+        choice = dict(autotune.DEFAULT, cached=None)
+        if headline and args.block_threads:
+            choice["block_threads"] = args.block_threads
+        if headline and args.smem_budget and gas_lists is not None:
+            choice["smem_budget"] = args.smem_budget
+        return choice
     import torch.distributed as dist
     multi = shared and dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1
-    choice = autotune.tune(ctx, mixes, cfgs) if not multi or dist.get_rank() == 0 else None
+    choice = (autotune.tune(ctx, mixes, cfgs, gas_lists=gas_lists)
+              if not multi or dist.get_rank() == 0 else None)
     if multi:
         box = [choice]
         dist.broadcast_object_list(box, src=0)
@@ -323,15 +344,19 @@ def counts_of(tallies):
 # --------------------------------------------------------------------------
 def batched_run(ctx, stream, flush, world, dev, specs, rank, args, clocks_gpu):
     """The headline: every swarm in one persistent launch replayed from a CUDA
-    graph with the autotuner's launch options; the same swarms one launch each
-    at the same window length; the autotuned window length's own gain."""
+    graph with the autotuner's launch options (and mixtures compiled for its
+    table budget); the same swarms one launch each at the same window length
+    and the library's default launch shape; the autotuned window length's
+    own gain."""
     from paper_1901_08140_gb300 import autotune, bz
     mixes = [bz.Mixture(ctx, s.gases) for s in specs]
     id_off = rank << 32  # weak scaling: every rank runs every swarm on its own ids
     cfgs = [bz.config_from_spec(s, trial_mode=bz.BZ_TRIAL_WINDOW, id_offset=id_off) for s in specs]
-    choice = tuned(ctx, mixes, cfgs, args)
+    gas_lists = [s.gases for s in specs]
+    choice = tuned(ctx, mixes, cfgs, args, gas_lists=gas_lists, headline=True)
     tuned_cfgs = autotune.apply(cfgs, choice)
-    batch = autotune.make_batch(ctx, mixes, tuned_cfgs, choice)
+    bmixes = autotune.mixtures_for(ctx, gas_lists, choice) if choice.get("smem_budget") else mixes
+    batch = autotune.make_batch(ctx, bmixes, tuned_cfgs, choice)
     for _ in range(args.warmup):
         batch.launch(stream)
         batch.tallies(check=False)
@@ -366,13 +391,16 @@ def batched_run(ctx, stream, flush, world, dev, specs, rank, args, clocks_gpu):
         out["plain"] = {"ms": pms, "steps": steps, "reals": preals}
         # the autotuned window length against the default one, batched both
         if any(abs(c.window_c - 2.0) > 1e-9 for c in tuned_cfgs):
-            b2 = autotune.make_batch(ctx, mixes, cfgs, dict(choice, window_c=2.0))
+            b2 = autotune.make_batch(ctx, bmixes, cfgs, dict(choice, window_c=2.0))
             b2.launch(stream)
             b2.tallies(check=False)
             dms, _ = _timed(stream, flush, 1, lambda: b2.launch(stream), world, dev)
             dreals = sum(t["n_real"] for t in b2.tallies())
             b2.close()
             out["default_window"] = {"ms": dms, "reals": dreals}
+    if bmixes is not mixes:
+        for m in bmixes:
+            m.close()
     return out
 
 
@@ -411,7 +439,8 @@ def e2e_run(ctx, stream, specs, rank, choice, steps):
     t0 = time.perf_counter()
     with cf.ThreadPoolExecutor(max_workers=16) as ex:
         def prepare():
-            mixes = list(ex.map(lambda s: bz.Mixture(ctx, s.gases), specs))
+            mixes = list(ex.map(lambda s: bz.Mixture(ctx, s.gases, smem_budget=int(choice.get("smem_budget", 0))),
+                                specs))
             return mixes, autotune.make_batch(ctx, mixes, cfgs, choice)
         nxt = prepare()
         for k in range(steps):
@@ -475,7 +504,7 @@ def sweep_run(ctx, stream, flush, world, dev, args, rank):
     return {"workload": sweep_name(args), "value": reals / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
             "plain": {"value": preals / (pms / 1e3), "ms_per_step": pms / 2},
             "batched_over_plain": (reals / ms) / (preals / pms),
-            "autotuned": {k: choice.get(k) for k in ("window_c", "tiles_per_block", "blocks_per_sm", "channels_in_l2", "block_threads", "cached")},
+            "autotuned": {k: choice.get(k) for k in ("window_c", "tiles_per_block", "blocks_per_sm", "channels_in_l2", "block_threads", "smem_budget", "cached")},
             "_tallies": tallies, "_kern_ms": kern / steps, "_specs": specs}
 
 
@@ -785,13 +814,16 @@ def run_ours(args):
     # ---- the headline workload
     if args.workload == "batched":
         r = batched_run(ctx, stream, flush, world, dev, specs, rank, args, lambda: Clocks(local))
-        kind, kernel = "field", "batch_kernel (lean FP32 build with the field's paths, 3 blocks/SM)"
+        bt = int(r["choice"].get("block_threads", 256))
+        kind, kernel = "field", (f"batch_kernel (lean FP32 build with the field's paths, {bt} threads x "
+                                 f"{768 // bt} blocks/SM, tables compiled for "
+                                 f"{int(r['choice'].get('smem_budget', 0)) or 73728} B per block)")
         prof = "batch_kernel_batched_256"
     else:
         from paper_1901_08140_gb300 import autotune
         mix = bz.Mixture(ctx, specs[0].gases)
         cfgs = [bz.config_from_spec(s, trial_mode=bz.BZ_TRIAL_WINDOW, id_offset=rank << 32) for s in specs]
-        choice = tuned(ctx, [mix] * len(cfgs), cfgs, args)
+        choice = tuned(ctx, [mix] * len(cfgs), cfgs, args, headline=True)
         tuned_cfgs = autotune.apply(cfgs, choice)
         b = autotune.make_batch(ctx, [mix] * len(cfgs), tuned_cfgs, choice)
         for _ in range(args.warmup):
@@ -817,11 +849,15 @@ def run_ours(args):
     sm_mhz = clk.get("sm_mhz") or 2070.0
     counts = counts_of(r["tallies"])
     out.update({"value": value, "ms_per_step": t_max / args.steps,
-                "roofline": roofline_of(kind, counts, r["kern_ms"], sm_count, sm_mhz, profiled_traffic(prof), kernel),
+                "roofline": roofline_of(kind, counts, r["kern_ms"], sm_count, sm_mhz,
+                                        profiled_traffic(prof, {k: r["choice"].get(k, 0) for k in
+                                                                ("block_threads", "smem_budget")}), kernel),
                 "shared_memory": shared_memory_roofline("batched" if args.workload == "batched" else "sweep",
-                                                        counts["reals"], r["kern_ms"], sm_count, sm_mhz),
+                                                        counts["reals"], r["kern_ms"], sm_count, sm_mhz,
+                                                        {k: r["choice"].get(k, 0) for k in
+                                                         ("block_threads", "smem_budget")}),
                 "clocks": clk, "gpu_launches": 5 * args.steps,
-                "autotuned": {k: r["choice"].get(k) for k in ("window_c", "tiles_per_block", "blocks_per_sm", "channels_in_l2", "block_threads", "cached")},
+                "autotuned": {k: r["choice"].get(k) for k in ("window_c", "tiles_per_block", "blocks_per_sm", "channels_in_l2", "block_threads", "smem_budget", "cached")},
                 "trial_collisions_per_s": counts["trials"] * world / (t_max / 1e3),
                 "efficiency": counts["reals"] / counts["trials"] if counts["trials"] else None,
                 "window_restarts_per_real": (counts["windows"] - counts["reals"]) / counts["reals"]})
@@ -849,9 +885,12 @@ def run_ours(args):
         sw = sweep_run(ctx, stream, flush, 1, dev, args, rank)  # rank 0 alone: no barrier
         sw_counts = counts_of(sw["_tallies"])
         sw["roofline"] = roofline_of("plain", sw_counts, sw["_kern_ms"], sm_count, sm_mhz,
-                                     profiled_traffic("batch_kernel_traffic_argon_sweep"),
+                                     profiled_traffic("batch_kernel_traffic_argon_sweep",
+                                                      {k: sw["autotuned"].get(k) for k in ("block_threads", "smem_budget")}),
                                      "batch_kernel (lean FP32 build without field paths; 4 blocks/SM)")
-        sw["shared_memory"] = shared_memory_roofline("sweep", sw_counts["reals"], sw["_kern_ms"], sm_count, sm_mhz)
+        sw["shared_memory"] = shared_memory_roofline("sweep", sw_counts["reals"], sw["_kern_ms"], sm_count, sm_mhz,
+                                                     {k: sw["autotuned"].get(k) for k in
+                                                      ("block_threads", "smem_budget")})
         if "oracle" in args.legs:
             sw["drift_velocity_vs_oracle"] = sweep_vs_oracle(sw["_tallies"], sw["_specs"], args.oracle_electrons)
             out["max_rel_err_W_vs_oracle"] = sw["drift_velocity_vs_oracle"]["max_abs_rel_W"]

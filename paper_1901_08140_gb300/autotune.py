@@ -7,10 +7,13 @@ the tile size, expressed as tiles per resident block so that the choice
 carries over between a copy of the batch and the batch itself (it sets how
 many electrons each lane runs, one after another, per tile), the resident
 blocks per SM, the threads per block (256, or 128 / 384 / 768 at the same
-register cap where the batch runs the lean FP32 kernel), and the
+register cap where the batch runs the lean FP32 kernel), the
 table-staging policy where every mixture could stage its channel tables
 (staged, or all channel choices from the cumulative tables in global
-memory).  It times candidates by coordinate descent on a
+memory), and -- for one block of 768 threads per SM, given the swarms' gas
+lists -- the shared-memory budget the mixtures' tables are compiled for
+(the default fits three blocks per SM; with one block the tables may keep
+their densest bucket index and every bin maximum in shared memory).  It times candidates by coordinate descent on a
 reduced copy of the batch -- every swarm keeps its mixture, fields and real
 collisions per electron but runs half of its electrons, so an electron's
 history looks like the full batch's -- checks the winner against the
@@ -34,11 +37,14 @@ CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_autotune_cach
 # window_c 1.5 and 16 tiles per block: the fastest point of a full-size sweep of
 # the 256-swarm workload on GB300 (window_c 1.0 / 1.5 / 2.0 / 3.0: 2.94 / 2.90 /
 # 2.99 / 3.18 s; 8 / 16 / 32 tiles per block: 2.98 / 2.90 / 2.91 s)
-DEFAULT = {"window_c": 1.5, "tiles_per_block": 16, "blocks_per_sm": 0, "channels_in_l2": False, "block_threads": 256}
+DEFAULT = {"window_c": 1.5, "tiles_per_block": 16, "blocks_per_sm": 0, "channels_in_l2": False, "block_threads": 256,
+           "smem_budget": 0}
 WINDOW_C = [1.0, 1.5, 2.0, 3.0]
 TILES_PER_BLOCK = [4, 8, 16, 32]
 BLOCKS = [0, 2]
 BLOCK_THREADS = [256, 128, 384, 768]
+# table budget per block with one block per SM (0: the library's three-block budget)
+ONE_BLOCK_BUDGET = 200 * 1024
 SM_COUNT = 152
 RESIDENT_BLOCKS = 3   # the FP32 step kernel's blocks of 256 threads per SM when its tables fit
 
@@ -89,6 +95,11 @@ def tile_size(cfgs: Sequence[bz.bz_swarm_config], choice: dict, sm_count: int = 
     return max(256, (t + 255) // 256 * 256)
 
 
+def mixtures_for(ctx, gas_lists: Sequence, choice: dict) -> List["bz.Mixture"]:
+    """One mixture per gas list, compiled for the choice's table budget."""
+    return [bz.Mixture(ctx, g, smem_budget=int(choice.get("smem_budget", 0))) for g in gas_lists]
+
+
 def make_batch(ctx, mixtures, cfgs, choice, use_graph: bool = True, sm_count: int = SM_COUNT) -> "bz.Batch":
     """A batch launched with the chosen options (cfgs already carry the
     chosen window length, see apply)."""
@@ -113,9 +124,12 @@ def _measure(ctx, mixtures, cfgs, choice, sm_count, repeats=2) -> float:
 
 def tune(ctx, mixtures: Sequence, cfgs: Sequence[bz.bz_swarm_config], scale: float = 0.5,
          use_cache: bool = True, cache_path: str = CACHE, gpu_name: Optional[str] = None,
-         margin: float = 0.02) -> dict:
+         margin: float = 0.02, gas_lists: Optional[Sequence] = None) -> dict:
     """Best launch options for this batch (cached per GPU and workload class).
 
+    mixtures were compiled with the library's default table budget; with
+    gas_lists (the gases of each swarm's mixture) the tuner may also choose
+    a larger budget, and the caller then runs the batch on mixtures_for(...).
     A candidate replaces the current best only if it is faster by more than
     `margin` on the reduced copy; at the end the choice and the defaults are
     timed once each on the batch itself and the faster is kept, so the
@@ -126,7 +140,7 @@ def tune(ctx, mixtures: Sequence, cfgs: Sequence[bz.bz_swarm_config], scale: flo
     sm_count = torch.cuda.get_device_properties(ctx.device).multi_processor_count
     key = f"{gpu_name}|{signature(cfgs)}"
     cache = load_cache(cache_path) if use_cache else {}
-    if key in cache and "block_threads" in cache[key]:
+    if key in cache and "smem_budget" in cache[key]:
         return dict(cache[key], cached=True)
     small = [_copy_cfg(c, n_electrons=max(256, int(c.n_electrons * scale))) for c in cfgs]
     best = dict(DEFAULT)
@@ -148,14 +162,24 @@ def tune(ctx, mixtures: Sequence, cfgs: Sequence[bz.bz_swarm_config], scale: flo
             r = _measure(ctx, mixtures, small, cand, sm_count)
             if r > best_rate * (1.0 + margin):
                 best, best_rate = cand, r
+    big = None
+    if gas_lists is not None and lean:
+        # one block of 768 threads per SM with tables compiled for it
+        big = mixtures_for(ctx, gas_lists, {"smem_budget": ONE_BLOCK_BUDGET})
+        cand = dict(best, block_threads=768, blocks_per_sm=0, smem_budget=ONE_BLOCK_BUDGET)
+        r = _measure(ctx, big, small, cand, sm_count)
+        if r > best_rate * (1.0 + margin):
+            best, best_rate = cand, r
     best["rate_per_ms_reduced"] = best_rate
     if any(best[k] != DEFAULT[k] for k in DEFAULT):
-        full_best = _measure(ctx, mixtures, cfgs, best, sm_count, repeats=1)
+        full_best = _measure(ctx, big if best["smem_budget"] else mixtures, cfgs, best, sm_count, repeats=1)
         full_default = _measure(ctx, mixtures, cfgs, DEFAULT, sm_count, repeats=1)
         if full_default >= full_best:
             best = dict(DEFAULT, rate_per_ms_reduced=best_rate, rejected=dict(best))
         best["rate_per_ms"] = max(full_best, full_default)
         best["default_rate_per_ms"] = full_default
+    for m in big or []:
+        m.close()
     cache[key] = best
     if use_cache:
         store_cache(cache, cache_path)

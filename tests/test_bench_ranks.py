@@ -28,7 +28,7 @@ def _worker(rank, world, port, out):
     from paper_1901_08140_gb300 import autotune
     calls = []
 
-    def fake_tune(ctx, mixes, cfgs):  # a tuning whose outcome differs per rank
+    def fake_tune(ctx, mixes, cfgs, gas_lists=None):  # a tuning whose outcome differs per rank
         calls.append(rank)
         return {"window_c": 1.0 + rank, "tiles_per_block": 8 * (rank + 1), "blocks_per_sm": 0, "cached": False}
 

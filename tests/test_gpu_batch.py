@@ -109,6 +109,39 @@ def _with(cfg, **over):
     return out
 
 
+def test_table_budget_gives_the_same_results(ctx):
+    """Mixtures compiled for one block per SM (a larger table budget: a
+    denser bucket index, every bin maximum in shared memory) locate the same
+    records and bin maxima, so a batch of 768-thread blocks on them gives the
+    default batch's values bit for bit (both leave the channel tables in
+    global memory)."""
+    import dataclasses
+    from paper_1901_08140_gb300 import autotune
+    specs = [dataclasses.replace(s, n_electrons=min(s.n_electrons, 2000))
+             for s in W.batched_swarms(count=64, real_collisions=50)]
+    small = [bz.Mixture(ctx, s.gases) for s in specs]
+    big = autotune.mixtures_for(ctx, [s.gases for s in specs], {"smem_budget": autotune.ONE_BLOCK_BUDGET})
+    keep = [i for i in range(len(specs)) if small[i].info["channels_in_smem"] == big[i].info["channels_in_smem"] == 0]
+    assert keep
+    assert any(big[i].info["smem_bytes"] > small[i].info["smem_bytes"] for i in keep)  # some layouts differ
+    cfgs = [bz.config_from_spec(specs[i], trial_mode=bz.BZ_TRIAL_WINDOW) for i in keep]
+    ref = bz.Batch(ctx, [small[i] for i in keep], cfgs)
+    got = bz.Batch(ctx, [big[i] for i in keep], cfgs, block_threads=768)
+    ref.launch()
+    got.launch()
+    rt, gt = ref.tallies(), got.tallies()
+    for j in range(len(keep)):
+        p, q = ref.particles(j), got.particles(j)
+        for k in ["x", "y", "z", "t", "sum_e", "sum_e2", "n_real", "n_null", "n_fail", "steps"]:
+            assert np.array_equal(p[k], q[k]), (j, k)
+        for k in ["W", "eps", "D_L", "D_T", "W_se"]:
+            assert gt[j][k] == rt[j][k], (j, k)
+    ref.close()
+    got.close()
+    for m in small + big:
+        m.close()
+
+
 def test_unsupported_block_sizes_are_rejected(ctx):
     mix, cfg = _items(ctx)[3]
     for bad in (64, 192, 512, 1024):

@@ -17,10 +17,12 @@ agree in every swarm statistic within their standard errors.
   0.999 quantile of chi-square with 32 degrees of freedom, and within 0.5 %
   wherever the two samples resolve 0.5 % (3 combined SE below it).
 * The 256-swarm batched workload exactly as the benchmark launches it (one
-  persistent launch from a CUDA graph, the autotuner's default options):
-  four of its swarms -- 3-4 gases, 30-300 Td, |B| >= 0.3 T at an oblique
-  angle, at least 1e5 electrons -- against 8000 oracle electrons each, W,
-  <eps>, D_L and D_T within 4 combined standard errors (16 comparisons).
+  persistent launch from a CUDA graph, the autotuner's default options, and
+  again as one 768-thread block per SM on tables compiled for it, which
+  gives the same tallies): four of its swarms -- 3-4 gases, 30-300 Td,
+  |B| >= 0.3 T at an oblique angle, at least 1e5 electrons -- against 8000
+  oracle electrons each, W, <eps>, D_L and D_T within 4 combined standard
+  errors (16 comparisons).
 * Four configurations at high statistics (1e7 GPU and 1e6 oracle electrons
   x 100 real collisions): three points of the sweep and the Ar/CO2 90/10
   mixture with B = 1 T perpendicular to E, all four in one batched launch:
@@ -158,6 +160,18 @@ def test_batched_workload_as_timed_against_oracle(ctx):
     batch.close()
     assert all(t["error_flags"] == 0 for t in tg)
     assert sum(t["n_real"] for t in tg) == 1000 * sum(sp.n_electrons for sp in specs)
+    # the launch form the benchmark's tuner takes on GB300 (one 768-thread
+    # block per SM, tables compiled for it) gives the same tallies
+    one = dict(autotune.DEFAULT, block_threads=768, smem_budget=autotune.ONE_BLOCK_BUDGET)
+    big = autotune.mixtures_for(ctx, [sp.gases for sp in specs], one)
+    b1 = autotune.make_batch(ctx, big, cfgs, one)
+    b1.launch()
+    t1 = b1.tallies()
+    b1.close()
+    for m in big:
+        m.close()
+    for a, b in zip(tg, t1):
+        assert all(a[k] == b[k] for k in ("W", "eps", "D_L", "D_T", "n_real", "n_null")), (a, b)
     picked = [i for i, sp in enumerate(specs) if 30.0 <= sp.e_over_n_Td <= 300.0 and len(sp.gases) >= 3
               and sp.b_T >= 0.3 and sp.n_electrons >= 100_000][:4]
     assert len(picked) == 4
