@@ -74,6 +74,8 @@ def parse():
     ap.add_argument("--electrons", type=int, default=1_000_000, help="electrons per point of the sweep")
     ap.add_argument("--legs", default="all", help="comma list of " + ",".join(LEGS) + ", or all / none")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="bound of the CPU-baseline sample")
+    ap.add_argument("--batched-oracle-electrons", type=int, default=32_000,
+                    help="oracle electrons per swarm of the batched workload's check against the oracle")
     ap.add_argument("--oracle-electrons", type=int, default=10_000,
                     help="oracle electrons per E/N point of the sweep's drift-velocity check")
     ap.add_argument("--serve-rates", default="250,400,600,800,2000", help="Poisson arrival rates [req/s]")
@@ -539,7 +541,7 @@ def sweep_vs_oracle(sweep_tallies, specs, n_oracle):
             "max_abs_rel_W": summ["W"]["max_abs_rel"], "per_point": rows}
 
 
-def batched_vs_oracle(tallies, specs, n_oracle=8000, count=4):
+def batched_vs_oracle(tallies, specs, n_oracle=32000, count=4):
     """Swarms of the timed batched workload (3-4 gases, 30-300 Td, |B| >= 0.3 T,
     at least 1e5 electrons: the first `count` of them) against the FP64
     oracle on n_oracle electrons each, ids after the GPU's: relative
@@ -566,6 +568,30 @@ def batched_vs_oracle(tallies, specs, n_oracle=8000, count=4):
     return {"oracle_electrons_per_swarm": n_oracle, "seconds": time.perf_counter() - t0,
             "max_abs_z": max(abs(r[k]["z"]) for r in rows for k in ("W", "eps", "D_L", "D_T")),
             "max_abs_rel_W": max(abs(r["W"]["rel"]) for r in rows), "per_swarm": rows}
+
+
+def w_qualifier(batched, sweep):
+    """The metric's drift-velocity qualifier: the largest |dW|/W against the
+    oracle among the comparisons whose samples resolve 0.5 % (three combined
+    standard errors below it), beside the figures over every comparison."""
+    rows = []
+    if batched:
+        rows += [("batched swarm %d" % r["swarm"], r["W"]) for r in batched["per_swarm"]]
+    if sweep:
+        rows += [("sweep %.4g Td" % r["E/N_Td"], r["W"]) for r in sweep["per_point"]]
+    if not rows:
+        return {}
+    res = [(n, w) for n, w in rows if 3 * w["rel_se"] <= 0.005]
+    worst = max(res, key=lambda nw: abs(nw[1]["rel"])) if res else None
+    return {"max_rel_err_W_vs_oracle": abs(worst[1]["rel"]) if worst else None,
+            "w_vs_oracle": {"resolving_0.5pct": len(res), "comparisons": len(rows),
+                            "worst_resolved": {"case": worst[0], **worst[1]} if worst else None,
+                            "within_0.5pct": sum(1 for _, w in res if abs(w["rel"]) <= 0.005),
+                            "max_abs_z_all": max(abs(w["z"]) for _, w in rows),
+                            "max_abs_rel_all": max(abs(w["rel"]) for _, w in rows),
+                            "note": "relative difference of W from the FP64 oracle (independent ids); the maximum is "
+                                    "taken where 3 combined standard errors are below 0.5 %; max_abs_z_all and "
+                                    "max_abs_rel_all are over every comparison"}}
 
 
 def configs_run(ctx, stream):
@@ -880,7 +906,7 @@ def run_ours(args):
         out["e2e"] = e2e_run(ctx, stream, specs, rank, r["choice"], min(max(args.steps, 2), 5))
     # ---- further legs (rank 0)
     if rank == 0 and args.workload == "batched" and "oracle" in args.legs and args.scale == 1:
-        out["batched_vs_oracle"] = batched_vs_oracle(r["tallies"][-len(specs):], specs)
+        out["batched_vs_oracle"] = batched_vs_oracle(r["tallies"][-len(specs):], specs, args.batched_oracle_electrons)
     if rank == 0 and args.workload == "batched" and ("sweep" in args.legs or "oracle" in args.legs):
         sw = sweep_run(ctx, stream, flush, 1, dev, args, rank)  # rank 0 alone: no barrier
         sw_counts = counts_of(sw["_tallies"])
@@ -893,7 +919,7 @@ def run_ours(args):
                                                       ("block_threads", "smem_budget")})
         if "oracle" in args.legs:
             sw["drift_velocity_vs_oracle"] = sweep_vs_oracle(sw["_tallies"], sw["_specs"], args.oracle_electrons)
-            out["max_rel_err_W_vs_oracle"] = sw["drift_velocity_vs_oracle"]["max_abs_rel_W"]
+            out.update(w_qualifier(out.get("batched_vs_oracle"), sw["drift_velocity_vs_oracle"]))
         for k in ("_tallies", "_kern_ms", "_specs"):
             sw.pop(k)
         out["argon_sweep"] = sw
