@@ -137,11 +137,14 @@ def tune(ctx, mixtures: Sequence, cfgs: Sequence[bz.bz_swarm_config], scale: flo
     import torch
     if gpu_name is None:
         gpu_name = torch.cuda.get_device_name(ctx.device)
-    sm_count = torch.cuda.get_device_properties(ctx.device).multi_processor_count
     key = f"{gpu_name}|{signature(cfgs)}"
     cache = load_cache(cache_path) if use_cache else {}
     if key in cache and "smem_budget" in cache[key]:
-        return dict(cache[key], cached=True)
+        hit = dict(cache[key], cached=True)
+        if gas_lists is None:
+            hit["smem_budget"] = 0  # the caller cannot compile mixtures for another budget
+        return hit
+    sm_count = torch.cuda.get_device_properties(ctx.device).multi_processor_count
     small = [_copy_cfg(c, n_electrons=max(256, int(c.n_electrons * scale))) for c in cfgs]
     best = dict(DEFAULT)
     best_rate = _measure(ctx, mixtures, small, best, sm_count)

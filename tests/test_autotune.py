@@ -40,6 +40,20 @@ def test_tile_size_from_tiles_per_block(L):
     assert autotune.tile_size(cfgs, {"tiles_per_block": 1, "blocks_per_sm": 0, "block_threads": 384}) == 4352
 
 
+def test_cached_choice_and_the_table_budget(tmp_path, L):
+    """A cached choice is returned as it is to a caller that passed the gas
+    lists; a caller without them gets the library's table budget (it runs
+    on the mixtures it compiled)."""
+    cfgs = [bz.make_config(n_electrons=5000, real_collisions=10, e_over_n_Td=1.0) for _ in range(3)]
+    path = str(tmp_path / "cache.json")
+    choice = dict(autotune.DEFAULT, block_threads=768, smem_budget=autotune.ONE_BLOCK_BUDGET)
+    autotune.store_cache({"GPU|" + autotune.signature(cfgs): choice}, path)
+    with_gases = autotune.tune(None, [], cfgs, cache_path=path, gpu_name="GPU", gas_lists=[[], [], []])
+    assert with_gases["cached"] is True and with_gases["smem_budget"] == autotune.ONE_BLOCK_BUDGET
+    without = autotune.tune(None, [], cfgs, cache_path=path, gpu_name="GPU")
+    assert without["block_threads"] == 768 and without["smem_budget"] == 0
+
+
 @pytest.mark.gpu
 def test_tune_a_small_batch(tmp_path, L):
     ctx = bz.Context(0)
