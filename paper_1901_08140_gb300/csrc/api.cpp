@@ -164,12 +164,14 @@ uint32_t tile_size_for(uint64_t n, uint64_t blocks, uint64_t per_block)
 // Tiles over the swarms in `order` (swarm index, electrons), in that order.
 // Blocks take tiles in list order, so a launch ends when the last tiles
 // taken end.  Tiles keep the full size while a quarter of an even share of
-// the work left exceeds it, then shrink with the work left down to 256
-// electrons (guided self-scheduling): a block that runs out of tiles waits
-// at most about one short tile for the others, whatever the cost of the
-// electrons that happen to come last.
+// the work left exceeds it, then shrink with the work left down to
+// `min_tile` electrons (guided self-scheduling; the block's threads rounded
+// up to a multiple of 256, so that the last tiles still give every lane an
+// electron): a block that runs out of tiles waits at most about one short
+// tile for the others, whatever the cost of the electrons that happen to
+// come last.
 void guided_tiles(const std::vector<std::pair<uint32_t, uint64_t>> &order, uint32_t tile, uint64_t blocks,
-                  std::vector<uint4> *tiles)
+                  uint32_t min_tile, std::vector<uint4> *tiles)
 {
     uint64_t left = 0;
     for (const auto &w : order) left += w.second;
@@ -177,7 +179,7 @@ void guided_tiles(const std::vector<std::pair<uint32_t, uint64_t>> &order, uint3
     for (const auto &w : order)
         for (uint64_t s0 = 0; s0 < w.second;) {
             uint64_t want = left / (4 * blocks);
-            want = std::min<uint64_t>(std::max<uint64_t>((want + 255) / 256 * 256, 256), tile);
+            want = std::min<uint64_t>(std::max<uint64_t>((want + 255) / 256 * 256, min_tile), tile);
             const uint64_t c = std::min<uint64_t>(want, w.second - s0);
             tiles->push_back(make_uint4(w.first, (unsigned)s0, (unsigned)c, 0u));
             s0 += c;
@@ -699,7 +701,8 @@ bz_status bz_run_swarm(bz_ctx *ctx, const bz_mixture *mix, const bz_swarm_config
         ba.single = a;
         // equal tiles computed in the kernel: a tile list would have to be
         // copied from pageable memory, which waits for the stream's earlier work
-        const uint32_t tile = tile_size_for(n, grid64, 8);
+        // (at least one electron per thread of a block)
+        const uint32_t tile = std::max<uint32_t>(tile_size_for(n, grid64, 8), (uint32_t)(block + 255) / 256 * 256);
         const uint64_t n_tiles = (n + tile - 1) / tile;
         ba.n_tiles = (int32_t)n_tiles;
         ba.tile_size = tile;
@@ -970,7 +973,8 @@ bz_status bz_create_batch(bz_ctx *ctx, int32_t n, const bz_mixture *const *mixtu
     std::vector<std::pair<uint32_t, uint64_t>> work;
     for (int i : order) work.emplace_back((uint32_t)i, cfgs[i].n_electrons);
     std::vector<uint4> tiles;
-    guided_tiles(work, tile, (uint64_t)ctx->sm_count * bps, &tiles);
+    const uint32_t min_tile = std::min<uint32_t>((uint32_t)(b->block + 255) / 256 * 256, tile);
+    guided_tiles(work, tile, (uint64_t)ctx->sm_count * bps, min_tile, &tiles);
     b->n_tiles = (int)tiles.size();
     b->grid = std::min(ctx->sm_count * bps, b->n_tiles);
     // one device allocation for everything
