@@ -122,6 +122,15 @@ def _measure(ctx, mixtures, cfgs, choice, sm_count, repeats=2) -> float:
     return best
 
 
+def _try_measure(ctx, mixtures, cfgs, choice, sm_count) -> float:
+    """_measure, or 0 for a candidate the library rejects (for example a
+    block size whose tables cannot be resident)."""
+    try:
+        return _measure(ctx, mixtures, cfgs, choice, sm_count)
+    except bz.BzError:
+        return 0.0
+
+
 def tune(ctx, mixtures: Sequence, cfgs: Sequence[bz.bz_swarm_config], scale: float = 0.5,
          use_cache: bool = True, cache_path: str = CACHE, gpu_name: Optional[str] = None,
          margin: float = 0.02, gas_lists: Optional[Sequence] = None) -> dict:
@@ -162,7 +171,7 @@ def tune(ctx, mixtures: Sequence, cfgs: Sequence[bz.bz_swarm_config], scale: flo
             if v == best[name]:
                 continue
             cand = dict(best, **{name: v})
-            r = _measure(ctx, mixtures, small, cand, sm_count)
+            r = _try_measure(ctx, mixtures, small, cand, sm_count)
             if r > best_rate * (1.0 + margin):
                 best, best_rate = cand, r
     big = None
@@ -170,7 +179,7 @@ def tune(ctx, mixtures: Sequence, cfgs: Sequence[bz.bz_swarm_config], scale: flo
         # one block of 768 threads per SM with tables compiled for it
         big = mixtures_for(ctx, gas_lists, {"smem_budget": ONE_BLOCK_BUDGET})
         cand = dict(best, block_threads=768, blocks_per_sm=0, smem_budget=ONE_BLOCK_BUDGET)
-        r = _measure(ctx, big, small, cand, sm_count)
+        r = _try_measure(ctx, big, small, cand, sm_count)
         if r > best_rate * (1.0 + margin):
             best, best_rate = cand, r
     best["rate_per_ms_reduced"] = best_rate
