@@ -506,7 +506,7 @@ def sweep_run(ctx, stream, flush, world, dev, args, rank):
     return {"workload": sweep_name(args), "value": reals / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
             "plain": {"value": preals / (pms / 1e3), "ms_per_step": pms / 2},
             "batched_over_plain": (reals / ms) / (preals / pms),
-            "autotuned": {k: choice.get(k) for k in ("window_c", "tiles_per_block", "blocks_per_sm", "channels_in_l2", "block_threads", "smem_budget", "cached")},
+            "autotuned": {k: choice.get(k) for k in ("window_c", "tiles_per_block", "blocks_per_sm", "channels_in_l2", "block_threads", "smem_budget", "rate_per_ms", "default_rate_per_ms", "cached")},
             "_tallies": tallies, "_kern_ms": kern / steps, "_specs": specs}
 
 
@@ -883,7 +883,7 @@ def run_ours(args):
                                                         {k: r["choice"].get(k, 0) for k in
                                                          ("block_threads", "smem_budget")}),
                 "clocks": clk, "gpu_launches": 5 * args.steps,
-                "autotuned": {k: r["choice"].get(k) for k in ("window_c", "tiles_per_block", "blocks_per_sm", "channels_in_l2", "block_threads", "smem_budget", "cached")},
+                "autotuned": {k: r["choice"].get(k) for k in ("window_c", "tiles_per_block", "blocks_per_sm", "channels_in_l2", "block_threads", "smem_budget", "rate_per_ms", "default_rate_per_ms", "cached")},
                 "trial_collisions_per_s": counts["trials"] * world / (t_max / 1e3),
                 "efficiency": counts["reals"] / counts["trials"] if counts["trials"] else None,
                 "window_restarts_per_real": (counts["windows"] - counts["reals"]) / counts["reals"]})
