@@ -355,8 +355,9 @@ void bz_destroy_swarm(bz_swarm *sw);
 typedef struct bz_batch bz_batch;
 
 typedef struct {
-    int32_t tile_particles;   /* electrons per tile at most (the last tiles shrink to 256 as the work left
-                                 runs out); <= 0: about 16 tiles per resident block */
+    int32_t tile_particles;   /* electrons per tile at most (the last tiles shrink as the work left runs out,
+                                 to 256 electrons or the block's threads rounded up to a multiple of 256);
+                                 <= 0: about 16 tiles per resident block */
     int32_t blocks_per_sm;    /* <= 0: as many as fit */
     int32_t use_graph;        /* 1: CUDA graph (default when opts is NULL), 0: plain launches */
     int32_t channels_in_l2;   /* table-staging policy: 1 = every mixture's channels are chosen from its cumulative
